@@ -1,0 +1,57 @@
+"""Planted mistakes: each mutation below is applied to a copy of the oracle
+source, compiled, and the pin suite (tests/test_oracle_pins.py) is run against
+it. Every mutation must make at least one pin fail, which shows the pins are
+not blind to that class of slip. The real oracle is never modified."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "gs_oracle.cpp")
+
+MUTATIONS = {
+    "no_dilation": ("const double kDilation = 0.3;", "const double kDilation = 0.0;"),
+    "conic_offdiag_sign": ("Q01 = -cov[0][1] / det", "Q01 = cov[0][1] / det"),
+    "quat_sign": ("R[0][1] = 2 * (x * y - w * z);", "R[0][1] = 2 * (x * y + w * z);"),
+    "camera_rotation_transposed": ("matmul3(cam.R, Sigma, tmp);\n        matmul3(tmp, Wt, Sc);",
+                                   "matmul3(Wt, Sigma, tmp);\n        matmul3(tmp, cam.R, Sc);"),
+    "alpha_clamp": ("const double kAlphaMax = 0.99;", "const double kAlphaMax = 1.0;"),
+    "no_alpha_skip": ("if (alpha < kAlphaMin) continue;", "if (alpha <= 0.0) continue;"),
+    "stop_after_adding": ("if (Tn < kTMin) break;\n        for (int ch = 0; ch < 3; ++ch) o.c[ch] += rgb[3 * g + ch] * alpha * T;",
+                          "for (int ch = 0; ch < 3; ++ch) o.c[ch] += rgb[3 * g + ch] * alpha * T;\n        if (Tn < kTMin) break;"),
+    "rect_off_by_one": ("rect[2] = tile_coord(u + (double)r + (tw - 1), tw, tiles_x);",
+                        "rect[2] = tile_coord(u + (double)r + tw, tw, tiles_x);"),
+    "sh_sin_cos_swapped": ("if (m > 0) return std::sqrt(2.0) * K * std::cos(am * phi) * P;",
+                           "if (m > 0) return std::sqrt(2.0) * K * std::sin(am * phi) * P;"),
+    "sh_index": ("s += sh[(i * K + l * l + l + m) * 3 + ch]", "s += sh[(i * K + l * l + l - m) * 3 + ch]"),
+    "sort_ignores_depth": ("items.emplace_back(ty * tiles_x + tx, f32_bits(depth[i]), i);",
+                           "items.emplace_back(ty * tiles_x + tx, 0u, i);"),
+    "guard_band": ("const double kGuard = 1.3;", "const double kGuard = 1.6;"),
+    "eigen_floor": ("std::max(0.1, mid * mid - det)", "std::max(0.0, mid * mid - det)"),
+    "near_inclusive": ("if (!(t[2] > cam.near_z)) continue;", "if (!(t[2] >= cam.near_z)) continue;"),
+    "jacobian_sign": ("{0.0, cam.fy / t[2], -cam.fy * ry / t[2]}", "{0.0, cam.fy / t[2], cam.fy * ry / t[2]}"),
+    "pixel_centre": ("x + 0.5, y + 0.5, last - first", "x, y, last - first"),
+    "opacity_not_sigmoid": ("opacity[i] = 1.0 / (1.0 + std::exp(-opacity_logits[i]));",
+                            "opacity[i] = 1.0 / (1.0 + std::exp(opacity_logits[i]));"),
+    "colour_no_offset": ("rgb[3 * i + ch] = std::max(0.0, s + 0.5);", "rgb[3 * i + ch] = std::max(0.0, s);"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    src = open(SRC).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutated = tmp_path / "mut.cpp"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libmut.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+                           "-o", str(lib), str(mutated)])
+    env = dict(os.environ, GS_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught mutation {name}:\n{r.stdout[-2000:]}"
