@@ -1,0 +1,341 @@
+"""Forward-render throughput of the 3DGS rasterizer on one GB300.
+
+Default workload: the 1M-Gaussian clustered scene (SH degree 3) rendered at
+1920x1080 with 16x16 screen tiles, camera inside the scene. One step = one
+whole forward pass (project -> bin -> blend) through the public C ABI
+(gs_render) with the Gaussians resident in HBM.
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (the reference arm for this build).
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under
+torchrun, every rank renders its own frame stream (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "clustered_1m_1080p": "1M Gaussians (90% in 200 clusters, 10% uniform, 20 m box), SH3, "
+                          "1920x1080, 16x16 tiles, camera inside the scene",
+    "uniform_box_256": "10k Gaussians uniform in a box, SH0, 256x256, 16x16 tiles",
+}
+
+# FP32 operations per evaluated (pixel, Gaussian) pair that every evaluated
+# pair needs (offset 2, quadratic form 9, alpha 2, cutoff test 1), plus the
+# ones a blended pair adds (transmittance 2, stop test 1, colour 7); the
+# exponential is counted separately (SFU).
+FLOPS_PER_EVAL = 14
+FLOPS_PER_BLEND = 10
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.gpu, self.period = gpu_index, period_ms
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 f"-lms={self.period}", f"--id={self.gpu}"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("GS_BENCH_BACKEND") != "gloo" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:
+    """Time the FP64 oracle on the host cores rendering whole frames of the
+    same workload until about ``budget_s`` seconds have passed."""
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    frames, t0 = 0, time.perf_counter()
+    while True:
+        oracle.render(scene, cam)
+        frames += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or frames >= 50:
+            break
+    return {"value": frames / el, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{frames} whole frames of the same workload, FP64, OpenMP over tiles",
+            "seconds": round(el, 2)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the machine's host cores."""
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    from paper_2607_15951_gb300 import scenes
+    import oracle
+    oracle.build()
+    scene, cams = scenes.workload(args.workload)
+    cam = cams[0]
+    for _ in range(args.warmup if args.warmup < 3 else 1):
+        oracle.render(scene, cam)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.render(scene, cam)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * float(np.mean(times))
+    value = 1000.0 / ms
+    line = {"impl": "reference", "metric": "frames/s (1080p, 1M Gaussians, forward)",
+            "value": round(value, 4), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+            "cpu_baseline": {"value": round(value, 4), "unit": "frames/s",
+                             "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} whole frames (each step one frame)"},
+            "e2e": {"value": round(value, 4), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--workload", default="clustered_1m_1080p", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    import paper_2607_15951_gb300 as gs
+    from paper_2607_15951_gb300 import build as gbuild
+    from paper_2607_15951_gb300 import scenes
+    gbuild.build()
+
+    scene, cams = scenes.workload(args.workload)
+    cam = cams[0]
+    H, W = cam.height, cam.width
+    g = gs.scene_to_device(scene)
+    ctx = gs.Context(local)
+    rgb = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        gs.gs_render(ctx, g, scene.sh_degree, cam, rgb)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    gs.gs_sync_status(ctx)
+
+    # Algorithmic work of one frame (deterministic): evaluated and blended pairs.
+    aux = gs.render(ctx, g, scene.sh_degree, cam)
+    torch.cuda.synchronize()
+    n_eval_total = int(aux["n_eval"].to(torch.int64).sum().item())
+    stats = gs.gs_last_render_stats(ctx)
+    del aux
+
+    # Timed region: per-step CUDA events, L2 flushed between steps outside them.
+    gs.gs_set_stage_timing(ctx, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_sum = {}
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.1)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+        if i % 50 == 0 or i == args.steps - 1:
+            st = gs.gs_last_stage_times(ctx)   # synchronises on this step's events
+            for k, v in st.items():
+                stage_sum.setdefault(k, []).append(v)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clk = clocks.stop()
+    gs.gs_set_stage_timing(ctx, False)
+    gs.gs_sync_status(ctx)
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    dev_ms = max_over_ranks(dev_ms, world)
+    ms_per_step = dev_ms / args.steps
+    frames = args.steps * world
+    value = frames / (dev_ms / 1000.0)
+    stage_ms = {k: float(np.median(v)) for k, v in stage_sum.items()}
+
+    # End to end: pinned host inputs copied in and the image copied out, every step.
+    host = {k: v.cpu().pin_memory() for k, v in g.items()}
+    dev_in = {k: torch.empty_like(v) for k, v in g.items()}
+    host_rgb = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = host_rgb.numel() * 4
+    for _ in range(3):
+        for k in host:
+            dev_in[k].copy_(host[k], non_blocking=True)
+        gs.gs_render(ctx, dev_in, scene.sh_degree, cam, rgb)
+        host_rgb.copy_(rgb, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        for k in host:
+            dev_in[k].copy_(host[k], non_blocking=True)
+        gs.gs_render(ctx, dev_in, scene.sh_degree, cam, rgb)
+        host_rgb.copy_(rgb, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_value = args.e2e_steps * world / (e2e_ms / 1000.0)
+
+    # Roofline of the dominant kernel (blend): FP32 work per launch / its time.
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_clock = (clk.get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0)
+    fp32_peak_tflops = sms * 128 * 2 * sm_clock * 1e6 / 1e12
+    blend_ms = stage_ms.get("blend_ms", float("nan"))
+    flops = FLOPS_PER_EVAL * n_eval_total
+    achieved = flops / (blend_ms / 1e3) / 1e12
+    roofline = {"kernel": "gs_blend", "bound": "alu", "achieved": round(achieved, 3),
+                "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak_tflops, 4), "traffic": None,
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_clock:.0f} MHz",
+                "units_per_launch": n_eval_total, "flops_per_unit": FLOPS_PER_EVAL,
+                "launch_ms": round(blend_ms, 4)}
+
+    line = {
+        "metric": "frames/s (1080p, 1M Gaussians, forward)",
+        "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "n_visible": stats["n_visible"], "n_keys": stats["n_keys"],
+                   "key_bits": stats["key_bits"]},
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "wall_s_timed_loop": round(wall, 3),
+        "e2e": {"value": round(e2e_value, 3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps},
+        "gpu_launches": None,
+        "roofline": roofline,
+        "peaks": {"source": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
+        "clocks": clk,
+    }
+    # Kernel launches per gs_render: project, scan, emit, histogram, one per
+    # digit pass, ranges, blend.
+    passes = (stats["key_bits"] + 7) // 8
+    per_step = 6 + passes
+    line["gpu_launches"] = per_step * args.steps
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, cam)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * gs.h — C ABI of the GB300 3D Gaussian Splatting forward rasterizer.
+ *
+ * The library renders the standard 3DGS formulation that the paper
+ * re-implements on an IPU (Sec. 3.1): cull and project every Gaussian,
+ * order Gaussians by depth per screen tile, and alpha-composite each pixel
+ * front to back with Eq. 1. Here the per-tile depth order comes from one
+ * global radix sort of 64-bit (tile id, depth) keys, as in the original GPU
+ * implementation the paper describes in Sec. 3.1, and each screen tile is
+ * blended by one CUDA thread block.
+ *
+ * Conventions for every entry point:
+ *  - Every array argument is a DEVICE pointer unless its comment says "host".
+ *    The caller allocates and owns all input and output buffers; the library
+ *    owns only the scratch workspace inside a gs_context.
+ *  - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *    as void*, NULL = legacy default stream) unless their comment says they
+ *    synchronise. GS_OK means "validated and launched".
+ *  - Errors are returned, never thrown or aborted on. Invalid arguments are
+ *    detected on the host before any launch. Errors that only the device can
+ *    see (a bounded wait that gave up, a count above a buffer's capacity) set
+ *    an error word in the context; gs_sync_status() reports it, and so does
+ *    the next synchronising call on the same context.
+ *  - A context may be used from one host thread at a time.
+ *  - Layouts: Gaussians are structure-of-arrays FP32; images are row-major
+ *    height x width, colour images HWC (3 floats per pixel).
+ *  - Pixel (i, j) covers [i, i+1) x [j, j+1) in image coordinates and is
+ *    sampled at its centre (i + 0.5, j + 0.5). Camera frame: x right,
+ *    y down, z forward.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* a null pointer, a size or an option out of range  */
+    GS_ERR_CUDA = 2,        /* a CUDA runtime call failed; see gs_last_error()    */
+    GS_ERR_OOM = 3,         /* the workspace could not grow                        */
+    GS_ERR_CAPACITY = 4,    /* an output buffer is smaller than the result         */
+    GS_ERR_TIMEOUT = 5,     /* a device-side bounded wait gave up                  */
+    GS_ERR_UNSUPPORTED = 6  /* a valid request this build does not implement       */
+} gs_status;
+
+typedef struct gs_context gs_context;
+
+/* The scene: n Gaussians (Sec. 3.1: mean, covariance from a rotation and a
+ * diagonal scale, opacity, SH colour). All pointers are device FP32.
+ *   means          n x 3 world-space means
+ *   log_scales     n x 3 per-axis log standard deviations (S = diag(exp(.)))
+ *   quats          n x 4 rotation quaternions (w, x, y, z); normalised inside
+ *   opacity_logits n     opacity = 1 / (1 + exp(-logit))
+ *   sh             n x (sh_degree+1)^2 x 3 real SH coefficients (coefficient
+ *                  k = l^2 + l + m, real basis with the Condon-Shortley
+ *                  phase), colour = max(0, sum_k c_k Y_k(dir) + 0.5) with
+ *                  dir the unit vector from the camera centre to the mean. */
+typedef struct {
+    const float *means;
+    const float *log_scales;
+    const float *quats;
+    const float *opacity_logits;
+    const float *sh;
+    int64_t n;         /* 0 <= n < 2^31                                        */
+    int32_t sh_degree; /* 0 .. 3                                               */
+} gs_gaussians;
+
+/* Pinhole camera (host struct). world_to_cam is the 3x4 row-major [R | t]
+ * mapping world points to camera space. A point projects to
+ * (fx x/z + cx, fy y/z + cy). Gaussians with camera z <= near_z are culled
+ * (Sec. 4.5 step 1). */
+typedef struct {
+    float world_to_cam[12];
+    float fx, fy, cx, cy;
+    int32_t width, height; /* 1 .. 16384                                       */
+    float near_z;          /* > 0; 0.2 in the standard formulation             */
+} gs_camera;
+
+/* Per-Gaussian projected record written by gs_project (48 bytes, 16-byte
+ * aligned). Only records of visible Gaussians (tiles[i] > 0, see gs_project)
+ * are written; the others keep whatever the buffer held. */
+typedef struct {
+    float mean2d[2];  /* projected mean in pixels                              */
+    float conic[3];   /* (Q00, Q01, Q11) of the inverse 2D covariance          */
+    float opacity;    /* sigmoid(logit)                                        */
+    float rgb[3];     /* SH colour                                             */
+    float depth;      /* camera-space z; the sort key uses its FP32 bits       */
+    int32_t radius;   /* ceil(3 sqrt(lambda_max)) in pixels (clamped to 2^30)  */
+    uint32_t tiles;   /* number of screen tiles in the record's tile rect      */
+} gs_record;
+
+/* Output images (device). rgb is required; the others may be NULL.
+ *   rgb        height x width x 3  C + T_final * bg
+ *   final_T    height x width      transmittance left after blending
+ *   n_contrib  height x width      1-based position, in the pixel's tile
+ *                                  list, of the last Gaussian blended (0: none)
+ *   n_eval     height x width      list entries evaluated by the pixel,
+ *                                  including the one that stopped it */
+typedef struct {
+    float *rgb;
+    float *final_T;
+    int32_t *n_contrib;
+    int32_t *n_eval;
+} gs_framebuffer;
+
+/* Options. gs_default_options() fills the standard values. */
+typedef struct {
+    int32_t tile_w, tile_h; /* screen tile: 16x16 (default), 16x8 or 8x8      */
+    float bg[3];            /* background colour added as T_final * bg         */
+    int32_t record_dtype;   /* 0 = FP32 records (only value in this version)   */
+    int32_t reserved[7];    /* must be zero                                    */
+} gs_options;
+
+void gs_default_options(gs_options *opts /* host */);
+
+/* Context: owns the scratch workspace (grown on demand) and the device error
+ * word, bound to one CUDA device. */
+gs_status gs_create(gs_context **ctx /* host out */, int device);
+void gs_destroy(gs_context *ctx);
+/* Message of the last failing call on this context (host string, valid until
+ * the next call on the context). */
+const char *gs_last_error(const gs_context *ctx);
+/* Synchronises the given stream, then returns and clears the device error
+ * word (GS_ERR_TIMEOUT / GS_ERR_CAPACITY) or a pending CUDA error. */
+gs_status gs_sync_status(gs_context *ctx, void *stream);
+/* Bytes of device workspace the context currently holds. */
+size_t gs_workspace_bytes(const gs_context *ctx);
+
+/* Stage 1 — projection (Sec. 3.1 stages 1-2; square 3-sigma bound of
+ * Sec. 4.4; near-plane cull of Sec. 4.5 step 1).
+ *   records  n x gs_record, 16-byte aligned: written for visible Gaussians
+ *   tiles    n x u32: number of screen tiles the Gaussian's rect covers, 0 for
+ *            a culled Gaussian (behind the near plane, degenerate, or with an
+ *            empty rect); always written. */
+gs_status gs_project(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
+                     const gs_options *opts, gs_record *records, uint32_t *tiles, void *stream);
+
+/* Stage 2 — binning (Sec. 3.1 stage 3; Sec. 4.5 step 2). Every record i with
+ * tiles[i] > 0 is listed once in each tile of its rect
+ *   columns [floor((u - r) / tw), floor((u + r + tw - 1) / tw)),
+ *   rows    [floor((v - r) / th), floor((v + r + th - 1) / th)),
+ * clamped to the tile grid, and the lists are ordered by
+ * (tile id, FP32 bits of depth, record index). tiles[i] must equal the
+ * rect's area (as gs_project writes it); a record where it does not is
+ * skipped and flagged (GS_ERR_INVALID_ARG from gs_sync_status).
+ *   keys     capacity x u64   out: tile << 32 | bits(depth), ascending
+ *   values   capacity x u32   out: record index
+ *   ranges   tiles x 2 x u32  out: [first, last+1) per tile, (0, 0) if empty,
+ *                             tiles = ceil(W / tw) * ceil(H / th), row-major
+ *   n_keys   host out: the number of pairs K.
+ * SYNCHRONISES the stream once to read K. If K > capacity nothing is
+ * written past the buffers, *n_keys holds K and GS_ERR_CAPACITY is
+ * returned. */
+gs_status gs_bin(gs_context *ctx, const gs_record *records, const uint32_t *tiles, int64_t n,
+                 const gs_camera *cam,
+                 const gs_options *opts, uint64_t *keys, uint32_t *values, int64_t capacity,
+                 uint32_t *ranges, int64_t *n_keys, void *stream);
+
+/* Stable ascending sort of n (key, value) pairs on the low key_bits bits of
+ * the keys (1 .. 64), in place. Least-significant-digit radix sort with
+ * 8-bit digits, one pass per digit, each pass a single launch that chains
+ * per-block digit counts by decoupled look-back (Onesweep, Adinets and
+ * Merrill 2022). Bits above key_bits must be zero. */
+gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *values, int64_t n,
+                        int32_t key_bits, void *stream);
+
+/* Per-tile [first, last+1) ranges of n sorted keys (tile id = key >> 32).
+ * ranges: n_tiles x 2 x u32, fully overwritten ((0, 0) for empty tiles). */
+gs_status gs_tile_ranges(gs_context *ctx, const uint64_t *keys, int64_t n, int32_t n_tiles,
+                         uint32_t *ranges, void *stream);
+
+/* Stage 3 — blending (Eq. 1; Sec. 4.5 step 3). For each pixel, front to back
+ * over its tile's list values[ranges[2t] .. ranges[2t+1]):
+ *   power = -(Q00 dx^2 + Q11 dy^2) / 2 - Q01 dx dy, d = pixel centre - mean2d;
+ *   skip if power > 0; alpha = min(0.99, opacity * exp(power));
+ *   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4 (that
+ *   Gaussian is not added); C += rgb alpha T; T = T'.
+ * records/values/ranges as produced by gs_project / gs_bin. */
+gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *values,
+                   const uint32_t *ranges, const gs_camera *cam, const gs_options *opts,
+                   const gs_framebuffer *fb, void *stream);
+
+/* Whole forward pass: gs_project -> gs_bin -> gs_blend on workspace owned by
+ * the context. SYNCHRONISES once (to size the key buffers). */
+gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
+                    const gs_options *opts, const gs_framebuffer *fb, void *stream);
+
+/* Statistics of the last gs_render on this context (host out). */
+typedef struct {
+    int64_t n_visible; /* records with radius > 0                              */
+    int64_t n_keys;    /* (tile, Gaussian) pairs K                             */
+    int32_t key_bits;  /* significant key bits sorted                          */
+    int32_t n_tiles;
+} gs_render_stats;
+gs_status gs_last_render_stats(const gs_context *ctx, gs_render_stats *out);
+
+/* Per-stage device times of gs_render, measured with CUDA events recorded on
+ * the render stream between the stages (tracing; off by default). */
+typedef struct {
+    float project_ms; /* gs_project kernel                                      */
+    float scan_ms;    /* tile-count scan                                        */
+    float host_ms;    /* gap while the host reads K and sizes the key buffers   */
+    float emit_ms;    /* key emission                                           */
+    float sort_ms;    /* histogram + digit passes                               */
+    float ranges_ms;  /* per-tile ranges                                        */
+    float blend_ms;   /* gs_blend kernel                                        */
+    float total_ms;   /* first event to last                                    */
+} gs_stage_times;
+/* enable != 0 turns per-stage events on for later gs_render calls. */
+gs_status gs_set_stage_timing(gs_context *ctx, int enable);
+/* Times of the last gs_render made with timing on; SYNCHRONISES on its last
+ * event. GS_ERR_INVALID_ARG if no timed render happened yet. */
+gs_status gs_last_stage_times(gs_context *ctx, gs_stage_times *out /* host */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -1,0 +1,237 @@
+"""GB300 rasterizer for standard 3D Gaussian Splatting (forward pass).
+
+Python binding of the C ABI in include/gs.h. Functions carry the C names
+(``gs_render``, ``gs_project``, ``gs_bin``, ...) and only marshal arguments:
+torch tensors become device pointers, the current torch CUDA stream becomes
+the ``cudaStream_t``, and non-zero statuses become ``GSError``. Every step of
+the pipeline runs in the CUDA kernels of libgs.so; if the library is not
+built, importing the binding's entry points raises.
+
+Torch is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _native as N
+
+__all__ = ["GSError", "Context", "camera_struct", "options_struct", "gaussians_struct",
+           "gs_create", "gs_destroy", "gs_project", "gs_bin", "gs_sort_pairs", "gs_tile_ranges",
+           "gs_blend", "gs_render", "gs_sync_status", "gs_last_render_stats",
+           "gs_set_stage_timing", "gs_last_stage_times", "RECORD_FLOATS"]
+
+RECORD_FLOATS = 12  # gs_record is 48 bytes = 12 x 4-byte words
+
+
+class GSError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{N.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _lib():
+    return N.load()
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def _stream(stream) -> int | None:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def camera_struct(cam) -> N.gs_camera:
+    """gs_camera from any object with world_to_cam (3x4), fx, fy, cx, cy,
+    width, height, near_z (e.g. ``scenes.Camera``)."""
+    import numpy as np
+    c = N.gs_camera()
+    w2c = np.asarray(cam.world_to_cam, dtype=np.float32).reshape(12)
+    for i in range(12):
+        c.world_to_cam[i] = float(w2c[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.near_z = float(getattr(cam, "near_z", 0.2))
+    return c
+
+
+def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0) -> N.gs_options:
+    o = N.gs_options()
+    _lib().gs_default_options(ctypes.byref(o))
+    o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
+    for i in range(3):
+        o.bg[i] = float(bg[i])
+    o.record_dtype = int(record_dtype)
+    return o
+
+
+def gaussians_struct(g: dict, sh_degree: int) -> N.gs_gaussians:
+    """gs_gaussians from a dict of contiguous float32 CUDA tensors with keys
+    means, log_scales, quats, opacity_logits, sh."""
+    s = N.gs_gaussians()
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        t = g[k]
+        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32", k
+        setattr(s, k, _ptr(t))
+    s.n = int(g["means"].shape[0])
+    s.sh_degree = int(sh_degree)
+    return s
+
+
+class Context:
+    """Owns one gs_context (workspace + device error word)."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        dev = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        st = _lib().gs_create(ctypes.byref(h), dev)
+        if st != N.GS_OK:
+            raise GSError(st, "gs_create failed")
+        self.handle = h
+        self.device = dev
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().gs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status: int):
+        if status != N.GS_OK:
+            msg = _lib().gs_last_error(self.handle)
+            raise GSError(status, msg.decode() if msg else "")
+
+    def workspace_bytes(self) -> int:
+        return int(_lib().gs_workspace_bytes(self.handle))
+
+
+# ---------------------------------------------------------------------------
+# Entry points (C names)
+# ---------------------------------------------------------------------------
+
+def gs_create(device: int | None = None) -> Context:
+    return Context(device)
+
+
+def gs_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def gs_sync_status(ctx: Context, stream=None) -> None:
+    ctx.check(_lib().gs_sync_status(ctx.handle, _stream(stream)))
+
+
+def gs_project(ctx: Context, g: dict, sh_degree: int, cam, records, tiles, *, tile=(16, 16),
+               stream=None) -> None:
+    """records: (n, 12) float32 CUDA tensor (gs_record words); tiles: (n,) int32."""
+    gs = gaussians_struct(g, sh_degree)
+    c, o = camera_struct(cam), options_struct(tile)
+    ctx.check(_lib().gs_project(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
+                                _ptr(records), _ptr(tiles), _stream(stream)))
+
+
+def gs_bin(ctx: Context, records, tiles, n: int, cam, keys, values, ranges, *, tile=(16, 16),
+           stream=None) -> int:
+    """Returns K; raises GSError(GS_ERR_CAPACITY) with K in ``.n_keys`` if the
+    key/value tensors are too small."""
+    c, o = camera_struct(cam), options_struct(tile)
+    nk = ctypes.c_int64(0)
+    cap = 0 if keys is None else int(keys.numel())
+    st = _lib().gs_bin(ctx.handle, _ptr(records), _ptr(tiles), int(n), ctypes.byref(c),
+                       ctypes.byref(o), _ptr(keys), _ptr(values), cap, _ptr(ranges),
+                       ctypes.byref(nk), _stream(stream))
+    if st != N.GS_OK:
+        msg = _lib().gs_last_error(ctx.handle)
+        err = GSError(st, msg.decode() if msg else "")
+        err.n_keys = int(nk.value)
+        raise err
+    return int(nk.value)
+
+
+def gs_sort_pairs(ctx: Context, keys, values, n: int, key_bits: int, stream=None) -> None:
+    ctx.check(_lib().gs_sort_pairs(ctx.handle, _ptr(keys), _ptr(values), int(n), int(key_bits),
+                                   _stream(stream)))
+
+
+def gs_tile_ranges(ctx: Context, keys, n: int, n_tiles: int, ranges, stream=None) -> None:
+    ctx.check(_lib().gs_tile_ranges(ctx.handle, _ptr(keys), int(n), int(n_tiles), _ptr(ranges),
+                                    _stream(stream)))
+
+
+def _fb(rgb, final_T=None, n_contrib=None, n_eval=None) -> N.gs_framebuffer:
+    fb = N.gs_framebuffer()
+    fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval = (_ptr(rgb), _ptr(final_T), _ptr(n_contrib),
+                                                   _ptr(n_eval))
+    return fb
+
+
+def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_contrib=None,
+             n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), stream=None) -> None:
+    c, o = camera_struct(cam), options_struct(tile, bg)
+    fb = _fb(rgb, final_T, n_contrib, n_eval)
+    ctx.check(_lib().gs_blend(ctx.handle, _ptr(records), _ptr(values), _ptr(ranges),
+                              ctypes.byref(c), ctypes.byref(o), ctypes.byref(fb), _stream(stream)))
+
+
+def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
+              n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), stream=None) -> None:
+    gs = gaussians_struct(g, sh_degree)
+    c, o = camera_struct(cam), options_struct(tile, bg)
+    fb = _fb(rgb, final_T, n_contrib, n_eval)
+    ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
+                               ctypes.byref(fb), _stream(stream)))
+
+
+def gs_last_render_stats(ctx: Context) -> dict:
+    s = N.gs_render_stats()
+    ctx.check(_lib().gs_last_render_stats(ctx.handle, ctypes.byref(s)))
+    return {"n_visible": s.n_visible, "n_keys": s.n_keys, "key_bits": s.key_bits,
+            "n_tiles": s.n_tiles}
+
+
+def gs_set_stage_timing(ctx: Context, enable: bool) -> None:
+    ctx.check(_lib().gs_set_stage_timing(ctx.handle, 1 if enable else 0))
+
+
+def gs_last_stage_times(ctx: Context) -> dict:
+    t = N.gs_stage_times()
+    ctx.check(_lib().gs_last_stage_times(ctx.handle, ctypes.byref(t)))
+    return {name: float(getattr(t, name)) for name, _ in N.gs_stage_times._fields_}
+
+
+# ---------------------------------------------------------------------------
+# Convenience (still marshalling only)
+# ---------------------------------------------------------------------------
+
+def scene_to_device(scene, device="cuda") -> dict:
+    """Copy a ``scenes.Scene`` to contiguous float32 CUDA tensors."""
+    import torch
+    return {k: torch.from_numpy(v).to(device=device, dtype=torch.float32).contiguous()
+            for k, v in scene.arrays().items()}
+
+
+def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
+           aux: bool = True, stream=None) -> dict:
+    """Allocate outputs with torch and call gs_render."""
+    import torch
+    H, W = int(cam.height), int(cam.width)
+    dev = g["means"].device
+    out = {"rgb": torch.empty((H, W, 3), dtype=torch.float32, device=dev)}
+    if aux:
+        out["final_T"] = torch.empty((H, W), dtype=torch.float32, device=dev)
+        out["n_contrib"] = torch.empty((H, W), dtype=torch.int32, device=dev)
+        out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
+    gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
+              out.get("n_eval"), tile=tile, bg=bg, stream=stream)
+    return out

@@ -1,0 +1,465 @@
+// gs_api.cu — the C ABI (include/gs.h): argument validation, the context
+// and its grow-only workspace, and the launch sequences of each entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+// Grow-only device buffer.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct gs_context {
+    int device = 0;
+    std::string last_error;
+    uint32_t *d_err = nullptr;               // device error word
+    unsigned long long *d_counts = nullptr;  // [K, n_visible]
+    unsigned long long *h_counts = nullptr;  // pinned mirror of d_counts
+    uint32_t *h_err = nullptr;               // pinned mirror of d_err
+    DevBuf records, tiles, offsets, scan_scratch, keys, values, alt_keys, alt_values, sort_scratch,
+        ranges;
+    gs_render_stats stats{};
+    bool timing = false;
+    bool timed_once = false;
+    cudaEvent_t ev[8] = {};
+};
+
+namespace {
+
+gs_status fail(gs_context *ctx, gs_status st, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+gs_status cuda_fail(gs_context *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, GS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GS_CUDA(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+gs_status ensure(gs_context *ctx, DevBuf &b, size_t bytes, const char *what) {
+    if (bytes <= b.bytes) return GS_OK;
+    size_t want = bytes + bytes / 4 + 256;
+    if (b.ptr) {
+        cudaError_t e = cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree");
+    }
+    cudaError_t e = cudaMalloc(&b.ptr, want);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, GS_ERR_OOM, std::string("cannot allocate ") + std::to_string(want) +
+                                         " bytes for " + what);
+    }
+    b.bytes = want;
+    return GS_OK;
+}
+
+bool finite(float v) { return std::isfinite(v); }
+
+gs_status check_camera(gs_context *ctx, const gs_camera *cam) {
+    if (!cam) return fail(ctx, GS_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+        return fail(ctx, GS_ERR_INVALID_ARG, "camera width/height must be in 1..16384");
+    if (!(cam->fx > 0) || !(cam->fy > 0) || !finite(cam->fx) || !finite(cam->fy) ||
+        !finite(cam->cx) || !finite(cam->cy))
+        return fail(ctx, GS_ERR_INVALID_ARG, "camera intrinsics must be finite with fx, fy > 0");
+    if (!(cam->near_z > 0) || !finite(cam->near_z))
+        return fail(ctx, GS_ERR_INVALID_ARG, "camera near_z must be finite and > 0");
+    for (int i = 0; i < 12; ++i)
+        if (!finite(cam->world_to_cam[i]))
+            return fail(ctx, GS_ERR_INVALID_ARG, "camera world_to_cam must be finite");
+    return GS_OK;
+}
+
+gs_status check_options(gs_context *ctx, const gs_options *o) {
+    if (!o) return fail(ctx, GS_ERR_INVALID_ARG, "options are NULL");
+    const bool ok_tile = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 16 && o->tile_h == 8) ||
+                         (o->tile_w == 8 && o->tile_h == 8);
+    if (!ok_tile) return fail(ctx, GS_ERR_INVALID_ARG, "tile must be 16x16, 16x8 or 8x8");
+    if (o->record_dtype != 0)
+        return fail(ctx, GS_ERR_UNSUPPORTED, "record_dtype must be 0 (FP32) in this version");
+    for (int i = 0; i < 7; ++i)
+        if (o->reserved[i] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
+    for (int i = 0; i < 3; ++i)
+        if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
+    return GS_OK;
+}
+
+gs_status check_gaussians(gs_context *ctx, const gs_gaussians *g) {
+    if (!g) return fail(ctx, GS_ERR_INVALID_ARG, "gaussians are NULL");
+    if (g->n < 0 || g->n >= (int64_t(1) << 31))
+        return fail(ctx, GS_ERR_INVALID_ARG, "n must be in 0 .. 2^31-1");
+    if (g->sh_degree < 0 || g->sh_degree > 3)
+        return fail(ctx, GS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return fail(ctx, GS_ERR_INVALID_ARG, "a Gaussian array is NULL");
+    return GS_OK;
+}
+
+GsGrid make_grid(const gs_camera *cam, const gs_options *o) {
+    GsGrid gr;
+    gr.tile_w = o->tile_w;
+    gr.tile_h = o->tile_h;
+    gr.tiles_x = (cam->width + o->tile_w - 1) / o->tile_w;
+    gr.tiles_y = (cam->height + o->tile_h - 1) / o->tile_h;
+    return gr;
+}
+
+GsCameraDev make_cam(const gs_camera *c) {
+    GsCameraDev k;
+    for (int r = 0; r < 3; ++r) {
+        for (int j = 0; j < 3; ++j) k.R[3 * r + j] = c->world_to_cam[4 * r + j];
+        k.t[r] = c->world_to_cam[4 * r + 3];
+    }
+    for (int j = 0; j < 3; ++j)  // C = -R^T t (in double, then rounded)
+        k.C[j] = (float)-((double)k.R[j] * k.t[0] + (double)k.R[3 + j] * k.t[1] +
+                          (double)k.R[6 + j] * k.t[2]);
+    k.fx = c->fx;
+    k.fy = c->fy;
+    k.cx = c->cx;
+    k.cy = c->cy;
+    k.near_z = c->near_z;
+    k.lim_x = gs::kGuard * (0.5f * c->width / c->fx);
+    k.lim_y = gs::kGuard * (0.5f * c->height / c->fy);
+    k.width = c->width;
+    k.height = c->height;
+    return k;
+}
+
+int key_bits_for(int n_tiles) {
+    int b = 0;
+    while ((1ll << b) < n_tiles) ++b;
+    return 32 + b;
+}
+
+// Reads the device error word after a synchronisation point.
+gs_status collect_device_error(gs_context *ctx, cudaStream_t s) {
+    GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(ctx, cudaStreamSynchronize(s));
+    const uint32_t w = *ctx->h_err;
+    if (w == 0) return GS_OK;
+    GS_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s));
+    if (w & gs::kErrTimeout)
+        return fail(ctx, GS_ERR_TIMEOUT, "a device-side wait gave up (look-back timeout)");
+    if (w & gs::kErrCapacity) return fail(ctx, GS_ERR_CAPACITY, "a device buffer was too small");
+    return fail(ctx, GS_ERR_INVALID_ARG, "records inconsistent with their tile counts");
+}
+
+enum { EV_START, EV_PROJECT, EV_SCAN, EV_EMIT0, EV_EMIT, EV_SORT, EV_RANGES, EV_BLEND, EV_COUNT };
+
+void mark(gs_context *ctx, int which, cudaStream_t s) {
+    if (ctx->timing) cudaEventRecord(ctx->ev[which], s);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Scan + emit + sort + ranges into the given key/value buffers (which must
+// hold `capacity` pairs); the other pair of buffers comes from the context.
+gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *tiles, int64_t n,
+                   const GsGrid &grid, uint64_t *keys, uint32_t *values, int64_t capacity,
+                   bool capacity_is_ctx, uint32_t *ranges, int64_t *n_keys, cudaStream_t s) {
+    gs_status st;
+    const int n_tiles = grid.tiles_x * grid.tiles_y;
+    if ((st = ensure(ctx, ctx->offsets, (size_t)(n > 0 ? n : 1) * 8, "offsets")) != GS_OK) return st;
+    if ((st = ensure(ctx, ctx->scan_scratch, gs_scan_scratch_bytes(n), "scan scratch")) != GS_OK)
+        return st;
+    GS_CUDA(ctx, gs_launch_scan(tiles, n, static_cast<unsigned long long *>(ctx->offsets.ptr),
+                                ctx->d_counts, ctx->scan_scratch.ptr, ctx->d_err, s));
+    mark(ctx, EV_SCAN, s);
+    GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 2 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+    if ((st = collect_device_error(ctx, s)) != GS_OK) return st;
+    const unsigned long long K = ctx->h_counts[0];
+    *n_keys = (int64_t)K;
+    ctx->stats.n_visible = (int64_t)ctx->h_counts[1];
+    ctx->stats.n_keys = (int64_t)K;
+    ctx->stats.n_tiles = n_tiles;
+    ctx->stats.key_bits = key_bits_for(n_tiles);
+    if (K >= (1ull << 32) - 1)
+        return fail(ctx, GS_ERR_CAPACITY, "more than 2^32-2 (tile, Gaussian) pairs in one pass");
+    if (capacity_is_ctx) {
+        if ((st = ensure(ctx, ctx->keys, (K + 1) * 8, "keys")) != GS_OK) return st;
+        if ((st = ensure(ctx, ctx->values, (K + 1) * 4, "values")) != GS_OK) return st;
+        keys = static_cast<uint64_t *>(ctx->keys.ptr);
+        values = static_cast<uint32_t *>(ctx->values.ptr);
+        capacity = (int64_t)(K + 1);
+    } else if ((int64_t)K > capacity) {
+        return fail(ctx, GS_ERR_CAPACITY, "key buffer capacity " + std::to_string(capacity) +
+                                              " < " + std::to_string(K) + " pairs");
+    }
+    if ((st = ensure(ctx, ctx->alt_keys, (K + 1) * 8, "alt keys")) != GS_OK) return st;
+    if ((st = ensure(ctx, ctx->alt_values, (K + 1) * 4, "alt values")) != GS_OK) return st;
+    const int bits = key_bits_for(n_tiles);
+    if ((st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes((int64_t)K, bits), "sort scratch")) !=
+        GS_OK)
+        return st;
+    // Emit into whichever buffer makes the sorted result land in `keys`.
+    const bool odd = (gs_sort_passes(bits) & 1) != 0 && K > 1;
+    uint64_t *ek = odd ? static_cast<uint64_t *>(ctx->alt_keys.ptr) : keys;
+    uint32_t *ev = odd ? static_cast<uint32_t *>(ctx->alt_values.ptr) : values;
+    uint64_t *ok = odd ? keys : static_cast<uint64_t *>(ctx->alt_keys.ptr);
+    uint32_t *ov = odd ? values : static_cast<uint32_t *>(ctx->alt_values.ptr);
+    mark(ctx, EV_EMIT0, s);
+    GS_CUDA(ctx, gs_launch_emit(records, tiles, static_cast<unsigned long long *>(ctx->offsets.ptr), n,
+                                grid, ek, ev, (int64_t)K, ctx->d_err, s));
+    mark(ctx, EV_EMIT, s);
+    bool in_alt = false;
+    GS_CUDA(ctx, gs_launch_sort(ek, ev, ok, ov, (int64_t)K, bits, ctx->sort_scratch.ptr, ctx->d_err,
+                                &in_alt, s));
+    mark(ctx, EV_SORT, s);
+    (void)capacity;
+    GS_CUDA(ctx, gs_launch_ranges(keys, (int64_t)K, n_tiles, ranges, ctx->d_err, s));
+    mark(ctx, EV_RANGES, s);
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gs_default_options(gs_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tile_w = 16;
+    o->tile_h = 16;
+}
+
+gs_status gs_create(gs_context **out, int device) {
+    if (!out) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        (void)cudaGetLastError();
+        return GS_ERR_INVALID_ARG;
+    }
+    gs_context *ctx = new gs_context();
+    ctx->device = device;
+    DeviceGuard g(device);
+    if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess ||
+        cudaMalloc(&ctx->d_counts, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_counts, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
+        (void)cudaGetLastError();
+        gs_destroy(ctx);
+        return GS_ERR_CUDA;
+    }
+    *out = ctx;
+    return GS_OK;
+}
+
+void gs_destroy(gs_context *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
+                      &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges};
+    for (DevBuf *b : bufs)
+        if (b->ptr) cudaFree(b->ptr);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_counts) cudaFree(ctx->d_counts);
+    if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    for (int i = 0; i < EV_COUNT; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+}
+
+const char *gs_last_error(const gs_context *ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+gs_status gs_sync_status(gs_context *ctx, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GS_CUDA(ctx, cudaGetLastError());
+    return collect_device_error(ctx, s);
+}
+
+size_t gs_workspace_bytes(const gs_context *ctx) {
+    if (!ctx) return 0;
+    const DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
+                            &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch,
+                            &ctx->ranges};
+    size_t t = 0;
+    for (const DevBuf *b : bufs) t += b->bytes;
+    return t;
+}
+
+gs_status gs_project(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
+                     const gs_options *opts, gs_record *records, uint32_t *tiles, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    gs_status st;
+    if ((st = check_gaussians(ctx, g)) != GS_OK || (st = check_camera(ctx, cam)) != GS_OK ||
+        (st = check_options(ctx, opts)) != GS_OK)
+        return st;
+    if (g->n > 0 && (!records || !tiles))
+        return fail(ctx, GS_ERR_INVALID_ARG, "records/tiles are NULL");
+    if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
+    DeviceGuard dg(ctx->device);
+    GS_CUDA(ctx, gs_launch_project(*g, make_cam(cam), make_grid(cam, opts), records, tiles,
+                                   static_cast<cudaStream_t>(stream)));
+    return GS_OK;
+}
+
+gs_status gs_bin(gs_context *ctx, const gs_record *records, const uint32_t *tiles, int64_t n,
+                 const gs_camera *cam, const gs_options *opts, uint64_t *keys, uint32_t *values,
+                 int64_t capacity, uint32_t *ranges, int64_t *n_keys, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    gs_status st;
+    if ((st = check_camera(ctx, cam)) != GS_OK || (st = check_options(ctx, opts)) != GS_OK) return st;
+    if (!n_keys || !ranges || n < 0 || n >= (int64_t(1) << 31) || capacity < 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "bad n, capacity, ranges or n_keys");
+    if (n > 0 && (!records || !tiles)) return fail(ctx, GS_ERR_INVALID_ARG, "records/tiles are NULL");
+    if (capacity > 0 && (!keys || !values)) return fail(ctx, GS_ERR_INVALID_ARG, "keys/values are NULL");
+    if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
+    DeviceGuard dg(ctx->device);
+    *n_keys = 0;
+    st = bin_impl(ctx, records, tiles, n, make_grid(cam, opts), keys, values, capacity, false, ranges,
+                  n_keys, static_cast<cudaStream_t>(stream));
+    return st;
+}
+
+gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *values, int64_t n, int32_t key_bits,
+                        void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (n < 0 || n >= (int64_t(1) << 32) - 1 || key_bits < 1 || key_bits > 64)
+        return fail(ctx, GS_ERR_INVALID_ARG, "n must be in 0..2^32-2 and key_bits in 1..64");
+    if (n > 0 && (!keys || !values)) return fail(ctx, GS_ERR_INVALID_ARG, "keys/values are NULL");
+    if (n <= 1) return GS_OK;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    gs_status st;
+    if ((st = ensure(ctx, ctx->alt_keys, (size_t)n * 8, "alt keys")) != GS_OK) return st;
+    if ((st = ensure(ctx, ctx->alt_values, (size_t)n * 4, "alt values")) != GS_OK) return st;
+    if ((st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes(n, key_bits), "sort scratch")) != GS_OK)
+        return st;
+    bool in_alt = false;
+    GS_CUDA(ctx, gs_launch_sort(keys, values, static_cast<uint64_t *>(ctx->alt_keys.ptr),
+                                static_cast<uint32_t *>(ctx->alt_values.ptr), n, key_bits,
+                                ctx->sort_scratch.ptr, ctx->d_err, &in_alt, s));
+    if (in_alt) {
+        GS_CUDA(ctx, cudaMemcpyAsync(keys, ctx->alt_keys.ptr, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        GS_CUDA(ctx, cudaMemcpyAsync(values, ctx->alt_values.ptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    return GS_OK;
+}
+
+gs_status gs_tile_ranges(gs_context *ctx, const uint64_t *keys, int64_t n, int32_t n_tiles,
+                         uint32_t *ranges, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (n < 0 || n >= (int64_t(1) << 32) - 1 || n_tiles < 1 || !ranges || (n > 0 && !keys))
+        return fail(ctx, GS_ERR_INVALID_ARG, "bad keys, n, n_tiles or ranges");
+    DeviceGuard dg(ctx->device);
+    GS_CUDA(ctx, gs_launch_ranges(keys, n, n_tiles, ranges, ctx->d_err, static_cast<cudaStream_t>(stream)));
+    return GS_OK;
+}
+
+gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *values,
+                   const uint32_t *ranges, const gs_camera *cam, const gs_options *opts,
+                   const gs_framebuffer *fb, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    gs_status st;
+    if ((st = check_camera(ctx, cam)) != GS_OK || (st = check_options(ctx, opts)) != GS_OK) return st;
+    if (!fb || !fb->rgb || !ranges) return fail(ctx, GS_ERR_INVALID_ARG, "framebuffer rgb/ranges NULL");
+    if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
+    DeviceGuard dg(ctx->device);
+    GS_CUDA(ctx, gs_launch_blend(records, values, ranges, make_grid(cam, opts), cam->width, cam->height,
+                                 opts->bg, *fb, static_cast<cudaStream_t>(stream)));
+    return GS_OK;
+}
+
+gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
+                    const gs_options *opts, const gs_framebuffer *fb, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    gs_status st;
+    if ((st = check_gaussians(ctx, g)) != GS_OK || (st = check_camera(ctx, cam)) != GS_OK ||
+        (st = check_options(ctx, opts)) != GS_OK)
+        return st;
+    if (!fb || !fb->rgb) return fail(ctx, GS_ERR_INVALID_ARG, "framebuffer rgb is NULL");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const GsGrid grid = make_grid(cam, opts);
+    const int64_t n = g->n;
+    const size_t n_tiles = (size_t)grid.tiles_x * grid.tiles_y;
+    if ((st = ensure(ctx, ctx->records, (size_t)(n > 0 ? n : 1) * sizeof(gs_record), "records")) != GS_OK ||
+        (st = ensure(ctx, ctx->tiles, (size_t)(n > 0 ? n : 1) * 4, "tiles")) != GS_OK ||
+        (st = ensure(ctx, ctx->ranges, n_tiles * 8, "ranges")) != GS_OK)
+        return st;
+    gs_record *rec = static_cast<gs_record *>(ctx->records.ptr);
+    uint32_t *tiles = static_cast<uint32_t *>(ctx->tiles.ptr);
+    uint32_t *ranges = static_cast<uint32_t *>(ctx->ranges.ptr);
+    mark(ctx, EV_START, s);
+    GS_CUDA(ctx, gs_launch_project(*g, make_cam(cam), grid, rec, tiles, s));
+    mark(ctx, EV_PROJECT, s);
+    int64_t K = 0;
+    if ((st = bin_impl(ctx, rec, tiles, n, grid, nullptr, nullptr, 0, true, ranges, &K, s)) != GS_OK)
+        return st;
+    GS_CUDA(ctx, gs_launch_blend(rec, static_cast<uint32_t *>(ctx->values.ptr), ranges, grid, cam->width,
+                                 cam->height, opts->bg, *fb, s));
+    mark(ctx, EV_BLEND, s);
+    if (ctx->timing) ctx->timed_once = true;
+    return GS_OK;
+}
+
+gs_status gs_set_stage_timing(gs_context *ctx, int enable) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    if (enable && !ctx->ev[0])
+        for (int i = 0; i < EV_COUNT; ++i) GS_CUDA(ctx, cudaEventCreate(&ctx->ev[i]));
+    ctx->timing = enable != 0;
+    return GS_OK;
+}
+
+gs_status gs_last_stage_times(gs_context *ctx, gs_stage_times *out) {
+    if (!ctx || !out) return GS_ERR_INVALID_ARG;
+    if (!ctx->timed_once) return fail(ctx, GS_ERR_INVALID_ARG, "no timed gs_render yet");
+    DeviceGuard dg(ctx->device);
+    GS_CUDA(ctx, cudaEventSynchronize(ctx->ev[EV_BLEND]));
+    auto el = [&](int a, int b) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]);
+        return ms;
+    };
+    out->project_ms = el(EV_START, EV_PROJECT);
+    out->scan_ms = el(EV_PROJECT, EV_SCAN);
+    out->host_ms = el(EV_SCAN, EV_EMIT0);
+    out->emit_ms = el(EV_EMIT0, EV_EMIT);
+    out->sort_ms = el(EV_EMIT, EV_SORT);
+    out->ranges_ms = el(EV_SORT, EV_RANGES);
+    out->blend_ms = el(EV_RANGES, EV_BLEND);
+    out->total_ms = el(EV_START, EV_BLEND);
+    return GS_OK;
+}
+
+gs_status gs_last_render_stats(const gs_context *ctx, gs_render_stats *out) {
+    if (!ctx || !out) return GS_ERR_INVALID_ARG;
+    *out = ctx->stats;
+    return GS_OK;
+}
+
+}  // extern "C"

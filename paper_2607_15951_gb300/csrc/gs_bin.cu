@@ -1,0 +1,245 @@
+// gs_bin.cu — screen-tile binning (Sec. 3.1 stage 3; Sec. 4.5 step 2):
+// exclusive scan of per-Gaussian tile counts, emission of (tile, depth) keys,
+// and per-tile ranges of the sorted keys. The sort itself is gs_sort.cu.
+#include "gs_internal.cuh"
+
+namespace {
+
+using namespace gs;
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Warp-wide decoupled look-back over per-partition status words: returns
+// the sum of the values of all partitions before p. Lanes inspect 32
+// predecessors at a time; a window is consumed once every lane sees a
+// published flag, up to and including the nearest inclusive prefix.
+// Sets kErrTimeout (and returns a meaningless sum) if a predecessor stays
+// unpublished for kSpinTimeoutNs or another block already timed out.
+__device__ unsigned long long warp_lookback(const unsigned long long *status, long long p,
+                                            uint32_t *d_err, bool *timed_out) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long excl = 0;
+    long long q = p - 1;
+    const unsigned long long t0 = global_ns();
+    *timed_out = false;
+    while (true) {
+        const long long idx = q - lane;
+        const unsigned long long s = idx >= 0 ? ld_relaxed_u64(status + idx) : kFlagIncl;
+        if (!__all_sync(0xffffffffu, (s >> 62) != 0)) {
+            const bool give_up = (global_ns() - t0 > kSpinTimeoutNs) ||
+                                 (ld_relaxed_u32(d_err) & kErrTimeout);
+            if (__any_sync(0xffffffffu, give_up)) {
+                if (lane == 0) atomicOr(d_err, kErrTimeout);
+                *timed_out = true;
+                return excl;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        const uint32_t incl = __ballot_sync(0xffffffffu, (s >> 62) == 2);
+        const int first = incl ? __ffs(incl) - 1 : 31;
+        unsigned long long v = lane <= first ? (s & kValueMask) : 0ull;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (incl) return excl;
+        q -= 32;
+    }
+}
+
+// Single-pass exclusive scan of u32 counts into u64 offsets (decoupled
+// look-back; partitions taken in launch order from an atomic counter so a
+// block only ever waits on blocks that are already running).
+__global__ void __launch_bounds__(kScanThreads)
+scan_kernel(const uint32_t *__restrict__ in, int64_t n, unsigned long long *__restrict__ out,
+            unsigned long long *counts, uint32_t *counter, unsigned long long *status,
+            int64_t num_parts, uint32_t *d_err) {
+    __shared__ uint32_t s_part;
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_vis[kScanThreads / 32];
+    __shared__ unsigned long long s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_part = atomicAdd(counter, 1u);
+    __syncthreads();
+    const long long p = s_part;
+    const long long base = p * kScanTile + (long long)tid * kScanItems;
+
+    uint32_t v[kScanItems];
+    unsigned long long sum = 0;
+    uint32_t vis = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long idx = base + j;
+        v[j] = idx < n ? in[idx] : 0u;
+        sum += v[j];
+        vis += v[j] != 0u;
+    }
+    // Block-wide exclusive scan of the per-thread sums.
+    unsigned long long incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    for (int o = 16; o > 0; o >>= 1) vis += __shfl_xor_sync(0xffffffffu, vis, o);
+    if (lane == 31) s_warp[warp] = incl;
+    if (lane == 0) s_vis[warp] = vis;
+    __syncthreads();
+    unsigned long long warp_prefix = 0, block_total = 0;
+    uint32_t block_vis = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        if (w < warp) warp_prefix += s_warp[w];
+        block_total += s_warp[w];
+        block_vis += s_vis[w];
+    }
+    const unsigned long long thread_excl = warp_prefix + incl - sum;
+
+    if (warp == 0) {
+        unsigned long long prefix = 0;
+        if (p == 0) {
+            if (lane == 0) st_relaxed_u64(status, kFlagIncl | block_total);
+        } else {
+            if (lane == 0) st_relaxed_u64(status + p, kFlagAgg | block_total);
+            bool to;
+            prefix = warp_lookback(status, p, d_err, &to);
+            if (lane == 0) st_relaxed_u64(status + p, kFlagIncl | ((prefix + block_total) & kValueMask));
+        }
+        if (lane == 0) {
+            s_prefix = prefix;
+            if (block_vis) atomicAdd(counts + 1, (unsigned long long)block_vis);
+            if (p == num_parts - 1) counts[0] = prefix + block_total;
+        }
+    }
+    __syncthreads();
+    unsigned long long run = s_prefix + thread_excl;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long idx = base + j;
+        if (idx < n) out[idx] = run;
+        run += v[j];
+    }
+}
+
+// Key emission. Gaussian i owns keys [offsets[i], offsets[i] + tiles[i]);
+// it writes one key per tile of its rect, row by row:
+//   key = tile_id << 32 | bits(depth), value = i.
+// Gaussians covering at most 32 tiles are written by their own thread; larger
+// ones are written by the whole warp, one at a time, with coalesced stores.
+__global__ void __launch_bounds__(256)
+emit_kernel(const float4 *__restrict__ rec, const uint32_t *__restrict__ tiles,
+            const unsigned long long *__restrict__ offsets, int64_t n, GsGrid grid,
+            uint64_t *__restrict__ keys, uint32_t *__restrict__ values, int64_t capacity,
+            uint32_t *d_err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    uint32_t t = i < n ? tiles[i] : 0u;
+    Rect R = {0, 0, 0, 0};
+    uint32_t dbits = 0;
+    unsigned long long off = 0;
+    if (t) {
+        const float4 r0 = rec[3 * i], r2 = rec[3 * i + 2];
+        R = tile_rect(r0.x, r0.y, __float_as_int(r2.z), grid.tile_w, grid.tile_h, grid.tiles_x,
+                      grid.tiles_y);
+        dbits = __float_as_uint(r2.y);
+        off = offsets[i];
+        const long long area = (long long)(R.x1 - R.x0) * (R.y1 - R.y0);
+        if (area != (long long)t) {
+            atomicOr(d_err, kErrRange);
+            t = 0;
+        } else if (off + t > (unsigned long long)capacity) {
+            atomicOr(d_err, kErrCapacity);
+            t = 0;
+        }
+    }
+    const bool big = t > 32u;
+    if (t && !big) {
+        unsigned long long k = off;
+        for (int ty = R.y0; ty < R.y1; ++ty)
+            for (int tx = R.x0; tx < R.x1; ++tx, ++k) {
+                keys[k] = ((uint64_t)(ty * grid.tiles_x + tx) << 32) | dbits;
+                values[k] = (uint32_t)i;
+            }
+    }
+    uint32_t bigmask = __ballot_sync(0xffffffffu, big);
+    while (bigmask) {
+        const int src = __ffs(bigmask) - 1;
+        bigmask &= bigmask - 1;
+        const int x0 = __shfl_sync(0xffffffffu, R.x0, src);
+        const int y0 = __shfl_sync(0xffffffffu, R.y0, src);
+        const int w = __shfl_sync(0xffffffffu, R.x1 - R.x0, src);
+        const uint32_t cnt = __shfl_sync(0xffffffffu, t, src);
+        const uint32_t db = __shfl_sync(0xffffffffu, dbits, src);
+        const unsigned long long o = __shfl_sync(0xffffffffu, off, src);
+        const uint32_t gi = (uint32_t)(i - lane + src);
+        for (uint32_t k = lane; k < cnt; k += 32) {
+            const int ty = y0 + (int)(k / (uint32_t)w), tx = x0 + (int)(k % (uint32_t)w);
+            keys[o + k] = ((uint64_t)(ty * grid.tiles_x + tx) << 32) | db;
+            values[o + k] = gi;
+        }
+    }
+}
+
+// Per-tile [first, last+1) of sorted keys; ranges must be zeroed first.
+__global__ void ranges_kernel(const uint64_t *__restrict__ keys, int64_t n, int32_t n_tiles,
+                              uint32_t *__restrict__ ranges, uint32_t *d_err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t tile = keys[i] >> 32;
+    if (tile >= (uint64_t)n_tiles) {
+        atomicOr(d_err, kErrRange);
+        return;
+    }
+    if (i == 0) {
+        ranges[2 * tile] = 0;
+    } else {
+        const uint64_t prev = keys[i - 1] >> 32;
+        if (prev != tile) {
+            ranges[2 * tile] = (uint32_t)i;
+            if (prev < (uint64_t)n_tiles) ranges[2 * prev + 1] = (uint32_t)i;
+        }
+    }
+    if (i == n - 1) ranges[2 * tile + 1] = (uint32_t)n;
+}
+
+}  // namespace
+
+size_t gs_scan_scratch_bytes(int64_t n) {
+    const int64_t parts = (n + kScanTile - 1) / kScanTile;
+    return 16 + (size_t)(parts > 0 ? parts : 1) * sizeof(unsigned long long);
+}
+
+cudaError_t gs_launch_scan(const uint32_t *tiles, int64_t n, unsigned long long *offsets,
+                           unsigned long long *counts, void *scratch, uint32_t *d_err,
+                           cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n == 0) return e;
+    e = cudaMemsetAsync(scratch, 0, gs_scan_scratch_bytes(n), s);
+    if (e != cudaSuccess) return e;
+    const int64_t parts = (n + kScanTile - 1) / kScanTile;
+    uint32_t *counter = static_cast<uint32_t *>(scratch);
+    unsigned long long *status =
+        reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 16);
+    scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(tiles, n, offsets, counts, counter, status,
+                                                         parts, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_emit(const gs_record *records, const uint32_t *tiles,
+                           const unsigned long long *offsets, int64_t n, const GsGrid &grid,
+                           uint64_t *keys, uint32_t *values, int64_t capacity, uint32_t *d_err,
+                           cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    emit_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4 *>(records), tiles, offsets, n,
+                                       grid, keys, values, capacity, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_ranges(const uint64_t *keys, int64_t n, int32_t n_tiles, uint32_t *ranges,
+                             uint32_t *d_err, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess || n == 0) return e;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n, n_tiles, ranges, d_err);
+    return cudaGetLastError();
+}

@@ -1,0 +1,265 @@
+// gs_sort.cu — stable LSD radix sort of (u64 key, u32 value) pairs, written
+// from the Onesweep design (Adinets and Merrill, 2022): one up-front pass
+// builds the digit histograms of every pass at once, then each 8-bit digit
+// pass is a single launch in which every block
+//   1. takes the next partition of 4096 pairs (atomic counter, so blocks
+//      only wait on blocks that are already running),
+//   2. ranks its pairs by digit, stably, with warp match + per-warp counters,
+//   3. publishes its per-digit counts and resolves its global per-digit
+//      offsets by decoupled look-back over earlier partitions' status words
+//      (one thread per digit; every wait is bounded in time),
+//   4. reorders the pairs in shared memory by digit and writes them out in
+//      digit-contiguous runs, so global stores are coalesced.
+#include "gs_internal.cuh"
+
+namespace {
+
+using namespace gs;
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // pairs per partition
+constexpr int kRadix = 256;
+constexpr int kMaxPasses = 8;
+
+struct SortScratch {
+    uint32_t *hist;    // passes x 256
+    uint32_t *bucket;  // passes x 256, exclusive offsets of each digit
+    uint32_t *counter; // passes partition counters
+    uint32_t *ticket;  // 1
+    unsigned long long *status;  // passes x parts x 256
+};
+
+inline int64_t num_parts(int64_t n) { return (n + kTile - 1) / kTile; }
+
+inline size_t header_bytes(int passes) {
+    size_t b = (size_t)passes * kRadix * 4 * 2 + (size_t)passes * 4 + 4;
+    return (b + 255) & ~(size_t)255;
+}
+
+SortScratch carve(void *base, int64_t n, int passes) {
+    char *p = static_cast<char *>(base);
+    SortScratch s;
+    s.hist = reinterpret_cast<uint32_t *>(p);
+    s.bucket = s.hist + passes * kRadix;
+    s.counter = s.bucket + passes * kRadix;
+    s.ticket = s.counter + passes;
+    s.status = reinterpret_cast<unsigned long long *>(p + header_bytes(passes));
+    (void)n;
+    return s;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t *s_tmp /* kWarps */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_tmp[warp] = incl;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_tmp[w];
+    __syncthreads();
+    return pre + incl - v;
+}
+
+// Histograms of every digit pass; the last block to finish turns them into
+// exclusive bucket offsets.
+__global__ void __launch_bounds__(kThreads)
+histogram_kernel(const uint64_t *__restrict__ keys, int64_t n, int passes, SortScratch sc) {
+    __shared__ uint32_t s_hist[kMaxPasses * kRadix];
+    __shared__ uint32_t s_tmp[kWarps];
+    __shared__ bool s_last;
+    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) s_hist[i] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * kRadix + ((k >> (8 * p)) & 255)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads)
+        if (s_hist[i]) atomicAdd(&sc.hist[i], s_hist[i]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(sc.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t c = __ldcg(&sc.hist[p * kRadix + threadIdx.x]);
+        const uint32_t e = block_exclusive_scan_256(c, s_tmp);
+        sc.bucket[p * kRadix + threadIdx.x] = e;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
+                int pass, int64_t parts, SortScratch sc, uint32_t *d_err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);                       // kTile
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kTile);            // kTile
+    uint32_t *s_whist = s_vals + kTile;                                         // kWarps x 256
+    uint32_t *s_doff = s_whist + kWarps * kRadix;                               // 256
+    uint32_t *s_gbase = s_doff + kRadix;                                        // 256
+    uint32_t *s_tmp = s_gbase + kRadix;                                         // kWarps
+    uint32_t *s_part = s_tmp + kWarps;                                          // 1
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int shift = 8 * pass;
+    if (tid == 0) *s_part = atomicAdd(sc.counter + pass, 1u);
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
+    __syncthreads();
+    const int64_t p = *s_part;
+    const int64_t base = p * kTile;
+
+    // Warp-striped load: warp w holds pairs [w*32*kItems, (w+1)*32*kItems) of
+    // the partition, item j of lane l at offset j*32 + l (coalesced).
+    uint64_t key[kItems];
+    uint32_t val[kItems];
+    uint32_t rank[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
+        key[j] = idx < n ? keys_in[idx] : ~0ull;
+        val[j] = idx < n ? vals_in[idx] : 0u;
+    }
+    // Stable rank within the warp, in (item, lane) order. Out-of-range items
+    // get digit 256, which matches nothing real and is never counted.
+    uint32_t *my_hist = s_whist + warp * kRadix;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
+        const uint32_t d = idx < n ? (uint32_t)((key[j] >> shift) & 255) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t lt = peers & lanemask_lt();
+        const uint32_t before = d < 256u ? my_hist[d] : 0u;
+        __syncwarp();
+        rank[j] = before + __popc(lt);
+        if (d < 256u && lt == 0u) my_hist[d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // Thread tid owns digit tid: prefix over warps, block total for the digit.
+    const uint32_t digit = tid;
+    uint32_t total = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_whist[w * kRadix + digit];
+        s_whist[w * kRadix + digit] = total;
+        total += c;
+    }
+    unsigned long long *st = sc.status + ((int64_t)pass * parts + p) * kRadix + digit;
+    if (p == 0) {
+        st_relaxed_u64(st, kFlagIncl | total);
+    } else {
+        st_relaxed_u64(st, kFlagAgg | total);
+    }
+    const uint32_t doff = block_exclusive_scan_256(total, s_tmp);
+    s_doff[digit] = doff;
+
+    // Decoupled look-back for this digit over partitions p-1, p-2, ...
+    unsigned long long excl = 0;
+    if (p > 0) {
+        const unsigned long long t0 = global_ns();
+        int64_t q = p - 1;
+        uint32_t polls = 0;
+        while (q >= 0) {
+            const unsigned long long s = ld_relaxed_u64(st - (p - q) * kRadix);
+            const unsigned long long f = s >> 62;
+            if (f == 0) {
+                if ((++polls & 63u) == 0u &&
+                    ((global_ns() - t0 > kSpinTimeoutNs) || (ld_relaxed_u32(d_err) & kErrTimeout))) {
+                    atomicOr(d_err, kErrTimeout);
+                    __threadfence();
+                    break;
+                }
+                continue;
+            }
+            excl += s & kValueMask;
+            if (f == 2) break;
+            --q;
+        }
+        st_relaxed_u64(st, kFlagIncl | ((excl + total) & kValueMask));
+    }
+    s_gbase[digit] = sc.bucket[pass * kRadix + digit] + (uint32_t)excl;
+    __syncthreads();
+
+    // Reorder by digit in shared memory.
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
+        if (idx < n) {
+            const uint32_t d = (uint32_t)((key[j] >> shift) & 255);
+            const uint32_t pos = s_doff[d] + my_hist[d] + rank[j];
+            s_keys[pos] = key[j];
+            s_vals[pos] = val[j];
+        }
+    }
+    __syncthreads();
+    const int valid = (int)((n - base) < kTile ? (n - base) : kTile);
+    for (int i = tid; i < valid; i += kThreads) {
+        const uint64_t k = s_keys[i];
+        const uint32_t d = (uint32_t)((k >> shift) & 255);
+        const uint64_t gp = (uint64_t)s_gbase[d] + (uint32_t)(i - s_doff[d]);
+        // Only reachable after a timed-out look-back left offsets meaningless.
+        if (gp >= (uint64_t)n) {
+            atomicOr(d_err, kErrRange);
+            continue;
+        }
+        keys_out[gp] = k;
+        vals_out[gp] = s_vals[i];
+    }
+}
+
+constexpr size_t kOnesweepSmem = (size_t)kTile * 8 + (size_t)kTile * 4 +
+                                 (size_t)kWarps * kRadix * 4 + 2 * kRadix * 4 + kWarps * 4 + 16;
+
+}  // namespace
+
+int gs_sort_passes(int key_bits) { return (key_bits + 7) / 8; }
+
+size_t gs_sort_scratch_bytes(int64_t n, int key_bits) {
+    const int passes = gs_sort_passes(key_bits);
+    const int64_t parts = num_parts(n) > 0 ? num_parts(n) : 1;
+    return header_bytes(passes) + (size_t)passes * parts * kRadix * sizeof(unsigned long long);
+}
+
+cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
+                           uint32_t *alt_values, int64_t n, int key_bits, void *scratch,
+                           uint32_t *d_err, bool *result_in_alt, cudaStream_t s) {
+    *result_in_alt = false;
+    if (n <= 1 || key_bits <= 0) return cudaSuccess;
+    const int passes = gs_sort_passes(key_bits);
+    const int64_t parts = num_parts(n);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, gs_sort_scratch_bytes(n, key_bits), s);
+    if (e != cudaSuccess) return e;
+    SortScratch sc = carve(scratch, n, passes);
+    e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kOnesweepSmem);
+    if (e != cudaSuccess) return e;
+    const unsigned hist_blocks = (unsigned)(parts < 608 ? parts : 608);
+    histogram_kernel<<<hist_blocks, kThreads, 0, s>>>(keys, n, passes, sc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t *kin = keys;
+    const uint32_t *vin = values;
+    uint64_t *kout = alt_keys;
+    uint32_t *vout = alt_values;
+    for (int pass = 0; pass < passes; ++pass) {
+        onesweep_kernel<<<(unsigned)parts, kThreads, kOnesweepSmem, s>>>(kin, vin, kout, vout, n, pass,
+                                                                        parts, sc, d_err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        kin = kout;
+        vin = vout;
+        kout = (kout == alt_keys) ? keys : alt_keys;
+        vout = (vout == alt_values) ? values : alt_values;
+    }
+    *result_in_alt = (passes & 1) != 0;
+    return cudaSuccess;
+}
