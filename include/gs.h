@@ -169,6 +169,23 @@ gs_status gs_bin(gs_context *ctx, const gs_record *records, const uint32_t *tile
 gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *values, int64_t n,
                         int32_t key_bits, void *stream);
 
+/* Allocation-free variant of gs_sort_pairs, for callers that may not
+ * allocate device memory (allocator or memory-pool callbacks, fixed-footprint
+ * real-time loops, hosts that own all device memory): same sort, same
+ * arguments, no gs_context. The paper has no counterpart; this is a library
+ * service. Its scratch is one array built into libgs.so, about 4 MiB, which
+ * every GPU that loads the library holds until the process exits.
+ *   n <= GS_NOALLOC_SORT_MAX_PAIRS, else GS_ERR_CAPACITY (nothing launched).
+ *   All calls share that array: calls that overlap on the GPU corrupt each
+ *   other; serialise them. The first call on a device looks the array up
+ *   with that device current (make it before any stream capture).
+ *   Returns after the sort has finished on `stream` (waits once to read the
+ *   device error word); GS_ERR_TIMEOUT if a bounded wait gave up. Calls no
+ *   cudaMalloc/cudaFree. */
+#define GS_NOALLOC_SORT_MAX_PAIRS 262144
+gs_status gs_sort_pairs_noalloc(uint64_t *keys, uint32_t *values, int64_t n, int32_t key_bits,
+                                void *stream);
+
 /* Per-tile [first, last+1) ranges of n sorted keys (tile id = key >> 32).
  * ranges: n_tiles x 2 x u32, fully overwritten ((0, 0) for empty tiles). */
 gs_status gs_tile_ranges(gs_context *ctx, const uint64_t *keys, int64_t n, int32_t n_tiles,

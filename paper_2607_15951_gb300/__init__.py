@@ -18,7 +18,8 @@ from . import _native as N
 __all__ = ["GSError", "Context", "camera_struct", "options_struct", "gaussians_struct",
            "gs_create", "gs_destroy", "gs_project", "gs_bin", "gs_sort_pairs", "gs_tile_ranges",
            "gs_blend", "gs_render", "gs_sync_status", "gs_last_render_stats",
-           "gs_set_stage_timing", "gs_last_stage_times", "RECORD_FLOATS"]
+           "gs_set_stage_timing", "gs_last_stage_times", "gs_sort_pairs_noalloc",
+           "RECORD_FLOATS"]
 
 RECORD_FLOATS = 12  # gs_record is 48 bytes = 12 x 4-byte words
 
@@ -162,6 +163,16 @@ def gs_bin(ctx: Context, records, tiles, n: int, cam, keys, values, ranges, *, t
 def gs_sort_pairs(ctx: Context, keys, values, n: int, key_bits: int, stream=None) -> None:
     ctx.check(_lib().gs_sort_pairs(ctx.handle, _ptr(keys), _ptr(values), int(n), int(key_bits),
                                    _stream(stream)))
+
+
+def gs_sort_pairs_noalloc(keys, values, n: int, key_bits: int, stream=None) -> None:
+    """The sort of gs_sort_pairs without a context and without any device
+    allocation (scratch lives in an array inside libgs.so); for callers that
+    may not allocate. n <= NOALLOC_SORT_MAX_PAIRS; calls must not overlap."""
+    st = _lib().gs_sort_pairs_noalloc(_ptr(keys), _ptr(values), int(n), int(key_bits),
+                                      _stream(stream))
+    if st != N.GS_OK:
+        raise GSError(st, "gs_sort_pairs_noalloc failed")
 
 
 def gs_tile_ranges(ctx: Context, keys, n: int, n_tiles: int, ranges, stream=None) -> None:

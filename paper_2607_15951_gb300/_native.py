@@ -19,6 +19,7 @@ GS_ERR_OOM = 3
 GS_ERR_CAPACITY = 4
 GS_ERR_TIMEOUT = 5
 GS_ERR_UNSUPPORTED = 6
+NOALLOC_SORT_MAX_PAIRS = 262144  # GS_NOALLOC_SORT_MAX_PAIRS in include/gs.h
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_CAPACITY", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}
 
@@ -81,6 +82,7 @@ SIGNATURES = {
                               ctypes.POINTER(gs_options), vp, vp, ctypes.c_int64, vp,
                               ctypes.POINTER(ctypes.c_int64), vp]),
     "gs_sort_pairs": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, ctypes.c_int32, vp]),
+    "gs_sort_pairs_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_int32, vp]),
     "gs_tile_ranges": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]),
     "gs_blend": (ctypes.c_int, [vp, vp, vp, vp, ctypes.POINTER(gs_camera),
                                 ctypes.POINTER(gs_options), ctypes.POINTER(gs_framebuffer), vp]),
