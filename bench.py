@@ -192,6 +192,7 @@ def main():
     ap.add_argument("--workload", default="clustered_1m_1080p", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--blend-variant", type=int, default=0, help="0 culled (default), 1 basic")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -216,7 +217,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step():
-        gs.gs_render(ctx, g, scene.sh_degree, cam, rgb)
+        gs.gs_render(ctx, g, scene.sh_degree, cam, rgb, variant=args.blend_variant)
 
     for _ in range(args.warmup):
         step()
@@ -224,7 +225,7 @@ def main():
     gs.gs_sync_status(ctx)
 
     # Algorithmic work of one frame (deterministic): evaluated and blended pairs.
-    aux = gs.render(ctx, g, scene.sh_degree, cam)
+    aux = gs.render(ctx, g, scene.sh_degree, cam, variant=args.blend_variant)
     torch.cuda.synchronize()
     n_eval_total = int(aux["n_eval"].to(torch.int64).sum().item())
     stats = gs.gs_last_render_stats(ctx)
@@ -272,7 +273,7 @@ def main():
     for _ in range(3):
         for k in host:
             dev_in[k].copy_(host[k], non_blocking=True)
-        gs.gs_render(ctx, dev_in, scene.sh_degree, cam, rgb)
+        gs.gs_render(ctx, dev_in, scene.sh_degree, cam, rgb, variant=args.blend_variant)
         host_rgb.copy_(rgb, non_blocking=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -282,7 +283,7 @@ def main():
     for _ in range(args.e2e_steps):
         for k in host:
             dev_in[k].copy_(host[k], non_blocking=True)
-        gs.gs_render(ctx, dev_in, scene.sh_degree, cam, rgb)
+        gs.gs_render(ctx, dev_in, scene.sh_degree, cam, rgb, variant=args.blend_variant)
         host_rgb.copy_(rgb, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -312,7 +313,7 @@ def main():
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "n_visible": stats["n_visible"], "n_keys": stats["n_keys"],
-                   "key_bits": stats["key_bits"]},
+                   "key_bits": stats["key_bits"], "blend_variant": args.blend_variant},
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "wall_s_timed_loop": round(wall, 3),
         "e2e": {"value": round(e2e_value, 3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),

@@ -108,12 +108,19 @@ typedef struct {
     int32_t *n_eval;
 } gs_framebuffer;
 
+/* Blend schedules; both produce identical outputs.
+ *   GS_BLEND_CULLED  each warp owns an 8x8 pixel block and skips records whose
+ *                    conservative alpha >= 1/255 box misses it (default)
+ *   GS_BLEND_BASIC   one thread per pixel evaluates every record of its tile */
+enum { GS_BLEND_CULLED = 0, GS_BLEND_BASIC = 1 };
+
 /* Options. gs_default_options() fills the standard values. */
 typedef struct {
     int32_t tile_w, tile_h; /* screen tile: 16x16 (default), 16x8 or 8x8      */
     float bg[3];            /* background colour added as T_final * bg         */
     int32_t record_dtype;   /* 0 = FP32 records (only value in this version)   */
-    int32_t reserved[7];    /* must be zero                                    */
+    int32_t blend_variant;  /* GS_BLEND_CULLED (default) or GS_BLEND_BASIC     */
+    int32_t reserved[6];    /* must be zero                                    */
 } gs_options;
 
 void gs_default_options(gs_options *opts /* host */);

@@ -61,13 +61,15 @@ def camera_struct(cam) -> N.gs_camera:
     return c
 
 
-def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0) -> N.gs_options:
+def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
+                   blend_variant: int = 0) -> N.gs_options:
     o = N.gs_options()
     _lib().gs_default_options(ctypes.byref(o))
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
     for i in range(3):
         o.bg[i] = float(bg[i])
     o.record_dtype = int(record_dtype)
+    o.blend_variant = int(blend_variant)
     return o
 
 
@@ -188,17 +190,19 @@ def _fb(rgb, final_T=None, n_contrib=None, n_eval=None) -> N.gs_framebuffer:
 
 
 def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_contrib=None,
-             n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), stream=None) -> None:
-    c, o = camera_struct(cam), options_struct(tile, bg)
+             n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
+             stream=None) -> None:
+    c, o = camera_struct(cam), options_struct(tile, bg, blend_variant=variant)
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_blend(ctx.handle, _ptr(records), _ptr(values), _ptr(ranges),
                               ctypes.byref(c), ctypes.byref(o), ctypes.byref(fb), _stream(stream)))
 
 
 def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
-              n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), stream=None) -> None:
+              n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
+              stream=None) -> None:
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg)
+    c, o = camera_struct(cam), options_struct(tile, bg, blend_variant=variant)
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
                                ctypes.byref(fb), _stream(stream)))
@@ -233,7 +237,7 @@ def scene_to_device(scene, device="cuda") -> dict:
 
 
 def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
-           aux: bool = True, stream=None) -> dict:
+           aux: bool = True, variant: int = 0, stream=None) -> dict:
     """Allocate outputs with torch and call gs_render."""
     import torch
     H, W = int(cam.height), int(cam.width)
@@ -244,5 +248,5 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
         out["n_contrib"] = torch.empty((H, W), dtype=torch.int32, device=dev)
         out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
-              out.get("n_eval"), tile=tile, bg=bg, stream=stream)
+              out.get("n_eval"), tile=tile, bg=bg, variant=variant, stream=stream)
     return out

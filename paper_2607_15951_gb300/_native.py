@@ -19,6 +19,8 @@ GS_ERR_OOM = 3
 GS_ERR_CAPACITY = 4
 GS_ERR_TIMEOUT = 5
 GS_ERR_UNSUPPORTED = 6
+GS_BLEND_CULLED = 0
+GS_BLEND_BASIC = 1
 NOALLOC_SORT_MAX_PAIRS = 262144  # GS_NOALLOC_SORT_MAX_PAIRS in include/gs.h
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_CAPACITY", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}
@@ -53,7 +55,7 @@ class gs_framebuffer(ctypes.Structure):
 class gs_options(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("bg", ctypes.c_float * 3), ("record_dtype", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("blend_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class gs_render_stats(ctypes.Structure):

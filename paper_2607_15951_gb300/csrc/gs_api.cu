@@ -92,7 +92,9 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
     if (!ok_tile) return fail(ctx, GS_ERR_INVALID_ARG, "tile must be 16x16, 16x8 or 8x8");
     if (o->record_dtype != 0)
         return fail(ctx, GS_ERR_UNSUPPORTED, "record_dtype must be 0 (FP32) in this version");
-    for (int i = 0; i < 7; ++i)
+    if (o->blend_variant != GS_BLEND_CULLED && o->blend_variant != GS_BLEND_BASIC)
+        return fail(ctx, GS_ERR_INVALID_ARG, "blend_variant must be GS_BLEND_CULLED or GS_BLEND_BASIC");
+    for (int i = 0; i < 6; ++i)
         if (o->reserved[i] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
@@ -389,7 +391,7 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
         return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
     DeviceGuard dg(ctx->device);
     GS_CUDA(ctx, gs_launch_blend(records, values, ranges, make_grid(cam, opts), cam->width, cam->height,
-                                 opts->bg, *fb, static_cast<cudaStream_t>(stream)));
+                                 opts->bg, *fb, opts->blend_variant, static_cast<cudaStream_t>(stream)));
     return GS_OK;
 }
 
@@ -420,7 +422,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     if ((st = bin_impl(ctx, rec, tiles, n, grid, nullptr, nullptr, 0, true, ranges, &K, s)) != GS_OK)
         return st;
     GS_CUDA(ctx, gs_launch_blend(rec, static_cast<uint32_t *>(ctx->values.ptr), ranges, grid, cam->width,
-                                 cam->height, opts->bg, *fb, s));
+                                 cam->height, opts->bg, *fb, opts->blend_variant, s));
     mark(ctx, EV_BLEND, s);
     if (ctx->timing) ctx->timed_once = true;
     return GS_OK;

@@ -144,4 +144,4 @@ int gs_sort_passes(int key_bits);
 
 cudaError_t gs_launch_blend(const gs_record *records, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
-                            const gs_framebuffer &fb, cudaStream_t s);
+                            const gs_framebuffer &fb, int variant, cudaStream_t s);

@@ -367,3 +367,38 @@ def test_invalid_arguments_rejected(ctx):
     bad.near_z = 0.0
     with pytest.raises(gs.GSError):
         gs.gs_render(ctx, g, 0, bad, rgb)
+
+
+# ---------------------------------------------------------------------------
+# Blend schedules: the culled schedule must equal the basic one bit for bit
+# ---------------------------------------------------------------------------
+
+def _needles(n=4000, seed=21):
+    s = scenes.uniform_box(n, seed)
+    s.log_scales[:, 0] += 3.5     # ~33x longer along one local axis
+    s.log_scales[:, 1:] -= 1.5
+    s.opacity_logits[:] = np.abs(s.opacity_logits) + 1.0
+    return s
+
+
+VARIANT_CASES = [
+    ("uniform_box_256_t16", lambda: (scenes.uniform_box(10_000, 0), scenes.pinhole(256, 256)), (16, 16)),
+    ("uniform_box_257x131_t16x8", lambda: (scenes.uniform_box(5_000, 3), scenes.pinhole(257, 131)), (16, 8)),
+    ("uniform_box_257x131_t8", lambda: (scenes.uniform_box(5_000, 4), scenes.pinhole(257, 131)), (8, 8)),
+    ("needles_320x200", lambda: (_needles(), scenes.pinhole(320, 200)), (16, 16)),
+    ("clustered_1m_1080p", lambda: scenes.workload("clustered_1m_1080p")[0:1] + (scenes.pinhole(1920, 1080),), (16, 16)),
+]
+
+
+@pytest.mark.parametrize("name,make,tile", VARIANT_CASES, ids=[c[0] for c in VARIANT_CASES])
+def test_blend_variants_identical(ctx, name, make, tile):
+    scene, cam = make()
+    g = gs.scene_to_device(scene)
+    outs = []
+    for variant in (gs._native.GS_BLEND_BASIC, gs._native.GS_BLEND_CULLED):
+        out = gs.render(ctx, g, scene.sh_degree, cam, tile=tile, variant=variant)
+        torch.cuda.synchronize()
+        outs.append({k: v.cpu().numpy() for k, v in out.items()})
+    gs.gs_sync_status(ctx)
+    for k in ("rgb", "final_T", "n_contrib", "n_eval"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
