@@ -209,10 +209,21 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
                    const uint32_t *ranges, const gs_camera *cam, const gs_options *opts,
                    const gs_framebuffer *fb, void *stream);
 
-/* Whole forward pass: gs_project -> gs_bin -> gs_blend on workspace owned by
- * the context. SYNCHRONISES once (to size the key buffers). */
+/* Whole forward pass (Sec. 3.1: cull, project, depth-sort per tile,
+ * composite) on workspace owned by the context, with the same results as
+ * gs_project -> gs_bin -> gs_blend. One fused kernel projects, scans the tile
+ * counts and emits the keys; the sort and the ranges read the key count on
+ * the device; the blend follows. The key buffers are sized from earlier
+ * frames (with headroom): the call SYNCHRONISES once at the end to check the
+ * count, and if the frame needed more room it grows the buffers and renders
+ * the frame again, so a returned image is never truncated. */
 gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
                     const gs_options *opts, const gs_framebuffer *fb, void *stream);
+
+/* Sets the number of (tile, Gaussian) pairs gs_render's key buffers hold and
+ * stops the context from shrinking it between frames (the buffers grow if a
+ * frame needs more). */
+gs_status gs_reserve_keys(gs_context *ctx, int64_t key_capacity);
 
 /* Statistics of the last gs_render on this context (host out). */
 typedef struct {

@@ -18,7 +18,7 @@ from . import _native as N
 __all__ = ["GSError", "Context", "camera_struct", "options_struct", "gaussians_struct",
            "gs_create", "gs_destroy", "gs_project", "gs_bin", "gs_sort_pairs", "gs_tile_ranges",
            "gs_blend", "gs_render", "gs_sync_status", "gs_last_render_stats",
-           "gs_set_stage_timing", "gs_last_stage_times", "gs_sort_pairs_noalloc",
+           "gs_set_stage_timing", "gs_last_stage_times", "gs_sort_pairs_noalloc", "gs_reserve_keys",
            "RECORD_FLOATS"]
 
 RECORD_FLOATS = 12  # gs_record is 48 bytes = 12 x 4-byte words
@@ -213,6 +213,10 @@ def gs_last_render_stats(ctx: Context) -> dict:
     ctx.check(_lib().gs_last_render_stats(ctx.handle, ctypes.byref(s)))
     return {"n_visible": s.n_visible, "n_keys": s.n_keys, "key_bits": s.key_bits,
             "n_tiles": s.n_tiles}
+
+
+def gs_reserve_keys(ctx: Context, key_capacity: int) -> None:
+    ctx.check(_lib().gs_reserve_keys(ctx.handle, int(key_capacity)))
 
 
 def gs_set_stage_timing(ctx: Context, enable: bool) -> None:

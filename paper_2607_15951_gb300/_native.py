@@ -91,6 +91,7 @@ SIGNATURES = {
     "gs_render": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
                                  ctypes.POINTER(gs_options), ctypes.POINTER(gs_framebuffer), vp]),
     "gs_last_render_stats": (ctypes.c_int, [vp, ctypes.POINTER(gs_render_stats)]),
+    "gs_reserve_keys": (ctypes.c_int, [vp, ctypes.c_int64]),
     "gs_set_stage_timing": (ctypes.c_int, [vp, ctypes.c_int]),
     "gs_last_stage_times": (ctypes.c_int, [vp, ctypes.POINTER(gs_stage_times)]),
 }

@@ -1,5 +1,6 @@
 // gs_api.cu — the C ABI (include/gs.h): argument validation, the context
 // and its grow-only workspace, and the launch sequences of each entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -21,12 +22,15 @@ struct gs_context {
     int device = 0;
     std::string last_error;
     uint32_t *d_err = nullptr;               // device error word
-    unsigned long long *d_counts = nullptr;  // [K, n_visible]
+    unsigned long long *d_counts = nullptr;  // [K, n_visible, K if it fitted, pad]
     unsigned long long *h_counts = nullptr;  // pinned mirror of d_counts
     uint32_t *h_err = nullptr;               // pinned mirror of d_err
     DevBuf records, tiles, offsets, scan_scratch, keys, values, alt_keys, alt_values, sort_scratch,
         ranges;
     gs_render_stats stats{};
+    int64_t key_capacity = 0;  // pairs the render path's key buffers hold
+    bool pinned_capacity = false;  // set by gs_reserve_keys: do not shrink
+    DevBuf fused_scratch;
     bool timing = false;
     bool timed_once = false;
     cudaEvent_t ev[8] = {};
@@ -261,8 +265,8 @@ gs_status gs_create(gs_context **out, int device) {
     ctx->device = device;
     DeviceGuard g(device);
     if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess ||
-        cudaMalloc(&ctx->d_counts, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_counts, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_counts, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_counts, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_err, sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -277,7 +281,8 @@ void gs_destroy(gs_context *ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
-                      &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges};
+                      &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
+                      &ctx->fused_scratch};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -303,7 +308,7 @@ size_t gs_workspace_bytes(const gs_context *ctx) {
     if (!ctx) return 0;
     const DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                             &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch,
-                            &ctx->ranges};
+                            &ctx->ranges, &ctx->fused_scratch};
     size_t t = 0;
     for (const DevBuf *b : bufs) t += b->bytes;
     return t;
@@ -406,25 +411,87 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const GsGrid grid = make_grid(cam, opts);
+    const GsCameraDev dcam = make_cam(cam);
     const int64_t n = g->n;
-    const size_t n_tiles = (size_t)grid.tiles_x * grid.tiles_y;
+    const int n_tiles = grid.tiles_x * grid.tiles_y;
+    const int bits = key_bits_for(n_tiles);
     if ((st = ensure(ctx, ctx->records, (size_t)(n > 0 ? n : 1) * sizeof(gs_record), "records")) != GS_OK ||
-        (st = ensure(ctx, ctx->tiles, (size_t)(n > 0 ? n : 1) * 4, "tiles")) != GS_OK ||
-        (st = ensure(ctx, ctx->ranges, n_tiles * 8, "ranges")) != GS_OK)
+        (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK ||
+        (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n), "scan scratch")) != GS_OK)
         return st;
+    if (ctx->key_capacity == 0) ctx->key_capacity = std::max<int64_t>(int64_t(1) << 20, 4 * n);
     gs_record *rec = static_cast<gs_record *>(ctx->records.ptr);
-    uint32_t *tiles = static_cast<uint32_t *>(ctx->tiles.ptr);
     uint32_t *ranges = static_cast<uint32_t *>(ctx->ranges.ptr);
-    mark(ctx, EV_START, s);
-    GS_CUDA(ctx, gs_launch_project(*g, make_cam(cam), grid, rec, tiles, s));
-    mark(ctx, EV_PROJECT, s);
-    int64_t K = 0;
-    if ((st = bin_impl(ctx, rec, tiles, n, grid, nullptr, nullptr, 0, true, ranges, &K, s)) != GS_OK)
-        return st;
-    GS_CUDA(ctx, gs_launch_blend(rec, static_cast<uint32_t *>(ctx->values.ptr), ranges, grid, cam->width,
-                                 cam->height, opts->bg, *fb, opts->blend_variant, s));
-    mark(ctx, EV_BLEND, s);
-    if (ctx->timing) ctx->timed_once = true;
+
+    // The key buffers are sized from earlier frames; if this frame needs more,
+    // the overflow is detected at the end and the frame is rendered again.
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        const int64_t cap = ctx->key_capacity;
+        if ((st = ensure(ctx, ctx->keys, (size_t)cap * 8, "keys")) != GS_OK ||
+            (st = ensure(ctx, ctx->values, (size_t)cap * 4, "values")) != GS_OK ||
+            (st = ensure(ctx, ctx->alt_keys, (size_t)cap * 8, "alt keys")) != GS_OK ||
+            (st = ensure(ctx, ctx->alt_values, (size_t)cap * 4, "alt values")) != GS_OK ||
+            (st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes(cap, bits), "sort scratch")) != GS_OK ||
+            (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n) + gs_key_block_bytes(cap),
+                         "front-end scratch")) != GS_OK)
+            return st;
+        uint64_t *keys = static_cast<uint64_t *>(ctx->keys.ptr);
+        uint32_t *vals = static_cast<uint32_t *>(ctx->values.ptr);
+        uint64_t *akeys = static_cast<uint64_t *>(ctx->alt_keys.ptr);
+        uint32_t *avals = static_cast<uint32_t *>(ctx->alt_values.ptr);
+        GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes(cap, bits), s));
+        const GsSortScratch sc = gs_sort_carve(ctx->sort_scratch.ptr, cap, bits);
+        mark(ctx, EV_START, s);
+        GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, keys, vals, cap, ctx->d_counts,
+                                           ctx->fused_scratch.ptr, sc, ctx->d_err, s));
+        mark(ctx, EV_PROJECT, s);
+        mark(ctx, EV_SCAN, s);
+        mark(ctx, EV_EMIT0, s);
+        mark(ctx, EV_EMIT, s);
+        bool in_alt = false;
+        GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, cap, ctx->d_counts + 2, sc, ctx->d_err,
+                                           &in_alt, s));
+        mark(ctx, EV_SORT, s);
+        uint64_t *sk = in_alt ? akeys : keys;
+        uint32_t *sv = in_alt ? avals : vals;
+        GS_CUDA(ctx, gs_launch_ranges_dev(sk, sv, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s));
+        mark(ctx, EV_RANGES, s);
+        GS_CUDA(ctx, gs_launch_blend(rec, sv, ranges, grid, cam->width, cam->height, opts->bg, *fb,
+                                     opts->blend_variant, s));
+        mark(ctx, EV_BLEND, s);
+        GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 4 * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, s));
+        GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        GS_CUDA(ctx, cudaStreamSynchronize(s));
+        const unsigned long long K = ctx->h_counts[0];
+        ctx->stats.n_visible = (int64_t)ctx->h_counts[1];
+        ctx->stats.n_keys = (int64_t)K;
+        ctx->stats.n_tiles = n_tiles;
+        ctx->stats.key_bits = bits;
+        if (K >= (1ull << 32) - 1)
+            return fail(ctx, GS_ERR_CAPACITY, "more than 2^32-2 (tile, Gaussian) pairs in one frame");
+        if ((int64_t)K > cap) {
+            // Overflow: nothing past the buffers was written and the frame
+            // composited empty lists; grow and render again.
+            GS_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s));
+            ctx->key_capacity = (int64_t)(K + K / 4 + 1024);
+            continue;
+        }
+        if (ctx->timing) ctx->timed_once = true;
+        // Keep about 25 % headroom over this frame's count for the next one
+        // (the buffers themselves only grow).
+        if (!ctx->pinned_capacity && (int64_t)K * 2 < cap)
+            ctx->key_capacity = std::max<int64_t>(65536, (int64_t)(K + K / 4 + 1024));
+        if (*ctx->h_err) return collect_device_error(ctx, s);
+        return GS_OK;
+    }
+    return fail(ctx, GS_ERR_CAPACITY, "key buffers could not be sized for this frame");
+}
+
+gs_status gs_reserve_keys(gs_context *ctx, int64_t key_capacity) {
+    if (!ctx || key_capacity < 1 || key_capacity >= (int64_t(1) << 32) - 1) return GS_ERR_INVALID_ARG;
+    ctx->key_capacity = key_capacity;
+    ctx->pinned_capacity = true;
     return GS_OK;
 }
 

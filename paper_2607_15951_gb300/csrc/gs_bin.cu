@@ -11,43 +11,6 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// Warp-wide decoupled look-back over per-partition status words: returns
-// the sum of the values of all partitions before p. Lanes inspect 32
-// predecessors at a time; a window is consumed once every lane sees a
-// published flag, up to and including the nearest inclusive prefix.
-// Sets kErrTimeout (and returns a meaningless sum) if a predecessor stays
-// unpublished for kSpinTimeoutNs or another block already timed out.
-__device__ unsigned long long warp_lookback(const unsigned long long *status, long long p,
-                                            uint32_t *d_err, bool *timed_out) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long excl = 0;
-    long long q = p - 1;
-    const unsigned long long t0 = global_ns();
-    *timed_out = false;
-    while (true) {
-        const long long idx = q - lane;
-        const unsigned long long s = idx >= 0 ? ld_relaxed_u64(status + idx) : kFlagIncl;
-        if (!__all_sync(0xffffffffu, (s >> 62) != 0)) {
-            const bool give_up = (global_ns() - t0 > kSpinTimeoutNs) ||
-                                 (ld_relaxed_u32(d_err) & kErrTimeout);
-            if (__any_sync(0xffffffffu, give_up)) {
-                if (lane == 0) atomicOr(d_err, kErrTimeout);
-                *timed_out = true;
-                return excl;
-            }
-            __nanosleep(32);
-            continue;
-        }
-        const uint32_t incl = __ballot_sync(0xffffffffu, (s >> 62) == 2);
-        const int first = incl ? __ffs(incl) - 1 : 31;
-        unsigned long long v = lane <= first ? (s & kValueMask) : 0ull;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        excl += v;
-        if (incl) return excl;
-        q -= 32;
-    }
-}
-
 // Single-pass exclusive scan of u32 counts into u64 offsets (decoupled
 // look-back; partitions taken in launch order from an atomic counter so a
 // block only ever waits on blocks that are already running).
@@ -179,11 +142,42 @@ emit_kernel(const float4 *__restrict__ rec, const uint32_t *__restrict__ tiles,
     }
 }
 
-// Per-tile [first, last+1) of sorted keys; ranges must be zeroed first.
-__global__ void ranges_kernel(const uint64_t *__restrict__ keys, int64_t n, int32_t n_tiles,
-                              uint32_t *__restrict__ ranges, uint32_t *d_err) {
+// Orders values[b, e) ascending (a run of equal keys): insertion sort for
+// short runs, Shell sort (Ciura gaps) for long ones.
+__device__ void sort_run(uint32_t *v, int64_t b, int64_t e) {
+    const int64_t m = e - b;
+    const int gaps[] = {701, 301, 132, 57, 23, 10, 4, 1};
+    for (int gi = 0; gi < 8; ++gi) {
+        const int64_t gap = gaps[gi];
+        if (gap >= m) continue;
+        for (int64_t i = b + gap; i < e; ++i) {
+            const uint32_t x = v[i];
+            int64_t j = i;
+            while (j - gap >= b && v[j - gap] > x) {
+                v[j] = v[j - gap];
+                j -= gap;
+            }
+            v[j] = x;
+        }
+    }
+}
+
+// Per-tile [first, last+1) of sorted keys; ranges must be zeroed first. The
+// key count is n_host, or *d_n when d_n is given. With fix_ties, each run of
+// equal keys (same tile, same depth bits) gets its values in ascending
+// Gaussian-index order, for keys emitted in an arbitrary order.
+__global__ void ranges_kernel(const uint64_t *__restrict__ keys, int64_t n_host,
+                              const unsigned long long *d_n, int32_t n_tiles,
+                              uint32_t *__restrict__ ranges, uint32_t *values, int fix_ties,
+                              uint32_t *d_err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
     if (i >= n) return;
+    if (fix_ties && (i == 0 || keys[i - 1] != keys[i]) && i + 1 < n && keys[i + 1] == keys[i]) {
+        int64_t e = i + 2;
+        while (e < n && keys[e] == keys[i]) ++e;
+        sort_run(values, i, e);
+    }
     const uint64_t tile = keys[i] >> 32;
     if (tile >= (uint64_t)n_tiles) {
         atomicOr(d_err, kErrRange);
@@ -240,6 +234,16 @@ cudaError_t gs_launch_ranges(const uint64_t *keys, int64_t n, int32_t n_tiles, u
     cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess || n == 0) return e;
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n, n_tiles, ranges, d_err);
+    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n, nullptr, n_tiles, ranges, nullptr, 0, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_ranges_dev(const uint64_t *keys, uint32_t *values, int64_t n_capacity,
+                                 const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
+                                 uint32_t *d_err, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess || n_capacity == 0) return e;
+    const unsigned blocks = (unsigned)((n_capacity + 255) / 256);
+    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n_capacity, d_n, n_tiles, ranges, values, 1, d_err);
     return cudaGetLastError();
 }

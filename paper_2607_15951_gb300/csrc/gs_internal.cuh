@@ -57,19 +57,70 @@ constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagIncl = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 
+// Warp-wide decoupled look-back over per-partition status words: returns
+// the sum of the values of all partitions before p. Lanes inspect 32
+// predecessors at a time; a window is consumed once every lane sees a
+// published flag, up to and including the nearest inclusive prefix.
+// Sets kErrTimeout (and returns a meaningless sum) if a predecessor stays
+// unpublished for kSpinTimeoutNs or another block already timed out.
+__device__ __forceinline__ unsigned long long warp_lookback(const unsigned long long *status, long long p,
+                                            uint32_t *d_err, bool *timed_out) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long excl = 0;
+    long long q = p - 1;
+    const unsigned long long t0 = global_ns();
+    *timed_out = false;
+    while (true) {
+        const long long idx = q - lane;
+        const unsigned long long s = idx >= 0 ? ld_relaxed_u64(status + idx) : kFlagIncl;
+        if (!__all_sync(0xffffffffu, (s >> 62) != 0)) {
+            const bool give_up = (global_ns() - t0 > kSpinTimeoutNs) ||
+                                 (ld_relaxed_u32(d_err) & kErrTimeout);
+            if (__any_sync(0xffffffffu, give_up)) {
+                if (lane == 0) atomicOr(d_err, kErrTimeout);
+                *timed_out = true;
+                return excl;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        const uint32_t incl = __ballot_sync(0xffffffffu, (s >> 62) == 2);
+        const int first = incl ? __ffs(incl) - 1 : 31;
+        unsigned long long v = lane <= first ? (s & kValueMask) : 0ull;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (incl) return excl;
+        q -= 32;
+    }
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t *s_tmp /* 8 */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_tmp[warp] = incl;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_tmp[w];
+    __syncthreads();
+    return pre + incl - v;
+}
+
 // Tile rectangle of a record: columns [floor((u-r)/tw), floor((u+r+tw-1)/tw))
 // and rows likewise, clamped to the grid. floor((u +- n)/t) for an integer n
-// equals floordiv(floor(u) +- n, t), so the bounds are exact integer
-// arithmetic on floor(u); |u| is clamped to 2^31, which cannot change an
-// answer once the radius is clamped to 2^30.
+// equals floor((floor(u) +- n)/t), so the bounds are exact integer arithmetic
+// on floor(u) (a shift, the tile sides being powers of two); |u| is clamped
+// to 2^31, which cannot change an answer once the radius is clamped to 2^30.
 struct Rect {
     int x0, y0, x1, y1;
 };
 
-__device__ __forceinline__ long long floordiv(long long a, int b) {
-    long long q = a / b;
-    return (a % b != 0 && a < 0) ? q - 1 : q;
-}
+// floor(a / 2^s): an arithmetic right shift (tile sides are powers of two).
+__device__ __forceinline__ long long floordiv_pow2(long long a, int s) { return a >> s; }
 
 __device__ __forceinline__ int clamp_tile(long long v, int limit) {
     return v < 0 ? 0 : (v > limit ? limit : (int)v);
@@ -81,10 +132,11 @@ __device__ __forceinline__ Rect tile_rect(float u, float v, int r, int tw, int t
     long long fu = (long long)floorf(fminf(fmaxf(u, -lim), lim));
     long long fv = (long long)floorf(fminf(fmaxf(v, -lim), lim));
     Rect R;
-    R.x0 = clamp_tile(floordiv(fu - r, tw), tiles_x);
-    R.x1 = clamp_tile(floordiv(fu + r + tw - 1, tw), tiles_x);
-    R.y0 = clamp_tile(floordiv(fv - r, th), tiles_y);
-    R.y1 = clamp_tile(floordiv(fv + r + th - 1, th), tiles_y);
+    const int sx = __ffs(tw) - 1, sy = __ffs(th) - 1;
+    R.x0 = clamp_tile(floordiv_pow2(fu - r, sx), tiles_x);
+    R.x1 = clamp_tile(floordiv_pow2(fu + r + tw - 1, sx), tiles_x);
+    R.y0 = clamp_tile(floordiv_pow2(fv - r, sy), tiles_y);
+    R.y1 = clamp_tile(floordiv_pow2(fv + r + th - 1, sy), tiles_y);
     return R;
 }
 
@@ -132,16 +184,64 @@ cudaError_t gs_launch_emit(const gs_record *records, const uint32_t *tiles,
 
 cudaError_t gs_launch_ranges(const uint64_t *keys, int64_t n, int32_t n_tiles, uint32_t *ranges,
                              uint32_t *d_err, cudaStream_t s);
+// Same with the key count read from *d_n (the grid covers n_capacity keys),
+// and each run of equal keys put in ascending value order.
+cudaError_t gs_launch_ranges_dev(const uint64_t *keys, uint32_t *values, int64_t n_capacity,
+                                 const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
+                                 uint32_t *d_err, cudaStream_t s);
 
-// Onesweep radix sort. Scratch: gs_sort_scratch_bytes(n, key_bits) bytes.
-// Sorts (keys, values) using (alt_keys, alt_values) as the ping-pong pair;
-// *result_in_alt tells which pair holds the result.
+
+
+// Onesweep radix sort. Pairs per partition (one block's share of a pass):
+#ifndef GS_SORT_ITEMS
+#define GS_SORT_ITEMS 16
+#endif
+#ifndef GS_SORT_LOOKAHEAD
+#define GS_SORT_LOOKAHEAD 8
+#endif
+constexpr int kSortThreads = 256;
+constexpr int kSortTile = kSortThreads * GS_SORT_ITEMS;
+// Scratch: gs_sort_scratch_bytes(n, key_bits) bytes, laid out as
+// GsSortScratch (digit histograms, their exclusive bucket offsets, one
+// partition counter per pass, a ticket, and the look-back status words).
+struct GsSortScratch {
+    uint32_t *hist;    // passes x 256 digit counts
+    uint32_t *bucket;  // passes x 256 exclusive bucket offsets
+    uint32_t *counter; // passes partition counters
+    uint32_t *ticket;  // last-block ticket of the histogram producer
+    unsigned long long *status;  // passes x parts x 256
+    int passes;
+    int64_t parts;     // partitions of the capacity the passes are launched for
+};
 size_t gs_sort_scratch_bytes(int64_t n, int key_bits);
+GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits);
+int gs_sort_passes(int key_bits);
+// Sorts (keys, values) using (alt_keys, alt_values) as the ping-pong pair;
+// *result_in_alt tells which pair holds the result. Zeroes the scratch and
+// builds the histograms itself.
 cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
                            uint32_t *alt_values, int64_t n, int key_bits, void *scratch,
                            uint32_t *d_err, bool *result_in_alt, cudaStream_t s);
-int gs_sort_passes(int key_bits);
+// Digit passes only, for a producer that already filled sc.hist / sc.bucket.
+// The grid covers n_capacity pairs; the pair count is read from *d_n.
+cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
+                                  uint32_t *alt_values, int64_t n_capacity,
+                                  const unsigned long long *d_n, const GsSortScratch &sc,
+                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s);
 
 cudaError_t gs_launch_blend(const gs_record *records, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s);
+
+// Per-frame binning front end (two kernels): projection of every Gaussian with
+// key-slot reservation per block, then emission of the (tile, depth) keys of
+// the visible Gaussians with the digit histograms + bucket offsets of the sort.
+// counts[0] = K, counts[1] = visible Gaussians, counts[2] = K if it fits in
+// `capacity` else 0 (the sort and ranges then see an empty list and the
+// overflow bit is set in d_err). `scan_scratch`: gs_fused_scratch_bytes(n).
+size_t gs_fused_scratch_bytes(int64_t n);    // + gs_key_block_bytes(capacity)
+size_t gs_key_block_bytes(int64_t capacity);
+cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
+                                  gs_record *records, uint64_t *keys, uint32_t *values,
+                                  int64_t capacity, unsigned long long *counts, void *scan_scratch,
+                                  const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s);

@@ -7,7 +7,7 @@
 // memory itself and forbids libraries from taking more. Such callers cannot
 // create a gs_context (its workspace grows with cudaMalloc). This entry point
 // takes its scratch from one array that is part of the library image
-// instead: a file-scope __device__ array of kScratchBytes (about 4 MiB),
+// instead: a file-scope __device__ array of kScratchBytes (4-6 MiB),
 // which every GPU that loads libgs.so holds until the process exits.
 //
 // Rules of use:
@@ -31,8 +31,9 @@ constexpr int64_t kMaxPairs = GS_NOALLOC_SORT_MAX_PAIRS;
 constexpr size_t kAltKeysBytes = (size_t)kMaxPairs * 8;
 constexpr size_t kAltValsBytes = (size_t)kMaxPairs * 4;
 // Sort scratch for 64-bit keys (8 passes): a header of histograms and
-// counters below 32 KiB, and 8 x ceil(n / 4096) x 256 status words.
-constexpr size_t kSortScratchBytes = 32768 + (size_t)8 * ((kMaxPairs + 4095) / 4096) * 256 * 8;
+// counters below 32 KiB, and 8 x ceil(n / kSortTile) x 256 status words.
+constexpr size_t kSortScratchBytes =
+    32768 + (size_t)8 * ((kMaxPairs + kSortTile - 1) / kSortTile) * 256 * 8;
 constexpr size_t kErrOffset = kAltKeysBytes + kAltValsBytes + kSortScratchBytes;
 constexpr size_t kScratchBytes = kErrOffset + 256;
 

@@ -13,6 +13,8 @@
 //    a0 c0 - b^2), which avoids the cancellation of a c - b^2;
 //  * lambda_max = mid + sqrt(max(0.1, ((a - c)/2)^2 + b^2)), the same value as
 //    mid + sqrt(max(0.1, mid^2 - det)) without its cancellation.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace {
@@ -33,42 +35,6 @@ constexpr float kY3c = 0.45704579946446572f;   // sqrt(21 / (32 pi))
 constexpr float kY3d = 0.37317633259011540f;   // sqrt(7 / (16 pi))
 constexpr float kY3e = 1.4453057213202769f;    // sqrt(105 / (16 pi))
 
-template <int DEG>
-__device__ __forceinline__ float3 sh_colour(const float *__restrict__ c, float x, float y, float z) {
-    // c points at this Gaussian's (DEG+1)^2 x 3 coefficients.
-    auto C = [&](int k, float w, float3 acc) {
-        acc.x = fmaf(w, __ldg(c + 3 * k + 0), acc.x);
-        acc.y = fmaf(w, __ldg(c + 3 * k + 1), acc.y);
-        acc.z = fmaf(w, __ldg(c + 3 * k + 2), acc.z);
-        return acc;
-    };
-    float3 s = make_float3(0.f, 0.f, 0.f);
-    s = C(0, kY00, s);
-    if (DEG >= 1) {
-        s = C(1, -kY1 * y, s);
-        s = C(2, kY1 * z, s);
-        s = C(3, -kY1 * x, s);
-    }
-    if (DEG >= 2) {
-        float xx = x * x, yy = y * y, zz = z * z;
-        s = C(4, kY2a * x * y, s);
-        s = C(5, -kY2a * y * z, s);
-        s = C(6, kY2b * (2.f * zz - xx - yy), s);
-        s = C(7, -kY2a * x * z, s);
-        s = C(8, kY2c * (xx - yy), s);
-        if (DEG >= 3) {
-            s = C(9, -kY3a * y * (3.f * xx - yy), s);
-            s = C(10, kY3b * x * y * z, s);
-            s = C(11, -kY3c * y * (4.f * zz - xx - yy), s);
-            s = C(12, kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy), s);
-            s = C(13, -kY3c * x * (4.f * zz - xx - yy), s);
-            s = C(14, kY3e * z * (xx - yy), s);
-            s = C(15, -kY3a * x * (xx - 3.f * yy), s);
-        }
-    }
-    return make_float3(fmaxf(s.x + 0.5f, 0.f), fmaxf(s.y + 0.5f, 0.f), fmaxf(s.z + 0.5f, 0.f));
-}
-
 struct ProjectArgs {
     const float *means, *log_scales, *quats, *logits, *sh;
     int64_t n;
@@ -76,30 +42,91 @@ struct ProjectArgs {
     GsGrid grid;
     float4 *records;
     uint32_t *tiles;
+    bool sh_vec;    // SH rows 16-byte aligned: load them as float4
+    bool quat_vec;  // quaternion array 16-byte aligned
+};
+
+// SH colour of one Gaussian: the basis values along (x, y, z) first, then
+// the coefficients streamed in (as float4 when the rows are 16-byte aligned)
+// and accumulated per channel.
+template <int DEG>
+__device__ __forceinline__ float3 sh_colour(const float *__restrict__ src, bool vec, float x,
+                                            float y, float z) {
+    constexpr int kK = (DEG + 1) * (DEG + 1);
+    constexpr int kN = kK * 3;
+    float Y[kK];
+    Y[0] = kY00;
+    if (DEG >= 1) {
+        Y[1] = -kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = -kY1 * x;
+    }
+    if (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;
+        Y[5] = -kY2a * y * z;
+        Y[6] = kY2b * (2.f * zz - xx - yy);
+        Y[7] = -kY2a * x * z;
+        Y[8] = kY2c * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -kY3a * y * (3.f * xx - yy);
+            Y[10] = kY3b * x * y * z;
+            Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+            Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+            Y[14] = kY3e * z * (xx - yy);
+            Y[15] = -kY3a * x * (xx - 3.f * yy);
+        }
+    }
+    float acc[3] = {0.f, 0.f, 0.f};
+    if (kN % 4 == 0 && vec) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int j = 0; j < kN / 4; ++j) {
+            const float4 v = __ldg(s4 + j);
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                acc[(4 * j + q) % 3] = fmaf(Y[(4 * j + q) / 3], e[q], acc[(4 * j + q) % 3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kN; ++j) acc[j % 3] = fmaf(Y[j / 3], __ldg(src + j), acc[j % 3]);
+    }
+    return make_float3(fmaxf(acc[0] + 0.5f, 0.f), fmaxf(acc[1] + 0.5f, 0.f), fmaxf(acc[2] + 0.5f, 0.f));
+}
+
+// Result of projecting one Gaussian.
+struct Projected {
+    float4 r0, r1, r2;  // gs_record words
+    Rect rect;
+    uint32_t tiles;     // 0 when culled
 };
 
 template <int DEG>
-__global__ void __launch_bounds__(256) project_kernel(const ProjectArgs P) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+__device__ __forceinline__ Projected project_one(const ProjectArgs &P, int64_t i) {
+    Projected out;
+    out.tiles = 0;
     const GsCameraDev &K = P.cam;
     const float mx = __ldg(P.means + 3 * i), my = __ldg(P.means + 3 * i + 1),
                 mz = __ldg(P.means + 3 * i + 2);
     const float tx = fmaf(K.R[0], mx, fmaf(K.R[1], my, fmaf(K.R[2], mz, K.t[0])));
     const float ty = fmaf(K.R[3], mx, fmaf(K.R[4], my, fmaf(K.R[5], mz, K.t[1])));
+    // The other per-Gaussian inputs are loaded before the near-plane test so
+    // that all of them are in flight together (one memory round trip).
+    const float4 q = P.quat_vec ? __ldg(reinterpret_cast<const float4 *>(P.quats) + i)
+                                : make_float4(__ldg(P.quats + 4 * i), __ldg(P.quats + 4 * i + 1),
+                                              __ldg(P.quats + 4 * i + 2), __ldg(P.quats + 4 * i + 3));
+    const float ls0 = __ldg(P.log_scales + 3 * i), ls1 = __ldg(P.log_scales + 3 * i + 1),
+                ls2 = __ldg(P.log_scales + 3 * i + 2);
+    const float logit = __ldg(P.logits + i);
     const float tz = fmaf(K.R[6], mx, fmaf(K.R[7], my, fmaf(K.R[8], mz, K.t[2])));
-    if (!(tz > K.near_z)) {
-        P.tiles[i] = 0;
-        return;
-    }
+    if (!(tz > K.near_z)) return out;
 
     // Rotation of the normalised quaternion (w, x, y, z), scaled columns M = R S.
-    float qw = __ldg(P.quats + 4 * i), qx = __ldg(P.quats + 4 * i + 1),
-          qy = __ldg(P.quats + 4 * i + 2), qz = __ldg(P.quats + 4 * i + 3);
-    const float qinv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
-    const float sx = expf(__ldg(P.log_scales + 3 * i)), sy = expf(__ldg(P.log_scales + 3 * i + 1)),
-                sz = expf(__ldg(P.log_scales + 3 * i + 2));
+    const float qinv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const float qw = q.x * qinv, qx = q.y * qinv, qy = q.z * qinv, qz = q.w * qinv;
+    const float sx = expf(ls0), sy = expf(ls1), sz = expf(ls2);
     float M[3][3];
     M[0][0] = (1.f - 2.f * (qy * qy + qz * qz)) * sx;
     M[0][1] = 2.f * (qx * qy - qw * qz) * sy;
@@ -142,37 +169,310 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs P) {
     const float half_diff = 0.5f * (a - c);
     const float lam = 0.5f * (a + c) + sqrtf(fmaxf(0.1f, fmaf(half_diff, half_diff, b * b)));
     const float ext = 3.f * sqrtf(lam);
-    if (!(det > 0.f) || !isfinite(u) || !isfinite(v) || !isfinite(ext)) {
-        P.tiles[i] = 0;
-        return;
-    }
+    if (!(det > 0.f) || !isfinite(u) || !isfinite(v) || !isfinite(ext)) return out;
     const int r = ext >= (float)kMaxRadius ? kMaxRadius : (int)ceilf(ext);
+    if (r <= 0) return out;
     const Rect R = tile_rect(u, v, r, P.grid.tile_w, P.grid.tile_h, P.grid.tiles_x, P.grid.tiles_y);
     const uint32_t ntiles = (uint32_t)((R.x1 - R.x0) * (R.y1 - R.y0));
-    P.tiles[i] = r > 0 ? ntiles : 0u;
-    if (ntiles == 0 || r <= 0) return;
+    if (ntiles == 0) return out;
     const float idet = 1.f / det;
 
     // View direction from the camera centre to the mean.
     float dx = mx - K.C[0], dy = my - K.C[1], dz = mz - K.C[2];
     const float dinv = rsqrtf(dx * dx + dy * dy + dz * dz);
     dx *= dinv; dy *= dinv; dz *= dinv;
-    const float3 rgb = sh_colour<DEG>(P.sh + (size_t)i * (DEG + 1) * (DEG + 1) * 3, dx, dy, dz);
-    const float opacity = 1.f / (1.f + expf(-__ldg(P.logits + i)));
+    const float3 rgb = sh_colour<DEG>(P.sh + (size_t)i * (DEG + 1) * (DEG + 1) * 3, P.sh_vec, dx, dy, dz);
+    const float opacity = 1.f / (1.f + expf(-logit));
 
-    float4 *out = P.records + 3 * i;
-    out[0] = make_float4(u, v, c * idet, -b * idet);
-    out[1] = make_float4(a * idet, opacity, rgb.x, rgb.y);
-    out[2] = make_float4(rgb.z, tz, __int_as_float(r), __uint_as_float(ntiles));
+    out.r0 = make_float4(u, v, c * idet, -b * idet);
+    out.r1 = make_float4(a * idet, opacity, rgb.x, rgb.y);
+    out.r2 = make_float4(rgb.z, tz, __int_as_float(r), __uint_as_float(ntiles));
+    out.rect = R;
+    out.tiles = ntiles;
+    return out;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_kernel(const ProjectArgs P) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const Projected pr = project_one<DEG>(P, i);
+    P.tiles[i] = pr.tiles;
+    if (pr.tiles) {
+        float4 *out = P.records + 3 * i;
+        out[0] = pr.r0;
+        out[1] = pr.r1;
+        out[2] = pr.r2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Front end of a frame, two kernels:
+//  P. project_reserve_kernel: one thread per Gaussian projects it, writes the
+//     record of a visible one, and every block reserves, with one atomicAdd
+//     on a packed 64-bit counter (visible count << 33 | key count), a range of
+//     key slots and a range of entries of a compact list of visible
+//     Gaussians (index, first key slot).
+//  E. emit_keys_kernel: threads own runs of eight key slots, find their
+//     Gaussians in the compact list (whose first slots ascend) and write the
+//     keys — balanced however large a single splat is — while counting
+//     the tile digits of the sort (kernel P counts the depth digits, once per
+//     Gaussian). The last block turns the counts into bucket offsets and
+//     publishes the key count the sort should use.
+// The slot order depends on scheduling; the sort orders keys by (tile,
+// depth) and the ranges kernel then puts each run of equal keys in Gaussian
+// index order, so the final lists are exactly ordered by (tile, depth bits,
+// index).
+// ---------------------------------------------------------------------------
+constexpr int kMaxPasses = 8;
+constexpr unsigned long long kKeyMask = (1ull << 33) - 1;
+constexpr int kKeyBlockLog2 = 11;              // key slots per emission block: 2048
+constexpr int kKeyBlock = 1 << kKeyBlockLog2;
+constexpr int kKeysPerThread = kKeyBlock / 256;
+
+struct ReserveArgs {
+    ProjectArgs P;
+    unsigned long long *packed;  // visible << 33 | keys
+    uint32_t *list_idx;          // n: Gaussian index of visible entry j
+    uint32_t *list_off;          // n: its first key slot (ascending in j)
+    uint32_t *hist;              // sort digit counts (passes x 256); depth digits added here
+    uint32_t *block_entry;       // per 256-slot block of keys: the entry covering its first slot
+    int64_t n_key_blocks;        // ceil(capacity / 256)
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_reserve_kernel(const ReserveArgs A) {
+    __shared__ uint32_t s_t[8], s_v[8];
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_hist[4 * 256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = tid; k < 4 * 256; k += 256) s_hist[k] = 0;
+    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+    Projected pr;
+    pr.tiles = 0;
+    if (i < A.P.n) pr = project_one<DEG>(A.P, i);
+    if (pr.tiles) {
+        float4 *out = A.P.records + 3 * i;
+        out[0] = pr.r0;
+        out[1] = pr.r1;
+        out[2] = pr.r2;
+    }
+    const uint32_t t = pr.tiles, v = t != 0u;
+    uint32_t it = t, iv = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, it, o);
+        const uint32_t b = __shfl_up_sync(0xffffffffu, iv, o);
+        if (lane >= o) { it += a; iv += b; }
+    }
+    if (lane == 31) { s_t[warp] = it; s_v[warp] = iv; }
+    __syncthreads();
+    uint32_t pt = 0, pv = 0, bt = 0, bv = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < warp) { pt += s_t[w]; pv += s_v[w]; }
+        bt += s_t[w];
+        bv += s_v[w];
+    }
+    if (tid == 0) s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) : 0ull;
+    __syncthreads();
+    if (v) {
+        const unsigned long long base = s_base;
+        const uint64_t j = (base >> 33) + pv + iv - 1;
+        const uint64_t off = (base & kKeyMask) + pt + it - t;
+        A.list_idx[j] = (uint32_t)i;
+        A.list_off[j] = (uint32_t)off;
+        // Key blocks whose first slot falls in [off, off + t) start in entry j.
+        const int64_t b1 = min((int64_t)((off + t - 1) >> kKeyBlockLog2), A.n_key_blocks - 1);
+        for (int64_t b = (int64_t)((off + kKeyBlock - 1) >> kKeyBlockLog2); b <= b1; ++b)
+            A.block_entry[b] = (uint32_t)j;
+        // The four depth digits are shared by all t keys of this Gaussian.
+        const uint32_t dbits = __float_as_uint(pr.r2.y);
+        for (int d = 0; d < 4; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], t);
+    }
+    __syncthreads();
+    if (bv)
+        for (int k = tid; k < 4 * 256; k += 256)
+            if (s_hist[k]) atomicAdd(&A.hist[k], s_hist[k]);
+}
+
+struct EmitArgs {
+    const float4 *records;
+    const unsigned long long *packed;
+    const uint32_t *list_idx;
+    const uint32_t *list_off;
+    const uint32_t *block_entry;
+    GsGrid grid;
+    uint64_t *keys;
+    uint32_t *values;
+    int64_t capacity;
+    unsigned long long *counts;  // out: [0] K, [1] visible, [2] K if it fits else 0
+    GsSortScratch sc;
+    uint32_t *d_err;
+};
+
+// Block b covers key slots [2048 b, 2048 b + 2048), eight consecutive slots
+// per thread. The list entries covering them (at most 2049, first slots
+// ascending) are staged in shared memory; a thread finds the entry of its
+// first slot by binary search and walks forward. Digit counts of a thread's
+// run of keys are merged before they are added to the block's histogram.
+__global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
+    __shared__ uint32_t s_hist[kMaxPasses * 256];
+    __shared__ uint32_t s_off[kKeyBlock + 2], s_idx[kKeyBlock + 2];
+    __shared__ uint32_t s_tmp[8];
+    __shared__ int s_j0, s_cnt;
+    __shared__ bool s_last;
+    const int tid = threadIdx.x;
+    const int passes = E.sc.passes;
+    const GsGrid &G = E.grid;
+    for (int k = tid; k < kMaxPasses * 256; k += 256) s_hist[k] = 0;
+    const unsigned long long packed = *E.packed;
+    const int64_t K = (int64_t)(packed & kKeyMask);
+    const int64_t nv = (int64_t)(packed >> 33);
+    const int64_t k0 = (int64_t)blockIdx.x * kKeyBlock;
+    const bool active = k0 < K && K <= E.capacity;
+    if (tid == 0 && active) {
+        const int64_t j0 = E.block_entry[blockIdx.x];  // entry covering slot k0
+        s_j0 = (int)j0;
+        s_cnt = (int)((nv - j0) < kKeyBlock + 2 ? (nv - j0) : kKeyBlock + 2);
+    }
+    __syncthreads();
+    if (active) {
+        for (int q = tid; q < s_cnt; q += 256) {
+            s_off[q] = E.list_off[s_j0 + q];
+            s_idx[q] = E.list_idx[s_j0 + q];
+        }
+    }
+    __syncthreads();
+    const int64_t kb = k0 + (int64_t)tid * kKeysPerThread;
+    if (active && kb < K) {
+        int lo = 0, hi = s_cnt - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)s_off[mid] <= kb) lo = mid; else hi = mid - 1;
+        }
+        int e = -1;
+        uint32_t g = 0, dbits = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0;
+        uint32_t run_digit[kMaxPasses], run_count[kMaxPasses];
+        for (int d = 0; d < kMaxPasses; ++d) { run_digit[d] = 0xffffffffu; run_count[d] = 0; }
+        for (int q = 0; q < kKeysPerThread; ++q) {
+            const int64_t k = kb + q;
+            if (k >= K) break;
+            if (e < 0 || (uint64_t)k >= eend) {
+                if (e >= 0) ++lo;
+                while (lo + 1 < s_cnt && (int64_t)s_off[lo + 1] <= k) ++lo;
+                e = lo;
+                g = s_idx[e];
+                ebase = s_off[e];
+                const float4 r0 = E.records[3 * (size_t)g];
+                const float4 r2 = E.records[3 * (size_t)g + 2];
+                const Rect R = tile_rect(r0.x, r0.y, __float_as_int(r2.z), G.tile_w, G.tile_h, G.tiles_x,
+                                         G.tiles_y);
+                w = (uint32_t)(R.x1 - R.x0);
+                x0 = (uint32_t)R.x0;
+                y0 = (uint32_t)R.y0;
+                eend = ebase + w * (uint32_t)(R.y1 - R.y0);
+                dbits = __float_as_uint(r2.y);
+            }
+            const uint32_t m = (uint32_t)(k - ebase);
+            const uint32_t qy = m / w, rx = m - qy * w;
+            const uint32_t tile = (y0 + qy) * (uint32_t)G.tiles_x + x0 + rx;
+            E.keys[k] = ((uint64_t)tile << 32) | dbits;
+            E.values[k] = g;
+            for (int d = 4; d < passes; ++d) {
+                const uint32_t dg = (tile >> (8 * (d - 4))) & 255u;
+                if (dg != run_digit[d]) {
+                    if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
+                    run_digit[d] = dg;
+                    run_count[d] = 0;
+                }
+                ++run_count[d];
+            }
+        }
+        for (int d = 4; d < passes; ++d)
+            if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
+    }
+    __syncthreads();
+    if (active)
+        for (int q = tid + 4 * 256; q < passes * 256; q += 256)
+            if (s_hist[q]) atomicAdd(&E.sc.hist[q], s_hist[q]);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(E.sc.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    // Last block: every histogram is complete.
+    __threadfence();
+    for (int d = 0; d < passes; ++d) {
+        const uint32_t c = __ldcg(&E.sc.hist[d * 256 + tid]);
+        E.sc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
+    }
+    if (tid == 0) {
+        E.counts[0] = (unsigned long long)K;
+        E.counts[1] = (unsigned long long)nv;
+        const bool fits = K <= E.capacity;
+        if (!fits) atomicOr(E.d_err, kErrCapacity);
+        E.counts[2] = fits ? (unsigned long long)K : 0ull;
+    }
 }
 
 }  // namespace
+
+size_t gs_fused_scratch_bytes(int64_t n) {
+    // packed counter, then the compact list (index, first slot) of up to n
+    // entries; the per-key-block entry table follows (gs_key_block_bytes).
+    return 256 + 2 * (((size_t)(n > 0 ? n : 1) * 4 + 255) / 256 * 256);
+}
+
+size_t gs_key_block_bytes(int64_t capacity) {
+    return ((size_t)(capacity + kKeyBlock - 1) / kKeyBlock + 1) * 4;
+}
+
+cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
+                                  gs_record *records, uint64_t *keys, uint32_t *values,
+                                  int64_t capacity, unsigned long long *counts, void *scan_scratch,
+                                  const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s) {
+    // counts and the packed counter start at zero; the sort scratch was
+    // zeroed by the caller.
+    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    char *base = static_cast<char *>(scan_scratch);
+    e = cudaMemsetAsync(base, 0, 256, s);
+    if (e != cudaSuccess || g.n == 0) return e;
+    const size_t list_bytes = ((size_t)g.n * 4 + 255) / 256 * 256;
+    ReserveArgs A;
+    A.P = ProjectArgs{g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.n, cam, grid,
+                      reinterpret_cast<float4 *>(records), nullptr,
+                      reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
+                      reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
+    A.packed = reinterpret_cast<unsigned long long *>(base);
+    A.list_idx = reinterpret_cast<uint32_t *>(base + 256);
+    A.list_off = reinterpret_cast<uint32_t *>(base + 256 + list_bytes);
+    A.hist = sc.hist;
+    A.block_entry = reinterpret_cast<uint32_t *>(base + 256 + 2 * list_bytes);
+    A.n_key_blocks = (capacity + kKeyBlock - 1) / kKeyBlock;
+    const unsigned blocks = (unsigned)((g.n + 255) / 256);
+    switch (g.sh_degree) {
+        case 0: project_reserve_kernel<0><<<blocks, 256, 0, s>>>(A); break;
+        case 1: project_reserve_kernel<1><<<blocks, 256, 0, s>>>(A); break;
+        case 2: project_reserve_kernel<2><<<blocks, 256, 0, s>>>(A); break;
+        default: project_reserve_kernel<3><<<blocks, 256, 0, s>>>(A); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    EmitArgs E{reinterpret_cast<const float4 *>(records), A.packed, A.list_idx, A.list_off,
+               A.block_entry, grid, keys, values, capacity, counts, sc, d_err};
+    // One block per 2048 key slots of the capacity (blocks past K only take
+    // their ticket).
+    emit_keys_kernel<<<(unsigned)((capacity + kKeyBlock - 1) / kKeyBlock), 256, 0, s>>>(E);
+    return cudaGetLastError();
+}
 
 cudaError_t gs_launch_project(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                               gs_record *records, uint32_t *tiles, cudaStream_t s) {
     if (g.n == 0) return cudaSuccess;
     ProjectArgs a{g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.n, cam, grid,
-                  reinterpret_cast<float4 *>(records), tiles};
+                  reinterpret_cast<float4 *>(records), tiles,
+                  reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
+                  reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
     const int threads = 256;
     const unsigned blocks = (unsigned)((g.n + threads - 1) / threads);
     switch (g.sh_degree) {

@@ -2,7 +2,7 @@
 // from the Onesweep design (Adinets and Merrill, 2022): one up-front pass
 // builds the digit histograms of every pass at once, then each 8-bit digit
 // pass is a single launch in which every block
-//   1. takes the next partition of 4096 pairs (atomic counter, so blocks
+//   1. takes the next partition of kSortTile pairs (atomic counter, so blocks
 //      only wait on blocks that are already running),
 //   2. ranks its pairs by digit, stably, with warp match + per-warp counters,
 //   3. publishes its per-digit counts and resolves its global per-digit
@@ -12,24 +12,24 @@
 //      digit-contiguous runs, so global stores are coalesced.
 #include "gs_internal.cuh"
 
+#ifndef GS_SORT_MIN_BLOCKS
+#define GS_SORT_MIN_BLOCKS 2
+#endif
+#ifndef GS_SORT_HIST_AGG
+#define GS_SORT_HIST_AGG 0
+#endif
+
 namespace {
 
 using namespace gs;
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kSortThreads;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;  // pairs per partition
+constexpr int kItems = GS_SORT_ITEMS;
+constexpr int kTile = kSortTile;          // pairs per partition
+constexpr int kLookAhead = GS_SORT_LOOKAHEAD;  // status words read per look-back step
 constexpr int kRadix = 256;
 constexpr int kMaxPasses = 8;
-
-struct SortScratch {
-    uint32_t *hist;    // passes x 256
-    uint32_t *bucket;  // passes x 256, exclusive offsets of each digit
-    uint32_t *counter; // passes partition counters
-    uint32_t *ticket;  // 1
-    unsigned long long *status;  // passes x parts x 256
-};
 
 inline int64_t num_parts(int64_t n) { return (n + kTile - 1) / kTile; }
 
@@ -38,33 +38,7 @@ inline size_t header_bytes(int passes) {
     return (b + 255) & ~(size_t)255;
 }
 
-SortScratch carve(void *base, int64_t n, int passes) {
-    char *p = static_cast<char *>(base);
-    SortScratch s;
-    s.hist = reinterpret_cast<uint32_t *>(p);
-    s.bucket = s.hist + passes * kRadix;
-    s.counter = s.bucket + passes * kRadix;
-    s.ticket = s.counter + passes;
-    s.status = reinterpret_cast<unsigned long long *>(p + header_bytes(passes));
-    (void)n;
-    return s;
-}
-
-// Exclusive scan of one value per thread over a 256-thread block.
-__device__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t *s_tmp /* kWarps */) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_tmp[warp] = incl;
-    __syncthreads();
-    uint32_t pre = 0;
-    for (int w = 0; w < warp; ++w) pre += s_tmp[w];
-    __syncthreads();
-    return pre + incl - v;
-}
+using SortScratch = GsSortScratch;
 
 // Histograms of every digit pass; the last block to finish turns them into
 // exclusive bucket offsets.
@@ -75,10 +49,23 @@ histogram_kernel(const uint64_t *__restrict__ keys, int64_t n, int passes, SortS
     __shared__ bool s_last;
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) s_hist[i] = 0;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kThreads) {
-        const uint64_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * kRadix + ((k >> (8 * p)) & 255)], 1u);
+    // Neighbouring keys often share digits (the tiles of one Gaussian share
+    // its depth bits), so lanes with equal digits add once through a leader.
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t n_up = (n + 31) & ~(int64_t)31;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n_up; i += stride) {
+        const bool ok = i < n;
+        const uint64_t k = ok ? keys[i] : 0ull;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = ok ? (uint32_t)((k >> (8 * p)) & 255) : 256u;
+#if GS_SORT_HIST_AGG
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256u && (peers & lanemask_lt()) == 0u)
+                atomicAdd(&s_hist[p * kRadix + d], (uint32_t)__popc(peers));
+#else
+            if (d < 256u) atomicAdd(&s_hist[p * kRadix + d], 1u);
+#endif
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads)
@@ -96,10 +83,11 @@ histogram_kernel(const uint64_t *__restrict__ keys, int64_t n, int passes, SortS
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, GS_SORT_MIN_BLOCKS)
 onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
-                int pass, int64_t parts, SortScratch sc, uint32_t *d_err) {
+                uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n_host,
+                const unsigned long long *d_n, int pass, int64_t parts, SortScratch sc,
+                uint32_t *d_err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);                       // kTile
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kTile);            // kTile
@@ -116,6 +104,10 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     __syncthreads();
     const int64_t p = *s_part;
     const int64_t base = p * kTile;
+    // With a device-side count the grid covers the capacity; partitions past
+    // the count have nothing to do (no later partition waits on them).
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    if (base >= n) return;
 
     // Warp-striped load: warp w holds pairs [w*32*kItems, (w+1)*32*kItems) of
     // the partition, item j of lane l at offset j*32 + l (coalesced).
@@ -162,27 +154,40 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     const uint32_t doff = block_exclusive_scan_256(total, s_tmp);
     s_doff[digit] = doff;
 
-    // Decoupled look-back for this digit over partitions p-1, p-2, ...
+    // Decoupled look-back for this digit over partitions p-1, p-2, ...,
+    // reading kLookAhead status words per step so a chain of aggregates costs
+    // one memory latency per kLookAhead partitions.
     unsigned long long excl = 0;
     if (p > 0) {
         const unsigned long long t0 = global_ns();
         int64_t q = p - 1;
         uint32_t polls = 0;
-        while (q >= 0) {
-            const unsigned long long s = ld_relaxed_u64(st - (p - q) * kRadix);
-            const unsigned long long f = s >> 62;
-            if (f == 0) {
-                if ((++polls & 63u) == 0u &&
-                    ((global_ns() - t0 > kSpinTimeoutNs) || (ld_relaxed_u32(d_err) & kErrTimeout))) {
-                    atomicOr(d_err, kErrTimeout);
-                    __threadfence();
+        bool found = false;
+        while (q >= 0 && !found) {
+            unsigned long long sw[kLookAhead];
+#pragma unroll
+            for (int k = 0; k < kLookAhead; ++k)
+                sw[k] = (q - k >= 0) ? ld_relaxed_u64(st - (p - (q - k)) * kRadix) : 0ull;
+            int consumed = 0;
+#pragma unroll
+            for (int k = 0; k < kLookAhead; ++k) {
+                if (q - k < 0 || consumed != k) break;
+                const unsigned long long f = sw[k] >> 62;
+                if (f == 0) break;
+                excl += sw[k] & kValueMask;
+                ++consumed;
+                if (f == 2) {
+                    found = true;
                     break;
                 }
-                continue;
             }
-            excl += s & kValueMask;
-            if (f == 2) break;
-            --q;
+            q -= consumed;
+            if (!found && consumed == 0 && (++polls & 63u) == 0u &&
+                ((global_ns() - t0 > kSpinTimeoutNs) || (ld_relaxed_u32(d_err) & kErrTimeout))) {
+                atomicOr(d_err, kErrTimeout);
+                __threadfence();
+                break;
+            }
         }
         st_relaxed_u64(st, kFlagIncl | ((excl + total) & kValueMask));
     }
@@ -229,30 +234,35 @@ size_t gs_sort_scratch_bytes(int64_t n, int key_bits) {
     return header_bytes(passes) + (size_t)passes * parts * kRadix * sizeof(unsigned long long);
 }
 
-cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
-                           uint32_t *alt_values, int64_t n, int key_bits, void *scratch,
-                           uint32_t *d_err, bool *result_in_alt, cudaStream_t s) {
-    *result_in_alt = false;
-    if (n <= 1 || key_bits <= 0) return cudaSuccess;
+GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits) {
     const int passes = gs_sort_passes(key_bits);
-    const int64_t parts = num_parts(n);
-    cudaError_t e = cudaMemsetAsync(scratch, 0, gs_sort_scratch_bytes(n, key_bits), s);
-    if (e != cudaSuccess) return e;
-    SortScratch sc = carve(scratch, n, passes);
-    e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kOnesweepSmem);
-    if (e != cudaSuccess) return e;
-    const unsigned hist_blocks = (unsigned)(parts < 608 ? parts : 608);
-    histogram_kernel<<<hist_blocks, kThreads, 0, s>>>(keys, n, passes, sc);
-    e = cudaGetLastError();
+    char *p = static_cast<char *>(base);
+    GsSortScratch s;
+    s.hist = reinterpret_cast<uint32_t *>(p);
+    s.bucket = s.hist + passes * kRadix;
+    s.counter = s.bucket + passes * kRadix;
+    s.ticket = s.counter + passes;
+    s.status = reinterpret_cast<unsigned long long *>(p + header_bytes(passes));
+    s.passes = passes;
+    s.parts = num_parts(n_capacity) > 0 ? num_parts(n_capacity) : 1;
+    return s;
+}
+
+cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
+                                  uint32_t *alt_values, int64_t n_capacity,
+                                  const unsigned long long *d_n, const GsSortScratch &sc,
+                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s) {
+    *result_in_alt = false;
+    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kOnesweepSmem);
     if (e != cudaSuccess) return e;
     const uint64_t *kin = keys;
     const uint32_t *vin = values;
     uint64_t *kout = alt_keys;
     uint32_t *vout = alt_values;
-    for (int pass = 0; pass < passes; ++pass) {
-        onesweep_kernel<<<(unsigned)parts, kThreads, kOnesweepSmem, s>>>(kin, vin, kout, vout, n, pass,
-                                                                        parts, sc, d_err);
+    for (int pass = 0; pass < sc.passes; ++pass) {
+        onesweep_kernel<<<(unsigned)sc.parts, kThreads, kOnesweepSmem, s>>>(
+            kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         kin = kout;
@@ -260,6 +270,22 @@ cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
         kout = (kout == alt_keys) ? keys : alt_keys;
         vout = (vout == alt_values) ? values : alt_values;
     }
-    *result_in_alt = (passes & 1) != 0;
+    *result_in_alt = (sc.passes & 1) != 0;
     return cudaSuccess;
+}
+
+cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
+                           uint32_t *alt_values, int64_t n, int key_bits, void *scratch,
+                           uint32_t *d_err, bool *result_in_alt, cudaStream_t s) {
+    *result_in_alt = false;
+    if (n <= 1 || key_bits <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, gs_sort_scratch_bytes(n, key_bits), s);
+    if (e != cudaSuccess) return e;
+    const GsSortScratch sc = gs_sort_carve(scratch, n, key_bits);
+    const unsigned hist_blocks = (unsigned)(sc.parts < 608 ? sc.parts : 608);
+    histogram_kernel<<<hist_blocks, kThreads, 0, s>>>(keys, n, sc.passes, sc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return gs_launch_sort_passes(keys, values, alt_keys, alt_values, n, nullptr, sc, d_err,
+                                 result_in_alt, s);
 }
