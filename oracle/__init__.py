@@ -69,6 +69,9 @@ def lib():
         L.gso_blend_bruteforce.argtypes = [i64, P, P, P, P, P, P, P, i32, i32, i32, i32,
                                            P, P, P, P, P, P]
         L.gso_blend_bruteforce.restype = None
+        L.gso_render_backward.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, i32, i32, P, P,
+                                          P, P, P, P, P, P]
+        L.gso_render_backward.restype = None
         _lib = L
     return _lib
 
@@ -234,3 +237,36 @@ def render(scene, cam, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0)):
     img = blend(pr.mean2d, pr.conic, pr.opacity, pr.rgb, bn.values, bn.ranges,
                 cam.width, cam.height, tile_w, tile_h, bg)
     return pr, bn, img
+
+
+# ---------------------------------------------------------------------------
+# Gradients
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Grads:
+    means: np.ndarray          # (n,3)
+    log_scales: np.ndarray     # (n,3)
+    quats: np.ndarray          # (n,4)
+    opacity_logits: np.ndarray # (n,)
+    sh: np.ndarray             # (n,K,3)
+    record: np.ndarray         # (n,9) dL/d(u, v, Q00, Q01, Q11, opacity, r, g, b)
+
+
+def render_backward(scene, cam, dL_dC, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0)) -> Grads:
+    """FP64 gradient of L = sum dL_dC * C with respect to every parameter:
+    Eq. 1 differentiated per pixel over its contributors, the projection
+    differentiated with dual numbers."""
+    n = int(np.asarray(scene.means).shape[0])
+    K = (int(scene.sh_degree) + 1) ** 2
+    cf, w, h = _cam(cam)
+    g = _f64(dL_dC).reshape(h, w, 3)
+    out = Grads(np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 4)), np.zeros(n),
+                np.zeros((n, K, 3)), np.zeros((n, 9)))
+    arrs = [_f64(scene.means), _f64(scene.log_scales), _f64(scene.quats),
+            _f64(scene.opacity_logits), _f64(scene.sh)]
+    b = _f64(bg)
+    lib().gso_render_backward(n, *[_p(a) for a in arrs], int(scene.sh_degree), _p(cf), w, h,
+                              tile_w, tile_h, _p(b), _p(g), _p(out.means), _p(out.log_scales),
+                              _p(out.quats), _p(out.opacity_logits), _p(out.sh), _p(out.record))
+    return out

@@ -13,29 +13,28 @@ SRC = os.path.join(ROOT, "oracle", "gs_oracle.cpp")
 
 MUTATIONS = {
     "no_dilation": ("const double kDilation = 0.3;", "const double kDilation = 0.0;"),
-    "conic_offdiag_sign": ("Q01 = -cov[0][1] / det", "Q01 = cov[0][1] / det"),
+    "conic_offdiag_sign": ("P.q[1] = -cov[0][1] / det", "P.q[1] = cov[0][1] / det"),
     "quat_sign": ("R[0][1] = 2 * (x * y - w * z);", "R[0][1] = 2 * (x * y + w * z);"),
-    "camera_rotation_transposed": ("matmul3(cam.R, Sigma, tmp);\n        matmul3(tmp, Wt, Sc);",
-                                   "matmul3(Wt, Sigma, tmp);\n        matmul3(tmp, cam.R, Sc);"),
+    "camera_rotation_transposed": ("matmul3(cam.R, Sigma, tmp);\n    matmul3(tmp, Wt, Sc);",
+                                   "matmul3(Wt, Sigma, tmp);\n    matmul3(tmp, cam.R, Sc);"),
     "alpha_clamp": ("const double kAlphaMax = 0.99;", "const double kAlphaMax = 1.0;"),
     "no_alpha_skip": ("if (alpha < kAlphaMin) continue;", "if (alpha <= 0.0) continue;"),
     "stop_after_adding": ("if (Tn < kTMin) break;\n        for (int ch = 0; ch < 3; ++ch) o.c[ch] += rgb[3 * g + ch] * alpha * T;",
                           "for (int ch = 0; ch < 3; ++ch) o.c[ch] += rgb[3 * g + ch] * alpha * T;\n        if (Tn < kTMin) break;"),
     "rect_off_by_one": ("rect[2] = tile_coord(u + (double)r + (tw - 1), tw, tiles_x);",
                         "rect[2] = tile_coord(u + (double)r + tw, tw, tiles_x);"),
-    "sh_sin_cos_swapped": ("if (m > 0) return std::sqrt(2.0) * K * std::cos(am * phi) * P;",
-                           "if (m > 0) return std::sqrt(2.0) * K * std::sin(am * phi) * P;"),
-    "sh_index": ("s += sh[(i * K + l * l + l + m) * 3 + ch]", "s += sh[(i * K + l * l + l - m) * 3 + ch]"),
+    "sh_sin_cos_swapped": ("if (m > 0) return std::sqrt(2.0) * K * cos(am * phi) * P;",
+                           "if (m > 0) return std::sqrt(2.0) * K * sin(am * phi) * P;"),
+    "sh_index": ("s = s + coef[(l * l + l + m) * 3 + ch]", "s = s + coef[(l * l + l - m) * 3 + ch]"),
     "sort_ignores_depth": ("items.emplace_back(ty * tiles_x + tx, f32_bits(depth[i]), i);",
                            "items.emplace_back(ty * tiles_x + tx, 0u, i);"),
     "guard_band": ("const double kGuard = 1.3;", "const double kGuard = 1.6;"),
-    "eigen_floor": ("std::max(0.1, mid * mid - det)", "std::max(0.0, mid * mid - det)"),
-    "near_inclusive": ("if (!(t[2] > cam.near_z)) continue;", "if (!(t[2] >= cam.near_z)) continue;"),
-    "jacobian_sign": ("{0.0, cam.fy / t[2], -cam.fy * ry / t[2]}", "{0.0, cam.fy / t[2], cam.fy * ry / t[2]}"),
+    "eigen_floor": ("std::max(0.1, mid * mid - val(det))", "std::max(0.0, mid * mid - val(det))"),
+    "near_inclusive": ("if (!(val(t[2]) > cam.near_z)) return false;", "if (!(val(t[2]) >= cam.near_z)) return false;"),
+    "jacobian_sign": ("{T(0.0), cam.fy / t[2], -cam.fy * ry / t[2]}", "{T(0.0), cam.fy / t[2], cam.fy * ry / t[2]}"),
     "pixel_centre": ("x + 0.5, y + 0.5, last - first", "x, y, last - first"),
-    "opacity_not_sigmoid": ("opacity[i] = 1.0 / (1.0 + std::exp(-opacity_logits[i]));",
-                            "opacity[i] = 1.0 / (1.0 + std::exp(opacity_logits[i]));"),
-    "colour_no_offset": ("rgb[3 * i + ch] = std::max(0.0, s + 0.5);", "rgb[3 * i + ch] = std::max(0.0, s);"),
+    "opacity_not_sigmoid": ("P.o = 1.0 / (1.0 + exp(-logit));", "P.o = 1.0 / (1.0 + exp(logit));"),
+    "colour_no_offset": ("P.rgb[ch] = vmax(s + 0.5, 0.0);", "P.rgb[ch] = vmax(s, 0.0);"),
 }
 
 
