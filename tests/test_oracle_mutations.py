@@ -18,7 +18,8 @@ MUTATIONS = {
     "camera_rotation_transposed": ("matmul3(cam.R, Sigma, tmp);\n    matmul3(tmp, Wt, Sc);",
                                    "matmul3(Wt, Sigma, tmp);\n    matmul3(tmp, cam.R, Sc);"),
     "alpha_clamp": ("const double kAlphaMax = 0.99;", "const double kAlphaMax = 1.0;"),
-    "no_alpha_skip": ("if (alpha < kAlphaMin) continue;", "if (alpha <= 0.0) continue;"),
+    "no_alpha_skip": ("o.flag = 1;\n        if (alpha < kAlphaMin) continue;",
+                      "o.flag = 1;\n        if (alpha <= 0.0) continue;"),
     "stop_after_adding": ("if (Tn < kTMin) break;\n        for (int ch = 0; ch < 3; ++ch) o.c[ch] += rgb[3 * g + ch] * alpha * T;",
                           "for (int ch = 0; ch < 3; ++ch) o.c[ch] += rgb[3 * g + ch] * alpha * T;\n        if (Tn < kTMin) break;"),
     "rect_off_by_one": ("rect[2] = tile_coord(u + (double)r + (tw - 1), tw, tiles_x);",
