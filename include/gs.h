@@ -220,6 +220,37 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
 gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
                     const gs_options *opts, const gs_framebuffer *fb, void *stream);
 
+/* Gradients of the Gaussian parameters (device, caller-owned, overwritten):
+ * shapes as in gs_gaussians. d_records is optional: n x 9 floats receive
+ * dL/d(u, v, Q00, Q01, Q11, opacity, r, g, b) of every projected record. */
+typedef struct {
+    float *d_means;
+    float *d_log_scales;
+    float *d_quats;
+    float *d_opacity_logits;
+    float *d_sh;
+    float *d_records;
+} gs_grads;
+
+/* Backward of the last gs_render made on this context (the paper's Sec. 7
+ * names the backward pass as the next step; Eq. 1 and the projection of
+ * Sec. 3.1 differentiated). Given dL/dC for that image (d_rgb, height x
+ * width x 3), writes dL/d(parameters) for a loss L of the image:
+ *   blend: each tile walked back to front from each pixel's last
+ *   contributor, transmittance recovered from the final T
+ *   (T_k = T_{k+1} / (1 - alpha_k)); alpha = min(0.99, o G) has no
+ *   derivative where it is clamped; skipped and stopped Gaussians none.
+ *   projection: chain rule through the conic inverse, J W R S, the
+ *   normalised quaternion, exp of the log-scales, the sigmoid and the SH
+ *   colour (zero where a channel was clamped at 0). The rect and radius are
+ *   discrete and have no derivative.
+ * g, cam and opts must be those of that gs_render, and fb must hold the
+ * final_T and n_contrib it wrote (both required here). Invisible Gaussians
+ * get zero gradients. */
+gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
+                             const gs_options *opts, const gs_framebuffer *fb, const float *d_rgb,
+                             const gs_grads *out, void *stream);
+
 /* Sets the number of (tile, Gaussian) pairs gs_render's key buffers hold and
  * stops the context from shrinking it between frames (the buffers grow if a
  * frame needs more). */

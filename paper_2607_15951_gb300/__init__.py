@@ -19,6 +19,7 @@ __all__ = ["GSError", "Context", "camera_struct", "options_struct", "gaussians_s
            "gs_create", "gs_destroy", "gs_project", "gs_bin", "gs_sort_pairs", "gs_tile_ranges",
            "gs_blend", "gs_render", "gs_sync_status", "gs_last_render_stats",
            "gs_set_stage_timing", "gs_last_stage_times", "gs_sort_pairs_noalloc", "gs_reserve_keys",
+           "gs_render_backward", "RasterizeGaussians",
            "RECORD_FLOATS"]
 
 RECORD_FLOATS = 12  # gs_record is 48 bytes = 12 x 4-byte words
@@ -208,6 +209,23 @@ def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_c
                                ctypes.byref(fb), _stream(stream)))
 
 
+def gs_render_backward(ctx: Context, g: dict, sh_degree: int, cam, final_T, n_contrib, d_rgb,
+                       grads: dict, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), stream=None) -> None:
+    """grads: dict of CUDA tensors shaped like g (keys means, log_scales, quats,
+    opacity_logits, sh) and optionally 'records' (n, 9)."""
+    gs = gaussians_struct(g, sh_degree)
+    c, o = camera_struct(cam), options_struct(tile, bg)
+    fb = _fb(None, final_T, n_contrib, None)
+    out = N.gs_grads()
+    out.d_means, out.d_log_scales, out.d_quats = (_ptr(grads["means"]), _ptr(grads["log_scales"]),
+                                                  _ptr(grads["quats"]))
+    out.d_opacity_logits, out.d_sh = _ptr(grads["opacity_logits"]), _ptr(grads["sh"])
+    out.d_records = _ptr(grads.get("records"))
+    ctx.check(_lib().gs_render_backward(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
+                                        ctypes.byref(fb), _ptr(d_rgb), ctypes.byref(out),
+                                        _stream(stream)))
+
+
 def gs_last_render_stats(ctx: Context) -> dict:
     s = N.gs_render_stats()
     ctx.check(_lib().gs_last_render_stats(ctx.handle, ctypes.byref(s)))
@@ -254,3 +272,50 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
               out.get("n_eval"), tile=tile, bg=bg, variant=variant, stream=stream)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Autograd (marshalling only: forward -> gs_render, backward -> gs_render_backward)
+# ---------------------------------------------------------------------------
+
+def _autograd_function():
+    import torch
+
+    class _Rasterize(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree, tile, bg):
+            g = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
+                 "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
+                 "sh": sh.contiguous()}
+            out = render(ctx, g, sh_degree, cam, tile=tile, bg=bg)
+            fctx.gs = (ctx, cam, sh_degree, tile, bg, g)
+            fctx.save_for_backward(out["final_T"], out["n_contrib"])
+            fctx.mark_non_differentiable(out["final_T"])
+            return out["rgb"], out["final_T"]
+
+        @staticmethod
+        def backward(fctx, d_rgb, d_T):
+            ctx, cam, sh_degree, tile, bg, g = fctx.gs
+            final_T, n_contrib = fctx.saved_tensors
+            grads = {k: torch.empty_like(v) for k, v in g.items()}
+            gs_render_backward(ctx, g, sh_degree, cam, final_T, n_contrib, d_rgb.contiguous(), grads,
+                               tile=tile, bg=bg)
+            return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
+                    grads["sh"], None, None, None, None, None)
+
+    return _Rasterize
+
+
+_RASTERIZE = None
+
+
+def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Context, cam, sh_degree: int,
+                       tile=(16, 16), bg=(0.0, 0.0, 0.0)):
+    """Differentiable render: returns (rgb (H,W,3), final_T (H,W)); gradients
+    flow to the five parameter tensors. The backward of a render must run
+    before the next render on the same context."""
+    global _RASTERIZE
+    if _RASTERIZE is None:
+        _RASTERIZE = _autograd_function()
+    return _RASTERIZE.apply(means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree,
+                            tuple(tile), tuple(bg))

@@ -52,6 +52,11 @@ class gs_framebuffer(ctypes.Structure):
     _fields_ = [("rgb", vp), ("final_T", vp), ("n_contrib", vp), ("n_eval", vp)]
 
 
+class gs_grads(ctypes.Structure):
+    _fields_ = [("d_means", vp), ("d_log_scales", vp), ("d_quats", vp), ("d_opacity_logits", vp),
+                ("d_sh", vp), ("d_records", vp)]
+
+
 class gs_options(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("bg", ctypes.c_float * 3), ("record_dtype", ctypes.c_int32),
@@ -92,6 +97,9 @@ SIGNATURES = {
                                  ctypes.POINTER(gs_options), ctypes.POINTER(gs_framebuffer), vp]),
     "gs_last_render_stats": (ctypes.c_int, [vp, ctypes.POINTER(gs_render_stats)]),
     "gs_reserve_keys": (ctypes.c_int, [vp, ctypes.c_int64]),
+    "gs_render_backward": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
+                                          ctypes.POINTER(gs_options), ctypes.POINTER(gs_framebuffer),
+                                          vp, ctypes.POINTER(gs_grads), vp]),
     "gs_set_stage_timing": (ctypes.c_int, [vp, ctypes.c_int]),
     "gs_last_stage_times": (ctypes.c_int, [vp, ctypes.POINTER(gs_stage_times)]),
 }

@@ -28,6 +28,12 @@ struct gs_context {
     DevBuf records, tiles, offsets, scan_scratch, keys, values, alt_keys, alt_values, sort_scratch,
         ranges;
     gs_render_stats stats{};
+    // State of the last gs_render, for gs_render_backward.
+    bool have_last = false;
+    int64_t last_n = 0;
+    int last_w = 0, last_h = 0, last_tw = 0, last_th = 0;
+    const uint32_t *last_values = nullptr;
+    DevBuf d_rec;
     int64_t key_capacity = 0;  // pairs the render path's key buffers hold
     bool pinned_capacity = false;  // set by gs_reserve_keys: do not shrink
     DevBuf fused_scratch;
@@ -282,7 +288,7 @@ void gs_destroy(gs_context *ctx) {
     DeviceGuard g(ctx->device);
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                       &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
-                      &ctx->fused_scratch};
+                      &ctx->fused_scratch, &ctx->d_rec};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -308,7 +314,7 @@ size_t gs_workspace_bytes(const gs_context *ctx) {
     if (!ctx) return 0;
     const DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                             &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch,
-                            &ctx->ranges, &ctx->fused_scratch};
+                            &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec};
     size_t t = 0;
     for (const DevBuf *b : bufs) t += b->bytes;
     return t;
@@ -478,6 +484,13 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             continue;
         }
         if (ctx->timing) ctx->timed_once = true;
+        ctx->have_last = true;
+        ctx->last_n = n;
+        ctx->last_w = cam->width;
+        ctx->last_h = cam->height;
+        ctx->last_tw = grid.tile_w;
+        ctx->last_th = grid.tile_h;
+        ctx->last_values = sv;
         // Keep about 25 % headroom over this frame's count for the next one
         // (the buffers themselves only grow).
         if (!ctx->pinned_capacity && (int64_t)K * 2 < cap)
@@ -486,6 +499,39 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         return GS_OK;
     }
     return fail(ctx, GS_ERR_CAPACITY, "key buffers could not be sized for this frame");
+}
+
+gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
+                             const gs_options *opts, const gs_framebuffer *fb, const float *d_rgb,
+                             const gs_grads *out, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    gs_status st;
+    if ((st = check_gaussians(ctx, g)) != GS_OK || (st = check_camera(ctx, cam)) != GS_OK ||
+        (st = check_options(ctx, opts)) != GS_OK)
+        return st;
+    if (!fb || !fb->final_T || !fb->n_contrib || !d_rgb || !out)
+        return fail(ctx, GS_ERR_INVALID_ARG, "final_T, n_contrib, d_rgb and the gradient struct are required");
+    if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
+        return fail(ctx, GS_ERR_INVALID_ARG, "a gradient array is NULL");
+    if (!ctx->have_last || ctx->last_n != g->n || ctx->last_w != cam->width || ctx->last_h != cam->height ||
+        ctx->last_tw != opts->tile_w || ctx->last_th != opts->tile_h)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward must follow gs_render of the same scene and camera");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const GsGrid grid = make_grid(cam, opts);
+    const int64_t n = g->n;
+    if ((st = ensure(ctx, ctx->d_rec, (size_t)(n > 0 ? n : 1) * 9 * sizeof(float), "record gradients")) != GS_OK)
+        return st;
+    float *d_rec = static_cast<float *>(ctx->d_rec.ptr);
+    GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)n * 9 * sizeof(float), s));
+    GS_CUDA(ctx, gs_launch_blend_bwd(static_cast<gs_record *>(ctx->records.ptr), ctx->last_values,
+                                     static_cast<uint32_t *>(ctx->ranges.ptr), grid, cam->width, cam->height,
+                                     opts->bg, d_rgb, fb->final_T, fb->n_contrib, d_rec, s));
+    GS_CUDA(ctx, gs_launch_project_bwd(*g, make_cam(cam), grid, d_rec, *out, s));
+    if (out->d_records && n > 0)
+        GS_CUDA(ctx, cudaMemcpyAsync(out->d_records, d_rec, (size_t)n * 9 * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, s));
+    return GS_OK;
 }
 
 gs_status gs_reserve_keys(gs_context *ctx, int64_t key_capacity) {

@@ -262,3 +262,225 @@ cudaError_t gs_launch_blend(const gs_record *records, const uint32_t *values, co
     }
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Backward of the blend (Eq. 1 differentiated). For a pixel with contributors
+// k = 1..m (alpha_k, T_k the transmittance in front of k, T_N the final one):
+//   dC/dc_k     = alpha_k T_k
+//   dC/dalpha_k = c_k T_k - (S_k + bg T_N) / (1 - alpha_k),
+//   S_k = sum_{l>k} c_l alpha_l T_l,
+// and alpha = min(0.99, o G) (no derivative where clamped), G = 2^e. Each tile
+// is walked back to front from its pixels' last contributors; T_k is
+// recovered as T_{k+1} / (1 - alpha_k) from the stored final T, and S grows as
+// the walk goes. Same warp layout and the same conservative record culling
+// as the forward kernel. Per record the 9 gradients
+// (u, v, Q00, Q01, Q11, opacity, r, g, b) are summed over the warp (transpose
+// reduction), over the block in shared memory, then added to global memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BlendBwdArgs {
+    const float4 *records;
+    const uint32_t *values;
+    const uint32_t *ranges;
+    GsGrid grid;
+    int width, height;
+    float bg[3];
+    const float *d_rgb;
+    const float *final_T;
+    const int32_t *n_contrib;
+    float *d_rec;  // n x 9
+};
+
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Sum of 9 values over the warp; lane l ends with slot (l >> 1) & 15.
+__device__ __forceinline__ float warp_sum9(float v[16], int lane) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? v[i] : v[i + 8];
+        const float keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? v[i] : v[i + 4];
+        const float keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? v[i] : v[i + 2];
+        const float keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+struct PixB {
+    float T, TN, S[3], g[3];
+    int32_t last;
+};
+
+// One backward step of a pixel at list position pos; adds the record's
+// gradients into acc (9 slots).
+__device__ __forceinline__ bool composite_bwd(PixB &p, float e, float o, float thr, float cr, float cg,
+                                              float cb, float dx, float dy, float q00, float q01,
+                                              float q11, const float bg[3], float acc[16]) {
+    if (e > 0.f || e < thr) return false;
+    const float G = ex2(e);
+    const float raw = o * G;
+    const float alpha = fminf(kAlphaMax, raw);
+    const float inv = 1.f / (1.f - alpha);
+    const float Tk = p.T * inv;
+    const float c[3] = {cr, cg, cb};
+    float dL_dalpha = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        dL_dalpha = fmaf(p.g[ch], fmaf(c[ch], Tk, -(p.S[ch] + bg[ch] * p.TN) * inv), dL_dalpha);
+        acc[6 + ch] = fmaf(p.g[ch], alpha * Tk, acc[6 + ch]);
+        p.S[ch] = fmaf(c[ch], alpha * Tk, p.S[ch]);
+    }
+    p.T = Tk;
+    if (raw < kAlphaMax) {
+        acc[5] = fmaf(dL_dalpha, G, acc[5]);
+        const float dp = dL_dalpha * raw;  // dL/dpower
+        acc[0] = fmaf(dp, fmaf(q00, dx, q01 * dy), acc[0]);
+        acc[1] = fmaf(dp, fmaf(q01, dx, q11 * dy), acc[1]);
+        acc[2] = fmaf(dp, -0.5f * dx * dx, acc[2]);
+        acc[3] = fmaf(dp, -dx * dy, acc[3]);
+        acc[4] = fmaf(dp, -0.5f * dy * dy, acc[4]);
+    }
+    return true;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_bwd_kernel(const BlendBwdArgs a) {
+    constexpr int kWX = TW / 8, kWarps = kWX * (TH / 8), kThreads = kWarps * 32;
+    __shared__ float4 s_a[kBatch], s_b[kBatch], s_box[kBatch];
+    __shared__ float2 s_rg[kBatch];
+    __shared__ float s_grad[kBatch * 9];
+    __shared__ uint32_t s_g[kBatch];
+    __shared__ int s_maxlast;
+    const SRec S{s_a, s_b, s_rg, s_box};
+
+    const int tile = blockIdx.x;
+    const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bx = tx * TW + (warp % kWX) * 8, by = ty * TH + (warp / kWX) * 8;
+    const int px = bx + (lane & 7), py0 = by + (lane >> 3), py1 = py0 + 4;
+    const float fx = px + 0.5f, fy0 = py0 + 0.5f, fy1 = py1 + 0.5f;
+    const float wx0 = bx + 0.5f, wx1 = fminf(bx + 7.5f, a.width - 0.5f);
+    const float wy0 = by + 0.5f, wy1 = fminf(by + 7.5f, a.height - 0.5f);
+    const uint32_t first = a.ranges[2 * tile];
+
+    PixB p[2];
+    const int pys[2] = {py0, py1};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const bool in = px < a.width && pys[q] < a.height;
+        const size_t i = in ? (size_t)pys[q] * a.width + px : 0;
+        p[q].T = in ? a.final_T[i] : 1.f;
+        p[q].TN = p[q].T;
+        p[q].last = in ? a.n_contrib[i] : 0;
+        for (int ch = 0; ch < 3; ++ch) {
+            p[q].S[ch] = 0.f;
+            p[q].g[ch] = in ? a.d_rgb[3 * i + ch] : 0.f;
+        }
+    }
+    if (tid == 0) s_maxlast = 0;
+    for (int s = tid; s < kBatch * 9; s += kThreads) s_grad[s] = 0.f;
+    __syncthreads();
+    const int my_last = max(p[0].last, p[1].last);
+    const int wmax = __reduce_max_sync(0xffffffffu, my_last);
+    if (lane == 0) atomicMax(&s_maxlast, wmax);
+    __syncthreads();
+    const int max_last = s_maxlast;
+    const float fy[2] = {fy0, fy1};
+
+    // Batches of positions (end - kBatch, end], end going down from max_last.
+    for (int end = max_last; end > 0; end -= kBatch) {
+        const int beg = max(0, end - kBatch);  // positions beg+1 .. end
+        const int cnt = end - beg;
+        for (int s = tid; s < cnt; s += kThreads) {
+            const uint32_t g = a.values[first + beg + s];
+            s_g[s] = g;
+            stage_record(a.records, g, s, S, true);
+        }
+        __syncthreads();
+        if (wmax > beg) {
+            for (int c = ((cnt - 1) / 32) * 32; c >= 0; c -= 32) {
+                const int j = c + lane;
+                bool hit = false;
+                if (j < cnt) {
+                    const float4 b4 = s_box[j];
+                    hit = b4.x <= wx1 && b4.y >= wx0 && b4.z <= wy1 && b4.w >= wy0;
+                }
+                uint32_t bits = __ballot_sync(0xffffffffu, hit);
+                while (bits) {
+                    const int hb = 31 - __clz(bits);
+                    bits &= ~(1u << hb);
+                    const int jj = c + hb;
+                    const int pos = beg + jj + 1;
+                    const float4 ra = s_a[jj];
+                    const float4 rb = s_b[jj];
+                    const float2 rg = s_rg[jj];
+                    const float q00 = -2.f * kLn2 * ra.z, q01 = -kLn2 * ra.w, q11 = -2.f * kLn2 * rb.x;
+                    const float dx = fx - ra.x;
+                    const float adx2 = ra.z * dx * dx, bdx = ra.w * dx;
+                    float acc[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+                    bool any = false;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (pos > p[q].last) continue;
+                        const float dy = fy[q] - ra.y;
+                        const float e = fmaf(dy, fmaf(rb.x, dy, bdx), adx2);
+                        any |= composite_bwd(p[q], e, rb.y, rb.z, rg.x, rg.y, rb.w, dx, dy, q00, q01, q11,
+                                             a.bg, acc);
+                    }
+                    if (__any_sync(0xffffffffu, any)) {
+                        const float v = warp_sum9(acc, lane);
+                        const int slot = (lane >> 1) & 15;
+                        if ((lane & 1) == 0 && slot < 9 && v != 0.f) atomicAdd(&s_grad[jj * 9 + slot], v);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int s = tid; s < cnt * 9; s += kThreads) {
+            const float v = s_grad[s];
+            if (v != 0.f) {
+                atomicAdd(&a.d_rec[(size_t)s_g[s / 9] * 9 + s % 9], v);
+                s_grad[s] = 0.f;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t gs_launch_blend_bwd(const gs_record *records, const uint32_t *values, const uint32_t *ranges,
+                                const GsGrid &grid, int width, int height, const float bg[3],
+                                const float *d_rgb, const float *final_T, const int32_t *n_contrib,
+                                float *d_rec, cudaStream_t s) {
+    BlendBwdArgs a{reinterpret_cast<const float4 *>(records), values, ranges, grid, width, height,
+                   {bg[0], bg[1], bg[2]}, d_rgb, final_T, n_contrib, d_rec};
+    const unsigned blocks = (unsigned)(grid.tiles_x * grid.tiles_y);
+    const int tw = grid.tile_w, th = grid.tile_h;
+    if (tw == 16 && th == 16) blend_bwd_kernel<16, 16><<<blocks, 128, 0, s>>>(a);
+    else if (tw == 16 && th == 8) blend_bwd_kernel<16, 8><<<blocks, 64, 0, s>>>(a);
+    else blend_bwd_kernel<8, 8><<<blocks, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}

@@ -245,3 +245,11 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
                                   gs_record *records, uint64_t *keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s);
+
+// Backward kernels.
+cudaError_t gs_launch_blend_bwd(const gs_record *records, const uint32_t *values, const uint32_t *ranges,
+                                const GsGrid &grid, int width, int height, const float bg[3],
+                                const float *d_rgb, const float *final_T, const int32_t *n_contrib,
+                                float *d_rec, cudaStream_t s);
+cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
+                                  const float *d_rec, const gs_grads &out, cudaStream_t s);

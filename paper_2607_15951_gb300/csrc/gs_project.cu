@@ -483,3 +483,234 @@ cudaError_t gs_launch_project(const gs_gaussians &g, const GsCameraDev &cam, con
     }
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Backward of the projection: from dL/d(u, v, Q00, Q01, Q11, opacity, r, g, b)
+// of each record to the Gaussian's parameters, by the chain rule written out
+// in reverse order of the forward computation (project_one).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ProjectBwdArgs {
+    ProjectArgs P;
+    const float *d_rec;  // n x 9
+    float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
+};
+
+// Gradient of the SH colour with respect to the unit direction and the
+// coefficients: rgb_c = max(0, sum_k Y_k(d) c_kc + 0.5).
+template <int DEG>
+__device__ __forceinline__ float3 sh_colour_bwd(const float *__restrict__ src, float *__restrict__ dsrc,
+                                                float x, float y, float z, const float gr[3]) {
+    constexpr int kK = (DEG + 1) * (DEG + 1);
+    float Y[kK], Dx[kK], Dy[kK], Dz[kK];
+    Y[0] = kY00; Dx[0] = Dy[0] = Dz[0] = 0.f;
+    if (DEG >= 1) {
+        Y[1] = -kY1 * y; Dx[1] = 0.f;   Dy[1] = -kY1; Dz[1] = 0.f;
+        Y[2] = kY1 * z;  Dx[2] = 0.f;   Dy[2] = 0.f;  Dz[2] = kY1;
+        Y[3] = -kY1 * x; Dx[3] = -kY1;  Dy[3] = 0.f;  Dz[3] = 0.f;
+    }
+    if (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;                 Dx[4] = kY2a * y;          Dy[4] = kY2a * x;          Dz[4] = 0.f;
+        Y[5] = -kY2a * y * z;                Dx[5] = 0.f;               Dy[5] = -kY2a * z;         Dz[5] = -kY2a * y;
+        Y[6] = kY2b * (2.f * zz - xx - yy);  Dx[6] = -2.f * kY2b * x;   Dy[6] = -2.f * kY2b * y;   Dz[6] = 4.f * kY2b * z;
+        Y[7] = -kY2a * x * z;                Dx[7] = -kY2a * z;         Dy[7] = 0.f;               Dz[7] = -kY2a * x;
+        Y[8] = kY2c * (xx - yy);             Dx[8] = 2.f * kY2c * x;    Dy[8] = -2.f * kY2c * y;   Dz[8] = 0.f;
+        if (DEG >= 3) {
+            Y[9] = -kY3a * y * (3.f * xx - yy);
+            Dx[9] = -6.f * kY3a * x * y; Dy[9] = -3.f * kY3a * (xx - yy); Dz[9] = 0.f;
+            Y[10] = kY3b * x * y * z;
+            Dx[10] = kY3b * y * z; Dy[10] = kY3b * x * z; Dz[10] = kY3b * x * y;
+            Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+            Dx[11] = 2.f * kY3c * x * y; Dy[11] = -kY3c * (4.f * zz - xx - 3.f * yy); Dz[11] = -8.f * kY3c * y * z;
+            Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Dx[12] = -6.f * kY3d * x * z; Dy[12] = -6.f * kY3d * y * z; Dz[12] = kY3d * (6.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+            Dx[13] = -kY3c * (4.f * zz - 3.f * xx - yy); Dy[13] = 2.f * kY3c * x * y; Dz[13] = -8.f * kY3c * x * z;
+            Y[14] = kY3e * z * (xx - yy);
+            Dx[14] = 2.f * kY3e * x * z; Dy[14] = -2.f * kY3e * y * z; Dz[14] = kY3e * (xx - yy);
+            Y[15] = -kY3a * x * (xx - 3.f * yy);
+            Dx[15] = -3.f * kY3a * (xx - yy); Dy[15] = 6.f * kY3a * x * y; Dz[15] = 0.f;
+        }
+    }
+    // Which channels were clamped at zero in the forward pass.
+    float s[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < kK; ++k)
+        for (int c = 0; c < 3; ++c) s[c] = fmaf(Y[k], __ldg(src + 3 * k + c), s[c]);
+    float g[3];
+    for (int c = 0; c < 3; ++c) g[c] = s[c] > 0.f ? gr[c] : 0.f;
+    float3 gd = make_float3(0.f, 0.f, 0.f);
+    for (int k = 0; k < kK; ++k) {
+        float dot = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            dsrc[3 * k + c] = Y[k] * g[c];
+            dot = fmaf(__ldg(src + 3 * k + c), g[c], dot);
+        }
+        gd.x = fmaf(Dx[k], dot, gd.x);
+        gd.y = fmaf(Dy[k], dot, gd.y);
+        gd.z = fmaf(Dz[k], dot, gd.z);
+    }
+    return gd;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs B) {
+    constexpr int kK = (DEG + 1) * (DEG + 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.P.n) return;
+    const ProjectArgs &P = B.P;
+    const GsCameraDev &K = P.cam;
+    float gr9[9];
+    bool any = false;
+    for (int f = 0; f < 9; ++f) {
+        gr9[f] = B.d_rec[9 * i + f];
+        any |= gr9[f] != 0.f;
+    }
+    float *dsh = B.d_sh + (size_t)i * kK * 3;
+    if (!any) {
+        for (int a = 0; a < 3; ++a) B.d_means[3 * i + a] = 0.f;
+        for (int a = 0; a < 3; ++a) B.d_log_scales[3 * i + a] = 0.f;
+        for (int a = 0; a < 4; ++a) B.d_quats[4 * i + a] = 0.f;
+        B.d_logits[i] = 0.f;
+        for (int a = 0; a < kK * 3; ++a) dsh[a] = 0.f;
+        return;
+    }
+    // ---- forward recomputation ----
+    const float mx = P.means[3 * i], my = P.means[3 * i + 1], mz = P.means[3 * i + 2];
+    const float tx = fmaf(K.R[0], mx, fmaf(K.R[1], my, fmaf(K.R[2], mz, K.t[0])));
+    const float ty = fmaf(K.R[3], mx, fmaf(K.R[4], my, fmaf(K.R[5], mz, K.t[1])));
+    const float tz = fmaf(K.R[6], mx, fmaf(K.R[7], my, fmaf(K.R[8], mz, K.t[2])));
+    const float q0 = P.quats[4 * i], q1 = P.quats[4 * i + 1], q2 = P.quats[4 * i + 2], q3 = P.quats[4 * i + 3];
+    const float qn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    const float qw = q0 / qn, qx = q1 / qn, qy = q2 / qn, qz = q3 / qn;
+    const float sc[3] = {expf(P.log_scales[3 * i]), expf(P.log_scales[3 * i + 1]), expf(P.log_scales[3 * i + 2])};
+    float Rm[3][3];
+    Rm[0][0] = 1.f - 2.f * (qy * qy + qz * qz); Rm[0][1] = 2.f * (qx * qy - qw * qz); Rm[0][2] = 2.f * (qx * qz + qw * qy);
+    Rm[1][0] = 2.f * (qx * qy + qw * qz); Rm[1][1] = 1.f - 2.f * (qx * qx + qz * qz); Rm[1][2] = 2.f * (qy * qz - qw * qx);
+    Rm[2][0] = 2.f * (qx * qz - qw * qy); Rm[2][1] = 2.f * (qy * qz + qw * qx); Rm[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+    float M[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[r][c] = Rm[r][c] * sc[c];
+    const float iz = 1.f / tz;
+    const float rx_raw = tx * iz, ry_raw = ty * iz;
+    const bool rx_free = rx_raw > -K.lim_x && rx_raw < K.lim_x;
+    const bool ry_free = ry_raw > -K.lim_y && ry_raw < K.lim_y;
+    const float rx = fminf(K.lim_x, fmaxf(-K.lim_x, rx_raw));
+    const float ry = fminf(K.lim_y, fmaxf(-K.lim_y, ry_raw));
+    float T0[3], T1[3];
+    for (int c = 0; c < 3; ++c) {
+        T0[c] = K.fx * iz * (K.R[c] - rx * K.R[6 + c]);
+        T1[c] = K.fy * iz * (K.R[3 + c] - ry * K.R[6 + c]);
+    }
+    float A0[3], A1[3];
+    for (int c = 0; c < 3; ++c) {
+        A0[c] = T0[0] * M[0][c] + T0[1] * M[1][c] + T0[2] * M[2][c];
+        A1[c] = T1[0] * M[0][c] + T1[1] * M[1][c] + T1[2] * M[2][c];
+    }
+    const float a = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2] + kDilation;
+    const float c = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2] + kDilation;
+    const float b = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
+    const float cr0 = A0[1] * A1[2] - A0[2] * A1[1], cr1 = A0[2] * A1[0] - A0[0] * A1[2],
+                cr2 = A0[0] * A1[1] - A0[1] * A1[0];
+    const float det = cr0 * cr0 + cr1 * cr1 + cr2 * cr2 + kDilation * (a + c - 2.f * kDilation) +
+                      kDilation * kDilation;
+    const float o = 1.f / (1.f + expf(-P.logits[i]));
+
+    // ---- backward ----
+    const float gu = gr9[0], gv = gr9[1], gQ00 = gr9[2], gQ01 = gr9[3], gQ11 = gr9[4], go = gr9[5];
+    // conic = (c, -b, a) / det
+    const float id = 1.f / det, id2 = id * id;
+    const float ga = gQ00 * (-c * c * id2) + gQ01 * (b * c * id2) + gQ11 * (id - a * c * id2);
+    const float gc = gQ00 * (id - a * c * id2) + gQ01 * (a * b * id2) + gQ11 * (-a * a * id2);
+    const float gb = gQ00 * (2.f * b * c * id2) + gQ01 * (-id - 2.f * b * b * id2) + gQ11 * (2.f * a * b * id2);
+    float gA0[3], gA1[3];
+    for (int k = 0; k < 3; ++k) {
+        gA0[k] = 2.f * ga * A0[k] + gb * A1[k];
+        gA1[k] = 2.f * gc * A1[k] + gb * A0[k];
+    }
+    // A = T M
+    float gT0[3], gT1[3], gM[3][3];
+    for (int r = 0; r < 3; ++r) {
+        gT0[r] = gA0[0] * M[r][0] + gA0[1] * M[r][1] + gA0[2] * M[r][2];
+        gT1[r] = gA1[0] * M[r][0] + gA1[1] * M[r][1] + gA1[2] * M[r][2];
+        for (int k = 0; k < 3; ++k) gM[r][k] = T0[r] * gA0[k] + T1[r] * gA1[k];
+    }
+    // M = R diag(s)
+    float gR[3][3], gls[3];
+    for (int k = 0; k < 3; ++k) {
+        float gs = 0.f;
+        for (int r = 0; r < 3; ++r) {
+            gR[r][k] = gM[r][k] * sc[k];
+            gs = fmaf(gM[r][k], Rm[r][k], gs);
+        }
+        gls[k] = gs * sc[k];
+    }
+    // R(q^) then q^ = q / |q|
+    const float gqw = 2.f * (-qz * gR[0][1] + qy * gR[0][2] + qz * gR[1][0] - qx * gR[1][2] - qy * gR[2][0] + qx * gR[2][1]);
+    const float gqx = 2.f * (qy * gR[0][1] + qz * gR[0][2] + qy * gR[1][0] - 2.f * qx * gR[1][1] - qw * gR[1][2] +
+                             qz * gR[2][0] + qw * gR[2][1] - 2.f * qx * gR[2][2]);
+    const float gqy = 2.f * (-2.f * qy * gR[0][0] + qx * gR[0][1] + qw * gR[0][2] + qx * gR[1][0] + qz * gR[1][2] -
+                             qw * gR[2][0] + qz * gR[2][1] - 2.f * qy * gR[2][2]);
+    const float gqz = 2.f * (-2.f * qz * gR[0][0] - qw * gR[0][1] + qx * gR[0][2] + qw * gR[1][0] - 2.f * qz * gR[1][1] +
+                             qy * gR[1][2] + qx * gR[2][0] + qy * gR[2][1]);
+    const float qdot = qw * gqw + qx * gqx + qy * gqy + qz * gqz;
+    // T0 = fx iz (W0 - rx W2), T1 = fy iz (W1 - ry W2)
+    float g_rx = 0.f, g_ry = 0.f, g_iz = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        g_rx = fmaf(gT0[k], -K.fx * iz * K.R[6 + k], g_rx);
+        g_ry = fmaf(gT1[k], -K.fy * iz * K.R[6 + k], g_ry);
+        g_iz = fmaf(gT0[k], K.fx * (K.R[k] - rx * K.R[6 + k]), g_iz);
+        g_iz = fmaf(gT1[k], K.fy * (K.R[3 + k] - ry * K.R[6 + k]), g_iz);
+    }
+    float g_tx = gu * K.fx * iz, g_ty = gv * K.fy * iz;
+    g_iz += gu * K.fx * tx + gv * K.fy * ty;
+    if (rx_free) { g_tx += g_rx * iz; g_iz += g_rx * tx; }
+    if (ry_free) { g_ty += g_ry * iz; g_iz += g_ry * ty; }
+    const float g_tz = -g_iz * iz * iz;
+    // t = W mu + t_c
+    float gm[3];
+    for (int k = 0; k < 3; ++k) gm[k] = K.R[k] * g_tx + K.R[3 + k] * g_ty + K.R[6 + k] * g_tz;
+    // colour: direction d = (mu - C) / |mu - C|
+    float vx = mx - K.C[0], vy = my - K.C[1], vz = mz - K.C[2];
+    const float vn = sqrtf(vx * vx + vy * vy + vz * vz);
+    const float dx = vx / vn, dy = vy / vn, dz = vz / vn;
+    const float grgb[3] = {gr9[6], gr9[7], gr9[8]};
+    const float3 gd = sh_colour_bwd<DEG>(P.sh + (size_t)i * kK * 3, dsh, dx, dy, dz, grgb);
+    const float ddot = dx * gd.x + dy * gd.y + dz * gd.z;
+    gm[0] += (gd.x - dx * ddot) / vn;
+    gm[1] += (gd.y - dy * ddot) / vn;
+    gm[2] += (gd.z - dz * ddot) / vn;
+
+    for (int k = 0; k < 3; ++k) B.d_means[3 * i + k] = gm[k];
+    for (int k = 0; k < 3; ++k) B.d_log_scales[3 * i + k] = gls[k];
+    B.d_quats[4 * i + 0] = (gqw - qw * qdot) / qn;
+    B.d_quats[4 * i + 1] = (gqx - qx * qdot) / qn;
+    B.d_quats[4 * i + 2] = (gqy - qy * qdot) / qn;
+    B.d_quats[4 * i + 3] = (gqz - qz * qdot) / qn;
+    B.d_logits[i] = go * o * (1.f - o);
+}
+
+}  // namespace
+
+cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
+                                  const float *d_rec, const gs_grads &out, cudaStream_t s) {
+    if (g.n == 0) return cudaSuccess;
+    ProjectBwdArgs B;
+    B.P = ProjectArgs{g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.n, cam, grid, nullptr, nullptr,
+                      false, false};
+    B.d_rec = d_rec;
+    B.d_means = out.d_means;
+    B.d_log_scales = out.d_log_scales;
+    B.d_quats = out.d_quats;
+    B.d_logits = out.d_opacity_logits;
+    B.d_sh = out.d_sh;
+    const unsigned blocks = (unsigned)((g.n + 255) / 256);
+    switch (g.sh_degree) {
+        case 0: project_bwd_kernel<0><<<blocks, 256, 0, s>>>(B); break;
+        case 1: project_bwd_kernel<1><<<blocks, 256, 0, s>>>(B); break;
+        case 2: project_bwd_kernel<2><<<blocks, 256, 0, s>>>(B); break;
+        default: project_bwd_kernel<3><<<blocks, 256, 0, s>>>(B); break;
+    }
+    return cudaGetLastError();
+}
