@@ -133,6 +133,54 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def fwd_bwd(gs, torch, args, flush, local) -> dict:
+    """Forward + backward through the autograd wrapper on the 500k-Gaussian
+    clustered scene at 1080p with an L1 loss against a seeded random target:
+    per-iteration device time (CUDA events; L2 flushed between iterations)."""
+    from paper_2607_15951_gb300 import scenes
+    scene, cams = scenes.workload("clustered_500k_1080p")
+    cam = cams[0]
+    g = gs.scene_to_device(scene)
+    params = [g[k].clone().requires_grad_(True) for k in ("means", "log_scales", "quats",
+                                                          "opacity_logits", "sh")]
+    target = torch.from_numpy(scenes.l1_target(cam.height, cam.width, 1002)).cuda()
+    ctx = gs.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def it():
+        for p in params:
+            p.grad = None
+        rgb, _ = gs.RasterizeGaussians(*params, ctx, cam, scene.sh_degree)
+        loss = (rgb - target).abs().mean()
+        loss.backward()
+
+    for _ in range(args.warmup):
+        it()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 10)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    fwd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        for p in params:
+            p.grad = None
+        ev[i][0].record(stream)
+        fwd[i][0].record(stream)
+        rgb, _ = gs.RasterizeGaussians(*params, ctx, cam, scene.sh_degree)
+        fwd[i][1].record(stream)
+        loss = (rgb - target).abs().mean()
+        loss.backward()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    fms = float(np.mean([a.elapsed_time(b) for a, b in fwd]))
+    ctx.close()
+    return {"workload": "clustered_500k_1080p", "description": "500k Gaussians as the 1M scene, SH3, "
+            "1920x1080, L1 loss vs a seeded U[0,1] target, torch.autograd through RasterizeGaussians",
+            "ms_per_iter": round(ms, 4), "forward_ms": round(fms, 4), "backward_ms": round(ms - fms, 4),
+            "iters": steps, "grads": "means, log_scales, quats, opacity_logits, sh (degree 3)"}
+
+
 def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:
     """Time the FP64 oracle on the host cores rendering whole frames of the
     same workload until about ``budget_s`` seconds have passed."""
@@ -192,6 +240,7 @@ def main():
     ap.add_argument("--workload", default="clustered_1m_1080p", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fwd-bwd", action="store_true")
     ap.add_argument("--blend-variant", type=int, default=0, help="0 culled (default), 1 basic")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -323,11 +372,13 @@ def main():
         "peaks": {"source": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
         "clocks": clk,
     }
-    # Kernel launches per gs_render: project, scan, emit, histogram, one per
-    # digit pass, ranges, blend.
+    # Kernel launches per gs_render: projection + slot reservation, key
+    # emission, one per digit pass, ranges, blend.
     passes = (stats["key_bits"] + 7) // 8
-    per_step = 6 + passes
+    per_step = 4 + passes
     line["gpu_launches"] = per_step * args.steps
+    if not args.no_fwd_bwd:
+        line["fwd_bwd"] = fwd_bwd(gs, torch, args, flush, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cam)
     if rank == 0:
