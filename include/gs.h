@@ -114,11 +114,21 @@ typedef struct {
  *   GS_BLEND_BASIC   one thread per pixel evaluates every record of its tile */
 enum { GS_BLEND_CULLED = 0, GS_BLEND_BASIC = 1 };
 
+/* Precision of the projected records the blend reads (gs_render,
+ * gs_render_backward, gs_render_batch). With F16 / BF16 the opacity and the
+ * colour are stored in 16 bits (28-byte records instead of 36 read bytes);
+ * the 2D mean and the conic stay FP32, because a 16-bit conic's relative
+ * error, multiplied by |power| up to ln 255 at the 1/255 edge, exceeds the
+ * image error bound on dense scenes. Values are decoded to FP32 when staged;
+ * compositing and transmittance stay FP32. Binning always uses the FP32
+ * projection, so the per-tile lists do not change. */
+enum { GS_RECORD_F32 = 0, GS_RECORD_F16 = 1, GS_RECORD_BF16 = 2 };
+
 /* Options. gs_default_options() fills the standard values. */
 typedef struct {
     int32_t tile_w, tile_h; /* screen tile: 16x16 (default), 16x8 or 8x8      */
     float bg[3];            /* background colour added as T_final * bg         */
-    int32_t record_dtype;   /* 0 = FP32 records (only value in this version)   */
+    int32_t record_dtype;   /* GS_RECORD_F32 (default), _F16 or _BF16          */
     int32_t blend_variant;  /* GS_BLEND_CULLED (default) or GS_BLEND_BASIC     */
     int32_t reserved[6];    /* must be zero                                    */
 } gs_options;

@@ -201,20 +201,21 @@ def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_co
 
 def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
               n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
-              stream=None) -> None:
+              record_dtype: int = 0, stream=None) -> None:
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg, blend_variant=variant)
+    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant)
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
                                ctypes.byref(fb), _stream(stream)))
 
 
 def gs_render_backward(ctx: Context, g: dict, sh_degree: int, cam, final_T, n_contrib, d_rgb,
-                       grads: dict, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), stream=None) -> None:
+                       grads: dict, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
+                       stream=None) -> None:
     """grads: dict of CUDA tensors shaped like g (keys means, log_scales, quats,
     opacity_logits, sh) and optionally 'records' (n, 9)."""
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg)
+    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype)
     fb = _fb(None, final_T, n_contrib, None)
     out = N.gs_grads()
     out.d_means, out.d_log_scales, out.d_quats = (_ptr(grads["means"]), _ptr(grads["log_scales"]),
@@ -259,7 +260,7 @@ def scene_to_device(scene, device="cuda") -> dict:
 
 
 def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
-           aux: bool = True, variant: int = 0, stream=None) -> dict:
+           aux: bool = True, variant: int = 0, record_dtype: int = 0, stream=None) -> dict:
     """Allocate outputs with torch and call gs_render."""
     import torch
     H, W = int(cam.height), int(cam.width)
@@ -270,7 +271,8 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
         out["n_contrib"] = torch.empty((H, W), dtype=torch.int32, device=dev)
         out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
-              out.get("n_eval"), tile=tile, bg=bg, variant=variant, stream=stream)
+              out.get("n_eval"), tile=tile, bg=bg, variant=variant, record_dtype=record_dtype,
+              stream=stream)
     return out
 
 

@@ -19,6 +19,9 @@ GS_ERR_OOM = 3
 GS_ERR_CAPACITY = 4
 GS_ERR_TIMEOUT = 5
 GS_ERR_UNSUPPORTED = 6
+GS_RECORD_F32 = 0
+GS_RECORD_F16 = 1
+GS_RECORD_BF16 = 2
 GS_BLEND_CULLED = 0
 GS_BLEND_BASIC = 1
 NOALLOC_SORT_MAX_PAIRS = 262144  # GS_NOALLOC_SORT_MAX_PAIRS in include/gs.h

@@ -34,6 +34,8 @@ struct gs_context {
     int last_w = 0, last_h = 0, last_tw = 0, last_th = 0;
     const uint32_t *last_values = nullptr;
     DevBuf d_rec;
+    DevBuf lp_geo, lp_oq, lp_gb;  // reduced-precision blend records
+    int last_dtype = GS_RECORD_F32;
     int64_t key_capacity = 0;  // pairs the render path's key buffers hold
     bool pinned_capacity = false;  // set by gs_reserve_keys: do not shrink
     DevBuf fused_scratch;
@@ -100,8 +102,8 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
     const bool ok_tile = (o->tile_w == 16 && o->tile_h == 16) || (o->tile_w == 16 && o->tile_h == 8) ||
                          (o->tile_w == 8 && o->tile_h == 8);
     if (!ok_tile) return fail(ctx, GS_ERR_INVALID_ARG, "tile must be 16x16, 16x8 or 8x8");
-    if (o->record_dtype != 0)
-        return fail(ctx, GS_ERR_UNSUPPORTED, "record_dtype must be 0 (FP32) in this version");
+    if (o->record_dtype != GS_RECORD_F32 && o->record_dtype != GS_RECORD_F16 && o->record_dtype != GS_RECORD_BF16)
+        return fail(ctx, GS_ERR_INVALID_ARG, "record_dtype must be GS_RECORD_F32, _F16 or _BF16");
     if (o->blend_variant != GS_BLEND_CULLED && o->blend_variant != GS_BLEND_BASIC)
         return fail(ctx, GS_ERR_INVALID_ARG, "blend_variant must be GS_BLEND_CULLED or GS_BLEND_BASIC");
     for (int i = 0; i < 6; ++i)
@@ -175,6 +177,16 @@ enum { EV_START, EV_PROJECT, EV_SCAN, EV_EMIT0, EV_EMIT, EV_SORT, EV_RANGES, EV_
 
 void mark(gs_context *ctx, int which, cudaStream_t s) {
     if (ctx->timing) cudaEventRecord(ctx->ev[which], s);
+}
+
+RecordReader reader(gs_context *ctx, const gs_record *rec, int dtype) {
+    RecordReader r;
+    r.rec32 = reinterpret_cast<const float4 *>(rec);
+    r.geo = static_cast<const float4 *>(ctx->lp_geo.ptr);
+    r.oq = static_cast<const uint2 *>(ctx->lp_oq.ptr);
+    r.gb = static_cast<const uint32_t *>(ctx->lp_gb.ptr);
+    r.dtype = dtype;
+    return r;
 }
 
 struct DeviceGuard {
@@ -288,7 +300,7 @@ void gs_destroy(gs_context *ctx) {
     DeviceGuard g(ctx->device);
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                       &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
-                      &ctx->fused_scratch, &ctx->d_rec};
+                      &ctx->fused_scratch, &ctx->d_rec, &ctx->lp_geo, &ctx->lp_oq, &ctx->lp_gb};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -314,7 +326,7 @@ size_t gs_workspace_bytes(const gs_context *ctx) {
     if (!ctx) return 0;
     const DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                             &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch,
-                            &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec};
+                            &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec, &ctx->lp_geo, &ctx->lp_oq, &ctx->lp_gb};
     size_t t = 0;
     for (const DevBuf *b : bufs) t += b->bytes;
     return t;
@@ -401,8 +413,11 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
     if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
         return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
     DeviceGuard dg(ctx->device);
-    GS_CUDA(ctx, gs_launch_blend(records, values, ranges, make_grid(cam, opts), cam->width, cam->height,
-                                 opts->bg, *fb, opts->blend_variant, static_cast<cudaStream_t>(stream)));
+    if (opts->record_dtype != GS_RECORD_F32)
+        return fail(ctx, GS_ERR_UNSUPPORTED, "gs_blend reads FP32 gs_records; use gs_render for F16/BF16");
+    GS_CUDA(ctx, gs_launch_blend(reader(ctx, records, GS_RECORD_F32), values, ranges, make_grid(cam, opts),
+                                 cam->width, cam->height, opts->bg, *fb, opts->blend_variant,
+                                 static_cast<cudaStream_t>(stream)));
     return GS_OK;
 }
 
@@ -421,6 +436,12 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     const int64_t n = g->n;
     const int n_tiles = grid.tiles_x * grid.tiles_y;
     const int bits = key_bits_for(n_tiles);
+    const int dtype = opts->record_dtype;
+    if (dtype != GS_RECORD_F32 &&
+        ((st = ensure(ctx, ctx->lp_geo, (size_t)(n > 0 ? n : 1) * 16, "reduced-precision records")) != GS_OK ||
+         (st = ensure(ctx, ctx->lp_oq, (size_t)(n > 0 ? n : 1) * 8, "reduced-precision records")) != GS_OK ||
+         (st = ensure(ctx, ctx->lp_gb, (size_t)(n > 0 ? n : 1) * 4, "reduced-precision records")) != GS_OK))
+        return st;
     if ((st = ensure(ctx, ctx->records, (size_t)(n > 0 ? n : 1) * sizeof(gs_record), "records")) != GS_OK ||
         (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK ||
         (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n), "scan scratch")) != GS_OK)
@@ -448,7 +469,10 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes(cap, bits), s));
         const GsSortScratch sc = gs_sort_carve(ctx->sort_scratch.ptr, cap, bits);
         mark(ctx, EV_START, s);
-        GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, keys, vals, cap, ctx->d_counts,
+        GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, static_cast<float4 *>(ctx->lp_geo.ptr),
+                                           static_cast<uint2 *>(ctx->lp_oq.ptr),
+                                           static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype, keys, vals, cap,
+                                           ctx->d_counts,
                                            ctx->fused_scratch.ptr, sc, ctx->d_err, s));
         mark(ctx, EV_PROJECT, s);
         mark(ctx, EV_SCAN, s);
@@ -462,8 +486,8 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         uint32_t *sv = in_alt ? avals : vals;
         GS_CUDA(ctx, gs_launch_ranges_dev(sk, sv, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s));
         mark(ctx, EV_RANGES, s);
-        GS_CUDA(ctx, gs_launch_blend(rec, sv, ranges, grid, cam->width, cam->height, opts->bg, *fb,
-                                     opts->blend_variant, s));
+        GS_CUDA(ctx, gs_launch_blend(reader(ctx, rec, dtype), sv, ranges, grid, cam->width, cam->height,
+                                     opts->bg, *fb, opts->blend_variant, s));
         mark(ctx, EV_BLEND, s);
         GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 4 * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, s));
@@ -491,6 +515,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         ctx->last_tw = grid.tile_w;
         ctx->last_th = grid.tile_h;
         ctx->last_values = sv;
+        ctx->last_dtype = dtype;
         // Keep about 25 % headroom over this frame's count for the next one
         // (the buffers themselves only grow).
         if (!ctx->pinned_capacity && (int64_t)K * 2 < cap)
@@ -514,7 +539,7 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
     if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
         return fail(ctx, GS_ERR_INVALID_ARG, "a gradient array is NULL");
     if (!ctx->have_last || ctx->last_n != g->n || ctx->last_w != cam->width || ctx->last_h != cam->height ||
-        ctx->last_tw != opts->tile_w || ctx->last_th != opts->tile_h)
+        ctx->last_tw != opts->tile_w || ctx->last_th != opts->tile_h || ctx->last_dtype != opts->record_dtype)
         return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward must follow gs_render of the same scene and camera");
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -524,7 +549,8 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
         return st;
     float *d_rec = static_cast<float *>(ctx->d_rec.ptr);
     GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)n * 9 * sizeof(float), s));
-    GS_CUDA(ctx, gs_launch_blend_bwd(static_cast<gs_record *>(ctx->records.ptr), ctx->last_values,
+    GS_CUDA(ctx, gs_launch_blend_bwd(reader(ctx, static_cast<gs_record *>(ctx->records.ptr), ctx->last_dtype),
+                                     ctx->last_values,
                                      static_cast<uint32_t *>(ctx->ranges.ptr), grid, cam->width, cam->height,
                                      opts->bg, d_rgb, fb->final_T, fb->n_contrib, d_rec, s));
     GS_CUDA(ctx, gs_launch_project_bwd(*g, make_cam(cam), grid, d_rec, *out, s));

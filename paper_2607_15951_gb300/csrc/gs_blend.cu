@@ -25,7 +25,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kBatch = 256;
 
 struct BlendArgs {
-    const float4 *records;
+    RecordReader rd;
     const uint32_t *values;
     const uint32_t *ranges;
     GsGrid grid;
@@ -52,11 +52,11 @@ struct SRec {
 };
 
 // Builds the shared form of record g at slot s.
-__device__ __forceinline__ void stage_record(const float4 *__restrict__ rec, uint32_t g, int s,
+__device__ __forceinline__ void stage_record(const RecordReader &rd, uint32_t g, int s,
                                              const SRec &S, bool want_box) {
-    const float4 r0 = __ldg(rec + 3 * (size_t)g);
-    const float4 r1 = __ldg(rec + 3 * (size_t)g + 1);
-    const float blue = __ldg(reinterpret_cast<const float *>(rec + 3 * (size_t)g + 2));
+    float4 r0, r1;
+    float blue;
+    rd.load(g, r0, r1, blue);
     const float q00 = r0.z, q01 = r0.w, q11 = r1.x, o = r1.y;
     const float A = -0.5f * kLog2e * q00, B = -kLog2e * q01, C = -0.5f * kLog2e * q11;
     const float thr = -log2f(255.f * o);
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_culled_kernel(
         if (__syncthreads_count(warp_done) == kThreads) break;
         for (int s = tid; s < kBatch; s += kThreads) {
             const uint32_t k = start + s;
-            if (k < last) stage_record(a.records, a.values[k], s, S, true);
+            if (k < last) stage_record(a.rd, a.values[k], s, S, true);
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)kBatch, last - start);
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) 
         if (__syncthreads_count(p.done) == kN) break;
         for (int s = tid; s < kBatch; s += kN) {
             const uint32_t k = start + s;
-            if (k < last) stage_record(a.records, a.values[k], s, S, false);
+            if (k < last) stage_record(a.rd, a.values[k], s, S, false);
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)kBatch, last - start);
@@ -244,10 +244,10 @@ __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) 
 
 }  // namespace
 
-cudaError_t gs_launch_blend(const gs_record *records, const uint32_t *values, const uint32_t *ranges,
+cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s) {
-    BlendArgs a{reinterpret_cast<const float4 *>(records), values, ranges, grid, width, height,
+    BlendArgs a{rd, values, ranges, grid, width, height,
                 {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
     const unsigned blocks = (unsigned)(grid.tiles_x * grid.tiles_y);
     const int tw = grid.tile_w, th = grid.tile_h;
@@ -280,7 +280,7 @@ cudaError_t gs_launch_blend(const gs_record *records, const uint32_t *values, co
 namespace {
 
 struct BlendBwdArgs {
-    const float4 *records;
+    RecordReader rd;
     const uint32_t *values;
     const uint32_t *ranges;
     GsGrid grid;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_bwd_kernel(con
         for (int s = tid; s < cnt; s += kThreads) {
             const uint32_t g = a.values[first + beg + s];
             s_g[s] = g;
-            stage_record(a.records, g, s, S, true);
+            stage_record(a.rd, g, s, S, true);
         }
         __syncthreads();
         if (wmax > beg) {
@@ -471,11 +471,11 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_bwd_kernel(con
 
 }  // namespace
 
-cudaError_t gs_launch_blend_bwd(const gs_record *records, const uint32_t *values, const uint32_t *ranges,
+cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                 const GsGrid &grid, int width, int height, const float bg[3],
                                 const float *d_rgb, const float *final_T, const int32_t *n_contrib,
                                 float *d_rec, cudaStream_t s) {
-    BlendBwdArgs a{reinterpret_cast<const float4 *>(records), values, ranges, grid, width, height,
+    BlendBwdArgs a{rd, values, ranges, grid, width, height,
                    {bg[0], bg[1], bg[2]}, d_rgb, final_T, n_contrib, d_rec};
     const unsigned blocks = (unsigned)(grid.tiles_x * grid.tiles_y);
     const int tw = grid.tile_w, th = grid.tile_h;

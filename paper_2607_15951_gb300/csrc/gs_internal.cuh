@@ -1,6 +1,8 @@
 // gs_internal.cuh — device-side definitions shared by the library's kernels.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -140,6 +142,49 @@ __device__ __forceinline__ Rect tile_rect(float u, float v, int r, int tw, int t
     return R;
 }
 
+// Compact reduced-precision blend record (structure of arrays, 28 bytes):
+//   geo  float4  (u, v, Q00, Q01)          FP32
+//   oq   uint2   (Q11 as FP32 bits, 16-bit pair (opacity, red))
+//   gb   uint32  16-bit pair (green, blue)
+// The 2D mean and the conic stay FP32: the exponent's error is the conic's
+// relative error times |power| (up to ln 255 at the 1/255 edge), which with
+// 16-bit conics exceeds the image bound on dense scenes.
+__device__ __forceinline__ uint32_t pack2(float a, float b, int dtype) {
+    if (dtype == GS_RECORD_BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ float2 unpack2(uint32_t w, int dtype) {
+    if (dtype == GS_RECORD_BF16) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+
+// What the blend kernels read of a record, in either precision.
+struct RecordReader {
+    const float4 *rec32;  // gs_record array (FP32)
+    const float4 *geo;    // reduced precision: (u, v, Q00, Q01)
+    const uint2 *oq;      // (Q11 bits, opacity | red)
+    const uint32_t *gb;   // green | blue
+    int dtype;            // GS_RECORD_*
+    __device__ __forceinline__ void load(uint32_t g, float4 &r0, float4 &r1, float &blue) const {
+        if (dtype == GS_RECORD_F32) {
+            r0 = __ldg(rec32 + 3 * (size_t)g);
+            r1 = __ldg(rec32 + 3 * (size_t)g + 1);
+            blue = __ldg(reinterpret_cast<const float *>(rec32 + 3 * (size_t)g + 2));
+            return;
+        }
+        r0 = __ldg(geo + g);
+        const uint2 w = __ldg(oq + g);
+        const float2 orr = unpack2(w.y, dtype), gbb = unpack2(__ldg(gb + g), dtype);
+        r1 = make_float4(__uint_as_float(w.x), orr.x, orr.y, gbb.x);
+        blue = gbb.y;
+    }
+};
+
 // Records as three float4s (the gs_record layout):
 //   r0 = (u, v, Q00, Q01), r1 = (Q11, opacity, red, green),
 //   r2 = (blue, depth, radius bits, tiles bits).
@@ -149,6 +194,8 @@ struct Rec {
 static_assert(sizeof(gs_record) == 48, "gs_record must be 48 bytes");
 
 }  // namespace gs
+
+using gs::RecordReader;
 
 // ---------------------------------------------------------------------------
 // Host-side launch helpers (implemented in the kernel files).
@@ -229,7 +276,7 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s);
 
-cudaError_t gs_launch_blend(const gs_record *records, const uint32_t *values, const uint32_t *ranges,
+cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s);
 
@@ -242,12 +289,14 @@ cudaError_t gs_launch_blend(const gs_record *records, const uint32_t *values, co
 size_t gs_fused_scratch_bytes(int64_t n);    // + gs_key_block_bytes(capacity)
 size_t gs_key_block_bytes(int64_t capacity);
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
-                                  gs_record *records, uint64_t *keys, uint32_t *values,
+                                  gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
+                                  int lp_dtype,
+                                  uint64_t *keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s);
 
 // Backward kernels.
-cudaError_t gs_launch_blend_bwd(const gs_record *records, const uint32_t *values, const uint32_t *ranges,
+cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                 const GsGrid &grid, int width, int height, const float bg[3],
                                 const float *d_rgb, const float *final_T, const int32_t *n_contrib,
                                 float *d_rec, cudaStream_t s);

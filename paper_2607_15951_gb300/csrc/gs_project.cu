@@ -232,6 +232,10 @@ constexpr int kKeysPerThread = kKeyBlock / 256;
 
 struct ReserveArgs {
     ProjectArgs P;
+    float4 *lp_geo;              // optional reduced-precision blend records
+    uint2 *lp_oq;
+    uint32_t *lp_gb;
+    int lp_dtype;
     unsigned long long *packed;  // visible << 33 | keys
     uint32_t *list_idx;          // n: Gaussian index of visible entry j
     uint32_t *list_off;          // n: its first key slot (ascending in j)
@@ -256,6 +260,11 @@ __global__ void __launch_bounds__(256) project_reserve_kernel(const ReserveArgs 
         out[0] = pr.r0;
         out[1] = pr.r1;
         out[2] = pr.r2;
+        if (A.lp_geo) {
+            A.lp_geo[i] = pr.r0;
+            A.lp_oq[i] = make_uint2(__float_as_uint(pr.r1.x), pack2(pr.r1.y, pr.r1.z, A.lp_dtype));
+            A.lp_gb[i] = pack2(pr.r1.w, pr.r2.x, A.lp_dtype);
+        }
     }
     const uint32_t t = pr.tiles, v = t != 0u;
     uint32_t it = t, iv = v;
@@ -427,7 +436,9 @@ size_t gs_key_block_bytes(int64_t capacity) {
 }
 
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
-                                  gs_record *records, uint64_t *keys, uint32_t *values,
+                                  gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
+                                  int lp_dtype,
+                                  uint64_t *keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s) {
     // counts and the packed counter start at zero; the sort scratch was
@@ -447,6 +458,10 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     A.list_idx = reinterpret_cast<uint32_t *>(base + 256);
     A.list_off = reinterpret_cast<uint32_t *>(base + 256 + list_bytes);
     A.hist = sc.hist;
+    A.lp_geo = lp_dtype == GS_RECORD_F32 ? nullptr : lp_geo;
+    A.lp_oq = lp_oq;
+    A.lp_gb = lp_gb;
+    A.lp_dtype = lp_dtype;
     A.block_entry = reinterpret_cast<uint32_t *>(base + 256 + 2 * list_bytes);
     A.n_key_blocks = (capacity + kKeyBlock - 1) / kKeyBlock;
     const unsigned blocks = (unsigned)((g.n + 255) / 256);
