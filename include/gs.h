@@ -130,7 +130,9 @@ typedef struct {
     float bg[3];            /* background colour added as T_final * bg         */
     int32_t record_dtype;   /* GS_RECORD_F32 (default), _F16 or _BF16          */
     int32_t blend_variant;  /* GS_BLEND_CULLED (default) or GS_BLEND_BASIC     */
-    int32_t reserved[6];    /* must be zero                                    */
+    int32_t direct_launch;  /* gs_render_batch: 0 = replay a captured CUDA graph
+                               (default), 1 = launch the kernels directly      */
+    int32_t reserved[5];    /* must be zero                                    */
 } gs_options;
 
 void gs_default_options(gs_options *opts /* host */);
@@ -260,6 +262,31 @@ typedef struct {
 gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
                              const gs_options *opts, const gs_framebuffer *fb, const float *d_rgb,
                              const gs_grads *out, void *stream);
+
+/* Renders n_views cameras (of any sizes) of one scene in one call — the
+ * batched form of gs_render with identical per-view results (same rules,
+ * same per-tile order). One launch projects every (view, Gaussian) pair into
+ * compact records; one sort orders all views' keys, whose tile ids are
+ * numbered across the views; one persistent blend kernel takes the tiles of
+ * all views from a queue ordered longest list first, which evens out the
+ * imbalance between dense and empty screen regions (the paper's Sec. 6
+ * load-imbalance finding). The whole sequence is captured once into a CUDA
+ * graph and replayed while the scene arrays, the number and sizes of the
+ * views, the options and the buffer sizes stay the same (cameras and
+ * framebuffer pointers may change: they travel in a table copied at the
+ * start of each replay). SYNCHRONISES once at the end; if the frame needed
+ * larger buffers they grow and the batch is rendered again.
+ *   cams, fbs: host arrays of n_views entries (1 .. 4096); fbs[v] as for
+ *   gs_render (rgb required). tile size, bg and record_dtype from opts. */
+gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
+                          const gs_options *opts, const gs_framebuffer *fbs, void *stream);
+
+/* Autotuner of gs_render_batch: renders the batch with each screen-tile
+ * shape (16x16, 16x8, 8x8), times three runs of each with CUDA events, and
+ * writes the fastest shape into opts->tile_w / tile_h. ms_out (host, 3
+ * floats, optional) receives the mean time of each shape in that order. */
+gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
+                            gs_options *opts, const gs_framebuffer *fbs, void *stream, float *ms_out);
 
 /* Sets the number of (tile, Gaussian) pairs gs_render's key buffers hold and
  * stops the context from shrinking it between frames (the buffers grow if a

@@ -321,3 +321,75 @@ def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Contex
         _RASTERIZE = _autograd_function()
     return _RASTERIZE.apply(means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree,
                             tuple(tile), tuple(bg))
+
+
+# ---------------------------------------------------------------------------
+# Batched views (marshalling only)
+# ---------------------------------------------------------------------------
+
+def _cams_fbs(cams, outs):
+    n = len(cams)
+    carr = (N.gs_camera * n)(*[camera_struct(c) for c in cams])
+    farr = (N.gs_framebuffer * n)(*[_fb(o["rgb"], o.get("final_T"), o.get("n_contrib"), o.get("n_eval"))
+                                     for o in outs])
+    return carr, farr
+
+
+def alloc_outputs(cams, aux: bool = False, device="cuda") -> list:
+    import torch
+    outs = []
+    for c in cams:
+        H, W = int(c.height), int(c.width)
+        o = {"rgb": torch.empty((H, W, 3), dtype=torch.float32, device=device)}
+        if aux:
+            o["final_T"] = torch.empty((H, W), dtype=torch.float32, device=device)
+            o["n_contrib"] = torch.empty((H, W), dtype=torch.int32, device=device)
+            o["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=device)
+        outs.append(o)
+    return outs
+
+
+def gs_render_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, tile=(16, 16),
+                    bg=(0.0, 0.0, 0.0), record_dtype: int = 0, direct: bool = False, stream=None):
+    gs = gaussians_struct(g, sh_degree)
+    o = options_struct(tile, bg, record_dtype)
+    o.direct_launch = 1 if direct else 0
+    carr, farr = _cams_fbs(cams, outs)
+    ctx.check(_lib().gs_render_batch(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
+                                     _stream(stream)))
+
+
+def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(0.0, 0.0, 0.0),
+                      record_dtype: int = 0, cache_path: str | None = None, stream=None):
+    """Runs the C autotuner (tile shapes 16x16, 16x8, 8x8) and returns
+    ((tile_w, tile_h), [ms per shape]). With cache_path, results are kept in a
+    JSON file keyed by GPU, scene size, view sizes and record precision."""
+    import json
+    import os
+    import torch
+    key = None
+    if cache_path:
+        sizes = ",".join(f"{c.width}x{c.height}" for c in cams)
+        n = int(g["means"].shape[0])
+        key = f"{torch.cuda.get_device_name()}|n{n}|d{sh_degree}|{sizes}|r{record_dtype}"
+        if os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+            if key in cache:
+                return tuple(cache[key]["tile"]), cache[key]["ms"]
+    gs = gaussians_struct(g, sh_degree)
+    o = options_struct((16, 16), bg, record_dtype)
+    carr, farr = _cams_fbs(cams, outs)
+    ms = (ctypes.c_float * 3)()
+    ctx.check(_lib().gs_autotune_batch(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
+                                       _stream(stream), ms))
+    tile, times = (int(o.tile_w), int(o.tile_h)), [float(x) for x in ms]
+    if cache_path:
+        cache = {}
+        if os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+        cache[key] = {"tile": list(tile), "ms": times}
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return tile, times

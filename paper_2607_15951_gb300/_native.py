@@ -63,7 +63,8 @@ class gs_grads(ctypes.Structure):
 class gs_options(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("bg", ctypes.c_float * 3), ("record_dtype", ctypes.c_int32),
-                ("blend_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("blend_variant", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class gs_render_stats(ctypes.Structure):
@@ -100,6 +101,13 @@ SIGNATURES = {
                                  ctypes.POINTER(gs_options), ctypes.POINTER(gs_framebuffer), vp]),
     "gs_last_render_stats": (ctypes.c_int, [vp, ctypes.POINTER(gs_render_stats)]),
     "gs_reserve_keys": (ctypes.c_int, [vp, ctypes.c_int64]),
+    "gs_render_batch": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
+                                       ctypes.c_int32, ctypes.POINTER(gs_options),
+                                       ctypes.POINTER(gs_framebuffer), vp]),
+    "gs_autotune_batch": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
+                                         ctypes.c_int32, ctypes.POINTER(gs_options),
+                                         ctypes.POINTER(gs_framebuffer), vp,
+                                         ctypes.POINTER(ctypes.c_float)]),
     "gs_render_backward": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
                                           ctypes.POINTER(gs_options), ctypes.POINTER(gs_framebuffer),
                                           vp, ctypes.POINTER(gs_grads), vp]),

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "gs_internal.cuh"
 
@@ -35,6 +36,16 @@ struct gs_context {
     const uint32_t *last_values = nullptr;
     DevBuf d_rec;
     DevBuf lp_geo, lp_oq, lp_gb;  // reduced-precision blend records
+    // Batched path (own buffers: a captured graph holds their addresses).
+    struct Batch {
+        DevBuf views, rec, meta, geo, oq, gb, scratch, ranges, order, queue, keys, vals, akeys, avals, sort;
+        ViewDesc *h_views = nullptr;
+        int h_views_cap = 0;
+        int64_t rec_cap = 0, key_cap = 0;
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t capture = nullptr;  // the graph is captured here, launched on the caller's stream
+        std::vector<int64_t> sig;  // what the captured graph was built for
+    } batch;
     int last_dtype = GS_RECORD_F32;
     int64_t key_capacity = 0;  // pairs the render path's key buffers hold
     bool pinned_capacity = false;  // set by gs_reserve_keys: do not shrink
@@ -106,7 +117,9 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
         return fail(ctx, GS_ERR_INVALID_ARG, "record_dtype must be GS_RECORD_F32, _F16 or _BF16");
     if (o->blend_variant != GS_BLEND_CULLED && o->blend_variant != GS_BLEND_BASIC)
         return fail(ctx, GS_ERR_INVALID_ARG, "blend_variant must be GS_BLEND_CULLED or GS_BLEND_BASIC");
-    for (int i = 0; i < 6; ++i)
+    if (o->direct_launch != 0 && o->direct_launch != 1)
+        return fail(ctx, GS_ERR_INVALID_ARG, "direct_launch must be 0 or 1");
+    for (int i = 0; i < 5; ++i)
         if (o->reserved[i] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
@@ -309,6 +322,14 @@ void gs_destroy(gs_context *ctx) {
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     for (int i = 0; i < EV_COUNT; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    auto &B = ctx->batch;
+    DevBuf *bb[] = {&B.views, &B.rec, &B.meta, &B.geo, &B.oq, &B.gb, &B.scratch, &B.ranges, &B.order,
+                    &B.queue, &B.keys, &B.vals, &B.akeys, &B.avals, &B.sort};
+    for (DevBuf *b : bb)
+        if (b->ptr) cudaFree(b->ptr);
+    if (B.exec) cudaGraphExecDestroy(B.exec);
+    if (B.capture) cudaStreamDestroy(B.capture);
+    if (B.h_views) cudaFreeHost(B.h_views);
     delete ctx;
 }
 
@@ -557,6 +578,217 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
     if (out->d_records && n > 0)
         GS_CUDA(ctx, cudaMemcpyAsync(out->d_records, d_rec, (size_t)n * 9 * sizeof(float),
                                      cudaMemcpyDeviceToDevice, s));
+    return GS_OK;
+}
+
+namespace {
+
+// Enqueues one whole batched frame on s (also used under stream capture).
+gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, const gs_options *opts,
+                        int32_t total_tiles, int bits, cudaStream_t s) {
+    auto &B = ctx->batch;
+    const int dtype = opts->record_dtype;
+    const ViewDesc *views = static_cast<const ViewDesc *>(B.views.ptr);
+    GS_CUDA(ctx, cudaMemcpyAsync(B.views.ptr, B.h_views, (size_t)n_views * sizeof(ViewDesc),
+                                 cudaMemcpyHostToDevice, s));
+    GS_CUDA(ctx, cudaMemsetAsync(B.sort.ptr, 0, gs_sort_scratch_bytes(B.key_cap, bits), s));
+    const GsSortScratch sc = gs_sort_carve(B.sort.ptr, B.key_cap, bits);
+    uint64_t *keys = static_cast<uint64_t *>(B.keys.ptr), *akeys = static_cast<uint64_t *>(B.akeys.ptr);
+    uint32_t *vals = static_cast<uint32_t *>(B.vals.ptr), *avals = static_cast<uint32_t *>(B.avals.ptr);
+    uint2 *meta = static_cast<uint2 *>(B.meta.ptr);
+    GS_CUDA(ctx, gs_launch_project_bin_batch(*g, views, n_views, static_cast<gs_record *>(B.rec.ptr),
+                                             static_cast<float4 *>(B.geo.ptr), static_cast<uint2 *>(B.oq.ptr),
+                                             static_cast<uint32_t *>(B.gb.ptr), dtype, meta, B.rec_cap, keys,
+                                             vals, B.key_cap, ctx->d_counts, B.scratch.ptr, sc, ctx->d_err, s));
+    bool in_alt = false;
+    GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, B.key_cap, ctx->d_counts + 2, sc, ctx->d_err,
+                                       &in_alt, s));
+    uint64_t *sk = in_alt ? akeys : keys;
+    uint32_t *sv = in_alt ? avals : vals;
+    uint32_t *ranges = static_cast<uint32_t *>(B.ranges.ptr);
+    GS_CUDA(ctx, gs_launch_ranges_batch(sk, sv, meta, B.key_cap, ctx->d_counts + 2, total_tiles, ranges,
+                                        ctx->d_err, s));
+    uint32_t *qs = static_cast<uint32_t *>(B.queue.ptr);
+    uint32_t *order = static_cast<uint32_t *>(B.order.ptr);
+    GS_CUDA(ctx, gs_launch_queue(ranges, total_tiles, qs, order, s));
+    RecordReader rd;
+    rd.rec32 = static_cast<const float4 *>(B.rec.ptr);
+    rd.geo = static_cast<const float4 *>(B.geo.ptr);
+    rd.oq = static_cast<const uint2 *>(B.oq.ptr);
+    rd.gb = static_cast<const uint32_t *>(B.gb.ptr);
+    rd.dtype = dtype;
+    GS_CUDA(ctx, gs_launch_blend_batch(rd, sv, ranges, views, n_views, opts->tile_w, opts->tile_h, order,
+                                       total_tiles, qs + 193, s));
+    GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 4 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+    GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
+                          const gs_options *opts, const gs_framebuffer *fbs, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    gs_status st;
+    if ((st = check_gaussians(ctx, g)) != GS_OK || (st = check_options(ctx, opts)) != GS_OK) return st;
+    if (n_views < 1 || n_views > 4096 || !cams || !fbs)
+        return fail(ctx, GS_ERR_INVALID_ARG, "n_views must be in 1..4096 with cameras and framebuffers");
+    for (int v = 0; v < n_views; ++v) {
+        if ((st = check_camera(ctx, &cams[v])) != GS_OK) return st;
+        if (!fbs[v].rgb) return fail(ctx, GS_ERR_INVALID_ARG, "a framebuffer rgb is NULL");
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto &B = ctx->batch;
+    const int64_t n = g->n;
+    // Host view table (pinned, read by the frame's first copy).
+    if (B.h_views_cap < n_views) {
+        if (B.h_views) cudaFreeHost(B.h_views);
+        B.h_views = nullptr;
+        B.h_views_cap = 0;
+        if (cudaMallocHost(&B.h_views, (size_t)n_views * sizeof(ViewDesc)) != cudaSuccess)
+            return fail(ctx, GS_ERR_OOM, "cannot allocate the pinned view table");
+        B.h_views_cap = n_views;
+        if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+    }
+    int64_t total_tiles = 0;
+    std::vector<int64_t> sig = {n, g->sh_degree, (int64_t)(uintptr_t)g->means, (int64_t)(uintptr_t)g->log_scales,
+                                (int64_t)(uintptr_t)g->quats, (int64_t)(uintptr_t)g->opacity_logits,
+                                (int64_t)(uintptr_t)g->sh, n_views, opts->tile_w, opts->tile_h,
+                                opts->record_dtype};
+    for (int v = 0; v < n_views; ++v) {
+        ViewDesc &V = B.h_views[v];
+        V.cam = make_cam(&cams[v]);
+        V.grid = make_grid(&cams[v], opts);
+        V.tile_base = (uint32_t)total_tiles;
+        for (int c = 0; c < 3; ++c) V.bg[c] = opts->bg[c];
+        V.rgb = fbs[v].rgb;
+        V.final_T = fbs[v].final_T;
+        V.n_contrib = fbs[v].n_contrib;
+        V.n_eval = fbs[v].n_eval;
+        total_tiles += (int64_t)V.grid.tiles_x * V.grid.tiles_y;
+        sig.push_back(cams[v].width);
+        sig.push_back(cams[v].height);
+    }
+    if (total_tiles >= (int64_t(1) << 31)) return fail(ctx, GS_ERR_INVALID_ARG, "too many tiles in one batch");
+    const int bits = key_bits_for((int)total_tiles);
+    if (B.rec_cap == 0) B.rec_cap = std::max<int64_t>(int64_t(1) << 20, n * n_views / 8);
+    if (B.key_cap == 0) B.key_cap = std::max<int64_t>(int64_t(1) << 22, 4 * B.rec_cap);
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        const int64_t rc = B.rec_cap, kc = B.key_cap;
+        void *before[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.oq.ptr, B.gb.ptr, B.scratch.ptr,
+                          B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,
+                          B.avals.ptr, B.sort.ptr};
+        const bool lp = opts->record_dtype != GS_RECORD_F32;
+        if ((st = ensure(ctx, B.views, (size_t)n_views * sizeof(ViewDesc), "view table")) != GS_OK ||
+            (st = ensure(ctx, B.rec, (size_t)rc * sizeof(gs_record), "batch records")) != GS_OK ||
+            (st = ensure(ctx, B.meta, (size_t)rc * 8, "batch record meta")) != GS_OK ||
+            (lp && (st = ensure(ctx, B.geo, (size_t)rc * 16, "batch records")) != GS_OK) ||
+            (lp && (st = ensure(ctx, B.oq, (size_t)rc * 8, "batch records")) != GS_OK) ||
+            (lp && (st = ensure(ctx, B.gb, (size_t)rc * 4, "batch records")) != GS_OK) ||
+            (st = ensure(ctx, B.scratch, gs_batch_scratch_bytes(rc, kc), "batch scratch")) != GS_OK ||
+            (st = ensure(ctx, B.ranges, (size_t)total_tiles * 8, "batch ranges")) != GS_OK ||
+            (st = ensure(ctx, B.order, (size_t)total_tiles * 4, "batch queue")) != GS_OK ||
+            (st = ensure(ctx, B.queue, gs_queue_scratch_bytes(), "batch queue")) != GS_OK ||
+            (st = ensure(ctx, B.keys, (size_t)kc * 8, "batch keys")) != GS_OK ||
+            (st = ensure(ctx, B.vals, (size_t)kc * 4, "batch values")) != GS_OK ||
+            (st = ensure(ctx, B.akeys, (size_t)kc * 8, "batch keys")) != GS_OK ||
+            (st = ensure(ctx, B.avals, (size_t)kc * 4, "batch values")) != GS_OK ||
+            (st = ensure(ctx, B.sort, gs_sort_scratch_bytes(kc, bits), "batch sort scratch")) != GS_OK)
+            return st;
+        void *after[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.oq.ptr, B.gb.ptr, B.scratch.ptr,
+                         B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,
+                         B.avals.ptr, B.sort.ptr};
+        std::vector<int64_t> full = sig;
+        full.push_back(rc);
+        full.push_back(kc);
+        bool moved = false;
+        for (size_t k = 0; k < sizeof(before) / sizeof(before[0]); ++k) moved |= before[k] != after[k];
+        if (moved || full != B.sig) {
+            if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+        }
+        if (opts->direct_launch == 0) {  // graph path (default)
+            if (!B.exec) {
+                if (!B.capture) GS_CUDA(ctx, cudaStreamCreateWithFlags(&B.capture, cudaStreamNonBlocking));
+                // Work already queued on the caller's stream comes first.
+                GS_CUDA(ctx, cudaStreamSynchronize(s));
+                cudaGraph_t graph = nullptr;
+                GS_CUDA(ctx, cudaStreamBeginCapture(B.capture, cudaStreamCaptureModeThreadLocal));
+                st = enqueue_batch(ctx, g, n_views, opts, (int32_t)total_tiles, bits, B.capture);
+                const cudaError_t ec = cudaStreamEndCapture(B.capture, &graph);
+                if (st != GS_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return st;
+                }
+                if (ec != cudaSuccess) return cuda_fail(ctx, ec, "cudaStreamEndCapture");
+                const cudaError_t ei = cudaGraphInstantiate(&B.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ei != cudaSuccess) return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+                B.sig = full;
+            }
+            GS_CUDA(ctx, cudaGraphLaunch(B.exec, s));
+        } else {
+            if ((st = enqueue_batch(ctx, g, n_views, opts, (int32_t)total_tiles, bits, s)) != GS_OK) return st;
+        }
+        GS_CUDA(ctx, cudaStreamSynchronize(s));
+        const unsigned long long K = ctx->h_counts[0], nv = ctx->h_counts[1];
+        ctx->stats.n_keys = (int64_t)K;
+        ctx->stats.n_visible = (int64_t)nv;
+        ctx->stats.n_tiles = (int32_t)total_tiles;
+        ctx->stats.key_bits = bits;
+        if (K >= (1ull << 32) - 1)
+            return fail(ctx, GS_ERR_CAPACITY, "more than 2^32-2 (tile, Gaussian) pairs in one batch");
+        if ((int64_t)K > kc || (int64_t)nv > rc) {
+            GS_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s));
+            if ((int64_t)K > kc) B.key_cap = (int64_t)(K + K / 4 + 4096);
+            if ((int64_t)nv > rc) B.rec_cap = (int64_t)(nv + nv / 4 + 4096);
+            continue;
+        }
+        if (*ctx->h_err) return collect_device_error(ctx, s);
+        return GS_OK;
+    }
+    return fail(ctx, GS_ERR_CAPACITY, "batch buffers could not be sized");
+}
+
+gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
+                            gs_options *opts, const gs_framebuffer *fbs, void *stream, float *ms_out) {
+    if (!ctx || !opts) return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int shapes[3][2] = {{16, 16}, {16, 8}, {8, 8}};
+    cudaEvent_t e0, e1;
+    GS_CUDA(ctx, cudaEventCreate(&e0));
+    GS_CUDA(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_k = 0;
+    gs_status st = GS_OK;
+    for (int k = 0; k < 3 && st == GS_OK; ++k) {
+        gs_options o = *opts;
+        o.tile_w = shapes[k][0];
+        o.tile_h = shapes[k][1];
+        for (int w = 0; w < 2 && st == GS_OK; ++w) st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
+        float total = 0.f;
+        for (int r = 0; r < 3 && st == GS_OK; ++r) {
+            cudaEventRecord(e0, s);
+            st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            total += ms;
+        }
+        if (ms_out) ms_out[k] = total / 3.f;
+        if (st == GS_OK && total < best) {
+            best = total;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GS_OK) return st;
+    opts->tile_w = shapes[best_k][0];
+    opts->tile_h = shapes[best_k][1];
     return GS_OK;
 }
 

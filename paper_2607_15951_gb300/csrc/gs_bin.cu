@@ -144,16 +144,18 @@ emit_kernel(const float4 *__restrict__ rec, const uint32_t *__restrict__ tiles,
 
 // Orders values[b, e) ascending (a run of equal keys): insertion sort for
 // short runs, Shell sort (Ciura gaps) for long ones.
-__device__ void sort_run(uint32_t *v, int64_t b, int64_t e) {
+__device__ void sort_run(uint32_t *v, int64_t b, int64_t e, const uint2 *meta) {
     const int64_t m = e - b;
     const int gaps[] = {701, 301, 132, 57, 23, 10, 4, 1};
+    auto order = [&](uint32_t x) { return meta ? meta[x].y : x; };
     for (int gi = 0; gi < 8; ++gi) {
         const int64_t gap = gaps[gi];
         if (gap >= m) continue;
         for (int64_t i = b + gap; i < e; ++i) {
             const uint32_t x = v[i];
+            const uint32_t ox = order(x);
             int64_t j = i;
-            while (j - gap >= b && v[j - gap] > x) {
+            while (j - gap >= b && order(v[j - gap]) > ox) {
                 v[j] = v[j - gap];
                 j -= gap;
             }
@@ -169,14 +171,14 @@ __device__ void sort_run(uint32_t *v, int64_t b, int64_t e) {
 __global__ void ranges_kernel(const uint64_t *__restrict__ keys, int64_t n_host,
                               const unsigned long long *d_n, int32_t n_tiles,
                               uint32_t *__restrict__ ranges, uint32_t *values, int fix_ties,
-                              uint32_t *d_err) {
+                              const uint2 *meta, uint32_t *d_err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = d_n ? (int64_t)*d_n : n_host;
     if (i >= n) return;
     if (fix_ties && (i == 0 || keys[i - 1] != keys[i]) && i + 1 < n && keys[i + 1] == keys[i]) {
         int64_t e = i + 2;
         while (e < n && keys[e] == keys[i]) ++e;
-        sort_run(values, i, e);
+        sort_run(values, i, e, meta);
     }
     const uint64_t tile = keys[i] >> 32;
     if (tile >= (uint64_t)n_tiles) {
@@ -234,7 +236,7 @@ cudaError_t gs_launch_ranges(const uint64_t *keys, int64_t n, int32_t n_tiles, u
     cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess || n == 0) return e;
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n, nullptr, n_tiles, ranges, nullptr, 0, d_err);
+    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n, nullptr, n_tiles, ranges, nullptr, 0, nullptr, d_err);
     return cudaGetLastError();
 }
 
@@ -244,6 +246,78 @@ cudaError_t gs_launch_ranges_dev(const uint64_t *keys, uint32_t *values, int64_t
     cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess || n_capacity == 0) return e;
     const unsigned blocks = (unsigned)((n_capacity + 255) / 256);
-    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n_capacity, d_n, n_tiles, ranges, values, 1, d_err);
+    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n_capacity, d_n, n_tiles, ranges, values, 1, nullptr, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_ranges_batch(const uint64_t *keys, uint32_t *values, const uint2 *meta, int64_t n_capacity,
+                                   const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
+                                   uint32_t *d_err, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess || n_capacity == 0) return e;
+    const unsigned blocks = (unsigned)((n_capacity + 255) / 256);
+    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n_capacity, d_n, n_tiles, ranges, values, 1, meta, d_err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Work queue of a batched blend: global tiles ordered by the bit length of
+// their list (longest first), so that the largest tiles start first and the
+// short ones fill the tail. Order inside a bucket is arbitrary (it does not
+// change any output).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kBuckets = 33;
+
+__global__ void queue_count_kernel(const uint32_t *__restrict__ ranges, int32_t n_tiles, uint32_t *qs) {
+    // qs: [0,64) counts, [64,128) starts, [128,192) cursors, 192 ticket, 193 head
+    __shared__ uint32_t s_c[kBuckets];
+    __shared__ bool s_last;
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) s_c[b] = 0;
+    __syncthreads();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        atomicAdd(&s_c[len ? 32 - __clz(len) : 0], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x)
+        if (s_c[b]) atomicAdd(&qs[b], s_c[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&qs[192], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    uint32_t run = 0;
+    for (int b = kBuckets - 1; b >= 0; --b) {
+        qs[64 + b] = run;
+        run += __ldcg(&qs[b]);
+    }
+}
+
+__global__ void queue_scatter_kernel(const uint32_t *__restrict__ ranges, int32_t n_tiles, uint32_t *qs,
+                                     uint32_t *__restrict__ order) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+    const int b = len ? 32 - __clz(len) : 0;
+    order[qs[64 + b] + atomicAdd(&qs[128 + b], 1u)] = (uint32_t)t;
+}
+
+}  // namespace
+
+size_t gs_queue_scratch_bytes() { return 256 * sizeof(uint32_t); }
+
+cudaError_t gs_launch_queue(const uint32_t *ranges, int32_t n_tiles, uint32_t *qs, uint32_t *order,
+                            cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(qs, 0, gs_queue_scratch_bytes(), s);
+    if (e != cudaSuccess || n_tiles == 0) return e;
+    const unsigned blocks = (unsigned)((n_tiles + 255) / 256);
+    queue_count_kernel<<<blocks < 608 ? blocks : 608, 256, 0, s>>>(ranges, n_tiles, qs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    queue_scatter_kernel<<<blocks, 256, 0, s>>>(ranges, n_tiles, qs, order);
     return cudaGetLastError();
 }

@@ -132,13 +132,12 @@ __device__ __forceinline__ void write_pixel(const BlendArgs &a, int px, int py, 
 // Culled variant: warps own 8x8 blocks, two pixels per lane.
 // ---------------------------------------------------------------------------
 template <int TW, int TH>
-__global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_culled_kernel(const BlendArgs a) {
+__device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) {
     constexpr int kWX = TW / 8, kWarps = kWX * (TH / 8), kThreads = kWarps * 32;
     __shared__ float4 s_a[kBatch], s_b[kBatch], s_box[kBatch];
     __shared__ float2 s_rg[kBatch];
     const SRec S{s_a, s_b, s_rg, s_box};
 
-    const int tile = blockIdx.x;
     const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bx = tx * TW + (warp % kWX) * 8, by = ty * TH + (warp / kWX) * 8;
@@ -202,6 +201,46 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_culled_kernel(
     write_pixel(a, px, py1, p1);
 }
 
+template <int TW, int TH>
+__global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_culled_kernel(const BlendArgs a) {
+    blend_tile_culled<TW, TH>(a, blockIdx.x);
+}
+
+// Persistent blend over many views: blocks take global tiles from a queue
+// (largest lists first); each tile is rendered with its view's parameters.
+struct BlendBatchArgs {
+    RecordReader rd;
+    const uint32_t *values;
+    const uint32_t *ranges;   // indexed by global tile
+    const ViewDesc *views;
+    int n_views;
+    const uint32_t *order;    // global tiles in queue order
+    int32_t n_tiles;
+    uint32_t *queue_head;
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(const BlendBatchArgs b) {
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.queue_head, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= b.n_tiles) return;
+        const uint32_t gt = b.order[item];
+        int lo = 0, hi = b.n_views - 1;  // last view whose first tile <= gt
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.views[mid].tile_base <= gt) lo = mid; else hi = mid - 1;
+        }
+        const ViewDesc &V = b.views[lo];
+        BlendArgs a{b.rd, b.values, b.ranges + 2 * (size_t)V.tile_base, V.grid, V.cam.width, V.cam.height,
+                    {V.bg[0], V.bg[1], V.bg[2]}, V.rgb, V.final_T, V.n_contrib, V.n_eval};
+        blend_tile_culled<TW, TH>(a, (int)(gt - V.tile_base));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Basic variant: one thread per pixel, every record evaluated.
 // ---------------------------------------------------------------------------
@@ -243,6 +282,27 @@ __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) 
 }
 
 }  // namespace
+
+cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                  const ViewDesc *views_dev, int n_views, int tile_w, int tile_h,
+                                  const uint32_t *order, int32_t n_tiles, uint32_t *queue_head, cudaStream_t s) {
+    BlendBatchArgs b{rd, values, ranges, views_dev, n_views, order, n_tiles, queue_head};
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 1;
+    if (tile_w == 16 && tile_h == 16) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<16, 16>, 128, 0);
+        blend_batch_kernel<16, 16><<<(unsigned)(sms * per_sm), 128, 0, s>>>(b);
+    } else if (tile_w == 16 && tile_h == 8) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<16, 8>, 64, 0);
+        blend_batch_kernel<16, 8><<<(unsigned)(sms * per_sm), 64, 0, s>>>(b);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<8, 8>, 32, 0);
+        blend_batch_kernel<8, 8><<<(unsigned)(sms * per_sm), 32, 0, s>>>(b);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],

@@ -213,6 +213,18 @@ struct GsGrid {
     int tile_w, tile_h, tiles_x, tiles_y;
 };
 
+// One view of a batched render (device table, filled by the host per call).
+struct ViewDesc {
+    GsCameraDev cam;
+    GsGrid grid;
+    uint32_t tile_base;  // global id of this view's first tile
+    float bg[3];
+    float *rgb;
+    float *final_T;
+    int32_t *n_contrib;
+    int32_t *n_eval;
+};
+
 cudaError_t gs_launch_project(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                               gs_record *records, uint32_t *tiles, cudaStream_t s);
 
@@ -302,3 +314,28 @@ cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, 
                                 float *d_rec, cudaStream_t s);
 cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   const float *d_rec, const gs_grads &out, cudaStream_t s);
+
+// Batched front end: projection of every (view, Gaussian) pair into compact
+// records (slot j: record, meta = (view, Gaussian index)), then emission of
+// the (global tile, depth) keys whose values are compact slots; digit
+// histograms and bucket offsets as in the single-view front end.
+// counts as in gs_launch_project_bin; counts[3] = compact records used.
+size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity);
+cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
+                                        gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
+                                        int lp_dtype, uint2 *meta, int64_t rec_capacity, uint64_t *keys,
+                                        uint32_t *values, int64_t key_capacity, unsigned long long *counts,
+                                        void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s);
+// Ranges over global tiles with the tie order taken from meta[value].y.
+cudaError_t gs_launch_ranges_batch(const uint64_t *keys, uint32_t *values, const uint2 *meta, int64_t n_capacity,
+                                   const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
+                                   uint32_t *d_err, cudaStream_t s);
+// Persistent blend over a queue of global tiles (largest lists first).
+cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                  const ViewDesc *views_dev, int n_views, int tile_w, int tile_h,
+                                  const uint32_t *order, int32_t n_tiles, uint32_t *queue_head, cudaStream_t s);
+// Largest-first work queue of global tiles; qs: gs_queue_scratch_bytes(),
+// the queue head the blend takes items from is qs[193].
+size_t gs_queue_scratch_bytes();
+cudaError_t gs_launch_queue(const uint32_t *ranges, int32_t n_tiles, uint32_t *qs, uint32_t *order,
+                            cudaStream_t s);

@@ -104,10 +104,10 @@ struct Projected {
 };
 
 template <int DEG>
-__device__ __forceinline__ Projected project_one(const ProjectArgs &P, int64_t i) {
+__device__ __forceinline__ Projected project_one(const ProjectArgs &P, const GsCameraDev &K, const GsGrid &G,
+                                                 int64_t i) {
     Projected out;
     out.tiles = 0;
-    const GsCameraDev &K = P.cam;
     const float mx = __ldg(P.means + 3 * i), my = __ldg(P.means + 3 * i + 1),
                 mz = __ldg(P.means + 3 * i + 2);
     const float tx = fmaf(K.R[0], mx, fmaf(K.R[1], my, fmaf(K.R[2], mz, K.t[0])));
@@ -172,7 +172,7 @@ __device__ __forceinline__ Projected project_one(const ProjectArgs &P, int64_t i
     if (!(det > 0.f) || !isfinite(u) || !isfinite(v) || !isfinite(ext)) return out;
     const int r = ext >= (float)kMaxRadius ? kMaxRadius : (int)ceilf(ext);
     if (r <= 0) return out;
-    const Rect R = tile_rect(u, v, r, P.grid.tile_w, P.grid.tile_h, P.grid.tiles_x, P.grid.tiles_y);
+    const Rect R = tile_rect(u, v, r, G.tile_w, G.tile_h, G.tiles_x, G.tiles_y);
     const uint32_t ntiles = (uint32_t)((R.x1 - R.x0) * (R.y1 - R.y0));
     if (ntiles == 0) return out;
     const float idet = 1.f / det;
@@ -196,7 +196,7 @@ template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs P) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
-    const Projected pr = project_one<DEG>(P, i);
+    const Projected pr = project_one<DEG>(P, P.cam, P.grid, i);
     P.tiles[i] = pr.tiles;
     if (pr.tiles) {
         float4 *out = P.records + 3 * i;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) project_reserve_kernel(const ReserveArgs 
     const int64_t i = (int64_t)blockIdx.x * 256 + tid;
     Projected pr;
     pr.tiles = 0;
-    if (i < A.P.n) pr = project_one<DEG>(A.P, i);
+    if (i < A.P.n) pr = project_one<DEG>(A.P, A.P.cam, A.P.grid, i);
     if (pr.tiles) {
         float4 *out = A.P.records + 3 * i;
         out[0] = pr.r0;
@@ -418,6 +418,205 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
         E.counts[0] = (unsigned long long)K;
         E.counts[1] = (unsigned long long)nv;
         const bool fits = K <= E.capacity;
+        if (!fits) atomicOr(E.d_err, kErrCapacity);
+        E.counts[2] = fits ? (unsigned long long)K : 0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched front end (many views of one scene). Block (b, v) projects
+// Gaussians [256 b, 256 b + 256) for view v and reserves, per block, compact
+// record slots and key slots with the packed counter; records go to compact
+// slot j with meta[j] = (view, Gaussian index). Emission then follows the
+// single-view kernel with the view's tile grid and a global tile id.
+// ---------------------------------------------------------------------------
+struct ReserveBatchArgs {
+    ProjectArgs P;               // scene arrays (cam / grid unused)
+    const ViewDesc *views;
+    unsigned long long *packed;  // visible << 33 | keys
+    uint32_t *list_off;          // per compact slot: first key slot
+    uint2 *meta;                 // per compact slot: (view, Gaussian index)
+    float4 *lp_geo;
+    uint2 *lp_oq;
+    uint32_t *lp_gb;
+    int lp_dtype;
+    int64_t rec_capacity;
+    uint32_t *hist;
+    uint32_t *block_entry;
+    int64_t n_key_blocks;
+    uint32_t *d_err;
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_reserve_batch_kernel(const ReserveBatchArgs A) {
+    __shared__ uint32_t s_t[8], s_v[8];
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_hist[4 * 256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int view = blockIdx.y;
+    const ViewDesc &V = A.views[view];
+    for (int k = tid; k < 4 * 256; k += 256) s_hist[k] = 0;
+    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+    Projected pr;
+    pr.tiles = 0;
+    if (i < A.P.n) pr = project_one<DEG>(A.P, V.cam, V.grid, i);
+    const uint32_t t = pr.tiles, v = t != 0u;
+    uint32_t it = t, iv = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, it, o);
+        const uint32_t b = __shfl_up_sync(0xffffffffu, iv, o);
+        if (lane >= o) { it += a; iv += b; }
+    }
+    if (lane == 31) { s_t[warp] = it; s_v[warp] = iv; }
+    __syncthreads();
+    uint32_t pt = 0, pv = 0, bt = 0, bv = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < warp) { pt += s_t[w]; pv += s_v[w]; }
+        bt += s_t[w];
+        bv += s_v[w];
+    }
+    if (tid == 0) s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) : 0ull;
+    __syncthreads();
+    if (v) {
+        const unsigned long long base = s_base;
+        const uint64_t j = (base >> 33) + pv + iv - 1;
+        if ((int64_t)j < A.rec_capacity) {
+            const uint64_t off = (base & kKeyMask) + pt + it - t;
+            float4 *out = A.P.records + 3 * j;
+            out[0] = pr.r0;
+            out[1] = pr.r1;
+            out[2] = pr.r2;
+            if (A.lp_geo) {
+                A.lp_geo[j] = pr.r0;
+                A.lp_oq[j] = make_uint2(__float_as_uint(pr.r1.x), pack2(pr.r1.y, pr.r1.z, A.lp_dtype));
+                A.lp_gb[j] = pack2(pr.r1.w, pr.r2.x, A.lp_dtype);
+            }
+            A.meta[j] = make_uint2((uint32_t)view, (uint32_t)i);
+            A.list_off[j] = (uint32_t)off;
+            const int64_t b1 = min((int64_t)((off + t - 1) >> kKeyBlockLog2), A.n_key_blocks - 1);
+            for (int64_t b = (int64_t)((off + kKeyBlock - 1) >> kKeyBlockLog2); b <= b1; ++b)
+                A.block_entry[b] = (uint32_t)j;
+            const uint32_t dbits = __float_as_uint(pr.r2.y);
+            for (int d = 0; d < 4; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], t);
+        } else {
+            atomicOr(A.d_err, kErrCapacity);
+        }
+    }
+    __syncthreads();
+    if (bv)
+        for (int k = tid; k < 4 * 256; k += 256)
+            if (s_hist[k]) atomicAdd(&A.hist[k], s_hist[k]);
+}
+
+struct EmitBatchArgs {
+    const float4 *records;       // compact FP32 records (always written)
+    const unsigned long long *packed;
+    const uint32_t *list_off;
+    const uint2 *meta;
+    const uint32_t *block_entry;
+    const ViewDesc *views;
+    int64_t rec_capacity;
+    uint64_t *keys;
+    uint32_t *values;
+    int64_t capacity;
+    unsigned long long *counts;
+    GsSortScratch sc;
+    uint32_t *d_err;
+};
+
+__global__ void __launch_bounds__(256) emit_keys_batch_kernel(const EmitBatchArgs E) {
+    __shared__ uint32_t s_hist[kMaxPasses * 256];
+    __shared__ uint32_t s_off[kKeyBlock + 2];
+    __shared__ uint32_t s_tmp[8];
+    __shared__ int s_j0, s_cnt;
+    __shared__ bool s_last;
+    const int tid = threadIdx.x;
+    const int passes = E.sc.passes;
+    for (int k = tid; k < kMaxPasses * 256; k += 256) s_hist[k] = 0;
+    const unsigned long long packed = *E.packed;
+    const int64_t K = (int64_t)(packed & kKeyMask);
+    const int64_t nv = (int64_t)(packed >> 33);
+    const int64_t k0 = (int64_t)blockIdx.x * kKeyBlock;
+    const bool active = k0 < K && K <= E.capacity && nv <= E.rec_capacity;
+    if (tid == 0 && active) {
+        const int64_t j0 = E.block_entry[blockIdx.x];
+        s_j0 = (int)j0;
+        s_cnt = (int)((nv - j0) < kKeyBlock + 2 ? (nv - j0) : kKeyBlock + 2);
+    }
+    __syncthreads();
+    if (active)
+        for (int q = tid; q < s_cnt; q += 256) s_off[q] = E.list_off[s_j0 + q];
+    __syncthreads();
+    const int64_t kb = k0 + (int64_t)tid * kKeysPerThread;
+    if (active && kb < K) {
+        int lo = 0, hi = s_cnt - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)s_off[mid] <= kb) lo = mid; else hi = mid - 1;
+        }
+        int e = -1;
+        uint32_t j = 0, dbits = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0, tiles_x = 1, tbase = 0;
+        uint32_t run_digit[kMaxPasses], run_count[kMaxPasses];
+        for (int d = 0; d < kMaxPasses; ++d) { run_digit[d] = 0xffffffffu; run_count[d] = 0; }
+        for (int q = 0; q < kKeysPerThread; ++q) {
+            const int64_t k = kb + q;
+            if (k >= K) break;
+            if (e < 0 || (uint64_t)k >= eend) {
+                if (e >= 0) ++lo;
+                while (lo + 1 < s_cnt && (int64_t)s_off[lo + 1] <= k) ++lo;
+                e = lo;
+                j = (uint32_t)(s_j0 + e);
+                ebase = s_off[e];
+                const ViewDesc &V = E.views[E.meta[j].x];
+                const float4 r0 = E.records[3 * (size_t)j];
+                const float4 r2 = E.records[3 * (size_t)j + 2];
+                const Rect R = tile_rect(r0.x, r0.y, __float_as_int(r2.z), V.grid.tile_w, V.grid.tile_h,
+                                         V.grid.tiles_x, V.grid.tiles_y);
+                w = (uint32_t)(R.x1 - R.x0);
+                x0 = (uint32_t)R.x0;
+                y0 = (uint32_t)R.y0;
+                tiles_x = (uint32_t)V.grid.tiles_x;
+                tbase = V.tile_base;
+                eend = ebase + w * (uint32_t)(R.y1 - R.y0);
+                dbits = __float_as_uint(r2.y);
+            }
+            const uint32_t m = (uint32_t)(k - ebase);
+            const uint32_t qy = m / w, rx = m - qy * w;
+            const uint32_t tile = tbase + (y0 + qy) * tiles_x + x0 + rx;
+            E.keys[k] = ((uint64_t)tile << 32) | dbits;
+            E.values[k] = j;
+            for (int d = 4; d < passes; ++d) {
+                const uint32_t dg = (tile >> (8 * (d - 4))) & 255u;
+                if (dg != run_digit[d]) {
+                    if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
+                    run_digit[d] = dg;
+                    run_count[d] = 0;
+                }
+                ++run_count[d];
+            }
+        }
+        for (int d = 4; d < passes; ++d)
+            if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
+    }
+    __syncthreads();
+    if (active)
+        for (int q = tid + 4 * 256; q < passes * 256; q += 256)
+            if (s_hist[q]) atomicAdd(&E.sc.hist[q], s_hist[q]);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(E.sc.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int d = 0; d < passes; ++d) {
+        const uint32_t c = __ldcg(&E.sc.hist[d * 256 + tid]);
+        E.sc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
+    }
+    if (tid == 0) {
+        E.counts[0] = (unsigned long long)K;
+        E.counts[1] = (unsigned long long)nv;
+        E.counts[3] = (unsigned long long)nv;
+        const bool fits = K <= E.capacity && nv <= E.rec_capacity;
         if (!fits) atomicOr(E.d_err, kErrCapacity);
         E.counts[2] = fits ? (unsigned long long)K : 0ull;
     }
@@ -727,5 +926,53 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
         case 2: project_bwd_kernel<2><<<blocks, 256, 0, s>>>(B); break;
         default: project_bwd_kernel<3><<<blocks, 256, 0, s>>>(B); break;
     }
+    return cudaGetLastError();
+}
+
+size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity) {
+    // packed counter, list_off per compact slot, key-block entry table
+    return 256 + ((size_t)rec_capacity * 4 + 255) / 256 * 256 + gs_key_block_bytes(key_capacity);
+}
+
+cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
+                                        gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
+                                        int lp_dtype, uint2 *meta, int64_t rec_capacity, uint64_t *keys,
+                                        uint32_t *values, int64_t key_capacity, unsigned long long *counts,
+                                        void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    char *base = static_cast<char *>(scratch);
+    e = cudaMemsetAsync(base, 0, 256, s);
+    if (e != cudaSuccess || g.n == 0 || n_views == 0) return e;
+    ReserveBatchArgs A;
+    A.P = ProjectArgs{g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.n, GsCameraDev{}, GsGrid{},
+                      reinterpret_cast<float4 *>(records), nullptr,
+                      reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
+                      reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
+    A.views = views_dev;
+    A.packed = reinterpret_cast<unsigned long long *>(base);
+    A.list_off = reinterpret_cast<uint32_t *>(base + 256);
+    A.meta = meta;
+    A.lp_geo = lp_dtype == GS_RECORD_F32 ? nullptr : lp_geo;
+    A.lp_oq = lp_oq;
+    A.lp_gb = lp_gb;
+    A.lp_dtype = lp_dtype;
+    A.rec_capacity = rec_capacity;
+    A.hist = sc.hist;
+    A.block_entry = reinterpret_cast<uint32_t *>(base + 256 + ((size_t)rec_capacity * 4 + 255) / 256 * 256);
+    A.n_key_blocks = (key_capacity + kKeyBlock - 1) / kKeyBlock;
+    A.d_err = d_err;
+    const dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)n_views);
+    switch (g.sh_degree) {
+        case 0: project_reserve_batch_kernel<0><<<grid, 256, 0, s>>>(A); break;
+        case 1: project_reserve_batch_kernel<1><<<grid, 256, 0, s>>>(A); break;
+        case 2: project_reserve_batch_kernel<2><<<grid, 256, 0, s>>>(A); break;
+        default: project_reserve_batch_kernel<3><<<grid, 256, 0, s>>>(A); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    EmitBatchArgs E{reinterpret_cast<const float4 *>(records), A.packed, A.list_off, meta, A.block_entry,
+                    views_dev, rec_capacity, keys, values, key_capacity, counts, sc, d_err};
+    emit_keys_batch_kernel<<<(unsigned)((key_capacity + kKeyBlock - 1) / kKeyBlock), 256, 0, s>>>(E);
     return cudaGetLastError();
 }
