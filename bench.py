@@ -181,6 +181,61 @@ def fwd_bwd(gs, torch, args, flush, local) -> dict:
             "iters": steps, "grads": "means, log_scales, quats, opacity_logits, sh (degree 3)"}
 
 
+def batched(gs, torch, args, flush, local) -> dict:
+    """64 views of the 1M-Gaussian clustered scene along a smooth camera path
+    (1280x720 and 640x480 alternating): one gs_render_batch call with FP16
+    records and the autotuned tile shape, against 64 separate FP32 gs_render
+    calls. Views per second from CUDA events; L2 flushed between iterations."""
+    from paper_2607_15951_gb300 import _native as N
+    from paper_2607_15951_gb300 import scenes
+    scene, cams = scenes.workload("clustered_1m_traj64")
+    g = gs.scene_to_device(scene)
+    ctx = gs.Context(local)
+    stream = torch.cuda.current_stream()
+    outs = gs.alloc_outputs(cams)
+    tile, tune_ms = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
+                                         record_dtype=N.GS_RECORD_F16)
+    iters = max(3, args.steps // 100)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for i in range(iters):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / iters
+
+    def per_view():
+        for c, o in zip(cams, outs):
+            gs.gs_render(ctx, g, scene.sh_degree, c, o["rgb"])
+
+    def batch():
+        gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile, record_dtype=N.GS_RECORD_F16)
+
+    ms_pv = timed(per_view)
+    ms_b = timed(batch)
+    ms_b32 = timed(lambda: gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs))
+    st = gs.gs_last_render_stats(ctx)
+    ctx.close()
+    v = len(cams)
+    return {"workload": "clustered_1m_traj64", "views": v,
+            "description": "1M Gaussians (seed 3), 64 poses on a Catmull-Rom path, 1280x720 / 640x480",
+            "per_view_f32_views_per_s": round(v / (ms_pv / 1e3), 1),
+            "batched_f16_views_per_s": round(v / (ms_b / 1e3), 1),
+            "batched_f32_views_per_s": round(v / (ms_b32 / 1e3), 1),
+            "speedup_batched_f16_vs_per_view_f32": round(ms_pv / ms_b, 3),
+            "ms_per_batch": round(ms_b, 3), "autotuned_tile": list(tile),
+            "autotune_ms_16x16_16x8_8x8": [round(x, 3) for x in tune_ms],
+            "keys_per_batch": st["n_keys"], "iters": iters}
+
+
 def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:
     """Time the FP64 oracle on the host cores rendering whole frames of the
     same workload until about ``budget_s`` seconds have passed."""
@@ -241,6 +296,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fwd-bwd", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--blend-variant", type=int, default=0, help="0 culled (default), 1 basic")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -379,6 +435,8 @@ def main():
     line["gpu_launches"] = per_step * args.steps
     if not args.no_fwd_bwd:
         line["fwd_bwd"] = fwd_bwd(gs, torch, args, flush, local)
+    if not args.no_batched:
+        line["batched"] = batched(gs, torch, args, flush, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cam)
     if rank == 0:
