@@ -288,6 +288,17 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
 gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
                             gs_options *opts, const gs_framebuffer *fbs, void *stream, float *ms_out);
 
+/* Self-test of the library's failure detection (no counterpart in the
+ * paper). Every wait of one thread block on another (the decoupled
+ * look-backs of the scan and of the sort) gives up after a time limit, sets
+ * the context's error word and stays in bounds, so a lost predecessor can
+ * never hang the GPU. This entry point makes such a wait run out on purpose:
+ * it runs the scan (kind 0) or one sort pass (kind 1) with partition 0 never
+ * taken, so every block waits on a status word nothing sets, with the given
+ * limit (1 us .. 5 s). Expected result: GS_ERR_TIMEOUT, after which the
+ * context works normally. SYNCHRONISES; allocates and frees its scratch. */
+gs_status gs_selftest_bounded_wait(gs_context *ctx, int32_t kind, int64_t timeout_ns, void *stream);
+
 /* Sets the number of (tile, Gaussian) pairs gs_render's key buffers hold and
  * stops the context from shrinking it between frames (the buffers grow if a
  * frame needs more). */

@@ -238,6 +238,13 @@ def gs_reserve_keys(ctx: Context, key_capacity: int) -> None:
     ctx.check(_lib().gs_reserve_keys(ctx.handle, int(key_capacity)))
 
 
+def gs_selftest_bounded_wait(ctx: Context, kind: int, timeout_ns: int, stream=None) -> int:
+    """Runs the bounded-wait self-test and returns its raw status (expected:
+    GS_ERR_TIMEOUT). Does not raise on that status."""
+    return int(_lib().gs_selftest_bounded_wait(ctx.handle, int(kind), int(timeout_ns),
+                                               _stream(stream)))
+
+
 def gs_set_stage_timing(ctx: Context, enable: bool) -> None:
     ctx.check(_lib().gs_set_stage_timing(ctx.handle, 1 if enable else 0))
 

@@ -792,6 +792,24 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     return GS_OK;
 }
 
+gs_status gs_selftest_bounded_wait(gs_context *ctx, int32_t kind, int64_t timeout_ns, void *stream) {
+    if (!ctx || (kind != 0 && kind != 1) || timeout_ns < 1000 || timeout_ns > 5000000000ll)
+        return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = 1 << 20;  // a few hundred blocks, all waiting on partition 0
+    gs_status st;
+    DevBuf buf;
+    if ((st = ensure(ctx, buf, gs_selftest_scratch_bytes(n), "self-test scratch")) != GS_OK) return st;
+    GS_CUDA(ctx, cudaStreamSynchronize(s));
+    GS_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s));
+    cudaError_t e = gs_launch_selftest_wait(kind, n, buf.ptr, ctx->d_err, (unsigned long long)timeout_ns, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf.ptr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bounded-wait self-test");
+    return collect_device_error(ctx, s);
+}
+
 gs_status gs_reserve_keys(gs_context *ctx, int64_t key_capacity) {
     if (!ctx || key_capacity < 1 || key_capacity >= (int64_t(1) << 32) - 1) return GS_ERR_INVALID_ARG;
     ctx->key_capacity = key_capacity;

@@ -17,7 +17,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 __global__ void __launch_bounds__(kScanThreads)
 scan_kernel(const uint32_t *__restrict__ in, int64_t n, unsigned long long *__restrict__ out,
             unsigned long long *counts, uint32_t *counter, unsigned long long *status,
-            int64_t num_parts, uint32_t *d_err) {
+            int64_t num_parts, uint32_t *d_err, unsigned long long timeout_ns) {
     __shared__ uint32_t s_part;
     __shared__ unsigned long long s_warp[kScanThreads / 32];
     __shared__ uint32_t s_vis[kScanThreads / 32];
@@ -64,7 +64,7 @@ scan_kernel(const uint32_t *__restrict__ in, int64_t n, unsigned long long *__re
         } else {
             if (lane == 0) st_relaxed_u64(status + p, kFlagAgg | block_total);
             bool to;
-            prefix = warp_lookback(status, p, d_err, &to);
+            prefix = warp_lookback(status, p, d_err, &to, timeout_ns);
             if (lane == 0) st_relaxed_u64(status + p, kFlagIncl | ((prefix + block_total) & kValueMask));
         }
         if (lane == 0) {
@@ -216,7 +216,7 @@ cudaError_t gs_launch_scan(const uint32_t *tiles, int64_t n, unsigned long long 
     unsigned long long *status =
         reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 16);
     scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(tiles, n, offsets, counts, counter, status,
-                                                         parts, d_err);
+                                                         parts, d_err, kSpinTimeoutNs);
     return cudaGetLastError();
 }
 
@@ -320,4 +320,46 @@ cudaError_t gs_launch_queue(const uint32_t *ranges, int32_t n_tiles, uint32_t *q
     if (e != cudaSuccess) return e;
     queue_scatter_kernel<<<blocks, 256, 0, s>>>(ranges, n_tiles, qs, order);
     return cudaGetLastError();
+}
+
+size_t gs_selftest_scratch_bytes(int64_t n) {
+    // scan: counter + status (parts + 1) + offsets + counts; sort: keys,
+    // values, their copies and the sort scratch
+    const int64_t parts = (n + kScanTile - 1) / kScanTile + 1;
+    const size_t scan = 256 + (size_t)parts * 8 + (size_t)n * 8 + 64;
+    const size_t sort = (size_t)n * 24 + gs_sort_scratch_bytes(n, 8) + 4096;
+    return scan > sort ? scan : sort;
+}
+
+cudaError_t gs_launch_selftest_wait(int kind, int64_t n, void *scratch, uint32_t *d_err,
+                                    unsigned long long timeout_ns, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0, gs_selftest_scratch_bytes(n), s);
+    if (e != cudaSuccess) return e;
+    char *base = static_cast<char *>(scratch);
+    const uint32_t one = 1;
+    if (kind == 0) {
+        const int64_t parts = (n + kScanTile - 1) / kScanTile;
+        uint32_t *counter = reinterpret_cast<uint32_t *>(base);
+        unsigned long long *status = reinterpret_cast<unsigned long long *>(base + 256);
+        unsigned long long *offsets = status + parts + 1;
+        unsigned long long *counts = offsets + n;
+        const uint32_t *tiles = reinterpret_cast<const uint32_t *>(counts + 4);  // zeros
+        e = cudaMemcpyAsync(counter, &one, 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        // Blocks take partitions 1 .. parts; partition 0 is never taken.
+        scan_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(tiles, n, offsets, counts, counter, status,
+                                                             parts + 1, d_err, timeout_ns);
+        return cudaGetLastError();
+    }
+    uint64_t *keys = reinterpret_cast<uint64_t *>(base);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(keys + n);
+    uint64_t *akeys = reinterpret_cast<uint64_t *>(vals + n);
+    uint32_t *avals = reinterpret_cast<uint32_t *>(akeys + n);
+    char *sbase = reinterpret_cast<char *>(avals + n);
+    sbase += (256 - reinterpret_cast<uintptr_t>(sbase) % 256) % 256;
+    const GsSortScratch sc = gs_sort_carve(sbase, n, 8);
+    e = cudaMemcpyAsync(sc.counter, &one, 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    bool in_alt = false;
+    return gs_launch_sort_passes(keys, vals, akeys, avals, n, nullptr, sc, d_err, &in_alt, s, timeout_ns, 1);
 }

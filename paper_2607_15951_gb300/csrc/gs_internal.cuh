@@ -66,7 +66,8 @@ constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 // Sets kErrTimeout (and returns a meaningless sum) if a predecessor stays
 // unpublished for kSpinTimeoutNs or another block already timed out.
 __device__ __forceinline__ unsigned long long warp_lookback(const unsigned long long *status, long long p,
-                                            uint32_t *d_err, bool *timed_out) {
+                                            uint32_t *d_err, bool *timed_out,
+                                            unsigned long long timeout_ns = kSpinTimeoutNs) {
     const int lane = threadIdx.x & 31;
     unsigned long long excl = 0;
     long long q = p - 1;
@@ -76,7 +77,7 @@ __device__ __forceinline__ unsigned long long warp_lookback(const unsigned long 
         const long long idx = q - lane;
         const unsigned long long s = idx >= 0 ? ld_relaxed_u64(status + idx) : kFlagIncl;
         if (!__all_sync(0xffffffffu, (s >> 62) != 0)) {
-            const bool give_up = (global_ns() - t0 > kSpinTimeoutNs) ||
+            const bool give_up = (global_ns() - t0 > timeout_ns) ||
                                  (ld_relaxed_u32(d_err) & kErrTimeout);
             if (__any_sync(0xffffffffu, give_up)) {
                 if (lane == 0) atomicOr(d_err, kErrTimeout);
@@ -235,6 +236,13 @@ size_t gs_scan_scratch_bytes(int64_t n);
 cudaError_t gs_launch_scan(const uint32_t *tiles, int64_t n, unsigned long long *offsets,
                            unsigned long long *counts, void *scratch, uint32_t *d_err,
                            cudaStream_t s);
+// Self-test of the bounded waits: runs the scan (kind 0) or one onesweep pass
+// (kind 1) on n zero items with the partition counter preset to 1, so that
+// partition 0 never publishes; every block waiting on it must give up after
+// timeout_ns and set kErrTimeout. Scratch: gs_selftest_scratch_bytes(n).
+size_t gs_selftest_scratch_bytes(int64_t n);
+cudaError_t gs_launch_selftest_wait(int kind, int64_t n, void *scratch, uint32_t *d_err,
+                                    unsigned long long timeout_ns, cudaStream_t s);
 
 cudaError_t gs_launch_emit(const gs_record *records, const uint32_t *tiles,
                            const unsigned long long *offsets, int64_t n, const GsGrid &grid,
@@ -286,7 +294,8 @@ cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
 cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
                                   uint32_t *alt_values, int64_t n_capacity,
                                   const unsigned long long *d_n, const GsSortScratch &sc,
-                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s);
+                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64);
 
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads, GS_SORT_MIN_BLOCKS)
 onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n_host,
                 const unsigned long long *d_n, int pass, int64_t parts, SortScratch sc,
-                uint32_t *d_err) {
+                uint32_t *d_err, unsigned long long timeout_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);                       // kTile
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kTile);            // kTile
@@ -183,7 +183,7 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
             }
             q -= consumed;
             if (!found && consumed == 0 && (++polls & 63u) == 0u &&
-                ((global_ns() - t0 > kSpinTimeoutNs) || (ld_relaxed_u32(d_err) & kErrTimeout))) {
+                ((global_ns() - t0 > timeout_ns) || (ld_relaxed_u32(d_err) & kErrTimeout))) {
                 atomicOr(d_err, kErrTimeout);
                 __threadfence();
                 break;
@@ -251,7 +251,8 @@ GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits) {
 cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
                                   uint32_t *alt_values, int64_t n_capacity,
                                   const unsigned long long *d_n, const GsSortScratch &sc,
-                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s) {
+                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                  unsigned long long timeout_ns, int max_passes) {
     *result_in_alt = false;
     cudaError_t e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kOnesweepSmem);
@@ -260,9 +261,10 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
     const uint32_t *vin = values;
     uint64_t *kout = alt_keys;
     uint32_t *vout = alt_values;
-    for (int pass = 0; pass < sc.passes; ++pass) {
+    const int passes = sc.passes < max_passes ? sc.passes : max_passes;
+    for (int pass = 0; pass < passes; ++pass) {
         onesweep_kernel<<<(unsigned)sc.parts, kThreads, kOnesweepSmem, s>>>(
-            kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err);
+            kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         kin = kout;
@@ -270,7 +272,7 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
         kout = (kout == alt_keys) ? keys : alt_keys;
         vout = (vout == alt_values) ? values : alt_values;
     }
-    *result_in_alt = (sc.passes & 1) != 0;
+    *result_in_alt = (passes & 1) != 0;
     return cudaSuccess;
 }
 
