@@ -132,8 +132,13 @@ typedef struct {
     int32_t blend_variant;  /* GS_BLEND_CULLED (default) or GS_BLEND_BASIC     */
     int32_t direct_launch;  /* gs_render_batch: 0 = replay a captured CUDA graph
                                (default), 1 = launch the kernels directly      */
-    int32_t reserved[5];    /* must be zero                                    */
+    int32_t sync_mode;      /* gs_render: GS_SYNC_FRAME (default) or
+                               GS_SYNC_DEFERRED, see gs_render                 */
+    int32_t reserved[4];    /* must be zero                                    */
 } gs_options;
+
+/* When gs_render checks a frame's key count (see gs_render). */
+enum { GS_SYNC_FRAME = 0, GS_SYNC_DEFERRED = 1 };
 
 void gs_default_options(gs_options *opts /* host */);
 
@@ -223,12 +228,25 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
 
 /* Whole forward pass (Sec. 3.1: cull, project, depth-sort per tile,
  * composite) on workspace owned by the context, with the same results as
- * gs_project -> gs_bin -> gs_blend. One fused kernel projects, scans the tile
- * counts and emits the keys; the sort and the ranges read the key count on
- * the device; the blend follows. The key buffers are sized from earlier
- * frames (with headroom): the call SYNCHRONISES once at the end to check the
- * count, and if the frame needed more room it grows the buffers and renders
- * the frame again, so a returned image is never truncated. */
+ * gs_project -> gs_bin -> gs_blend. Two kernels project the Gaussians,
+ * reserve key slots and emit the keys with the sort's digit histograms; the
+ * sort and the ranges read the key count on the device; the blend follows.
+ * The key buffers are sized from earlier frames (with headroom); a frame that
+ * needs more writes nothing past them and is detected by its count:
+ *   GS_SYNC_FRAME     the call SYNCHRONISES once at the end to check the
+ *                     count; if the frame needed more room it grows the
+ *                     buffers and renders the frame again, so a returned
+ *                     image is never truncated.
+ *   GS_SYNC_DEFERRED  the call does not synchronise (up to 4 frames in
+ *                     flight). The count and the error word of each frame
+ *                     are read back asynchronously and checked by later calls
+ *                     on the context (gs_render, gs_render_backward,
+ *                     gs_sync_status, gs_last_render_stats). A frame that
+ *                     overflowed makes that later call return
+ *                     GS_ERR_CAPACITY without doing its own work: the buffers
+ *                     have then grown and the caller renders again.
+ *                     gs_render_backward waits for the frame it
+ *                     differentiates and fails if that frame overflowed. */
 gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
                     const gs_options *opts, const gs_framebuffer *fb, void *stream);
 
@@ -304,14 +322,16 @@ gs_status gs_selftest_bounded_wait(gs_context *ctx, int32_t kind, int64_t timeou
  * frame needs more). */
 gs_status gs_reserve_keys(gs_context *ctx, int64_t key_capacity);
 
-/* Statistics of the last gs_render on this context (host out). */
+/* Statistics of the last gs_render on this context (host out). Waits for
+ * deferred frames first and returns the first error among them (the
+ * statistics are still filled in). */
 typedef struct {
     int64_t n_visible; /* records with radius > 0                              */
     int64_t n_keys;    /* (tile, Gaussian) pairs K                             */
     int32_t key_bits;  /* significant key bits sorted                          */
     int32_t n_tiles;
 } gs_render_stats;
-gs_status gs_last_render_stats(const gs_context *ctx, gs_render_stats *out);
+gs_status gs_last_render_stats(gs_context *ctx, gs_render_stats *out);
 
 /* Per-stage device times of gs_render, measured with CUDA events recorded on
  * the render stream between the stages (tracing; off by default). */

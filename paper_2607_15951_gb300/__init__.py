@@ -63,7 +63,7 @@ def camera_struct(cam) -> N.gs_camera:
 
 
 def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
-                   blend_variant: int = 0) -> N.gs_options:
+                   blend_variant: int = 0, deferred: bool = False) -> N.gs_options:
     o = N.gs_options()
     _lib().gs_default_options(ctypes.byref(o))
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
@@ -71,6 +71,7 @@ def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
         o.bg[i] = float(bg[i])
     o.record_dtype = int(record_dtype)
     o.blend_variant = int(blend_variant)
+    o.sync_mode = N.GS_SYNC_DEFERRED if deferred else N.GS_SYNC_FRAME
     return o
 
 
@@ -201,9 +202,11 @@ def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_co
 
 def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
               n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
-              record_dtype: int = 0, stream=None) -> None:
+              record_dtype: int = 0, deferred: bool = False, stream=None) -> None:
+    """deferred=True: GS_SYNC_DEFERRED (no host synchronisation; an overflow
+    or device error is raised by a later call on the context)."""
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant)
+    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred)
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
                                ctypes.byref(fb), _stream(stream)))
@@ -267,7 +270,8 @@ def scene_to_device(scene, device="cuda") -> dict:
 
 
 def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
-           aux: bool = True, variant: int = 0, record_dtype: int = 0, stream=None) -> dict:
+           aux: bool = True, variant: int = 0, record_dtype: int = 0, deferred: bool = False,
+           stream=None) -> dict:
     """Allocate outputs with torch and call gs_render."""
     import torch
     H, W = int(cam.height), int(cam.width)
@@ -279,7 +283,7 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
         out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
               out.get("n_eval"), tile=tile, bg=bg, variant=variant, record_dtype=record_dtype,
-              stream=stream)
+              deferred=deferred, stream=stream)
     return out
 
 
@@ -292,11 +296,17 @@ def _autograd_function():
 
     class _Rasterize(torch.autograd.Function):
         @staticmethod
-        def forward(fctx, means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree, tile, bg):
+        def forward(fctx, means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree, tile, bg,
+                    deferred):
             g = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
                  "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
                  "sh": sh.contiguous()}
-            out = render(ctx, g, sh_degree, cam, tile=tile, bg=bg)
+            H, W = int(cam.height), int(cam.width)
+            out = {"rgb": torch.empty((H, W, 3), dtype=torch.float32, device=means.device),
+                   "final_T": torch.empty((H, W), dtype=torch.float32, device=means.device),
+                   "n_contrib": torch.empty((H, W), dtype=torch.int32, device=means.device)}
+            gs_render(ctx, g, sh_degree, cam, out["rgb"], out["final_T"], out["n_contrib"], None,
+                      tile=tile, bg=bg, deferred=deferred)
             fctx.gs = (ctx, cam, sh_degree, tile, bg, g)
             fctx.save_for_backward(out["final_T"], out["n_contrib"])
             fctx.mark_non_differentiable(out["final_T"])
@@ -310,7 +320,7 @@ def _autograd_function():
             gs_render_backward(ctx, g, sh_degree, cam, final_T, n_contrib, d_rgb.contiguous(), grads,
                                tile=tile, bg=bg)
             return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
-                    grads["sh"], None, None, None, None, None)
+                    grads["sh"], None, None, None, None, None, None)
 
     return _Rasterize
 
@@ -319,15 +329,20 @@ _RASTERIZE = None
 
 
 def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Context, cam, sh_degree: int,
-                       tile=(16, 16), bg=(0.0, 0.0, 0.0)):
+                       tile=(16, 16), bg=(0.0, 0.0, 0.0), deferred: bool = True):
     """Differentiable render: returns (rgb (H,W,3), final_T (H,W)); gradients
     flow to the five parameter tensors. The backward of a render must run
-    before the next render on the same context."""
+    before the next render on the same context.
+
+    deferred=True (default) renders with GS_SYNC_DEFERRED: the forward does
+    not wait for the GPU; the backward checks the forward's key count and
+    raises GSError (GS_ERR_CAPACITY) if that frame overflowed its buffers,
+    which have then grown, so the iteration can simply be repeated."""
     global _RASTERIZE
     if _RASTERIZE is None:
         _RASTERIZE = _autograd_function()
     return _RASTERIZE.apply(means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree,
-                            tuple(tile), tuple(bg))
+                            tuple(tile), tuple(bg), bool(deferred))
 
 
 # ---------------------------------------------------------------------------

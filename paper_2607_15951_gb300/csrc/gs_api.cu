@@ -53,6 +53,21 @@ struct gs_context {
     bool timing = false;
     bool timed_once = false;
     cudaEvent_t ev[8] = {};
+    // Frames rendered with GS_SYNC_DEFERRED whose counts are not checked yet
+    // (a ring, oldest at ring_head). h_ring holds per slot the four counts and
+    // the error word, copied back after the frame.
+    static constexpr int kRing = 4;
+    struct Pending {
+        cudaEvent_t done = nullptr;
+        uint64_t seq = 0;
+        int64_t cap = 0;
+        int n_tiles = 0, bits = 0;
+    } ring[kRing];
+    unsigned long long *h_ring = nullptr;
+    int ring_head = 0, ring_count = 0;
+    uint64_t next_seq = 1;   // sequence number of the next deferred frame
+    uint64_t clear_seq = 0;  // frames before this one saw an error word already reported
+    uint64_t last_seq = 0;   // the last gs_render, if it was deferred
 };
 
 namespace {
@@ -119,7 +134,9 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
         return fail(ctx, GS_ERR_INVALID_ARG, "blend_variant must be GS_BLEND_CULLED or GS_BLEND_BASIC");
     if (o->direct_launch != 0 && o->direct_launch != 1)
         return fail(ctx, GS_ERR_INVALID_ARG, "direct_launch must be 0 or 1");
-    for (int i = 0; i < 5; ++i)
+    if (o->sync_mode != GS_SYNC_FRAME && o->sync_mode != GS_SYNC_DEFERRED)
+        return fail(ctx, GS_ERR_INVALID_ARG, "sync_mode must be GS_SYNC_FRAME or GS_SYNC_DEFERRED");
+    for (int i = 0; i < 4; ++i)
         if (o->reserved[i] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
@@ -184,6 +201,64 @@ gs_status collect_device_error(gs_context *ctx, cudaStream_t s) {
         return fail(ctx, GS_ERR_TIMEOUT, "a device-side wait gave up (look-back timeout)");
     if (w & gs::kErrCapacity) return fail(ctx, GS_ERR_CAPACITY, "a device buffer was too small");
     return fail(ctx, GS_ERR_INVALID_ARG, "records inconsistent with their tile counts");
+}
+
+// Checks the oldest deferred frame: with wait, blocks until it is done;
+// otherwise returns at once if it is still running (*retired = false).
+gs_status retire_oldest(gs_context *ctx, bool wait, cudaStream_t s, bool *retired) {
+    *retired = false;
+    if (ctx->ring_count == 0) return GS_OK;
+    const int i = ctx->ring_head;
+    const gs_context::Pending p = ctx->ring[i];
+    const cudaError_t e = wait ? cudaEventSynchronize(p.done) : cudaEventQuery(p.done);
+    if (e == cudaErrorNotReady) return GS_OK;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "deferred frame");
+    *retired = true;
+    ctx->ring_head = (i + 1) % gs_context::kRing;
+    --ctx->ring_count;
+    const unsigned long long *h = ctx->h_ring + 5 * i;
+    const unsigned long long K = h[0];
+    const uint32_t w = static_cast<uint32_t>(h[4]);
+    ctx->stats.n_visible = (int64_t)h[1];
+    ctx->stats.n_keys = (int64_t)K;
+    ctx->stats.n_tiles = p.n_tiles;
+    ctx->stats.key_bits = p.bits;
+    const bool overflow = (int64_t)K > p.cap;
+    if (overflow && p.seq == ctx->last_seq) ctx->have_last = false;
+    // The error word is sticky: frames enqueued before it was cleared see the
+    // bits of an earlier frame, which are reported once.
+    const bool fresh = p.seq >= ctx->clear_seq;
+    if ((overflow || w) && fresh) {
+        GS_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s));
+        ctx->clear_seq = ctx->next_seq;
+    }
+    if (K >= (1ull << 32) - 1)
+        return fail(ctx, GS_ERR_CAPACITY, "more than 2^32-2 (tile, Gaussian) pairs in one frame");
+    if (overflow) {
+        ctx->key_capacity = std::max<int64_t>(ctx->key_capacity, (int64_t)(K + K / 4 + 1024));
+        return fail(ctx, GS_ERR_CAPACITY,
+                    "a deferred frame needed " + std::to_string(K) + " key pairs but the buffers held " +
+                        std::to_string(p.cap) + "; its image is incomplete. The buffers have grown: render it again");
+    }
+    if (w && fresh) {
+        if (w & gs::kErrTimeout)
+            return fail(ctx, GS_ERR_TIMEOUT, "a device-side wait gave up (look-back timeout)");
+        if (w & gs::kErrCapacity) return fail(ctx, GS_ERR_CAPACITY, "a device buffer was too small");
+        return fail(ctx, GS_ERR_INVALID_ARG, "records inconsistent with their tile counts");
+    }
+    return GS_OK;
+}
+
+// Checks deferred frames, oldest first: all of them (waiting) or those that
+// are done. Stops at the first error.
+gs_status drain_deferred(gs_context *ctx, bool wait, cudaStream_t s) {
+    while (ctx->ring_count > 0) {
+        bool retired = false;
+        const gs_status st = retire_oldest(ctx, wait, s, &retired);
+        if (st != GS_OK) return st;
+        if (!retired) break;
+    }
+    return GS_OK;
 }
 
 enum { EV_START, EV_PROJECT, EV_SCAN, EV_EMIT0, EV_EMIT, EV_SORT, EV_RANGES, EV_BLEND, EV_COUNT };
@@ -299,10 +374,18 @@ gs_status gs_create(gs_context **out, int device) {
         cudaMalloc(&ctx->d_counts, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_counts, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ring, 5 * gs_context::kRing * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
         (void)cudaGetLastError();
         gs_destroy(ctx);
         return GS_ERR_CUDA;
+    }
+    for (auto &p : ctx->ring) {
+        if (cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            gs_destroy(ctx);
+            return GS_ERR_CUDA;
+        }
     }
     *out = ctx;
     return GS_OK;
@@ -320,6 +403,10 @@ void gs_destroy(gs_context *ctx) {
     if (ctx->d_counts) cudaFree(ctx->d_counts);
     if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    if (ctx->ring_count > 0) cudaDeviceSynchronize();  // frames in flight still write h_ring
+    if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+    for (auto &p : ctx->ring)
+        if (p.done) cudaEventDestroy(p.done);
     for (int i = 0; i < EV_COUNT; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     auto &B = ctx->batch;
@@ -339,7 +426,10 @@ gs_status gs_sync_status(gs_context *ctx, void *stream) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GS_CUDA(ctx, cudaGetLastError());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess && e != cudaErrorNotReady) return cuda_fail(ctx, e, "pending CUDA error");
+    gs_status st = drain_deferred(ctx, true, s);
+    if (st != GS_OK) return st;
     return collect_device_error(ctx, s);
 }
 
@@ -467,6 +557,14 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK ||
         (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n), "scan scratch")) != GS_OK)
         return st;
+    const bool deferred = opts->sync_mode == GS_SYNC_DEFERRED;
+    // Earlier deferred frames: all of them before a synchronised frame, the
+    // finished ones otherwise (and the oldest if the ring is full).
+    if ((st = drain_deferred(ctx, !deferred, s)) != GS_OK) return st;
+    if (deferred && ctx->ring_count == gs_context::kRing) {
+        bool retired = false;
+        if ((st = retire_oldest(ctx, true, s, &retired)) != GS_OK) return st;
+    }
     if (ctx->key_capacity == 0) ctx->key_capacity = std::max<int64_t>(int64_t(1) << 20, 4 * n);
     gs_record *rec = static_cast<gs_record *>(ctx->records.ptr);
     uint32_t *ranges = static_cast<uint32_t *>(ctx->ranges.ptr);
@@ -510,6 +608,32 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         GS_CUDA(ctx, gs_launch_blend(reader(ctx, rec, dtype), sv, ranges, grid, cam->width, cam->height,
                                      opts->bg, *fb, opts->blend_variant, s));
         mark(ctx, EV_BLEND, s);
+        if (deferred) {
+            const int slot = (ctx->ring_head + ctx->ring_count) % gs_context::kRing;
+            unsigned long long *h = ctx->h_ring + 5 * slot;
+            h[4] = 0;
+            GS_CUDA(ctx, cudaMemcpyAsync(h, ctx->d_counts, 4 * sizeof(unsigned long long),
+                                         cudaMemcpyDeviceToHost, s));
+            GS_CUDA(ctx, cudaMemcpyAsync(h + 4, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            gs_context::Pending &p = ctx->ring[slot];
+            GS_CUDA(ctx, cudaEventRecord(p.done, s));
+            p.seq = ctx->next_seq++;
+            p.cap = cap;
+            p.n_tiles = n_tiles;
+            p.bits = bits;
+            ++ctx->ring_count;
+            if (ctx->timing) ctx->timed_once = true;
+            ctx->have_last = true;
+            ctx->last_seq = p.seq;
+            ctx->last_n = n;
+            ctx->last_w = cam->width;
+            ctx->last_h = cam->height;
+            ctx->last_tw = grid.tile_w;
+            ctx->last_th = grid.tile_h;
+            ctx->last_values = sv;
+            ctx->last_dtype = dtype;
+            return GS_OK;
+        }
         GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 4 * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, s));
         GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -530,6 +654,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         }
         if (ctx->timing) ctx->timed_once = true;
         ctx->have_last = true;
+        ctx->last_seq = 0;
         ctx->last_n = n;
         ctx->last_w = cam->width;
         ctx->last_h = cam->height;
@@ -559,11 +684,16 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
         return fail(ctx, GS_ERR_INVALID_ARG, "final_T, n_contrib, d_rgb and the gradient struct are required");
     if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
         return fail(ctx, GS_ERR_INVALID_ARG, "a gradient array is NULL");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // A deferred forward frame must have fitted its key buffers.
+    while (ctx->last_seq != 0 && ctx->ring_count > 0 && ctx->ring[ctx->ring_head].seq <= ctx->last_seq) {
+        bool retired = false;
+        if ((st = retire_oldest(ctx, true, s, &retired)) != GS_OK) return st;
+    }
     if (!ctx->have_last || ctx->last_n != g->n || ctx->last_w != cam->width || ctx->last_h != cam->height ||
         ctx->last_tw != opts->tile_w || ctx->last_th != opts->tile_h || ctx->last_dtype != opts->record_dtype)
         return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward must follow gs_render of the same scene and camera");
-    DeviceGuard dg(ctx->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const GsGrid grid = make_grid(cam, opts);
     const int64_t n = g->n;
     if ((st = ensure(ctx, ctx->d_rec, (size_t)(n > 0 ? n : 1) * 9 * sizeof(float), "record gradients")) != GS_OK)
@@ -847,10 +977,12 @@ gs_status gs_last_stage_times(gs_context *ctx, gs_stage_times *out) {
     return GS_OK;
 }
 
-gs_status gs_last_render_stats(const gs_context *ctx, gs_render_stats *out) {
+gs_status gs_last_render_stats(gs_context *ctx, gs_render_stats *out) {
     if (!ctx || !out) return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    const gs_status st = drain_deferred(ctx, true, nullptr);
     *out = ctx->stats;
-    return GS_OK;
+    return st;
 }
 
 }  // extern "C"
