@@ -768,11 +768,22 @@ __device__ __forceinline__ float3 sh_colour_bwd(const float *__restrict__ src, f
     return gd;
 }
 
+// Shared-memory rows of one block's gradients: the SH row is padded to an
+// odd length so that the per-thread writes hit distinct banks.
 template <int DEG>
-__global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs B) {
+struct BwdSmem {
+    static constexpr int kS = (DEG + 1) * (DEG + 1) * 3;
+    static constexpr int kSP = kS | 1;
+    static constexpr size_t bytes = (size_t)256 * (kSP + 11) * sizeof(float);
+};
+
+// One thread per Gaussian computes its gradients into shared memory; the
+// block then writes its contiguous output ranges with coalesced stores
+// (Gaussians that received no gradient get zeros).
+template <int DEG>
+__device__ __forceinline__ void project_bwd_one(const ProjectBwdArgs &B, int64_t i, float *dsh, float *gm_out,
+                                                float *gls_out, float *gq_out, float *go_out) {
     constexpr int kK = (DEG + 1) * (DEG + 1);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B.P.n) return;
     const ProjectArgs &P = B.P;
     const GsCameraDev &K = P.cam;
     float gr9[9];
@@ -781,12 +792,11 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs B
         gr9[f] = B.d_rec[9 * i + f];
         any |= gr9[f] != 0.f;
     }
-    float *dsh = B.d_sh + (size_t)i * kK * 3;
     if (!any) {
-        for (int a = 0; a < 3; ++a) B.d_means[3 * i + a] = 0.f;
-        for (int a = 0; a < 3; ++a) B.d_log_scales[3 * i + a] = 0.f;
-        for (int a = 0; a < 4; ++a) B.d_quats[4 * i + a] = 0.f;
-        B.d_logits[i] = 0.f;
+        for (int a = 0; a < 3; ++a) gm_out[a] = 0.f;
+        for (int a = 0; a < 3; ++a) gls_out[a] = 0.f;
+        for (int a = 0; a < 4; ++a) gq_out[a] = 0.f;
+        *go_out = 0.f;
         for (int a = 0; a < kK * 3; ++a) dsh[a] = 0.f;
         return;
     }
@@ -896,15 +906,52 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs B
     gm[1] += (gd.y - dy * ddot) / vn;
     gm[2] += (gd.z - dz * ddot) / vn;
 
-    for (int k = 0; k < 3; ++k) B.d_means[3 * i + k] = gm[k];
-    for (int k = 0; k < 3; ++k) B.d_log_scales[3 * i + k] = gls[k];
-    B.d_quats[4 * i + 0] = (gqw - qw * qdot) / qn;
-    B.d_quats[4 * i + 1] = (gqx - qx * qdot) / qn;
-    B.d_quats[4 * i + 2] = (gqy - qy * qdot) / qn;
-    B.d_quats[4 * i + 3] = (gqz - qz * qdot) / qn;
-    B.d_logits[i] = go * o * (1.f - o);
+    for (int k = 0; k < 3; ++k) gm_out[k] = gm[k];
+    for (int k = 0; k < 3; ++k) gls_out[k] = gls[k];
+    gq_out[0] = (gqw - qw * qdot) / qn;
+    gq_out[1] = (gqx - qx * qdot) / qn;
+    gq_out[2] = (gqy - qy * qdot) / qn;
+    gq_out[3] = (gqz - qz * qdot) / qn;
+    *go_out = go * o * (1.f - o);
 }
 
+template <int DEG>
+__global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs B) {
+    using L = BwdSmem<DEG>;
+    extern __shared__ float smem[];
+    float *s_sh = smem;                  // 256 x kSP
+    float *s_m = s_sh + 256 * L::kSP;    // 256 x 3
+    float *s_l = s_m + 256 * 3;          // 256 x 3
+    float *s_q = s_l + 256 * 3;          // 256 x 4
+    float *s_o = s_q + 256 * 4;          // 256
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * 256;
+    const int64_t i = base + t;
+    if (i < B.P.n) project_bwd_one<DEG>(B, i, s_sh + t * L::kSP, s_m + 3 * t, s_l + 3 * t, s_q + 4 * t, s_o + t);
+    __syncthreads();
+    const int cnt = (int)(B.P.n - base < 256 ? B.P.n - base : 256);
+    float *dsh = B.d_sh + base * L::kS;
+    for (int idx = t; idx < cnt * L::kS; idx += 256) dsh[idx] = s_sh[(idx / L::kS) * L::kSP + idx % L::kS];
+    for (int idx = t; idx < cnt * 3; idx += 256) {
+        B.d_means[base * 3 + idx] = s_m[idx];
+        B.d_log_scales[base * 3 + idx] = s_l[idx];
+    }
+    for (int idx = t; idx < cnt * 4; idx += 256) B.d_quats[base * 4 + idx] = s_q[idx];
+    if (t < cnt) B.d_logits[base + t] = s_o[t];
+}
+
+}  // namespace
+
+namespace {
+template <int DEG>
+cudaError_t launch_project_bwd(const ProjectBwdArgs &B, unsigned blocks, cudaStream_t s) {
+    const size_t smem = BwdSmem<DEG>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    project_bwd_kernel<DEG><<<blocks, 256, smem, s>>>(B);
+    return cudaGetLastError();
+}
 }  // namespace
 
 cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
@@ -921,12 +968,11 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
     B.d_sh = out.d_sh;
     const unsigned blocks = (unsigned)((g.n + 255) / 256);
     switch (g.sh_degree) {
-        case 0: project_bwd_kernel<0><<<blocks, 256, 0, s>>>(B); break;
-        case 1: project_bwd_kernel<1><<<blocks, 256, 0, s>>>(B); break;
-        case 2: project_bwd_kernel<2><<<blocks, 256, 0, s>>>(B); break;
-        default: project_bwd_kernel<3><<<blocks, 256, 0, s>>>(B); break;
+        case 0: return launch_project_bwd<0>(B, blocks, s);
+        case 1: return launch_project_bwd<1>(B, blocks, s);
+        case 2: return launch_project_bwd<2>(B, blocks, s);
+        default: return launch_project_bwd<3>(B, blocks, s);
     }
-    return cudaGetLastError();
 }
 
 size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity) {
