@@ -336,14 +336,14 @@ gs_status gs_last_render_stats(gs_context *ctx, gs_render_stats *out);
 /* Per-stage device times of gs_render, measured with CUDA events recorded on
  * the render stream between the stages (tracing; off by default). */
 typedef struct {
-    float project_ms; /* gs_project kernel                                      */
-    float scan_ms;    /* tile-count scan                                        */
-    float host_ms;    /* gap while the host reads K and sizes the key buffers   */
-    float emit_ms;    /* key emission                                           */
-    float sort_ms;    /* histogram + digit passes                               */
-    float ranges_ms;  /* per-tile ranges                                        */
-    float blend_ms;   /* gs_blend kernel                                        */
-    float total_ms;   /* first event to last                                    */
+    float project_ms;     /* projection + compact list of visible Gaussians     */
+    float depth_sort_ms;  /* depth sort of the compact list                     */
+    float entry_scan_ms;  /* scan of the tile counts in depth order             */
+    float emit_ms;        /* key emission                                       */
+    float tile_sort_ms;   /* tile-digit passes of the key sort                  */
+    float ranges_ms;      /* per-tile ranges                                    */
+    float blend_ms;       /* gs_blend kernel                                    */
+    float total_ms;       /* first event to last                                */
 } gs_stage_times;
 /* enable != 0 turns per-stage events on for later gs_render calls. */
 gs_status gs_set_stage_timing(gs_context *ctx, int enable);

@@ -76,8 +76,8 @@ class gs_render_stats(ctypes.Structure):
 
 
 class gs_stage_times(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_float) for n in ("project_ms", "scan_ms", "host_ms", "emit_ms",
-                                              "sort_ms", "ranges_ms", "blend_ms", "total_ms")]
+    _fields_ = [(n, ctypes.c_float) for n in ("project_ms", "depth_sort_ms", "entry_scan_ms", "emit_ms",
+                                              "tile_sort_ms", "ranges_ms", "blend_ms", "total_ms")]
 
 
 assert ctypes.sizeof(gs_record) == 48

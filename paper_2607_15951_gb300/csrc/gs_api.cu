@@ -261,7 +261,7 @@ gs_status drain_deferred(gs_context *ctx, bool wait, cudaStream_t s) {
     return GS_OK;
 }
 
-enum { EV_START, EV_PROJECT, EV_SCAN, EV_EMIT0, EV_EMIT, EV_SORT, EV_RANGES, EV_BLEND, EV_COUNT };
+enum { EV_START, EV_PROJECT, EV_DEPTH, EV_SCAN, EV_EMIT, EV_SORT, EV_RANGES, EV_BLEND, EV_COUNT };
 
 void mark(gs_context *ctx, int which, cudaStream_t s) {
     if (ctx->timing) cudaEventRecord(ctx->ev[which], s);
@@ -300,7 +300,6 @@ gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *ti
         return st;
     GS_CUDA(ctx, gs_launch_scan(tiles, n, static_cast<unsigned long long *>(ctx->offsets.ptr),
                                 ctx->d_counts, ctx->scan_scratch.ptr, ctx->d_err, s));
-    mark(ctx, EV_SCAN, s);
     GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 2 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, s));
     if ((st = collect_device_error(ctx, s)) != GS_OK) return st;
@@ -334,17 +333,13 @@ gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *ti
     uint32_t *ev = odd ? static_cast<uint32_t *>(ctx->alt_values.ptr) : values;
     uint64_t *ok = odd ? keys : static_cast<uint64_t *>(ctx->alt_keys.ptr);
     uint32_t *ov = odd ? values : static_cast<uint32_t *>(ctx->alt_values.ptr);
-    mark(ctx, EV_EMIT0, s);
     GS_CUDA(ctx, gs_launch_emit(records, tiles, static_cast<unsigned long long *>(ctx->offsets.ptr), n,
                                 grid, ek, ev, (int64_t)K, ctx->d_err, s));
-    mark(ctx, EV_EMIT, s);
     bool in_alt = false;
     GS_CUDA(ctx, gs_launch_sort(ek, ev, ok, ov, (int64_t)K, bits, ctx->sort_scratch.ptr, ctx->d_err,
                                 &in_alt, s));
-    mark(ctx, EV_SORT, s);
     (void)capacity;
     GS_CUDA(ctx, gs_launch_ranges(keys, (int64_t)K, n_tiles, ranges, ctx->d_err, s));
-    mark(ctx, EV_RANGES, s);
     return GS_OK;
 }
 
@@ -547,6 +542,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     const int64_t n = g->n;
     const int n_tiles = grid.tiles_x * grid.tiles_y;
     const int bits = key_bits_for(n_tiles);
+    const int tile_passes = (bits - 32 + 7) / 8;
     const int dtype = opts->record_dtype;
     if (dtype != GS_RECORD_F32 &&
         ((st = ensure(ctx, ctx->lp_geo, (size_t)(n > 0 ? n : 1) * 16, "reduced-precision records")) != GS_OK ||
@@ -554,8 +550,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
          (st = ensure(ctx, ctx->lp_gb, (size_t)(n > 0 ? n : 1) * 4, "reduced-precision records")) != GS_OK))
         return st;
     if ((st = ensure(ctx, ctx->records, (size_t)(n > 0 ? n : 1) * sizeof(gs_record), "records")) != GS_OK ||
-        (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK ||
-        (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n), "scan scratch")) != GS_OK)
+        (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK)
         return st;
     const bool deferred = opts->sync_mode == GS_SYNC_DEFERRED;
     // Earlier deferred frames: all of them before a synchronised frame, the
@@ -577,25 +572,30 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             (st = ensure(ctx, ctx->values, (size_t)cap * 4, "values")) != GS_OK ||
             (st = ensure(ctx, ctx->alt_keys, (size_t)cap * 8, "alt keys")) != GS_OK ||
             (st = ensure(ctx, ctx->alt_values, (size_t)cap * 4, "alt values")) != GS_OK ||
-            (st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes(cap, bits), "sort scratch")) != GS_OK ||
-            (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n) + gs_key_block_bytes(cap),
-                         "front-end scratch")) != GS_OK)
+            (st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes_digits(cap, tile_passes), "sort scratch")) !=
+                GS_OK ||
+            (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n, cap), "front-end scratch")) != GS_OK)
             return st;
         uint64_t *keys = static_cast<uint64_t *>(ctx->keys.ptr);
         uint32_t *vals = static_cast<uint32_t *>(ctx->values.ptr);
         uint64_t *akeys = static_cast<uint64_t *>(ctx->alt_keys.ptr);
         uint32_t *avals = static_cast<uint32_t *>(ctx->alt_values.ptr);
-        GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes(cap, bits), s));
-        const GsSortScratch sc = gs_sort_carve(ctx->sort_scratch.ptr, cap, bits);
+        // The tile sort: keys arrive in depth order, so only the tile digits
+        // (digits 4.. of the key) are sorted.
+        GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes_digits(cap, tile_passes), s));
+        const GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, cap, 4, tile_passes);
         mark(ctx, EV_START, s);
+        cudaEvent_t ev3[3] = {nullptr, nullptr, nullptr};
+        if (ctx->timing) {
+            ev3[0] = ctx->ev[EV_PROJECT];
+            ev3[1] = ctx->ev[EV_DEPTH];
+            ev3[2] = ctx->ev[EV_SCAN];
+        }
         GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, static_cast<float4 *>(ctx->lp_geo.ptr),
                                            static_cast<uint2 *>(ctx->lp_oq.ptr),
                                            static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype, keys, vals, cap,
                                            ctx->d_counts,
-                                           ctx->fused_scratch.ptr, sc, ctx->d_err, s));
-        mark(ctx, EV_PROJECT, s);
-        mark(ctx, EV_SCAN, s);
-        mark(ctx, EV_EMIT0, s);
+                                           ctx->fused_scratch.ptr, sc, ctx->d_err, s, ev3));
         mark(ctx, EV_EMIT, s);
         bool in_alt = false;
         GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, cap, ctx->d_counts + 2, sc, ctx->d_err,
@@ -967,10 +967,10 @@ gs_status gs_last_stage_times(gs_context *ctx, gs_stage_times *out) {
         return ms;
     };
     out->project_ms = el(EV_START, EV_PROJECT);
-    out->scan_ms = el(EV_PROJECT, EV_SCAN);
-    out->host_ms = el(EV_SCAN, EV_EMIT0);
-    out->emit_ms = el(EV_EMIT0, EV_EMIT);
-    out->sort_ms = el(EV_EMIT, EV_SORT);
+    out->depth_sort_ms = el(EV_PROJECT, EV_DEPTH);
+    out->entry_scan_ms = el(EV_DEPTH, EV_SCAN);
+    out->emit_ms = el(EV_SCAN, EV_EMIT);
+    out->tile_sort_ms = el(EV_EMIT, EV_SORT);
     out->ranges_ms = el(EV_SORT, EV_RANGES);
     out->blend_ms = el(EV_RANGES, EV_BLEND);
     out->total_ms = el(EV_START, EV_BLEND);

@@ -246,6 +246,7 @@ cudaError_t gs_launch_ranges_dev(const uint64_t *keys, uint32_t *values, int64_t
     cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess || n_capacity == 0) return e;
     const unsigned blocks = (unsigned)((n_capacity + 255) / 256);
+    gs_carveout(ranges_kernel);
     ranges_kernel<<<blocks, 256, 0, s>>>(keys, n_capacity, d_n, n_tiles, ranges, values, 1, nullptr, d_err);
     return cudaGetLastError();
 }

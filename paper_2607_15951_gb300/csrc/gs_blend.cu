@@ -316,6 +316,7 @@ cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, cons
         else if (tw == 16 && th == 8) blend_basic_kernel<16, 8><<<blocks, 128, 0, s>>>(a);
         else blend_basic_kernel<8, 8><<<blocks, 64, 0, s>>>(a);
     } else {
+        if (tw == 16 && th == 16) gs_carveout(blend_culled_kernel<16, 16>);
         if (tw == 16 && th == 16) blend_culled_kernel<16, 16><<<blocks, 128, 0, s>>>(a);
         else if (tw == 16 && th == 8) blend_culled_kernel<16, 8><<<blocks, 64, 0, s>>>(a);
         else blend_culled_kernel<8, 8><<<blocks, 32, 0, s>>>(a);

@@ -8,6 +8,18 @@
 
 #include "../../include/gs.h"
 
+// Shared-memory carveout preference for the kernels of the render path
+// (-1: leave the driver's choice).
+#ifndef GS_CARVEOUT
+#define GS_CARVEOUT -1
+#endif
+template <class F>
+inline void gs_carveout(F *kernel) {
+    if (GS_CARVEOUT >= 0)
+        cudaFuncSetAttribute(reinterpret_cast<const void *>(kernel), cudaFuncAttributePreferredSharedMemoryCarveout,
+                             GS_CARVEOUT);
+}
+
 namespace gs {
 
 // Constants of the standard 3DGS formulation (the paper cites it for Eq. 1
@@ -71,14 +83,21 @@ __device__ __forceinline__ unsigned long long warp_lookback(const unsigned long 
     const int lane = threadIdx.x & 31;
     unsigned long long excl = 0;
     long long q = p - 1;
-    const unsigned long long t0 = global_ns();
+    // The clock starts at the first unpublished read and is checked every
+    // 16th poll, so a look-back that finds its prefix at once reads no timer.
+    unsigned long long t0 = 0;
+    uint32_t polls = 0;
     *timed_out = false;
     while (true) {
         const long long idx = q - lane;
         const unsigned long long s = idx >= 0 ? ld_relaxed_u64(status + idx) : kFlagIncl;
         if (!__all_sync(0xffffffffu, (s >> 62) != 0)) {
-            const bool give_up = (global_ns() - t0 > timeout_ns) ||
-                                 (ld_relaxed_u32(d_err) & kErrTimeout);
+            bool give_up = false;
+            if ((polls++ & 15u) == 0u) {
+                const unsigned long long now = global_ns();
+                if (polls == 1) t0 = now;
+                give_up = (now - t0 > timeout_ns) || (ld_relaxed_u32(d_err) & kErrTimeout);
+            }
             if (__any_sync(0xffffffffu, give_up)) {
                 if (lane == 0) atomicOr(d_err, kErrTimeout);
                 *timed_out = true;
@@ -279,9 +298,17 @@ struct GsSortScratch {
     unsigned long long *status;  // passes x parts x 256
     int passes;
     int64_t parts;     // partitions of the capacity the passes are launched for
+    int digit0;        // pass p sorts the 8-bit digit digit0 + p of the key
+    int items;         // pairs per thread of a partition (256 threads): 8 or GS_SORT_ITEMS
 };
 size_t gs_sort_scratch_bytes(int64_t n, int key_bits);
 GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits);
+// Scratch for `passes` digit passes starting at digit `digit0`, with
+// partitions of 256 x items pairs (items 8 suits short lists: shorter
+// per-partition latency).
+size_t gs_sort_scratch_bytes_digits(int64_t n, int passes, int items = GS_SORT_ITEMS);
+GsSortScratch gs_sort_carve_digits(void *base, int64_t n_capacity, int digit0, int passes,
+                                   int items = GS_SORT_ITEMS);
 int gs_sort_passes(int key_bits);
 // Sorts (keys, values) using (alt_keys, alt_values) as the ping-pong pair;
 // *result_in_alt tells which pair holds the result. Zeroes the scratch and
@@ -301,20 +328,27 @@ cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, cons
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s);
 
-// Per-frame binning front end (two kernels): projection of every Gaussian with
-// key-slot reservation per block, then emission of the (tile, depth) keys of
-// the visible Gaussians with the digit histograms + bucket offsets of the sort.
+// Per-frame binning front end, depth first: (1) projection of every Gaussian,
+// appending each visible one to a compact list as (tiles << 32 | depth bits,
+// index) with the depth digit histograms; (2) a stable radix sort of that list
+// by depth (4 digit passes over the visible Gaussians only); (3) a scan of the
+// tile counts in depth order giving each entry its first key slot; (4)
+// emission of the (tile, depth) keys in depth order with the tile digit
+// histograms + bucket offsets of the tile sort `sc` (carved with digit0 = 4),
+// which then needs only the tile digits because it is stable.
 // counts[0] = K, counts[1] = visible Gaussians, counts[2] = K if it fits in
-// `capacity` else 0 (the sort and ranges then see an empty list and the
-// overflow bit is set in d_err). `scan_scratch`: gs_fused_scratch_bytes(n).
-size_t gs_fused_scratch_bytes(int64_t n);    // + gs_key_block_bytes(capacity)
+// `capacity` else 0 (the tile sort and ranges then see an empty list and the
+// overflow bit is set in d_err), counts[3] = visible Gaussians (the depth
+// sort's count). `scan_scratch`: gs_fused_scratch_bytes(n, capacity).
+size_t gs_fused_scratch_bytes(int64_t n, int64_t capacity);
 size_t gs_key_block_bytes(int64_t capacity);
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
                                   int lp_dtype,
                                   uint64_t *keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
-                                  const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s);
+                                  const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
+                                  const cudaEvent_t *marks = nullptr /* 3 events or null */);
 
 // Backward kernels.
 cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,

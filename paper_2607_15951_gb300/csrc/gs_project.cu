@@ -207,50 +207,61 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs P) {
 }
 
 // ---------------------------------------------------------------------------
-// Front end of a frame, two kernels:
-//  P. project_reserve_kernel: one thread per Gaussian projects it, writes the
-//     record of a visible one, and every block reserves, with one atomicAdd
-//     on a packed 64-bit counter (visible count << 33 | key count), a range of
-//     key slots and a range of entries of a compact list of visible
-//     Gaussians (index, first key slot).
+// Front end of a frame, depth first:
+//  P. project_list_kernel: one thread per Gaussian projects it and writes the
+//     record of a visible one; every block reserves, with one atomicAdd on a
+//     packed 64-bit counter (visible count << 33 | key count), a range of a
+//     compact list of the visible Gaussians (tiles << 32 | depth bits, index)
+//     and counts the four depth digits. The last block turns the counts into
+//     the depth sort's bucket offsets.
+//  D. the depth sort: four onesweep digit passes over the compact list.
+//  S. entry_scan_kernel: exclusive scan of the tile counts in depth order
+//     (decoupled look-back) giving each entry its first key slot, and the
+//     entry that covers the first slot of every key block.
 //  E. emit_keys_kernel: threads own runs of eight key slots, find their
-//     Gaussians in the compact list (whose first slots ascend) and write the
-//     keys — balanced however large a single splat is — while counting
-//     the tile digits of the sort (kernel P counts the depth digits, once per
-//     Gaussian). The last block turns the counts into bucket offsets and
-//     publishes the key count the sort should use.
-// The slot order depends on scheduling; the sort orders keys by (tile,
-// depth) and the ranges kernel then puts each run of equal keys in Gaussian
-// index order, so the final lists are exactly ordered by (tile, depth bits,
-// index).
+//     entries (whose first slots ascend) and write the keys — balanced
+//     however large a single splat is — while counting the tile digits. The
+//     last block turns the counts into the tile sort's bucket offsets and
+//     publishes the key count it should use.
+// The keys are emitted in depth order, so the stable sort on the tile digits
+// alone leaves them ordered by (tile, depth). Entries of equal depth keep the
+// compact list's order, which depends on scheduling; the ranges kernel puts
+// each run of equal keys in Gaussian index order, so the final lists are
+// exactly ordered by (tile, depth bits, index).
 // ---------------------------------------------------------------------------
-constexpr int kMaxPasses = 8;
+constexpr int kMaxPasses = 8;                  // batched path: depth and tile digits
+constexpr int kMaxTilePasses = 4;
 constexpr unsigned long long kKeyMask = (1ull << 33) - 1;
 constexpr int kKeyBlockLog2 = 11;              // key slots per emission block: 2048
 constexpr int kKeyBlock = 1 << kKeyBlockLog2;
 constexpr int kKeysPerThread = kKeyBlock / 256;
+constexpr int kDepthPasses = 4;                // the depth bits are the low word of a list key
+constexpr int kDepthItems = 8;                 // short list: smaller sort partitions, shorter latency
+constexpr int kEntryItems = 8;                 // list entries per thread of the entry scan
+constexpr int kEntryTile = 256 * kEntryItems;
 
-struct ReserveArgs {
+struct ListArgs {
     ProjectArgs P;
     float4 *lp_geo;              // optional reduced-precision blend records
     uint2 *lp_oq;
     uint32_t *lp_gb;
     int lp_dtype;
     unsigned long long *packed;  // visible << 33 | keys
-    uint32_t *list_idx;          // n: Gaussian index of visible entry j
-    uint32_t *list_off;          // n: its first key slot (ascending in j)
-    uint32_t *hist;              // sort digit counts (passes x 256); depth digits added here
-    uint32_t *block_entry;       // per 256-slot block of keys: the entry covering its first slot
-    int64_t n_key_blocks;        // ceil(capacity / 256)
+    uint64_t *lkeys;             // n: tiles << 32 | depth bits of visible entry j
+    uint32_t *lvals;             // n: its Gaussian index
+    GsSortScratch dsc;           // the depth sort's histograms, bucket offsets, ticket
+    unsigned long long *counts;  // [3] <- visible count (the depth sort's count)
 };
 
 template <int DEG>
-__global__ void __launch_bounds__(256) project_reserve_kernel(const ReserveArgs A) {
+__global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
     __shared__ uint32_t s_t[8], s_v[8];
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_hist[4 * 256];
+    __shared__ uint32_t s_hist[kDepthPasses * 256];
+    __shared__ uint32_t s_tmp[8];
+    __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int k = tid; k < 4 * 256; k += 256) s_hist[k] = 0;
+    for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
     const int64_t i = (int64_t)blockIdx.x * 256 + tid;
     Projected pr;
     pr.tiles = 0;
@@ -275,46 +286,125 @@ __global__ void __launch_bounds__(256) project_reserve_kernel(const ReserveArgs 
     }
     if (lane == 31) { s_t[warp] = it; s_v[warp] = iv; }
     __syncthreads();
-    uint32_t pt = 0, pv = 0, bt = 0, bv = 0;
+    uint32_t pv = 0, bt = 0, bv = 0;
     for (int w = 0; w < 8; ++w) {
-        if (w < warp) { pt += s_t[w]; pv += s_v[w]; }
+        if (w < warp) pv += s_v[w];
         bt += s_t[w];
         bv += s_v[w];
     }
     if (tid == 0) s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) : 0ull;
     __syncthreads();
     if (v) {
-        const unsigned long long base = s_base;
-        const uint64_t j = (base >> 33) + pv + iv - 1;
-        const uint64_t off = (base & kKeyMask) + pt + it - t;
-        A.list_idx[j] = (uint32_t)i;
-        A.list_off[j] = (uint32_t)off;
-        // Key blocks whose first slot falls in [off, off + t) start in entry j.
-        const int64_t b1 = min((int64_t)((off + t - 1) >> kKeyBlockLog2), A.n_key_blocks - 1);
-        for (int64_t b = (int64_t)((off + kKeyBlock - 1) >> kKeyBlockLog2); b <= b1; ++b)
-            A.block_entry[b] = (uint32_t)j;
-        // The four depth digits are shared by all t keys of this Gaussian.
+        const uint64_t j = (s_base >> 33) + pv + iv - 1;
         const uint32_t dbits = __float_as_uint(pr.r2.y);
-        for (int d = 0; d < 4; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], t);
+        A.lkeys[j] = ((uint64_t)t << 32) | dbits;
+        A.lvals[j] = (uint32_t)i;
+        for (int d = 0; d < kDepthPasses; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
     }
     __syncthreads();
     if (bv)
-        for (int k = tid; k < 4 * 256; k += 256)
-            if (s_hist[k]) atomicAdd(&A.hist[k], s_hist[k]);
+        for (int k = tid; k < kDepthPasses * 256; k += 256)
+            if (s_hist[k]) atomicAdd(&A.dsc.hist[k], s_hist[k]);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    // Last block: every block's counts and list entries are in.
+    __threadfence();
+    for (int d = 0; d < kDepthPasses; ++d) {
+        const uint32_t c = __ldcg(&A.dsc.hist[d * 256 + tid]);
+        A.dsc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
+    }
+    if (tid == 0) A.counts[3] = __ldcg(A.packed) >> 33;
+}
+
+struct EntryScanArgs {
+    const uint64_t *lkeys;             // depth-sorted list keys (tile count in the high word)
+    const unsigned long long *packed;  // visible << 33 | keys
+    uint32_t *off;                     // out: first key slot of entry j
+    uint32_t *block_entry;             // out: entry covering the first slot of each key block
+    int64_t n_key_blocks;              // ceil(capacity / kKeyBlock)
+    uint32_t *counter;                 // partition counter (zeroed)
+    unsigned long long *status;        // one look-back word per partition (zeroed)
+    uint32_t *d_err;
+};
+
+// Exclusive scan of the tile counts of the depth-sorted entries. Blocks take
+// partitions of kEntryTile entries in launch order and resolve their prefix
+// by decoupled look-back (bounded waits); partitions past the visible count
+// return at once (no partition waits on a later one).
+__global__ void __launch_bounds__(256) entry_scan_kernel(const EntryScanArgs A) {
+    __shared__ uint32_t s_part;
+    __shared__ unsigned long long s_warp[8];
+    __shared__ unsigned long long s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_part = atomicAdd(A.counter, 1u);
+    __syncthreads();
+    const int64_t p = s_part;
+    const int64_t nv = (int64_t)(*A.packed >> 33);
+    if (p * kEntryTile >= nv) return;
+    const int64_t base = p * kEntryTile + (int64_t)tid * kEntryItems;
+    uint32_t t[kEntryItems];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < kEntryItems; ++j) {
+        const int64_t idx = base + j;
+        t[j] = idx < nv ? (uint32_t)(A.lkeys[idx] >> 32) : 0u;
+        sum += t[j];
+    }
+    unsigned long long incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    unsigned long long warp_prefix = 0, block_total = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < warp) warp_prefix += s_warp[w];
+        block_total += s_warp[w];
+    }
+    if (warp == 0) {
+        unsigned long long prefix = 0;
+        if (p == 0) {
+            if (lane == 0) st_relaxed_u64(A.status, kFlagIncl | block_total);
+        } else {
+            if (lane == 0) st_relaxed_u64(A.status + p, kFlagAgg | block_total);
+            bool to;
+            prefix = warp_lookback(A.status, p, A.d_err, &to);
+            if (lane == 0) st_relaxed_u64(A.status + p, kFlagIncl | ((prefix + block_total) & kValueMask));
+        }
+        if (lane == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    unsigned long long run = s_prefix + warp_prefix + incl - sum;
+#pragma unroll
+    for (int j = 0; j < kEntryItems; ++j) {
+        const int64_t idx = base + j;
+        if (idx < nv) {
+            A.off[idx] = (uint32_t)run;
+            // Key blocks whose first slot falls in [run, run + t) start in this entry.
+            const int64_t b0 = (int64_t)((run + kKeyBlock - 1) >> kKeyBlockLog2);
+            const int64_t b1 = min((int64_t)((run + t[j] - 1) >> kKeyBlockLog2), A.n_key_blocks - 1);
+            for (int64_t b = b0; b <= b1; ++b) A.block_entry[b] = (uint32_t)idx;
+        }
+        run += t[j];
+    }
 }
 
 struct EmitArgs {
     const float4 *records;
     const unsigned long long *packed;
-    const uint32_t *list_idx;
-    const uint32_t *list_off;
+    const uint32_t *list_idx;     // Gaussian index of entry j (depth order)
+    const uint32_t *list_off;     // first key slot of entry j (ascending)
     const uint32_t *block_entry;
     GsGrid grid;
     uint64_t *keys;
     uint32_t *values;
     int64_t capacity;
     unsigned long long *counts;  // out: [0] K, [1] visible, [2] K if it fits else 0
-    GsSortScratch sc;
+    GsSortScratch sc;            // the tile sort (its digits are the tile id's)
     uint32_t *d_err;
 };
 
@@ -324,7 +414,7 @@ struct EmitArgs {
 // first slot by binary search and walks forward. Digit counts of a thread's
 // run of keys are merged before they are added to the block's histogram.
 __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
-    __shared__ uint32_t s_hist[kMaxPasses * 256];
+    __shared__ uint32_t s_hist[kMaxTilePasses * 256];
     __shared__ uint32_t s_off[kKeyBlock + 2], s_idx[kKeyBlock + 2];
     __shared__ uint32_t s_tmp[8];
     __shared__ int s_j0, s_cnt;
@@ -332,7 +422,7 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
     const int tid = threadIdx.x;
     const int passes = E.sc.passes;
     const GsGrid &G = E.grid;
-    for (int k = tid; k < kMaxPasses * 256; k += 256) s_hist[k] = 0;
+    for (int k = tid; k < kMaxTilePasses * 256; k += 256) s_hist[k] = 0;
     const unsigned long long packed = *E.packed;
     const int64_t K = (int64_t)(packed & kKeyMask);
     const int64_t nv = (int64_t)(packed >> 33);
@@ -360,8 +450,8 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
         }
         int e = -1;
         uint32_t g = 0, dbits = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0;
-        uint32_t run_digit[kMaxPasses], run_count[kMaxPasses];
-        for (int d = 0; d < kMaxPasses; ++d) { run_digit[d] = 0xffffffffu; run_count[d] = 0; }
+        uint32_t run_digit[kMaxTilePasses], run_count[kMaxTilePasses];
+        for (int d = 0; d < kMaxTilePasses; ++d) { run_digit[d] = 0xffffffffu; run_count[d] = 0; }
         for (int q = 0; q < kKeysPerThread; ++q) {
             const int64_t k = kb + q;
             if (k >= K) break;
@@ -386,8 +476,8 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
             const uint32_t tile = (y0 + qy) * (uint32_t)G.tiles_x + x0 + rx;
             E.keys[k] = ((uint64_t)tile << 32) | dbits;
             E.values[k] = g;
-            for (int d = 4; d < passes; ++d) {
-                const uint32_t dg = (tile >> (8 * (d - 4))) & 255u;
+            for (int d = 0; d < passes; ++d) {
+                const uint32_t dg = (tile >> (8 * d)) & 255u;
                 if (dg != run_digit[d]) {
                     if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
                     run_digit[d] = dg;
@@ -396,12 +486,12 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
                 ++run_count[d];
             }
         }
-        for (int d = 4; d < passes; ++d)
+        for (int d = 0; d < passes; ++d)
             if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
     }
     __syncthreads();
     if (active)
-        for (int q = tid + 4 * 256; q < passes * 256; q += 256)
+        for (int q = tid; q < passes * 256; q += 256)
             if (s_hist[q]) atomicAdd(&E.sc.hist[q], s_hist[q]);
     __threadfence();
     __syncthreads();
@@ -624,11 +714,45 @@ __global__ void __launch_bounds__(256) emit_keys_batch_kernel(const EmitBatchArg
 
 }  // namespace
 
-size_t gs_fused_scratch_bytes(int64_t n) {
-    // packed counter, then the compact list (index, first slot) of up to n
-    // entries; the per-key-block entry table follows (gs_key_block_bytes).
-    return 256 + 2 * (((size_t)(n > 0 ? n : 1) * 4 + 255) / 256 * 256);
+namespace {
+
+// Front-end scratch: the packed counter and the entry scan's partition
+// counter, the depth sort's scratch and the entry scan's status words (all
+// zeroed per frame), then the compact list, its sort buffers, the entries'
+// first slots and the key-block table.
+struct FrontLayout {
+    size_t dsort, scan_status, zero, lkeys, lvals, akeys, avals, off, block_entry, total;
+};
+
+FrontLayout front_layout(int64_t n, int64_t capacity) {
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const int64_t nn = n > 0 ? n : 1;
+    FrontLayout L;
+    size_t o = 256;
+    L.dsort = o;
+    o += al(gs_sort_scratch_bytes_digits(nn, kDepthPasses, kDepthItems));
+    L.scan_status = o;
+    o += al((size_t)((nn + kEntryTile - 1) / kEntryTile + 1) * 8);
+    L.zero = o;
+    L.lkeys = o;
+    o += al((size_t)nn * 8);
+    L.lvals = o;
+    o += al((size_t)nn * 4);
+    L.akeys = o;
+    o += al((size_t)nn * 8);
+    L.avals = o;
+    o += al((size_t)nn * 4);
+    L.off = o;
+    o += al((size_t)nn * 4);
+    L.block_entry = o;
+    o += al(gs_key_block_bytes(capacity));
+    L.total = o;
+    return L;
 }
+
+}  // namespace
+
+size_t gs_fused_scratch_bytes(int64_t n, int64_t capacity) { return front_layout(n, capacity).total; }
 
 size_t gs_key_block_bytes(int64_t capacity) {
     return ((size_t)(capacity + kKeyBlock - 1) / kKeyBlock + 1) * 4;
@@ -639,43 +763,68 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
                                   int lp_dtype,
                                   uint64_t *keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
-                                  const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s) {
-    // counts and the packed counter start at zero; the sort scratch was
-    // zeroed by the caller.
+                                  const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
+                                  const cudaEvent_t *marks) {
+    // counts and the front-end counters start at zero; the tile sort's
+    // scratch was zeroed by the caller.
     cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    const FrontLayout L = front_layout(g.n, capacity);
     char *base = static_cast<char *>(scan_scratch);
-    e = cudaMemsetAsync(base, 0, 256, s);
+    e = cudaMemsetAsync(base, 0, L.zero, s);
     if (e != cudaSuccess || g.n == 0) return e;
-    const size_t list_bytes = ((size_t)g.n * 4 + 255) / 256 * 256;
-    ReserveArgs A;
+    ListArgs A;
     A.P = ProjectArgs{g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.n, cam, grid,
                       reinterpret_cast<float4 *>(records), nullptr,
                       reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
                       reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
-    A.packed = reinterpret_cast<unsigned long long *>(base);
-    A.list_idx = reinterpret_cast<uint32_t *>(base + 256);
-    A.list_off = reinterpret_cast<uint32_t *>(base + 256 + list_bytes);
-    A.hist = sc.hist;
     A.lp_geo = lp_dtype == GS_RECORD_F32 ? nullptr : lp_geo;
     A.lp_oq = lp_oq;
     A.lp_gb = lp_gb;
     A.lp_dtype = lp_dtype;
-    A.block_entry = reinterpret_cast<uint32_t *>(base + 256 + 2 * list_bytes);
-    A.n_key_blocks = (capacity + kKeyBlock - 1) / kKeyBlock;
+    A.packed = reinterpret_cast<unsigned long long *>(base);
+    A.lkeys = reinterpret_cast<uint64_t *>(base + L.lkeys);
+    A.lvals = reinterpret_cast<uint32_t *>(base + L.lvals);
+    A.dsc = gs_sort_carve_digits(base + L.dsort, g.n, 0, kDepthPasses, kDepthItems);
+    A.counts = counts;
     const unsigned blocks = (unsigned)((g.n + 255) / 256);
     switch (g.sh_degree) {
-        case 0: project_reserve_kernel<0><<<blocks, 256, 0, s>>>(A); break;
-        case 1: project_reserve_kernel<1><<<blocks, 256, 0, s>>>(A); break;
-        case 2: project_reserve_kernel<2><<<blocks, 256, 0, s>>>(A); break;
-        default: project_reserve_kernel<3><<<blocks, 256, 0, s>>>(A); break;
+        case 0: project_list_kernel<0><<<blocks, 256, 0, s>>>(A); break;
+        case 1: project_list_kernel<1><<<blocks, 256, 0, s>>>(A); break;
+        case 2: project_list_kernel<2><<<blocks, 256, 0, s>>>(A); break;
+        default: gs_carveout(project_list_kernel<3>); project_list_kernel<3><<<blocks, 256, 0, s>>>(A); break;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    EmitArgs E{reinterpret_cast<const float4 *>(records), A.packed, A.list_idx, A.list_off,
-               A.block_entry, grid, keys, values, capacity, counts, sc, d_err};
+    if (marks && marks[0]) cudaEventRecord(marks[0], s);
+    // Depth sort of the compact list (its count is counts[3]).
+    bool in_alt = false;
+    e = gs_launch_sort_passes(A.lkeys, A.lvals, reinterpret_cast<uint64_t *>(base + L.akeys),
+                              reinterpret_cast<uint32_t *>(base + L.avals), g.n, counts + 3, A.dsc, d_err,
+                              &in_alt, s);
+    if (e != cudaSuccess) return e;
+    if (marks && marks[1]) cudaEventRecord(marks[1], s);
+    const uint64_t *skeys = in_alt ? reinterpret_cast<const uint64_t *>(base + L.akeys) : A.lkeys;
+    const uint32_t *svals = in_alt ? reinterpret_cast<const uint32_t *>(base + L.avals) : A.lvals;
+    EntryScanArgs S;
+    S.lkeys = skeys;
+    S.packed = A.packed;
+    S.off = reinterpret_cast<uint32_t *>(base + L.off);
+    S.block_entry = reinterpret_cast<uint32_t *>(base + L.block_entry);
+    S.n_key_blocks = (capacity + kKeyBlock - 1) / kKeyBlock;
+    S.counter = reinterpret_cast<uint32_t *>(base + 8);
+    S.status = reinterpret_cast<unsigned long long *>(base + L.scan_status);
+    S.d_err = d_err;
+    gs_carveout(entry_scan_kernel);
+    entry_scan_kernel<<<(unsigned)((g.n + kEntryTile - 1) / kEntryTile), 256, 0, s>>>(S);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (marks && marks[2]) cudaEventRecord(marks[2], s);
+    EmitArgs E{reinterpret_cast<const float4 *>(records), A.packed, svals, S.off, S.block_entry, grid, keys,
+               values, capacity, counts, sc, d_err};
     // One block per 2048 key slots of the capacity (blocks past K only take
     // their ticket).
+    gs_carveout(emit_keys_kernel);
     emit_keys_kernel<<<(unsigned)((capacity + kKeyBlock - 1) / kKeyBlock), 256, 0, s>>>(E);
     return cudaGetLastError();
 }

@@ -25,13 +25,15 @@ using namespace gs;
 
 constexpr int kThreads = kSortThreads;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = GS_SORT_ITEMS;
-constexpr int kTile = kSortTile;          // pairs per partition
+constexpr int kItems = GS_SORT_ITEMS;     // items per thread of the default variant
 constexpr int kLookAhead = GS_SORT_LOOKAHEAD;  // status words read per look-back step
 constexpr int kRadix = 256;
 constexpr int kMaxPasses = 8;
 
-inline int64_t num_parts(int64_t n) { return (n + kTile - 1) / kTile; }
+inline int64_t num_parts(int64_t n, int items = kItems) {
+    const int64_t tile = (int64_t)kThreads * items;
+    return (n + tile - 1) / tile;
+}
 
 inline size_t header_bytes(int passes) {
     size_t b = (size_t)passes * kRadix * 4 * 2 + (size_t)passes * 4 + 4;
@@ -83,11 +85,13 @@ histogram_kernel(const uint64_t *__restrict__ keys, int64_t n, int passes, SortS
     }
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kThreads, GS_SORT_MIN_BLOCKS)
 onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n_host,
                 const unsigned long long *d_n, int pass, int64_t parts, SortScratch sc,
                 uint32_t *d_err, unsigned long long timeout_ns) {
+    constexpr int kItems = ITEMS, kTile = kThreads * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);                       // kTile
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kTile);            // kTile
@@ -98,7 +102,7 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     uint32_t *s_part = s_tmp + kWarps;                                          // 1
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int shift = 8 * pass;
+    const int shift = 8 * (pass + sc.digit0);
     if (tid == 0) *s_part = atomicAdd(sc.counter + pass, 1u);
     for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
     __syncthreads();
@@ -159,7 +163,7 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     // one memory latency per kLookAhead partitions.
     unsigned long long excl = 0;
     if (p > 0) {
-        const unsigned long long t0 = global_ns();
+        unsigned long long t0 = 0;  // read at the first unpublished status word
         int64_t q = p - 1;
         uint32_t polls = 0;
         bool found = false;
@@ -182,11 +186,14 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
                 }
             }
             q -= consumed;
-            if (!found && consumed == 0 && (++polls & 63u) == 0u &&
-                ((global_ns() - t0 > timeout_ns) || (ld_relaxed_u32(d_err) & kErrTimeout))) {
-                atomicOr(d_err, kErrTimeout);
-                __threadfence();
-                break;
+            if (!found && consumed == 0) {
+                if (polls == 0) t0 = global_ns();
+                if ((++polls & 63u) == 0u &&
+                    ((global_ns() - t0 > timeout_ns) || (ld_relaxed_u32(d_err) & kErrTimeout))) {
+                    atomicOr(d_err, kErrTimeout);
+                    __threadfence();
+                    break;
+                }
             }
         }
         st_relaxed_u64(st, kFlagIncl | ((excl + total) & kValueMask));
@@ -221,21 +228,29 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     }
 }
 
-constexpr size_t kOnesweepSmem = (size_t)kTile * 8 + (size_t)kTile * 4 +
-                                 (size_t)kWarps * kRadix * 4 + 2 * kRadix * 4 + kWarps * 4 + 16;
+template <int ITEMS>
+constexpr size_t onesweep_smem() {
+    return (size_t)kThreads * ITEMS * 12 + (size_t)kWarps * kRadix * 4 + 2 * kRadix * 4 + kWarps * 4 + 16;
+}
 
 }  // namespace
 
 int gs_sort_passes(int key_bits) { return (key_bits + 7) / 8; }
 
 size_t gs_sort_scratch_bytes(int64_t n, int key_bits) {
-    const int passes = gs_sort_passes(key_bits);
-    const int64_t parts = num_parts(n) > 0 ? num_parts(n) : 1;
-    return header_bytes(passes) + (size_t)passes * parts * kRadix * sizeof(unsigned long long);
+    return gs_sort_scratch_bytes_digits(n, gs_sort_passes(key_bits));
 }
 
 GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits) {
-    const int passes = gs_sort_passes(key_bits);
+    return gs_sort_carve_digits(base, n_capacity, 0, gs_sort_passes(key_bits));
+}
+
+size_t gs_sort_scratch_bytes_digits(int64_t n, int passes, int items) {
+    const int64_t parts = num_parts(n, items) > 0 ? num_parts(n, items) : 1;
+    return header_bytes(passes) + (size_t)passes * parts * kRadix * sizeof(unsigned long long);
+}
+
+GsSortScratch gs_sort_carve_digits(void *base, int64_t n_capacity, int digit0, int passes, int items) {
     char *p = static_cast<char *>(base);
     GsSortScratch s;
     s.hist = reinterpret_cast<uint32_t *>(p);
@@ -244,7 +259,9 @@ GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits) {
     s.ticket = s.counter + passes;
     s.status = reinterpret_cast<unsigned long long *>(p + header_bytes(passes));
     s.passes = passes;
-    s.parts = num_parts(n_capacity) > 0 ? num_parts(n_capacity) : 1;
+    s.parts = num_parts(n_capacity, items) > 0 ? num_parts(n_capacity, items) : 1;
+    s.digit0 = digit0;
+    s.items = items;
     return s;
 }
 
@@ -254,8 +271,13 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
                                   unsigned long long timeout_ns, int max_passes) {
     *result_in_alt = false;
-    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kOnesweepSmem);
+    if (sc.items != 8 && sc.items != kItems) return cudaErrorInvalidValue;
+    const bool small = sc.items == 8 && kItems != 8;
+    const size_t smem = small ? onesweep_smem<8>() : onesweep_smem<kItems>();
+    cudaError_t e = small ? cudaFuncSetAttribute(onesweep_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem)
+                          : cudaFuncSetAttribute(onesweep_kernel<kItems>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t *kin = keys;
     const uint32_t *vin = values;
@@ -263,8 +285,12 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
     uint32_t *vout = alt_values;
     const int passes = sc.passes < max_passes ? sc.passes : max_passes;
     for (int pass = 0; pass < passes; ++pass) {
-        onesweep_kernel<<<(unsigned)sc.parts, kThreads, kOnesweepSmem, s>>>(
-            kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
+        if (small)
+            onesweep_kernel<8><<<(unsigned)sc.parts, kThreads, smem, s>>>(kin, vin, kout, vout, n_capacity, d_n,
+                                                                           pass, sc.parts, sc, d_err, timeout_ns);
+        else
+            onesweep_kernel<kItems><<<(unsigned)sc.parts, kThreads, smem, s>>>(
+                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         kin = kout;
