@@ -305,9 +305,13 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
     if (bv)
         for (int k = tid; k < kDepthPasses * 256; k += 256)
             if (s_hist[k]) atomicAdd(&A.dsc.hist[k], s_hist[k]);
-    __threadfence();
+    // The barrier orders the block's counter updates before thread 0's fence,
+    // which publishes them (cumulatively) before its ticket.
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x - 1;
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (!s_last) return;
     // Last block: every block's counts and list entries are in.
@@ -493,9 +497,11 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
     if (active)
         for (int q = tid; q < passes * 256; q += 256)
             if (s_hist[q]) atomicAdd(&E.sc.hist[q], s_hist[q]);
-    __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(E.sc.ticket, 1u) == gridDim.x - 1;
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(E.sc.ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (!s_last) return;
     // Last block: every histogram is complete.
