@@ -133,6 +133,63 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary under
+    profiles/, or None if the kernel's source changed since that capture."""
+    import glob
+    import hashlib
+    import re
+    pat = re.compile(r"<!-- traffic kernel=(\S+) bytes_per_launch=(\d+) source=(\S+) sha256_16=([0-9a-f]+) -->")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            text = f.read()
+        for m in pat.finditer(text):
+            if m.group(1) != kernel:
+                continue
+            src = os.path.join(ROOT, m.group(3))
+            if not os.path.exists(src):
+                return None, None
+            with open(src, "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest()[:16] != m.group(4):
+                    return None, None
+            return int(m.group(2)), os.path.relpath(path, ROOT)
+    return None, None
+
+
+def in_front(scene, cam) -> int:
+    """Gaussians in front of the near plane (they read scale, rotation and
+    opacity in the projection; the rest read only their mean)."""
+    w = np.asarray(cam.world_to_cam, dtype=np.float64).reshape(3, 4)
+    tz = scene.means.astype(np.float64) @ w[2, :3] + w[2, 3]
+    return int((tz > cam.near_z).sum())
+
+
+def frame_bytes(n, n_front, n_vis, K, sh_degree, tile_passes, n_tiles, pixels) -> dict:
+    """Bytes each forward stage has to move in DRAM, per frame (records 48 B,
+    keys 8 B, values 4 B; the image is rgb + final T + last contributor)."""
+    s = 3 * (sh_degree + 1) ** 2
+    return {
+        "project": n * 12 + n_front * 32 + n_vis * (4 * s) + n_vis * (48 + 12),
+        "depth_sort": 4 * n_vis * 24,
+        "entry_scan": n_vis * 12,
+        "emit": n_vis * (32 + 8) + K * 12,
+        "tile_sort": tile_passes * K * 24,
+        "ranges": K * 8 + n_tiles * 8,
+        "blend": K * 4 + n_vis * 48 + pixels * 20,
+    }
+
+
+def backward_bytes(n, n_vis, K, sh_degree, pixels) -> int:
+    """Bytes of gs_render_backward: the blend backward reads the lists, the
+    records and (d_rgb, final T, last contributor) and accumulates 9 floats
+    per visible record; the projection backward reads them back with the
+    parameters of visible Gaussians and writes every gradient array."""
+    s = 3 * (sh_degree + 1) ** 2
+    blend = K * 4 + n_vis * 48 + pixels * 20 + n_vis * 36 + n * 36
+    project = n * 36 + n_vis * (44 + 4 * s) + n * (44 + 4 * s)
+    return blend + project
+
+
 def fwd_bwd(gs, torch, args, flush, local) -> dict:
     """Forward + backward through the autograd wrapper on the 500k-Gaussian
     clustered scene at 1080p with an L1 loss against a seeded random target:
@@ -174,11 +231,23 @@ def fwd_bwd(gs, torch, args, flush, local) -> dict:
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     fms = float(np.mean([a.elapsed_time(b) for a, b in fwd]))
+    st = gs.gs_last_render_stats(ctx)
     ctx.close()
+    pk, _ = peaks()
+    n_tiles = st["n_tiles"]
+    fb = frame_bytes(scene.n, in_front(scene, cam), st["n_visible"], st["n_keys"], scene.sh_degree,
+                     (st["key_bits"] - 32 + 7) // 8, n_tiles, cam.width * cam.height)
+    total = sum(fb.values()) + backward_bytes(scene.n, st["n_visible"], st["n_keys"], scene.sh_degree,
+                                              cam.width * cam.height)
+    gbs = total / (ms / 1e3) / 1e9
     return {"workload": "clustered_500k_1080p", "description": "500k Gaussians as the 1M scene, SH3, "
             "1920x1080, L1 loss vs a seeded U[0,1] target, torch.autograd through RasterizeGaussians",
             "ms_per_iter": round(ms, 4), "forward_ms": round(fms, 4), "backward_ms": round(ms - fms, 4),
-            "iters": steps, "grads": "means, log_scales, quats, opacity_logits, sh (degree 3)"}
+            "iters": steps, "grads": "means, log_scales, quats, opacity_logits, sh (degree 3)",
+            "n_visible": st["n_visible"], "n_keys": st["n_keys"],
+            "hbm": {"bytes_per_iter": int(total), "GB/s": round(gbs, 1),
+                    "frac_of_measured_peak": round(gbs / pk["hbm_gbs"], 4),
+                    "note": "render + backward kernel bytes only (the torch loss kernels are not counted)"}}
 
 
 def batched(gs, torch, args, flush, local) -> dict:
@@ -417,12 +486,31 @@ def main():
     blend_ms = stage_ms.get("blend_ms", float("nan"))
     flops = FLOPS_PER_EVAL * n_eval_total
     achieved = flops / (blend_ms / 1e3) / 1e12
+    traffic, traffic_src = profiled_traffic("blend_culled_kernel" if args.blend_variant == 0 else "blend_basic_kernel")
     roofline = {"kernel": "gs_blend", "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak_tflops, 4), "traffic": None,
+                "frac": round(achieved / fp32_peak_tflops, 4), "traffic": traffic,
+                "traffic_source": traffic_src,
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_clock:.0f} MHz",
                 "units_per_launch": n_eval_total, "flops_per_unit": FLOPS_PER_EVAL,
                 "launch_ms": round(blend_ms, 4)}
+
+    # HBM view of the same frame: bytes each stage must move / its live time.
+    tile_passes = (stats["key_bits"] - 32 + 7) // 8
+    fbytes = frame_bytes(scene.n, in_front(scene, cam), stats["n_visible"], stats["n_keys"], scene.sh_degree,
+                         tile_passes, stats["n_tiles"], W * H)
+    stage_of = {"project": "project_ms", "depth_sort": "depth_sort_ms", "entry_scan": "entry_scan_ms",
+                "emit": "emit_ms", "tile_sort": "tile_sort_ms", "ranges": "ranges_ms", "blend": "blend_ms"}
+    hbm_peak = pk.get("hbm_gbs") or 6800.0
+    hbm = {}
+    for k, b in fbytes.items():
+        t = stage_ms.get(stage_of[k], float("nan"))
+        gbs = b / (t / 1e3) / 1e9 if t > 0 else float("nan")
+        hbm[k] = {"bytes": int(b), "ms": round(t, 4), "GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)}
+    frame_gbs = sum(fbytes.values()) / (ms_per_step / 1e3) / 1e9
+    hbm["frame"] = {"bytes": int(sum(fbytes.values())), "ms": round(ms_per_step, 4), "GB/s": round(frame_gbs, 1),
+                    "frac": round(frame_gbs / hbm_peak, 4), "peak_GB/s": hbm_peak,
+                    "peak_source": "measured" if pk_kind == "measured" else "fallback"}
 
     line = {
         "metric": "frames/s (1080p, 1M Gaussians, forward)",
@@ -439,6 +527,7 @@ def main():
                 "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps},
         "gpu_launches": None,
         "roofline": roofline,
+        "hbm_roofline": hbm,
         "peaks": {"source": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
         "clocks": clk,
     }
