@@ -319,6 +319,56 @@ def batched(gs, torch, args, flush, local) -> dict:
             "keys_per_batch": st["n_keys"], "iters": iters}
 
 
+def temporal(gs, torch, args, flush, local) -> dict:
+    """Temporal re-binning on the 1M-Gaussian 1080p scene under the camera
+    motions of the paper's churn experiment: per motion, the churn (Gaussians
+    whose tile rect changed, per frame, over all and over visible Gaussians),
+    the share of frames re-binned, and device time per frame with and without
+    re-binning (CUDA events, L2 flushed between frames)."""
+    from paper_2607_15951_gb300 import scenes
+    scene, cams0 = scenes.workload("clustered_1m_1080p")
+    g = gs.scene_to_device(scene)
+    W, H = cams0[0].width, cams0[0].height
+    rgb = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    frames = max(8, min(40, args.steps // 50))
+    res = {}
+    for kind, step in (("static", None), ("orbit", 0.1), ("orbit", 0.5), ("orbit", 2.0), ("translate", 0.01),
+                       ("rotate", 1.0), ("teleport", None)):
+        cams = scenes.motion(kind, frames + 1, W, H, step=step)
+        row = {}
+        for mode in (False, True):
+            ctx = gs.Context(local)
+            gs.gs_render(ctx, g, scene.sh_degree, cams[0], rgb, temporal=mode)
+            times, moved, vis, reb = [], [], [], 0
+            for c in cams[1:]:
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                gs.gs_render(ctx, g, scene.sh_degree, c, rgb, temporal=mode)
+                b.record(stream)
+                b.synchronize()
+                st = gs.gs_last_render_stats(ctx)
+                times.append(a.elapsed_time(b))
+                moved.append(st["n_moved"])
+                vis.append(max(1, st["n_visible"]))
+                reb += int(st["rebinned"])
+            ctx.close()
+            if mode:
+                row["ms_rebinning"] = round(float(np.mean(times)), 4)
+                row["rebinned_frames"] = f"{reb}/{frames}"
+                row["moved_per_frame"] = round(float(np.mean(moved)), 1)
+                row["churn_of_all_pct"] = round(100.0 * float(np.mean(moved)) / scene.n, 3)
+                row["churn_of_visible_pct"] = round(100.0 * float(np.mean(np.array(moved) / np.array(vis))), 2)
+            else:
+                row["ms_full"] = round(float(np.mean(times)), 4)
+        row["speedup"] = round(row["ms_full"] / row["ms_rebinning"], 3)
+        res[kind if step is None else f"{kind}_{step}"] = row
+    return {"workload": "clustered_1m_1080p", "frames_per_motion": frames,
+            "note": "orbit about a point 4 m ahead (deg/frame), translate (m/frame), rotate in place (deg/frame)",
+            "motions": res}
+
+
 def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:
     """Time the FP64 oracle on the host cores rendering whole frames of the
     same workload until about ``budget_s`` seconds have passed."""
@@ -380,6 +430,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fwd-bwd", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-temporal", action="store_true")
     ap.add_argument("--blend-variant", type=int, default=0, help="0 culled (default), 1 basic")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -541,6 +592,8 @@ def main():
         line["fwd_bwd"] = fwd_bwd(gs, torch, args, flush, local)
     if not args.no_batched:
         line["batched"] = batched(gs, torch, args, flush, local)
+    if not args.no_temporal:
+        line["temporal"] = temporal(gs, torch, args, flush, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cam)
     if rank == 0:

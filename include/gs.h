@@ -134,7 +134,9 @@ typedef struct {
                                (default), 1 = launch the kernels directly      */
     int32_t sync_mode;      /* gs_render: GS_SYNC_FRAME (default) or
                                GS_SYNC_DEFERRED, see gs_render                 */
-    int32_t reserved[4];    /* must be zero                                    */
+    int32_t temporal;       /* gs_render: 1 = temporal re-binning, see
+                               gs_render (needs GS_SYNC_FRAME)                 */
+    int32_t reserved[3];    /* must be zero                                    */
 } gs_options;
 
 /* When gs_render checks a frame's key count (see gs_render). */
@@ -247,6 +249,16 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
  *                     have then grown and the caller renders again.
  *                     gs_render_backward waits for the frame it
  *                     differentiates and fails if that frame overflowed. */
+/* Temporal re-binning (opts->temporal = 1; the paper's temporal-locality
+ * idea, Sec. 5.4 and Sec. 6): when the previous frame on this context was
+ * rendered the same way with the same Gaussian count and tile grid, this
+ * frame's per-tile lists are rebuilt from that frame's: only Gaussians whose
+ * tile rect changed ("moved", counted in gs_render_stats.n_moved) leave and
+ * enter tiles, and each tile is put in this frame's (depth, index) order by
+ * a merge or an in-tile sort. The lists, and so the image, are identical to
+ * those of a full binning. The frame is binned from scratch instead when
+ * there is no such state, when more than a quarter of the visible Gaussians
+ * moved in the previous frame, or when a tile list exceeds 4096 entries. */
 gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
                     const gs_options *opts, const gs_framebuffer *fb, void *stream);
 
@@ -330,6 +342,11 @@ typedef struct {
     int64_t n_keys;    /* (tile, Gaussian) pairs K                             */
     int32_t key_bits;  /* significant key bits sorted                          */
     int32_t n_tiles;
+    int64_t n_moved;   /* temporal re-binning: Gaussians whose tile rect
+                          changed since the previous frame (0 otherwise)     */
+    int32_t rebinned;  /* 1 if the lists were re-binned from the previous
+                          frame's, 0 if binned from scratch                  */
+    int32_t reserved;
 } gs_render_stats;
 gs_status gs_last_render_stats(gs_context *ctx, gs_render_stats *out);
 

@@ -63,7 +63,7 @@ def camera_struct(cam) -> N.gs_camera:
 
 
 def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
-                   blend_variant: int = 0, deferred: bool = False) -> N.gs_options:
+                   blend_variant: int = 0, deferred: bool = False, temporal: bool = False) -> N.gs_options:
     o = N.gs_options()
     _lib().gs_default_options(ctypes.byref(o))
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
@@ -72,6 +72,7 @@ def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
     o.record_dtype = int(record_dtype)
     o.blend_variant = int(blend_variant)
     o.sync_mode = N.GS_SYNC_DEFERRED if deferred else N.GS_SYNC_FRAME
+    o.temporal = 1 if temporal else 0
     return o
 
 
@@ -202,11 +203,12 @@ def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_co
 
 def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
               n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
-              record_dtype: int = 0, deferred: bool = False, stream=None) -> None:
+              record_dtype: int = 0, deferred: bool = False, temporal: bool = False, stream=None) -> None:
     """deferred=True: GS_SYNC_DEFERRED (no host synchronisation; an overflow
-    or device error is raised by a later call on the context)."""
+    or device error is raised by a later call on the context).
+    temporal=True: re-bin from the previous frame's lists (same results)."""
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred)
+    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred, temporal)
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
                                ctypes.byref(fb), _stream(stream)))
@@ -234,7 +236,7 @@ def gs_last_render_stats(ctx: Context) -> dict:
     s = N.gs_render_stats()
     ctx.check(_lib().gs_last_render_stats(ctx.handle, ctypes.byref(s)))
     return {"n_visible": s.n_visible, "n_keys": s.n_keys, "key_bits": s.key_bits,
-            "n_tiles": s.n_tiles}
+            "n_tiles": s.n_tiles, "n_moved": s.n_moved, "rebinned": bool(s.rebinned)}
 
 
 def gs_reserve_keys(ctx: Context, key_capacity: int) -> None:
@@ -271,7 +273,7 @@ def scene_to_device(scene, device="cuda") -> dict:
 
 def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
            aux: bool = True, variant: int = 0, record_dtype: int = 0, deferred: bool = False,
-           stream=None) -> dict:
+           temporal: bool = False, stream=None) -> dict:
     """Allocate outputs with torch and call gs_render."""
     import torch
     H, W = int(cam.height), int(cam.width)
@@ -283,7 +285,7 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
         out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
               out.get("n_eval"), tile=tile, bg=bg, variant=variant, record_dtype=record_dtype,
-              deferred=deferred, stream=stream)
+              deferred=deferred, temporal=temporal, stream=stream)
     return out
 
 

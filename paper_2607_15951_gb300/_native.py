@@ -66,13 +66,14 @@ class gs_options(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("bg", ctypes.c_float * 3), ("record_dtype", ctypes.c_int32),
                 ("blend_variant", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
-                ("sync_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("sync_mode", ctypes.c_int32), ("temporal", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class gs_render_stats(ctypes.Structure):
     _fields_ = [("n_visible", ctypes.c_int64), ("n_keys", ctypes.c_int64),
-                ("key_bits", ctypes.c_int32), ("n_tiles", ctypes.c_int32)]
+                ("key_bits", ctypes.c_int32), ("n_tiles", ctypes.c_int32),
+                ("n_moved", ctypes.c_int64), ("rebinned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gs_stage_times(ctypes.Structure):

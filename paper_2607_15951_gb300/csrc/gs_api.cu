@@ -23,7 +23,7 @@ struct gs_context {
     int device = 0;
     std::string last_error;
     uint32_t *d_err = nullptr;               // device error word
-    unsigned long long *d_counts = nullptr;  // [K, n_visible, K if it fitted, pad]
+    unsigned long long *d_counts = nullptr;  // [K, n_visible, K if it fitted, visible, rects changed, pad...]
     unsigned long long *h_counts = nullptr;  // pinned mirror of d_counts
     uint32_t *h_err = nullptr;               // pinned mirror of d_err
     DevBuf records, tiles, offsets, scan_scratch, keys, values, alt_keys, alt_values, sort_scratch,
@@ -68,6 +68,21 @@ struct gs_context {
     uint64_t next_seq = 1;   // sequence number of the next deferred frame
     uint64_t clear_seq = 0;  // frames before this one saw an error word already reported
     uint64_t last_seq = 0;   // the last gs_render, if it was deferred
+    const uint32_t *last_ranges = nullptr;  // per-tile ranges of the last gs_render
+    // Temporal re-binning state: the lists and tile rects of the last frame
+    // rendered with opts->temporal (prev_* may point into the full path's
+    // buffers; an incremental frame writes vals[cur] / ranges[cur]).
+    struct Temporal {
+        bool valid = false;
+        int64_t n = 0;
+        int tiles_x = 0, tiles_y = 0, tw = 0, th = 0;
+        DevBuf rects[2], moved, moved_list, tile_scratch, vals[2], ranges[2], ins_vals;
+        const uint32_t *prev_vals = nullptr, *prev_ranges = nullptr;
+        int cur = 0;
+        int rcur = 0;         // rects[rcur] holds the last frame's packed tile rects
+        int64_t rects_n = -1;  // ... for this many Gaussians (-1: none)
+        double last_churn = 0.0;  // moved / visible of the last frame
+    } temporal;
 };
 
 namespace {
@@ -136,7 +151,10 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
         return fail(ctx, GS_ERR_INVALID_ARG, "direct_launch must be 0 or 1");
     if (o->sync_mode != GS_SYNC_FRAME && o->sync_mode != GS_SYNC_DEFERRED)
         return fail(ctx, GS_ERR_INVALID_ARG, "sync_mode must be GS_SYNC_FRAME or GS_SYNC_DEFERRED");
-    for (int i = 0; i < 4; ++i)
+    if (o->temporal != 0 && o->temporal != 1) return fail(ctx, GS_ERR_INVALID_ARG, "temporal must be 0 or 1");
+    if (o->temporal && o->sync_mode != GS_SYNC_FRAME)
+        return fail(ctx, GS_ERR_INVALID_ARG, "temporal re-binning needs sync_mode GS_SYNC_FRAME");
+    for (int i = 0; i < 3; ++i)
         if (o->reserved[i] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
@@ -290,9 +308,14 @@ struct DeviceGuard {
 
 // Scan + emit + sort + ranges into the given key/value buffers (which must
 // hold `capacity` pairs); the other pair of buffers comes from the context.
+// Temporal state may point into the context's key buffers, which the stage
+// entry points reuse: they drop it.
+void drop_temporal(gs_context *ctx) { ctx->temporal.valid = false; }
+
 gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *tiles, int64_t n,
                    const GsGrid &grid, uint64_t *keys, uint32_t *values, int64_t capacity,
                    bool capacity_is_ctx, uint32_t *ranges, int64_t *n_keys, cudaStream_t s) {
+    drop_temporal(ctx);
     gs_status st;
     const int n_tiles = grid.tiles_x * grid.tiles_y;
     if ((st = ensure(ctx, ctx->offsets, (size_t)(n > 0 ? n : 1) * 8, "offsets")) != GS_OK) return st;
@@ -343,6 +366,145 @@ gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *ti
     return GS_OK;
 }
 
+// Above this fraction of moved Gaussians (of the visible ones) in the last
+// frame, the next frame is binned from scratch: re-binning pays off only
+// while few tiles change (measured break-even near 10 % on a 1M-Gaussian
+// 1080p scene).
+constexpr double kTemporalMaxChurn = 0.08;
+// Largest tile list the per-tile merge holds in shared memory (a power of two).
+constexpr int kTemporalTileCap = 4096;
+
+// One frame with temporal re-binning. *done = false (and GS_OK) when the
+// frame has to be binned from scratch instead: a tile above the per-tile
+// limit, more pairs than the buffers hold, or state inconsistent with it.
+gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam, const gs_options *opts,
+                          const gs_framebuffer *fb, cudaStream_t s, bool *done) {
+    *done = false;
+    auto &T = ctx->temporal;
+    gs_status st;
+    const GsGrid grid = make_grid(cam, opts);
+    const int64_t n = g->n;
+    const int n_tiles = grid.tiles_x * grid.tiles_y;
+    const int64_t cap = ctx->key_capacity;
+    const int dtype = opts->record_dtype;
+    const size_t tiles4 = ((size_t)n_tiles * 4 + 255) / 256 * 256;
+    const size_t status_bytes = (gs_temporal_scan_status_bytes(n_tiles) + 255) / 256 * 256;
+    // tile scratch: removed, added, ins_cursor (zeroed), ins_first, then 256 B
+    // of counters (zeroed) and the scan status (zeroed)
+    const size_t zero_bytes = 3 * tiles4 + 256 + status_bytes;
+    const int out = T.cur;
+    // Work items: one per moved Gaussian plus one per 256 tiles of its rects.
+    const int64_t item_cap = n + 2 * (cap / 256) + 4096;
+    if ((st = ensure(ctx, T.rects[T.rcur ^ 1], (size_t)n * 8, "temporal rects")) != GS_OK ||
+        (st = ensure(ctx, T.moved, (size_t)n, "temporal flags")) != GS_OK ||
+        (st = ensure(ctx, T.moved_list, (size_t)item_cap * 8, "temporal work items")) != GS_OK ||
+        (st = ensure(ctx, T.tile_scratch, zero_bytes + tiles4, "temporal tile scratch")) != GS_OK ||
+        (st = ensure(ctx, T.vals[out], (size_t)cap * 4, "temporal values")) != GS_OK ||
+        (st = ensure(ctx, T.ranges[out], (size_t)n_tiles * 8, "temporal ranges")) != GS_OK ||
+        (st = ensure(ctx, T.ins_vals, (size_t)cap * 4, "temporal arrivals")) != GS_OK)
+        return st;
+    char *ts = static_cast<char *>(T.tile_scratch.ptr);
+    uint32_t *removed = reinterpret_cast<uint32_t *>(ts);
+    uint32_t *added = reinterpret_cast<uint32_t *>(ts + tiles4);
+    uint32_t *ins_cursor = reinterpret_cast<uint32_t *>(ts + 2 * tiles4);
+    unsigned long long *counters = reinterpret_cast<unsigned long long *>(ts + 3 * tiles4);
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(ts + 3 * tiles4 + 256);
+    uint32_t *ins_first = reinterpret_cast<uint32_t *>(ts + zero_bytes);
+    // counters: [0] visible << 33 | keys, [1] moved Gaussians, [2] their work items,
+    // [3] entries, [4] arrivals, [5] the scan's partition counter
+    GS_CUDA(ctx, cudaMemsetAsync(ts, 0, zero_bytes, s));
+    gs_record *rec = static_cast<gs_record *>(ctx->records.ptr);
+    uint32_t *vals = static_cast<uint32_t *>(T.vals[out].ptr);
+    uint32_t *ranges = static_cast<uint32_t *>(T.ranges[out].ptr);
+    mark(ctx, EV_START, s);
+    const uint2 *prev_rect = static_cast<const uint2 *>(T.rects[T.rcur].ptr);
+    uint2 *rect = static_cast<uint2 *>(T.rects[T.rcur ^ 1].ptr);
+    GS_CUDA(ctx, gs_launch_project_temporal(*g, make_cam(cam), grid, rec, static_cast<float4 *>(ctx->lp_geo.ptr),
+                                            static_cast<uint2 *>(ctx->lp_oq.ptr),
+                                            static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype, prev_rect, rect,
+                                            static_cast<uint8_t *>(T.moved.ptr),
+                                            static_cast<unsigned long long *>(T.moved_list.ptr), item_cap,
+                                            counters, ctx->d_err, s));
+    mark(ctx, EV_PROJECT, s);
+    mark(ctx, EV_DEPTH, s);
+    mark(ctx, EV_SCAN, s);
+    mark(ctx, EV_EMIT, s);
+    GsTemporalRebin R;
+    R.records = reinterpret_cast<const float4 *>(rec);
+    R.prev_vals = T.prev_vals;
+    R.prev_ranges = T.prev_ranges;
+    R.moved = static_cast<const uint8_t *>(T.moved.ptr);
+    R.removed = removed;
+    R.added = added;
+    R.items = static_cast<const unsigned long long *>(T.moved_list.ptr);
+    R.n_items = counters + 2;
+    R.item_capacity = item_cap;
+    R.prev_rect = prev_rect;
+    R.rect = rect;
+    R.n_tiles = n_tiles;
+    R.tiles_x = grid.tiles_x;
+    R.n_gaussians = n;
+    R.ranges = ranges;
+    R.vals = vals;
+    R.capacity = cap;
+    R.ins_first = ins_first;
+    R.ins_cursor = ins_cursor;
+    R.ins_vals = static_cast<uint32_t *>(T.ins_vals.ptr);
+    R.ins_capacity = cap;
+    R.totals = counters + 3;
+    R.scan_counter = reinterpret_cast<uint32_t *>(counters + 5);
+    R.scan_status = status;
+    R.cap_entries = kTemporalTileCap;
+    R.d_err = ctx->d_err;
+    GS_CUDA(ctx, gs_launch_temporal_rebin(R, s));
+    mark(ctx, EV_SORT, s);
+    mark(ctx, EV_RANGES, s);
+    GS_CUDA(ctx, gs_launch_blend(reader(ctx, rec, dtype), vals, ranges, grid, cam->width, cam->height, opts->bg,
+                                 *fb, opts->blend_variant, s));
+    mark(ctx, EV_BLEND, s);
+    unsigned long long *h = ctx->h_ring;  // no deferred frame is in flight (drained before)
+    h[5] = 0;
+    GS_CUDA(ctx, cudaMemcpyAsync(h, counters, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(ctx, cudaMemcpyAsync(h + 5, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(ctx, cudaStreamSynchronize(s));
+    const uint32_t w = static_cast<uint32_t>(h[5]);
+    const unsigned long long K = h[3];
+    if ((w & gs::kErrTemporal) || (int64_t)K > cap) {
+        // Rebuild this frame from scratch (it also recaptures the state).
+        GS_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s));
+        T.valid = false;
+        if ((int64_t)K > cap) ctx->key_capacity = (int64_t)(K + K / 4 + 1024);
+        return GS_OK;
+    }
+    const int64_t visible = (int64_t)(h[0] >> 33);
+    ctx->stats.n_visible = visible;
+    ctx->stats.n_keys = (int64_t)K;
+    ctx->stats.n_tiles = n_tiles;
+    ctx->stats.key_bits = key_bits_for(n_tiles);
+    ctx->stats.n_moved = (int64_t)h[1];
+    ctx->stats.rebinned = 1;
+    T.prev_vals = vals;
+    T.prev_ranges = ranges;
+    T.cur = out ^ 1;
+    T.rcur ^= 1;
+    T.rects_n = n;
+    T.last_churn = visible > 0 ? (double)h[1] / (double)visible : 0.0;
+    if (ctx->timing) ctx->timed_once = true;
+    ctx->have_last = true;
+    ctx->last_seq = 0;
+    ctx->last_n = n;
+    ctx->last_w = cam->width;
+    ctx->last_h = cam->height;
+    ctx->last_tw = grid.tile_w;
+    ctx->last_th = grid.tile_h;
+    ctx->last_values = vals;
+    ctx->last_ranges = ranges;
+    ctx->last_dtype = dtype;
+    *done = true;
+    if (w) return collect_device_error(ctx, s);
+    return GS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -366,8 +528,8 @@ gs_status gs_create(gs_context **out, int device) {
     ctx->device = device;
     DeviceGuard g(device);
     if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess ||
-        cudaMalloc(&ctx->d_counts, 4 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_counts, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_counts, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_counts, 8 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_err, sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_ring, 5 * gs_context::kRing * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
@@ -481,6 +643,7 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *values, int64
         return fail(ctx, GS_ERR_INVALID_ARG, "n must be in 0..2^32-2 and key_bits in 1..64");
     if (n > 0 && (!keys || !values)) return fail(ctx, GS_ERR_INVALID_ARG, "keys/values are NULL");
     if (n <= 1) return GS_OK;
+    drop_temporal(ctx);
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     gs_status st;
@@ -563,6 +726,32 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     if (ctx->key_capacity == 0) ctx->key_capacity = std::max<int64_t>(int64_t(1) << 20, 4 * n);
     gs_record *rec = static_cast<gs_record *>(ctx->records.ptr);
     uint32_t *ranges = static_cast<uint32_t *>(ctx->ranges.ptr);
+    auto &T = ctx->temporal;
+    const bool temporal = opts->temporal != 0;
+    if (!temporal) {
+        T.valid = false;
+        T.rects_n = -1;
+    } else {
+        if (T.valid && (T.n != n || T.tiles_x != grid.tiles_x || T.tiles_y != grid.tiles_y ||
+                        T.tw != grid.tile_w || T.th != grid.tile_h))
+            T.valid = false;
+        if (T.valid && T.last_churn <= kTemporalMaxChurn && n > 0) {
+            bool done = false;
+            if ((st = render_rebinned(ctx, g, cam, opts, fb, s, &done)) != GS_OK) return st;
+            if (done) return GS_OK;
+        }
+        if ((st = ensure(ctx, T.rects[0], (size_t)(n > 0 ? n : 1) * 8, "temporal rects")) != GS_OK ||
+            (st = ensure(ctx, T.rects[1], (size_t)(n > 0 ? n : 1) * 8, "temporal rects")) != GS_OK)
+            return st;
+    }
+    // A full frame with temporal re-binning on writes this frame's rects next
+    // to the previous frame's (if that frame had the same Gaussians and tile
+    // grid) and counts the rects that changed: the churn that decides how the
+    // next frame is binned.
+    const bool have_prev_rects = temporal && T.rects_n == n && T.tiles_x == grid.tiles_x &&
+                                 T.tiles_y == grid.tiles_y && T.tw == grid.tile_w && T.th == grid.tile_h;
+    uint2 *prect = temporal ? static_cast<uint2 *>(T.rects[T.rcur ^ (have_prev_rects ? 1 : 0)].ptr) : nullptr;
+    const uint2 *prev_rect = have_prev_rects ? static_cast<const uint2 *>(T.rects[T.rcur].ptr) : nullptr;
 
     // The key buffers are sized from earlier frames; if this frame needs more,
     // the overflow is detected at the end and the frame is rendered again.
@@ -595,7 +784,8 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
                                            static_cast<uint2 *>(ctx->lp_oq.ptr),
                                            static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype, keys, vals, cap,
                                            ctx->d_counts,
-                                           ctx->fused_scratch.ptr, sc, ctx->d_err, s, ev3));
+                                           ctx->fused_scratch.ptr, sc, ctx->d_err, s, ev3, prect, prev_rect,
+                                           ctx->d_counts + 4));
         mark(ctx, EV_EMIT, s);
         bool in_alt = false;
         GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, cap, ctx->d_counts + 2, sc, ctx->d_err,
@@ -631,10 +821,11 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             ctx->last_tw = grid.tile_w;
             ctx->last_th = grid.tile_h;
             ctx->last_values = sv;
+            ctx->last_ranges = ranges;
             ctx->last_dtype = dtype;
             return GS_OK;
         }
-        GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 4 * sizeof(unsigned long long),
+        GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 5 * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, s));
         GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         GS_CUDA(ctx, cudaStreamSynchronize(s));
@@ -661,10 +852,29 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         ctx->last_tw = grid.tile_w;
         ctx->last_th = grid.tile_h;
         ctx->last_values = sv;
+        ctx->last_ranges = ranges;
         ctx->last_dtype = dtype;
+        ctx->stats.n_moved = have_prev_rects ? (int64_t)ctx->h_counts[4] : 0;
+        ctx->stats.rebinned = 0;
+        if (temporal) {
+            T.valid = true;
+            T.n = n;
+            T.tiles_x = grid.tiles_x;
+            T.tiles_y = grid.tiles_y;
+            T.tw = grid.tile_w;
+            T.th = grid.tile_h;
+            T.prev_vals = sv;
+            T.prev_ranges = ranges;
+            T.cur = 0;
+            if (have_prev_rects) T.rcur ^= 1;
+            T.rects_n = n;
+            T.last_churn = have_prev_rects && ctx->stats.n_visible > 0
+                               ? (double)ctx->h_counts[4] / (double)ctx->stats.n_visible
+                               : 0.0;
+        }
         // Keep about 25 % headroom over this frame's count for the next one
         // (the buffers themselves only grow).
-        if (!ctx->pinned_capacity && (int64_t)K * 2 < cap)
+        if (!temporal && !ctx->pinned_capacity && (int64_t)K * 2 < cap)
             ctx->key_capacity = std::max<int64_t>(65536, (int64_t)(K + K / 4 + 1024));
         if (*ctx->h_err) return collect_device_error(ctx, s);
         return GS_OK;
@@ -701,8 +911,7 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
     float *d_rec = static_cast<float *>(ctx->d_rec.ptr);
     GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)n * 9 * sizeof(float), s));
     GS_CUDA(ctx, gs_launch_blend_bwd(reader(ctx, static_cast<gs_record *>(ctx->records.ptr), ctx->last_dtype),
-                                     ctx->last_values,
-                                     static_cast<uint32_t *>(ctx->ranges.ptr), grid, cam->width, cam->height,
+                                     ctx->last_values, ctx->last_ranges, grid, cam->width, cam->height,
                                      opts->bg, d_rgb, fb->final_T, fb->n_contrib, d_rec, s));
     GS_CUDA(ctx, gs_launch_project_bwd(*g, make_cam(cam), grid, d_rec, *out, s));
     if (out->d_records && n > 0)

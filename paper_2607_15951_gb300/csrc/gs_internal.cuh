@@ -32,7 +32,9 @@ constexpr float kGuard = 1.3f;            // Jacobian view-ratio clamp, x tan(ha
 constexpr int kMaxRadius = 1 << 30;       // radius clamp so tile arithmetic fits int64
 
 // Device error word bits (gs_context::d_err).
-enum : uint32_t { kErrTimeout = 1u, kErrCapacity = 2u, kErrRange = 4u };
+// kErrTemporal: an incremental re-binning could not produce this frame's
+// lists (the caller rebuilds them with the full binning); not a user error.
+enum : uint32_t { kErrTimeout = 1u, kErrCapacity = 2u, kErrRange = 4u, kErrTemporal = 8u };
 
 // Every spin-wait on another block gives up after this much wall time and
 // sets kErrTimeout; other waiting blocks see the error word and leave early.
@@ -348,7 +350,47 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
                                   uint64_t *keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
-                                  const cudaEvent_t *marks = nullptr /* 3 events or null */);
+                                  const cudaEvent_t *marks = nullptr /* 3 events or null */,
+                                  uint2 *prect = nullptr /* n packed tile rects, for re-binning */,
+                                  const uint2 *prev_rect = nullptr /* previous frame's: */,
+                                  unsigned long long *moved = nullptr /* count of rects that differ */);
+
+// Temporal re-binning (gs_temporal.cu). Projection step: records as
+// gs_launch_project_bin, plus per Gaussian its packed tile rect (`rect`),
+// compared with the previous frame's (`prev_rect`): `moved` flags, work
+// items (index << 32 | chunk, one per 256 tiles of the larger of a moved
+// Gaussian's two rects) and counters (zeroed): [0] visible << 33 | keys,
+// [1] moved Gaussians, [2] work items.
+cudaError_t gs_launch_project_temporal(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
+                                       gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
+                                       int lp_dtype, const uint2 *prev_rect, uint2 *rect, uint8_t *moved,
+                                       unsigned long long *items, int64_t item_capacity,
+                                       unsigned long long *counters, uint32_t *d_err, cudaStream_t s);
+struct GsTemporalRebin {
+    const float4 *records;          // FP32 records of this frame
+    const uint32_t *prev_vals, *prev_ranges;
+    const uint8_t *moved;
+    uint32_t *removed, *added;      // per tile, zeroed
+    const unsigned long long *items;   // moved-Gaussian work items
+    const unsigned long long *n_items;
+    int64_t item_capacity;
+    const uint2 *prev_rect, *rect;  // previous and this frame's packed rects
+    int32_t n_tiles, tiles_x;
+    int64_t n_gaussians;
+    uint32_t *ranges;               // out
+    uint32_t *vals;                 // out
+    int64_t capacity;               // entries vals holds
+    uint32_t *ins_first, *ins_cursor, *ins_vals;  // ins_cursor zeroed
+    int64_t ins_capacity;
+    unsigned long long *totals;     // out: [0] entries, [1] arrivals
+    uint32_t *scan_counter;         // zeroed
+    unsigned long long *scan_status;  // zeroed, gs_temporal_scan_status_bytes
+    int cap_entries;                // per-tile entry limit (power of two)
+    uint32_t *d_err;
+};
+size_t gs_temporal_merge_smem(int cap_entries);
+size_t gs_temporal_scan_status_bytes(int32_t n_tiles);
+cudaError_t gs_launch_temporal_rebin(const GsTemporalRebin &r, cudaStream_t s);
 
 // Backward kernels.
 cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,

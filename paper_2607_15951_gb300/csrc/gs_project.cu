@@ -251,7 +251,18 @@ struct ListArgs {
     uint32_t *lvals;             // n: its Gaussian index
     GsSortScratch dsc;           // the depth sort's histograms, bucket offsets, ticket
     unsigned long long *counts;  // [3] <- visible count (the depth sort's count)
+    uint2 *prect;                // optional, n: packed tile rect of every Gaussian (0 = none),
+                                 // kept for temporal re-binning
+    const uint2 *prev_rect;      // optional, n: the previous frame's; rects that differ
+    unsigned long long *moved;   // are counted here (the churn)
 };
+
+// Tile rect packed in 2 words (x0 | x1 << 16, y0 | y1 << 16); 0 = no tiles.
+__device__ __forceinline__ uint2 pack_rect(const Projected &pr) {
+    return pr.tiles ? make_uint2((uint32_t)pr.rect.x0 | ((uint32_t)pr.rect.x1 << 16),
+                                 (uint32_t)pr.rect.y0 | ((uint32_t)pr.rect.y1 << 16))
+                    : make_uint2(0u, 0u);
+}
 
 template <int DEG>
 __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
@@ -276,6 +287,19 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
             A.lp_oq[i] = make_uint2(__float_as_uint(pr.r1.x), pack2(pr.r1.y, pr.r1.z, A.lp_dtype));
             A.lp_gb[i] = pack2(pr.r1.w, pr.r2.x, A.lp_dtype);
         }
+    }
+    bool mv = false;
+    if (A.prect && i < A.P.n) {
+        const uint2 nr = pack_rect(pr);
+        A.prect[i] = nr;
+        if (A.prev_rect) {
+            const uint2 orr = A.prev_rect[i];
+            mv = nr.x != orr.x || nr.y != orr.y;
+        }
+    }
+    if (A.prev_rect) {
+        const uint32_t wm = __ballot_sync(0xffffffffu, mv);
+        if (lane == 0 && wm) atomicAdd(A.moved, (unsigned long long)__popc(wm));
     }
     const uint32_t t = pr.tiles, v = t != 0u;
     uint32_t it = t, iv = v;
@@ -321,6 +345,105 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
         A.dsc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
     }
     if (tid == 0) A.counts[3] = __ldcg(A.packed) >> 33;
+}
+
+// ---------------------------------------------------------------------------
+// Temporal re-binning, projection step: projects every Gaussian as above,
+// writes its packed tile rect into `rect` and compares it with the previous
+// frame's (`prev_rect`). A Gaussian whose rect changed (including becoming
+// visible or culled) is "moved" and appended to the moved list; the per-tile
+// bookkeeping of moved Gaussians runs in gs_temporal.cu, spread over warps.
+// Counters: [0] visible << 33 | keys (as in project_list_kernel), [1] moved.
+// ---------------------------------------------------------------------------
+struct TemporalProjectArgs {
+    ProjectArgs P;
+    float4 *lp_geo;
+    uint2 *lp_oq;
+    uint32_t *lp_gb;
+    int lp_dtype;
+    const uint2 *prev_rect;        // n: previous frame's packed rects
+    uint2 *rect;                   // n: this frame's
+    uint8_t *moved;                // n: 1 if the rect changed
+    unsigned long long *items;     // work items of moved Gaussians: index << 32 | chunk
+    int64_t item_capacity;
+    unsigned long long *counters;  // zeroed
+    uint32_t *d_err;
+};
+
+// Tiles of a rect handled by one work item of the moved-Gaussian kernels.
+constexpr int kChunkTiles = 256;
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_temporal_kernel(const TemporalProjectArgs A) {
+    __shared__ uint32_t s_t[8], s_v[8], s_m[8], s_c[8];
+    __shared__ unsigned long long s_cbase;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+    Projected pr;
+    pr.tiles = 0;
+    if (i < A.P.n) pr = project_one<DEG>(A.P, A.P.cam, A.P.grid, i);
+    if (pr.tiles) {
+        float4 *out = A.P.records + 3 * i;
+        out[0] = pr.r0;
+        out[1] = pr.r1;
+        out[2] = pr.r2;
+        if (A.lp_geo) {
+            A.lp_geo[i] = pr.r0;
+            A.lp_oq[i] = make_uint2(__float_as_uint(pr.r1.x), pack2(pr.r1.y, pr.r1.z, A.lp_dtype));
+            A.lp_gb[i] = pack2(pr.r1.w, pr.r2.x, A.lp_dtype);
+        }
+    }
+    bool mv = false;
+    uint32_t chunks = 0;  // work items: one per kChunkTiles tiles of the larger rect
+    if (i < A.P.n) {
+        const uint2 nr = pack_rect(pr), orr = A.prev_rect[i];
+        mv = nr.x != orr.x || nr.y != orr.y;
+        A.rect[i] = nr;
+        A.moved[i] = mv ? 1 : 0;
+        if (mv) {
+            const uint32_t ow = (orr.x >> 16) - (orr.x & 0xffffu), oh = (orr.y >> 16) - (orr.y & 0xffffu);
+            const uint32_t t_old = ow * oh, t_new = pr.tiles;
+            const uint32_t t_max = t_old > t_new ? t_old : t_new;
+            chunks = t_max ? (t_max + kChunkTiles - 1) / kChunkTiles : 1u;
+        }
+    }
+    const uint32_t t = pr.tiles, v = t != 0u, m = mv;
+    uint32_t it = t, iv = v, im = m, ic = chunks;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, it, o);
+        const uint32_t b = __shfl_up_sync(0xffffffffu, iv, o);
+        const uint32_t c = __shfl_up_sync(0xffffffffu, im, o);
+        const uint32_t d = __shfl_up_sync(0xffffffffu, ic, o);
+        if (lane >= o) { it += a; iv += b; im += c; ic += d; }
+    }
+    if (lane == 31) { s_t[warp] = it; s_v[warp] = iv; s_m[warp] = im; s_c[warp] = ic; }
+    __syncthreads();
+    uint32_t pc = 0, bt = 0, bv = 0, bm = 0, bc = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < warp) pc += s_c[w];
+        bt += s_t[w];
+        bv += s_v[w];
+        bm += s_m[w];
+        bc += s_c[w];
+    }
+    if (tid == 0) {
+        if (bv) atomicAdd(A.counters, ((unsigned long long)bv << 33) | bt);
+        if (bm) atomicAdd(A.counters + 1, (unsigned long long)bm);
+        s_cbase = bc ? atomicAdd(A.counters + 2, (unsigned long long)bc) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long first = s_cbase + pc + ic - chunks;
+    for (uint32_t c = 0; c < chunks; ++c) {
+        if ((int64_t)(first + c) < A.item_capacity)
+            A.items[first + c] = ((unsigned long long)i << 32) | c;
+        else
+            atomicOr(A.d_err, kErrTemporal);
+    }
+}
+
+template <int DEG>
+void launch_project_temporal(const TemporalProjectArgs &A, unsigned blocks, cudaStream_t s) {
+    project_temporal_kernel<DEG><<<blocks, 256, 0, s>>>(A);
 }
 
 struct EntryScanArgs {
@@ -770,10 +893,11 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
                                   uint64_t *keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
-                                  const cudaEvent_t *marks) {
+                                  const cudaEvent_t *marks, uint2 *prect, const uint2 *prev_rect,
+                                  unsigned long long *moved) {
     // counts and the front-end counters start at zero; the tile sort's
     // scratch was zeroed by the caller.
-    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const FrontLayout L = front_layout(g.n, capacity);
     char *base = static_cast<char *>(scan_scratch);
@@ -793,6 +917,9 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     A.lvals = reinterpret_cast<uint32_t *>(base + L.lvals);
     A.dsc = gs_sort_carve_digits(base + L.dsort, g.n, 0, kDepthPasses, kDepthItems);
     A.counts = counts;
+    A.prect = prect;
+    A.prev_rect = prect ? prev_rect : nullptr;
+    A.moved = moved;
     const unsigned blocks = (unsigned)((g.n + 255) / 256);
     switch (g.sh_degree) {
         case 0: project_list_kernel<0><<<blocks, 256, 0, s>>>(A); break;
@@ -832,6 +959,38 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     // their ticket).
     gs_carveout(emit_keys_kernel);
     emit_keys_kernel<<<(unsigned)((capacity + kKeyBlock - 1) / kKeyBlock), 256, 0, s>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_project_temporal(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
+                                       gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
+                                       int lp_dtype, const uint2 *prev_rect, uint2 *rect, uint8_t *moved,
+                                       unsigned long long *items, int64_t item_capacity,
+                                       unsigned long long *counters, uint32_t *d_err, cudaStream_t s) {
+    if (g.n == 0) return cudaSuccess;
+    TemporalProjectArgs A;
+    A.P = ProjectArgs{g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.n, cam, grid,
+                      reinterpret_cast<float4 *>(records), nullptr,
+                      reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
+                      reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
+    A.lp_geo = lp_dtype == GS_RECORD_F32 ? nullptr : lp_geo;
+    A.lp_oq = lp_oq;
+    A.lp_gb = lp_gb;
+    A.lp_dtype = lp_dtype;
+    A.prev_rect = prev_rect;
+    A.rect = rect;
+    A.moved = moved;
+    A.items = items;
+    A.item_capacity = item_capacity;
+    A.counters = counters;
+    A.d_err = d_err;
+    const unsigned blocks = (unsigned)((g.n + 255) / 256);
+    switch (g.sh_degree) {
+        case 0: launch_project_temporal<0>(A, blocks, s); break;
+        case 1: launch_project_temporal<1>(A, blocks, s); break;
+        case 2: launch_project_temporal<2>(A, blocks, s); break;
+        default: launch_project_temporal<3>(A, blocks, s); break;
+    }
     return cudaGetLastError();
 }
 

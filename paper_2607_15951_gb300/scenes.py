@@ -244,6 +244,44 @@ def random_poses(n_views: int, seed: int, radius: float = 2.0,
     return cams
 
 
+def _rot_y(deg: float) -> np.ndarray:
+    a = math.radians(deg)
+    return np.array([[math.cos(a), 0.0, math.sin(a)], [0.0, 1.0, 0.0], [-math.sin(a), 0.0, math.cos(a)]])
+
+
+def motion(kind: str, n_frames: int, width: int = 1920, height: int = 1080, step: float | None = None,
+           seed: int = 1005, fov_x_deg: float = 60.0) -> list[Camera]:
+    """Camera motions of the paper's churn experiment (Sec. 5.4), starting
+    from the identity camera (at the origin, looking +z):
+      'orbit'     about a target 4 m ahead, ``step`` degrees per frame (0.5);
+      'translate' sideways along +x, ``step`` metres per frame (0.01);
+      'rotate'    in place about the vertical axis, ``step`` degrees per frame (1);
+      'teleport'  an independent seeded pose every frame;
+      'static'    the same pose every frame."""
+    cams = []
+    rng = np.random.default_rng(seed)
+    target = np.array([0.0, 0.0, 4.0])
+    for f in range(n_frames):
+        if kind == "static":
+            w2c = look_at([0.0, 0.0, 0.0], [0.0, 0.0, 1.0])
+        elif kind == "orbit":
+            rot = _rot_y((0.5 if step is None else step) * f)
+            pos = target + rot @ np.array([0.0, 0.0, -4.0])
+            w2c = look_at(pos, target - pos)
+        elif kind == "translate":
+            w2c = look_at([(0.01 if step is None else step) * f, 0.0, 0.0], [0.0, 0.0, 1.0])
+        elif kind == "rotate":
+            w2c = look_at([0.0, 0.0, 0.0], _rot_y((1.0 if step is None else step) * f) @ np.array([0.0, 0.0, 1.0]))
+        elif kind == "teleport":
+            pos = rng.uniform(-2.0, 2.0, 3)
+            fwd = rng.standard_normal(3)
+            w2c = look_at(pos, fwd)
+        else:
+            raise KeyError(kind)
+        cams.append(pinhole(width, height, fov_x_deg, w2c))
+    return cams
+
+
 def l1_target(height: int, width: int, seed: int) -> np.ndarray:
     """Seeded random target image, U[0,1], HWC float32."""
     rng = np.random.default_rng(seed)
