@@ -369,6 +369,76 @@ def temporal(gs, torch, args, flush, local) -> dict:
             "motions": res}
 
 
+def imbalance_stress(gs, torch, args, flush, local) -> dict:
+    """The imbalance stress configuration: 6M Gaussians (20 % packed into 2 %
+    of the first view, 1 % splats above 256 px), SH3, 8 views at 3840x2160.
+    Forward: one gs_render_batch with BF16 records (autotuned tile) against 8
+    deferred per-view FP32 gs_render calls. Forward + backward: the 8 views
+    through the autograd wrapper with BF16 records and an L1 loss each."""
+    from paper_2607_15951_gb300 import _native as N
+    from paper_2607_15951_gb300 import scenes
+    scene, cams = scenes.workload("imbalance_6m_4k_x8")
+    g = gs.scene_to_device(scene)
+    ctx = gs.Context(local)
+    stream = torch.cuda.current_stream()
+    outs = gs.alloc_outputs(cams)
+    tile, tune_ms = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs, record_dtype=N.GS_RECORD_BF16)
+    iters = 3
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for i in range(iters):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / iters
+
+    ms_batch = timed(lambda: gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile,
+                                                record_dtype=N.GS_RECORD_BF16))
+    keys_batch = gs.gs_last_render_stats(ctx)["n_keys"]
+    k_max = 0
+    for c, o in zip(cams, outs):
+        gs.gs_render(ctx, g, scene.sh_degree, c, o["rgb"])
+        k_max = max(k_max, gs.gs_last_render_stats(ctx)["n_keys"])
+    gs.gs_reserve_keys(ctx, k_max + k_max // 4 + 1024)
+
+    def per_view():
+        for c, o in zip(cams, outs):
+            gs.gs_render(ctx, g, scene.sh_degree, c, o["rgb"], deferred=True)
+        gs.gs_sync_status(ctx)
+
+    ms_pv = timed(per_view)
+    params = [g[k].clone().requires_grad_(True) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    targets = [torch.from_numpy(scenes.l1_target(c.height, c.width, 1100 + i)).cuda() for i, c in enumerate(cams)]
+
+    def fwd_bwd_views():
+        for p in params:
+            p.grad = None
+        for c, tgt in zip(cams, targets):
+            rgb, _ = gs.RasterizeGaussians(*params, ctx, c, scene.sh_degree, record_dtype=N.GS_RECORD_BF16)
+            (rgb - tgt).abs().mean().backward()
+
+    ms_fb = timed(fwd_bwd_views)
+    ctx.close()
+    v = len(cams)
+    return {"workload": "imbalance_6m_4k_x8",
+            "description": "6M Gaussians (seed 4), 20% packed into 2% of view 0, 1% splats > 256 px, SH3, "
+                           "8 seeded poses at 3840x2160",
+            "batched_bf16_ms": round(ms_batch, 3), "batched_bf16_views_per_s": round(v / (ms_batch / 1e3), 2),
+            "per_view_f32_ms": round(ms_pv, 3), "per_view_f32_views_per_s": round(v / (ms_pv / 1e3), 2),
+            "speedup_batched_bf16_vs_per_view_f32": round(ms_pv / ms_batch, 3),
+            "fwd_bwd_bf16_ms_per_8_views": round(ms_fb, 3),
+            "fwd_bwd_note": "per view through RasterizeGaussians (BF16 records, FP32 compositing), L1 loss each",
+            "keys_per_batch": keys_batch, "autotuned_tile": list(tile),
+            "autotune_ms_16x16_16x8_8x8": [round(x, 3) for x in tune_ms], "iters": iters}
+
+
 def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:
     """Time the FP64 oracle on the host cores rendering whole frames of the
     same workload until about ``budget_s`` seconds have passed."""
@@ -431,6 +501,7 @@ def main():
     ap.add_argument("--no-fwd-bwd", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-temporal", action="store_true")
+    ap.add_argument("--no-imbalance", action="store_true")
     ap.add_argument("--blend-variant", type=int, default=0, help="0 culled (default), 1 basic")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -594,6 +665,8 @@ def main():
         line["batched"] = batched(gs, torch, args, flush, local)
     if not args.no_temporal:
         line["temporal"] = temporal(gs, torch, args, flush, local)
+    if not args.no_imbalance:
+        line["imbalance"] = imbalance_stress(gs, torch, args, flush, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cam)
     if rank == 0:

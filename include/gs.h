@@ -136,8 +136,18 @@ typedef struct {
                                GS_SYNC_DEFERRED, see gs_render                 */
     int32_t temporal;       /* gs_render: 1 = temporal re-binning, see
                                gs_render (needs GS_SYNC_FRAME)                 */
-    int32_t reserved[3];    /* must be zero                                    */
+    int32_t batch_mode;     /* gs_render_batch: GS_BATCH_AUTO (default),
+                               GS_BATCH_JOINT or GS_BATCH_PER_VIEW             */
+    int32_t reserved[2];    /* must be zero                                    */
 } gs_options;
+
+/* How gs_render_batch schedules the views. JOINT: one projection, one key
+ * sort and one persistent blend over all views (pays off for many short
+ * per-tile lists). PER_VIEW: the views one after another through the
+ * single-view pipeline, whose depth-first sort needs fewer digit passes over
+ * long key lists. AUTO: PER_VIEW after a batch that averaged more than 8M
+ * keys per view, JOINT otherwise. */
+enum { GS_BATCH_AUTO = 0, GS_BATCH_JOINT = 1, GS_BATCH_PER_VIEW = 2 };
 
 /* When gs_render checks a frame's key count (see gs_render). */
 enum { GS_SYNC_FRAME = 0, GS_SYNC_DEFERRED = 1 };

@@ -299,7 +299,7 @@ def _autograd_function():
     class _Rasterize(torch.autograd.Function):
         @staticmethod
         def forward(fctx, means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree, tile, bg,
-                    deferred):
+                    deferred, record_dtype):
             g = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
                  "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
                  "sh": sh.contiguous()}
@@ -308,21 +308,21 @@ def _autograd_function():
                    "final_T": torch.empty((H, W), dtype=torch.float32, device=means.device),
                    "n_contrib": torch.empty((H, W), dtype=torch.int32, device=means.device)}
             gs_render(ctx, g, sh_degree, cam, out["rgb"], out["final_T"], out["n_contrib"], None,
-                      tile=tile, bg=bg, deferred=deferred)
-            fctx.gs = (ctx, cam, sh_degree, tile, bg, g)
+                      tile=tile, bg=bg, deferred=deferred, record_dtype=record_dtype)
+            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype)
             fctx.save_for_backward(out["final_T"], out["n_contrib"])
             fctx.mark_non_differentiable(out["final_T"])
             return out["rgb"], out["final_T"]
 
         @staticmethod
         def backward(fctx, d_rgb, d_T):
-            ctx, cam, sh_degree, tile, bg, g = fctx.gs
+            ctx, cam, sh_degree, tile, bg, g, record_dtype = fctx.gs
             final_T, n_contrib = fctx.saved_tensors
             grads = {k: torch.empty_like(v) for k, v in g.items()}
             gs_render_backward(ctx, g, sh_degree, cam, final_T, n_contrib, d_rgb.contiguous(), grads,
-                               tile=tile, bg=bg)
+                               tile=tile, bg=bg, record_dtype=record_dtype)
             return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
-                    grads["sh"], None, None, None, None, None, None)
+                    grads["sh"], None, None, None, None, None, None, None)
 
     return _Rasterize
 
@@ -331,7 +331,7 @@ _RASTERIZE = None
 
 
 def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Context, cam, sh_degree: int,
-                       tile=(16, 16), bg=(0.0, 0.0, 0.0), deferred: bool = True):
+                       tile=(16, 16), bg=(0.0, 0.0, 0.0), deferred: bool = True, record_dtype: int = 0):
     """Differentiable render: returns (rgb (H,W,3), final_T (H,W)); gradients
     flow to the five parameter tensors. The backward of a render must run
     before the next render on the same context.
@@ -339,12 +339,14 @@ def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Contex
     deferred=True (default) renders with GS_SYNC_DEFERRED: the forward does
     not wait for the GPU; the backward checks the forward's key count and
     raises GSError (GS_ERR_CAPACITY) if that frame overflowed its buffers,
-    which have then grown, so the iteration can simply be repeated."""
+    which have then grown, so the iteration can simply be repeated.
+    record_dtype: precision of the blend records (GS_RECORD_F32 / F16 / BF16),
+    used by the forward and the backward blend alike."""
     global _RASTERIZE
     if _RASTERIZE is None:
         _RASTERIZE = _autograd_function()
     return _RASTERIZE.apply(means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree,
-                            tuple(tile), tuple(bg), bool(deferred))
+                            tuple(tile), tuple(bg), bool(deferred), int(record_dtype))
 
 
 # ---------------------------------------------------------------------------
@@ -374,10 +376,13 @@ def alloc_outputs(cams, aux: bool = False, device="cuda") -> list:
 
 
 def gs_render_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, tile=(16, 16),
-                    bg=(0.0, 0.0, 0.0), record_dtype: int = 0, direct: bool = False, stream=None):
+                    bg=(0.0, 0.0, 0.0), record_dtype: int = 0, direct: bool = False,
+                    batch_mode: int = 0, stream=None):
+    """batch_mode: N.GS_BATCH_AUTO (0), GS_BATCH_JOINT (1) or GS_BATCH_PER_VIEW (2)."""
     gs = gaussians_struct(g, sh_degree)
     o = options_struct(tile, bg, record_dtype)
     o.direct_launch = 1 if direct else 0
+    o.batch_mode = int(batch_mode)
     carr, farr = _cams_fbs(cams, outs)
     ctx.check(_lib().gs_render_batch(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
                                      _stream(stream)))

@@ -26,6 +26,9 @@ GS_BLEND_CULLED = 0
 GS_BLEND_BASIC = 1
 GS_SYNC_FRAME = 0
 GS_SYNC_DEFERRED = 1
+GS_BATCH_AUTO = 0
+GS_BATCH_JOINT = 1
+GS_BATCH_PER_VIEW = 2
 NOALLOC_SORT_MAX_PAIRS = 262144  # GS_NOALLOC_SORT_MAX_PAIRS in include/gs.h
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_CAPACITY", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}
@@ -67,7 +70,8 @@ class gs_options(ctypes.Structure):
                 ("bg", ctypes.c_float * 3), ("record_dtype", ctypes.c_int32),
                 ("blend_variant", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
                 ("sync_mode", ctypes.c_int32), ("temporal", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("batch_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class gs_render_stats(ctypes.Structure):

@@ -45,6 +45,7 @@ struct gs_context {
         cudaGraphExec_t exec = nullptr;
         cudaStream_t capture = nullptr;  // the graph is captured here, launched on the caller's stream
         std::vector<int64_t> sig;  // what the captured graph was built for
+        int64_t keys_per_view = 0;  // of the last batch (chooses GS_BATCH_AUTO's schedule)
     } batch;
     int last_dtype = GS_RECORD_F32;
     int64_t key_capacity = 0;  // pairs the render path's key buffers hold
@@ -154,7 +155,9 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
     if (o->temporal != 0 && o->temporal != 1) return fail(ctx, GS_ERR_INVALID_ARG, "temporal must be 0 or 1");
     if (o->temporal && o->sync_mode != GS_SYNC_FRAME)
         return fail(ctx, GS_ERR_INVALID_ARG, "temporal re-binning needs sync_mode GS_SYNC_FRAME");
-    for (int i = 0; i < 3; ++i)
+    if (o->batch_mode < GS_BATCH_AUTO || o->batch_mode > GS_BATCH_PER_VIEW)
+        return fail(ctx, GS_ERR_INVALID_ARG, "batch_mode must be GS_BATCH_AUTO, _JOINT or _PER_VIEW");
+    for (int i = 0; i < 2; ++i)
         if (o->reserved[i] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
@@ -371,6 +374,8 @@ gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *ti
 // while few tiles change (measured break-even near 10 % on a 1M-Gaussian
 // 1080p scene).
 constexpr double kTemporalMaxChurn = 0.08;
+// GS_BATCH_AUTO renders views one by one after a batch with more keys per view.
+constexpr int64_t kBatchPerViewKeys = int64_t(8) << 20;
 // Largest tile list the per-tile merge holds in shared memory (a power of two).
 constexpr int kTemporalTileCap = 4096;
 
@@ -872,10 +877,12 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
                                ? (double)ctx->h_counts[4] / (double)ctx->stats.n_visible
                                : 0.0;
         }
-        // Keep about 25 % headroom over this frame's count for the next one
-        // (the buffers themselves only grow).
-        if (!temporal && !ctx->pinned_capacity && (int64_t)K * 2 < cap)
-            ctx->key_capacity = std::max<int64_t>(65536, (int64_t)(K + K / 4 + 1024));
+        // The sort grids cover the capacity: when it is far above this frame's
+        // count, bring it down to twice the count (the buffers themselves only
+        // grow). A smaller margin would make the next frame of a larger view
+        // overflow, which deferred frames report as an error.
+        if (!temporal && !ctx->pinned_capacity && (int64_t)K * 4 < cap)
+            ctx->key_capacity = std::max<int64_t>(65536, (int64_t)(2 * K + 1024));
         if (*ctx->h_err) return collect_device_error(ctx, s);
         return GS_OK;
     }
@@ -981,6 +988,26 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto &B = ctx->batch;
     const int64_t n = g->n;
+    const bool per_view = opts->batch_mode == GS_BATCH_PER_VIEW ||
+                          (opts->batch_mode == GS_BATCH_AUTO && B.keys_per_view > kBatchPerViewKeys);
+    if (per_view) {
+        gs_options o = *opts;
+        o.sync_mode = GS_SYNC_FRAME;
+        o.temporal = 0;
+        o.batch_mode = GS_BATCH_AUTO;
+        int64_t keys = 0, visible = 0, tiles = 0;
+        for (int v = 0; v < n_views; ++v) {
+            if ((st = gs_render(ctx, g, &cams[v], &o, &fbs[v], stream)) != GS_OK) return st;
+            keys += ctx->stats.n_keys;
+            visible += ctx->stats.n_visible;
+            tiles += ctx->stats.n_tiles;
+        }
+        ctx->stats.n_keys = keys;
+        ctx->stats.n_visible = visible;
+        ctx->stats.n_tiles = (int32_t)tiles;
+        B.keys_per_view = keys / n_views;
+        return GS_OK;
+    }
     // Host view table (pinned, read by the frame's first copy).
     if (B.h_views_cap < n_views) {
         if (B.h_views) cudaFreeHost(B.h_views);
@@ -1084,6 +1111,7 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
             if ((int64_t)nv > rc) B.rec_cap = (int64_t)(nv + nv / 4 + 4096);
             continue;
         }
+        B.keys_per_view = (int64_t)K / n_views;
         if (*ctx->h_err) return collect_device_error(ctx, s);
         return GS_OK;
     }

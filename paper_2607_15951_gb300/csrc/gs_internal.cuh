@@ -306,11 +306,12 @@ struct GsSortScratch {
 size_t gs_sort_scratch_bytes(int64_t n, int key_bits);
 GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits);
 // Scratch for `passes` digit passes starting at digit `digit0`, with
-// partitions of 256 x items pairs (items 8 suits short lists: shorter
-// per-partition latency).
-size_t gs_sort_scratch_bytes_digits(int64_t n, int passes, int items = GS_SORT_ITEMS);
-GsSortScratch gs_sort_carve_digits(void *base, int64_t n_capacity, int digit0, int passes,
-                                   int items = GS_SORT_ITEMS);
+// partitions of 256 x items pairs: 8 (short lists: shorter per-partition
+// latency), GS_SORT_ITEMS, 12 (long lists, three blocks per SM), or 0 to
+// choose by capacity (gs_sort_items_for).
+int gs_sort_items_for(int64_t n_capacity);
+size_t gs_sort_scratch_bytes_digits(int64_t n, int passes, int items = 0);
+GsSortScratch gs_sort_carve_digits(void *base, int64_t n_capacity, int digit0, int passes, int items = 0);
 int gs_sort_passes(int key_bits);
 // Sorts (keys, values) using (alt_keys, alt_values) as the ping-pong pair;
 // *result_in_alt tells which pair holds the result. Zeroes the scratch and

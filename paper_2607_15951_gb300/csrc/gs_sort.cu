@@ -26,6 +26,8 @@ using namespace gs;
 constexpr int kThreads = kSortThreads;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = GS_SORT_ITEMS;     // items per thread of the default variant
+constexpr int kLargeItems = 12;           // ... of the variant for long lists
+constexpr int64_t kLargeSortPairs = int64_t(1) << 23;  // capacities from here on use it
 constexpr int kLookAhead = GS_SORT_LOOKAHEAD;  // status words read per look-back step
 constexpr int kRadix = 256;
 constexpr int kMaxPasses = 8;
@@ -85,8 +87,8 @@ histogram_kernel(const uint64_t *__restrict__ keys, int64_t n, int passes, SortS
     }
 }
 
-template <int ITEMS>
-__global__ void __launch_bounds__(kThreads, GS_SORT_MIN_BLOCKS)
+template <int ITEMS, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kThreads, MIN_BLOCKS)
 onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n_host,
                 const unsigned long long *d_n, int pass, int64_t parts, SortScratch sc,
@@ -245,12 +247,16 @@ GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits) {
     return gs_sort_carve_digits(base, n_capacity, 0, gs_sort_passes(key_bits));
 }
 
+int gs_sort_items_for(int64_t n) { return n >= kLargeSortPairs ? kLargeItems : kItems; }
+
 size_t gs_sort_scratch_bytes_digits(int64_t n, int passes, int items) {
+    if (items == 0) items = gs_sort_items_for(n);
     const int64_t parts = num_parts(n, items) > 0 ? num_parts(n, items) : 1;
     return header_bytes(passes) + (size_t)passes * parts * kRadix * sizeof(unsigned long long);
 }
 
 GsSortScratch gs_sort_carve_digits(void *base, int64_t n_capacity, int digit0, int passes, int items) {
+    if (items == 0) items = gs_sort_items_for(n_capacity);
     char *p = static_cast<char *>(base);
     GsSortScratch s;
     s.hist = reinterpret_cast<uint32_t *>(p);
@@ -271,13 +277,19 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
                                   unsigned long long timeout_ns, int max_passes) {
     *result_in_alt = false;
-    if (sc.items != 8 && sc.items != kItems) return cudaErrorInvalidValue;
-    const bool small = sc.items == 8 && kItems != 8;
-    const size_t smem = small ? onesweep_smem<8>() : onesweep_smem<kItems>();
-    cudaError_t e = small ? cudaFuncSetAttribute(onesweep_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem)
-                          : cudaFuncSetAttribute(onesweep_kernel<kItems>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // Three partition shapes: 8 items per thread for short lists (shorter
+    // per-partition latency), GS_SORT_ITEMS (16) by default, 12 items with
+    // three blocks per SM for long lists (more partitions in flight).
+    if (sc.items != 8 && sc.items != kItems && sc.items != kLargeItems) return cudaErrorInvalidValue;
+    const int shape = sc.items == kLargeItems && kLargeItems != kItems ? 2 : (sc.items == 8 && kItems != 8 ? 0 : 1);
+    const size_t smem = shape == 0 ? onesweep_smem<8>() : shape == 2 ? onesweep_smem<kLargeItems>()
+                                                                     : onesweep_smem<kItems>();
+    cudaError_t e = shape == 0   ? cudaFuncSetAttribute(onesweep_kernel<8, GS_SORT_MIN_BLOCKS>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                    : shape == 2 ? cudaFuncSetAttribute(onesweep_kernel<kLargeItems, 3>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                                 : cudaFuncSetAttribute(onesweep_kernel<kItems, GS_SORT_MIN_BLOCKS>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t *kin = keys;
     const uint32_t *vin = values;
@@ -285,11 +297,14 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
     uint32_t *vout = alt_values;
     const int passes = sc.passes < max_passes ? sc.passes : max_passes;
     for (int pass = 0; pass < passes; ++pass) {
-        if (small)
-            onesweep_kernel<8><<<(unsigned)sc.parts, kThreads, smem, s>>>(kin, vin, kout, vout, n_capacity, d_n,
-                                                                           pass, sc.parts, sc, d_err, timeout_ns);
+        if (shape == 0)
+            onesweep_kernel<8, GS_SORT_MIN_BLOCKS><<<(unsigned)sc.parts, kThreads, smem, s>>>(
+                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
+        else if (shape == 2)
+            onesweep_kernel<kLargeItems, 3><<<(unsigned)sc.parts, kThreads, smem, s>>>(
+                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
         else
-            onesweep_kernel<kItems><<<(unsigned)sc.parts, kThreads, smem, s>>>(
+            onesweep_kernel<kItems, GS_SORT_MIN_BLOCKS><<<(unsigned)sc.parts, kThreads, smem, s>>>(
                 kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

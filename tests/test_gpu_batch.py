@@ -89,3 +89,17 @@ def test_batch_matches_oracle(ctx, oracle_mod):
         keep = ~img.flag.astype(bool)
         err = np.abs(o["rgb"].cpu().numpy().astype(np.float64) - img.rgb)[keep].max()
         assert err <= 1e-3, err
+
+
+@pytest.mark.parametrize("mode", [N.GS_BATCH_JOINT, N.GS_BATCH_PER_VIEW], ids=["joint", "per_view"])
+def test_batch_schedules_agree(ctx, mode):
+    scene = scenes.clustered(60_000, 25, box=5.0)
+    cams = scenes.trajectory(5, 1025, radius=2.0, sizes=((256, 144), (200, 120)))
+    g = gs.scene_to_device(scene)
+    ref = per_view(ctx, g, scene.sh_degree, cams, record_dtype=N.GS_RECORD_BF16)
+    outs = gs.alloc_outputs(cams, aux=True)
+    gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, record_dtype=N.GS_RECORD_BF16, batch_mode=mode)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, ref):
+        for k in ("rgb", "final_T", "n_contrib", "n_eval"):
+            assert torch.equal(a[k], b[k]), k
