@@ -502,7 +502,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-temporal", action="store_true")
     ap.add_argument("--no-imbalance", action="store_true")
-    ap.add_argument("--blend-variant", type=int, default=0, help="0 culled (default), 1 basic")
+    ap.add_argument("--blend-variant", type=int, default=0,
+                    help="0 culled 8x4 blocks (default), 1 basic, 2 culled 16x8, 3 culled tile, 4 culled 8x8")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -108,11 +108,19 @@ typedef struct {
     int32_t *n_eval;
 } gs_framebuffer;
 
-/* Blend schedules; both produce identical outputs.
- *   GS_BLEND_CULLED  each warp owns an 8x8 pixel block and skips records whose
- *                    conservative alpha >= 1/255 box misses it (default)
- *   GS_BLEND_BASIC   one thread per pixel evaluates every record of its tile */
-enum { GS_BLEND_CULLED = 0, GS_BLEND_BASIC = 1 };
+/* Blend schedules; all produce identical outputs.
+ *   GS_BLEND_CULLED       each warp owns an 8x4 pixel block and skips records
+ *                         whose conservative alpha >= 1/255 box misses it
+ *                         (default)
+ *   GS_BLEND_BASIC        one thread per pixel evaluates every record of its
+ *                         tile
+ *   GS_BLEND_CULLED_WIDE  as CULLED with 16x8 blocks (16-wide tiles; 8x8
+ *                         tiles use 8x4 blocks)
+ *   GS_BLEND_CULLED_TILE  as CULLED with one warp per 16x16 tile (other
+ *                         tiles use 8x4 blocks)
+ *   GS_BLEND_CULLED_8X8   as CULLED with 8x8 blocks */
+enum { GS_BLEND_CULLED = 0, GS_BLEND_BASIC = 1, GS_BLEND_CULLED_WIDE = 2, GS_BLEND_CULLED_TILE = 3,
+       GS_BLEND_CULLED_8X8 = 4 };
 
 /* Precision of the projected records the blend reads (gs_render,
  * gs_render_backward, gs_render_batch). With F16 / BF16 the opacity and the
@@ -129,7 +137,8 @@ typedef struct {
     int32_t tile_w, tile_h; /* screen tile: 16x16 (default), 16x8 or 8x8      */
     float bg[3];            /* background colour added as T_final * bg         */
     int32_t record_dtype;   /* GS_RECORD_F32 (default), _F16 or _BF16          */
-    int32_t blend_variant;  /* GS_BLEND_CULLED (default) or GS_BLEND_BASIC     */
+    int32_t blend_variant;  /* GS_BLEND_CULLED (default), _BASIC, _CULLED_WIDE,
+                               _CULLED_TILE, _CULLED_8X8                       */
     int32_t direct_launch;  /* gs_render_batch: 0 = replay a captured CUDA graph
                                (default), 1 = launch the kernels directly      */
     int32_t sync_mode;      /* gs_render: GS_SYNC_FRAME (default) or

@@ -24,6 +24,9 @@ GS_RECORD_F16 = 1
 GS_RECORD_BF16 = 2
 GS_BLEND_CULLED = 0
 GS_BLEND_BASIC = 1
+GS_BLEND_CULLED_WIDE = 2
+GS_BLEND_CULLED_TILE = 3
+GS_BLEND_CULLED_8X8 = 4
 GS_SYNC_FRAME = 0
 GS_SYNC_DEFERRED = 1
 GS_BATCH_AUTO = 0

@@ -395,13 +395,16 @@ def test_blend_variants_identical(ctx, name, make, tile):
     scene, cam = make()
     g = gs.scene_to_device(scene)
     outs = []
-    for variant in (gs._native.GS_BLEND_BASIC, gs._native.GS_BLEND_CULLED):
+    N_ = gs._native
+    for variant in (N_.GS_BLEND_BASIC, N_.GS_BLEND_CULLED, N_.GS_BLEND_CULLED_WIDE, N_.GS_BLEND_CULLED_TILE,
+                    N_.GS_BLEND_CULLED_8X8):
         out = gs.render(ctx, g, scene.sh_degree, cam, tile=tile, variant=variant)
         torch.cuda.synchronize()
         outs.append({k: v.cpu().numpy() for k, v in out.items()})
     gs.gs_sync_status(ctx)
-    for k in ("rgb", "final_T", "n_contrib", "n_eval"):
-        assert np.array_equal(outs[0][k], outs[1][k]), k
+    for o in outs[1:]:
+        for k in ("rgb", "final_T", "n_contrib", "n_eval"):
+            assert np.array_equal(outs[0][k], o[k]), k
 
 
 def test_render_regrows_key_buffers(oracle_mod):
