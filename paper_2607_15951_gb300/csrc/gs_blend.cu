@@ -49,10 +49,11 @@ __device__ __forceinline__ float ex2(float x) {
 }
 
 // Shared-memory form of one record.
+// The alpha test reads only a and b; col is read for the pairs that pass it.
 struct SRec {
     float4 *a;    // (u, v, A, B)
-    float4 *b;    // (C, opacity, thr, blue)
-    float2 *rg;   // (red, green)
+    float2 *b;    // (C, thr)
+    float4 *col;  // (opacity, red, green, blue)
     float4 *box;  // (x0, x1, y0, y1) pixel-centre box where alpha can reach 1/255
 };
 
@@ -66,8 +67,8 @@ __device__ __forceinline__ void stage_record(const RecordReader &rd, uint32_t g,
     const float A = -0.5f * kLog2e * q00, B = -kLog2e * q01, C = -0.5f * kLog2e * q11;
     const float thr = -log2f(255.f * o);
     S.a[s] = make_float4(r0.x, r0.y, A, B);
-    S.b[s] = make_float4(C, o, thr, blue);
-    S.rg[s] = make_float2(r1.z, r1.w);
+    S.b[s] = make_float2(C, thr);
+    S.col[s] = make_float4(o, r1.z, r1.w, blue);
     if (!want_box) return;
     // alpha >= 1/255 needs (1/2) d^T Q d <= L = ln(255 o). The axis-aligned
     // box of that ellipse has half-widths sqrt(2 L Sigma00), sqrt(2 L Sigma11)
@@ -104,10 +105,11 @@ struct Pix {
 
 // One (pixel, record) step of Eq. 1 with the standard rules; e = exponent in
 // base 2. Returns after updating the pixel.
-__device__ __forceinline__ void composite(Pix &p, float e, float o, float thr, float cr, float cg,
-                                          float cb, int32_t pos) {
+__device__ __forceinline__ void composite(Pix &p, float e, float thr, const float4 *col, int32_t pos) {
     if (e > 0.f || e < thr) return;  // power > 0, or alpha < 1/255
-    const float alpha = fminf(kAlphaMax, o * ex2(e));
+    const float4 c = *col;           // opacity, red, green, blue
+    const float cr = c.y, cg = c.z, cb = c.w;
+    const float alpha = fminf(kAlphaMax, c.x * ex2(e));
     const float Tn = p.T * (1.f - alpha);
     if (Tn < kTMin) {
         p.done = true;
@@ -145,9 +147,9 @@ __device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) 
     constexpr int kRows = 32 / BW;     // rows covered by the warp's lanes at once
     constexpr int kNP = BW * BH / 32;  // pixels per lane
     static_assert(kNP >= 1 && kRows * kNP == BH, "block shape");
-    __shared__ float4 s_a[kBatch], s_b[kBatch], s_box[kBatch];
-    __shared__ float2 s_rg[kBatch];
-    const SRec S{s_a, s_b, s_rg, s_box};
+    __shared__ float4 s_a[kBatch], s_col[kBatch], s_box[kBatch];
+    __shared__ float2 s_b[kBatch];
+    const SRec S{s_a, s_b, s_col, s_box};
 
     const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -190,16 +192,14 @@ __device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) 
                     const int jj = c + __ffs(bits) - 1;
                     bits &= bits - 1;
                     const float4 ra = s_a[jj];
-                    const float4 rb = s_b[jj];
-                    const float2 rg = s_rg[jj];
+                    const float2 rb = s_b[jj];
                     const float dx = fx - ra.x;
                     const float adx2 = ra.z * dx * dx, bdx = ra.w * dx;
 #pragma unroll
                     for (int q = 0; q < kNP; ++q) {
                         if (!p[q].done) {
                             const float dy = (float)(py_base + q * kRows) + 0.5f - ra.y;
-                            composite(p[q], fmaf(dy, fmaf(rb.x, dy, bdx), adx2), rb.y, rb.z, rg.x, rg.y,
-                                      rb.w, pos0 + jj);
+                            composite(p[q], fmaf(dy, fmaf(rb.x, dy, bdx), adx2), rb.y, &s_col[jj], pos0 + jj);
                         }
                     }
                 }
@@ -265,9 +265,9 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(c
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) {
     constexpr int kN = TW * TH;
-    __shared__ float4 s_a[kBatch], s_b[kBatch];
-    __shared__ float2 s_rg[kBatch];
-    const SRec S{s_a, s_b, s_rg, nullptr};
+    __shared__ float4 s_a[kBatch], s_col[kBatch];
+    __shared__ float2 s_b[kBatch];
+    const SRec S{s_a, s_b, s_col, nullptr};
 
     const int tile = blockIdx.x;
     const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
@@ -288,11 +288,10 @@ __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) 
         const int32_t pos0 = (int32_t)(start - first) + 1;
         for (int j = 0; j < cnt && !p.done; ++j) {
             const float4 ra = s_a[j];
-            const float4 rb = s_b[j];
-            const float2 rg = s_rg[j];
+            const float2 rb = s_b[j];
             const float dx = fx - ra.x, dy = fy - ra.y;
             const float e = fmaf(dy, fmaf(rb.x, dy, ra.w * dx), ra.z * dx * dx);
-            composite(p, e, rb.y, rb.z, rg.x, rg.y, rb.w, pos0 + j);
+            composite(p, e, rb.y, &s_col[j], pos0 + j);
         }
     }
     if (!p.done) p.eval = (int32_t)(last - first);
@@ -423,10 +422,12 @@ struct PixB {
 
 // One backward step of a pixel at list position pos; adds the record's
 // gradients into acc (9 slots).
-__device__ __forceinline__ bool composite_bwd(PixB &p, float e, float o, float thr, float cr, float cg,
-                                              float cb, float dx, float dy, float q00, float q01,
-                                              float q11, const float bg[3], float acc[16]) {
+__device__ __forceinline__ bool composite_bwd(PixB &p, float e, float thr, const float4 *col, float dx, float dy,
+                                              float q00, float q01, float q11, const float bg[3],
+                                              float acc[16]) {
     if (e > 0.f || e < thr) return false;
+    const float4 c4 = *col;  // opacity, red, green, blue
+    const float o = c4.x, cr = c4.y, cg = c4.z, cb = c4.w;
     const float G = ex2(e);
     const float raw = o * G;
     const float alpha = fminf(kAlphaMax, raw);
@@ -457,12 +458,12 @@ template <int TW, int TH, int BW, int BH>
 __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32) blend_bwd_kernel(const BlendBwdArgs a) {
     constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
     constexpr int kRows = 32 / BW, kNP = BW * BH / 32;  // rows per lane step, pixels per lane
-    __shared__ float4 s_a[kBatch], s_b[kBatch], s_box[kBatch];
-    __shared__ float2 s_rg[kBatch];
+    __shared__ float4 s_a[kBatch], s_col[kBatch], s_box[kBatch];
+    __shared__ float2 s_b[kBatch];
     __shared__ float s_grad[kBatch * 9];
     __shared__ uint32_t s_g[kBatch];
     __shared__ int s_maxlast;
-    const SRec S{s_a, s_b, s_rg, s_box};
+    const SRec S{s_a, s_b, s_col, s_box};
 
     const int tile = blockIdx.x;
     const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
@@ -530,8 +531,7 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32) blend_bwd_kernel(c
                     const int jj = c + hb;
                     const int pos = beg + jj + 1;
                     const float4 ra = s_a[jj];
-                    const float4 rb = s_b[jj];
-                    const float2 rg = s_rg[jj];
+                    const float2 rb = s_b[jj];
                     const float q00 = -2.f * kLn2 * ra.z, q01 = -kLn2 * ra.w, q11 = -2.f * kLn2 * rb.x;
                     const float dx = fx - ra.x;
                     const float adx2 = ra.z * dx * dx, bdx = ra.w * dx;
@@ -544,8 +544,7 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32) blend_bwd_kernel(c
                         if (pos > p[q].last) continue;
                         const float dy = fy[q] - ra.y;
                         const float e = fmaf(dy, fmaf(rb.x, dy, bdx), adx2);
-                        any |= composite_bwd(p[q], e, rb.y, rb.z, rg.x, rg.y, rb.w, dx, dy, q00, q01, q11,
-                                             a.bg, acc);
+                        any |= composite_bwd(p[q], e, rb.y, &s_col[jj], dx, dy, q00, q01, q11, a.bg, acc);
                     }
                     if (__any_sync(0xffffffffu, any)) {
                         const float v = warp_sum9(acc, lane);
