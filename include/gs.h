@@ -118,9 +118,15 @@ typedef struct {
  *                         tiles use 8x4 blocks)
  *   GS_BLEND_CULLED_TILE  as CULLED with one warp per 16x16 tile (other
  *                         tiles use 8x4 blocks)
- *   GS_BLEND_CULLED_8X8   as CULLED with 8x8 blocks */
+ *   GS_BLEND_CULLED_8X8   as CULLED with 8x8 blocks
+ *   GS_BLEND_TMA          gs_render only (gs_blend falls back to CULLED): the
+ *                         records of the sorted lists are first gathered in
+ *                         list order, then each tile's batches are staged in
+ *                         shared memory with bulk copies (cp.async.bulk,
+ *                         double-buffered, mbarrier completion) and blended as
+ *                         CULLED */
 enum { GS_BLEND_CULLED = 0, GS_BLEND_BASIC = 1, GS_BLEND_CULLED_WIDE = 2, GS_BLEND_CULLED_TILE = 3,
-       GS_BLEND_CULLED_8X8 = 4 };
+       GS_BLEND_CULLED_8X8 = 4, GS_BLEND_TMA = 5 };
 
 /* Precision of the projected records the blend reads (gs_render,
  * gs_render_backward, gs_render_batch). With F16 / BF16 the opacity and the
@@ -138,7 +144,7 @@ typedef struct {
     float bg[3];            /* background colour added as T_final * bg         */
     int32_t record_dtype;   /* GS_RECORD_F32 (default), _F16 or _BF16          */
     int32_t blend_variant;  /* GS_BLEND_CULLED (default), _BASIC, _CULLED_WIDE,
-                               _CULLED_TILE, _CULLED_8X8                       */
+                               _CULLED_TILE, _CULLED_8X8, _TMA                 */
     int32_t direct_launch;  /* gs_render_batch: 0 = replay a captured CUDA graph
                                (default), 1 = launch the kernels directly      */
     int32_t sync_mode;      /* gs_render: GS_SYNC_FRAME (default) or

@@ -27,6 +27,7 @@ GS_BLEND_BASIC = 1
 GS_BLEND_CULLED_WIDE = 2
 GS_BLEND_CULLED_TILE = 3
 GS_BLEND_CULLED_8X8 = 4
+GS_BLEND_TMA = 5
 GS_SYNC_FRAME = 0
 GS_SYNC_DEFERRED = 1
 GS_BATCH_AUTO = 0

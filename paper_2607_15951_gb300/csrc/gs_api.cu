@@ -51,6 +51,7 @@ struct gs_context {
     int64_t key_capacity = 0;  // pairs the render path's key buffers hold
     bool pinned_capacity = false;  // set by gs_reserve_keys: do not shrink
     DevBuf fused_scratch;
+    DevBuf gathered;  // records in list order (GS_BLEND_TMA)
     bool timing = false;
     bool timed_once = false;
     cudaEvent_t ev[8] = {};
@@ -146,7 +147,7 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
     if (!ok_tile) return fail(ctx, GS_ERR_INVALID_ARG, "tile must be 16x16, 16x8 or 8x8");
     if (o->record_dtype != GS_RECORD_F32 && o->record_dtype != GS_RECORD_F16 && o->record_dtype != GS_RECORD_BF16)
         return fail(ctx, GS_ERR_INVALID_ARG, "record_dtype must be GS_RECORD_F32, _F16 or _BF16");
-    if (o->blend_variant < GS_BLEND_CULLED || o->blend_variant > GS_BLEND_CULLED_8X8)
+    if (o->blend_variant < GS_BLEND_CULLED || o->blend_variant > GS_BLEND_TMA)
         return fail(ctx, GS_ERR_INVALID_ARG, "blend_variant must be one of the GS_BLEND_* schedules");
     if (o->direct_launch != 0 && o->direct_launch != 1)
         return fail(ctx, GS_ERR_INVALID_ARG, "direct_launch must be 0 or 1");
@@ -378,6 +379,23 @@ int blend_schedule(const gs_context *ctx, const gs_options *opts, int n_tiles) {
     return ctx->stats.n_keys > (int64_t)1024 * n_tiles ? GS_BLEND_CULLED_8X8 : GS_BLEND_CULLED;
 }
 
+// The blend of a gs_render frame with `d_n` (device count, at most n_cap)
+// pairs in its lists.
+gs_status launch_blend(gs_context *ctx, const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                       const GsGrid &grid, const gs_camera *cam, const gs_options *opts, const gs_framebuffer *fb,
+                       const unsigned long long *d_n, int64_t n_cap, cudaStream_t s) {
+    const int variant = blend_schedule(ctx, opts, grid.tiles_x * grid.tiles_y);
+    if (variant == GS_BLEND_TMA) {
+        gs_status st = ensure(ctx, ctx->gathered, (size_t)(n_cap > 0 ? n_cap : 1) * 48, "gathered records");
+        if (st != GS_OK) return st;
+        GS_CUDA(ctx, gs_launch_blend_tma(rd, values, ranges, grid, cam->width, cam->height, opts->bg, *fb,
+                                         static_cast<float4 *>(ctx->gathered.ptr), d_n, n_cap, ctx->d_err, s));
+        return GS_OK;
+    }
+    GS_CUDA(ctx, gs_launch_blend(rd, values, ranges, grid, cam->width, cam->height, opts->bg, *fb, variant, s));
+    return GS_OK;
+}
+
 // Above this fraction of moved Gaussians (of the visible ones) in the last
 // frame, the next frame is binned from scratch: re-binning pays off only
 // while few tiles change (measured break-even near 10 % on a 1M-Gaussian
@@ -473,8 +491,9 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     GS_CUDA(ctx, gs_launch_temporal_rebin(R, s));
     mark(ctx, EV_SORT, s);
     mark(ctx, EV_RANGES, s);
-    GS_CUDA(ctx, gs_launch_blend(reader(ctx, rec, dtype), vals, ranges, grid, cam->width, cam->height, opts->bg,
-                                 *fb, blend_schedule(ctx, opts, n_tiles), s));
+    if ((st = launch_blend(ctx, reader(ctx, rec, dtype), vals, ranges, grid, cam, opts, fb, counters + 3, cap, s)) !=
+        GS_OK)
+        return st;
     mark(ctx, EV_BLEND, s);
     unsigned long long *h = ctx->h_ring;  // no deferred frame is in flight (drained before)
     h[5] = 0;
@@ -567,7 +586,7 @@ void gs_destroy(gs_context *ctx) {
     DeviceGuard g(ctx->device);
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                       &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
-                      &ctx->fused_scratch, &ctx->d_rec, &ctx->lp_geo, &ctx->lp_oq, &ctx->lp_gb};
+                      &ctx->fused_scratch, &ctx->d_rec, &ctx->lp_geo, &ctx->lp_oq, &ctx->lp_gb, &ctx->gathered};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -809,8 +828,9 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         uint32_t *sv = in_alt ? avals : vals;
         GS_CUDA(ctx, gs_launch_ranges_dev(sk, sv, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s));
         mark(ctx, EV_RANGES, s);
-        GS_CUDA(ctx, gs_launch_blend(reader(ctx, rec, dtype), sv, ranges, grid, cam->width, cam->height,
-                                     opts->bg, *fb, blend_schedule(ctx, opts, n_tiles), s));
+        if ((st = launch_blend(ctx, reader(ctx, rec, dtype), sv, ranges, grid, cam, opts, fb, ctx->d_counts + 2,
+                               cap, s)) != GS_OK)
+            return st;
         mark(ctx, EV_BLEND, s);
         if (deferred) {
             const int slot = (ctx->ring_head + ctx->ring_count) % gs_context::kRing;

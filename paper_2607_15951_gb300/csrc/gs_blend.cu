@@ -57,12 +57,10 @@ struct SRec {
     float4 *box;  // (x0, x1, y0, y1) pixel-centre box where alpha can reach 1/255
 };
 
-// Builds the shared form of record g at slot s.
-__device__ __forceinline__ void stage_record(const RecordReader &rd, uint32_t g, int s,
-                                             const SRec &S, bool want_box) {
-    float4 r0, r1;
-    float blue;
-    rd.load(g, r0, r1, blue);
+// Builds the shared form of a record (words r0, r1 and blue of gs_record)
+// at slot s.
+__device__ __forceinline__ void stage_values(const float4 &r0, const float4 &r1, float blue, int s, const SRec &S,
+                                             bool want_box) {
     const float q00 = r0.z, q01 = r0.w, q11 = r1.x, o = r1.y;
     const float A = -0.5f * kLog2e * q00, B = -kLog2e * q01, C = -0.5f * kLog2e * q11;
     const float thr = -log2f(255.f * o);
@@ -94,6 +92,15 @@ __device__ __forceinline__ void stage_record(const RecordReader &rd, uint32_t g,
         }
     }
     S.box[s] = box;
+}
+
+// Builds the shared form of record g at slot s.
+__device__ __forceinline__ void stage_record(const RecordReader &rd, uint32_t g, int s,
+                                             const SRec &S, bool want_box) {
+    float4 r0, r1;
+    float blue;
+    rd.load(g, r0, r1, blue);
+    stage_values(r0, r1, blue, s, S, want_box);
 }
 
 // Per-pixel compositing state.
@@ -260,6 +267,179 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(c
 }
 
 // ---------------------------------------------------------------------------
+// Bulk-copy variant. A gather kernel writes each key's record (decoded to
+// FP32, 48 bytes) in list order, so a tile's records are contiguous; the
+// blend stages them 128 at a time with one cp.async.bulk copy into shared
+// memory, double-buffered (the copy of batch b + 1 overlaps batch b), each
+// completing on an mbarrier. The compute is the culled schedule's, so the
+// outputs are identical. Every wait is bounded in time and sets the error
+// word instead of hanging; a block waits for its copies in flight before it
+// exits.
+// ---------------------------------------------------------------------------
+constexpr int kTmaBatch = 128;  // records per bulk copy (6 KB)
+
+__global__ void __launch_bounds__(256) gather_records_kernel(RecordReader rd, const uint32_t *__restrict__ values,
+                                                             const unsigned long long *d_n, int64_t n_cap,
+                                                             float4 *__restrict__ out) {
+    const int64_t n = d_n ? (int64_t)*d_n : n_cap;
+    for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x; k < n && k < n_cap;
+         k += (int64_t)gridDim.x * 256) {
+        float4 r0, r1;
+        float blue;
+        rd.load(values[k], r0, r1, blue);
+        out[3 * k] = r0;
+        out[3 * k + 1] = r1;
+        out[3 * k + 2] = make_float4(blue, 0.f, 0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    // Generic-proxy accesses of this buffer (made visible by the preceding
+    // block barrier) are ordered before the async-proxy write.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Waits for the phase with the given parity to complete; gives up after
+// kSpinTimeoutNs (sets kErrTimeout) so that a copy that never lands cannot
+// hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *d_err) {
+    unsigned long long t0 = 0;
+    for (uint32_t i = 0;; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((i & 63u) == 0u) {
+            const unsigned long long now = global_ns();
+            if (i == 0) t0 = now;
+            else if (now - t0 > kSpinTimeoutNs || (ld_relaxed_u32(d_err) & kErrTimeout)) {
+                atomicOr(d_err, kErrTimeout);
+                return false;
+            }
+        }
+    }
+}
+
+template <int TW, int TH, int BW, int BH>
+__global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32)
+    blend_tma_kernel(const BlendArgs a, const float4 *__restrict__ srec, uint32_t *d_err) {
+    constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
+    constexpr int kRows = 32 / BW, kNP = BW * BH / 32;
+    __shared__ __align__(128) float4 s_raw[2][kTmaBatch * 3];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ float4 s_a[kTmaBatch], s_col[kTmaBatch], s_box[kTmaBatch];
+    __shared__ float2 s_b[kTmaBatch];
+    const SRec S{s_a, s_b, s_col, s_box};
+
+    const int tile = blockIdx.x;
+    const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
+    const int px = bx + (lane % BW), py_base = by + lane / BW;
+    const float fx = px + 0.5f;
+    const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
+    const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
+
+    const uint32_t first = a.ranges[2 * tile], last = a.ranges[2 * tile + 1];
+    const int n_list = (int)(last - first);
+    const int nb = (n_list + kTmaBatch - 1) / kTmaBatch;
+    Pix p[kNP];
+    bool mine_done = true;
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {
+        p[q] = Pix{1.f, 0.f, 0.f, 0.f, 0, 0, !(px < a.width && py_base + q * kRows < a.height)};
+        mine_done = mine_done && p[q].done;
+    }
+    bool warp_done = __all_sync(0xffffffffu, mine_done);
+    auto issue = [&](int b) {
+        const uint32_t k0 = first + (uint32_t)b * kTmaBatch;
+        const uint32_t cnt = min((uint32_t)kTmaBatch, last - k0);
+        bulk_load(s_raw[b & 1], srec + 3 * (size_t)k0, cnt * 48u, &s_bar[b & 1]);
+    };
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (nb > 0) issue(0);
+    }
+    __syncthreads();
+    int issued = nb > 0 ? 1 : 0, consumed = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (__syncthreads_count(warp_done) == kThreads) break;
+        if (b + 1 < nb) {
+            if (tid == 0) issue(b + 1);  // its buffer was last read before the barrier above
+            issued = b + 2;
+        }
+        const bool ok = mbar_wait(&s_bar[b & 1], (uint32_t)(b >> 1) & 1u, d_err);
+        consumed = b + 1;
+        if (__syncthreads_or(!ok)) break;
+        const int cnt = min(kTmaBatch, n_list - b * kTmaBatch);
+        for (int s = tid; s < cnt; s += kThreads) {
+            const float4 *r = &s_raw[b & 1][3 * s];
+            stage_values(r[0], r[1], r[2].x, s, S, true);
+        }
+        __syncthreads();
+        const int32_t pos0 = b * kTmaBatch + 1;
+        if (!warp_done) {
+            for (int c = 0; c < cnt; c += 32) {
+                const int j = c + lane;
+                bool hit = false;
+                if (j < cnt) {
+                    const float4 bx4 = s_box[j];
+                    hit = bx4.x <= wx1 && bx4.y >= wx0 && bx4.z <= wy1 && bx4.w >= wy0;
+                }
+                uint32_t bits = __ballot_sync(0xffffffffu, hit);
+                while (bits) {
+                    const int jj = c + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const float4 ra = s_a[jj];
+                    const float2 rb = s_b[jj];
+                    const float dx = fx - ra.x;
+                    const float adx2 = ra.z * dx * dx, bdx = ra.w * dx;
+#pragma unroll
+                    for (int q = 0; q < kNP; ++q) {
+                        if (!p[q].done) {
+                            const float dy = (float)(py_base + q * kRows) + 0.5f - ra.y;
+                            composite(p[q], fmaf(dy, fmaf(rb.x, dy, bdx), adx2), rb.y, &s_col[jj], pos0 + jj);
+                        }
+                    }
+                }
+                mine_done = true;
+#pragma unroll
+                for (int q = 0; q < kNP; ++q) mine_done = mine_done && p[q].done;
+                warp_done = __all_sync(0xffffffffu, mine_done);
+                if (warp_done) break;
+            }
+        }
+    }
+    // A copy still in flight (the block stopped early) must land before the
+    // block's shared memory is released.
+    if (tid == 0)
+        for (int b = consumed; b < issued; ++b) mbar_wait(&s_bar[b & 1], (uint32_t)(b >> 1) & 1u, d_err);
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {
+        if (!p[q].done) p[q].eval = n_list;
+        write_pixel(a, px, py_base + q * kRows, p[q]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Basic variant: one thread per pixel, every record evaluated.
 // ---------------------------------------------------------------------------
 template <int TW, int TH>
@@ -320,6 +500,27 @@ cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<8, 8>, 32, 0);
         blend_batch_kernel<8, 8><<<(unsigned)(sms * per_sm), 32, 0, s>>>(b);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_blend_tma(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                const GsGrid &grid, int width, int height, const float bg[3],
+                                const gs_framebuffer &fb, float4 *gather, const unsigned long long *d_n,
+                                int64_t n_cap, uint32_t *d_err, cudaStream_t s) {
+    if (n_cap > 0) {
+        int64_t blocks = (n_cap + 255) / 256;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        gather_records_kernel<<<(unsigned)blocks, 256, 0, s>>>(rd, values, d_n, n_cap, gather);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    BlendArgs a{rd, values, ranges, grid, width, height,
+                {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
+    const unsigned blocks = (unsigned)(grid.tiles_x * grid.tiles_y);
+    const int tw = grid.tile_w, th = grid.tile_h;
+    if (tw == 16 && th == 16) blend_tma_kernel<16, 16, 8, 4><<<blocks, 256, 0, s>>>(a, gather, d_err);
+    else if (tw == 16 && th == 8) blend_tma_kernel<16, 8, 8, 4><<<blocks, 128, 0, s>>>(a, gather, d_err);
+    else blend_tma_kernel<8, 8, 8, 4><<<blocks, 64, 0, s>>>(a, gather, d_err);
     return cudaGetLastError();
 }
 

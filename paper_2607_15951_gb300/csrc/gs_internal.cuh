@@ -330,6 +330,13 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s);
+// GS_BLEND_TMA: gathers the records of the sorted list (*d_n pairs, or n_cap
+// without a device count) into `gather` (n_cap x 48 bytes, 16-byte aligned),
+// then blends with bulk copies of contiguous record batches.
+cudaError_t gs_launch_blend_tma(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                const GsGrid &grid, int width, int height, const float bg[3],
+                                const gs_framebuffer &fb, float4 *gather, const unsigned long long *d_n,
+                                int64_t n_cap, uint32_t *d_err, cudaStream_t s);
 
 // Per-frame binning front end, depth first: (1) projection of every Gaussian,
 // appending each visible one to a compact list as (tiles << 32 | depth bits,

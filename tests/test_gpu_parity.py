@@ -397,7 +397,7 @@ def test_blend_variants_identical(ctx, name, make, tile):
     outs = []
     N_ = gs._native
     for variant in (N_.GS_BLEND_BASIC, N_.GS_BLEND_CULLED, N_.GS_BLEND_CULLED_WIDE, N_.GS_BLEND_CULLED_TILE,
-                    N_.GS_BLEND_CULLED_8X8):
+                    N_.GS_BLEND_CULLED_8X8, N_.GS_BLEND_TMA):
         out = gs.render(ctx, g, scene.sh_degree, cam, tile=tile, variant=variant)
         torch.cuda.synchronize()
         outs.append({k: v.cpu().numpy() for k, v in out.items()})
