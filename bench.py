@@ -304,6 +304,28 @@ def batched(gs, torch, args, flush, local) -> dict:
     ms_b = timed(batch)
     ms_b32 = timed(lambda: gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs))
     st = gs.gs_last_render_stats(ctx)
+    # Forward + backward of all views (L1 loss per view): one joint batch
+    # through RasterizeGaussiansBatch against the views one by one through
+    # RasterizeGaussians; FP16 records for the batch, FP32 for the views.
+    params = [g[k].clone().requires_grad_(True) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    targets = [torch.from_numpy(scenes.l1_target(c.height, c.width, 1200 + i)).cuda() for i, c in enumerate(cams)]
+
+    def fb_batch():
+        for p in params:
+            p.grad = None
+        rgbs = gs.RasterizeGaussiansBatch(*params, ctx, cams, scene.sh_degree, tile=tile,
+                                          record_dtype=N.GS_RECORD_F16)
+        sum((r - t).abs().mean() for r, t in zip(rgbs, targets)).backward()
+
+    def fb_views():
+        for p in params:
+            p.grad = None
+        for c, t in zip(cams, targets):
+            rgb, _ = gs.RasterizeGaussians(*params, ctx, c, scene.sh_degree)
+            (rgb - t).abs().mean().backward()
+
+    ms_fb_b = timed(fb_batch)
+    ms_fb_v = timed(fb_views)
     ctx.close()
     v = len(cams)
     return {"workload": "clustered_1m_traj64", "views": v,
@@ -316,7 +338,11 @@ def batched(gs, torch, args, flush, local) -> dict:
             "speedup_batched_f16_vs_per_view_f32": round(ms_pv / ms_b, 3),
             "ms_per_batch": round(ms_b, 3), "autotuned_tile": list(tile),
             "autotune_ms_16x16_16x8_8x8": [round(x, 3) for x in tune_ms],
-            "keys_per_batch": st["n_keys"], "iters": iters}
+            "keys_per_batch": st["n_keys"], "iters": iters,
+            "fwd_bwd_batched_f16_ms": round(ms_fb_b, 3), "fwd_bwd_per_view_f32_ms": round(ms_fb_v, 3),
+            "fwd_bwd_speedup": round(ms_fb_v / ms_fb_b, 3),
+            "fwd_bwd_note": "L1 loss per view over the 64 views; RasterizeGaussiansBatch (joint batch, one "
+                            "batched backward) vs RasterizeGaussians per view"}
 
 
 def temporal(gs, torch, args, flush, local) -> dict:

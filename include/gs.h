@@ -336,6 +336,21 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
 gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
                           const gs_options *opts, const gs_framebuffer *fbs, void *stream);
 
+/* Backward of the last gs_render_batch, which must have used the joint
+ * schedule (GS_BATCH_JOINT, or AUTO on short lists) with the same Gaussians,
+ * number of views and options: the gradients of sum over views v of
+ * <d_rgb[v], rgb_v> with respect to the five parameter arrays, as the sum of
+ * gs_render_backward over the views. One blend-gradient launch covers the
+ * tiles of all views; one projection-gradient launch covers every visible
+ * (view, Gaussian) pair and adds into the Gaussian's gradients (overwritten,
+ * not accumulated across calls).
+ *   fbs[v].final_T / n_contrib: the buffers the forward wrote (required);
+ *   d_rgb: host array of n_views device pointers, each height x width x 3;
+ *   out->d_records (optional): per visible (view, Gaussian) record, 9 floats. */
+gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
+                                   const gs_options *opts, const gs_framebuffer *fbs, const float *const *d_rgb,
+                                   const gs_grads *out, void *stream);
+
 /* Autotuner of gs_render_batch: renders the batch with each screen-tile
  * shape (16x16, 16x8, 8x8), times three runs of each with CUDA events, and
  * writes the fastest shape into opts->tile_w / tile_h. ms_out (host, 3

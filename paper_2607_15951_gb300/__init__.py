@@ -388,6 +388,71 @@ def gs_render_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, tile=(
                                      _stream(stream)))
 
 
+def gs_render_batch_backward(ctx: Context, g: dict, sh_degree: int, cams, outs, d_rgbs, grads: dict, *,
+                             tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0, stream=None) -> None:
+    """outs: the per-view dicts the joint gs_render_batch wrote (with final_T
+    and n_contrib); d_rgbs: per-view CUDA tensors (H, W, 3); grads: dict of
+    CUDA tensors shaped like g (and optionally 'records')."""
+    gs = gaussians_struct(g, sh_degree)
+    o = options_struct(tile, bg, record_dtype)
+    carr, farr = _cams_fbs(cams, outs)
+    ptrs = (ctypes.c_void_p * len(cams))(*[_ptr(d) for d in d_rgbs])
+    out = N.gs_grads()
+    out.d_means, out.d_log_scales, out.d_quats = (_ptr(grads["means"]), _ptr(grads["log_scales"]),
+                                                  _ptr(grads["quats"]))
+    out.d_opacity_logits, out.d_sh = _ptr(grads["opacity_logits"]), _ptr(grads["sh"])
+    out.d_records = _ptr(grads.get("records"))
+    ctx.check(_lib().gs_render_batch_backward(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
+                                              ptrs, ctypes.byref(out), _stream(stream)))
+
+
+def _batch_autograd_function():
+    import torch
+
+    class _RasterizeBatch(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, means, log_scales, quats, opacity_logits, sh, ctx, cams, sh_degree, tile, bg,
+                    record_dtype):
+            g = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
+                 "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
+                 "sh": sh.contiguous()}
+            outs = alloc_outputs(cams, aux=True, device=means.device)
+            gs_render_batch(ctx, g, sh_degree, cams, outs, tile=tile, bg=bg, record_dtype=record_dtype,
+                            batch_mode=N.GS_BATCH_JOINT)
+            fctx.gs = (ctx, cams, sh_degree, tile, bg, g, record_dtype, outs)
+            for o in outs:
+                fctx.mark_non_differentiable(o["final_T"])
+            return tuple(o["rgb"] for o in outs)
+
+        @staticmethod
+        def backward(fctx, *d_rgbs):
+            ctx, cams, sh_degree, tile, bg, g, record_dtype, outs = fctx.gs
+            d = [x.contiguous() if x is not None else torch.zeros_like(o["rgb"]) for x, o in zip(d_rgbs, outs)]
+            grads = {k: torch.empty_like(v) for k, v in g.items()}
+            gs_render_batch_backward(ctx, g, sh_degree, cams, outs, d, grads, tile=tile, bg=bg,
+                                     record_dtype=record_dtype)
+            return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
+                    grads["sh"], None, None, None, None, None, None)
+
+    return _RasterizeBatch
+
+
+_RASTERIZE_BATCH = None
+
+
+def RasterizeGaussiansBatch(means, log_scales, quats, opacity_logits, sh, ctx: Context, cams, sh_degree: int,
+                            tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0):
+    """Differentiable joint render of several views: returns one rgb tensor
+    (H, W, 3) per camera; the backward runs gs_render_batch_backward once for
+    all views. The backward of a batch must run before the next batch on the
+    same context."""
+    global _RASTERIZE_BATCH
+    if _RASTERIZE_BATCH is None:
+        _RASTERIZE_BATCH = _batch_autograd_function()
+    return _RASTERIZE_BATCH.apply(means, log_scales, quats, opacity_logits, sh, ctx, list(cams), sh_degree,
+                                  tuple(tile), tuple(bg), int(record_dtype))
+
+
 def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(0.0, 0.0, 0.0),
                       record_dtype: int = 0, cache_path: str | None = None, stream=None):
     """Runs the C autotuner (tile shapes 16x16, 16x8, 8x8) and returns

@@ -113,6 +113,10 @@ SIGNATURES = {
                                  ctypes.POINTER(gs_options), ctypes.POINTER(gs_framebuffer), vp]),
     "gs_last_render_stats": (ctypes.c_int, [vp, ctypes.POINTER(gs_render_stats)]),
     "gs_reserve_keys": (ctypes.c_int, [vp, ctypes.c_int64]),
+    "gs_render_batch_backward": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
+                                                ctypes.c_int32, ctypes.POINTER(gs_options),
+                                                ctypes.POINTER(gs_framebuffer), ctypes.POINTER(vp),
+                                                ctypes.POINTER(gs_grads), vp]),
     "gs_selftest_bounded_wait": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int64, vp]),
     "gs_render_batch": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
                                        ctypes.c_int32, ctypes.POINTER(gs_options),

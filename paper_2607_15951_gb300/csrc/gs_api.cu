@@ -46,6 +46,13 @@ struct gs_context {
         cudaStream_t capture = nullptr;  // the graph is captured here, launched on the caller's stream
         std::vector<int64_t> sig;  // what the captured graph was built for
         int64_t keys_per_view = 0;  // of the last batch (chooses GS_BATCH_AUTO's schedule)
+        // The last joint batch, for gs_render_batch_backward.
+        bool have_joint = false;
+        int64_t joint_n = 0, joint_records = 0;
+        int joint_views = 0, joint_tw = 0, joint_th = 0, joint_dtype = 0;
+        int32_t joint_tiles = 0;
+        const uint32_t *joint_values = nullptr;
+        DevBuf d_rec, bviews;
     } batch;
     int last_dtype = GS_RECORD_F32;
     int64_t key_capacity = 0;  // pairs the render path's key buffers hold
@@ -601,7 +608,7 @@ void gs_destroy(gs_context *ctx) {
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     auto &B = ctx->batch;
     DevBuf *bb[] = {&B.views, &B.rec, &B.meta, &B.geo, &B.oq, &B.gb, &B.scratch, &B.ranges, &B.order,
-                    &B.queue, &B.keys, &B.vals, &B.akeys, &B.avals, &B.sort};
+                    &B.queue, &B.keys, &B.vals, &B.akeys, &B.avals, &B.sort, &B.d_rec, &B.bviews};
     for (DevBuf *b : bb)
         if (b->ptr) cudaFree(b->ptr);
     if (B.exec) cudaGraphExecDestroy(B.exec);
@@ -980,6 +987,7 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
                                        &in_alt, s));
     uint64_t *sk = in_alt ? akeys : keys;
     uint32_t *sv = in_alt ? avals : vals;
+    B.joint_values = sv;
     uint32_t *ranges = static_cast<uint32_t *>(B.ranges.ptr);
     GS_CUDA(ctx, gs_launch_ranges_batch(sk, sv, meta, B.key_cap, ctx->d_counts + 2, total_tiles, ranges,
                                         ctx->d_err, s));
@@ -1019,6 +1027,7 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
     const int64_t n = g->n;
     const bool per_view = opts->batch_mode == GS_BATCH_PER_VIEW ||
                           (opts->batch_mode == GS_BATCH_AUTO && B.keys_per_view > kBatchPerViewKeys);
+    B.have_joint = false;
     if (per_view) {
         gs_options o = *opts;
         o.sync_mode = GS_SYNC_FRAME;
@@ -1141,10 +1150,76 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
             continue;
         }
         B.keys_per_view = (int64_t)K / n_views;
+        B.have_joint = true;
+        B.joint_n = n;
+        B.joint_records = (int64_t)nv;
+        B.joint_views = n_views;
+        B.joint_tw = opts->tile_w;
+        B.joint_th = opts->tile_h;
+        B.joint_dtype = opts->record_dtype;
+        B.joint_tiles = (int32_t)total_tiles;
         if (*ctx->h_err) return collect_device_error(ctx, s);
         return GS_OK;
     }
     return fail(ctx, GS_ERR_CAPACITY, "batch buffers could not be sized");
+}
+
+gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
+                                   const gs_options *opts, const gs_framebuffer *fbs, const float *const *d_rgb,
+                                   const gs_grads *out, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    gs_status st;
+    if ((st = check_gaussians(ctx, g)) != GS_OK || (st = check_options(ctx, opts)) != GS_OK) return st;
+    if (n_views < 1 || !cams || !fbs || !d_rgb || !out)
+        return fail(ctx, GS_ERR_INVALID_ARG, "cameras, framebuffers, d_rgb and the gradient struct are required");
+    auto &B = ctx->batch;
+    if (!B.have_joint || B.joint_n != g->n || B.joint_views != n_views || B.joint_tw != opts->tile_w ||
+        B.joint_th != opts->tile_h || B.joint_dtype != opts->record_dtype)
+        return fail(ctx, GS_ERR_INVALID_ARG,
+                    "gs_render_batch_backward must follow a joint gs_render_batch of the same scene, views and options");
+    if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
+        return fail(ctx, GS_ERR_INVALID_ARG, "a gradient array is NULL");
+    std::vector<GsBwdView> bv((size_t)n_views);
+    for (int v = 0; v < n_views; ++v) {
+        if ((st = check_camera(ctx, &cams[v])) != GS_OK) return st;
+        if (!fbs[v].final_T || !fbs[v].n_contrib || !d_rgb[v])
+            return fail(ctx, GS_ERR_INVALID_ARG, "every view needs final_T, n_contrib and d_rgb");
+        bv[v] = GsBwdView{d_rgb[v], fbs[v].final_T, fbs[v].n_contrib};
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = g->n, nr = B.joint_records;
+    if ((st = ensure(ctx, B.d_rec, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(float), "batch record gradients")) !=
+            GS_OK ||
+        (st = ensure(ctx, B.bviews, (size_t)n_views * sizeof(GsBwdView), "batch backward views")) != GS_OK)
+        return st;
+    // A copy from pageable memory: the host table may be reused at once.
+    GS_CUDA(ctx, cudaMemcpyAsync(B.bviews.ptr, bv.data(), bv.size() * sizeof(GsBwdView), cudaMemcpyHostToDevice, s));
+    float *d_rec = static_cast<float *>(B.d_rec.ptr);
+    GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(float), s));
+    const size_t kS = (size_t)(g->sh_degree + 1) * (g->sh_degree + 1) * 3;
+    if (n > 0) {
+        GS_CUDA(ctx, cudaMemsetAsync(out->d_means, 0, (size_t)n * 3 * sizeof(float), s));
+        GS_CUDA(ctx, cudaMemsetAsync(out->d_log_scales, 0, (size_t)n * 3 * sizeof(float), s));
+        GS_CUDA(ctx, cudaMemsetAsync(out->d_quats, 0, (size_t)n * 4 * sizeof(float), s));
+        GS_CUDA(ctx, cudaMemsetAsync(out->d_opacity_logits, 0, (size_t)n * sizeof(float), s));
+        GS_CUDA(ctx, cudaMemsetAsync(out->d_sh, 0, (size_t)n * kS * sizeof(float), s));
+    }
+    RecordReader rd;
+    rd.rec32 = static_cast<const float4 *>(B.rec.ptr);
+    rd.geo = static_cast<const float4 *>(B.geo.ptr);
+    rd.oq = static_cast<const uint2 *>(B.oq.ptr);
+    rd.gb = static_cast<const uint32_t *>(B.gb.ptr);
+    rd.dtype = opts->record_dtype;
+    const ViewDesc *views = static_cast<const ViewDesc *>(B.views.ptr);
+    GS_CUDA(ctx, gs_launch_blend_bwd_batch(rd, B.joint_values, static_cast<const uint32_t *>(B.ranges.ptr), views,
+                                           static_cast<const GsBwdView *>(B.bviews.ptr), n_views, opts->tile_w,
+                                           opts->tile_h, B.joint_tiles, d_rec, s));
+    GS_CUDA(ctx, gs_launch_project_bwd_batch(*g, views, static_cast<const uint2 *>(B.meta.ptr), nr, d_rec, *out, s));
+    if (out->d_records && nr > 0)
+        GS_CUDA(ctx, cudaMemcpyAsync(out->d_records, d_rec, (size_t)nr * 9 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                     s));
+    return GS_OK;
 }
 
 gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,

@@ -656,7 +656,7 @@ __device__ __forceinline__ bool composite_bwd(PixB &p, float e, float thr, const
 }
 
 template <int TW, int TH, int BW, int BH>
-__global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32) blend_bwd_kernel(const BlendBwdArgs a) {
+__device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs &a, int tile) {
     constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
     constexpr int kRows = 32 / BW, kNP = BW * BH / 32;  // rows per lane step, pixels per lane
     __shared__ float4 s_a[kBatch], s_col[kBatch], s_box[kBatch];
@@ -666,7 +666,6 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32) blend_bwd_kernel(c
     __shared__ int s_maxlast;
     const SRec S{s_a, s_b, s_col, s_box};
 
-    const int tile = blockIdx.x;
     const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
@@ -767,7 +766,51 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32) blend_bwd_kernel(c
     }
 }
 
+template <int TW, int TH, int BW, int BH>
+__global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32) blend_bwd_kernel(const BlendBwdArgs a) {
+    blend_bwd_tile<TW, TH, BW, BH>(a, blockIdx.x);
+}
+
+// Backward of a joint batch: block b takes global tile b of the batch and
+// differentiates it with its view's parameters; record gradients are indexed
+// by compact record slot (one per visible (view, Gaussian) pair).
+struct BlendBwdBatchArgs {
+    RecordReader rd;
+    const uint32_t *values;     // compact record slots, per-tile lists
+    const uint32_t *ranges;     // by global tile
+    const ViewDesc *views;
+    const GsBwdView *bviews;    // d_rgb, final_T, n_contrib per view
+    int n_views;
+    float *d_rec;               // record slots x 9
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_bwd_batch_kernel(const BlendBwdBatchArgs b) {
+    const uint32_t gt = blockIdx.x;
+    int lo = 0, hi = b.n_views - 1;  // last view whose first tile <= gt
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.views[mid].tile_base <= gt) lo = mid; else hi = mid - 1;
+    }
+    const ViewDesc &V = b.views[lo];
+    const GsBwdView &W = b.bviews[lo];
+    BlendBwdArgs a{b.rd, b.values, b.ranges + 2 * (size_t)V.tile_base, V.grid, V.cam.width, V.cam.height,
+                   {V.bg[0], V.bg[1], V.bg[2]}, W.d_rgb, W.final_T, W.n_contrib, b.d_rec};
+    blend_bwd_tile<TW, TH, 8, 8>(a, (int)(gt - V.tile_base));
+}
+
 }  // namespace
+
+cudaError_t gs_launch_blend_bwd_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                      const ViewDesc *views, const GsBwdView *bviews, int n_views, int tile_w,
+                                      int tile_h, int32_t total_tiles, float *d_rec, cudaStream_t s) {
+    if (total_tiles <= 0) return cudaSuccess;
+    BlendBwdBatchArgs b{rd, values, ranges, views, bviews, n_views, d_rec};
+    if (tile_w == 16 && tile_h == 16) blend_bwd_batch_kernel<16, 16><<<(unsigned)total_tiles, 128, 0, s>>>(b);
+    else if (tile_w == 16 && tile_h == 8) blend_bwd_batch_kernel<16, 8><<<(unsigned)total_tiles, 64, 0, s>>>(b);
+    else blend_bwd_batch_kernel<8, 8><<<(unsigned)total_tiles, 32, 0, s>>>(b);
+    return cudaGetLastError();
+}
 
 cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                 const GsGrid &grid, int width, int height, const float bg[3],

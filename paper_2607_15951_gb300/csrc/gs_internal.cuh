@@ -247,6 +247,13 @@ struct ViewDesc {
     int32_t *n_eval;
 };
 
+// Per-view inputs of a batched backward.
+struct GsBwdView {
+    const float *d_rgb;
+    const float *final_T;
+    const int32_t *n_contrib;
+};
+
 cudaError_t gs_launch_project(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                               gs_record *records, uint32_t *tiles, cudaStream_t s);
 
@@ -405,6 +412,15 @@ cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, 
                                 const GsGrid &grid, int width, int height, const float bg[3],
                                 const float *d_rgb, const float *final_T, const int32_t *n_contrib,
                                 float *d_rec, cudaStream_t s);
+// Backward of a joint batch (gs_render_batch): blend gradients per compact
+// record slot over all views' tiles, then, per record slot (view, Gaussian),
+// the projection gradients under that view's camera, added to the Gaussian's
+// gradients (which the caller zeroed).
+cudaError_t gs_launch_blend_bwd_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                      const ViewDesc *views, const GsBwdView *bviews, int n_views, int tile_w,
+                                      int tile_h, int32_t total_tiles, float *d_rec, cudaStream_t s);
+cudaError_t gs_launch_project_bwd_batch(const gs_gaussians &g, const ViewDesc *views, const uint2 *meta,
+                                        int64_t n_records, const float *d_rec, const gs_grads &out, cudaStream_t s);
 cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   const float *d_rec, const gs_grads &out, cudaStream_t s);
 

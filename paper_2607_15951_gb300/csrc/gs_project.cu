@@ -1095,15 +1095,14 @@ struct BwdSmem {
 // block then writes its contiguous output ranges with coalesced stores
 // (Gaussians that received no gradient get zeros).
 template <int DEG>
-__device__ __forceinline__ void project_bwd_one(const ProjectBwdArgs &B, int64_t i, float *dsh, float *gm_out,
-                                                float *gls_out, float *gq_out, float *go_out) {
+__device__ __forceinline__ bool project_bwd_one(const ProjectArgs &P, const GsCameraDev &K, int64_t i,
+                                                const float *rec_grad, float *dsh, float *gm_out, float *gls_out,
+                                                float *gq_out, float *go_out) {
     constexpr int kK = (DEG + 1) * (DEG + 1);
-    const ProjectArgs &P = B.P;
-    const GsCameraDev &K = P.cam;
     float gr9[9];
     bool any = false;
     for (int f = 0; f < 9; ++f) {
-        gr9[f] = B.d_rec[9 * i + f];
+        gr9[f] = rec_grad[f];
         any |= gr9[f] != 0.f;
     }
     if (!any) {
@@ -1112,7 +1111,7 @@ __device__ __forceinline__ void project_bwd_one(const ProjectBwdArgs &B, int64_t
         for (int a = 0; a < 4; ++a) gq_out[a] = 0.f;
         *go_out = 0.f;
         for (int a = 0; a < kK * 3; ++a) dsh[a] = 0.f;
-        return;
+        return false;
     }
     // ---- forward recomputation ----
     const float mx = P.means[3 * i], my = P.means[3 * i + 1], mz = P.means[3 * i + 2];
@@ -1227,6 +1226,7 @@ __device__ __forceinline__ void project_bwd_one(const ProjectBwdArgs &B, int64_t
     gq_out[2] = (gqy - qy * qdot) / qn;
     gq_out[3] = (gqz - qz * qdot) / qn;
     *go_out = go * o * (1.f - o);
+    return true;
 }
 
 template <int DEG>
@@ -1241,7 +1241,9 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs B
     const int t = threadIdx.x;
     const int64_t base = (int64_t)blockIdx.x * 256;
     const int64_t i = base + t;
-    if (i < B.P.n) project_bwd_one<DEG>(B, i, s_sh + t * L::kSP, s_m + 3 * t, s_l + 3 * t, s_q + 4 * t, s_o + t);
+    if (i < B.P.n)
+        project_bwd_one<DEG>(B.P, B.P.cam, i, B.d_rec + 9 * i, s_sh + t * L::kSP, s_m + 3 * t, s_l + 3 * t,
+                             s_q + 4 * t, s_o + t);
     __syncthreads();
     const int cnt = (int)(B.P.n - base < 256 ? B.P.n - base : 256);
     float *dsh = B.d_sh + base * L::kS;
@@ -1267,6 +1269,49 @@ cudaError_t launch_project_bwd(const ProjectBwdArgs &B, unsigned blocks, cudaStr
     return cudaGetLastError();
 }
 }  // namespace
+
+namespace {
+
+// One thread per compact record slot of a joint batch: the gradients of
+// Gaussian i under view v's camera, added to i's gradients (several views
+// see the same Gaussian).
+template <int DEG>
+__global__ void __launch_bounds__(128)
+    project_bwd_batch_kernel(const ProjectArgs P, const ViewDesc *views, const uint2 *meta, int64_t n_records,
+                             const float *d_rec, const gs_grads out) {
+    constexpr int kS = (DEG + 1) * (DEG + 1) * 3;
+    const int64_t j = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (j >= n_records) return;
+    const uint2 m = meta[j];  // (view, Gaussian)
+    const int64_t i = m.y;
+    float dsh[kS], gm[3], gls[3], gq[4], go;
+    if (!project_bwd_one<DEG>(P, views[m.x].cam, i, d_rec + 9 * j, dsh, gm, gls, gq, &go)) return;
+    for (int a = 0; a < 3; ++a) atomicAdd(out.d_means + 3 * i + a, gm[a]);
+    for (int a = 0; a < 3; ++a) atomicAdd(out.d_log_scales + 3 * i + a, gls[a]);
+    for (int a = 0; a < 4; ++a) atomicAdd(out.d_quats + 4 * i + a, gq[a]);
+    atomicAdd(out.d_opacity_logits + i, go);
+#pragma unroll
+    for (int a = 0; a < kS; ++a)
+        if (dsh[a] != 0.f) atomicAdd(out.d_sh + kS * i + a, dsh[a]);
+}
+
+}  // namespace
+
+cudaError_t gs_launch_project_bwd_batch(const gs_gaussians &g, const ViewDesc *views, const uint2 *meta,
+                                        int64_t n_records, const float *d_rec, const gs_grads &out, cudaStream_t s) {
+    const int64_t rec_capacity = n_records;
+    if (rec_capacity <= 0 || g.n == 0) return cudaSuccess;
+    const ProjectArgs P{g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.n, GsCameraDev{}, GsGrid{},
+                        nullptr, nullptr, false, false};
+    const unsigned blocks = (unsigned)((rec_capacity + 127) / 128);
+    switch (g.sh_degree) {
+        case 0: project_bwd_batch_kernel<0><<<blocks, 128, 0, s>>>(P, views, meta, n_records, d_rec, out); break;
+        case 1: project_bwd_batch_kernel<1><<<blocks, 128, 0, s>>>(P, views, meta, n_records, d_rec, out); break;
+        case 2: project_bwd_batch_kernel<2><<<blocks, 128, 0, s>>>(P, views, meta, n_records, d_rec, out); break;
+        default: project_bwd_batch_kernel<3><<<blocks, 128, 0, s>>>(P, views, meta, n_records, d_rec, out); break;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   const float *d_rec, const gs_grads &out, cudaStream_t s) {
