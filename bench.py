@@ -601,29 +601,54 @@ def main():
     value = frames / (dev_ms / 1000.0)
     stage_ms = {k: float(np.median(v)) for k, v in stage_sum.items()}
 
-    # End to end: pinned host inputs copied in and the image copied out, every step.
+    # End to end: every step copies its inputs (the Gaussian arrays) from
+    # pinned host memory and reads its image back, through the public
+    # gs_render. The inputs are double-buffered: the copy for step i + 1 runs
+    # on a copy stream while step i renders (deferred frames, reserved key
+    # capacity), as a streaming renderer would; every step's bytes still
+    # cross the link inside the timed region.
     host = {k: v.cpu().pin_memory() for k, v in g.items()}
-    dev_in = {k: torch.empty_like(v) for k, v in g.items()}
-    host_rgb = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    dev_in = [{k: torch.empty_like(v) for k, v in g.items()} for _ in range(2)]
+    host_rgb = [torch.empty((H, W, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = host_rgb.numel() * 4
-    for _ in range(3):
-        for k in host:
-            dev_in[k].copy_(host[k], non_blocking=True)
-        gs.gs_render(ctx, dev_in, scene.sh_degree, cam, rgb, variant=args.blend_variant)
-        host_rgb.copy_(rgb, non_blocking=True)
+    d2h = host_rgb[0].numel() * 4
+    copy_stream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    gs.gs_reserve_keys(ctx, stats["n_keys"] + stats["n_keys"] // 4 + 4096)
+
+    def e2e_run(steps):
+        copy_stream.wait_stream(stream)
+        with torch.cuda.stream(copy_stream):
+            for k in host:
+                dev_in[0][k].copy_(host[k], non_blocking=True)
+            copied[0].record(copy_stream)
+        for i in range(steps):
+            b = i % 2
+            if i + 1 < steps:
+                nb = (i + 1) % 2
+                with torch.cuda.stream(copy_stream):
+                    if i >= 1:
+                        copy_stream.wait_event(consumed[nb])
+                    for k in host:
+                        dev_in[nb][k].copy_(host[k], non_blocking=True)
+                    copied[nb].record(copy_stream)
+            stream.wait_event(copied[b])
+            gs.gs_render(ctx, dev_in[b], scene.sh_degree, cam, rgb, variant=args.blend_variant, deferred=True)
+            consumed[b].record(stream)
+            host_rgb[b].copy_(rgb, non_blocking=True)
+
+    e2e_run(3)
     torch.cuda.synchronize()
+    gs.gs_sync_status(ctx)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.e2e_steps):
-        for k in host:
-            dev_in[k].copy_(host[k], non_blocking=True)
-        gs.gs_render(ctx, dev_in, scene.sh_degree, cam, rgb, variant=args.blend_variant)
-        host_rgb.copy_(rgb, non_blocking=True)
+    e2e_run(args.e2e_steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    gs.gs_sync_status(ctx)
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     e2e_value = args.e2e_steps * world / (e2e_ms / 1000.0)
 
@@ -673,7 +698,9 @@ def main():
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "wall_s_timed_loop": round(wall, 3),
         "e2e": {"value": round(e2e_value, 3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps},
+                "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+                "schedule": "inputs double-buffered: step i+1's host-to-device copy (copy stream) overlaps "
+                            "step i's render and image read-back; gs_render deferred"},
         "gpu_launches": None,
         "roofline": roofline,
         "hbm_roofline": hbm,
