@@ -262,8 +262,8 @@ def batched(gs, torch, args, flush, local) -> dict:
     ctx = gs.Context(local)
     stream = torch.cuda.current_stream()
     outs = gs.alloc_outputs(cams)
-    tile, tune_ms = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
-                                         record_dtype=N.GS_RECORD_F16)
+    tile, tune_ms, depth = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
+                                                record_dtype=N.GS_RECORD_F16)
     iters = max(3, args.steps // 100)
 
     def timed(fn):
@@ -291,7 +291,8 @@ def batched(gs, torch, args, flush, local) -> dict:
         gs.gs_sync_status(ctx)
 
     def batch():
-        gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile, record_dtype=N.GS_RECORD_F16)
+        gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile, record_dtype=N.GS_RECORD_F16,
+                           batch_depth=depth)
 
     ms_pv_sync = timed(per_view)
     # Deferred frames cannot regrow in place: reserve room for the largest view.
@@ -336,7 +337,7 @@ def batched(gs, torch, args, flush, local) -> dict:
             "batched_f16_views_per_s": round(v / (ms_b / 1e3), 1),
             "batched_f32_views_per_s": round(v / (ms_b32 / 1e3), 1),
             "speedup_batched_f16_vs_per_view_f32": round(ms_pv / ms_b, 3),
-            "ms_per_batch": round(ms_b, 3), "autotuned_tile": list(tile),
+            "ms_per_batch": round(ms_b, 3), "autotuned_tile": list(tile), "autotuned_depth": depth,
             "autotune_ms_16x16_16x8_8x8": [round(x, 3) for x in tune_ms],
             "keys_per_batch": st["n_keys"], "iters": iters,
             "fwd_bwd_batched_f16_ms": round(ms_fb_b, 3), "fwd_bwd_per_view_f32_ms": round(ms_fb_v, 3),
@@ -408,7 +409,8 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
     ctx = gs.Context(local)
     stream = torch.cuda.current_stream()
     outs = gs.alloc_outputs(cams)
-    tile, tune_ms = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs, record_dtype=N.GS_RECORD_BF16)
+    tile, tune_ms, depth = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
+                                                record_dtype=N.GS_RECORD_BF16)
     iters = 3
 
     def timed(fn):
@@ -426,7 +428,7 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
         return tot / iters
 
     ms_batch = timed(lambda: gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile,
-                                                record_dtype=N.GS_RECORD_BF16))
+                                                record_dtype=N.GS_RECORD_BF16, batch_depth=depth))
     keys_batch = gs.gs_last_render_stats(ctx)["n_keys"]
     k_max = 0
     for c, o in zip(cams, outs):

@@ -153,7 +153,10 @@ typedef struct {
                                gs_render (needs GS_SYNC_FRAME)                 */
     int32_t batch_mode;     /* gs_render_batch: GS_BATCH_AUTO (default),
                                GS_BATCH_JOINT or GS_BATCH_PER_VIEW             */
-    int32_t reserved[2];    /* must be zero                                    */
+    int32_t batch_depth;    /* gs_render_batch, joint schedule: records staged
+                               per shared-memory batch of the blend, 64, 128
+                               or 256 (0 = 256)                                */
+    int32_t reserved[1];    /* must be zero                                    */
 } gs_options;
 
 /* How gs_render_batch schedules the views. JOINT: one projection, one key
@@ -352,9 +355,11 @@ gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const
                                    const gs_grads *out, void *stream);
 
 /* Autotuner of gs_render_batch: renders the batch with each screen-tile
- * shape (16x16, 16x8, 8x8), times three runs of each with CUDA events, and
- * writes the fastest shape into opts->tile_w / tile_h. ms_out (host, 3
- * floats, optional) receives the mean time of each shape in that order. */
+ * shape (16x16, 16x8, 8x8) and, for the joint schedule, each blend staging
+ * depth (256, 128, 64 records), times three runs of each with CUDA events,
+ * and writes the fastest into opts->tile_w / tile_h / batch_depth. ms_out
+ * (host, 3 floats, optional) receives per shape the mean time of its best
+ * depth, in that order. */
 gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
                             gs_options *opts, const gs_framebuffer *fbs, void *stream, float *ms_out);
 

@@ -377,12 +377,14 @@ def alloc_outputs(cams, aux: bool = False, device="cuda") -> list:
 
 def gs_render_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, tile=(16, 16),
                     bg=(0.0, 0.0, 0.0), record_dtype: int = 0, direct: bool = False,
-                    batch_mode: int = 0, stream=None):
-    """batch_mode: N.GS_BATCH_AUTO (0), GS_BATCH_JOINT (1) or GS_BATCH_PER_VIEW (2)."""
+                    batch_mode: int = 0, batch_depth: int = 0, stream=None):
+    """batch_mode: N.GS_BATCH_AUTO (0), GS_BATCH_JOINT (1) or GS_BATCH_PER_VIEW (2);
+    batch_depth: blend staging depth of the joint schedule (0 = 256)."""
     gs = gaussians_struct(g, sh_degree)
     o = options_struct(tile, bg, record_dtype)
     o.direct_launch = 1 if direct else 0
     o.batch_mode = int(batch_mode)
+    o.batch_depth = int(batch_depth)
     carr, farr = _cams_fbs(cams, outs)
     ctx.check(_lib().gs_render_batch(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
                                      _stream(stream)))
@@ -455,9 +457,10 @@ def RasterizeGaussiansBatch(means, log_scales, quats, opacity_logits, sh, ctx: C
 
 def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(0.0, 0.0, 0.0),
                       record_dtype: int = 0, cache_path: str | None = None, stream=None):
-    """Runs the C autotuner (tile shapes 16x16, 16x8, 8x8) and returns
-    ((tile_w, tile_h), [ms per shape]). With cache_path, results are kept in a
-    JSON file keyed by GPU, scene size, view sizes and record precision."""
+    """Runs the C autotuner (tile shapes 16x16, 16x8, 8x8 and, for the joint
+    schedule, staging depths 256, 128, 64) and returns ((tile_w, tile_h),
+    [ms per shape], depth). With cache_path, results are kept in a JSON file
+    keyed by GPU, scene size, view sizes and record precision."""
     import json
     import os
     import torch
@@ -470,20 +473,20 @@ def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(
             with open(cache_path) as f:
                 cache = json.load(f)
             if key in cache:
-                return tuple(cache[key]["tile"]), cache[key]["ms"]
+                return tuple(cache[key]["tile"]), cache[key]["ms"], cache[key].get("depth", 256)
     gs = gaussians_struct(g, sh_degree)
     o = options_struct((16, 16), bg, record_dtype)
     carr, farr = _cams_fbs(cams, outs)
     ms = (ctypes.c_float * 3)()
     ctx.check(_lib().gs_autotune_batch(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
                                        _stream(stream), ms))
-    tile, times = (int(o.tile_w), int(o.tile_h)), [float(x) for x in ms]
+    tile, times, depth = (int(o.tile_w), int(o.tile_h)), [float(x) for x in ms], int(o.batch_depth)
     if cache_path:
         cache = {}
         if os.path.exists(cache_path):
             with open(cache_path) as f:
                 cache = json.load(f)
-        cache[key] = {"tile": list(tile), "ms": times}
+        cache[key] = {"tile": list(tile), "ms": times, "depth": depth}
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
-    return tile, times
+    return tile, times, depth

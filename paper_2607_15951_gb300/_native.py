@@ -74,8 +74,8 @@ class gs_options(ctypes.Structure):
                 ("bg", ctypes.c_float * 3), ("record_dtype", ctypes.c_int32),
                 ("blend_variant", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
                 ("sync_mode", ctypes.c_int32), ("temporal", ctypes.c_int32),
-                ("batch_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("batch_mode", ctypes.c_int32), ("batch_depth", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class gs_render_stats(ctypes.Structure):

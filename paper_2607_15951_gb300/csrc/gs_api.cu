@@ -165,8 +165,9 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
         return fail(ctx, GS_ERR_INVALID_ARG, "temporal re-binning needs sync_mode GS_SYNC_FRAME");
     if (o->batch_mode < GS_BATCH_AUTO || o->batch_mode > GS_BATCH_PER_VIEW)
         return fail(ctx, GS_ERR_INVALID_ARG, "batch_mode must be GS_BATCH_AUTO, _JOINT or _PER_VIEW");
-    for (int i = 0; i < 2; ++i)
-        if (o->reserved[i] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
+    if (o->batch_depth != 0 && o->batch_depth != 64 && o->batch_depth != 128 && o->batch_depth != 256)
+        return fail(ctx, GS_ERR_INVALID_ARG, "batch_depth must be 0, 64, 128 or 256");
+    if (o->reserved[0] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
     return GS_OK;
@@ -1000,7 +1001,8 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
     rd.oq = static_cast<const uint2 *>(B.oq.ptr);
     rd.gb = static_cast<const uint32_t *>(B.gb.ptr);
     rd.dtype = dtype;
-    GS_CUDA(ctx, gs_launch_blend_batch(rd, sv, ranges, views, n_views, opts->tile_w, opts->tile_h, order,
+    GS_CUDA(ctx, gs_launch_blend_batch(rd, sv, ranges, views, n_views, opts->tile_w, opts->tile_h,
+                                       opts->batch_depth ? opts->batch_depth : 256, order,
                                        total_tiles, qs + 193, s));
     GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 4 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, s));
@@ -1060,7 +1062,7 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
     std::vector<int64_t> sig = {n, g->sh_degree, (int64_t)(uintptr_t)g->means, (int64_t)(uintptr_t)g->log_scales,
                                 (int64_t)(uintptr_t)g->quats, (int64_t)(uintptr_t)g->opacity_logits,
                                 (int64_t)(uintptr_t)g->sh, n_views, opts->tile_w, opts->tile_h,
-                                opts->record_dtype};
+                                opts->record_dtype, opts->batch_depth};
     for (int v = 0; v < n_views; ++v) {
         ViewDesc &V = B.h_views[v];
         V.cam = make_cam(&cams[v]);
@@ -1228,38 +1230,49 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int shapes[3][2] = {{16, 16}, {16, 8}, {8, 8}};
+    const int depths[3] = {256, 128, 64};
     cudaEvent_t e0, e1;
     GS_CUDA(ctx, cudaEventCreate(&e0));
     GS_CUDA(ctx, cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_k = 0;
+    int best_k = 0, best_d = 0;
     gs_status st = GS_OK;
     for (int k = 0; k < 3 && st == GS_OK; ++k) {
-        gs_options o = *opts;
-        o.tile_w = shapes[k][0];
-        o.tile_h = shapes[k][1];
-        for (int w = 0; w < 2 && st == GS_OK; ++w) st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
-        float total = 0.f;
-        for (int r = 0; r < 3 && st == GS_OK; ++r) {
-            cudaEventRecord(e0, s);
-            st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            total += ms;
+        float best_shape = 1e30f;
+        for (int d = 0; d < 3 && st == GS_OK; ++d) {
+            gs_options o = *opts;
+            o.tile_w = shapes[k][0];
+            o.tile_h = shapes[k][1];
+            o.batch_depth = depths[d];
+            for (int w = 0; w < 2 && st == GS_OK; ++w) st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
+            // The depth only matters to the joint schedule.
+            const bool joint = ctx->batch.have_joint;
+            float total = 0.f;
+            for (int r = 0; r < 3 && st == GS_OK; ++r) {
+                cudaEventRecord(e0, s);
+                st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+            if (st == GS_OK && total < best_shape) best_shape = total;
+            if (st == GS_OK && total < best) {
+                best = total;
+                best_k = k;
+                best_d = d;
+            }
+            if (!joint) break;
         }
-        if (ms_out) ms_out[k] = total / 3.f;
-        if (st == GS_OK && total < best) {
-            best = total;
-            best_k = k;
-        }
+        if (ms_out) ms_out[k] = best_shape / 3.f;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != GS_OK) return st;
     opts->tile_w = shapes[best_k][0];
     opts->tile_h = shapes[best_k][1];
+    opts->batch_depth = depths[best_d];
     return GS_OK;
 }
 

@@ -148,14 +148,14 @@ __device__ __forceinline__ void write_pixel(const BlendArgs &a, int px, int py, 
 // 8x8 blocks (default) cull finely; wider blocks amortise each record's
 // ballot, shared-memory reads and x terms over more pixels.
 // ---------------------------------------------------------------------------
-template <int TW, int TH, int BW, int BH>
+template <int TW, int TH, int BW, int BH, int DEPTH = kBatch>
 __device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) {
     constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
     constexpr int kRows = 32 / BW;     // rows covered by the warp's lanes at once
     constexpr int kNP = BW * BH / 32;  // pixels per lane
     static_assert(kNP >= 1 && kRows * kNP == BH, "block shape");
-    __shared__ float4 s_a[kBatch], s_col[kBatch], s_box[kBatch];
-    __shared__ float2 s_b[kBatch];
+    __shared__ float4 s_a[DEPTH], s_col[DEPTH], s_box[DEPTH];
+    __shared__ float2 s_b[DEPTH];
     const SRec S{s_a, s_b, s_col, s_box};
 
     const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
@@ -177,14 +177,14 @@ __device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) 
     }
     bool warp_done = __all_sync(0xffffffffu, mine_done);
 
-    for (uint32_t start = first; start < last; start += kBatch) {
+    for (uint32_t start = first; start < last; start += DEPTH) {
         if (__syncthreads_count(warp_done) == kThreads) break;
-        for (int s = tid; s < kBatch; s += kThreads) {
+        for (int s = tid; s < DEPTH; s += kThreads) {
             const uint32_t k = start + s;
             if (k < last) stage_record(a.rd, a.values[k], s, S, true);
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)kBatch, last - start);
+        const int cnt = (int)min((uint32_t)DEPTH, last - start);
         const int32_t pos0 = (int32_t)(start - first) + 1;  // list position of slot 0
         if (!warp_done) {
             for (int c = 0; c < cnt; c += 32) {
@@ -244,7 +244,7 @@ struct BlendBatchArgs {
     uint32_t *queue_head;
 };
 
-template <int TW, int TH>
+template <int TW, int TH, int DEPTH>
 __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(const BlendBatchArgs b) {
     __shared__ int s_item;
     for (;;) {
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(c
         const ViewDesc &V = b.views[lo];
         BlendArgs a{b.rd, b.values, b.ranges + 2 * (size_t)V.tile_base, V.grid, V.cam.width, V.cam.height,
                     {V.bg[0], V.bg[1], V.bg[2]}, V.rgb, V.final_T, V.n_contrib, V.n_eval};
-        blend_tile_culled<TW, TH, 8, 8>(a, (int)(gt - V.tile_base));
+        blend_tile_culled<TW, TH, 8, 8, DEPTH>(a, (int)(gt - V.tile_base));
     }
 }
 
@@ -480,26 +480,36 @@ __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) 
 
 }  // namespace
 
+namespace {
+template <int TW, int TH, int DEPTH>
+void launch_blend_batch(const BlendBatchArgs &b, int sms, cudaStream_t s) {
+    constexpr int kThreads = (TW / 8) * (TH / 8) * 32;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<TW, TH, DEPTH>, kThreads, 0);
+    blend_batch_kernel<TW, TH, DEPTH><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), kThreads, 0, s>>>(b);
+}
+
+template <int DEPTH>
+void launch_blend_batch_shape(const BlendBatchArgs &b, int tile_w, int tile_h, int sms, cudaStream_t s) {
+    if (tile_w == 16 && tile_h == 16) launch_blend_batch<16, 16, DEPTH>(b, sms, s);
+    else if (tile_w == 16 && tile_h == 8) launch_blend_batch<16, 8, DEPTH>(b, sms, s);
+    else launch_blend_batch<8, 8, DEPTH>(b, sms, s);
+}
+}  // namespace
+
 cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
-                                  const ViewDesc *views_dev, int n_views, int tile_w, int tile_h,
+                                  const ViewDesc *views_dev, int n_views, int tile_w, int tile_h, int depth,
                                   const uint32_t *order, int32_t n_tiles, uint32_t *queue_head, cudaStream_t s) {
     BlendBatchArgs b{rd, values, ranges, views_dev, n_views, order, n_tiles, queue_head};
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 1;
-    // 8x8 warp blocks: in the persistent queue loop the 8x4 blocks' larger
-    // thread blocks measured slower (7770 vs 8985 views/s on 64 views).
-    if (tile_w == 16 && tile_h == 16) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<16, 16>, 128, 0);
-        blend_batch_kernel<16, 16><<<(unsigned)(sms * per_sm), 128, 0, s>>>(b);
-    } else if (tile_w == 16 && tile_h == 8) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<16, 8>, 64, 0);
-        blend_batch_kernel<16, 8><<<(unsigned)(sms * per_sm), 64, 0, s>>>(b);
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<8, 8>, 32, 0);
-        blend_batch_kernel<8, 8><<<(unsigned)(sms * per_sm), 32, 0, s>>>(b);
-    }
+    // Persistent grid sized by occupancy; 8x8 warp blocks (in the queue loop
+    // the 8x4 blocks' larger thread blocks measured slower: 7770 vs 8985
+    // views/s on 64 views). depth = records staged per shared-memory batch.
+    if (depth == 64) launch_blend_batch_shape<64>(b, tile_w, tile_h, sms, s);
+    else if (depth == 128) launch_blend_batch_shape<128>(b, tile_w, tile_h, sms, s);
+    else launch_blend_batch_shape<256>(b, tile_w, tile_h, sms, s);
     return cudaGetLastError();
 }
 

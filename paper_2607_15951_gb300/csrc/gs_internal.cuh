@@ -441,7 +441,7 @@ cudaError_t gs_launch_ranges_batch(const uint64_t *keys, uint32_t *values, const
                                    uint32_t *d_err, cudaStream_t s);
 // Persistent blend over a queue of global tiles (largest lists first).
 cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
-                                  const ViewDesc *views_dev, int n_views, int tile_w, int tile_h,
+                                  const ViewDesc *views_dev, int n_views, int tile_w, int tile_h, int depth,
                                   const uint32_t *order, int32_t n_tiles, uint32_t *queue_head, cudaStream_t s);
 // Largest-first work queue of global tiles; qs: gs_queue_scratch_bytes(),
 // the queue head the blend takes items from is qs[193].

@@ -72,9 +72,17 @@ def test_batch_tile_shapes_and_autotune(ctx, tmp_path):
         for a, b in zip(outs, ref):
             assert torch.equal(a["rgb"], b["rgb"]), tile
     cache = str(tmp_path / "tune.json")
-    tile, ms = gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams), cache_path=cache)
+    tile, ms, depth = gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams), cache_path=cache)
     assert tile in ((16, 16), (16, 8), (8, 8)) and len(ms) == 3 and all(m > 0 for m in ms)
-    assert gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams), cache_path=cache)[0] == tile
+    assert depth in (64, 128, 256)
+    assert gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams), cache_path=cache)[:3:2] == (tile, depth)
+    for d in (64, 128, 256):  # every staging depth renders the same image
+        outs = gs.alloc_outputs(cams, aux=True)
+        gs.gs_render_batch(ctx, g, 0, cams, outs, tile=tile, batch_depth=d, batch_mode=N.GS_BATCH_JOINT)
+        ref = per_view(ctx, g, 0, cams, tile=tile)
+        for a, b in zip(outs, ref):
+            for k in ("rgb", "final_T", "n_contrib", "n_eval"):
+                assert torch.equal(a[k], b[k]), (d, k)
 
 
 def test_batch_matches_oracle(ctx, oracle_mod):
