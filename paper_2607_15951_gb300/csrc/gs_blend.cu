@@ -103,6 +103,30 @@ __device__ __forceinline__ void stage_record(const RecordReader &rd, uint32_t g,
     stage_values(r0, r1, blue, s, S, want_box);
 }
 
+// Can a record reach alpha >= 1/255 at some pixel centre of the rectangle
+// [x0, x1] x [y0, y1]? First its conservative box, then the exact maximum of
+// the exponent e(d) = A dx^2 + B dx dy + C dy^2 (A, C < 0: a concave
+// quadratic) over the rectangle: 0 if the mean is inside, else the largest of
+// the four edge maxima, each at the clamped stationary point of e along that
+// edge. The margin covers the FP32 rounding of both this maximum and the
+// per-pixel exponent (far above a few ulps of the summed term magnitudes),
+// so a record this rejects is one every pixel of the rectangle would skip.
+__device__ __forceinline__ bool record_touches(const float4 &ra, const float2 &rb, const float4 &box, float x0,
+                                               float x1, float y0, float y1) {
+    if (!(box.x <= x1 && box.y >= x0 && box.z <= y1 && box.w >= y0)) return false;
+    const float dx0 = x0 - ra.x, dx1 = x1 - ra.x, dy0 = y0 - ra.y, dy1 = y1 - ra.y;
+    if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
+    const float A = ra.z, B = ra.w, C = rb.x, thr = rb.y;
+    const float i2a = -0.5f / A, i2c = -0.5f / C;  // stationary points: dx = -B dy / 2A, dy = -B dx / 2C
+    auto e = [&](float dx, float dy) { return fmaf(dy, fmaf(C, dy, B * dx), A * dx * dx); };
+    const float ya = fminf(fmaxf(B * dx0 * i2c, dy0), dy1), yb = fminf(fmaxf(B * dx1 * i2c, dy0), dy1);
+    const float xa = fminf(fmaxf(B * dy0 * i2a, dx0), dx1), xb = fminf(fmaxf(B * dy1 * i2a, dx0), dx1);
+    const float m = fmaxf(fmaxf(e(dx0, ya), e(dx1, yb)), fmaxf(e(xa, dy0), e(xb, dy1)));
+    const float dxm = fmaxf(fabsf(dx0), fabsf(dx1)), dym = fmaxf(fabsf(dy0), fabsf(dy1));
+    const float scale = fmaf(-A, dxm * dxm, fmaf(fabsf(B), dxm * dym, -C * dym * dym));
+    return m >= thr - (1e-5f * scale + 1e-6f);
+}
+
 // Per-pixel compositing state.
 struct Pix {
     float T, r, g, b;
@@ -189,11 +213,7 @@ __device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) 
         if (!warp_done) {
             for (int c = 0; c < cnt; c += 32) {
                 const int j = c + lane;
-                bool hit = false;
-                if (j < cnt) {
-                    const float4 bx4 = s_box[j];
-                    hit = bx4.x <= wx1 && bx4.y >= wx0 && bx4.z <= wy1 && bx4.w >= wy0;
-                }
+                const bool hit = j < cnt && record_touches(s_a[j], s_b[j], s_box[j], wx0, wx1, wy0, wy1);
                 uint32_t bits = __ballot_sync(0xffffffffu, hit);
                 while (bits) {
                     const int jj = c + __ffs(bits) - 1;
@@ -399,11 +419,7 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32)
         if (!warp_done) {
             for (int c = 0; c < cnt; c += 32) {
                 const int j = c + lane;
-                bool hit = false;
-                if (j < cnt) {
-                    const float4 bx4 = s_box[j];
-                    hit = bx4.x <= wx1 && bx4.y >= wx0 && bx4.z <= wy1 && bx4.w >= wy0;
-                }
+                const bool hit = j < cnt && record_touches(s_a[j], s_b[j], s_box[j], wx0, wx1, wy0, wy1);
                 uint32_t bits = __ballot_sync(0xffffffffu, hit);
                 while (bits) {
                     const int jj = c + __ffs(bits) - 1;
@@ -729,11 +745,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs &a, int tile) 
         if (wmax > beg) {
             for (int c = ((cnt - 1) / 32) * 32; c >= 0; c -= 32) {
                 const int j = c + lane;
-                bool hit = false;
-                if (j < cnt) {
-                    const float4 b4 = s_box[j];
-                    hit = b4.x <= wx1 && b4.y >= wx0 && b4.z <= wy1 && b4.w >= wy0;
-                }
+                const bool hit = j < cnt && record_touches(s_a[j], s_b[j], s_box[j], wx0, wx1, wy0, wy1);
                 uint32_t bits = __ballot_sync(0xffffffffu, hit);
                 while (bits) {
                     const int hb = 31 - __clz(bits);
