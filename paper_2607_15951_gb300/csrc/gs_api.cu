@@ -747,6 +747,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     const int n_tiles = grid.tiles_x * grid.tiles_y;
     const int bits = key_bits_for(n_tiles);
     const int tile_passes = (bits - 32 + 7) / 8;
+    const int key_bytes = n_tiles <= 65536 ? 2 : 4;  // tile-id keys of the tile sort
     const int dtype = opts->record_dtype;
     if (dtype != GS_RECORD_F32 &&
         ((st = ensure(ctx, ctx->lp_geo, (size_t)(n > 0 ? n : 1) * 16, "reduced-precision records")) != GS_OK ||
@@ -798,22 +799,21 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     // the overflow is detected at the end and the frame is rendered again.
     for (int attempt = 0; attempt < 3; ++attempt) {
         const int64_t cap = ctx->key_capacity;
-        if ((st = ensure(ctx, ctx->keys, (size_t)cap * 8, "keys")) != GS_OK ||
+        if ((st = ensure(ctx, ctx->keys, (size_t)cap * key_bytes, "keys")) != GS_OK ||
             (st = ensure(ctx, ctx->values, (size_t)cap * 4, "values")) != GS_OK ||
-            (st = ensure(ctx, ctx->alt_keys, (size_t)cap * 8, "alt keys")) != GS_OK ||
+            (st = ensure(ctx, ctx->alt_keys, (size_t)cap * key_bytes, "alt keys")) != GS_OK ||
             (st = ensure(ctx, ctx->alt_values, (size_t)cap * 4, "alt values")) != GS_OK ||
             (st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes_digits(cap, tile_passes), "sort scratch")) !=
                 GS_OK ||
             (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n, cap), "front-end scratch")) != GS_OK)
             return st;
-        uint64_t *keys = static_cast<uint64_t *>(ctx->keys.ptr);
+        void *keys = ctx->keys.ptr, *akeys = ctx->alt_keys.ptr;
         uint32_t *vals = static_cast<uint32_t *>(ctx->values.ptr);
-        uint64_t *akeys = static_cast<uint64_t *>(ctx->alt_keys.ptr);
         uint32_t *avals = static_cast<uint32_t *>(ctx->alt_values.ptr);
-        // The tile sort: keys arrive in depth order, so only the tile digits
-        // (digits 4.. of the key) are sorted.
+        // The tile sort: keys are tile ids emitted in (depth, index) order,
+        // so the stable sort on them alone gives each tile's list in order.
         GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes_digits(cap, tile_passes), s));
-        const GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, cap, 4, tile_passes);
+        const GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, cap, 0, tile_passes);
         mark(ctx, EV_START, s);
         cudaEvent_t ev3[3] = {nullptr, nullptr, nullptr};
         if (ctx->timing) {
@@ -823,18 +823,22 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         }
         GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, static_cast<float4 *>(ctx->lp_geo.ptr),
                                            static_cast<uint2 *>(ctx->lp_oq.ptr),
-                                           static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype, keys, vals, cap,
-                                           ctx->d_counts,
+                                           static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype, keys, key_bytes, vals,
+                                           cap, ctx->d_counts,
                                            ctx->fused_scratch.ptr, sc, ctx->d_err, s, ev3, prect, prev_rect,
                                            ctx->d_counts + 4));
         mark(ctx, EV_EMIT, s);
         bool in_alt = false;
-        GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, cap, ctx->d_counts + 2, sc, ctx->d_err,
-                                           &in_alt, s));
+        if (key_bytes == 2)
+            GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint16_t *>(keys), vals, static_cast<uint16_t *>(akeys),
+                                               avals, cap, ctx->d_counts + 2, sc, ctx->d_err, &in_alt, s));
+        else
+            GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint32_t *>(keys), vals, static_cast<uint32_t *>(akeys),
+                                               avals, cap, ctx->d_counts + 2, sc, ctx->d_err, &in_alt, s));
         mark(ctx, EV_SORT, s);
-        uint64_t *sk = in_alt ? akeys : keys;
+        const void *sk = in_alt ? akeys : keys;
         uint32_t *sv = in_alt ? avals : vals;
-        GS_CUDA(ctx, gs_launch_ranges_dev(sk, sv, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s));
+        GS_CUDA(ctx, gs_launch_ranges_tiles(sk, key_bytes, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s));
         mark(ctx, EV_RANGES, s);
         if ((st = launch_blend(ctx, reader(ctx, rec, dtype), sv, ranges, grid, cam, opts, fb, ctx->d_counts + 2,
                                cap, s)) != GS_OK)

@@ -197,7 +197,69 @@ __global__ void ranges_kernel(const uint64_t *__restrict__ keys, int64_t n_host,
     if (i == n - 1) ranges[2 * tile + 1] = (uint32_t)n;
 }
 
+// Per-tile [first, last+1) of sorted tile-id keys; ranges must be zeroed
+// first. Thread t looks at keys [8t, 8t + 8) (one or two 16-byte loads while
+// the capacity allows, so the grid covers the capacity) and the key before
+// them; a boundary between keys i-1 and i opens tile key[i] and closes tile
+// key[i-1].
+template <typename KT>
+__global__ void __launch_bounds__(256) ranges_tiles_kernel(const KT *__restrict__ keys, int64_t n_capacity,
+                                                          const unsigned long long *d_n, int32_t n_tiles,
+                                                          uint32_t *__restrict__ ranges, uint32_t *d_err) {
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+    const int64_t n = (int64_t)*d_n;
+    if (i0 >= n) return;
+    uint32_t k[8];
+    if (i0 + 8 <= n_capacity) {
+        const uint4 a = reinterpret_cast<const uint4 *>(keys + i0)[0];
+        if (sizeof(KT) == 2) {
+            k[0] = a.x & 0xffffu; k[1] = a.x >> 16; k[2] = a.y & 0xffffu; k[3] = a.y >> 16;
+            k[4] = a.z & 0xffffu; k[5] = a.z >> 16; k[6] = a.w & 0xffffu; k[7] = a.w >> 16;
+        } else {
+            const uint4 b = reinterpret_cast<const uint4 *>(keys + i0)[1];
+            k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+            k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) k[j] = i0 + j < n ? (uint32_t)keys[i0 + j] : 0u;
+    }
+    uint32_t prev = i0 > 0 ? (uint32_t)keys[i0 - 1] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int64_t i = i0 + j;
+        if (i >= n) break;
+        const uint32_t t = k[j];
+        if (t >= (uint32_t)n_tiles) {
+            atomicOr(d_err, kErrRange);
+            return;
+        }
+        if (t != prev) {
+            ranges[2 * t] = (uint32_t)i;
+            if (prev < (uint32_t)n_tiles) ranges[2 * prev + 1] = (uint32_t)i;
+        }
+        if (i == n - 1) ranges[2 * t + 1] = (uint32_t)n;
+        prev = t;
+    }
+}
+
 }  // namespace
+
+cudaError_t gs_launch_ranges_tiles(const void *keys, int key_bytes, int64_t n_capacity,
+                                   const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
+                                   uint32_t *d_err, cudaStream_t s) {
+    if (key_bytes != 2 && key_bytes != 4) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess || n_capacity == 0) return e;
+    const unsigned blocks = (unsigned)((n_capacity + 8 * 256 - 1) / (8 * 256));
+    if (key_bytes == 2)
+        ranges_tiles_kernel<uint16_t><<<blocks, 256, 0, s>>>(static_cast<const uint16_t *>(keys), n_capacity, d_n,
+                                                            n_tiles, ranges, d_err);
+    else
+        ranges_tiles_kernel<uint32_t><<<blocks, 256, 0, s>>>(static_cast<const uint32_t *>(keys), n_capacity, d_n,
+                                                            n_tiles, ranges, d_err);
+    return cudaGetLastError();
+}
 
 size_t gs_scan_scratch_bytes(int64_t n) {
     const int64_t parts = (n + kScanTile - 1) / kScanTile;

@@ -22,6 +22,9 @@ inline void gs_carveout(F *kernel) {
 
 namespace gs {
 
+// Key slots per block of the key emission kernel (2^11 = 2048).
+constexpr int kKeyBlockLog2 = 11;
+
 // Constants of the standard 3DGS formulation (the paper cites it for Eq. 1
 // and for the 3-sigma bound of Sec. 4.4 but prints none of them).
 constexpr float kDilation = 0.3f;         // px^2 added to the 2D covariance diagonal
@@ -333,6 +336,17 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
                                   unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64);
+// The same over 32- and 16-bit keys (tile ids of a frame's tile sort).
+cudaError_t gs_launch_sort_passes(uint32_t *keys, uint32_t *values, uint32_t *alt_keys,
+                                  uint32_t *alt_values, int64_t n_capacity,
+                                  const unsigned long long *d_n, const GsSortScratch &sc,
+                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64);
+cudaError_t gs_launch_sort_passes(uint16_t *keys, uint32_t *values, uint16_t *alt_keys,
+                                  uint32_t *alt_values, int64_t n_capacity,
+                                  const unsigned long long *d_n, const GsSortScratch &sc,
+                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64);
 
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
@@ -347,22 +361,31 @@ cudaError_t gs_launch_blend_tma(const RecordReader &rd, const uint32_t *values, 
 
 // Per-frame binning front end, depth first: (1) projection of every Gaussian,
 // appending each visible one to a compact list as (tiles << 32 | depth bits,
-// index) with the depth digit histograms; (2) a stable radix sort of that list
-// by depth (4 digit passes over the visible Gaussians only); (3) a scan of the
-// tile counts in depth order giving each entry its first key slot; (4)
-// emission of the (tile, depth) keys in depth order with the tile digit
-// histograms + bucket offsets of the tile sort `sc` (carved with digit0 = 4),
-// which then needs only the tile digits because it is stable.
+// index), in index order (the list slots come from a decoupled look-back
+// scan), with the depth digit histograms; (2) a stable radix sort of that
+// list by depth (4 digit passes over the visible Gaussians only), which so
+// orders it by (depth bits, index); (3) a scan of the tile counts in depth
+// order giving each entry its first key slot; (4) emission of the keys — the
+// tile id alone, key_bytes = 2 (fewer than 65536 tiles) or 4 — in that
+// order, with the tile digit histograms + bucket offsets of the tile sort
+// `sc` (carved with digit0 = 0). The stable tile sort then leaves every
+// tile's list in (depth bits, index) order.
 // counts[0] = K, counts[1] = visible Gaussians, counts[2] = K if it fits in
 // `capacity` else 0 (the tile sort and ranges then see an empty list and the
 // overflow bit is set in d_err), counts[3] = visible Gaussians (the depth
 // sort's count). `scan_scratch`: gs_fused_scratch_bytes(n, capacity).
 size_t gs_fused_scratch_bytes(int64_t n, int64_t capacity);
 size_t gs_key_block_bytes(int64_t capacity);
+// Per-tile [first, last + 1) of tile-id keys sorted by gs_launch_project_bin
+// + the tile sort (key_bytes 2 or 4; *d_n keys, the grid covering
+// n_capacity); empty tiles get [0, 0).
+cudaError_t gs_launch_ranges_tiles(const void *keys, int key_bytes, int64_t n_capacity,
+                                   const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
+                                   uint32_t *d_err, cudaStream_t s);
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
                                   int lp_dtype,
-                                  uint64_t *keys, uint32_t *values,
+                                  void *keys, int key_bytes, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
                                   const cudaEvent_t *marks = nullptr /* 3 events or null */,

@@ -210,31 +210,36 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs P) {
 // Front end of a frame, depth first:
 //  P. project_list_kernel: one thread per Gaussian projects it and writes the
 //     record of a visible one; every block reserves, with one atomicAdd on a
-//     packed 64-bit counter (visible count << 33 | key count), a range of a
-//     compact list of the visible Gaussians (tiles << 32 | depth bits, index)
-//     and counts the four depth digits. The last block turns the counts into
-//     the depth sort's bucket offsets.
+//     packed 64-bit counter (visible count << 33 | key count), a segment of a
+//     compact list of the visible Gaussians (tiles << 32 | depth bits, index),
+//     notes the segment in a per-block table and counts the four depth
+//     digits. The last block turns the counts into the depth sort's bucket
+//     offsets and the table's counts, in block order, into the segments'
+//     places in index order.
+//  G. list_gather_kernel: one warp per segment copies it to its place, so
+//     the list is in Gaussian index order.
 //  D. the depth sort: four onesweep digit passes over the compact list.
 //  S. entry_scan_kernel: exclusive scan of the tile counts in depth order
 //     (decoupled look-back) giving each entry its first key slot, and the
 //     entry that covers the first slot of every key block.
 //  E. emit_keys_kernel: threads own runs of eight key slots, find their
-//     entries (whose first slots ascend) and write the keys — balanced
-//     however large a single splat is — while counting the tile digits. The
+//     entries (whose first slots ascend) and produce the keys — balanced
+//     however large a single splat is — while counting the tile digits; the
+//     block writes its keys and values out in coalesced 16-byte stores. A
+//     key is the tile id alone (16 bits below 65536 tiles, else 32). The
 //     last block turns the counts into the tile sort's bucket offsets and
 //     publishes the key count it should use.
-// The keys are emitted in depth order, so the stable sort on the tile digits
-// alone leaves them ordered by (tile, depth). Entries of equal depth keep the
-// compact list's order, which depends on scheduling; the ranges kernel puts
-// each run of equal keys in Gaussian index order, so the final lists are
-// exactly ordered by (tile, depth bits, index).
+// The gathered list is in index order and the depth sort is stable, so
+// entries are in (depth bits, index) order and the keys are emitted in it; the stable sort
+// on the tile id then leaves every tile's list exactly in (depth bits, index)
+// order, with no tie fix-up.
 // ---------------------------------------------------------------------------
 constexpr int kMaxPasses = 8;                  // batched path: depth and tile digits
 constexpr int kMaxTilePasses = 4;
 constexpr unsigned long long kKeyMask = (1ull << 33) - 1;
-constexpr int kKeyBlockLog2 = 11;              // key slots per emission block: 2048
 constexpr int kKeyBlock = 1 << kKeyBlockLog2;
 constexpr int kKeysPerThread = kKeyBlock / 256;
+static_assert(kKeysPerThread == 8, "emission stages eight keys per thread");
 constexpr int kDepthPasses = 4;                // the depth bits are the low word of a list key
 constexpr int kDepthItems = 8;                 // short list: smaller sort partitions, shorter latency
 constexpr int kEntryItems = 8;                 // list entries per thread of the entry scan
@@ -247,6 +252,8 @@ struct ListArgs {
     uint32_t *lp_gb;
     int lp_dtype;
     unsigned long long *packed;  // visible << 33 | keys
+    uint2 *seg;                  // per block: (first list slot, visible count)
+    uint32_t *seg_dst;           // per block: first slot of its segment in index order
     uint64_t *lkeys;             // n: tiles << 32 | depth bits of visible entry j
     uint32_t *lvals;             // n: its Gaussian index
     GsSortScratch dsc;           // the depth sort's histograms, bucket offsets, ticket
@@ -316,10 +323,13 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
         bt += s_t[w];
         bv += s_v[w];
     }
-    if (tid == 0) s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) : 0ull;
+    if (tid == 0) {
+        s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) >> 33 : 0ull;
+        A.seg[blockIdx.x] = make_uint2((uint32_t)s_base, bv);
+    }
     __syncthreads();
     if (v) {
-        const uint64_t j = (s_base >> 33) + pv + iv - 1;
+        const uint64_t j = s_base + pv + iv - 1;
         const uint32_t dbits = __float_as_uint(pr.r2.y);
         A.lkeys[j] = ((uint64_t)t << 32) | dbits;
         A.lvals[j] = (uint32_t)i;
@@ -344,7 +354,58 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
         const uint32_t c = __ldcg(&A.dsc.hist[d * 256 + tid]);
         A.dsc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
     }
+    // Segments in block (= index) order, 4096 blocks per round: thread tid
+    // takes 16 consecutive table entries (eight 16-byte loads in flight).
+    const int64_t nb = gridDim.x;
+    uint32_t carry = 0;
+    for (int64_t r0 = 0; r0 < nb; r0 += 256 * 16) {
+        const int64_t b0 = r0 + (int64_t)tid * 16;
+        uint32_t cnt[16];
+        if (b0 + 16 <= nb) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(A.seg + b0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint4 x = __ldcg(q + k);
+                cnt[2 * k] = x.y;
+                cnt[2 * k + 1] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) cnt[k] = b0 + k < nb ? __ldcg(&A.seg[b0 + k].y) : 0u;
+        }
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sum += cnt[k];
+        const uint32_t ex = block_exclusive_scan_256(sum, s_tmp);
+        uint32_t pre = carry + ex;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (b0 + k < nb) A.seg_dst[b0 + k] = pre;
+            pre += cnt[k];
+        }
+        if (tid == 255) s_tmp[0] = ex + sum;  // the round's total (s_tmp is free again)
+        __syncthreads();
+        carry += s_tmp[0];
+        __syncthreads();
+    }
     if (tid == 0) A.counts[3] = __ldcg(A.packed) >> 33;
+}
+
+// Warp w of block b copies list segment 8 b + w (the visible Gaussians of
+// one projection block, in index order) to its place in index order.
+__global__ void __launch_bounds__(256) list_gather_kernel(const uint2 *__restrict__ seg,
+                                                         const uint32_t *__restrict__ seg_dst, int64_t n_seg,
+                                                         const uint64_t *__restrict__ lkeys,
+                                                         const uint32_t *__restrict__ lvals, uint64_t *okeys,
+                                                         uint32_t *ovals) {
+    const int64_t b = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (b >= n_seg) return;
+    const uint2 sg = seg[b];
+    const uint32_t dst = seg_dst[b];
+    for (uint32_t k = threadIdx.x & 31; k < sg.y; k += 32) {
+        okeys[dst + k] = lkeys[sg.x + k];
+        ovals[dst + k] = lvals[sg.x + k];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -448,7 +509,7 @@ void launch_project_temporal(const TemporalProjectArgs &A, unsigned blocks, cuda
 
 struct EntryScanArgs {
     const uint64_t *lkeys;             // depth-sorted list keys (tile count in the high word)
-    const unsigned long long *packed;  // visible << 33 | keys
+    const unsigned long long *count;   // list entries
     uint32_t *off;                     // out: first key slot of entry j
     uint32_t *block_entry;             // out: entry covering the first slot of each key block
     int64_t n_key_blocks;              // ceil(capacity / kKeyBlock)
@@ -469,7 +530,7 @@ __global__ void __launch_bounds__(256) entry_scan_kernel(const EntryScanArgs A) 
     if (tid == 0) s_part = atomicAdd(A.counter, 1u);
     __syncthreads();
     const int64_t p = s_part;
-    const int64_t nv = (int64_t)(*A.packed >> 33);
+    const int64_t nv = (int64_t)*A.count;
     if (p * kEntryTile >= nv) return;
     const int64_t base = p * kEntryTile + (int64_t)tid * kEntryItems;
     uint32_t t[kEntryItems];
@@ -527,7 +588,7 @@ struct EmitArgs {
     const uint32_t *list_off;     // first key slot of entry j (ascending)
     const uint32_t *block_entry;
     GsGrid grid;
-    uint64_t *keys;
+    void *keys;                   // tile ids (KT)
     uint32_t *values;
     int64_t capacity;
     unsigned long long *counts;  // out: [0] K, [1] visible, [2] K if it fits else 0
@@ -540,9 +601,15 @@ struct EmitArgs {
 // ascending) are staged in shared memory; a thread finds the entry of its
 // first slot by binary search and walks forward. Digit counts of a thread's
 // run of keys are merged before they are added to the block's histogram.
+// Keys and values are staged in shared memory and written with 16-byte
+// stores (the key buffers are 256-byte aligned and blocks start at multiples
+// of 2048 slots).
+template <typename KT>
 __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
     __shared__ uint32_t s_hist[kMaxTilePasses * 256];
     __shared__ uint32_t s_off[kKeyBlock + 2], s_idx[kKeyBlock + 2];
+    __shared__ __align__(16) KT s_key[kKeyBlock];
+    __shared__ __align__(16) uint32_t s_val[kKeyBlock];
     __shared__ uint32_t s_tmp[8];
     __shared__ int s_j0, s_cnt;
     __shared__ bool s_last;
@@ -576,12 +643,16 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
             if ((int64_t)s_off[mid] <= kb) lo = mid; else hi = mid - 1;
         }
         int e = -1;
-        uint32_t g = 0, dbits = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0;
+        uint32_t g = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0;
         uint32_t run_digit[kMaxTilePasses], run_count[kMaxTilePasses];
+        uint32_t tk[kKeysPerThread], tv[kKeysPerThread];
         for (int d = 0; d < kMaxTilePasses; ++d) { run_digit[d] = 0xffffffffu; run_count[d] = 0; }
+#pragma unroll
         for (int q = 0; q < kKeysPerThread; ++q) {
             const int64_t k = kb + q;
-            if (k >= K) break;
+            tk[q] = 0u;
+            tv[q] = 0u;
+            if (k >= K) continue;
             if (e < 0 || (uint64_t)k >= eend) {
                 if (e >= 0) ++lo;
                 while (lo + 1 < s_cnt && (int64_t)s_off[lo + 1] <= k) ++lo;
@@ -596,13 +667,12 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
                 x0 = (uint32_t)R.x0;
                 y0 = (uint32_t)R.y0;
                 eend = ebase + w * (uint32_t)(R.y1 - R.y0);
-                dbits = __float_as_uint(r2.y);
             }
             const uint32_t m = (uint32_t)(k - ebase);
             const uint32_t qy = m / w, rx = m - qy * w;
             const uint32_t tile = (y0 + qy) * (uint32_t)G.tiles_x + x0 + rx;
-            E.keys[k] = ((uint64_t)tile << 32) | dbits;
-            E.values[k] = g;
+            tk[q] = tile;
+            tv[q] = g;
             for (int d = 0; d < passes; ++d) {
                 const uint32_t dg = (tile >> (8 * d)) & 255u;
                 if (dg != run_digit[d]) {
@@ -615,11 +685,36 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
         }
         for (int d = 0; d < passes; ++d)
             if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
+        // A thread's eight slots are contiguous: vector stores into the
+        // staging arrays (entries past K are never written out).
+        uint4 *sv4 = reinterpret_cast<uint4 *>(s_val + tid * kKeysPerThread);
+        sv4[0] = make_uint4(tv[0], tv[1], tv[2], tv[3]);
+        sv4[1] = make_uint4(tv[4], tv[5], tv[6], tv[7]);
+        uint4 *sk4 = reinterpret_cast<uint4 *>(s_key + tid * kKeysPerThread);
+        if (sizeof(KT) == 2) {
+            sk4[0] = make_uint4(tk[0] | tk[1] << 16, tk[2] | tk[3] << 16, tk[4] | tk[5] << 16, tk[6] | tk[7] << 16);
+        } else {
+            sk4[0] = make_uint4(tk[0], tk[1], tk[2], tk[3]);
+            sk4[1] = make_uint4(tk[4], tk[5], tk[6], tk[7]);
+        }
     }
     __syncthreads();
-    if (active)
+    if (active) {
+        // Slots [k0, k0 + nk) of this block, in 16-byte vectors (the ragged
+        // end of the last block element by element).
+        const int nk = (int)((K - k0) < kKeyBlock ? (K - k0) : kKeyBlock);
+        constexpr int kPerVec = 16 / sizeof(KT);
+        KT *gk = static_cast<KT *>(E.keys) + k0;
+        uint32_t *gv = E.values + k0;
+        for (int q = tid; q < nk / kPerVec; q += 256)
+            reinterpret_cast<uint4 *>(gk)[q] = reinterpret_cast<const uint4 *>(s_key)[q];
+        for (int q = (nk / kPerVec) * kPerVec + tid; q < nk; q += 256) gk[q] = s_key[q];
+        for (int q = tid; q < nk / 4; q += 256)
+            reinterpret_cast<uint4 *>(gv)[q] = reinterpret_cast<const uint4 *>(s_val)[q];
+        for (int q = (nk / 4) * 4 + tid; q < nk; q += 256) gv[q] = s_val[q];
         for (int q = tid; q < passes * 256; q += 256)
             if (s_hist[q]) atomicAdd(&E.sc.hist[q], s_hist[q]);
+    }
     __syncthreads();
     if (tid == 0) {
         __threadfence();
@@ -847,10 +942,10 @@ namespace {
 
 // Front-end scratch: the packed counter and the entry scan's partition
 // counter, the depth sort's scratch and the entry scan's status words (all
-// zeroed per frame), then the compact list, its sort buffers, the entries'
+// zeroed per frame), then the segment table, the compact list, its sort buffers, the entries'
 // first slots and the key-block table.
 struct FrontLayout {
-    size_t dsort, scan_status, zero, lkeys, lvals, akeys, avals, off, block_entry, total;
+    size_t dsort, scan_status, zero, seg, seg_dst, lkeys, lvals, akeys, avals, off, block_entry, total;
 };
 
 FrontLayout front_layout(int64_t n, int64_t capacity) {
@@ -863,6 +958,10 @@ FrontLayout front_layout(int64_t n, int64_t capacity) {
     L.scan_status = o;
     o += al((size_t)((nn + kEntryTile - 1) / kEntryTile + 1) * 8);
     L.zero = o;
+    L.seg = o;
+    o += al((size_t)((nn + 255) / 256) * 8);
+    L.seg_dst = o;
+    o += al((size_t)((nn + 255) / 256) * 4);
     L.lkeys = o;
     o += al((size_t)nn * 8);
     L.lvals = o;
@@ -890,13 +989,14 @@ size_t gs_key_block_bytes(int64_t capacity) {
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
                                   int lp_dtype,
-                                  uint64_t *keys, uint32_t *values,
+                                  void *keys, int key_bytes, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
                                   const cudaEvent_t *marks, uint2 *prect, const uint2 *prev_rect,
                                   unsigned long long *moved) {
     // counts and the front-end counters start at zero; the tile sort's
     // scratch was zeroed by the caller.
+    if (key_bytes != 2 && key_bytes != 4) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const FrontLayout L = front_layout(g.n, capacity);
@@ -913,6 +1013,8 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     A.lp_gb = lp_gb;
     A.lp_dtype = lp_dtype;
     A.packed = reinterpret_cast<unsigned long long *>(base);
+    A.seg = reinterpret_cast<uint2 *>(base + L.seg);
+    A.seg_dst = reinterpret_cast<uint32_t *>(base + L.seg_dst);
     A.lkeys = reinterpret_cast<uint64_t *>(base + L.lkeys);
     A.lvals = reinterpret_cast<uint32_t *>(base + L.lvals);
     A.dsc = gs_sort_carve_digits(base + L.dsort, g.n, 0, kDepthPasses, kDepthItems);
@@ -930,21 +1032,29 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (marks && marks[0]) cudaEventRecord(marks[0], s);
-    // Depth sort of the compact list (its count is counts[3]).
+    // The list in index order (in the alternate buffers), then its depth sort
+    // (count counts[3]; an even number of passes leaves it there).
+    uint64_t *gkeys = reinterpret_cast<uint64_t *>(base + L.akeys);
+    uint32_t *gvals = reinterpret_cast<uint32_t *>(base + L.avals);
+    list_gather_kernel<<<(blocks + 7) / 8, 256, 0, s>>>(A.seg, A.seg_dst, (int64_t)blocks, A.lkeys, A.lvals, gkeys,
+                                                         gvals);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uint32_t *off = reinterpret_cast<uint32_t *>(base + L.off);
+    uint32_t *block_entry = reinterpret_cast<uint32_t *>(base + L.block_entry);
+    const int64_t n_key_blocks = (capacity + kKeyBlock - 1) / kKeyBlock;
     bool in_alt = false;
-    e = gs_launch_sort_passes(A.lkeys, A.lvals, reinterpret_cast<uint64_t *>(base + L.akeys),
-                              reinterpret_cast<uint32_t *>(base + L.avals), g.n, counts + 3, A.dsc, d_err,
-                              &in_alt, s);
+    e = gs_launch_sort_passes(gkeys, gvals, A.lkeys, A.lvals, g.n, counts + 3, A.dsc, d_err, &in_alt, s);
     if (e != cudaSuccess) return e;
     if (marks && marks[1]) cudaEventRecord(marks[1], s);
-    const uint64_t *skeys = in_alt ? reinterpret_cast<const uint64_t *>(base + L.akeys) : A.lkeys;
-    const uint32_t *svals = in_alt ? reinterpret_cast<const uint32_t *>(base + L.avals) : A.lvals;
+    const uint64_t *skeys = in_alt ? A.lkeys : gkeys;
+    const uint32_t *svals = in_alt ? A.lvals : gvals;
     EntryScanArgs S;
     S.lkeys = skeys;
-    S.packed = A.packed;
-    S.off = reinterpret_cast<uint32_t *>(base + L.off);
-    S.block_entry = reinterpret_cast<uint32_t *>(base + L.block_entry);
-    S.n_key_blocks = (capacity + kKeyBlock - 1) / kKeyBlock;
+    S.count = counts + 3;
+    S.off = off;
+    S.block_entry = block_entry;
+    S.n_key_blocks = n_key_blocks;
     S.counter = reinterpret_cast<uint32_t *>(base + 8);
     S.status = reinterpret_cast<unsigned long long *>(base + L.scan_status);
     S.d_err = d_err;
@@ -957,8 +1067,14 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
                values, capacity, counts, sc, d_err};
     // One block per 2048 key slots of the capacity (blocks past K only take
     // their ticket).
-    gs_carveout(emit_keys_kernel);
-    emit_keys_kernel<<<(unsigned)((capacity + kKeyBlock - 1) / kKeyBlock), 256, 0, s>>>(E);
+    const unsigned eblocks = (unsigned)((capacity + kKeyBlock - 1) / kKeyBlock);
+    if (key_bytes == 2) {
+        gs_carveout(emit_keys_kernel<uint16_t>);
+        emit_keys_kernel<uint16_t><<<eblocks, 256, 0, s>>>(E);
+    } else {
+        gs_carveout(emit_keys_kernel<uint32_t>);
+        emit_keys_kernel<uint32_t><<<eblocks, 256, 0, s>>>(E);
+    }
     return cudaGetLastError();
 }
 

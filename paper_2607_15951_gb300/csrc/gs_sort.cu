@@ -1,4 +1,4 @@
-// gs_sort.cu — stable LSD radix sort of (u64 key, u32 value) pairs, written
+// gs_sort.cu — stable LSD radix sort of (key, u32 value) pairs, written
 // from the Onesweep design (Adinets and Merrill, 2022): one up-front pass
 // builds the digit histograms of every pass at once, then each 8-bit digit
 // pass is a single launch in which every block
@@ -10,6 +10,9 @@
 //      (one thread per digit; every wait is bounded in time),
 //   4. reorders the pairs in shared memory by digit and writes them out in
 //      digit-contiguous runs, so global stores are coalesced.
+// Keys are 64-bit (tile << 32 | depth bits, the staged binning entry points),
+// or 16/32-bit tile ids (a frame's tile sort, whose keys arrive in depth
+// order: the sort moves 6 or 8 bytes per pair and pass instead of 12).
 #include "gs_internal.cuh"
 
 #ifndef GS_SORT_MIN_BLOCKS
@@ -18,6 +21,7 @@
 #ifndef GS_SORT_HIST_AGG
 #define GS_SORT_HIST_AGG 0
 #endif
+
 
 namespace {
 
@@ -87,15 +91,15 @@ histogram_kernel(const uint64_t *__restrict__ keys, int64_t n, int passes, SortS
     }
 }
 
-template <int ITEMS, int MIN_BLOCKS>
+template <typename KT, int ITEMS, int MIN_BLOCKS>
 __global__ void __launch_bounds__(kThreads, MIN_BLOCKS)
-onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n_host,
+onesweep_kernel(const KT *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                KT *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n_host,
                 const unsigned long long *d_n, int pass, int64_t parts, SortScratch sc,
-                uint32_t *d_err, unsigned long long timeout_ns) {
+                uint32_t *d_err, unsigned long long timeout_ns, bool ballot_rank) {
     constexpr int kItems = ITEMS, kTile = kThreads * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);                       // kTile
+    KT *s_keys = reinterpret_cast<KT *>(smem);                                  // kTile
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kTile);            // kTile
     uint32_t *s_whist = s_vals + kTile;                                         // kWarps x 256
     uint32_t *s_doff = s_whist + kWarps * kRadix;                               // 256
@@ -117,13 +121,13 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
 
     // Warp-striped load: warp w holds pairs [w*32*kItems, (w+1)*32*kItems) of
     // the partition, item j of lane l at offset j*32 + l (coalesced).
-    uint64_t key[kItems];
+    KT key[kItems];
     uint32_t val[kItems];
     uint32_t rank[kItems];
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
-        key[j] = idx < n ? keys_in[idx] : ~0ull;
+        key[j] = idx < n ? keys_in[idx] : (KT)~(KT)0;
         val[j] = idx < n ? vals_in[idx] : 0u;
     }
     // Stable rank within the warp, in (item, lane) order. Out-of-range items
@@ -133,7 +137,21 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     for (int j = 0; j < kItems; ++j) {
         const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
         const uint32_t d = idx < n ? (uint32_t)((key[j] >> shift) & 255) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // Lanes with equal digits: warp match (fast when a warp holds few
+        // distinct digits), or 9 ballots, one per bit of 0..256 (constant
+        // cost, faster when digits are diverse).
+        uint32_t peers;
+        if (ballot_rank) {
+            peers = 0xffffffffu;
+#pragma unroll
+            for (int b = 0; b < 9; ++b) {
+                const bool bit = (d >> b) & 1u;
+                const uint32_t m = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? m : ~m;
+            }
+        } else {
+            peers = __match_any_sync(0xffffffffu, d);
+        }
         const uint32_t lt = peers & lanemask_lt();
         const uint32_t before = d < 256u ? my_hist[d] : 0u;
         __syncwarp();
@@ -217,7 +235,7 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     __syncthreads();
     const int valid = (int)((n - base) < kTile ? (n - base) : kTile);
     for (int i = tid; i < valid; i += kThreads) {
-        const uint64_t k = s_keys[i];
+        const KT k = s_keys[i];
         const uint32_t d = (uint32_t)((k >> shift) & 255);
         const uint64_t gp = (uint64_t)s_gbase[d] + (uint32_t)(i - s_doff[d]);
         // Only reachable after a timed-out look-back left offsets meaningless.
@@ -230,9 +248,63 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     }
 }
 
-template <int ITEMS>
+template <typename KT, int ITEMS>
 constexpr size_t onesweep_smem() {
-    return (size_t)kThreads * ITEMS * 12 + (size_t)kWarps * kRadix * 4 + 2 * kRadix * 4 + kWarps * 4 + 16;
+    return (size_t)kThreads * ITEMS * (sizeof(KT) + 4) + (size_t)kWarps * kRadix * 4 + 2 * kRadix * 4 +
+           kWarps * 4 + 16;
+}
+
+template <typename KT, int ITEMS, int MIN_BLOCKS>
+cudaError_t prepare_shape() {
+    return cudaFuncSetAttribute(onesweep_kernel<KT, ITEMS, MIN_BLOCKS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)onesweep_smem<KT, ITEMS>());
+}
+
+// The digit passes of sc over n_capacity pairs (count *d_n when given),
+// ping-ponging between the two buffers.
+template <typename KT>
+cudaError_t launch_passes(KT *keys, uint32_t *values, KT *alt_keys, uint32_t *alt_values, int64_t n_capacity,
+                          const unsigned long long *d_n, const GsSortScratch &sc, uint32_t *d_err,
+                          bool *result_in_alt, cudaStream_t s, unsigned long long timeout_ns, int max_passes) {
+    *result_in_alt = false;
+    // Three partition shapes: 8 items per thread for short lists (shorter
+    // per-partition latency), GS_SORT_ITEMS (16) by default, 12 items with
+    // three blocks per SM for long lists (more partitions in flight).
+    if (sc.items != 8 && sc.items != kItems && sc.items != kLargeItems) return cudaErrorInvalidValue;
+    const int shape = sc.items == kLargeItems && kLargeItems != kItems ? 2 : (sc.items == 8 && kItems != 8 ? 0 : 1);
+    const size_t smem = shape == 0 ? onesweep_smem<KT, 8>() : shape == 2 ? onesweep_smem<KT, kLargeItems>()
+                                                                         : onesweep_smem<KT, kItems>();
+    cudaError_t e = shape == 0   ? prepare_shape<KT, 8, GS_SORT_MIN_BLOCKS>()
+                    : shape == 2 ? prepare_shape<KT, kLargeItems, 3>()
+                                 : prepare_shape<KT, kItems, GS_SORT_MIN_BLOCKS>();
+    if (e != cudaSuccess) return e;
+    const KT *kin = keys;
+    const uint32_t *vin = values;
+    KT *kout = alt_keys;
+    uint32_t *vout = alt_values;
+    const int passes = sc.passes < max_passes ? sc.passes : max_passes;
+    for (int pass = 0; pass < passes; ++pass) {
+        // Lower digits of depth bits and tile ids are diverse within a warp;
+        // the top digit (exponent byte, high tile bits) takes few values.
+        const bool ballot = pass + 1 < sc.passes;
+        if (shape == 0)
+            onesweep_kernel<KT, 8, GS_SORT_MIN_BLOCKS><<<(unsigned)sc.parts, kThreads, smem, s>>>(
+                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns, ballot);
+        else if (shape == 2)
+            onesweep_kernel<KT, kLargeItems, 3><<<(unsigned)sc.parts, kThreads, smem, s>>>(
+                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns, ballot);
+        else
+            onesweep_kernel<KT, kItems, GS_SORT_MIN_BLOCKS><<<(unsigned)sc.parts, kThreads, smem, s>>>(
+                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns, ballot);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        kin = kout;
+        vin = vout;
+        kout = (kout == alt_keys) ? keys : alt_keys;
+        vout = (vout == alt_values) ? values : alt_values;
+    }
+    *result_in_alt = (passes & 1) != 0;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -276,45 +348,26 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
                                   unsigned long long timeout_ns, int max_passes) {
-    *result_in_alt = false;
-    // Three partition shapes: 8 items per thread for short lists (shorter
-    // per-partition latency), GS_SORT_ITEMS (16) by default, 12 items with
-    // three blocks per SM for long lists (more partitions in flight).
-    if (sc.items != 8 && sc.items != kItems && sc.items != kLargeItems) return cudaErrorInvalidValue;
-    const int shape = sc.items == kLargeItems && kLargeItems != kItems ? 2 : (sc.items == 8 && kItems != 8 ? 0 : 1);
-    const size_t smem = shape == 0 ? onesweep_smem<8>() : shape == 2 ? onesweep_smem<kLargeItems>()
-                                                                     : onesweep_smem<kItems>();
-    cudaError_t e = shape == 0   ? cudaFuncSetAttribute(onesweep_kernel<8, GS_SORT_MIN_BLOCKS>,
-                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                    : shape == 2 ? cudaFuncSetAttribute(onesweep_kernel<kLargeItems, 3>,
-                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                                 : cudaFuncSetAttribute(onesweep_kernel<kItems, GS_SORT_MIN_BLOCKS>,
-                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const uint64_t *kin = keys;
-    const uint32_t *vin = values;
-    uint64_t *kout = alt_keys;
-    uint32_t *vout = alt_values;
-    const int passes = sc.passes < max_passes ? sc.passes : max_passes;
-    for (int pass = 0; pass < passes; ++pass) {
-        if (shape == 0)
-            onesweep_kernel<8, GS_SORT_MIN_BLOCKS><<<(unsigned)sc.parts, kThreads, smem, s>>>(
-                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
-        else if (shape == 2)
-            onesweep_kernel<kLargeItems, 3><<<(unsigned)sc.parts, kThreads, smem, s>>>(
-                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
-        else
-            onesweep_kernel<kItems, GS_SORT_MIN_BLOCKS><<<(unsigned)sc.parts, kThreads, smem, s>>>(
-                kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        kin = kout;
-        vin = vout;
-        kout = (kout == alt_keys) ? keys : alt_keys;
-        vout = (vout == alt_values) ? values : alt_values;
-    }
-    *result_in_alt = (passes & 1) != 0;
-    return cudaSuccess;
+    return launch_passes<uint64_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, d_err, result_in_alt, s,
+                                   timeout_ns, max_passes);
+}
+
+cudaError_t gs_launch_sort_passes(uint32_t *keys, uint32_t *values, uint32_t *alt_keys,
+                                  uint32_t *alt_values, int64_t n_capacity,
+                                  const unsigned long long *d_n, const GsSortScratch &sc,
+                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                  unsigned long long timeout_ns, int max_passes) {
+    return launch_passes<uint32_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, d_err, result_in_alt, s,
+                                   timeout_ns, max_passes);
+}
+
+cudaError_t gs_launch_sort_passes(uint16_t *keys, uint32_t *values, uint16_t *alt_keys,
+                                  uint32_t *alt_values, int64_t n_capacity,
+                                  const unsigned long long *d_n, const GsSortScratch &sc,
+                                  uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                  unsigned long long timeout_ns, int max_passes) {
+    return launch_passes<uint16_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, d_err, result_in_alt, s,
+                                   timeout_ns, max_passes);
 }
 
 cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,

@@ -446,6 +446,27 @@ def test_render_equal_depths_follow_index_order(ctx, oracle_mod):
                           img.last[~img.flag.astype(bool)])
 
 
+@pytest.mark.parametrize("n", [20_000, 90_000])
+def test_render_depth_ties_short_and_long_lists(ctx, oracle_mod, n):
+    """Depths drawn from eight values, so most Gaussians tie with thousands of
+    others, in lists of 18k and 82k visible Gaussians (9 and 41 depth-sort
+    partitions): every tile's list must be in (depth, index) order, as the
+    oracle's."""
+    s = scenes.uniform_box(n, 29)
+    rng = np.random.default_rng(29)
+    s.means[:, 2] = rng.choice(np.arange(3.0, 7.0, 0.5, dtype=np.float32), n)
+    s.log_scales[:] = s.log_scales - 1.0
+    cam = scenes.pinhole(320, 240)
+    out = gs.render(ctx, gs.scene_to_device(s), 0, cam)
+    torch.cuda.synchronize()
+    _, _, img = oracle_mod.render(s, cam)
+    st = compare_image(out["rgb"].cpu().numpy(), out["final_T"].cpu().numpy(), img)
+    st.pop("keep")
+    assert st["max_rgb_err"] <= RGB_TOL, st
+    keep = ~img.flag.astype(bool)
+    assert np.array_equal(out["n_contrib"].cpu().numpy()[keep], img.last[keep])
+
+
 def test_render_is_deterministic(ctx):
     scene, cams = scenes.workload("clustered_1m_1080p")
     g = gs.scene_to_device(scene)
