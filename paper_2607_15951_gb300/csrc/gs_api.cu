@@ -978,9 +978,12 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
     const ViewDesc *views = static_cast<const ViewDesc *>(B.views.ptr);
     GS_CUDA(ctx, cudaMemcpyAsync(B.views.ptr, B.h_views, (size_t)n_views * sizeof(ViewDesc),
                                  cudaMemcpyHostToDevice, s));
-    GS_CUDA(ctx, cudaMemsetAsync(B.sort.ptr, 0, gs_sort_scratch_bytes(B.key_cap, bits), s));
-    const GsSortScratch sc = gs_sort_carve(B.sort.ptr, B.key_cap, bits);
-    uint64_t *keys = static_cast<uint64_t *>(B.keys.ptr), *akeys = static_cast<uint64_t *>(B.akeys.ptr);
+    // The tile sort: 32-bit global tile ids emitted in (depth, view, index)
+    // order, so the stable sort on them alone orders every tile's list.
+    const int tile_passes = (bits - 32 + 7) / 8;
+    GS_CUDA(ctx, cudaMemsetAsync(B.sort.ptr, 0, gs_sort_scratch_bytes_digits(B.key_cap, tile_passes), s));
+    const GsSortScratch sc = gs_sort_carve_digits(B.sort.ptr, B.key_cap, 0, tile_passes);
+    uint32_t *keys = static_cast<uint32_t *>(B.keys.ptr), *akeys = static_cast<uint32_t *>(B.akeys.ptr);
     uint32_t *vals = static_cast<uint32_t *>(B.vals.ptr), *avals = static_cast<uint32_t *>(B.avals.ptr);
     uint2 *meta = static_cast<uint2 *>(B.meta.ptr);
     GS_CUDA(ctx, gs_launch_project_bin_batch(*g, views, n_views, static_cast<gs_record *>(B.rec.ptr),
@@ -990,12 +993,11 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
     bool in_alt = false;
     GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, B.key_cap, ctx->d_counts + 2, sc, ctx->d_err,
                                        &in_alt, s));
-    uint64_t *sk = in_alt ? akeys : keys;
+    const uint32_t *sk = in_alt ? akeys : keys;
     uint32_t *sv = in_alt ? avals : vals;
     B.joint_values = sv;
     uint32_t *ranges = static_cast<uint32_t *>(B.ranges.ptr);
-    GS_CUDA(ctx, gs_launch_ranges_batch(sk, sv, meta, B.key_cap, ctx->d_counts + 2, total_tiles, ranges,
-                                        ctx->d_err, s));
+    GS_CUDA(ctx, gs_launch_ranges_tiles(sk, 4, B.key_cap, ctx->d_counts + 2, total_tiles, ranges, ctx->d_err, s));
     uint32_t *qs = static_cast<uint32_t *>(B.queue.ptr);
     uint32_t *order = static_cast<uint32_t *>(B.order.ptr);
     GS_CUDA(ctx, gs_launch_queue(ranges, total_tiles, qs, order, s));
@@ -1097,15 +1099,16 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
             (lp && (st = ensure(ctx, B.geo, (size_t)rc * 16, "batch records")) != GS_OK) ||
             (lp && (st = ensure(ctx, B.oq, (size_t)rc * 8, "batch records")) != GS_OK) ||
             (lp && (st = ensure(ctx, B.gb, (size_t)rc * 4, "batch records")) != GS_OK) ||
-            (st = ensure(ctx, B.scratch, gs_batch_scratch_bytes(rc, kc), "batch scratch")) != GS_OK ||
+            (st = ensure(ctx, B.scratch, gs_batch_scratch_bytes(rc, kc, n, n_views), "batch scratch")) != GS_OK ||
             (st = ensure(ctx, B.ranges, (size_t)total_tiles * 8, "batch ranges")) != GS_OK ||
             (st = ensure(ctx, B.order, (size_t)total_tiles * 4, "batch queue")) != GS_OK ||
             (st = ensure(ctx, B.queue, gs_queue_scratch_bytes(), "batch queue")) != GS_OK ||
-            (st = ensure(ctx, B.keys, (size_t)kc * 8, "batch keys")) != GS_OK ||
+            (st = ensure(ctx, B.keys, (size_t)kc * 4, "batch keys")) != GS_OK ||
             (st = ensure(ctx, B.vals, (size_t)kc * 4, "batch values")) != GS_OK ||
-            (st = ensure(ctx, B.akeys, (size_t)kc * 8, "batch keys")) != GS_OK ||
+            (st = ensure(ctx, B.akeys, (size_t)kc * 4, "batch keys")) != GS_OK ||
             (st = ensure(ctx, B.avals, (size_t)kc * 4, "batch values")) != GS_OK ||
-            (st = ensure(ctx, B.sort, gs_sort_scratch_bytes(kc, bits), "batch sort scratch")) != GS_OK)
+            (st = ensure(ctx, B.sort, gs_sort_scratch_bytes_digits(kc, (bits - 32 + 7) / 8), "batch sort scratch")) !=
+                GS_OK)
             return st;
         void *after[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.oq.ptr, B.gb.ptr, B.scratch.ptr,
                          B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,

@@ -142,44 +142,12 @@ emit_kernel(const float4 *__restrict__ rec, const uint32_t *__restrict__ tiles,
     }
 }
 
-// Orders values[b, e) ascending (a run of equal keys): insertion sort for
-// short runs, Shell sort (Ciura gaps) for long ones.
-__device__ void sort_run(uint32_t *v, int64_t b, int64_t e, const uint2 *meta) {
-    const int64_t m = e - b;
-    const int gaps[] = {701, 301, 132, 57, 23, 10, 4, 1};
-    auto order = [&](uint32_t x) { return meta ? meta[x].y : x; };
-    for (int gi = 0; gi < 8; ++gi) {
-        const int64_t gap = gaps[gi];
-        if (gap >= m) continue;
-        for (int64_t i = b + gap; i < e; ++i) {
-            const uint32_t x = v[i];
-            const uint32_t ox = order(x);
-            int64_t j = i;
-            while (j - gap >= b && order(v[j - gap]) > ox) {
-                v[j] = v[j - gap];
-                j -= gap;
-            }
-            v[j] = x;
-        }
-    }
-}
-
-// Per-tile [first, last+1) of sorted keys; ranges must be zeroed first. The
-// key count is n_host, or *d_n when d_n is given. With fix_ties, each run of
-// equal keys (same tile, same depth bits) gets its values in ascending
-// Gaussian-index order, for keys emitted in an arbitrary order.
-__global__ void ranges_kernel(const uint64_t *__restrict__ keys, int64_t n_host,
-                              const unsigned long long *d_n, int32_t n_tiles,
-                              uint32_t *__restrict__ ranges, uint32_t *values, int fix_ties,
-                              const uint2 *meta, uint32_t *d_err) {
+// Per-tile [first, last+1) of n sorted (tile << 32 | depth bits) keys;
+// ranges must be zeroed first.
+__global__ void ranges_kernel(const uint64_t *__restrict__ keys, int64_t n, int32_t n_tiles,
+                              uint32_t *__restrict__ ranges, uint32_t *d_err) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t n = d_n ? (int64_t)*d_n : n_host;
     if (i >= n) return;
-    if (fix_ties && (i == 0 || keys[i - 1] != keys[i]) && i + 1 < n && keys[i + 1] == keys[i]) {
-        int64_t e = i + 2;
-        while (e < n && keys[e] == keys[i]) ++e;
-        sort_run(values, i, e, meta);
-    }
     const uint64_t tile = keys[i] >> 32;
     if (tile >= (uint64_t)n_tiles) {
         atomicOr(d_err, kErrRange);
@@ -298,28 +266,7 @@ cudaError_t gs_launch_ranges(const uint64_t *keys, int64_t n, int32_t n_tiles, u
     cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess || n == 0) return e;
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n, nullptr, n_tiles, ranges, nullptr, 0, nullptr, d_err);
-    return cudaGetLastError();
-}
-
-cudaError_t gs_launch_ranges_dev(const uint64_t *keys, uint32_t *values, int64_t n_capacity,
-                                 const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
-                                 uint32_t *d_err, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
-    if (e != cudaSuccess || n_capacity == 0) return e;
-    const unsigned blocks = (unsigned)((n_capacity + 255) / 256);
-    gs_carveout(ranges_kernel);
-    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n_capacity, d_n, n_tiles, ranges, values, 1, nullptr, d_err);
-    return cudaGetLastError();
-}
-
-cudaError_t gs_launch_ranges_batch(const uint64_t *keys, uint32_t *values, const uint2 *meta, int64_t n_capacity,
-                                   const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
-                                   uint32_t *d_err, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
-    if (e != cudaSuccess || n_capacity == 0) return e;
-    const unsigned blocks = (unsigned)((n_capacity + 255) / 256);
-    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n_capacity, d_n, n_tiles, ranges, values, 1, meta, d_err);
+    ranges_kernel<<<blocks, 256, 0, s>>>(keys, n, n_tiles, ranges, d_err);
     return cudaGetLastError();
 }
 

@@ -282,11 +282,7 @@ cudaError_t gs_launch_emit(const gs_record *records, const uint32_t *tiles,
 
 cudaError_t gs_launch_ranges(const uint64_t *keys, int64_t n, int32_t n_tiles, uint32_t *ranges,
                              uint32_t *d_err, cudaStream_t s);
-// Same with the key count read from *d_n (the grid covers n_capacity keys),
-// and each run of equal keys put in ascending value order.
-cudaError_t gs_launch_ranges_dev(const uint64_t *keys, uint32_t *values, int64_t n_capacity,
-                                 const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
-                                 uint32_t *d_err, cudaStream_t s);
+
 
 
 
@@ -447,21 +443,19 @@ cudaError_t gs_launch_project_bwd_batch(const gs_gaussians &g, const ViewDesc *v
 cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   const float *d_rec, const gs_grads &out, cudaStream_t s);
 
-// Batched front end: projection of every (view, Gaussian) pair into compact
-// records (slot j: record, meta = (view, Gaussian index)), then emission of
-// the (global tile, depth) keys whose values are compact slots; digit
-// histograms and bucket offsets as in the single-view front end.
-// counts as in gs_launch_project_bin; counts[3] = compact records used.
-size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity);
+// Batched front end, depth first as gs_launch_project_bin: projection of
+// every (view, Gaussian) pair into compact records (slot j: record, meta =
+// (view, Gaussian index)), the list of slots gathered into (view, index)
+// order and sorted by depth, then emission of 32-bit global tile ids (the
+// view's first tile + tile) whose values are compact slots, with the tile
+// sort's histograms + bucket offsets in sc (digit0 = 0). counts as in
+// gs_launch_project_bin, with [1] = records used.
+size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity, int64_t n, int n_views);
 cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
                                         gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
-                                        int lp_dtype, uint2 *meta, int64_t rec_capacity, uint64_t *keys,
+                                        int lp_dtype, uint2 *meta, int64_t rec_capacity, uint32_t *keys,
                                         uint32_t *values, int64_t key_capacity, unsigned long long *counts,
                                         void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s);
-// Ranges over global tiles with the tie order taken from meta[value].y.
-cudaError_t gs_launch_ranges_batch(const uint64_t *keys, uint32_t *values, const uint2 *meta, int64_t n_capacity,
-                                   const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
-                                   uint32_t *d_err, cudaStream_t s);
 // Persistent blend over a queue of global tiles (largest lists first).
 cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                   const ViewDesc *views_dev, int n_views, int tile_w, int tile_h, int depth,

@@ -271,6 +271,58 @@ __device__ __forceinline__ uint2 pack_rect(const Projected &pr) {
                     : make_uint2(0u, 0u);
 }
 
+// The last block of a list-building projection: the depth sort's bucket
+// offsets, and the places of the n_seg list segments (one per projection
+// block, in index order); counts[3] = the list's length, or 0 when it
+// exceeds list_cap (nothing is then sorted).
+__device__ void list_tail(const GsSortScratch &dsc, const uint2 *seg, uint32_t *seg_dst, int64_t n_seg,
+                          const unsigned long long *packed, unsigned long long *counts, int64_t list_cap,
+                          uint32_t *s_tmp) {
+    const int tid = threadIdx.x;
+    __threadfence();
+    for (int d = 0; d < kDepthPasses; ++d) {
+        const uint32_t c = __ldcg(&dsc.hist[d * 256 + tid]);
+        dsc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
+    }
+    // Segments in order, 4096 per round: thread tid takes 16 consecutive
+    // table entries (eight 16-byte loads in flight).
+    uint32_t carry = 0;
+    for (int64_t r0 = 0; r0 < n_seg; r0 += 256 * 16) {
+        const int64_t b0 = r0 + (int64_t)tid * 16;
+        uint32_t cnt[16];
+        if (b0 + 16 <= n_seg) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(seg + b0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint4 x = __ldcg(q + k);
+                cnt[2 * k] = x.y;
+                cnt[2 * k + 1] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) cnt[k] = b0 + k < n_seg ? __ldcg(&seg[b0 + k].y) : 0u;
+        }
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sum += cnt[k];
+        const uint32_t ex = block_exclusive_scan_256(sum, s_tmp);
+        uint32_t pre = carry + ex;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (b0 + k < n_seg) seg_dst[b0 + k] = pre;
+            pre += cnt[k];
+        }
+        if (tid == 255) s_tmp[0] = ex + sum;  // the round's total (s_tmp is free again)
+        __syncthreads();
+        carry += s_tmp[0];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const unsigned long long nl = __ldcg(packed) >> 33;
+        counts[3] = (int64_t)nl <= list_cap ? nl : 0ull;
+    }
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
     __shared__ uint32_t s_t[8], s_v[8];
@@ -349,57 +401,20 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
     __syncthreads();
     if (!s_last) return;
     // Last block: every block's counts and list entries are in.
-    __threadfence();
-    for (int d = 0; d < kDepthPasses; ++d) {
-        const uint32_t c = __ldcg(&A.dsc.hist[d * 256 + tid]);
-        A.dsc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
-    }
-    // Segments in block (= index) order, 4096 blocks per round: thread tid
-    // takes 16 consecutive table entries (eight 16-byte loads in flight).
-    const int64_t nb = gridDim.x;
-    uint32_t carry = 0;
-    for (int64_t r0 = 0; r0 < nb; r0 += 256 * 16) {
-        const int64_t b0 = r0 + (int64_t)tid * 16;
-        uint32_t cnt[16];
-        if (b0 + 16 <= nb) {
-            const uint4 *q = reinterpret_cast<const uint4 *>(A.seg + b0);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint4 x = __ldcg(q + k);
-                cnt[2 * k] = x.y;
-                cnt[2 * k + 1] = x.w;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) cnt[k] = b0 + k < nb ? __ldcg(&A.seg[b0 + k].y) : 0u;
-        }
-        uint32_t sum = 0;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) sum += cnt[k];
-        const uint32_t ex = block_exclusive_scan_256(sum, s_tmp);
-        uint32_t pre = carry + ex;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (b0 + k < nb) A.seg_dst[b0 + k] = pre;
-            pre += cnt[k];
-        }
-        if (tid == 255) s_tmp[0] = ex + sum;  // the round's total (s_tmp is free again)
-        __syncthreads();
-        carry += s_tmp[0];
-        __syncthreads();
-    }
-    if (tid == 0) A.counts[3] = __ldcg(A.packed) >> 33;
+    list_tail(A.dsc, A.seg, A.seg_dst, gridDim.x, A.packed, A.counts, A.P.n, s_tmp);
 }
 
 // Warp w of block b copies list segment 8 b + w (the visible Gaussians of
-// one projection block, in index order) to its place in index order.
+// one projection block, in index order) to its place in index order
+// (segments of a batch are in (view, block) order).
 __global__ void __launch_bounds__(256) list_gather_kernel(const uint2 *__restrict__ seg,
                                                          const uint32_t *__restrict__ seg_dst, int64_t n_seg,
+                                                         const unsigned long long *count,
                                                          const uint64_t *__restrict__ lkeys,
                                                          const uint32_t *__restrict__ lvals, uint64_t *okeys,
                                                          uint32_t *ovals) {
     const int64_t b = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (b >= n_seg) return;
+    if (b >= n_seg || *count == 0ull) return;  // nothing listed, or more than the list holds
     const uint2 sg = seg[b];
     const uint32_t dst = seg_dst[b];
     for (uint32_t k = threadIdx.x & 31; k < sg.y; k += 32) {
@@ -584,10 +599,13 @@ __global__ void __launch_bounds__(256) entry_scan_kernel(const EntryScanArgs A) 
 struct EmitArgs {
     const float4 *records;
     const unsigned long long *packed;
-    const uint32_t *list_idx;     // Gaussian index of entry j (depth order)
+    const uint32_t *list_idx;     // record of entry j (depth order): Gaussian index, or compact slot
     const uint32_t *list_off;     // first key slot of entry j (ascending)
     const uint32_t *block_entry;
-    GsGrid grid;
+    GsGrid grid;                  // single view
+    const uint2 *meta;            // batch: (view, Gaussian) of a compact slot
+    const ViewDesc *views;        // batch: grids and first global tiles
+    int64_t list_capacity;        // entries the list holds
     void *keys;                   // tile ids (KT)
     uint32_t *values;
     int64_t capacity;
@@ -604,7 +622,7 @@ struct EmitArgs {
 // Keys and values are staged in shared memory and written with 16-byte
 // stores (the key buffers are 256-byte aligned and blocks start at multiples
 // of 2048 slots).
-template <typename KT>
+template <typename KT, bool BATCH>
 __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
     __shared__ uint32_t s_hist[kMaxTilePasses * 256];
     __shared__ uint32_t s_off[kKeyBlock + 2], s_idx[kKeyBlock + 2];
@@ -621,7 +639,7 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
     const int64_t K = (int64_t)(packed & kKeyMask);
     const int64_t nv = (int64_t)(packed >> 33);
     const int64_t k0 = (int64_t)blockIdx.x * kKeyBlock;
-    const bool active = k0 < K && K <= E.capacity;
+    const bool active = k0 < K && K <= E.capacity && nv <= E.list_capacity;
     if (tid == 0 && active) {
         const int64_t j0 = E.block_entry[blockIdx.x];  // entry covering slot k0
         s_j0 = (int)j0;
@@ -643,7 +661,7 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
             if ((int64_t)s_off[mid] <= kb) lo = mid; else hi = mid - 1;
         }
         int e = -1;
-        uint32_t g = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0;
+        uint32_t g = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0, tiles_x = (uint32_t)G.tiles_x, tbase = 0;
         uint32_t run_digit[kMaxTilePasses], run_count[kMaxTilePasses];
         uint32_t tk[kKeysPerThread], tv[kKeysPerThread];
         for (int d = 0; d < kMaxTilePasses; ++d) { run_digit[d] = 0xffffffffu; run_count[d] = 0; }
@@ -661,8 +679,15 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
                 ebase = s_off[e];
                 const float4 r0 = E.records[3 * (size_t)g];
                 const float4 r2 = E.records[3 * (size_t)g + 2];
-                const Rect R = tile_rect(r0.x, r0.y, __float_as_int(r2.z), G.tile_w, G.tile_h, G.tiles_x,
-                                         G.tiles_y);
+                GsGrid vg = G;
+                if (BATCH) {
+                    const ViewDesc &V = E.views[E.meta[g].x];
+                    vg = V.grid;
+                    tbase = V.tile_base;
+                    tiles_x = (uint32_t)vg.tiles_x;
+                }
+                const Rect R = tile_rect(r0.x, r0.y, __float_as_int(r2.z), vg.tile_w, vg.tile_h, vg.tiles_x,
+                                         vg.tiles_y);
                 w = (uint32_t)(R.x1 - R.x0);
                 x0 = (uint32_t)R.x0;
                 y0 = (uint32_t)R.y0;
@@ -670,7 +695,7 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
             }
             const uint32_t m = (uint32_t)(k - ebase);
             const uint32_t qy = m / w, rx = m - qy * w;
-            const uint32_t tile = (y0 + qy) * (uint32_t)G.tiles_x + x0 + rx;
+            const uint32_t tile = tbase + (y0 + qy) * tiles_x + x0 + rx;
             tk[q] = tile;
             tv[q] = g;
             for (int d = 0; d < passes; ++d) {
@@ -731,45 +756,52 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
     if (tid == 0) {
         E.counts[0] = (unsigned long long)K;
         E.counts[1] = (unsigned long long)nv;
-        const bool fits = K <= E.capacity;
+        const bool fits = K <= E.capacity && nv <= E.list_capacity;
         if (!fits) atomicOr(E.d_err, kErrCapacity);
         E.counts[2] = fits ? (unsigned long long)K : 0ull;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Batched front end (many views of one scene). Block (b, v) projects
-// Gaussians [256 b, 256 b + 256) for view v and reserves, per block, compact
-// record slots and key slots with the packed counter; records go to compact
-// slot j with meta[j] = (view, Gaussian index). Emission then follows the
-// single-view kernel with the view's tile grid and a global tile id.
+// Batched front end (many views of one scene), depth first as a single view:
+// block (b, v) projects Gaussians [256 b, 256 b + 256) for view v and
+// reserves compact record slots with the packed counter; slot j gets the
+// record, meta[j] = (view, Gaussian index) and list entry j (tiles << 32 |
+// depth bits, j). The list segments, placed in (view, block) order, give the
+// list in (view, index) order; the stable depth sort, the entry scan and the
+// emission follow, the keys being global tile ids (view's first tile + tile),
+// so every global tile's list ends in (depth bits, index) order.
 // ---------------------------------------------------------------------------
-struct ReserveBatchArgs {
-    ProjectArgs P;               // scene arrays (cam / grid unused)
+struct ListBatchArgs {
+    ProjectArgs P;               // scene arrays (cam / grid unused; records compact)
     const ViewDesc *views;
-    unsigned long long *packed;  // visible << 33 | keys
-    uint32_t *list_off;          // per compact slot: first key slot
-    uint2 *meta;                 // per compact slot: (view, Gaussian index)
     float4 *lp_geo;
     uint2 *lp_oq;
     uint32_t *lp_gb;
     int lp_dtype;
+    uint2 *meta;
     int64_t rec_capacity;
-    uint32_t *hist;
-    uint32_t *block_entry;
-    int64_t n_key_blocks;
+    unsigned long long *packed;  // records << 33 | keys
+    uint2 *seg;                  // per (view, block): (first slot, records)
+    uint32_t *seg_dst;
+    uint64_t *lkeys;
+    uint32_t *lvals;
+    GsSortScratch dsc;
+    unsigned long long *counts;
     uint32_t *d_err;
 };
 
 template <int DEG>
-__global__ void __launch_bounds__(256) project_reserve_batch_kernel(const ReserveBatchArgs A) {
+__global__ void __launch_bounds__(256) project_list_batch_kernel(const ListBatchArgs A) {
     __shared__ uint32_t s_t[8], s_v[8];
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_hist[4 * 256];
+    __shared__ uint32_t s_hist[kDepthPasses * 256];
+    __shared__ uint32_t s_tmp[8];
+    __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int view = blockIdx.y;
     const ViewDesc &V = A.views[view];
-    for (int k = tid; k < 4 * 256; k += 256) s_hist[k] = 0;
+    for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
     const int64_t i = (int64_t)blockIdx.x * 256 + tid;
     Projected pr;
     pr.tiles = 0;
@@ -783,19 +815,20 @@ __global__ void __launch_bounds__(256) project_reserve_batch_kernel(const Reserv
     }
     if (lane == 31) { s_t[warp] = it; s_v[warp] = iv; }
     __syncthreads();
-    uint32_t pt = 0, pv = 0, bt = 0, bv = 0;
+    uint32_t pv = 0, bt = 0, bv = 0;
     for (int w = 0; w < 8; ++w) {
-        if (w < warp) { pt += s_t[w]; pv += s_v[w]; }
+        if (w < warp) pv += s_v[w];
         bt += s_t[w];
         bv += s_v[w];
     }
-    if (tid == 0) s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) : 0ull;
+    if (tid == 0) {
+        s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) >> 33 : 0ull;
+        A.seg[(int64_t)view * gridDim.x + blockIdx.x] = make_uint2((uint32_t)s_base, bv);
+    }
     __syncthreads();
     if (v) {
-        const unsigned long long base = s_base;
-        const uint64_t j = (base >> 33) + pv + iv - 1;
+        const uint64_t j = s_base + pv + iv - 1;
         if ((int64_t)j < A.rec_capacity) {
-            const uint64_t off = (base & kKeyMask) + pt + it - t;
             float4 *out = A.P.records + 3 * j;
             out[0] = pr.r0;
             out[1] = pr.r1;
@@ -806,134 +839,26 @@ __global__ void __launch_bounds__(256) project_reserve_batch_kernel(const Reserv
                 A.lp_gb[j] = pack2(pr.r1.w, pr.r2.x, A.lp_dtype);
             }
             A.meta[j] = make_uint2((uint32_t)view, (uint32_t)i);
-            A.list_off[j] = (uint32_t)off;
-            const int64_t b1 = min((int64_t)((off + t - 1) >> kKeyBlockLog2), A.n_key_blocks - 1);
-            for (int64_t b = (int64_t)((off + kKeyBlock - 1) >> kKeyBlockLog2); b <= b1; ++b)
-                A.block_entry[b] = (uint32_t)j;
             const uint32_t dbits = __float_as_uint(pr.r2.y);
-            for (int d = 0; d < 4; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], t);
+            A.lkeys[j] = ((uint64_t)t << 32) | dbits;
+            A.lvals[j] = (uint32_t)j;
+            for (int d = 0; d < kDepthPasses; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
         } else {
             atomicOr(A.d_err, kErrCapacity);
         }
     }
     __syncthreads();
     if (bv)
-        for (int k = tid; k < 4 * 256; k += 256)
-            if (s_hist[k]) atomicAdd(&A.hist[k], s_hist[k]);
-}
-
-struct EmitBatchArgs {
-    const float4 *records;       // compact FP32 records (always written)
-    const unsigned long long *packed;
-    const uint32_t *list_off;
-    const uint2 *meta;
-    const uint32_t *block_entry;
-    const ViewDesc *views;
-    int64_t rec_capacity;
-    uint64_t *keys;
-    uint32_t *values;
-    int64_t capacity;
-    unsigned long long *counts;
-    GsSortScratch sc;
-    uint32_t *d_err;
-};
-
-__global__ void __launch_bounds__(256) emit_keys_batch_kernel(const EmitBatchArgs E) {
-    __shared__ uint32_t s_hist[kMaxPasses * 256];
-    __shared__ uint32_t s_off[kKeyBlock + 2];
-    __shared__ uint32_t s_tmp[8];
-    __shared__ int s_j0, s_cnt;
-    __shared__ bool s_last;
-    const int tid = threadIdx.x;
-    const int passes = E.sc.passes;
-    for (int k = tid; k < kMaxPasses * 256; k += 256) s_hist[k] = 0;
-    const unsigned long long packed = *E.packed;
-    const int64_t K = (int64_t)(packed & kKeyMask);
-    const int64_t nv = (int64_t)(packed >> 33);
-    const int64_t k0 = (int64_t)blockIdx.x * kKeyBlock;
-    const bool active = k0 < K && K <= E.capacity && nv <= E.rec_capacity;
-    if (tid == 0 && active) {
-        const int64_t j0 = E.block_entry[blockIdx.x];
-        s_j0 = (int)j0;
-        s_cnt = (int)((nv - j0) < kKeyBlock + 2 ? (nv - j0) : kKeyBlock + 2);
+        for (int k = tid; k < kDepthPasses * 256; k += 256)
+            if (s_hist[k]) atomicAdd(&A.dsc.hist[k], s_hist[k]);
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x * gridDim.y - 1;
     }
-    __syncthreads();
-    if (active)
-        for (int q = tid; q < s_cnt; q += 256) s_off[q] = E.list_off[s_j0 + q];
-    __syncthreads();
-    const int64_t kb = k0 + (int64_t)tid * kKeysPerThread;
-    if (active && kb < K) {
-        int lo = 0, hi = s_cnt - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((int64_t)s_off[mid] <= kb) lo = mid; else hi = mid - 1;
-        }
-        int e = -1;
-        uint32_t j = 0, dbits = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0, tiles_x = 1, tbase = 0;
-        uint32_t run_digit[kMaxPasses], run_count[kMaxPasses];
-        for (int d = 0; d < kMaxPasses; ++d) { run_digit[d] = 0xffffffffu; run_count[d] = 0; }
-        for (int q = 0; q < kKeysPerThread; ++q) {
-            const int64_t k = kb + q;
-            if (k >= K) break;
-            if (e < 0 || (uint64_t)k >= eend) {
-                if (e >= 0) ++lo;
-                while (lo + 1 < s_cnt && (int64_t)s_off[lo + 1] <= k) ++lo;
-                e = lo;
-                j = (uint32_t)(s_j0 + e);
-                ebase = s_off[e];
-                const ViewDesc &V = E.views[E.meta[j].x];
-                const float4 r0 = E.records[3 * (size_t)j];
-                const float4 r2 = E.records[3 * (size_t)j + 2];
-                const Rect R = tile_rect(r0.x, r0.y, __float_as_int(r2.z), V.grid.tile_w, V.grid.tile_h,
-                                         V.grid.tiles_x, V.grid.tiles_y);
-                w = (uint32_t)(R.x1 - R.x0);
-                x0 = (uint32_t)R.x0;
-                y0 = (uint32_t)R.y0;
-                tiles_x = (uint32_t)V.grid.tiles_x;
-                tbase = V.tile_base;
-                eend = ebase + w * (uint32_t)(R.y1 - R.y0);
-                dbits = __float_as_uint(r2.y);
-            }
-            const uint32_t m = (uint32_t)(k - ebase);
-            const uint32_t qy = m / w, rx = m - qy * w;
-            const uint32_t tile = tbase + (y0 + qy) * tiles_x + x0 + rx;
-            E.keys[k] = ((uint64_t)tile << 32) | dbits;
-            E.values[k] = j;
-            for (int d = 4; d < passes; ++d) {
-                const uint32_t dg = (tile >> (8 * (d - 4))) & 255u;
-                if (dg != run_digit[d]) {
-                    if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
-                    run_digit[d] = dg;
-                    run_count[d] = 0;
-                }
-                ++run_count[d];
-            }
-        }
-        for (int d = 4; d < passes; ++d)
-            if (run_count[d]) atomicAdd(&s_hist[d * 256 + run_digit[d]], run_count[d]);
-    }
-    __syncthreads();
-    if (active)
-        for (int q = tid + 4 * 256; q < passes * 256; q += 256)
-            if (s_hist[q]) atomicAdd(&E.sc.hist[q], s_hist[q]);
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(E.sc.ticket, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
-    for (int d = 0; d < passes; ++d) {
-        const uint32_t c = __ldcg(&E.sc.hist[d * 256 + tid]);
-        E.sc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
-    }
-    if (tid == 0) {
-        E.counts[0] = (unsigned long long)K;
-        E.counts[1] = (unsigned long long)nv;
-        E.counts[3] = (unsigned long long)nv;
-        const bool fits = K <= E.capacity && nv <= E.rec_capacity;
-        if (!fits) atomicOr(E.d_err, kErrCapacity);
-        E.counts[2] = fits ? (unsigned long long)K : 0ull;
-    }
+    list_tail(A.dsc, A.seg, A.seg_dst, (int64_t)gridDim.x * gridDim.y, A.packed, A.counts, A.rec_capacity, s_tmp);
 }
 
 }  // namespace
@@ -948,9 +873,11 @@ struct FrontLayout {
     size_t dsort, scan_status, zero, seg, seg_dst, lkeys, lvals, akeys, avals, off, block_entry, total;
 };
 
-FrontLayout front_layout(int64_t n, int64_t capacity) {
+// n_list: entries the list holds; n_seg: projection blocks (list segments).
+FrontLayout front_layout(int64_t n_list, int64_t capacity, int64_t n_seg) {
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const int64_t nn = n > 0 ? n : 1;
+    const int64_t nn = n_list > 0 ? n_list : 1;
+    const int64_t ns = n_seg > 0 ? n_seg : 1;
     FrontLayout L;
     size_t o = 256;
     L.dsort = o;
@@ -959,9 +886,9 @@ FrontLayout front_layout(int64_t n, int64_t capacity) {
     o += al((size_t)((nn + kEntryTile - 1) / kEntryTile + 1) * 8);
     L.zero = o;
     L.seg = o;
-    o += al((size_t)((nn + 255) / 256) * 8);
+    o += al((size_t)ns * 8);
     L.seg_dst = o;
-    o += al((size_t)((nn + 255) / 256) * 4);
+    o += al((size_t)ns * 4);
     L.lkeys = o;
     o += al((size_t)nn * 8);
     L.lvals = o;
@@ -978,9 +905,68 @@ FrontLayout front_layout(int64_t n, int64_t capacity) {
     return L;
 }
 
+// After the list-building projection: gather into index order (into the
+// alternate buffers), depth sort (count counts[3]; the even number of passes
+// leaves the list there), entry scan and key emission. E carries the
+// record, grid and output fields; the list fields are filled here.
+cudaError_t launch_list_stages(const FrontLayout &L, char *base, int64_t n_list, int64_t n_seg,
+                               const GsSortScratch &dsc, EmitArgs E, int key_bytes, bool batch,
+                               unsigned long long *counts, uint32_t *d_err, cudaStream_t s, const cudaEvent_t *marks) {
+    const uint2 *seg = reinterpret_cast<const uint2 *>(base + L.seg);
+    const uint32_t *seg_dst = reinterpret_cast<const uint32_t *>(base + L.seg_dst);
+    uint64_t *lkeys = reinterpret_cast<uint64_t *>(base + L.lkeys);
+    uint32_t *lvals = reinterpret_cast<uint32_t *>(base + L.lvals);
+    uint64_t *gkeys = reinterpret_cast<uint64_t *>(base + L.akeys);
+    uint32_t *gvals = reinterpret_cast<uint32_t *>(base + L.avals);
+    list_gather_kernel<<<(unsigned)((n_seg + 7) / 8), 256, 0, s>>>(seg, seg_dst, n_seg, counts + 3, lkeys, lvals,
+                                                                  gkeys, gvals);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bool in_alt = false;
+    e = gs_launch_sort_passes(gkeys, gvals, lkeys, lvals, n_list, counts + 3, dsc, d_err, &in_alt, s);
+    if (e != cudaSuccess) return e;
+    if (marks && marks[1]) cudaEventRecord(marks[1], s);
+    EntryScanArgs S;
+    S.lkeys = in_alt ? lkeys : gkeys;
+    S.count = counts + 3;
+    S.off = reinterpret_cast<uint32_t *>(base + L.off);
+    S.block_entry = reinterpret_cast<uint32_t *>(base + L.block_entry);
+    S.n_key_blocks = (E.capacity + kKeyBlock - 1) / kKeyBlock;
+    S.counter = reinterpret_cast<uint32_t *>(base + 8);
+    S.status = reinterpret_cast<unsigned long long *>(base + L.scan_status);
+    S.d_err = d_err;
+    gs_carveout(entry_scan_kernel);
+    entry_scan_kernel<<<(unsigned)((n_list + kEntryTile - 1) / kEntryTile), 256, 0, s>>>(S);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (marks && marks[2]) cudaEventRecord(marks[2], s);
+    E.packed = reinterpret_cast<const unsigned long long *>(base);
+    E.list_idx = in_alt ? lvals : gvals;
+    E.list_off = S.off;
+    E.block_entry = S.block_entry;
+    E.list_capacity = n_list;
+    E.counts = counts;
+    E.d_err = d_err;
+    // One block per 2048 key slots of the capacity (blocks past K only take
+    // their ticket).
+    const unsigned eblocks = (unsigned)((E.capacity + kKeyBlock - 1) / kKeyBlock);
+    if (batch) {
+        emit_keys_kernel<uint32_t, true><<<eblocks, 256, 0, s>>>(E);
+    } else if (key_bytes == 2) {
+        gs_carveout(emit_keys_kernel<uint16_t, false>);
+        emit_keys_kernel<uint16_t, false><<<eblocks, 256, 0, s>>>(E);
+    } else {
+        gs_carveout(emit_keys_kernel<uint32_t, false>);
+        emit_keys_kernel<uint32_t, false><<<eblocks, 256, 0, s>>>(E);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-size_t gs_fused_scratch_bytes(int64_t n, int64_t capacity) { return front_layout(n, capacity).total; }
+size_t gs_fused_scratch_bytes(int64_t n, int64_t capacity) {
+    return front_layout(n, capacity, (n + 255) / 256).total;
+}
 
 size_t gs_key_block_bytes(int64_t capacity) {
     return ((size_t)(capacity + kKeyBlock - 1) / kKeyBlock + 1) * 4;
@@ -999,7 +985,8 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     if (key_bytes != 2 && key_bytes != 4) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const FrontLayout L = front_layout(g.n, capacity);
+    const int64_t blocks = (g.n + 255) / 256;
+    const FrontLayout L = front_layout(g.n, capacity, blocks);
     char *base = static_cast<char *>(scan_scratch);
     e = cudaMemsetAsync(base, 0, L.zero, s);
     if (e != cudaSuccess || g.n == 0) return e;
@@ -1022,60 +1009,26 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     A.prect = prect;
     A.prev_rect = prect ? prev_rect : nullptr;
     A.moved = moved;
-    const unsigned blocks = (unsigned)((g.n + 255) / 256);
     switch (g.sh_degree) {
-        case 0: project_list_kernel<0><<<blocks, 256, 0, s>>>(A); break;
-        case 1: project_list_kernel<1><<<blocks, 256, 0, s>>>(A); break;
-        case 2: project_list_kernel<2><<<blocks, 256, 0, s>>>(A); break;
-        default: gs_carveout(project_list_kernel<3>); project_list_kernel<3><<<blocks, 256, 0, s>>>(A); break;
+        case 0: project_list_kernel<0><<<(unsigned)blocks, 256, 0, s>>>(A); break;
+        case 1: project_list_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(A); break;
+        case 2: project_list_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(A); break;
+        default:
+            gs_carveout(project_list_kernel<3>);
+            project_list_kernel<3><<<(unsigned)blocks, 256, 0, s>>>(A);
+            break;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (marks && marks[0]) cudaEventRecord(marks[0], s);
-    // The list in index order (in the alternate buffers), then its depth sort
-    // (count counts[3]; an even number of passes leaves it there).
-    uint64_t *gkeys = reinterpret_cast<uint64_t *>(base + L.akeys);
-    uint32_t *gvals = reinterpret_cast<uint32_t *>(base + L.avals);
-    list_gather_kernel<<<(blocks + 7) / 8, 256, 0, s>>>(A.seg, A.seg_dst, (int64_t)blocks, A.lkeys, A.lvals, gkeys,
-                                                         gvals);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    uint32_t *off = reinterpret_cast<uint32_t *>(base + L.off);
-    uint32_t *block_entry = reinterpret_cast<uint32_t *>(base + L.block_entry);
-    const int64_t n_key_blocks = (capacity + kKeyBlock - 1) / kKeyBlock;
-    bool in_alt = false;
-    e = gs_launch_sort_passes(gkeys, gvals, A.lkeys, A.lvals, g.n, counts + 3, A.dsc, d_err, &in_alt, s);
-    if (e != cudaSuccess) return e;
-    if (marks && marks[1]) cudaEventRecord(marks[1], s);
-    const uint64_t *skeys = in_alt ? A.lkeys : gkeys;
-    const uint32_t *svals = in_alt ? A.lvals : gvals;
-    EntryScanArgs S;
-    S.lkeys = skeys;
-    S.count = counts + 3;
-    S.off = off;
-    S.block_entry = block_entry;
-    S.n_key_blocks = n_key_blocks;
-    S.counter = reinterpret_cast<uint32_t *>(base + 8);
-    S.status = reinterpret_cast<unsigned long long *>(base + L.scan_status);
-    S.d_err = d_err;
-    gs_carveout(entry_scan_kernel);
-    entry_scan_kernel<<<(unsigned)((g.n + kEntryTile - 1) / kEntryTile), 256, 0, s>>>(S);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (marks && marks[2]) cudaEventRecord(marks[2], s);
-    EmitArgs E{reinterpret_cast<const float4 *>(records), A.packed, svals, S.off, S.block_entry, grid, keys,
-               values, capacity, counts, sc, d_err};
-    // One block per 2048 key slots of the capacity (blocks past K only take
-    // their ticket).
-    const unsigned eblocks = (unsigned)((capacity + kKeyBlock - 1) / kKeyBlock);
-    if (key_bytes == 2) {
-        gs_carveout(emit_keys_kernel<uint16_t>);
-        emit_keys_kernel<uint16_t><<<eblocks, 256, 0, s>>>(E);
-    } else {
-        gs_carveout(emit_keys_kernel<uint32_t>);
-        emit_keys_kernel<uint32_t><<<eblocks, 256, 0, s>>>(E);
-    }
-    return cudaGetLastError();
+    EmitArgs E{};
+    E.records = reinterpret_cast<const float4 *>(records);
+    E.grid = grid;
+    E.keys = keys;
+    E.values = values;
+    E.capacity = capacity;
+    E.sc = sc;
+    return launch_list_stages(L, base, g.n, blocks, A.dsc, E, key_bytes, false, counts, d_err, s, marks);
 }
 
 cudaError_t gs_launch_project_temporal(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
@@ -1450,50 +1403,58 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
     }
 }
 
-size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity) {
-    // packed counter, list_off per compact slot, key-block entry table
-    return 256 + ((size_t)rec_capacity * 4 + 255) / 256 * 256 + gs_key_block_bytes(key_capacity);
+size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity, int64_t n, int n_views) {
+    return front_layout(rec_capacity, key_capacity, (n + 255) / 256 * n_views).total;
 }
 
 cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
                                         gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
-                                        int lp_dtype, uint2 *meta, int64_t rec_capacity, uint64_t *keys,
+                                        int lp_dtype, uint2 *meta, int64_t rec_capacity, uint32_t *keys,
                                         uint32_t *values, int64_t key_capacity, unsigned long long *counts,
                                         void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    const int64_t nb = (g.n + 255) / 256, n_seg = nb * n_views;
+    const FrontLayout L = front_layout(rec_capacity, key_capacity, n_seg);
     char *base = static_cast<char *>(scratch);
-    e = cudaMemsetAsync(base, 0, 256, s);
+    e = cudaMemsetAsync(base, 0, L.zero, s);
     if (e != cudaSuccess || g.n == 0 || n_views == 0) return e;
-    ReserveBatchArgs A;
+    ListBatchArgs A;
     A.P = ProjectArgs{g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.n, GsCameraDev{}, GsGrid{},
                       reinterpret_cast<float4 *>(records), nullptr,
                       reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
                       reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
     A.views = views_dev;
-    A.packed = reinterpret_cast<unsigned long long *>(base);
-    A.list_off = reinterpret_cast<uint32_t *>(base + 256);
-    A.meta = meta;
     A.lp_geo = lp_dtype == GS_RECORD_F32 ? nullptr : lp_geo;
     A.lp_oq = lp_oq;
     A.lp_gb = lp_gb;
     A.lp_dtype = lp_dtype;
+    A.meta = meta;
     A.rec_capacity = rec_capacity;
-    A.hist = sc.hist;
-    A.block_entry = reinterpret_cast<uint32_t *>(base + 256 + ((size_t)rec_capacity * 4 + 255) / 256 * 256);
-    A.n_key_blocks = (key_capacity + kKeyBlock - 1) / kKeyBlock;
+    A.packed = reinterpret_cast<unsigned long long *>(base);
+    A.seg = reinterpret_cast<uint2 *>(base + L.seg);
+    A.seg_dst = reinterpret_cast<uint32_t *>(base + L.seg_dst);
+    A.lkeys = reinterpret_cast<uint64_t *>(base + L.lkeys);
+    A.lvals = reinterpret_cast<uint32_t *>(base + L.lvals);
+    A.dsc = gs_sort_carve_digits(base + L.dsort, rec_capacity, 0, kDepthPasses, kDepthItems);
+    A.counts = counts;
     A.d_err = d_err;
-    const dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)n_views);
+    const dim3 grid((unsigned)nb, (unsigned)n_views);
     switch (g.sh_degree) {
-        case 0: project_reserve_batch_kernel<0><<<grid, 256, 0, s>>>(A); break;
-        case 1: project_reserve_batch_kernel<1><<<grid, 256, 0, s>>>(A); break;
-        case 2: project_reserve_batch_kernel<2><<<grid, 256, 0, s>>>(A); break;
-        default: project_reserve_batch_kernel<3><<<grid, 256, 0, s>>>(A); break;
+        case 0: project_list_batch_kernel<0><<<grid, 256, 0, s>>>(A); break;
+        case 1: project_list_batch_kernel<1><<<grid, 256, 0, s>>>(A); break;
+        case 2: project_list_batch_kernel<2><<<grid, 256, 0, s>>>(A); break;
+        default: project_list_batch_kernel<3><<<grid, 256, 0, s>>>(A); break;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    EmitBatchArgs E{reinterpret_cast<const float4 *>(records), A.packed, A.list_off, meta, A.block_entry,
-                    views_dev, rec_capacity, keys, values, key_capacity, counts, sc, d_err};
-    emit_keys_batch_kernel<<<(unsigned)((key_capacity + kKeyBlock - 1) / kKeyBlock), 256, 0, s>>>(E);
-    return cudaGetLastError();
+    EmitArgs E{};
+    E.records = reinterpret_cast<const float4 *>(records);
+    E.meta = meta;
+    E.views = views_dev;
+    E.keys = keys;
+    E.values = values;
+    E.capacity = key_capacity;
+    E.sc = sc;
+    return launch_list_stages(L, base, rec_capacity, n_seg, A.dsc, E, 4, true, counts, d_err, s, nullptr);
 }
