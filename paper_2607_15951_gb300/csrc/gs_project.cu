@@ -101,9 +101,13 @@ struct Projected {
     float4 r0, r1, r2;  // gs_record words
     Rect rect;
     uint32_t tiles;     // 0 when culled
+    float3 dir;         // unit view direction (for a deferred colour)
 };
 
-template <int DEG>
+// COLOUR = false leaves the colour words (r1.z, r1.w, r2.x) unset and
+// returns the view direction instead, for a colour evaluated later by
+// finish_colours.
+template <int DEG, bool COLOUR = true>
 __device__ __forceinline__ Projected project_one(const ProjectArgs &P, const GsCameraDev &K, const GsGrid &G,
                                                  int64_t i) {
     Projected out;
@@ -181,7 +185,9 @@ __device__ __forceinline__ Projected project_one(const ProjectArgs &P, const GsC
     float dx = mx - K.C[0], dy = my - K.C[1], dz = mz - K.C[2];
     const float dinv = rsqrtf(dx * dx + dy * dy + dz * dz);
     dx *= dinv; dy *= dinv; dz *= dinv;
-    const float3 rgb = sh_colour<DEG>(P.sh + (size_t)i * (DEG + 1) * (DEG + 1) * 3, P.sh_vec, dx, dy, dz);
+    const float3 rgb = COLOUR ? sh_colour<DEG>(P.sh + (size_t)i * (DEG + 1) * (DEG + 1) * 3, P.sh_vec, dx, dy, dz)
+                              : make_float3(0.f, 0.f, 0.f);
+    out.dir = make_float3(dx, dy, dz);
     const float opacity = 1.f / (1.f + expf(-logit));
 
     out.r0 = make_float4(u, v, c * idet, -b * idet);
@@ -190,6 +196,49 @@ __device__ __forceinline__ Projected project_one(const ProjectArgs &P, const GsC
     out.rect = R;
     out.tiles = ntiles;
     return out;
+}
+
+// Deferred colours of a block's visible Gaussians. The SH colour is the
+// costliest part of a projection and only the few visible Gaussians need it;
+// evaluated by their own threads it would hold a whole warp (and, through
+// the block's barriers, the block) for one lane. Instead each visible
+// Gaussian's record words are staged at its rank among the block's visible
+// ones, and after the block's last barrier the first threads evaluate the
+// colours of consecutive entries and write the colour-bearing words.
+struct ColourStage {
+    float4 r1[256], r2[256];  // record words 1 and 2 without the colour
+    float4 dir[256];          // view direction, Gaussian index (bits) in w
+    uint32_t slot[256];       // record slot (0xffffffff: not written)
+};
+
+__device__ __forceinline__ void stage_colour(ColourStage &S, int e, const Projected &pr, int64_t i, uint32_t slot) {
+    S.r1[e] = pr.r1;
+    S.r2[e] = pr.r2;
+    S.dir[e] = make_float4(pr.dir.x, pr.dir.y, pr.dir.z, __uint_as_float((uint32_t)i));
+    S.slot[e] = slot;
+}
+
+template <int DEG>
+__device__ __forceinline__ void finish_colours(const ColourStage &S, int n_vis, const ProjectArgs &P,
+                                               uint2 *lp_oq, uint32_t *lp_gb, int lp_dtype) {
+    for (int e = threadIdx.x; e < n_vis; e += blockDim.x) {
+        const uint32_t slot = S.slot[e];
+        if (slot == 0xffffffffu) continue;
+        const float4 d = S.dir[e];
+        const size_t i = __float_as_uint(d.w);
+        const float3 rgb = sh_colour<DEG>(P.sh + i * (DEG + 1) * (DEG + 1) * 3, P.sh_vec, d.x, d.y, d.z);
+        float4 r1 = S.r1[e], r2 = S.r2[e];
+        r1.z = rgb.x;
+        r1.w = rgb.y;
+        r2.x = rgb.z;
+        float4 *out = P.records + 3 * (size_t)slot;
+        out[1] = r1;
+        out[2] = r2;
+        if (lp_oq) {
+            lp_oq[slot] = make_uint2(__float_as_uint(r1.x), pack2(r1.y, r1.z, lp_dtype));
+            lp_gb[slot] = pack2(r1.w, r2.x, lp_dtype);
+        }
+    }
 }
 
 template <int DEG>
@@ -330,22 +379,16 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
     __shared__ uint32_t s_hist[kDepthPasses * 256];
     __shared__ uint32_t s_tmp[8];
     __shared__ bool s_last;
+    __shared__ ColourStage s_col;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
     const int64_t i = (int64_t)blockIdx.x * 256 + tid;
     Projected pr;
     pr.tiles = 0;
-    if (i < A.P.n) pr = project_one<DEG>(A.P, A.P.cam, A.P.grid, i);
+    if (i < A.P.n) pr = project_one<DEG, false>(A.P, A.P.cam, A.P.grid, i);
     if (pr.tiles) {
-        float4 *out = A.P.records + 3 * i;
-        out[0] = pr.r0;
-        out[1] = pr.r1;
-        out[2] = pr.r2;
-        if (A.lp_geo) {
-            A.lp_geo[i] = pr.r0;
-            A.lp_oq[i] = make_uint2(__float_as_uint(pr.r1.x), pack2(pr.r1.y, pr.r1.z, A.lp_dtype));
-            A.lp_gb[i] = pack2(pr.r1.w, pr.r2.x, A.lp_dtype);
-        }
+        A.P.records[3 * i] = pr.r0;
+        if (A.lp_geo) A.lp_geo[i] = pr.r0;
     }
     bool mv = false;
     if (A.prect && i < A.P.n) {
@@ -386,6 +429,7 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
         A.lkeys[j] = ((uint64_t)t << 32) | dbits;
         A.lvals[j] = (uint32_t)i;
         for (int d = 0; d < kDepthPasses; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
+        stage_colour(s_col, (int)(pv + iv - 1), pr, i, (uint32_t)i);
     }
     __syncthreads();
     if (bv)
@@ -399,6 +443,7 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
         s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
+    finish_colours<DEG>(s_col, (int)bv, A.P, A.lp_geo ? A.lp_oq : nullptr, A.lp_gb, A.lp_dtype);
     if (!s_last) return;
     // Last block: every block's counts and list entries are in.
     list_tail(A.dsc, A.seg, A.seg_dst, gridDim.x, A.packed, A.counts, A.P.n, s_tmp);
@@ -798,6 +843,7 @@ __global__ void __launch_bounds__(256) project_list_batch_kernel(const ListBatch
     __shared__ uint32_t s_hist[kDepthPasses * 256];
     __shared__ uint32_t s_tmp[8];
     __shared__ bool s_last;
+    __shared__ ColourStage s_col;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int view = blockIdx.y;
     const ViewDesc &V = A.views[view];
@@ -805,7 +851,7 @@ __global__ void __launch_bounds__(256) project_list_batch_kernel(const ListBatch
     const int64_t i = (int64_t)blockIdx.x * 256 + tid;
     Projected pr;
     pr.tiles = 0;
-    if (i < A.P.n) pr = project_one<DEG>(A.P, V.cam, V.grid, i);
+    if (i < A.P.n) pr = project_one<DEG, false>(A.P, V.cam, V.grid, i);
     const uint32_t t = pr.tiles, v = t != 0u;
     uint32_t it = t, iv = v;
     for (int o = 1; o < 32; o <<= 1) {
@@ -828,16 +874,10 @@ __global__ void __launch_bounds__(256) project_list_batch_kernel(const ListBatch
     __syncthreads();
     if (v) {
         const uint64_t j = s_base + pv + iv - 1;
-        if ((int64_t)j < A.rec_capacity) {
-            float4 *out = A.P.records + 3 * j;
-            out[0] = pr.r0;
-            out[1] = pr.r1;
-            out[2] = pr.r2;
-            if (A.lp_geo) {
-                A.lp_geo[j] = pr.r0;
-                A.lp_oq[j] = make_uint2(__float_as_uint(pr.r1.x), pack2(pr.r1.y, pr.r1.z, A.lp_dtype));
-                A.lp_gb[j] = pack2(pr.r1.w, pr.r2.x, A.lp_dtype);
-            }
+        const bool fits = (int64_t)j < A.rec_capacity;
+        if (fits) {
+            A.P.records[3 * j] = pr.r0;
+            if (A.lp_geo) A.lp_geo[j] = pr.r0;
             A.meta[j] = make_uint2((uint32_t)view, (uint32_t)i);
             const uint32_t dbits = __float_as_uint(pr.r2.y);
             A.lkeys[j] = ((uint64_t)t << 32) | dbits;
@@ -846,6 +886,7 @@ __global__ void __launch_bounds__(256) project_list_batch_kernel(const ListBatch
         } else {
             atomicOr(A.d_err, kErrCapacity);
         }
+        stage_colour(s_col, (int)(pv + iv - 1), pr, i, fits ? (uint32_t)j : 0xffffffffu);
     }
     __syncthreads();
     if (bv)
@@ -857,6 +898,7 @@ __global__ void __launch_bounds__(256) project_list_batch_kernel(const ListBatch
         s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
+    finish_colours<DEG>(s_col, (int)bv, A.P, A.lp_geo ? A.lp_oq : nullptr, A.lp_gb, A.lp_dtype);
     if (!s_last) return;
     list_tail(A.dsc, A.seg, A.seg_dst, (int64_t)gridDim.x * gridDim.y, A.packed, A.counts, A.rec_capacity, s_tmp);
 }
