@@ -198,6 +198,39 @@ __device__ __forceinline__ Projected project_one(const ProjectArgs &P, const GsC
     return out;
 }
 
+// Conservative screen test from the mean and the largest scale only: false
+// only for Gaussians the full projection culls (behind the near plane, or a
+// tile rect that misses the grid). The rows of T = J W are
+// (fx/tz)(W0 - rx W2) and (fy/tz)(W1 - ry W2), so |T0| <= (fx/tz)(|W0| +
+// |rx| |W2|) for any W; with s_max the largest scale, |A0|^2 + |A1|^2 <=
+// s_max^2 (|T0|^2 + |T1|^2) =: B (R(q) is a rotation). lambda_max as the
+// projection computes it is at most the trace + sqrt(0.1) = a0 + c0 + 0.6 +
+// 0.317, so the pixel radius is at most 3 sqrt(B + 0.92); 1 % of B and 2
+// pixels of slack cover FP32 rounding. A non-finite bound keeps the
+// Gaussian (every comparison with NaN is false).
+__device__ __forceinline__ bool maybe_visible(const ProjectArgs &P, const GsCameraDev &K, const GsGrid &G,
+                                              int64_t i) {
+    const float mx = __ldg(P.means + 3 * i), my = __ldg(P.means + 3 * i + 1), mz = __ldg(P.means + 3 * i + 2);
+    const float ls = fmaxf(__ldg(P.log_scales + 3 * i), fmaxf(__ldg(P.log_scales + 3 * i + 1),
+                                                              __ldg(P.log_scales + 3 * i + 2)));
+    const float tz = fmaf(K.R[6], mx, fmaf(K.R[7], my, fmaf(K.R[8], mz, K.t[2])));
+    if (!(tz > K.near_z)) return false;
+    const float tx = fmaf(K.R[0], mx, fmaf(K.R[1], my, fmaf(K.R[2], mz, K.t[0])));
+    const float ty = fmaf(K.R[3], mx, fmaf(K.R[4], my, fmaf(K.R[5], mz, K.t[1])));
+    const float iz = 1.f / tz;
+    const float rx = fminf(K.lim_x, fmaxf(-K.lim_x, tx * iz));
+    const float ry = fminf(K.lim_y, fmaxf(-K.lim_y, ty * iz));
+    const float n0 = sqrtf(fmaf(K.R[0], K.R[0], fmaf(K.R[1], K.R[1], K.R[2] * K.R[2])));
+    const float n1 = sqrtf(fmaf(K.R[3], K.R[3], fmaf(K.R[4], K.R[4], K.R[5] * K.R[5])));
+    const float n2 = sqrtf(fmaf(K.R[6], K.R[6], fmaf(K.R[7], K.R[7], K.R[8] * K.R[8])));
+    const float t0 = K.fx * iz * fmaf(fabsf(rx), n2, n0), t1 = K.fy * iz * fmaf(fabsf(ry), n2, n1);
+    const float B = expf(2.f * ls) * fmaf(t0, t0, t1 * t1);
+    const float rb = 3.f * sqrtf(fmaf(B, 1.01f, 0.92f)) + 2.f;
+    const float u = fmaf(K.fx * tx, iz, K.cx), v = fmaf(K.fy * ty, iz, K.cy);
+    return !(u + rb < 0.f || u - rb > (float)(G.tiles_x * G.tile_w) || v + rb < 0.f ||
+             v - rb > (float)(G.tiles_y * G.tile_h));
+}
+
 // Deferred colours of a block's visible Gaussians. The SH colour is the
 // costliest part of a projection and only the few visible Gaussians need it;
 // evaluated by their own threads it would hold a whole warp (and, through
@@ -379,29 +412,52 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
     __shared__ uint32_t s_hist[kDepthPasses * 256];
     __shared__ uint32_t s_tmp[8];
     __shared__ bool s_last;
+    __shared__ uint32_t s_cand[256];
     __shared__ ColourStage s_col;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
-    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
-    Projected pr;
-    pr.tiles = 0;
-    if (i < A.P.n) pr = project_one<DEG, false>(A.P, A.P.cam, A.P.grid, i);
-    if (pr.tiles) {
-        A.P.records[3 * i] = pr.r0;
-        if (A.lp_geo) A.lp_geo[i] = pr.r0;
-    }
+    const int64_t i0 = (int64_t)blockIdx.x * 256, i = i0 + tid;
+    // Candidates (conservative screen test), compacted in index order: only
+    // they are projected in full, by the block's first threads.
+    const bool cand = i < A.P.n && maybe_visible(A.P, A.P.cam, A.P.grid, i);
+    const uint32_t cm = __ballot_sync(0xffffffffu, cand);
+    if (lane == 0) s_t[warp] = __popc(cm);
     bool mv = false;
-    if (A.prect && i < A.P.n) {
-        const uint2 nr = pack_rect(pr);
-        A.prect[i] = nr;
+    if (A.prect && i < A.P.n && !cand) {
+        A.prect[i] = make_uint2(0u, 0u);
         if (A.prev_rect) {
             const uint2 orr = A.prev_rect[i];
-            mv = nr.x != orr.x || nr.y != orr.y;
+            mv = (orr.x | orr.y) != 0u;
+        }
+    }
+    __syncthreads();
+    uint32_t cbase = 0, nc = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < warp) cbase += s_t[w];
+        nc += s_t[w];
+    }
+    if (cand) s_cand[cbase + __popc(cm & lanemask_lt())] = (uint32_t)tid;
+    __syncthreads();
+    Projected pr;
+    pr.tiles = 0;
+    const int64_t g = (uint32_t)tid < nc ? i0 + s_cand[tid] : -1;  // this thread's candidate
+    if (g >= 0) pr = project_one<DEG, false>(A.P, A.P.cam, A.P.grid, g);
+    if (pr.tiles) {
+        A.P.records[3 * g] = pr.r0;
+        if (A.lp_geo) A.lp_geo[g] = pr.r0;
+    }
+    bool mv2 = false;
+    if (A.prect && g >= 0) {
+        const uint2 nr = pack_rect(pr);
+        A.prect[g] = nr;
+        if (A.prev_rect) {
+            const uint2 orr = A.prev_rect[g];
+            mv2 = nr.x != orr.x || nr.y != orr.y;
         }
     }
     if (A.prev_rect) {
-        const uint32_t wm = __ballot_sync(0xffffffffu, mv);
-        if (lane == 0 && wm) atomicAdd(A.moved, (unsigned long long)__popc(wm));
+        const uint32_t wm = __popc(__ballot_sync(0xffffffffu, mv)) + __popc(__ballot_sync(0xffffffffu, mv2));
+        if (lane == 0 && wm) atomicAdd(A.moved, (unsigned long long)wm);
     }
     const uint32_t t = pr.tiles, v = t != 0u;
     uint32_t it = t, iv = v;
@@ -427,9 +483,9 @@ __global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
         const uint64_t j = s_base + pv + iv - 1;
         const uint32_t dbits = __float_as_uint(pr.r2.y);
         A.lkeys[j] = ((uint64_t)t << 32) | dbits;
-        A.lvals[j] = (uint32_t)i;
+        A.lvals[j] = (uint32_t)g;
         for (int d = 0; d < kDepthPasses; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
-        stage_colour(s_col, (int)(pv + iv - 1), pr, i, (uint32_t)i);
+        stage_colour(s_col, (int)(pv + iv - 1), pr, g, (uint32_t)g);
     }
     __syncthreads();
     if (bv)
@@ -843,15 +899,30 @@ __global__ void __launch_bounds__(256) project_list_batch_kernel(const ListBatch
     __shared__ uint32_t s_hist[kDepthPasses * 256];
     __shared__ uint32_t s_tmp[8];
     __shared__ bool s_last;
+    __shared__ uint32_t s_cand[256];
     __shared__ ColourStage s_col;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int view = blockIdx.y;
     const ViewDesc &V = A.views[view];
     for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
-    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+    const int64_t i0 = (int64_t)blockIdx.x * 256;
+    // Candidates compacted in index order, projected in full by the block's
+    // first threads (as in the single-view kernel).
+    const bool cand = i0 + tid < A.P.n && maybe_visible(A.P, V.cam, V.grid, i0 + tid);
+    const uint32_t cm = __ballot_sync(0xffffffffu, cand);
+    if (lane == 0) s_t[warp] = __popc(cm);
+    __syncthreads();
+    uint32_t cbase = 0, nc = 0;
+    for (int w = 0; w < 8; ++w) {
+        if (w < warp) cbase += s_t[w];
+        nc += s_t[w];
+    }
+    if (cand) s_cand[cbase + __popc(cm & lanemask_lt())] = (uint32_t)tid;
+    __syncthreads();
+    const int64_t i = (uint32_t)tid < nc ? i0 + s_cand[tid] : -1;  // this thread's candidate
     Projected pr;
     pr.tiles = 0;
-    if (i < A.P.n) pr = project_one<DEG, false>(A.P, V.cam, V.grid, i);
+    if (i >= 0) pr = project_one<DEG, false>(A.P, V.cam, V.grid, i);
     const uint32_t t = pr.tiles, v = t != 0u;
     uint32_t it = t, iv = v;
     for (int o = 1; o < 32; o <<= 1) {

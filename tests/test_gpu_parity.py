@@ -467,6 +467,45 @@ def test_render_depth_ties_short_and_long_lists(ctx, oracle_mod, n):
     assert np.array_equal(out["n_contrib"].cpu().numpy()[keep], img.last[keep])
 
 
+@pytest.mark.parametrize("case", ["clustered_rotated", "large_anisotropic", "skewed_camera"])
+def test_frame_visible_set_equals_full_projection(ctx, case):
+    """A frame skips the full projection of Gaussians that a screen bound
+    built from the mean and the largest scale rules out. That bound must be
+    conservative: the frame's visible Gaussians and key count equal those of
+    projecting every Gaussian in full (gs_project), on scenes that stress it
+    (rotated cameras, large anisotropic splats around the borders, a camera
+    matrix with scaled rows)."""
+    rng = np.random.default_rng(71)
+    if case == "clustered_rotated":
+        s = scenes.clustered(200_000, 71)
+        cams = [scenes.pinhole(1280, 720, 70.0, world_to_cam=scenes.look_at(rng.uniform(-3, 3, 3),
+                                                                              rng.normal(size=3)))
+                for _ in range(3)]
+    elif case == "large_anisotropic":
+        s = scenes.uniform_box(50_000, 72)
+        s.means[:, 0:2] *= 2.5
+        s.log_scales[:] = rng.normal(-1.5, 1.0, s.log_scales.shape).astype(np.float32)
+        s.log_scales[:, 0] += 1.5
+        cams = [scenes.pinhole(640, 480, 60.0), scenes.pinhole(300, 900, 40.0)]
+    else:
+        s = scenes.uniform_box(50_000, 73)
+        w2c = scenes.look_at([0.3, -0.2, -1.0], [0.1, 0.05, 1.0])
+        w2c[0, :3] *= 1.7
+        w2c[1, :3] *= 0.6
+        cams = [scenes.pinhole(512, 384, 60.0, world_to_cam=w2c)]
+    g = gs.scene_to_device(s)
+    for cam in cams:
+        rec = torch.zeros((s.n, 12), dtype=torch.float32, device="cuda")
+        tiles = torch.zeros(s.n, dtype=torch.int32, device="cuda")
+        gs.gs_project(ctx, g, s.sh_degree, cam, rec, tiles)
+        gs.render(ctx, g, s.sh_degree, cam, aux=False)
+        torch.cuda.synchronize()
+        st = gs.gs_last_render_stats(ctx)
+        t = tiles.to(torch.int64)
+        assert st["n_visible"] == int((t > 0).sum())
+        assert st["n_keys"] == int(t.sum())
+
+
 def test_render_is_deterministic(ctx):
     scene, cams = scenes.workload("clustered_1m_1080p")
     g = gs.scene_to_device(scene)
