@@ -156,25 +156,22 @@ def profiled_traffic(kernel: str):
     return None, None
 
 
-def in_front(scene, cam) -> int:
-    """Gaussians in front of the near plane (they read scale, rotation and
-    opacity in the projection; the rest read only their mean)."""
-    w = np.asarray(cam.world_to_cam, dtype=np.float64).reshape(3, 4)
-    tz = scene.means.astype(np.float64) @ w[2, :3] + w[2, 3]
-    return int((tz > cam.near_z).sum())
-
-
-def frame_bytes(n, n_front, n_vis, K, sh_degree, tile_passes, n_tiles, pixels) -> dict:
-    """Bytes each forward stage has to move in DRAM, per frame (records 48 B,
-    keys 8 B, values 4 B; the image is rgb + final T + last contributor)."""
+def frame_bytes(n, n_vis, K, sh_degree, tile_passes, n_tiles, pixels) -> dict:
+    """Bytes each forward stage has to move in DRAM, per frame: every mean
+    and log-scale (the screen bound), rotation, opacity and SH of the visible
+    Gaussians, records of 48 B, list entries of 12 B (gathered into index
+    order, then four depth passes), tile-id keys of 2 B (4 B from 65,536
+    tiles) with 4-byte values, and the image (rgb + final T + last
+    contributor)."""
     s = 3 * (sh_degree + 1) ** 2
+    kb = 2 if n_tiles <= 65536 else 4
     return {
-        "project": n * 12 + n_front * 32 + n_vis * (4 * s) + n_vis * (48 + 12),
-        "depth_sort": 4 * n_vis * 24,
+        "project": n * 24 + n_vis * (20 + 4 * s) + n_vis * (48 + 12),
+        "depth_sort": n_vis * 24 + 4 * n_vis * 24,
         "entry_scan": n_vis * 12,
-        "emit": n_vis * (32 + 8) + K * 12,
-        "tile_sort": tile_passes * K * 24,
-        "ranges": K * 8 + n_tiles * 8,
+        "emit": n_vis * (32 + 8) + K * (kb + 4),
+        "tile_sort": tile_passes * K * 2 * (kb + 4),
+        "ranges": K * kb + n_tiles * 8,
         "blend": K * 4 + n_vis * 48 + pixels * 20,
     }
 
@@ -235,7 +232,7 @@ def fwd_bwd(gs, torch, args, flush, local) -> dict:
     ctx.close()
     pk, _ = peaks()
     n_tiles = st["n_tiles"]
-    fb = frame_bytes(scene.n, in_front(scene, cam), st["n_visible"], st["n_keys"], scene.sh_degree,
+    fb = frame_bytes(scene.n, st["n_visible"], st["n_keys"], scene.sh_degree,
                      (st["key_bits"] - 32 + 7) // 8, n_tiles, cam.width * cam.height)
     total = sum(fb.values()) + backward_bytes(scene.n, st["n_visible"], st["n_keys"], scene.sh_degree,
                                               cam.width * cam.height)
@@ -673,7 +670,7 @@ def main():
 
     # HBM view of the same frame: bytes each stage must move / its live time.
     tile_passes = (stats["key_bits"] - 32 + 7) // 8
-    fbytes = frame_bytes(scene.n, in_front(scene, cam), stats["n_visible"], stats["n_keys"], scene.sh_degree,
+    fbytes = frame_bytes(scene.n, stats["n_visible"], stats["n_keys"], scene.sh_degree,
                          tile_passes, stats["n_tiles"], W * H)
     stage_of = {"project": "project_ms", "depth_sort": "depth_sort_ms", "entry_scan": "entry_scan_ms",
                 "emit": "emit_ms", "tile_sort": "tile_sort_ms", "ranges": "ranges_ms", "blend": "blend_ms"}

@@ -406,7 +406,7 @@ __device__ void list_tail(const GsSortScratch &dsc, const uint2 *seg, uint32_t *
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) project_list_kernel(const ListArgs A) {
+__global__ void __launch_bounds__(256, 6) project_list_kernel(const ListArgs A) {
     __shared__ uint32_t s_t[8], s_v[8];
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_hist[kDepthPasses * 256];
@@ -742,9 +742,14 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
     const int64_t k0 = (int64_t)blockIdx.x * kKeyBlock;
     const bool active = k0 < K && K <= E.capacity && nv <= E.list_capacity;
     if (tid == 0 && active) {
-        const int64_t j0 = E.block_entry[blockIdx.x];  // entry covering slot k0
+        // Entries from the one covering slot k0 to the one covering the next
+        // block's first slot (at most 2049 of them; one for a large splat).
+        const int64_t j0 = E.block_entry[blockIdx.x];
+        const int64_t last = (K - 1) >> kKeyBlockLog2;
+        int64_t j1 = (int64_t)blockIdx.x < last ? (int64_t)E.block_entry[blockIdx.x + 1] + 1 : nv;
+        j1 = min(j1, min(nv, j0 + kKeyBlock + 2));
         s_j0 = (int)j0;
-        s_cnt = (int)((nv - j0) < kKeyBlock + 2 ? (nv - j0) : kKeyBlock + 2);
+        s_cnt = (int)(j1 - j0);
     }
     __syncthreads();
     if (active) {
@@ -893,7 +898,7 @@ struct ListBatchArgs {
 };
 
 template <int DEG>
-__global__ void __launch_bounds__(256) project_list_batch_kernel(const ListBatchArgs A) {
+__global__ void __launch_bounds__(256, 6) project_list_batch_kernel(const ListBatchArgs A) {
     __shared__ uint32_t s_t[8], s_v[8];
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_hist[kDepthPasses * 256];
