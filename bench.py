@@ -552,11 +552,16 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def step():
-        gs.gs_render(ctx, g, scene.sh_degree, cam, rgb, variant=args.blend_variant)
+    def step(deferred=True):
+        # GS_SYNC_DEFERRED: the frame is enqueued without a host round trip
+        # (its counts are checked by a later call), so frames run back to back.
+        gs.gs_render(ctx, g, scene.sh_degree, cam, rgb, variant=args.blend_variant, deferred=deferred)
 
     for _ in range(args.warmup):
+        step(False)
+    for _ in range(args.warmup):
         step()
+    gs.gs_sync_status(ctx)
     torch.cuda.synchronize()
     gs.gs_sync_status(ctx)
 
@@ -598,6 +603,17 @@ def main():
     ms_per_step = dev_ms / args.steps
     frames = args.steps * world
     value = frames / (dev_ms / 1000.0)
+    # The same frames rendered synchronously (the host waits for each frame's
+    # counts): the host round trip then shows between frames.
+    n_sync = min(args.steps, 100)
+    sync_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_sync)]
+    for i in range(n_sync):
+        flush.fill_(float(i))
+        sync_ev[i][0].record(stream)
+        step(False)
+        sync_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    sync_ms = sum(a.elapsed_time(b) for a, b in sync_ev) / n_sync
     stage_ms = {k: float(np.median(v)) for k, v in stage_sum.items()}
 
     # End to end: every step copies its inputs (the Gaussian arrays) from
@@ -693,7 +709,9 @@ def main():
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "n_visible": stats["n_visible"], "n_keys": stats["n_keys"],
-                   "key_bits": stats["key_bits"], "blend_variant": args.blend_variant},
+                   "key_bits": stats["key_bits"], "blend_variant": args.blend_variant,
+                   "sync_mode": "deferred (GS_SYNC_DEFERRED)",
+                   "sync_frame_ms": round(sync_ms, 4)},
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "wall_s_timed_loop": round(wall, 3),
         "e2e": {"value": round(e2e_value, 3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
