@@ -326,6 +326,8 @@ constexpr int kDepthPasses = 4;                // the depth bits are the low wor
 constexpr int kDepthItems = 8;                 // short list: smaller sort partitions, shorter latency
 constexpr int kEntryItems = 8;                 // list entries per thread of the entry scan
 constexpr int kEntryTile = 256 * kEntryItems;
+constexpr int kProjPer = 4;                       // Gaussians per thread of the list projection
+constexpr int kProjBlock = 256 * kProjPer;        // ... and per block (one list segment)
 
 struct ListArgs {
     ProjectArgs P;
@@ -405,87 +407,131 @@ __device__ void list_tail(const GsSortScratch &dsc, const uint2 *seg, uint32_t *
     }
 }
 
+// A block of the list projection takes kProjBlock Gaussians (kProjPer per
+// thread), so its chain of dependent steps (screen test, full projection of
+// the candidates, reservation, list writes, ticket, colours) is paid once
+// per 1024 Gaussians. Candidates and the colour inputs are staged in
+// shared memory by candidate rank (index order).
+struct ListStage {
+    uint32_t cand[kProjBlock];   // candidate -> Gaussian offset in the block
+    uint32_t tiles[kProjBlock];  // candidate -> tile count (0: culled)
+    uint32_t dbits[kProjBlock];  // depth bits
+    float qa[kProjBlock], op[kProjBlock], tz[kProjBlock];  // record words r1.x, r1.y, r2.y
+    float rad[kProjBlock];       // r2.z (radius bits)
+    float dx[kProjBlock], dy[kProjBlock], dz[kProjBlock];  // view direction
+};
+
 template <int DEG>
-__global__ void __launch_bounds__(256, 6) project_list_kernel(const ListArgs A) {
-    __shared__ uint32_t s_t[8], s_v[8];
+__global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) {
+    __shared__ uint32_t s_cnt[kProjPer * 8];
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_hist[kDepthPasses * 256];
     __shared__ uint32_t s_tmp[8];
     __shared__ bool s_last;
-    __shared__ uint32_t s_cand[256];
-    __shared__ ColourStage s_col;
+    __shared__ ListStage S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
-    const int64_t i0 = (int64_t)blockIdx.x * 256, i = i0 + tid;
-    // Candidates (conservative screen test), compacted in index order: only
-    // they are projected in full, by the block's first threads.
-    const bool cand = i < A.P.n && maybe_visible(A.P, A.P.cam, A.P.grid, i);
-    const uint32_t cm = __ballot_sync(0xffffffffu, cand);
-    if (lane == 0) s_t[warp] = __popc(cm);
-    bool mv = false;
-    if (A.prect && i < A.P.n && !cand) {
-        A.prect[i] = make_uint2(0u, 0u);
-        if (A.prev_rect) {
-            const uint2 orr = A.prev_rect[i];
-            mv = (orr.x | orr.y) != 0u;
+    const int64_t i0 = (int64_t)blockIdx.x * kProjBlock;
+    // Screen test of Gaussians i0 + 256 q + tid; candidates keep index order,
+    // which is (q, warp, lane) order.
+    bool cand[kProjPer];
+    uint32_t cm[kProjPer];
+    uint32_t n_moved = 0;  // rects that changed (temporal re-binning's churn)
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) {
+        const int64_t i = i0 + q * 256 + tid;
+        cand[q] = i < A.P.n && maybe_visible(A.P, A.P.cam, A.P.grid, i);
+        if (A.prect && i < A.P.n && !cand[q]) {
+            A.prect[i] = make_uint2(0u, 0u);
+            if (A.prev_rect) {
+                const uint2 orr = A.prev_rect[i];
+                n_moved += (orr.x | orr.y) != 0u ? 1u : 0u;
+            }
         }
     }
-    __syncthreads();
-    uint32_t cbase = 0, nc = 0;
-    for (int w = 0; w < 8; ++w) {
-        if (w < warp) cbase += s_t[w];
-        nc += s_t[w];
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) {
+        cm[q] = __ballot_sync(0xffffffffu, cand[q]);
+        if (lane == 0) s_cnt[q * 8 + warp] = __popc(cm[q]);
     }
-    if (cand) s_cand[cbase + __popc(cm & lanemask_lt())] = (uint32_t)tid;
     __syncthreads();
-    Projected pr;
-    pr.tiles = 0;
-    const int64_t g = (uint32_t)tid < nc ? i0 + s_cand[tid] : -1;  // this thread's candidate
-    if (g >= 0) pr = project_one<DEG, false>(A.P, A.P.cam, A.P.grid, g);
-    if (pr.tiles) {
-        A.P.records[3 * g] = pr.r0;
-        if (A.lp_geo) A.lp_geo[g] = pr.r0;
+    uint32_t nc = 0;
+    uint32_t pre[kProjPer];
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) pre[q] = 0;
+    for (int k = 0; k < kProjPer * 8; ++k) {
+        const uint32_t x = s_cnt[k];
+#pragma unroll
+        for (int q = 0; q < kProjPer; ++q)
+            if (k < q * 8 + warp) pre[q] += x;
+        nc += x;
     }
-    bool mv2 = false;
-    if (A.prect && g >= 0) {
-        const uint2 nr = pack_rect(pr);
-        A.prect[g] = nr;
-        if (A.prev_rect) {
-            const uint2 orr = A.prev_rect[g];
-            mv2 = nr.x != orr.x || nr.y != orr.y;
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q)
+        if (cand[q]) S.cand[pre[q] + __popc(cm[q] & lanemask_lt())] = (uint32_t)(q * 256 + tid);
+    __syncthreads();
+    // Full projection of candidates tid, tid + 256, ...
+    for (uint32_t c = tid; c < nc; c += 256) {
+        const int64_t g = i0 + S.cand[c];
+        const Projected pr = project_one<DEG, false>(A.P, A.P.cam, A.P.grid, g);
+        S.tiles[c] = pr.tiles;
+        if (pr.tiles) {
+            A.P.records[3 * g] = pr.r0;
+            if (A.lp_geo) A.lp_geo[g] = pr.r0;
+            S.dbits[c] = __float_as_uint(pr.r2.y);
+            S.qa[c] = pr.r1.x;
+            S.op[c] = pr.r1.y;
+            S.tz[c] = pr.r2.y;
+            S.rad[c] = pr.r2.z;
+            S.dx[c] = pr.dir.x;
+            S.dy[c] = pr.dir.y;
+            S.dz[c] = pr.dir.z;
+        }
+        if (A.prect) {
+            const uint2 nr = pack_rect(pr);
+            A.prect[g] = nr;
+            if (A.prev_rect) {
+                const uint2 orr = A.prev_rect[g];
+                n_moved += (nr.x != orr.x || nr.y != orr.y) ? 1u : 0u;
+            }
         }
     }
     if (A.prev_rect) {
-        const uint32_t wm = __popc(__ballot_sync(0xffffffffu, mv)) + __popc(__ballot_sync(0xffffffffu, mv2));
+        const uint32_t wm = __reduce_add_sync(0xffffffffu, n_moved);
         if (lane == 0 && wm) atomicAdd(A.moved, (unsigned long long)wm);
     }
-    const uint32_t t = pr.tiles, v = t != 0u;
-    uint32_t it = t, iv = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t a = __shfl_up_sync(0xffffffffu, it, o);
-        const uint32_t b = __shfl_up_sync(0xffffffffu, iv, o);
-        if (lane >= o) { it += a; iv += b; }
-    }
-    if (lane == 31) { s_t[warp] = it; s_v[warp] = iv; }
     __syncthreads();
-    uint32_t pv = 0, bt = 0, bv = 0;
-    for (int w = 0; w < 8; ++w) {
-        if (w < warp) pv += s_v[w];
-        bt += s_t[w];
-        bv += s_v[w];
+    // List slots: thread tid owns candidates [4 tid, 4 tid + 4).
+    uint32_t tsum = 0, vsum = 0;
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) {
+        const uint32_t c = kProjPer * tid + q;
+        const uint32_t t = c < nc ? S.tiles[c] : 0u;
+        tsum += t;
+        vsum += t != 0u;
     }
-    if (tid == 0) {
+    const uint32_t vpre = block_exclusive_scan_256(vsum, s_tmp);
+    const uint32_t tpre = block_exclusive_scan_256(tsum, s_tmp);
+    if (tid == 255) {
+        const uint32_t bv = vpre + vsum, bt = tpre + tsum;
         s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) >> 33 : 0ull;
         A.seg[blockIdx.x] = make_uint2((uint32_t)s_base, bv);
+        s_cnt[0] = bv;
     }
     __syncthreads();
-    if (v) {
-        const uint64_t j = s_base + pv + iv - 1;
-        const uint32_t dbits = __float_as_uint(pr.r2.y);
-        A.lkeys[j] = ((uint64_t)t << 32) | dbits;
-        A.lvals[j] = (uint32_t)g;
-        for (int d = 0; d < kDepthPasses; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
-        stage_colour(s_col, (int)(pv + iv - 1), pr, g, (uint32_t)g);
+    const uint32_t bv = s_cnt[0];
+    uint64_t j = s_base + vpre;
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) {
+        const uint32_t c = kProjPer * tid + q;
+        const uint32_t t = c < nc ? S.tiles[c] : 0u;
+        if (t) {
+            const uint32_t dbits = S.dbits[c];
+            A.lkeys[j] = ((uint64_t)t << 32) | dbits;
+            A.lvals[j] = (uint32_t)(i0 + S.cand[c]);
+            for (int d = 0; d < kDepthPasses; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
+            ++j;
+        }
     }
     __syncthreads();
     if (bv)
@@ -499,7 +545,23 @@ __global__ void __launch_bounds__(256, 6) project_list_kernel(const ListArgs A) 
         s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    finish_colours<DEG>(s_col, (int)bv, A.P, A.lp_geo ? A.lp_oq : nullptr, A.lp_gb, A.lp_dtype);
+    // Colours of the visible candidates, after the block's last barrier.
+    for (uint32_t c = tid; c < nc; c += 256) {
+        const uint32_t t = S.tiles[c];
+        if (!t) continue;
+        const size_t g = (size_t)(i0 + S.cand[c]);
+        const float3 rgb = sh_colour<DEG>(A.P.sh + g * (DEG + 1) * (DEG + 1) * 3, A.P.sh_vec, S.dx[c], S.dy[c],
+                                          S.dz[c]);
+        const float4 r1 = make_float4(S.qa[c], S.op[c], rgb.x, rgb.y);
+        const float4 r2 = make_float4(rgb.z, S.tz[c], S.rad[c], __uint_as_float(t));
+        float4 *out = A.P.records + 3 * g;
+        out[1] = r1;
+        out[2] = r2;
+        if (A.lp_geo) {
+            A.lp_oq[g] = make_uint2(__float_as_uint(r1.x), pack2(r1.y, r1.z, A.lp_dtype));
+            A.lp_gb[g] = pack2(r1.w, r2.x, A.lp_dtype);
+        }
+    }
     if (!s_last) return;
     // Last block: every block's counts and list entries are in.
     list_tail(A.dsc, A.seg, A.seg_dst, gridDim.x, A.packed, A.counts, A.P.n, s_tmp);
@@ -1083,7 +1145,7 @@ cudaError_t launch_list_stages(const FrontLayout &L, char *base, int64_t n_list,
 }  // namespace
 
 size_t gs_fused_scratch_bytes(int64_t n, int64_t capacity) {
-    return front_layout(n, capacity, (n + 255) / 256).total;
+    return front_layout(n, capacity, (n + kProjBlock - 1) / kProjBlock).total;
 }
 
 size_t gs_key_block_bytes(int64_t capacity) {
@@ -1103,7 +1165,7 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     if (key_bytes != 2 && key_bytes != 4) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (g.n + 255) / 256;
+    const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
     const FrontLayout L = front_layout(g.n, capacity, blocks);
     char *base = static_cast<char *>(scan_scratch);
     e = cudaMemsetAsync(base, 0, L.zero, s);
