@@ -105,8 +105,11 @@ struct Projected {
 };
 
 // COLOUR = false leaves the colour words (r1.z, r1.w, r2.x) unset and
-// returns the view direction instead, for a colour evaluated later by
-// finish_colours.
+// returns the view direction instead, for a colour evaluated later (the list
+// projections evaluate the SH colours of a block's visible Gaussians after
+// its last barrier, by consecutive threads: visible Gaussians are a few
+// percent of a frame's, and evaluated by their own threads they would hold
+// whole warps, and through the barriers whole blocks, for one lane).
 template <int DEG, bool COLOUR = true>
 __device__ __forceinline__ Projected project_one(const ProjectArgs &P, const GsCameraDev &K, const GsGrid &G,
                                                  int64_t i) {
@@ -229,49 +232,6 @@ __device__ __forceinline__ bool maybe_visible(const ProjectArgs &P, const GsCame
     const float u = fmaf(K.fx * tx, iz, K.cx), v = fmaf(K.fy * ty, iz, K.cy);
     return !(u + rb < 0.f || u - rb > (float)(G.tiles_x * G.tile_w) || v + rb < 0.f ||
              v - rb > (float)(G.tiles_y * G.tile_h));
-}
-
-// Deferred colours of a block's visible Gaussians. The SH colour is the
-// costliest part of a projection and only the few visible Gaussians need it;
-// evaluated by their own threads it would hold a whole warp (and, through
-// the block's barriers, the block) for one lane. Instead each visible
-// Gaussian's record words are staged at its rank among the block's visible
-// ones, and after the block's last barrier the first threads evaluate the
-// colours of consecutive entries and write the colour-bearing words.
-struct ColourStage {
-    float4 r1[256], r2[256];  // record words 1 and 2 without the colour
-    float4 dir[256];          // view direction, Gaussian index (bits) in w
-    uint32_t slot[256];       // record slot (0xffffffff: not written)
-};
-
-__device__ __forceinline__ void stage_colour(ColourStage &S, int e, const Projected &pr, int64_t i, uint32_t slot) {
-    S.r1[e] = pr.r1;
-    S.r2[e] = pr.r2;
-    S.dir[e] = make_float4(pr.dir.x, pr.dir.y, pr.dir.z, __uint_as_float((uint32_t)i));
-    S.slot[e] = slot;
-}
-
-template <int DEG>
-__device__ __forceinline__ void finish_colours(const ColourStage &S, int n_vis, const ProjectArgs &P,
-                                               uint2 *lp_oq, uint32_t *lp_gb, int lp_dtype) {
-    for (int e = threadIdx.x; e < n_vis; e += blockDim.x) {
-        const uint32_t slot = S.slot[e];
-        if (slot == 0xffffffffu) continue;
-        const float4 d = S.dir[e];
-        const size_t i = __float_as_uint(d.w);
-        const float3 rgb = sh_colour<DEG>(P.sh + i * (DEG + 1) * (DEG + 1) * 3, P.sh_vec, d.x, d.y, d.z);
-        float4 r1 = S.r1[e], r2 = S.r2[e];
-        r1.z = rgb.x;
-        r1.w = rgb.y;
-        r2.x = rgb.z;
-        float4 *out = P.records + 3 * (size_t)slot;
-        out[1] = r1;
-        out[2] = r2;
-        if (lp_oq) {
-            lp_oq[slot] = make_uint2(__float_as_uint(r1.x), pack2(r1.y, r1.z, lp_dtype));
-            lp_gb[slot] = pack2(r1.w, r2.x, lp_dtype);
-        }
-    }
 }
 
 template <int DEG>
@@ -959,72 +919,114 @@ struct ListBatchArgs {
     uint32_t *d_err;
 };
 
+// Candidates of a batched block (kProjBlock Gaussians of one view) staged by
+// rank: the records go to compact slots, known only after the block's
+// reservation.
+struct BatchStage {
+    float4 r0[kProjBlock];
+    uint32_t cand[kProjBlock], tiles[kProjBlock];
+    uint32_t dbits[kProjBlock];  // depth bits, then the record slot
+    float qa[kProjBlock], op[kProjBlock], tz[kProjBlock], rad[kProjBlock];
+    float dx[kProjBlock], dy[kProjBlock], dz[kProjBlock];
+};
+
 template <int DEG>
-__global__ void __launch_bounds__(256, 6) project_list_batch_kernel(const ListBatchArgs A) {
-    __shared__ uint32_t s_t[8], s_v[8];
+__global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBatchArgs A) {
+    __shared__ uint32_t s_cnt[kProjPer * 8];
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_hist[kDepthPasses * 256];
     __shared__ uint32_t s_tmp[8];
     __shared__ bool s_last;
-    __shared__ uint32_t s_cand[256];
-    __shared__ ColourStage s_col;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    BatchStage &S = *reinterpret_cast<BatchStage *>(s_dyn);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int view = blockIdx.y;
     const ViewDesc &V = A.views[view];
     for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
-    const int64_t i0 = (int64_t)blockIdx.x * 256;
-    // Candidates compacted in index order, projected in full by the block's
-    // first threads (as in the single-view kernel).
-    const bool cand = i0 + tid < A.P.n && maybe_visible(A.P, V.cam, V.grid, i0 + tid);
-    const uint32_t cm = __ballot_sync(0xffffffffu, cand);
-    if (lane == 0) s_t[warp] = __popc(cm);
-    __syncthreads();
-    uint32_t cbase = 0, nc = 0;
-    for (int w = 0; w < 8; ++w) {
-        if (w < warp) cbase += s_t[w];
-        nc += s_t[w];
+    const int64_t i0 = (int64_t)blockIdx.x * kProjBlock;
+    // Screen test, candidates in index order (as the single-view kernel).
+    bool cand[kProjPer];
+    uint32_t cm[kProjPer];
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) {
+        const int64_t i = i0 + q * 256 + tid;
+        cand[q] = i < A.P.n && maybe_visible(A.P, V.cam, V.grid, i);
+        cm[q] = __ballot_sync(0xffffffffu, cand[q]);
+        if (lane == 0) s_cnt[q * 8 + warp] = __popc(cm[q]);
     }
-    if (cand) s_cand[cbase + __popc(cm & lanemask_lt())] = (uint32_t)tid;
     __syncthreads();
-    const int64_t i = (uint32_t)tid < nc ? i0 + s_cand[tid] : -1;  // this thread's candidate
-    Projected pr;
-    pr.tiles = 0;
-    if (i >= 0) pr = project_one<DEG, false>(A.P, V.cam, V.grid, i);
-    const uint32_t t = pr.tiles, v = t != 0u;
-    uint32_t it = t, iv = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t a = __shfl_up_sync(0xffffffffu, it, o);
-        const uint32_t b = __shfl_up_sync(0xffffffffu, iv, o);
-        if (lane >= o) { it += a; iv += b; }
+    uint32_t nc = 0;
+    uint32_t pre[kProjPer];
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) pre[q] = 0;
+    for (int k = 0; k < kProjPer * 8; ++k) {
+        const uint32_t x = s_cnt[k];
+#pragma unroll
+        for (int q = 0; q < kProjPer; ++q)
+            if (k < q * 8 + warp) pre[q] += x;
+        nc += x;
     }
-    if (lane == 31) { s_t[warp] = it; s_v[warp] = iv; }
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q)
+        if (cand[q]) S.cand[pre[q] + __popc(cm[q] & lanemask_lt())] = (uint32_t)(q * 256 + tid);
     __syncthreads();
-    uint32_t pv = 0, bt = 0, bv = 0;
-    for (int w = 0; w < 8; ++w) {
-        if (w < warp) pv += s_v[w];
-        bt += s_t[w];
-        bv += s_v[w];
+    for (uint32_t c = tid; c < nc; c += 256) {
+        const Projected pr = project_one<DEG, false>(A.P, V.cam, V.grid, i0 + S.cand[c]);
+        S.tiles[c] = pr.tiles;
+        if (pr.tiles) {
+            S.r0[c] = pr.r0;
+            S.dbits[c] = __float_as_uint(pr.r2.y);
+            S.qa[c] = pr.r1.x;
+            S.op[c] = pr.r1.y;
+            S.tz[c] = pr.r2.y;
+            S.rad[c] = pr.r2.z;
+            S.dx[c] = pr.dir.x;
+            S.dy[c] = pr.dir.y;
+            S.dz[c] = pr.dir.z;
+        }
     }
-    if (tid == 0) {
+    __syncthreads();
+    // Compact slots: thread tid owns candidates [4 tid, 4 tid + 4).
+    uint32_t tsum = 0, vsum = 0;
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) {
+        const uint32_t c = kProjPer * tid + q;
+        const uint32_t t = c < nc ? S.tiles[c] : 0u;
+        tsum += t;
+        vsum += t != 0u;
+    }
+    const uint32_t vpre = block_exclusive_scan_256(vsum, s_tmp);
+    const uint32_t tpre = block_exclusive_scan_256(tsum, s_tmp);
+    if (tid == 255) {
+        const uint32_t bv = vpre + vsum, bt = tpre + tsum;
         s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) >> 33 : 0ull;
         A.seg[(int64_t)view * gridDim.x + blockIdx.x] = make_uint2((uint32_t)s_base, bv);
+        s_cnt[0] = bv;
     }
     __syncthreads();
-    if (v) {
-        const uint64_t j = s_base + pv + iv - 1;
-        const bool fits = (int64_t)j < A.rec_capacity;
-        if (fits) {
-            A.P.records[3 * j] = pr.r0;
-            if (A.lp_geo) A.lp_geo[j] = pr.r0;
-            A.meta[j] = make_uint2((uint32_t)view, (uint32_t)i);
-            const uint32_t dbits = __float_as_uint(pr.r2.y);
-            A.lkeys[j] = ((uint64_t)t << 32) | dbits;
-            A.lvals[j] = (uint32_t)j;
-            for (int d = 0; d < kDepthPasses; ++d) atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
-        } else {
-            atomicOr(A.d_err, kErrCapacity);
+    const uint32_t bv = s_cnt[0];
+    uint64_t j = s_base + vpre;
+#pragma unroll
+    for (int q = 0; q < kProjPer; ++q) {
+        const uint32_t c = kProjPer * tid + q;
+        const uint32_t t = c < nc ? S.tiles[c] : 0u;
+        if (t) {
+            const uint32_t dbits = S.dbits[c];
+            const bool fits = (int64_t)j < A.rec_capacity;
+            if (fits) {
+                A.P.records[3 * j] = S.r0[c];
+                if (A.lp_geo) A.lp_geo[j] = S.r0[c];
+                A.meta[j] = make_uint2((uint32_t)view, (uint32_t)(i0 + S.cand[c]));
+                A.lkeys[j] = ((uint64_t)t << 32) | dbits;
+                A.lvals[j] = (uint32_t)j;
+                for (int d = 0; d < kDepthPasses; ++d)
+                    atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
+            } else {
+                atomicOr(A.d_err, kErrCapacity);
+            }
+            S.dbits[c] = fits ? (uint32_t)j : 0xffffffffu;
+            ++j;
         }
-        stage_colour(s_col, (int)(pv + iv - 1), pr, i, fits ? (uint32_t)j : 0xffffffffu);
     }
     __syncthreads();
     if (bv)
@@ -1036,9 +1038,34 @@ __global__ void __launch_bounds__(256, 6) project_list_batch_kernel(const ListBa
         s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
-    finish_colours<DEG>(s_col, (int)bv, A.P, A.lp_geo ? A.lp_oq : nullptr, A.lp_gb, A.lp_dtype);
+    // Colours of the visible candidates, after the block's last barrier.
+    for (uint32_t c = tid; c < nc; c += 256) {
+        const uint32_t t = S.tiles[c], slot = S.dbits[c];
+        if (!t || slot == 0xffffffffu) continue;
+        const size_t g = (size_t)(i0 + S.cand[c]);
+        const float3 rgb = sh_colour<DEG>(A.P.sh + g * (DEG + 1) * (DEG + 1) * 3, A.P.sh_vec, S.dx[c], S.dy[c],
+                                          S.dz[c]);
+        const float4 r1 = make_float4(S.qa[c], S.op[c], rgb.x, rgb.y);
+        const float4 r2 = make_float4(rgb.z, S.tz[c], S.rad[c], __uint_as_float(t));
+        float4 *out = A.P.records + 3 * (size_t)slot;
+        out[1] = r1;
+        out[2] = r2;
+        if (A.lp_geo) {
+            A.lp_oq[slot] = make_uint2(__float_as_uint(r1.x), pack2(r1.y, r1.z, A.lp_dtype));
+            A.lp_gb[slot] = pack2(r1.w, r2.x, A.lp_dtype);
+        }
+    }
     if (!s_last) return;
     list_tail(A.dsc, A.seg, A.seg_dst, (int64_t)gridDim.x * gridDim.y, A.packed, A.counts, A.rec_capacity, s_tmp);
+}
+
+template <int DEG>
+cudaError_t launch_project_list_batch(const ListBatchArgs &A, dim3 grid, cudaStream_t s) {
+    const cudaError_t e = cudaFuncSetAttribute(project_list_batch_kernel<DEG>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BatchStage));
+    if (e != cudaSuccess) return e;
+    project_list_batch_kernel<DEG><<<grid, 256, sizeof(BatchStage), s>>>(A);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -1584,7 +1611,7 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
 }
 
 size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity, int64_t n, int n_views) {
-    return front_layout(rec_capacity, key_capacity, (n + 255) / 256 * n_views).total;
+    return front_layout(rec_capacity, key_capacity, (n + kProjBlock - 1) / kProjBlock * n_views).total;
 }
 
 cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
@@ -1594,7 +1621,7 @@ cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *v
                                         void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const int64_t nb = (g.n + 255) / 256, n_seg = nb * n_views;
+    const int64_t nb = (g.n + kProjBlock - 1) / kProjBlock, n_seg = nb * n_views;
     const FrontLayout L = front_layout(rec_capacity, key_capacity, n_seg);
     char *base = static_cast<char *>(scratch);
     e = cudaMemsetAsync(base, 0, L.zero, s);
@@ -1621,12 +1648,11 @@ cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *v
     A.d_err = d_err;
     const dim3 grid((unsigned)nb, (unsigned)n_views);
     switch (g.sh_degree) {
-        case 0: project_list_batch_kernel<0><<<grid, 256, 0, s>>>(A); break;
-        case 1: project_list_batch_kernel<1><<<grid, 256, 0, s>>>(A); break;
-        case 2: project_list_batch_kernel<2><<<grid, 256, 0, s>>>(A); break;
-        default: project_list_batch_kernel<3><<<grid, 256, 0, s>>>(A); break;
+        case 0: e = launch_project_list_batch<0>(A, grid, s); break;
+        case 1: e = launch_project_list_batch<1>(A, grid, s); break;
+        case 2: e = launch_project_list_batch<2>(A, grid, s); break;
+        default: e = launch_project_list_batch<3>(A, grid, s); break;
     }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     EmitArgs E{};
     E.records = reinterpret_cast<const float4 *>(records);
