@@ -765,7 +765,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         bool retired = false;
         if ((st = retire_oldest(ctx, true, s, &retired)) != GS_OK) return st;
     }
-    if (ctx->key_capacity == 0) ctx->key_capacity = std::max<int64_t>(int64_t(1) << 20, 4 * n);
+    if (ctx->key_capacity == 0) ctx->key_capacity = std::max<int64_t>(int64_t(1) << 20, 2 * n);
     gs_record *rec = static_cast<gs_record *>(ctx->records.ptr);
     uint32_t *ranges = static_cast<uint32_t *>(ctx->ranges.ptr);
     auto &T = ctx->temporal;
@@ -922,7 +922,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         // count, bring it down to twice the count (the buffers themselves only
         // grow). A smaller margin would make the next frame of a larger view
         // overflow, which deferred frames report as an error.
-        if (!temporal && !ctx->pinned_capacity && (int64_t)K * 4 < cap)
+        if (!temporal && !ctx->pinned_capacity && (int64_t)K * 3 < cap)
             ctx->key_capacity = std::max<int64_t>(65536, (int64_t)(2 * K + 1024));
         if (*ctx->h_err) return collect_device_error(ctx, s);
         return GS_OK;

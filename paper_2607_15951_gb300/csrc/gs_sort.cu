@@ -110,7 +110,6 @@ onesweep_kernel(const KT *__restrict__ keys_in, const uint32_t *__restrict__ val
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int shift = 8 * (pass + sc.digit0);
     if (tid == 0) *s_part = atomicAdd(sc.counter + pass, 1u);
-    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
     __syncthreads();
     const int64_t p = *s_part;
     const int64_t base = p * kTile;
@@ -118,6 +117,8 @@ onesweep_kernel(const KT *__restrict__ keys_in, const uint32_t *__restrict__ val
     // the count have nothing to do (no later partition waits on them).
     const int64_t n = d_n ? (int64_t)*d_n : n_host;
     if (base >= n) return;
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
+    __syncthreads();
 
     // Warp-striped load: warp w holds pairs [w*32*kItems, (w+1)*32*kItems) of
     // the partition, item j of lane l at offset j*32 + l (coalesced).
