@@ -724,11 +724,11 @@ def main():
         "peaks": {"source": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
         "clocks": clk,
     }
-    # Kernel launches per gs_render: projection + compact list, four depth
-    # digit passes, the entry scan, key emission, one pass per tile digit,
-    # ranges, blend.
+    # Kernel launches per gs_render: projection + compact list, the list
+    # gather, four depth digit passes, the entry scan, key emission, one pass
+    # per tile digit, ranges, blend.
     tile_passes = (stats["key_bits"] - 32 + 7) // 8
-    per_step = 9 + tile_passes
+    per_step = 10 + tile_passes
     line["gpu_launches"] = per_step * args.steps
     if not args.no_fwd_bwd:
         line["fwd_bwd"] = fwd_bwd(gs, torch, args, flush, local)
