@@ -746,8 +746,16 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     const int64_t n = g->n;
     const int n_tiles = grid.tiles_x * grid.tiles_y;
     const int bits = key_bits_for(n_tiles);
-    const int tile_passes = (bits - 32 + 7) / 8;
-    const int key_bytes = n_tiles <= 65536 ? 2 : 4;  // tile-id keys of the tile sort
+    // Tile keys: (row << 8 | column) for grids at most 256 tiles wide (the
+    // tile sort's histograms then come from the rects and its first pass is
+    // fused with the emission), else tile ids.
+    const bool xy_keys = grid.tiles_x <= 256;
+    int row_bits = 0;
+    while ((1 << row_bits) < grid.tiles_y) ++row_bits;
+    const int tkey_bits = xy_keys ? 8 + row_bits : bits - 32;
+    const int tile_passes = (tkey_bits + 7) / 8;
+    const int sort_passes = tile_passes > 0 ? tile_passes : 1;
+    const int key_bytes = tkey_bits <= 16 ? 2 : 4;
     const int dtype = opts->record_dtype;
     if (dtype != GS_RECORD_F32 &&
         ((st = ensure(ctx, ctx->lp_geo, (size_t)(n > 0 ? n : 1) * 16, "reduced-precision records")) != GS_OK ||
@@ -803,7 +811,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             (st = ensure(ctx, ctx->values, (size_t)cap * 4, "values")) != GS_OK ||
             (st = ensure(ctx, ctx->alt_keys, (size_t)cap * key_bytes, "alt keys")) != GS_OK ||
             (st = ensure(ctx, ctx->alt_values, (size_t)cap * 4, "alt values")) != GS_OK ||
-            (st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes_digits(cap, tile_passes), "sort scratch")) !=
+            (st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes_digits(cap, sort_passes), "sort scratch")) !=
                 GS_OK ||
             (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n, cap), "front-end scratch")) != GS_OK)
             return st;
@@ -812,8 +820,12 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         uint32_t *avals = static_cast<uint32_t *>(ctx->alt_values.ptr);
         // The tile sort: keys are tile ids emitted in (depth, index) order,
         // so the stable sort on them alone gives each tile's list in order.
-        GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes_digits(cap, tile_passes), s));
-        const GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, cap, 0, tile_passes);
+        // Its digit histograms are counted from the tile rects during the
+        // projection, and its first pass is fused with the emission (whose
+        // output lands in the alternate buffers); at least one pass runs.
+        GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes_digits(cap, sort_passes), s));
+        GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, cap, 0, sort_passes);
+        sc.diverse_last = xy_keys;  // the row digit takes many values within a warp
         mark(ctx, EV_START, s);
         cudaEvent_t ev3[3] = {nullptr, nullptr, nullptr};
         if (ctx->timing) {
@@ -823,22 +835,31 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         }
         GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, static_cast<float4 *>(ctx->lp_geo.ptr),
                                            static_cast<uint2 *>(ctx->lp_oq.ptr),
-                                           static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype, keys, key_bytes, vals,
+                                           static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype,
+                                           xy_keys ? akeys : keys, key_bytes, xy_keys, xy_keys ? avals : vals,
                                            cap, ctx->d_counts,
                                            ctx->fused_scratch.ptr, sc, ctx->d_err, s, ev3, prect, prev_rect,
                                            ctx->d_counts + 4));
         mark(ctx, EV_EMIT, s);
-        bool in_alt = false;
+        // The remaining passes, from the emission's output (the alternate
+        // buffers after the fused first pass, else keys / vals).
+        void *in_k = xy_keys ? akeys : keys, *out_k = xy_keys ? keys : akeys;
+        uint32_t *in_v = xy_keys ? avals : vals, *out_v = xy_keys ? vals : avals;
+        const int first_pass = xy_keys ? 1 : 0;
+        bool moved = false;
         if (key_bytes == 2)
-            GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint16_t *>(keys), vals, static_cast<uint16_t *>(akeys),
-                                               avals, cap, ctx->d_counts + 2, sc, ctx->d_err, &in_alt, s));
+            GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint16_t *>(in_k), in_v, static_cast<uint16_t *>(out_k),
+                                               out_v, cap, ctx->d_counts + 2, sc, ctx->d_err, &moved, s,
+                                               gs::kSpinTimeoutNs, 64, first_pass));
         else
-            GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint32_t *>(keys), vals, static_cast<uint32_t *>(akeys),
-                                               avals, cap, ctx->d_counts + 2, sc, ctx->d_err, &in_alt, s));
+            GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint32_t *>(in_k), in_v, static_cast<uint32_t *>(out_k),
+                                               out_v, cap, ctx->d_counts + 2, sc, ctx->d_err, &moved, s,
+                                               gs::kSpinTimeoutNs, 64, first_pass));
         mark(ctx, EV_SORT, s);
-        const void *sk = in_alt ? akeys : keys;
-        uint32_t *sv = in_alt ? avals : vals;
-        GS_CUDA(ctx, gs_launch_ranges_tiles(sk, key_bytes, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s));
+        const void *sk = moved ? out_k : in_k;
+        uint32_t *sv = moved ? out_v : in_v;
+        GS_CUDA(ctx, gs_launch_ranges_tiles(sk, key_bytes, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s,
+                                            xy_keys ? grid.tiles_x : 0));
         mark(ctx, EV_RANGES, s);
         if ((st = launch_blend(ctx, reader(ctx, rec, dtype), sv, ranges, grid, cam, opts, fb, ctx->d_counts + 2,
                                cap, s)) != GS_OK)

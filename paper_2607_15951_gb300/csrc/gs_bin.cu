@@ -173,7 +173,8 @@ __global__ void ranges_kernel(const uint64_t *__restrict__ keys, int64_t n, int3
 template <typename KT>
 __global__ void __launch_bounds__(256) ranges_tiles_kernel(const KT *__restrict__ keys, int64_t n_capacity,
                                                           const unsigned long long *d_n, int32_t n_tiles,
-                                                          uint32_t *__restrict__ ranges, uint32_t *d_err) {
+                                                          uint32_t *__restrict__ ranges, uint32_t *d_err,
+                                                          int xy_tiles_x) {
     const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
     const int64_t n = (int64_t)*d_n;
     if (i0 >= n) return;
@@ -192,12 +193,16 @@ __global__ void __launch_bounds__(256) ranges_tiles_kernel(const KT *__restrict_
 #pragma unroll
         for (int j = 0; j < 8; ++j) k[j] = i0 + j < n ? (uint32_t)keys[i0 + j] : 0u;
     }
-    uint32_t prev = i0 > 0 ? (uint32_t)keys[i0 - 1] : 0xffffffffu;
+    // (row << 8 | column) keys to tile ids (the order is the same).
+    auto tile_of = [&](uint32_t key) {
+        return xy_tiles_x ? (key >> 8) * (uint32_t)xy_tiles_x + (key & 255u) : key;
+    };
+    uint32_t prev = i0 > 0 ? tile_of((uint32_t)keys[i0 - 1]) : 0xffffffffu;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int64_t i = i0 + j;
         if (i >= n) break;
-        const uint32_t t = k[j];
+        const uint32_t t = tile_of(k[j]);
         if (t >= (uint32_t)n_tiles) {
             atomicOr(d_err, kErrRange);
             return;
@@ -215,17 +220,17 @@ __global__ void __launch_bounds__(256) ranges_tiles_kernel(const KT *__restrict_
 
 cudaError_t gs_launch_ranges_tiles(const void *keys, int key_bytes, int64_t n_capacity,
                                    const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
-                                   uint32_t *d_err, cudaStream_t s) {
+                                   uint32_t *d_err, cudaStream_t s, int xy_tiles_x) {
     if (key_bytes != 2 && key_bytes != 4) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess || n_capacity == 0) return e;
     const unsigned blocks = (unsigned)((n_capacity + 8 * 256 - 1) / (8 * 256));
     if (key_bytes == 2)
         ranges_tiles_kernel<uint16_t><<<blocks, 256, 0, s>>>(static_cast<const uint16_t *>(keys), n_capacity, d_n,
-                                                            n_tiles, ranges, d_err);
+                                                            n_tiles, ranges, d_err, xy_tiles_x);
     else
         ranges_tiles_kernel<uint32_t><<<blocks, 256, 0, s>>>(static_cast<const uint32_t *>(keys), n_capacity, d_n,
-                                                            n_tiles, ranges, d_err);
+                                                            n_tiles, ranges, d_err, xy_tiles_x);
     return cudaGetLastError();
 }
 

@@ -308,6 +308,7 @@ struct GsSortScratch {
     int64_t parts;     // partitions of the capacity the passes are launched for
     int digit0;        // pass p sorts the 8-bit digit digit0 + p of the key
     int items;         // pairs per thread of a partition (256 threads): 8 or GS_SORT_ITEMS
+    bool diverse_last; // the last digit is diverse too (rank it with ballots, as the others)
 };
 size_t gs_sort_scratch_bytes(int64_t n, int key_bits);
 GsSortScratch gs_sort_carve(void *base, int64_t n_capacity, int key_bits);
@@ -331,18 +332,21 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
                                   uint32_t *alt_values, int64_t n_capacity,
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
-                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64);
+                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64,
+                                  int first_pass = 0);
 // The same over 32- and 16-bit keys (tile ids of a frame's tile sort).
 cudaError_t gs_launch_sort_passes(uint32_t *keys, uint32_t *values, uint32_t *alt_keys,
                                   uint32_t *alt_values, int64_t n_capacity,
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
-                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64);
+                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64,
+                                  int first_pass = 0);
 cudaError_t gs_launch_sort_passes(uint16_t *keys, uint32_t *values, uint16_t *alt_keys,
                                   uint32_t *alt_values, int64_t n_capacity,
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
-                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64);
+                                  unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64,
+                                  int first_pass = 0);
 
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
@@ -361,27 +365,32 @@ cudaError_t gs_launch_blend_tma(const RecordReader &rd, const uint32_t *values, 
 // scan), with the depth digit histograms; (2) a stable radix sort of that
 // list by depth (4 digit passes over the visible Gaussians only), which so
 // orders it by (depth bits, index); (3) a scan of the tile counts in depth
-// order giving each entry its first key slot; (4) emission of the keys — the
-// tile id alone, key_bytes = 2 (fewer than 65536 tiles) or 4 — in that
-// order, with the tile digit histograms + bucket offsets of the tile sort
-// `sc` (carved with digit0 = 0). The stable tile sort then leaves every
-// tile's list in (depth bits, index) order.
+// order giving each entry its first key slot; (4) emission of the keys in
+// that order: with xy_keys (grids at most 256 tiles wide) the key is (row <<
+// 8 | column), the tile sort's digit histograms are counted from the rects
+// in (1) and the emission is fused with the sort's first pass, whose output
+// lands in keys / values (the caller runs passes 1..); otherwise the key is
+// the tile id, counted by the emission, and all passes are the caller's.
+// key_bytes = 2 or 4; `sc` is the tile sort's scratch (digit0 = 0, at least
+// one pass). The stable tile sort leaves every tile's list in (depth bits,
+// index) order.
 // counts[0] = K, counts[1] = visible Gaussians, counts[2] = K if it fits in
 // `capacity` else 0 (the tile sort and ranges then see an empty list and the
 // overflow bit is set in d_err), counts[3] = visible Gaussians (the depth
 // sort's count). `scan_scratch`: gs_fused_scratch_bytes(n, capacity).
 size_t gs_fused_scratch_bytes(int64_t n, int64_t capacity);
 size_t gs_key_block_bytes(int64_t capacity);
-// Per-tile [first, last + 1) of tile-id keys sorted by gs_launch_project_bin
+// Per-tile [first, last + 1) of tile keys sorted by gs_launch_project_bin
 // + the tile sort (key_bytes 2 or 4; *d_n keys, the grid covering
-// n_capacity); empty tiles get [0, 0).
+// n_capacity); empty tiles get [0, 0). Keys are tile ids, or (row << 8 |
+// column) when xy_tiles_x (the grid's width in tiles) is non-zero.
 cudaError_t gs_launch_ranges_tiles(const void *keys, int key_bytes, int64_t n_capacity,
                                    const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
-                                   uint32_t *d_err, cudaStream_t s);
+                                   uint32_t *d_err, cudaStream_t s, int xy_tiles_x = 0);
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
                                   int lp_dtype,
-                                  void *keys, int key_bytes, uint32_t *values,
+                                  void *keys, int key_bytes, bool xy_keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
                                   const cudaEvent_t *marks = nullptr /* 3 events or null */,

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "gs_internal.cuh"
+#include "gs_onesweep.cuh"
 
 namespace {
 
@@ -301,7 +302,12 @@ struct ListArgs {
     uint64_t *lkeys;             // n: tiles << 32 | depth bits of visible entry j
     uint32_t *lvals;             // n: its Gaussian index
     GsSortScratch dsc;           // the depth sort's histograms, bucket offsets, ticket
-    unsigned long long *counts;  // [3] <- visible count (the depth sort's count)
+    unsigned long long *counts;  // [0] K, [1] visible, [2] K if it fits, [3] visible (depth sort's count)
+    bool xy_keys;                // keys (row << 8 | column): the tile sort's histograms are counted
+    GsSortScratch tsc;           // here from the rects, for the emission fused with its first pass
+    int tile_passes;             // at least 1
+    int64_t key_capacity;
+    uint32_t *d_err;
     uint2 *prect;                // optional, n: packed tile rect of every Gaussian (0 = none),
                                  // kept for temporal re-binning
     const uint2 *prev_rect;      // optional, n: the previous frame's; rects that differ
@@ -315,18 +321,88 @@ __device__ __forceinline__ uint2 pack_rect(const Projected &pr) {
                     : make_uint2(0u, 0u);
 }
 
+// Digit histograms of a frame's tile keys, counted from the tile rects when
+// the keys are (tile row << 8 | tile column) (grids at most 256 tiles wide):
+// the low digit is the column, so a rect adds its height to each of its
+// columns (a difference array: two updates), the next digit the low byte of
+// the row (its width to each of its rows, a circular range), the third the
+// row's high byte. Four updates per Gaussian, however large its rect.
+struct TileDigitHist {
+    int dx[257];       // column digit: difference array
+    int dy[257];       // row low byte: difference array
+    uint32_t turns;    // whole turns of the row range (256 rows or more) x width
+    uint32_t hy[256];  // row high byte
+};
+
+__device__ __forceinline__ void count_rect_digits(TileDigitHist &H, const Rect &R, int passes) {
+    const int w = R.x1 - R.x0, h = R.y1 - R.y0;
+    atomicAdd(&H.dx[R.x0], h);
+    atomicAdd(&H.dx[R.x1], -h);
+    if (passes > 1) {
+        const uint32_t t = (uint32_t)h >> 8, r = (uint32_t)h & 255u, st = (uint32_t)R.y0 & 255u;
+        if (t) atomicAdd(&H.turns, t * (uint32_t)w);
+        if (r) {
+            atomicAdd(&H.dy[st], w);
+            if (st + r <= 256u) {
+                atomicAdd(&H.dy[st + r], -w);
+            } else {
+                atomicAdd(&H.dy[0], w);
+                atomicAdd(&H.dy[st + r - 256u], -w);
+            }
+        }
+    }
+    if (passes > 2)
+        for (int v = R.y0 >> 8; v <= (R.y1 - 1) >> 8; ++v) {
+            const int lo = max(R.y0, v << 8), hi = min(R.y1, (v + 1) << 8);
+            atomicAdd(&H.hy[v & 255], (uint32_t)((hi - lo) * w));
+        }
+}
+
+// Adds a block's counts to the global histograms (passes x 256).
+__device__ __forceinline__ void flush_tile_digits(TileDigitHist &H, uint32_t *hist, int passes, uint32_t *s_tmp) {
+    const int tid = threadIdx.x;
+    // Inclusive prefixes of the difference arrays give the counts.
+    const int cx = H.dx[tid];
+    const uint32_t nx = block_exclusive_scan_256((uint32_t)cx, s_tmp) + (uint32_t)cx;
+    if (nx) atomicAdd(&hist[tid], nx);
+    if (passes > 1) {
+        const int cy = H.dy[tid];
+        const uint32_t ny = block_exclusive_scan_256((uint32_t)cy, s_tmp) + (uint32_t)cy + H.turns;
+        if (ny) atomicAdd(&hist[256 + tid], ny);
+    }
+    if (passes > 2 && H.hy[tid]) atomicAdd(&hist[512 + tid], H.hy[tid]);
+}
+
 // The last block of a list-building projection: the depth sort's bucket
 // offsets, and the places of the n_seg list segments (one per projection
 // block, in index order); counts[3] = the list's length, or 0 when it
 // exceeds list_cap (nothing is then sorted).
 __device__ void list_tail(const GsSortScratch &dsc, const uint2 *seg, uint32_t *seg_dst, int64_t n_seg,
                           const unsigned long long *packed, unsigned long long *counts, int64_t list_cap,
-                          uint32_t *s_tmp) {
+                          uint32_t *s_tmp, const GsSortScratch *tsc = nullptr, int tile_passes = 0,
+                          int64_t key_cap = 0, uint32_t *d_err = nullptr) {
     const int tid = threadIdx.x;
     __threadfence();
     for (int d = 0; d < kDepthPasses; ++d) {
         const uint32_t c = __ldcg(&dsc.hist[d * 256 + tid]);
         dsc.bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
+    }
+    // With the tile histograms counted from the rects: the tile sort's bucket
+    // offsets and the key count (which the emission would publish).
+    if (tsc) {
+        for (int d = 0; d < tile_passes; ++d) {
+            const uint32_t c = __ldcg(&tsc->hist[d * 256 + tid]);
+            tsc->bucket[d * 256 + tid] = block_exclusive_scan_256(c, s_tmp);
+        }
+        if (tid == 0) {
+            const unsigned long long pk = __ldcg(packed);
+            const unsigned long long K = pk & kKeyMask;
+            counts[0] = K;
+            counts[1] = pk >> 33;
+            const bool fits = (int64_t)K <= key_cap;
+            if (!fits) atomicOr(d_err, kErrCapacity);
+            counts[2] = fits ? K : 0ull;
+        }
     }
     // Segments in order, 4096 per round: thread tid takes 16 consecutive
     // table entries (eight 16-byte loads in flight).
@@ -375,8 +451,8 @@ __device__ void list_tail(const GsSortScratch &dsc, const uint2 *seg, uint32_t *
 struct ListStage {
     uint32_t cand[kProjBlock];   // candidate -> Gaussian offset in the block
     uint32_t tiles[kProjBlock];  // candidate -> tile count (0: culled)
-    uint32_t dbits[kProjBlock];  // depth bits
-    float qa[kProjBlock], op[kProjBlock], tz[kProjBlock];  // record words r1.x, r1.y, r2.y
+    uint32_t dbits[kProjBlock];  // depth bits (record word r2.y)
+    float qa[kProjBlock], op[kProjBlock];  // record words r1.x, r1.y
     float rad[kProjBlock];       // r2.z (radius bits)
     float dx[kProjBlock], dy[kProjBlock], dz[kProjBlock];  // view direction
 };
@@ -389,8 +465,15 @@ __global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) 
     __shared__ uint32_t s_tmp[8];
     __shared__ bool s_last;
     __shared__ ListStage S;
+    __shared__ TileDigitHist s_th;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
+    for (int k = tid; k < 257; k += 256) {
+        s_th.dx[k] = 0;
+        s_th.dy[k] = 0;
+    }
+    s_th.hy[tid] = 0;
+    if (tid == 0) s_th.turns = 0;
     const int64_t i0 = (int64_t)blockIdx.x * kProjBlock;
     // Screen test of Gaussians i0 + 256 q + tid; candidates keep index order,
     // which is (q, warp, lane) order.
@@ -438,10 +521,10 @@ __global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) 
         if (pr.tiles) {
             A.P.records[3 * g] = pr.r0;
             if (A.lp_geo) A.lp_geo[g] = pr.r0;
+            if (A.xy_keys) count_rect_digits(s_th, pr.rect, A.tile_passes);
             S.dbits[c] = __float_as_uint(pr.r2.y);
             S.qa[c] = pr.r1.x;
             S.op[c] = pr.r1.y;
-            S.tz[c] = pr.r2.y;
             S.rad[c] = pr.r2.z;
             S.dx[c] = pr.dir.x;
             S.dy[c] = pr.dir.y;
@@ -494,9 +577,11 @@ __global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) 
         }
     }
     __syncthreads();
-    if (bv)
+    if (bv) {
         for (int k = tid; k < kDepthPasses * 256; k += 256)
             if (s_hist[k]) atomicAdd(&A.dsc.hist[k], s_hist[k]);
+        if (A.xy_keys) flush_tile_digits(s_th, A.tsc.hist, A.tile_passes, s_tmp);
+    }
     // The barrier orders the block's counter updates before thread 0's fence,
     // which publishes them (cumulatively) before its ticket.
     __syncthreads();
@@ -513,7 +598,7 @@ __global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) 
         const float3 rgb = sh_colour<DEG>(A.P.sh + g * (DEG + 1) * (DEG + 1) * 3, A.P.sh_vec, S.dx[c], S.dy[c],
                                           S.dz[c]);
         const float4 r1 = make_float4(S.qa[c], S.op[c], rgb.x, rgb.y);
-        const float4 r2 = make_float4(rgb.z, S.tz[c], S.rad[c], __uint_as_float(t));
+        const float4 r2 = make_float4(rgb.z, __uint_as_float(S.dbits[c]), S.rad[c], __uint_as_float(t));
         float4 *out = A.P.records + 3 * g;
         out[1] = r1;
         out[2] = r2;
@@ -524,7 +609,8 @@ __global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) 
     }
     if (!s_last) return;
     // Last block: every block's counts and list entries are in.
-    list_tail(A.dsc, A.seg, A.seg_dst, gridDim.x, A.packed, A.counts, A.P.n, s_tmp);
+    list_tail(A.dsc, A.seg, A.seg_dst, gridDim.x, A.packed, A.counts, A.P.n, s_tmp, A.xy_keys ? &A.tsc : nullptr,
+              A.tile_passes, A.key_capacity, A.d_err);
 }
 
 // Warp w of block b copies list segment 8 b + w (the visible Gaussians of
@@ -890,6 +976,129 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
     }
 }
 
+// Key emission fused with the first (column) pass of the tile sort, for a
+// single view at most 256 tiles wide whose keys are (row << 8 | column) and
+// whose digit histograms were counted from the rects in the projection:
+// block p (taken in ticket order) produces the keys of
+// slots [2048 p, 2048 p + 2048) as emit_keys_kernel does, stages them in
+// shared memory, reads them back warp-striped and runs one Onesweep
+// partition on them, writing the pass's output. The keys never make a round
+// trip through memory before their first pass.
+struct EmitSortArgs {
+    EmitArgs E;                     // entries and records; keys / values receive the pass's output
+    const uint32_t *bucket;         // the pass's 256 exclusive digit offsets
+    unsigned long long *status;     // the pass's look-back words (one row of 256 per key block, zeroed)
+    uint32_t *ticket;               // key-block tickets (zeroed)
+    unsigned long long timeout_ns;
+};
+
+template <typename KT>
+constexpr int emit_sort_smem() {
+    constexpr int emit = (kKeyBlock + 2) * 8 + kKeyBlock * (int)(sizeof(KT) + 4);
+    constexpr int part = (int)onesweep_partition_smem<KT, kKeysPerThread>();
+    return emit > part ? emit : part;
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(256, 2) emit_sort_kernel(const EmitSortArgs A) {
+    const EmitArgs &E = A.E;
+    __shared__ __align__(16) unsigned char s_raw[emit_sort_smem<KT>()];
+    __shared__ int s_j0, s_cnt;
+    __shared__ uint32_t s_part;
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(s_raw);
+    uint32_t *s_idx = s_off + kKeyBlock + 2;
+    KT *s_key = reinterpret_cast<KT *>(s_idx + kKeyBlock + 2);
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(s_key + kKeyBlock);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const GsGrid &G = E.grid;
+    if (tid == 0) s_part = atomicAdd(A.ticket, 1u);
+    __syncthreads();
+    const int64_t p = s_part;
+    const unsigned long long packed = *E.packed;
+    const int64_t K = (int64_t)(packed & kKeyMask);
+    const int64_t nv = (int64_t)(packed >> 33);
+    const int64_t k0 = p * kKeyBlock;
+    // Blocks past the keys (or every block, when the keys overflow the
+    // buffers) have nothing to do; no block waits on a later one.
+    if (!(k0 < K && K <= E.capacity && nv <= E.list_capacity)) return;
+    if (tid == 0) {
+        const int64_t j0 = E.block_entry[p];
+        const int64_t last = (K - 1) >> kKeyBlockLog2;
+        int64_t j1 = p < last ? (int64_t)E.block_entry[p + 1] + 1 : nv;
+        j1 = min(j1, min(nv, j0 + kKeyBlock + 2));
+        s_j0 = (int)j0;
+        s_cnt = (int)(j1 - j0);
+    }
+    __syncthreads();
+    for (int q = tid; q < s_cnt; q += 256) {
+        s_off[q] = E.list_off[s_j0 + q];
+        s_idx[q] = E.list_idx[s_j0 + q];
+    }
+    __syncthreads();
+    const int64_t kb = k0 + (int64_t)tid * kKeysPerThread;
+    if (kb < K) {
+        int lo = 0, hi = s_cnt - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)s_off[mid] <= kb) lo = mid; else hi = mid - 1;
+        }
+        int e = -1;
+        uint32_t g = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0;
+        uint32_t tk[kKeysPerThread], tv[kKeysPerThread];
+#pragma unroll
+        for (int q = 0; q < kKeysPerThread; ++q) {
+            const int64_t k = kb + q;
+            tk[q] = 0u;
+            tv[q] = 0u;
+            if (k >= K) continue;
+            if (e < 0 || (uint64_t)k >= eend) {
+                if (e >= 0) ++lo;
+                while (lo + 1 < s_cnt && (int64_t)s_off[lo + 1] <= k) ++lo;
+                e = lo;
+                g = s_idx[e];
+                ebase = s_off[e];
+                const float4 r0 = E.records[3 * (size_t)g];
+                const float4 r2 = E.records[3 * (size_t)g + 2];
+                const Rect R = tile_rect(r0.x, r0.y, __float_as_int(r2.z), G.tile_w, G.tile_h, G.tiles_x,
+                                         G.tiles_y);
+                w = (uint32_t)(R.x1 - R.x0);
+                x0 = (uint32_t)R.x0;
+                y0 = (uint32_t)R.y0;
+                eend = ebase + w * (uint32_t)(R.y1 - R.y0);
+            }
+            const uint32_t m = (uint32_t)(k - ebase);
+            const uint32_t qy = m / w, rx = m - qy * w;
+            tk[q] = ((y0 + qy) << 8) | (x0 + rx);
+            tv[q] = g;
+        }
+        uint4 *sv4 = reinterpret_cast<uint4 *>(s_val + tid * kKeysPerThread);
+        sv4[0] = make_uint4(tv[0], tv[1], tv[2], tv[3]);
+        sv4[1] = make_uint4(tv[4], tv[5], tv[6], tv[7]);
+        uint4 *sk4 = reinterpret_cast<uint4 *>(s_key + tid * kKeysPerThread);
+        if (sizeof(KT) == 2) {
+            sk4[0] = make_uint4(tk[0] | tk[1] << 16, tk[2] | tk[3] << 16, tk[4] | tk[5] << 16, tk[6] | tk[7] << 16);
+        } else {
+            sk4[0] = make_uint4(tk[0], tk[1], tk[2], tk[3]);
+            sk4[1] = make_uint4(tk[4], tk[5], tk[6], tk[7]);
+        }
+    }
+    __syncthreads();
+    // Slot order within the block is (thread, item); read back warp-striped
+    // so that the partition's (item, lane) order within a warp is slot order.
+    KT key[kKeysPerThread];
+    uint32_t val[kKeysPerThread];
+#pragma unroll
+    for (int j = 0; j < kKeysPerThread; ++j) {
+        const int i = warp * 32 * kKeysPerThread + j * 32 + lane;
+        const bool ok = k0 + i < K;
+        key[j] = ok ? s_key[i] : (KT)~(KT)0;
+        val[j] = ok ? s_val[i] : 0u;
+    }
+    __syncthreads();  // the partition reuses the staging memory
+    onesweep_partition<KT, kKeysPerThread>(key, val, k0, K, p, 0, A.status, A.bucket, static_cast<KT *>(E.keys),
+                                           E.values, E.d_err, A.timeout_ns, true, s_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Batched front end (many views of one scene), depth first as a single view:
 // block (b, v) projects Gaussians [256 b, 256 b + 256) for view v and
@@ -1077,11 +1286,12 @@ namespace {
 // zeroed per frame), then the segment table, the compact list, its sort buffers, the entries'
 // first slots and the key-block table.
 struct FrontLayout {
-    size_t dsort, scan_status, zero, seg, seg_dst, lkeys, lvals, akeys, avals, off, block_entry, total;
+    size_t dsort, scan_status, st0, zero, seg, seg_dst, lkeys, lvals, akeys, avals, off, block_entry, total;
 };
 
-// n_list: entries the list holds; n_seg: projection blocks (list segments).
-FrontLayout front_layout(int64_t n_list, int64_t capacity, int64_t n_seg) {
+// n_list: entries the list holds; n_seg: projection blocks (list segments);
+// fused: emission fused with the first tile pass (single view).
+FrontLayout front_layout(int64_t n_list, int64_t capacity, int64_t n_seg, bool fused) {
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const int64_t nn = n_list > 0 ? n_list : 1;
     const int64_t ns = n_seg > 0 ? n_seg : 1;
@@ -1091,6 +1301,8 @@ FrontLayout front_layout(int64_t n_list, int64_t capacity, int64_t n_seg) {
     o += al(gs_sort_scratch_bytes_digits(nn, kDepthPasses, kDepthItems));
     L.scan_status = o;
     o += al((size_t)((nn + kEntryTile - 1) / kEntryTile + 1) * 8);
+    L.st0 = o;  // the fused emission pass: look-back words per key block, then its ticket
+    if (fused) o += al((size_t)((capacity + kKeyBlock - 1) / kKeyBlock + 1) * kOsRadix * 8 + 16);
     L.zero = o;
     L.seg = o;
     o += al((size_t)ns * 8);
@@ -1117,7 +1329,7 @@ FrontLayout front_layout(int64_t n_list, int64_t capacity, int64_t n_seg) {
 // leaves the list there), entry scan and key emission. E carries the
 // record, grid and output fields; the list fields are filled here.
 cudaError_t launch_list_stages(const FrontLayout &L, char *base, int64_t n_list, int64_t n_seg,
-                               const GsSortScratch &dsc, EmitArgs E, int key_bytes, bool batch,
+                               const GsSortScratch &dsc, EmitArgs E, int key_bytes, bool batch, bool xy_keys,
                                unsigned long long *counts, uint32_t *d_err, cudaStream_t s, const cudaEvent_t *marks) {
     const uint2 *seg = reinterpret_cast<const uint2 *>(base + L.seg);
     const uint32_t *seg_dst = reinterpret_cast<const uint32_t *>(base + L.seg_dst);
@@ -1159,12 +1371,32 @@ cudaError_t launch_list_stages(const FrontLayout &L, char *base, int64_t n_list,
     const unsigned eblocks = (unsigned)((E.capacity + kKeyBlock - 1) / kKeyBlock);
     if (batch) {
         emit_keys_kernel<uint32_t, true><<<eblocks, 256, 0, s>>>(E);
-    } else if (key_bytes == 2) {
-        gs_carveout(emit_keys_kernel<uint16_t, false>);
-        emit_keys_kernel<uint16_t, false><<<eblocks, 256, 0, s>>>(E);
+        return cudaGetLastError();
+    }
+    if (!xy_keys) {  // wide grids: tile ids, histograms counted by the emission
+        if (key_bytes == 2) {
+            gs_carveout(emit_keys_kernel<uint16_t, false>);
+            emit_keys_kernel<uint16_t, false><<<eblocks, 256, 0, s>>>(E);
+        } else {
+            gs_carveout(emit_keys_kernel<uint32_t, false>);
+            emit_keys_kernel<uint32_t, false><<<eblocks, 256, 0, s>>>(E);
+        }
+        return cudaGetLastError();
+    }
+    // Single view: the histograms came from the projection; emission and the
+    // first tile pass are one kernel writing that pass's output.
+    EmitSortArgs F;
+    F.E = E;
+    F.bucket = E.sc.bucket;
+    F.status = reinterpret_cast<unsigned long long *>(base + L.st0);
+    F.ticket = reinterpret_cast<uint32_t *>(base + L.st0 + (size_t)(eblocks + 1) * kOsRadix * 8);
+    F.timeout_ns = kSpinTimeoutNs;
+    if (key_bytes == 2) {
+        gs_carveout(emit_sort_kernel<uint16_t>);
+        emit_sort_kernel<uint16_t><<<eblocks, 256, 0, s>>>(F);
     } else {
-        gs_carveout(emit_keys_kernel<uint32_t, false>);
-        emit_keys_kernel<uint32_t, false><<<eblocks, 256, 0, s>>>(E);
+        gs_carveout(emit_sort_kernel<uint32_t>);
+        emit_sort_kernel<uint32_t><<<eblocks, 256, 0, s>>>(F);
     }
     return cudaGetLastError();
 }
@@ -1172,7 +1404,7 @@ cudaError_t launch_list_stages(const FrontLayout &L, char *base, int64_t n_list,
 }  // namespace
 
 size_t gs_fused_scratch_bytes(int64_t n, int64_t capacity) {
-    return front_layout(n, capacity, (n + kProjBlock - 1) / kProjBlock).total;
+    return front_layout(n, capacity, (n + kProjBlock - 1) / kProjBlock, true).total;
 }
 
 size_t gs_key_block_bytes(int64_t capacity) {
@@ -1182,7 +1414,7 @@ size_t gs_key_block_bytes(int64_t capacity) {
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
                                   int lp_dtype,
-                                  void *keys, int key_bytes, uint32_t *values,
+                                  void *keys, int key_bytes, bool xy_keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
                                   const cudaEvent_t *marks, uint2 *prect, const uint2 *prev_rect,
@@ -1193,7 +1425,7 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
-    const FrontLayout L = front_layout(g.n, capacity, blocks);
+    const FrontLayout L = front_layout(g.n, capacity, blocks, xy_keys);
     char *base = static_cast<char *>(scan_scratch);
     e = cudaMemsetAsync(base, 0, L.zero, s);
     if (e != cudaSuccess || g.n == 0) return e;
@@ -1213,6 +1445,11 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     A.lvals = reinterpret_cast<uint32_t *>(base + L.lvals);
     A.dsc = gs_sort_carve_digits(base + L.dsort, g.n, 0, kDepthPasses, kDepthItems);
     A.counts = counts;
+    A.xy_keys = xy_keys;
+    A.tsc = sc;
+    A.tile_passes = sc.passes > 0 ? sc.passes : 1;
+    A.key_capacity = capacity;
+    A.d_err = d_err;
     A.prect = prect;
     A.prev_rect = prect ? prev_rect : nullptr;
     A.moved = moved;
@@ -1235,7 +1472,7 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     E.values = values;
     E.capacity = capacity;
     E.sc = sc;
-    return launch_list_stages(L, base, g.n, blocks, A.dsc, E, key_bytes, false, counts, d_err, s, marks);
+    return launch_list_stages(L, base, g.n, blocks, A.dsc, E, key_bytes, false, xy_keys, counts, d_err, s, marks);
 }
 
 cudaError_t gs_launch_project_temporal(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
@@ -1611,7 +1848,7 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
 }
 
 size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity, int64_t n, int n_views) {
-    return front_layout(rec_capacity, key_capacity, (n + kProjBlock - 1) / kProjBlock * n_views).total;
+    return front_layout(rec_capacity, key_capacity, (n + kProjBlock - 1) / kProjBlock * n_views, false).total;
 }
 
 cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
@@ -1622,7 +1859,7 @@ cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *v
     cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int64_t nb = (g.n + kProjBlock - 1) / kProjBlock, n_seg = nb * n_views;
-    const FrontLayout L = front_layout(rec_capacity, key_capacity, n_seg);
+    const FrontLayout L = front_layout(rec_capacity, key_capacity, n_seg, false);
     char *base = static_cast<char *>(scratch);
     e = cudaMemsetAsync(base, 0, L.zero, s);
     if (e != cudaSuccess || g.n == 0 || n_views == 0) return e;
@@ -1662,5 +1899,5 @@ cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *v
     E.values = values;
     E.capacity = key_capacity;
     E.sc = sc;
-    return launch_list_stages(L, base, rec_capacity, n_seg, A.dsc, E, 4, true, counts, d_err, s, nullptr);
+    return launch_list_stages(L, base, rec_capacity, n_seg, A.dsc, E, 4, true, false, counts, d_err, s, nullptr);
 }

@@ -14,6 +14,7 @@
 // or 16/32-bit tile ids (a frame's tile sort, whose keys arrive in depth
 // order: the sort moves 6 or 8 bytes per pair and pass instead of 12).
 #include "gs_internal.cuh"
+#include "gs_onesweep.cuh"
 
 #ifndef GS_SORT_MIN_BLOCKS
 #define GS_SORT_MIN_BLOCKS 2
@@ -32,7 +33,6 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kItems = GS_SORT_ITEMS;     // items per thread of the default variant
 constexpr int kLargeItems = 12;           // ... of the variant for long lists
 constexpr int64_t kLargeSortPairs = int64_t(1) << 23;  // capacities from here on use it
-constexpr int kLookAhead = GS_SORT_LOOKAHEAD;  // status words read per look-back step
 constexpr int kRadix = 256;
 constexpr int kMaxPasses = 8;
 
@@ -99,160 +99,36 @@ onesweep_kernel(const KT *__restrict__ keys_in, const uint32_t *__restrict__ val
                 uint32_t *d_err, unsigned long long timeout_ns, bool ballot_rank) {
     constexpr int kItems = ITEMS, kTile = kThreads * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
-    KT *s_keys = reinterpret_cast<KT *>(smem);                                  // kTile
-    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kTile);            // kTile
-    uint32_t *s_whist = s_vals + kTile;                                         // kWarps x 256
-    uint32_t *s_doff = s_whist + kWarps * kRadix;                               // 256
-    uint32_t *s_gbase = s_doff + kRadix;                                        // 256
-    uint32_t *s_tmp = s_gbase + kRadix;                                         // kWarps
-    uint32_t *s_part = s_tmp + kWarps;                                          // 1
-
+    __shared__ uint32_t s_part;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int shift = 8 * (pass + sc.digit0);
-    if (tid == 0) *s_part = atomicAdd(sc.counter + pass, 1u);
+    if (tid == 0) s_part = atomicAdd(sc.counter + pass, 1u);
     __syncthreads();
-    const int64_t p = *s_part;
+    const int64_t p = s_part;
     const int64_t base = p * kTile;
     // With a device-side count the grid covers the capacity; partitions past
     // the count have nothing to do (no later partition waits on them).
     const int64_t n = d_n ? (int64_t)*d_n : n_host;
     if (base >= n) return;
-    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
-    __syncthreads();
 
     // Warp-striped load: warp w holds pairs [w*32*kItems, (w+1)*32*kItems) of
     // the partition, item j of lane l at offset j*32 + l (coalesced).
     KT key[kItems];
     uint32_t val[kItems];
-    uint32_t rank[kItems];
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
         key[j] = idx < n ? keys_in[idx] : (KT)~(KT)0;
         val[j] = idx < n ? vals_in[idx] : 0u;
     }
-    // Stable rank within the warp, in (item, lane) order. Out-of-range items
-    // get digit 256, which matches nothing real and is never counted.
-    uint32_t *my_hist = s_whist + warp * kRadix;
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
-        const uint32_t d = idx < n ? (uint32_t)((key[j] >> shift) & 255) : 256u;
-        // Lanes with equal digits: warp match (fast when a warp holds few
-        // distinct digits), or 9 ballots, one per bit of 0..256 (constant
-        // cost, faster when digits are diverse).
-        uint32_t peers;
-        if (ballot_rank) {
-            peers = 0xffffffffu;
-#pragma unroll
-            for (int b = 0; b < 9; ++b) {
-                const bool bit = (d >> b) & 1u;
-                const uint32_t m = __ballot_sync(0xffffffffu, bit);
-                peers &= bit ? m : ~m;
-            }
-        } else {
-            peers = __match_any_sync(0xffffffffu, d);
-        }
-        const uint32_t lt = peers & lanemask_lt();
-        const uint32_t before = d < 256u ? my_hist[d] : 0u;
-        __syncwarp();
-        rank[j] = before + __popc(lt);
-        if (d < 256u && lt == 0u) my_hist[d] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-
-    // Thread tid owns digit tid: prefix over warps, block total for the digit.
-    const uint32_t digit = tid;
-    uint32_t total = 0;
-    for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_whist[w * kRadix + digit];
-        s_whist[w * kRadix + digit] = total;
-        total += c;
-    }
-    unsigned long long *st = sc.status + ((int64_t)pass * parts + p) * kRadix + digit;
-    if (p == 0) {
-        st_relaxed_u64(st, kFlagIncl | total);
-    } else {
-        st_relaxed_u64(st, kFlagAgg | total);
-    }
-    const uint32_t doff = block_exclusive_scan_256(total, s_tmp);
-    s_doff[digit] = doff;
-
-    // Decoupled look-back for this digit over partitions p-1, p-2, ...,
-    // reading kLookAhead status words per step so a chain of aggregates costs
-    // one memory latency per kLookAhead partitions.
-    unsigned long long excl = 0;
-    if (p > 0) {
-        unsigned long long t0 = 0;  // read at the first unpublished status word
-        int64_t q = p - 1;
-        uint32_t polls = 0;
-        bool found = false;
-        while (q >= 0 && !found) {
-            unsigned long long sw[kLookAhead];
-#pragma unroll
-            for (int k = 0; k < kLookAhead; ++k)
-                sw[k] = (q - k >= 0) ? ld_relaxed_u64(st - (p - (q - k)) * kRadix) : 0ull;
-            int consumed = 0;
-#pragma unroll
-            for (int k = 0; k < kLookAhead; ++k) {
-                if (q - k < 0 || consumed != k) break;
-                const unsigned long long f = sw[k] >> 62;
-                if (f == 0) break;
-                excl += sw[k] & kValueMask;
-                ++consumed;
-                if (f == 2) {
-                    found = true;
-                    break;
-                }
-            }
-            q -= consumed;
-            if (!found && consumed == 0) {
-                if (polls == 0) t0 = global_ns();
-                if ((++polls & 63u) == 0u &&
-                    ((global_ns() - t0 > timeout_ns) || (ld_relaxed_u32(d_err) & kErrTimeout))) {
-                    atomicOr(d_err, kErrTimeout);
-                    __threadfence();
-                    break;
-                }
-            }
-        }
-        st_relaxed_u64(st, kFlagIncl | ((excl + total) & kValueMask));
-    }
-    s_gbase[digit] = sc.bucket[pass * kRadix + digit] + (uint32_t)excl;
-    __syncthreads();
-
-    // Reorder by digit in shared memory.
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
-        if (idx < n) {
-            const uint32_t d = (uint32_t)((key[j] >> shift) & 255);
-            const uint32_t pos = s_doff[d] + my_hist[d] + rank[j];
-            s_keys[pos] = key[j];
-            s_vals[pos] = val[j];
-        }
-    }
-    __syncthreads();
-    const int valid = (int)((n - base) < kTile ? (n - base) : kTile);
-    for (int i = tid; i < valid; i += kThreads) {
-        const KT k = s_keys[i];
-        const uint32_t d = (uint32_t)((k >> shift) & 255);
-        const uint64_t gp = (uint64_t)s_gbase[d] + (uint32_t)(i - s_doff[d]);
-        // Only reachable after a timed-out look-back left offsets meaningless.
-        if (gp >= (uint64_t)n) {
-            atomicOr(d_err, kErrRange);
-            continue;
-        }
-        keys_out[gp] = k;
-        vals_out[gp] = s_vals[i];
-    }
+    onesweep_partition<KT, kItems>(key, val, base, n, p, shift, sc.status + (int64_t)pass * parts * kRadix,
+                                   sc.bucket + pass * kRadix, keys_out, vals_out, d_err, timeout_ns, ballot_rank,
+                                   smem);
 }
 
 template <typename KT, int ITEMS>
 constexpr size_t onesweep_smem() {
-    return (size_t)kThreads * ITEMS * (sizeof(KT) + 4) + (size_t)kWarps * kRadix * 4 + 2 * kRadix * 4 +
-           kWarps * 4 + 16;
+    return onesweep_partition_smem<KT, ITEMS>();
 }
 
 template <typename KT, int ITEMS, int MIN_BLOCKS>
@@ -266,7 +142,8 @@ cudaError_t prepare_shape() {
 template <typename KT>
 cudaError_t launch_passes(KT *keys, uint32_t *values, KT *alt_keys, uint32_t *alt_values, int64_t n_capacity,
                           const unsigned long long *d_n, const GsSortScratch &sc, uint32_t *d_err,
-                          bool *result_in_alt, cudaStream_t s, unsigned long long timeout_ns, int max_passes) {
+                          bool *result_in_alt, cudaStream_t s, unsigned long long timeout_ns, int max_passes,
+                          int first_pass) {
     *result_in_alt = false;
     // Three partition shapes: 8 items per thread for short lists (shorter
     // per-partition latency), GS_SORT_ITEMS (16) by default, 12 items with
@@ -284,10 +161,10 @@ cudaError_t launch_passes(KT *keys, uint32_t *values, KT *alt_keys, uint32_t *al
     KT *kout = alt_keys;
     uint32_t *vout = alt_values;
     const int passes = sc.passes < max_passes ? sc.passes : max_passes;
-    for (int pass = 0; pass < passes; ++pass) {
+    for (int pass = first_pass; pass < passes; ++pass) {
         // Lower digits of depth bits and tile ids are diverse within a warp;
         // the top digit (exponent byte, high tile bits) takes few values.
-        const bool ballot = pass + 1 < sc.passes;
+        const bool ballot = pass + 1 < sc.passes || sc.diverse_last;
         if (shape == 0)
             onesweep_kernel<KT, 8, GS_SORT_MIN_BLOCKS><<<(unsigned)sc.parts, kThreads, smem, s>>>(
                 kin, vin, kout, vout, n_capacity, d_n, pass, sc.parts, sc, d_err, timeout_ns, ballot);
@@ -304,7 +181,7 @@ cudaError_t launch_passes(KT *keys, uint32_t *values, KT *alt_keys, uint32_t *al
         kout = (kout == alt_keys) ? keys : alt_keys;
         vout = (vout == alt_values) ? values : alt_values;
     }
-    *result_in_alt = (passes & 1) != 0;
+    *result_in_alt = passes > first_pass && ((passes - first_pass) & 1) != 0;
     return cudaSuccess;
 }
 
@@ -341,6 +218,7 @@ GsSortScratch gs_sort_carve_digits(void *base, int64_t n_capacity, int digit0, i
     s.parts = num_parts(n_capacity, items) > 0 ? num_parts(n_capacity, items) : 1;
     s.digit0 = digit0;
     s.items = items;
+    s.diverse_last = false;
     return s;
 }
 
@@ -348,27 +226,27 @@ cudaError_t gs_launch_sort_passes(uint64_t *keys, uint32_t *values, uint64_t *al
                                   uint32_t *alt_values, int64_t n_capacity,
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
-                                  unsigned long long timeout_ns, int max_passes) {
+                                  unsigned long long timeout_ns, int max_passes, int first_pass) {
     return launch_passes<uint64_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, d_err, result_in_alt, s,
-                                   timeout_ns, max_passes);
+                                   timeout_ns, max_passes, first_pass);
 }
 
 cudaError_t gs_launch_sort_passes(uint32_t *keys, uint32_t *values, uint32_t *alt_keys,
                                   uint32_t *alt_values, int64_t n_capacity,
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
-                                  unsigned long long timeout_ns, int max_passes) {
+                                  unsigned long long timeout_ns, int max_passes, int first_pass) {
     return launch_passes<uint32_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, d_err, result_in_alt, s,
-                                   timeout_ns, max_passes);
+                                   timeout_ns, max_passes, first_pass);
 }
 
 cudaError_t gs_launch_sort_passes(uint16_t *keys, uint32_t *values, uint16_t *alt_keys,
                                   uint32_t *alt_values, int64_t n_capacity,
                                   const unsigned long long *d_n, const GsSortScratch &sc,
                                   uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
-                                  unsigned long long timeout_ns, int max_passes) {
+                                  unsigned long long timeout_ns, int max_passes, int first_pass) {
     return launch_passes<uint16_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, d_err, result_in_alt, s,
-                                   timeout_ns, max_passes);
+                                   timeout_ns, max_passes, first_pass);
 }
 
 cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,

@@ -467,6 +467,31 @@ def test_render_depth_ties_short_and_long_lists(ctx, oracle_mod, n):
     assert np.array_equal(out["n_contrib"].cpu().numpy()[keep], img.last[keep])
 
 
+@pytest.mark.parametrize("shape", ["wide", "tall"])
+def test_render_extreme_aspect_grids(ctx, oracle_mod, shape):
+    """Grids wider than 256 tiles use tile-id keys with histograms counted
+    by the emission; grids taller than 256 tiles use (row << 8 | column) keys
+    of 17 bits (32-bit keys, a third tile pass over the row's high byte).
+    Both must match the oracle."""
+    s = scenes.uniform_box(40_000, 31)
+    if shape == "wide":
+        cam = scenes.pinhole(4200, 48, 90.0)        # 263 x 3 tiles
+        s.means[:, 1] *= 0.01
+    else:
+        cam = scenes.pinhole(48, 4200, 1.0)         # 3 x 263 tiles
+        s.means[:, 0] *= 0.004
+    s.log_scales[:] = s.log_scales - 1.0
+    out = gs.render(ctx, gs.scene_to_device(s), 0, cam)
+    torch.cuda.synchronize()
+    assert gs.gs_last_render_stats(ctx)["n_visible"] > 500
+    _, _, img = oracle_mod.render(s, cam)
+    st = compare_image(out["rgb"].cpu().numpy(), out["final_T"].cpu().numpy(), img)
+    st.pop("keep")
+    assert st["max_rgb_err"] <= RGB_TOL, st
+    keep = ~img.flag.astype(bool)
+    assert np.array_equal(out["n_contrib"].cpu().numpy()[keep], img.last[keep])
+
+
 @pytest.mark.parametrize("case", ["clustered_rotated", "large_anisotropic", "skewed_camera"])
 def test_frame_visible_set_equals_full_projection(ctx, case):
     """A frame skips the full projection of Gaussians that a screen bound
