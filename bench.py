@@ -777,10 +777,15 @@ def main():
         "clocks_single_stream": clk,
     }
     # Kernel launches per gs_render: projection + compact list, the list
-    # gather, four depth digit passes, the entry scan, key emission, one pass
-    # per tile digit, ranges, blend.
-    tile_passes = (stats["key_bits"] - 32 + 7) // 8
-    per_step = 10 + tile_passes
+    # gather, four depth digit passes, the entry scan, key emission fused with
+    # the first tile pass (grids at most 256 tiles wide), the other tile
+    # passes, ranges, blend.
+    tiles_x = (W + 15) // 16
+    row_bits = int(np.ceil(np.log2(max(1, (H + 15) // 16))))
+    if tiles_x <= 256:
+        per_step = 9 + (8 + row_bits + 7) // 8
+    else:
+        per_step = 10 + (stats["key_bits"] - 32 + 7) // 8
     line["gpu_launches"] = per_step * args.steps
     if not args.no_fwd_bwd:
         line["fwd_bwd"] = fwd_bwd(gs, torch, args, flush, local)
