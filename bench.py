@@ -531,10 +531,13 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-temporal", action="store_true")
     ap.add_argument("--no-imbalance", action="store_true")
-    ap.add_argument("--frames-in-flight", type=int, default=4,
+    ap.add_argument("--frames-in-flight", type=int, default=8,
                     help="consecutive frames rendered on this many contexts / streams at once (headline value)")
+    ap.add_argument("--pipeline-blend-variant", type=int, default=4,
+                    help="blend schedule of the frames-in-flight loop (4: 8x8 blocks, fewest instructions)")
     ap.add_argument("--blend-variant", type=int, default=0,
-                    help="0 culled 8x4 blocks (default), 1 basic, 2 culled 16x8, 3 culled tile, 4 culled 8x8")
+                    help="0 culled 8x4 blocks (default), 1 basic, 2 culled 16x8, 3 culled tile, 4 culled 8x8, "
+                         "5 TMA staging")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -620,7 +623,7 @@ def main():
     prgb = [rgb] + [torch.empty_like(rgb) for _ in range(F - 1)]
     for k in range(F):
         for _ in range(args.warmup):
-            gs.gs_render(pctx[k], g, scene.sh_degree, cam, prgb[k], variant=args.blend_variant)
+            gs.gs_render(pctx[k], g, scene.sh_degree, cam, prgb[k], variant=args.pipeline_blend_variant)
     torch.cuda.synchronize()
     barrier(world)
     clocks2 = ClockSampler(local)
@@ -634,7 +637,7 @@ def main():
         k = i % F
         with torch.cuda.stream(pstreams[k]):
             gs.gs_render(pctx[k], copies[i % len(copies)], scene.sh_degree, cam, prgb[k],
-                         variant=args.blend_variant, deferred=True, stream=pstreams[k])
+                         variant=args.pipeline_blend_variant, deferred=True, stream=pstreams[k])
     for ps in pstreams:
         stream.wait_stream(ps)
     p1.record(stream)
@@ -759,6 +762,7 @@ def main():
                    "key_bits": stats["key_bits"], "blend_variant": args.blend_variant,
                    "sync_mode": "deferred (GS_SYNC_DEFERRED)",
                    "frames_in_flight": F,
+                   "frames_in_flight_blend_variant": args.pipeline_blend_variant,
                    "inputs": "8 rotating copies of the scene (8 x 236 MB, above L2) in the frames-in-flight loop",
                    "single_stream_frame_ms": round(single_ms, 4),
                    "single_stream_frames_per_s": round(1000.0 / single_ms, 3),

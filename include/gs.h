@@ -118,7 +118,11 @@ typedef struct {
  *                         tiles use 8x4 blocks)
  *   GS_BLEND_CULLED_TILE  as CULLED with one warp per 16x16 tile (other
  *                         tiles use 8x4 blocks)
- *   GS_BLEND_CULLED_8X8   as CULLED with 8x8 blocks
+ *   GS_BLEND_CULLED_8X8   as CULLED with 8x8 blocks (two pixels per lane):
+ *                         fewer instructions per frame than CULLED but a
+ *                         longer critical path per tile — slower for one
+ *                         frame alone, faster when several frames are in
+ *                         flight on other streams
  *   GS_BLEND_TMA          gs_render only (gs_blend falls back to CULLED): the
  *                         records of the sorted lists are first gathered in
  *                         list order, then each tile's batches are staged in
