@@ -92,3 +92,41 @@ def test_backward_after_overflowed_deferred_forward_fails(built):
     got = _grads(ctx, scene, cam, target, deferred=True)  # buffers have grown
     for a, b in zip(ref, got):  # float atomics: equal up to summation order
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * float(a.abs().max()) + 1e-12)
+
+
+def test_frames_in_flight_on_several_contexts_and_streams(built):
+    """Consecutive frames on four contexts, each on its own stream, deferred
+    (how a renderer keeps several frames in flight): every frame equals the
+    same camera rendered alone and synchronously, for both blend schedules."""
+    scene = scenes.clustered(200_000, 41)
+    g = gs.scene_to_device(scene)
+    rng = np.random.default_rng(41)
+    cams = [scenes.pinhole(640, 360, 60.0, world_to_cam=scenes.look_at(rng.uniform(-1, 1, 3),
+                                                                        [0.0, 0.0, 1.0] + rng.normal(0, 0.2, 3)))
+            for _ in range(8)]
+    ref_ctx = gs.Context(0)
+    for variant in (0, 4):
+        refs = [gs.render(ref_ctx, g, scene.sh_degree, c, variant=variant) for c in cams]
+        torch.cuda.synchronize()
+        ctxs = [gs.Context(0) for _ in range(4)]
+        streams = [torch.cuda.Stream() for _ in range(4)]
+        outs = [{"rgb": torch.empty((c.height, c.width, 3), device="cuda"),
+                 "final_T": torch.empty((c.height, c.width), device="cuda"),
+                 "n_contrib": torch.empty((c.height, c.width), dtype=torch.int32, device="cuda")} for c in cams]
+        start = torch.cuda.Event()
+        start.record()
+        for s in streams:
+            s.wait_event(start)
+        for i, (c, o) in enumerate(zip(cams, outs)):
+            k = i % 4
+            with torch.cuda.stream(streams[k]):
+                gs.gs_render(ctxs[k], g, scene.sh_degree, c, o["rgb"], o["final_T"], o["n_contrib"],
+                             variant=variant, deferred=True, stream=streams[k])
+        torch.cuda.synchronize()
+        for c in ctxs:
+            gs.gs_sync_status(c)
+            c.close()
+        for r, o in zip(refs, outs):
+            for key in ("rgb", "final_T", "n_contrib"):
+                assert torch.equal(r[key], o[key]), key
+    ref_ctx.close()
