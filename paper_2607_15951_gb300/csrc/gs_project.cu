@@ -277,7 +277,6 @@ __global__ void __launch_bounds__(256) project_kernel(const ProjectArgs P) {
 // on the tile id then leaves every tile's list exactly in (depth bits, index)
 // order, with no tie fix-up.
 // ---------------------------------------------------------------------------
-constexpr int kMaxPasses = 8;                  // batched path: depth and tile digits
 constexpr int kMaxTilePasses = 4;
 constexpr unsigned long long kKeyMask = (1ull << 33) - 1;
 constexpr int kKeyBlock = 1 << kKeyBlockLog2;
@@ -1101,7 +1100,7 @@ __global__ void __launch_bounds__(256, 2) emit_sort_kernel(const EmitSortArgs A)
 
 // ---------------------------------------------------------------------------
 // Batched front end (many views of one scene), depth first as a single view:
-// block (b, v) projects Gaussians [256 b, 256 b + 256) for view v and
+// block (b, v) projects Gaussians [1024 b, 1024 b + 1024) for view v and
 // reserves compact record slots with the packed counter; slot j gets the
 // record, meta[j] = (view, Gaussian index) and list entry j (tiles << 32 |
 // depth bits, j). The list segments, placed in (view, block) order, give the
@@ -1111,6 +1110,7 @@ __global__ void __launch_bounds__(256, 2) emit_sort_kernel(const EmitSortArgs A)
 // ---------------------------------------------------------------------------
 struct ListBatchArgs {
     ProjectArgs P;               // scene arrays (cam / grid unused; records compact)
+    bool views_fast;             // grid (views, ranges) rather than (ranges, views)
     const ViewDesc *views;
     float4 *lp_geo;
     uint2 *lp_oq;
@@ -1149,10 +1149,15 @@ __global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBa
     extern __shared__ __align__(16) unsigned char s_dyn[];
     BatchStage &S = *reinterpret_cast<BatchStage *>(s_dyn);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int view = blockIdx.y;
+    // With views_fast the views of one Gaussian range are neighbouring blocks,
+    // so they read that range's parameters from L2 rather than each from DRAM
+    // (grid.y holds the ranges, at most 65,535 of them).
+    const int view = A.views_fast ? blockIdx.x : blockIdx.y;
+    const int64_t rb = A.views_fast ? blockIdx.y : blockIdx.x;
+    const int64_t nb = A.views_fast ? gridDim.y : gridDim.x;
     const ViewDesc &V = A.views[view];
     for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
-    const int64_t i0 = (int64_t)blockIdx.x * kProjBlock;
+    const int64_t i0 = rb * kProjBlock;
     // Screen test, candidates in index order (as the single-view kernel).
     bool cand[kProjPer];
     uint32_t cm[kProjPer];
@@ -1209,7 +1214,7 @@ __global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBa
     if (tid == 255) {
         const uint32_t bv = vpre + vsum, bt = tpre + tsum;
         s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) >> 33 : 0ull;
-        A.seg[(int64_t)view * gridDim.x + blockIdx.x] = make_uint2((uint32_t)s_base, bv);
+        A.seg[(int64_t)view * nb + rb] = make_uint2((uint32_t)s_base, bv);
         s_cnt[0] = bv;
     }
     __syncthreads();
@@ -1883,7 +1888,8 @@ cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *v
     A.dsc = gs_sort_carve_digits(base + L.dsort, rec_capacity, 0, kDepthPasses, kDepthItems);
     A.counts = counts;
     A.d_err = d_err;
-    const dim3 grid((unsigned)nb, (unsigned)n_views);
+    A.views_fast = nb <= 65535;
+    const dim3 grid = A.views_fast ? dim3((unsigned)n_views, (unsigned)nb) : dim3((unsigned)nb, (unsigned)n_views);
     switch (g.sh_degree) {
         case 0: e = launch_project_list_batch<0>(A, grid, s); break;
         case 1: e = launch_project_list_batch<1>(A, grid, s); break;
