@@ -999,7 +999,7 @@ constexpr int emit_sort_smem() {
 }
 
 template <typename KT>
-__global__ void __launch_bounds__(256, 2) emit_sort_kernel(const EmitSortArgs A) {
+__global__ void __launch_bounds__(256, 3) emit_sort_kernel(const EmitSortArgs A) {
     const EmitArgs &E = A.E;
     __shared__ __align__(16) unsigned char s_raw[emit_sort_smem<KT>()];
     __shared__ int s_j0, s_cnt;
