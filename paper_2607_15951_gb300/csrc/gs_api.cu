@@ -209,6 +209,11 @@ GsCameraDev make_cam(const gs_camera *c) {
     k.near_z = c->near_z;
     k.lim_x = gs::kGuard * (0.5f * c->width / c->fx);
     k.lim_y = gs::kGuard * (0.5f * c->height / c->fy);
+    for (int r = 0; r < 3; ++r) {
+        const double nr = std::sqrt((double)k.R[3 * r] * k.R[3 * r] + (double)k.R[3 * r + 1] * k.R[3 * r + 1] +
+                                    (double)k.R[3 * r + 2] * k.R[3 * r + 2]);
+        k.rn[r] = (float)(nr * (1.0 + 1e-6));
+    }
     k.width = c->width;
     k.height = c->height;
     return k;

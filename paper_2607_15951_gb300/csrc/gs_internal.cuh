@@ -231,6 +231,7 @@ struct GsCameraDev {
     float C[3];  // camera centre -R^T t
     float fx, fy, cx, cy, near_z;
     float lim_x, lim_y;  // 1.3 tan(half fov) per axis
+    float rn[3];         // row norms of R, rounded up (the conservative screen bound)
     int width, height;
 };
 

@@ -210,7 +210,9 @@ __device__ __forceinline__ Projected project_one(const ProjectArgs &P, const GsC
 // s_max^2 (|T0|^2 + |T1|^2) =: B (R(q) is a rotation). lambda_max as the
 // projection computes it is at most the trace + sqrt(0.1) = a0 + c0 + 0.6 +
 // 0.317, so the pixel radius is at most 3 sqrt(B + 0.92); 1 % of B and 2
-// pixels of slack cover FP32 rounding. A non-finite bound keeps the
+// pixels of slack cover FP32 rounding and the approximate reciprocal,
+// exponential and square root used here (relative errors below 1e-6). The
+// row norms come precomputed with the camera. A non-finite bound keeps the
 // Gaussian (every comparison with NaN is false).
 __device__ __forceinline__ bool maybe_visible(const ProjectArgs &P, const GsCameraDev &K, const GsGrid &G,
                                               int64_t i) {
@@ -221,15 +223,16 @@ __device__ __forceinline__ bool maybe_visible(const ProjectArgs &P, const GsCame
     if (!(tz > K.near_z)) return false;
     const float tx = fmaf(K.R[0], mx, fmaf(K.R[1], my, fmaf(K.R[2], mz, K.t[0])));
     const float ty = fmaf(K.R[3], mx, fmaf(K.R[4], my, fmaf(K.R[5], mz, K.t[1])));
-    const float iz = 1.f / tz;
+    const float iz = __fdividef(1.f, tz);
     const float rx = fminf(K.lim_x, fmaxf(-K.lim_x, tx * iz));
     const float ry = fminf(K.lim_y, fmaxf(-K.lim_y, ty * iz));
-    const float n0 = sqrtf(fmaf(K.R[0], K.R[0], fmaf(K.R[1], K.R[1], K.R[2] * K.R[2])));
-    const float n1 = sqrtf(fmaf(K.R[3], K.R[3], fmaf(K.R[4], K.R[4], K.R[5] * K.R[5])));
-    const float n2 = sqrtf(fmaf(K.R[6], K.R[6], fmaf(K.R[7], K.R[7], K.R[8] * K.R[8])));
-    const float t0 = K.fx * iz * fmaf(fabsf(rx), n2, n0), t1 = K.fy * iz * fmaf(fabsf(ry), n2, n1);
-    const float B = expf(2.f * ls) * fmaf(t0, t0, t1 * t1);
-    const float rb = 3.f * sqrtf(fmaf(B, 1.01f, 0.92f)) + 2.f;
+    const float t0 = K.fx * iz * fmaf(fabsf(rx), K.rn[2], K.rn[0]), t1 = K.fy * iz * fmaf(fabsf(ry), K.rn[2], K.rn[1]);
+    float s2;  // s_max^2 = 2^(2 ls log2 e)
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(s2) : "f"(2.f * 1.4426950408889634f * ls));
+    const float B = s2 * fmaf(t0, t0, t1 * t1);
+    float sq;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(fmaf(B, 1.01f, 0.92f)));
+    const float rb = fmaf(3.f, sq, 2.f);
     const float u = fmaf(K.fx * tx, iz, K.cx), v = fmaf(K.fy * ty, iz, K.cy);
     return !(u + rb < 0.f || u - rb > (float)(G.tiles_x * G.tile_w) || v + rb < 0.f ||
              v - rb > (float)(G.tiles_y * G.tile_h));
