@@ -732,7 +732,12 @@ def main():
                 "traffic_source": traffic_src,
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_clock:.0f} MHz",
                 "units_per_launch": n_eval_total, "flops_per_unit": FLOPS_PER_EVAL,
-                "launch_ms": round(blend_ms, 4)}
+                "launch_ms": round(blend_ms, 4),
+                "note": "blend kernel alone, one frame at a time (default 8x4 blocks); with frames in "
+                        "flight the blend work of a frame per frame interval is in frames_in_flight_effective",
+                "frames_in_flight_effective": {
+                    "TFLOP/s": round(flops * value / world / 1e12, 3),
+                    "frac": round(flops * value / world / 1e12 / fp32_peak_tflops, 4)}}
 
     # HBM view of the same frame: bytes each stage must move / its live time.
     tile_passes = (stats["key_bits"] - 32 + 7) // 8
