@@ -1103,7 +1103,7 @@ __global__ void __launch_bounds__(256, 3) emit_sort_kernel(const EmitSortArgs A)
 
 // ---------------------------------------------------------------------------
 // Batched front end (many views of one scene), depth first as a single view:
-// block (b, v) projects Gaussians [1024 b, 1024 b + 1024) for view v and
+// block (b, v) projects Gaussians [2048 b, 2048 b + 2048) for view v and
 // reserves compact record slots with the packed counter; slot j gets the
 // record, meta[j] = (view, Gaussian index) and list entry j (tiles << 32 |
 // depth bits, j). The list segments, placed in (view, block) order, give the
@@ -1134,9 +1134,18 @@ struct ListBatchArgs {
 // Candidates of a batched block (kProjBlock Gaussians of one view) staged by
 // rank: the records go to compact slots, known only after the block's
 // reservation.
+// A batched block takes kBatchBlock Gaussians of one view (kBatchPer per
+// thread); its candidates are projected, reserved and written in rounds of
+// up to kProjBlock (the stage's size), each round one list segment. The
+// stage holds a round's candidates until their compact slots are known.
+constexpr int kBatchPer = 8;
+constexpr int kBatchBlock = 256 * kBatchPer;          // 2048
+constexpr int kBatchRounds = kBatchBlock / kProjBlock;  // list segments per block
+
 struct BatchStage {
     float4 r0[kProjBlock];
-    uint32_t cand[kProjBlock], tiles[kProjBlock];
+    uint32_t cand[kBatchBlock];  // every candidate of the block, in index order
+    uint32_t tiles[kProjBlock];
     uint32_t dbits[kProjBlock];  // depth bits, then the record slot
     float qa[kProjBlock], op[kProjBlock], tz[kProjBlock], rad[kProjBlock];
     float dx[kProjBlock], dy[kProjBlock], dz[kProjBlock];
@@ -1144,7 +1153,8 @@ struct BatchStage {
 
 template <int DEG>
 __global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBatchArgs A) {
-    __shared__ uint32_t s_cnt[kProjPer * 8];
+    __shared__ uint32_t s_cnt[kBatchPer * 8];
+    __shared__ uint32_t s_nc;
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_hist[kDepthPasses * 256];
     __shared__ uint32_t s_tmp[8];
@@ -1160,93 +1170,118 @@ __global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBa
     const int64_t nb = A.views_fast ? gridDim.y : gridDim.x;
     const ViewDesc &V = A.views[view];
     for (int k = tid; k < kDepthPasses * 256; k += 256) s_hist[k] = 0;
-    const int64_t i0 = rb * kProjBlock;
-    // Screen test, candidates in index order (as the single-view kernel).
-    bool cand[kProjPer];
-    uint32_t cm[kProjPer];
+    const int64_t i0 = rb * kBatchBlock;
+    // Screen test, candidates in index order ((q, warp, lane) order).
+    bool cand[kBatchPer];
+    uint32_t cm[kBatchPer];
 #pragma unroll
-    for (int q = 0; q < kProjPer; ++q) {
+    for (int q = 0; q < kBatchPer; ++q) {
         const int64_t i = i0 + q * 256 + tid;
         cand[q] = i < A.P.n && maybe_visible(A.P, V.cam, V.grid, i);
         cm[q] = __ballot_sync(0xffffffffu, cand[q]);
         if (lane == 0) s_cnt[q * 8 + warp] = __popc(cm[q]);
     }
     __syncthreads();
-    uint32_t nc = 0;
-    uint32_t pre[kProjPer];
-#pragma unroll
-    for (int q = 0; q < kProjPer; ++q) pre[q] = 0;
-    for (int k = 0; k < kProjPer * 8; ++k) {
-        const uint32_t x = s_cnt[k];
-#pragma unroll
-        for (int q = 0; q < kProjPer; ++q)
-            if (k < q * 8 + warp) pre[q] += x;
-        nc += x;
+    {
+        const uint32_t c = tid < kBatchPer * 8 ? s_cnt[tid] : 0u;
+        const uint32_t ex = block_exclusive_scan_256(c, s_tmp);
+        if (tid < kBatchPer * 8) s_cnt[tid] = ex;
+        if (tid == kBatchPer * 8 - 1) s_nc = ex + c;
     }
-#pragma unroll
-    for (int q = 0; q < kProjPer; ++q)
-        if (cand[q]) S.cand[pre[q] + __popc(cm[q] & lanemask_lt())] = (uint32_t)(q * 256 + tid);
     __syncthreads();
-    for (uint32_t c = tid; c < nc; c += 256) {
-        const Projected pr = project_one<DEG, false>(A.P, V.cam, V.grid, i0 + S.cand[c]);
-        S.tiles[c] = pr.tiles;
-        if (pr.tiles) {
-            S.r0[c] = pr.r0;
-            S.dbits[c] = __float_as_uint(pr.r2.y);
-            S.qa[c] = pr.r1.x;
-            S.op[c] = pr.r1.y;
-            S.tz[c] = pr.r2.y;
-            S.rad[c] = pr.r2.z;
-            S.dx[c] = pr.dir.x;
-            S.dy[c] = pr.dir.y;
-            S.dz[c] = pr.dir.z;
+    const uint32_t nc = s_nc;
+#pragma unroll
+    for (int q = 0; q < kBatchPer; ++q)
+        if (cand[q]) S.cand[s_cnt[q * 8 + warp] + __popc(cm[q] & lanemask_lt())] = (uint32_t)(q * 256 + tid);
+    __syncthreads();
+    uint32_t bv_all = 0;
+    for (int r = 0; r < kBatchRounds; ++r) {
+        const uint32_t c0 = (uint32_t)r * kProjBlock;
+        const uint32_t cn = nc > c0 ? min(nc - c0, (uint32_t)kProjBlock) : 0u;
+        if (cn == 0) {  // block-uniform
+            if (tid == 0) A.seg[((int64_t)view * nb + rb) * kBatchRounds + r] = make_uint2(0u, 0u);
+            continue;
         }
-    }
-    __syncthreads();
-    // Compact slots: thread tid owns candidates [4 tid, 4 tid + 4).
-    uint32_t tsum = 0, vsum = 0;
-#pragma unroll
-    for (int q = 0; q < kProjPer; ++q) {
-        const uint32_t c = kProjPer * tid + q;
-        const uint32_t t = c < nc ? S.tiles[c] : 0u;
-        tsum += t;
-        vsum += t != 0u;
-    }
-    const uint32_t vpre = block_exclusive_scan_256(vsum, s_tmp);
-    const uint32_t tpre = block_exclusive_scan_256(tsum, s_tmp);
-    if (tid == 255) {
-        const uint32_t bv = vpre + vsum, bt = tpre + tsum;
-        s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) >> 33 : 0ull;
-        A.seg[(int64_t)view * nb + rb] = make_uint2((uint32_t)s_base, bv);
-        s_cnt[0] = bv;
-    }
-    __syncthreads();
-    const uint32_t bv = s_cnt[0];
-    uint64_t j = s_base + vpre;
-#pragma unroll
-    for (int q = 0; q < kProjPer; ++q) {
-        const uint32_t c = kProjPer * tid + q;
-        const uint32_t t = c < nc ? S.tiles[c] : 0u;
-        if (t) {
-            const uint32_t dbits = S.dbits[c];
-            const bool fits = (int64_t)j < A.rec_capacity;
-            if (fits) {
-                A.P.records[3 * j] = S.r0[c];
-                if (A.lp_geo) A.lp_geo[j] = S.r0[c];
-                A.meta[j] = make_uint2((uint32_t)view, (uint32_t)(i0 + S.cand[c]));
-                A.lkeys[j] = ((uint64_t)t << 32) | dbits;
-                A.lvals[j] = (uint32_t)j;
-                for (int d = 0; d < kDepthPasses; ++d)
-                    atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
-            } else {
-                atomicOr(A.d_err, kErrCapacity);
+        for (uint32_t c = tid; c < cn; c += 256) {
+            const Projected pr = project_one<DEG, false>(A.P, V.cam, V.grid, i0 + S.cand[c0 + c]);
+            S.tiles[c] = pr.tiles;
+            if (pr.tiles) {
+                S.r0[c] = pr.r0;
+                S.dbits[c] = __float_as_uint(pr.r2.y);
+                S.qa[c] = pr.r1.x;
+                S.op[c] = pr.r1.y;
+                S.tz[c] = pr.r2.y;
+                S.rad[c] = pr.r2.z;
+                S.dx[c] = pr.dir.x;
+                S.dy[c] = pr.dir.y;
+                S.dz[c] = pr.dir.z;
             }
-            S.dbits[c] = fits ? (uint32_t)j : 0xffffffffu;
-            ++j;
         }
+        __syncthreads();
+        // Compact slots: thread tid owns the round's candidates [4 tid, 4 tid + 4).
+        uint32_t tsum = 0, vsum = 0;
+#pragma unroll
+        for (int q = 0; q < kProjPer; ++q) {
+            const uint32_t c = kProjPer * tid + q;
+            const uint32_t t = c < cn ? S.tiles[c] : 0u;
+            tsum += t;
+            vsum += t != 0u;
+        }
+        const uint32_t vpre = block_exclusive_scan_256(vsum, s_tmp);
+        const uint32_t tpre = block_exclusive_scan_256(tsum, s_tmp);
+        if (tid == 255) {
+            const uint32_t bv = vpre + vsum, bt = tpre + tsum;
+            s_base = bv ? atomicAdd(A.packed, ((unsigned long long)bv << 33) | bt) >> 33 : 0ull;
+            A.seg[((int64_t)view * nb + rb) * kBatchRounds + r] = make_uint2((uint32_t)s_base, bv);
+            s_cnt[0] = bv;
+        }
+        __syncthreads();
+        bv_all += s_cnt[0];
+        uint64_t j = s_base + vpre;
+#pragma unroll
+        for (int q = 0; q < kProjPer; ++q) {
+            const uint32_t c = kProjPer * tid + q;
+            const uint32_t t = c < cn ? S.tiles[c] : 0u;
+            if (t) {
+                const uint32_t dbits = S.dbits[c];
+                const bool fits = (int64_t)j < A.rec_capacity;
+                if (fits) {
+                    A.P.records[3 * j] = S.r0[c];
+                    if (A.lp_geo) A.lp_geo[j] = S.r0[c];
+                    A.meta[j] = make_uint2((uint32_t)view, (uint32_t)(i0 + S.cand[c0 + c]));
+                    A.lkeys[j] = ((uint64_t)t << 32) | dbits;
+                    A.lvals[j] = (uint32_t)j;
+                    for (int d = 0; d < kDepthPasses; ++d)
+                        atomicAdd(&s_hist[d * 256 + ((dbits >> (8 * d)) & 255u)], 1u);
+                } else {
+                    atomicOr(A.d_err, kErrCapacity);
+                }
+                S.dbits[c] = fits ? (uint32_t)j : 0xffffffffu;
+                ++j;
+            }
+        }
+        __syncthreads();
+        // Colours of this round's visible candidates (the stage is reused by
+        // the next round).
+        for (uint32_t c = tid; c < cn; c += 256) {
+            const uint32_t t = S.tiles[c], slot = S.dbits[c];
+            if (!t || slot == 0xffffffffu) continue;
+            const size_t g = (size_t)(i0 + S.cand[c0 + c]);
+            const float3 rgb = sh_colour<DEG>(A.P.sh + g * (DEG + 1) * (DEG + 1) * 3, A.P.sh_vec, S.dx[c], S.dy[c],
+                                              S.dz[c]);
+            const float4 r1 = make_float4(S.qa[c], S.op[c], rgb.x, rgb.y);
+            const float4 r2 = make_float4(rgb.z, S.tz[c], S.rad[c], __uint_as_float(t));
+            float4 *out = A.P.records + 3 * (size_t)slot;
+            out[1] = r1;
+            out[2] = r2;
+            if (A.lp_geo) {
+                A.lp_oq[slot] = make_uint2(__float_as_uint(r1.x), pack2(r1.y, r1.z, A.lp_dtype));
+                A.lp_gb[slot] = pack2(r1.w, r2.x, A.lp_dtype);
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (bv)
+    if (bv_all)
         for (int k = tid; k < kDepthPasses * 256; k += 256)
             if (s_hist[k]) atomicAdd(&A.dsc.hist[k], s_hist[k]);
     __syncthreads();
@@ -1255,25 +1290,9 @@ __global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBa
         s_last = atomicAdd(A.dsc.ticket, 1u) == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
-    // Colours of the visible candidates, after the block's last barrier.
-    for (uint32_t c = tid; c < nc; c += 256) {
-        const uint32_t t = S.tiles[c], slot = S.dbits[c];
-        if (!t || slot == 0xffffffffu) continue;
-        const size_t g = (size_t)(i0 + S.cand[c]);
-        const float3 rgb = sh_colour<DEG>(A.P.sh + g * (DEG + 1) * (DEG + 1) * 3, A.P.sh_vec, S.dx[c], S.dy[c],
-                                          S.dz[c]);
-        const float4 r1 = make_float4(S.qa[c], S.op[c], rgb.x, rgb.y);
-        const float4 r2 = make_float4(rgb.z, S.tz[c], S.rad[c], __uint_as_float(t));
-        float4 *out = A.P.records + 3 * (size_t)slot;
-        out[1] = r1;
-        out[2] = r2;
-        if (A.lp_geo) {
-            A.lp_oq[slot] = make_uint2(__float_as_uint(r1.x), pack2(r1.y, r1.z, A.lp_dtype));
-            A.lp_gb[slot] = pack2(r1.w, r2.x, A.lp_dtype);
-        }
-    }
     if (!s_last) return;
-    list_tail(A.dsc, A.seg, A.seg_dst, (int64_t)gridDim.x * gridDim.y, A.packed, A.counts, A.rec_capacity, s_tmp);
+    list_tail(A.dsc, A.seg, A.seg_dst, (int64_t)gridDim.x * gridDim.y * kBatchRounds, A.packed, A.counts,
+              A.rec_capacity, s_tmp);
 }
 
 template <int DEG>
@@ -1856,7 +1875,9 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
 }
 
 size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity, int64_t n, int n_views) {
-    return front_layout(rec_capacity, key_capacity, (n + kProjBlock - 1) / kProjBlock * n_views, false).total;
+    return front_layout(rec_capacity, key_capacity, (n + kBatchBlock - 1) / kBatchBlock * n_views * kBatchRounds,
+                        false)
+        .total;
 }
 
 cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
@@ -1866,7 +1887,7 @@ cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *v
                                         void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const int64_t nb = (g.n + kProjBlock - 1) / kProjBlock, n_seg = nb * n_views;
+    const int64_t nb = (g.n + kBatchBlock - 1) / kBatchBlock, n_seg = nb * n_views * kBatchRounds;
     const FrontLayout L = front_layout(rec_capacity, key_capacity, n_seg, false);
     char *base = static_cast<char *>(scratch);
     e = cudaMemsetAsync(base, 0, L.zero, s);
