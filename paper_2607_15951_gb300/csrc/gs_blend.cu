@@ -141,13 +141,13 @@ __device__ __forceinline__ void composite(Pix &p, float e, float thr, const floa
     const float4 c = *col;           // opacity, red, green, blue
     const float cr = c.y, cg = c.z, cb = c.w;
     const float alpha = fminf(kAlphaMax, c.x * ex2(e));
-    const float Tn = p.T * (1.f - alpha);
+    const float w = alpha * p.T;  // this Gaussian's weight; T (1 - alpha) = T - w
+    const float Tn = p.T - w;
     if (Tn < kTMin) {
         p.done = true;
         p.eval = pos;
         return;
     }
-    const float w = alpha * p.T;
     p.r = fmaf(cr, w, p.r);
     p.g = fmaf(cg, w, p.g);
     p.b = fmaf(cb, w, p.b);
