@@ -18,7 +18,7 @@ constexpr int kOsLookAhead = GS_SORT_LOOKAHEAD;  // status words read per look-b
 // Shared memory the partition needs: the reordered pairs, per-warp digit
 // counters, digit offsets and bases, scan scratch.
 template <typename KT, int ITEMS>
-constexpr size_t onesweep_partition_smem() {
+__host__ __device__ constexpr size_t onesweep_partition_smem() {
     return (size_t)kOsThreads * ITEMS * (sizeof(KT) + 4) + (size_t)kOsWarps * kOsRadix * 4 + 2 * kOsRadix * 4 +
            kOsWarps * 4 + 16;
 }

@@ -995,7 +995,7 @@ struct EmitSortArgs {
 };
 
 template <typename KT>
-constexpr int emit_sort_smem() {
+__host__ __device__ constexpr int emit_sort_smem() {
     constexpr int emit = (kKeyBlock + 2) * 8 + kKeyBlock * (int)(sizeof(KT) + 4);
     constexpr int part = (int)onesweep_partition_smem<KT, kKeysPerThread>();
     return emit > part ? emit : part;
