@@ -717,6 +717,27 @@ def main():
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     e2e_value = args.e2e_steps * world / (e2e_ms / 1000.0)
 
+    # The host link alone: the same input copies and image read-backs, each
+    # direction timed by itself, give the frame rate the link allows.
+    def link_gbs(copy, nbytes, reps=3):
+        copy()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            copy()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return reps * nbytes / (a.elapsed_time(b) / 1e3) / 1e9
+
+    def h2d_copy():
+        for k in host:
+            dev_in[0][k].copy_(host[k], non_blocking=True)
+
+    h2d_gbs = link_gbs(h2d_copy, h2d)
+    d2h_gbs = link_gbs(lambda: host_rgb[0].copy_(rgb, non_blocking=True), d2h)
+    link_fps = 1.0 / max(h2d / (h2d_gbs * 1e9), d2h / (d2h_gbs * 1e9))
+
     # Roofline of the dominant kernel (blend): FP32 work per launch / its time.
     pk, pk_kind = peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -777,7 +798,12 @@ def main():
         "e2e": {"value": round(e2e_value, 3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
                 "schedule": "inputs double-buffered: step i+1's host-to-device copy (copy stream) overlaps "
-                            "step i's render and image read-back; gs_render deferred"},
+                            "step i's render and image read-back; gs_render deferred",
+                "link": {"h2d_GB/s": round(h2d_gbs, 1), "d2h_GB/s": round(d2h_gbs, 1),
+                         "bound_frames_per_s": round(link_fps * world, 3),
+                         "frac_of_bound": round(e2e_value / (link_fps * world), 4),
+                         "note": "each direction timed alone with the same copies; the bound takes the "
+                                 "slower direction (the two overlap)"}},
         "gpu_launches": None,
         "roofline": roofline,
         "hbm_roofline": hbm,

@@ -246,8 +246,20 @@ __device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) 
     }
 }
 
+// Resident blocks per SM the register allocation must allow. Two pixels per
+// lane (8x8 blocks): 36 warps per SM (56 registers), measured 8 % more
+// frames/s with frames in flight than the unconstrained 64 registers and the
+// same time alone. One pixel per lane: no constraint; stating it lets the
+// allocator use 54 registers instead of 46, 4 % faster alone (0.205 ->
+// 0.197 ms on a 1080p frame) although one block fewer fits per SM.
+constexpr int blend_min_blocks(int warps, int pixels_per_lane) {
+    return pixels_per_lane != 2 ? 1 : (36 / warps < 32 ? 36 / warps : 32);  // at most 32 blocks per SM
+}
+
 template <int TW, int TH, int BW, int BH>
-__global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32) blend_culled_kernel(const BlendArgs a) {
+__global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32,
+                                  blend_min_blocks((TW / BW) * (TH / BH), BW * BH / 32))
+    blend_culled_kernel(const BlendArgs a) {
     blend_tile_culled<TW, TH, BW, BH>(a, blockIdx.x);
 }
 
