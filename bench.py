@@ -486,6 +486,9 @@ def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:
             "seconds": round(el, 2)}
 
 
+REFERENCE_BUDGET_S = 120.0
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on the machine's host cores."""
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
@@ -496,10 +499,17 @@ def run_reference(args):
     oracle.build()
     scene, cams = scenes.workload(args.workload)
     cam = cams[0]
-    for _ in range(args.warmup if args.warmup < 3 else 1):
+    # Warm-up frames (at most 3: each is a whole FP64 frame), the last one
+    # also sizing the sample: whole frames are timed until about two minutes
+    # of CPU time, at most one per step, so that any --steps ends in minutes.
+    t_frame = 0.0
+    for _ in range(max(1, min(args.warmup, 3))):
+        t0 = time.perf_counter()
         oracle.render(scene, cam)
+        t_frame = time.perf_counter() - t0
+    n_frames = int(max(1, min(args.steps, REFERENCE_BUDGET_S // max(t_frame, 1e-3))))
     times = []
-    for _ in range(args.steps):
+    for _ in range(n_frames):
         t0 = time.perf_counter()
         oracle.render(scene, cam)
         times.append(time.perf_counter() - t0)
@@ -512,7 +522,8 @@ def run_reference(args):
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
             "cpu_baseline": {"value": round(value, 4), "unit": "frames/s",
                              "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"{args.steps} whole frames (each step one frame)"},
+                             "sample": f"{n_frames} whole frames timed for the {args.steps} steps (one frame "
+                                       f"per step, at most {REFERENCE_BUDGET_S:.0f} s of frames)"},
             "e2e": {"value": round(value, 4), "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
