@@ -119,13 +119,22 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The largest of the ranks' values (a timed region's length: the job
+    takes as long as its slowest rank)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, max_ms: float, world: int) -> float:
+    """Units all ranks processed per second over the slowest rank's time (each
+    rank renders its own independent frames: weak scaling, no exchange)."""
+    return units_per_rank * world / (max_ms / 1000.0)
 
 
 def peaks():
@@ -659,8 +668,7 @@ def main():
         gs.gs_sync_status(c)
     pipe_ms = max_over_ranks(p0.elapsed_time(p1), world)
     ms_per_step = pipe_ms / args.steps
-    frames = args.steps * world
-    value = frames / (pipe_ms / 1000.0)
+    value = whole_job_rate(args.steps, pipe_ms, world)
     for c in pctx[1:]:
         c.close()
     del copies
@@ -726,7 +734,7 @@ def main():
     torch.cuda.synchronize()
     gs.gs_sync_status(ctx)
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-    e2e_value = args.e2e_steps * world / (e2e_ms / 1000.0)
+    e2e_value = whole_job_rate(args.e2e_steps, e2e_ms, world)
 
     # The host link alone: the same input copies and image read-backs, each
     # direction timed by itself, give the frame rate the link allows.
