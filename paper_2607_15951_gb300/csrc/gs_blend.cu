@@ -15,8 +15,9 @@
 //  * culled 8x8 / wide / tile: the same with 8x8 blocks (2 pixels per lane
 //    sharing the x terms), 16x8 blocks (4) or one warp per 16x16 tile (8).
 //    Finer blocks cull more records than the wider ones save in per-record
-//    overhead (measured on a 1080p frame: 8x4 0.221 ms, 8x8 0.240, 16x8 0.369,
-//    16x16 0.694).
+//    overhead (one 1080p frame alone: 8x4 0.197 ms, 8x8 0.229; with the box
+//    test only, 16x8 0.369 and 16x16 0.694). 8x8 blocks issue the fewest
+//    instructions and win when several frames' kernels share the GPU.
 //  * basic: one thread per pixel walks every record (reference schedule).
 // Both evaluate a (pixel, record) pair with the same function, so a record a
 // warp skips is exactly one whose evaluation would have been skipped.
