@@ -110,8 +110,10 @@ typedef struct {
 
 /* Blend schedules; all produce identical outputs.
  *   GS_BLEND_CULLED       each warp owns an 8x4 pixel block and skips records
- *                         whose conservative alpha >= 1/255 box misses it
- *                         (default)
+ *                         that cannot reach alpha >= 1/255 in it (default);
+ *                         gs_render switches to 8x8 blocks (as
+ *                         GS_BLEND_CULLED_8X8) after a frame that averaged
+ *                         more than 1024 keys per tile
  *   GS_BLEND_BASIC        one thread per pixel evaluates every record of its
  *                         tile
  *   GS_BLEND_CULLED_WIDE  as CULLED with 16x8 blocks (16-wide tiles; 8x8
