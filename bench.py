@@ -169,21 +169,38 @@ def profiled_traffic(kernel: str):
     return None, None
 
 
-def frame_bytes(n, n_vis, K, sh_degree, tile_passes, n_tiles, pixels) -> dict:
+def tile_key_plan(tiles_x: int, tiles_y: int, key_bits: int) -> tuple:
+    """(key bytes, digit passes, passes run inside the emission) of gs_render's
+    tile sort. Grids at most 256 tiles wide use (row << 8 | column) keys whose
+    first (column) pass runs inside the emission kernel; wider grids sort
+    tile ids (key_bits - 32 bits, key_bits as the library reports it) in
+    separate passes. Keys of at most 16 bits are 2 bytes, else 4."""
+    if tiles_x <= 256:
+        row_bits = max(0, (tiles_y - 1).bit_length())
+        tkey_bits, fused = 8 + row_bits, 1
+    else:
+        tkey_bits, fused = key_bits - 32, 0
+    passes = max(1, (tkey_bits + 7) // 8)
+    return (2 if tkey_bits <= 16 else 4), passes, min(fused, passes)
+
+
+def frame_bytes(n, n_vis, K, sh_degree, tiles_x, tiles_y, key_bits, pixels) -> dict:
     """Bytes each forward stage has to move in DRAM, per frame: every mean
     and log-scale (the screen bound), rotation, opacity and SH of the visible
     Gaussians, records of 48 B, list entries of 12 B (gathered into index
-    order, then four depth passes), tile-id keys of 2 B (4 B from 65,536
-    tiles) with 4-byte values, and the image (rgb + final T + last
-    contributor)."""
+    order, then four depth passes), tile keys of 2 or 4 B with 4-byte values
+    (written once by the emission, after its fused pass where there is one,
+    then read and written by each remaining pass), and the image (rgb + final
+    T + last contributor)."""
     s = 3 * (sh_degree + 1) ** 2
-    kb = 2 if n_tiles <= 65536 else 4
+    kb, passes, fused = tile_key_plan(tiles_x, tiles_y, key_bits)
+    n_tiles = tiles_x * tiles_y
     return {
         "project": n * 24 + n_vis * (20 + 4 * s) + n_vis * (48 + 12),
         "depth_sort": n_vis * 24 + 4 * n_vis * 24,
         "entry_scan": n_vis * 12,
         "emit": n_vis * (32 + 8) + K * (kb + 4),
-        "tile_sort": tile_passes * K * 2 * (kb + 4),
+        "tile_sort": (passes - fused) * K * 2 * (kb + 4),
         "ranges": K * kb + n_tiles * 8,
         "blend": K * 4 + n_vis * 48 + pixels * 20,
     }
@@ -244,9 +261,8 @@ def fwd_bwd(gs, torch, args, flush, local) -> dict:
     st = gs.gs_last_render_stats(ctx)
     ctx.close()
     pk, _ = peaks()
-    n_tiles = st["n_tiles"]
-    fb = frame_bytes(scene.n, st["n_visible"], st["n_keys"], scene.sh_degree,
-                     (st["key_bits"] - 32 + 7) // 8, n_tiles, cam.width * cam.height)
+    fb = frame_bytes(scene.n, st["n_visible"], st["n_keys"], scene.sh_degree, (cam.width + 15) // 16,
+                     (cam.height + 15) // 16, st["key_bits"], cam.width * cam.height)
     total = sum(fb.values()) + backward_bytes(scene.n, st["n_visible"], st["n_keys"], scene.sh_degree,
                                               cam.width * cam.height)
     gbs = total / (ms / 1e3) / 1e9
@@ -780,9 +796,8 @@ def main():
                     "frac": round(flops * value / world / 1e12 / fp32_peak_tflops, 4)}}
 
     # HBM view of the same frame: bytes each stage must move / its live time.
-    tile_passes = (stats["key_bits"] - 32 + 7) // 8
-    fbytes = frame_bytes(scene.n, stats["n_visible"], stats["n_keys"], scene.sh_degree,
-                         tile_passes, stats["n_tiles"], W * H)
+    fbytes = frame_bytes(scene.n, stats["n_visible"], stats["n_keys"], scene.sh_degree, (W + 15) // 16,
+                         (H + 15) // 16, stats["key_bits"], W * H)
     stage_of = {"project": "project_ms", "depth_sort": "depth_sort_ms", "entry_scan": "entry_scan_ms",
                 "emit": "emit_ms", "tile_sort": "tile_sort_ms", "ranges": "ranges_ms", "blend": "blend_ms"}
     hbm_peak = pk.get("hbm_gbs") or 6800.0
@@ -831,15 +846,11 @@ def main():
         "clocks_single_stream": clk,
     }
     # Kernel launches per gs_render: projection + compact list, the list
-    # gather, four depth digit passes, the entry scan, key emission fused with
-    # the first tile pass (grids at most 256 tiles wide), the other tile
-    # passes, ranges, blend.
-    tiles_x = (W + 15) // 16
-    row_bits = int(np.ceil(np.log2(max(1, (H + 15) // 16))))
-    if tiles_x <= 256:
-        per_step = 9 + (8 + row_bits + 7) // 8
-    else:
-        per_step = 10 + (stats["key_bits"] - 32 + 7) // 8
+    # gather, four depth digit passes, the entry scan, the key emission (with
+    # the first tile pass inside it on grids at most 256 tiles wide), the
+    # other tile passes, ranges, blend.
+    _, passes, fused = tile_key_plan((W + 15) // 16, (H + 15) // 16, stats["key_bits"])
+    per_step = 10 + passes - fused
     line["gpu_launches"] = per_step * args.steps
     if not args.no_fwd_bwd:
         line["fwd_bwd"] = fwd_bwd(gs, torch, args, flush, local)
