@@ -1,10 +1,19 @@
 // gs_project.cu — per-Gaussian projection (Sec. 3.1 stages 1-2; the square
 // 3-sigma bound of Sec. 4.4; the near-plane cull of Sec. 4.5 step 1).
 //
-// One thread per Gaussian. Every thread reads the 12-byte mean; only
-// Gaussians in front of the near plane go on to read scale, rotation,
-// opacity and SH, so the HBM traffic of a mostly-culled scene is ~16 B per
-// Gaussian (mean in, tile count out) plus ~250 B per visible one.
+// Two kernels share the per-Gaussian arithmetic (project_one):
+//  * project_kernel, the gs_project stage entry point: one thread per
+//    Gaussian; every thread reads the 12-byte mean, only Gaussians in front
+//    of the near plane go on to read scale, rotation, opacity and SH (~16 B
+//    per culled Gaussian, ~250 B per visible one), and every Gaussian gets a
+//    record slot and a tile count.
+//  * project_list_kernel, the first launch of gs_render: 1024 Gaussians per
+//    block; a conservative screen bound from the mean and the largest scale
+//    (24 B per Gaussian) picks the candidates, which alone get the full
+//    projection; the visible ones get a record and an entry of the compact
+//    list, the depth digits and the tile sort's digit histograms are counted
+//    on the way, and SH colours are evaluated after the block's last barrier.
+//    The batched variant (project_list_batch_kernel) does the same per view.
 //
 // Numerics, all FP32:
 //  * 2D covariance as (T M)(T M)^T with T = J W (2x3) and M = R(q) S, so the
