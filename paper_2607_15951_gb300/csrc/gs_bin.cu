@@ -1,6 +1,10 @@
 // gs_bin.cu — screen-tile binning (Sec. 3.1 stage 3; Sec. 4.5 step 2):
-// exclusive scan of per-Gaussian tile counts, emission of (tile, depth) keys,
-// and per-tile ranges of the sorted keys. The sort itself is gs_sort.cu.
+// for the gs_bin stage entry point, the exclusive scan of per-Gaussian tile
+// counts and the emission of (tile << 32 | depth bits, index) pairs; for
+// every path, the per-tile ranges of the sorted keys (64-bit keys, or the
+// 16/32-bit tile keys of gs_render and gs_render_batch) and the batch blend's
+// longest-list-first work queue. gs_render emits its keys in depth order in
+// gs_project.cu; the sort itself is gs_sort.cu.
 #include "gs_internal.cuh"
 
 namespace {
