@@ -107,8 +107,12 @@ def dist_init():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl" if os.environ.get("GS_BENCH_BACKEND") != "gloo" else "gloo")
+        backend = "gloo" if os.environ.get("GS_BENCH_BACKEND") == "gloo" else "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(local)  # each rank on its own GPU before NCCL starts
+        dist.init_process_group(backend)
     return world, rank, local
 
 
