@@ -1,7 +1,10 @@
 """Planted mistakes: each mutation below is applied to a copy of the oracle
-source, compiled, and the pin suite (tests/test_oracle_pins.py) is run against
-it. Every mutation must make at least one pin fail, which shows the pins are
-not blind to that class of slip. The real oracle is never modified."""
+source, compiled, and a pin suite is run against it: the forward pins
+(tests/test_oracle_pins.py) for mistakes in the projection, binning and
+blend, the finite-difference gradient pins (tests/test_oracle_grad_pins.py)
+for mistakes in the gradient. Every mutation must make at least one pin
+fail, which shows the pins are not blind to that class of slip. The real
+oracle is never modified."""
 import os
 import subprocess
 import sys
@@ -39,11 +42,31 @@ MUTATIONS = {
 }
 
 
+# Mistakes in the gradient (Eq. 1 differentiated per pixel, then the
+# projection in forward mode), caught by the finite-difference pins.
+GRAD_MUTATIONS = {
+    "grad_no_background_term": ("(S[ch] + bg[ch] * T_N) / (1.0 - c.alpha)", "(S[ch]) / (1.0 - c.alpha)"),
+    "grad_suffix_sign": ("ck[ch] * c.T - (S[ch] + bg[ch] * T_N)", "ck[ch] * c.T + (S[ch] + bg[ch] * T_N)"),
+    "grad_no_one_minus_alpha": ("(S[ch] + bg[ch] * T_N) / (1.0 - c.alpha);", "(S[ch] + bg[ch] * T_N);"),
+    "grad_mean_sign": ("const double du = dL_dpower * (q[0] * c.dx + q[1] * c.dy);",
+                       "const double du = -dL_dpower * (q[0] * c.dx + q[1] * c.dy);"),
+    "grad_cross_term_factor": ("const double dq01 = dL_dpower * (-c.dx * c.dy);",
+                               "const double dq01 = dL_dpower * (-0.5 * c.dx * c.dy);"),
+    "grad_opacity_without_G": ("const double dL_do = dL_dalpha * c.G;", "const double dL_do = dL_dalpha;"),
+    "grad_log_scale_seed": ("ls[a] = Dual(log_scales[3 * i + a], j == 3 + a ? 1.0 : 0.0);",
+                            "ls[a] = Dual(log_scales[3 * i + a], j == 4 + a ? 1.0 : 0.0);"),
+    "grad_colour_weight": ("dr[6 + ch] += gp[ch] * c.alpha * c.T;", "dr[6 + ch] += gp[ch] * c.alpha;"),
+}
+
+CASES = [(n, "test_oracle_pins.py") for n in sorted(MUTATIONS)] + \
+        [(n, "test_oracle_grad_pins.py") for n in sorted(GRAD_MUTATIONS)]
+
+
 @pytest.mark.slow
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+@pytest.mark.parametrize("name,pins", CASES, ids=[c[0] for c in CASES])
+def test_pins_catch_planted_mistake(name, pins, tmp_path):
     src = open(SRC).read()
-    old, new = MUTATIONS[name]
+    old, new = {**MUTATIONS, **GRAD_MUTATIONS}[name]
     assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
     mutated = tmp_path / "mut.cpp"
     mutated.write_text(src.replace(old, new))
@@ -52,6 +75,6 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                            "-o", str(lib), str(mutated)])
     env = dict(os.environ, GS_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught mutation {name}:\n{r.stdout[-2000:]}"
