@@ -121,3 +121,31 @@ def test_screen_bound_keeps_tiny_gaussians_at_the_border(oracle_mod):
     assert vis.sum() > n // 2
     keep = screen_bound_keeps(s, cam, tile)
     assert not np.any(vis & ~keep)
+
+
+def test_screen_bound_uses_the_guard_band_of_the_jacobian(oracle_mod):
+    """Means past the guard band (view ratio 1.3-1.7 x the half field of view)
+    of a camera whose z row is scaled by 10, Gaussians long along world z: the
+    footprint reaching into the image comes from the |r| n2 term at the
+    clamped ratio, so the bound must clamp where the Jacobian does (1.3)."""
+    rng = np.random.default_rng(5)
+    n = 20_000
+    w2c = np.concatenate([np.eye(3), np.zeros((3, 1))], axis=1).astype(np.float32)
+    w2c[2, :3] *= 10.0
+    cam = scenes.pinhole(400, 300, 60.0, world_to_cam=w2c)
+    half_x = 0.5 * cam.width / cam.fx
+    half_y = 0.5 * cam.height / cam.fy
+    z = rng.uniform(2.0, 6.0, n)                      # camera depth is 10 z
+    rx = rng.choice([-1.0, 1.0], n) * half_x * rng.uniform(1.3, 1.7, n)
+    ry = rng.uniform(-0.3, 0.3, n) * half_y
+    s = scenes.uniform_box(n, 5)
+    s.means[:] = np.stack([rx * 10 * z, ry * 10 * z, z], axis=1).astype(np.float32)
+    ls = np.full((n, 3), math.log(1e-3))
+    ls[:, 2] = np.log(rng.uniform(0.05, 3.0, n))
+    s.log_scales[:] = ls.astype(np.float32)
+    s.quats[:] = np.array([1.0, 0.0, 0.0, 0.0], np.float32)
+    pr = oracle_mod.project(s, cam)
+    vis = pr.visible > 0
+    assert vis.sum() > 1000
+    keep = screen_bound_keeps(s, cam)
+    assert not np.any(vis & ~keep)
