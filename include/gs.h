@@ -179,7 +179,11 @@ enum { GS_SYNC_FRAME = 0, GS_SYNC_DEFERRED = 1 };
 void gs_default_options(gs_options *opts /* host */);
 
 /* Context: owns the scratch workspace (grown on demand) and the device error
- * word, bound to one CUDA device. */
+ * word, bound to one CUDA device. *ctx is set to NULL on failure:
+ * GS_ERR_INVALID_ARG for a null ctx or a device index that does not exist
+ * (also when the machine has no CUDA device), GS_ERR_CUDA if the context's
+ * small device and pinned host buffers or its events cannot be created.
+ * gs_destroy(NULL) does nothing. */
 gs_status gs_create(gs_context **ctx /* host out */, int device);
 void gs_destroy(gs_context *ctx);
 /* Message of the last failing call on this context (host string, valid until

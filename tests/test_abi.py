@@ -75,3 +75,39 @@ def test_null_context_rejected(lib):
 def test_kernels_built_for_sm103a_only():
     # The build passes exactly one -gencode, for sm_103a.
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_plain_c_program_links_and_calls_the_library(lib, tmp_path):
+    """A C99 program (no Python, no torch) links against libgs.so and calls
+    it: default options, argument checks, and a context that is created where
+    a device exists and refused with a status (not a crash) where none does."""
+    src = tmp_path / "use_gs.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "gs.h"
+int main(void) {
+  gs_options o;
+  gs_default_options(&o);
+  if (o.tile_w != 16 || o.tile_h != 16 || o.record_dtype != GS_RECORD_F32) return 1;
+  if (gs_render(NULL, NULL, NULL, NULL, NULL, NULL) != GS_ERR_INVALID_ARG) return 2;
+  gs_context *ctx = NULL;
+  gs_status st = gs_create(&ctx, 0);
+  if (st == GS_OK) {
+    if (!ctx) return 3;
+    gs_destroy(ctx);
+  } else if (ctx != NULL) {
+    return 4;
+  }
+  printf("%d\n", (int)st);
+  return 0;
+}
+''')
+    exe = tmp_path / "use_gs"
+    libdir = os.path.dirname(B.LIB)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), str(src),
+                           "-L", libdir, "-l:" + os.path.basename(B.LIB), "-Wl,-rpath," + libdir,
+                           "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    # GS_OK where device 0 exists, GS_ERR_INVALID_ARG where it does not.
+    assert int(r.stdout.split()[0]) in (N.GS_OK, N.GS_ERR_INVALID_ARG)
