@@ -237,15 +237,18 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *values, int64
  * allocate device memory (allocator or memory-pool callbacks, fixed-footprint
  * real-time loops, hosts that own all device memory): same sort, same
  * arguments, no gs_context. The paper has no counterpart; this is a library
- * service. Its scratch is one array built into libgs.so, about 4 MiB, which
- * every GPU that loads the library holds until the process exits.
+ * service. Its scratch is one array built into libgs.so, about 4 MiB
+ * (4,227,328 bytes), which every GPU that loads the library holds until the
+ * process exits.
  *   n <= GS_NOALLOC_SORT_MAX_PAIRS, else GS_ERR_CAPACITY (nothing launched).
  *   All calls share that array: calls that overlap on the GPU corrupt each
  *   other; serialise them. The first call on a device looks the array up
- *   with that device current (make it before any stream capture).
- *   Returns after the sort has finished on `stream` (waits once to read the
- *   device error word); GS_ERR_TIMEOUT if a bounded wait gave up. Calls no
- *   cudaMalloc/cudaFree. */
+ *   with that device current (make it before any stream capture); the
+ *   address is kept, so that device must not be reset after the first call.
+ *   Device indices of 64 and above are not served (GS_ERR_CUDA).
+ *   Returns after the sort has finished on `stream` (waits once on that
+ *   stream to read the device error word); GS_ERR_TIMEOUT if a bounded wait
+ *   gave up. Calls no cudaMalloc/cudaFree. */
 #define GS_NOALLOC_SORT_MAX_PAIRS 262144
 gs_status gs_sort_pairs_noalloc(uint64_t *keys, uint32_t *values, int64_t n, int32_t key_bits,
                                 void *stream);
@@ -326,7 +329,15 @@ typedef struct {
  *   discrete and have no derivative.
  * g, cam and opts must be those of that gs_render, and fb must hold the
  * final_T and n_contrib it wrote (both required here). Invisible Gaussians
- * get zero gradients. */
+ * get zero gradients. The call checks that the context's last frame is that
+ * frame: the same five parameter pointers, count and SH degree, every camera
+ * field, tile shape, background and record precision; otherwise (another
+ * gs_render came in between, e.g. a second view rendered before the first
+ * view's backward) it returns GS_ERR_INVALID_ARG and writes nothing. The
+ * caller then renders that frame again (a render is deterministic, so its
+ * final_T and n_contrib come out bit for bit the same) and calls again.
+ * gs_bin and gs_sort_pairs reuse the buffers the lists live in, so after them
+ * there is no frame to differentiate. */
 gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
                              const gs_options *opts, const gs_framebuffer *fb, const float *d_rgb,
                              const gs_grads *out, void *stream);
@@ -388,6 +399,14 @@ gs_status gs_selftest_bounded_wait(gs_context *ctx, int32_t kind, int64_t timeou
  * stops the context from shrinking it between frames (the buffers grow if a
  * frame needs more). */
 gs_status gs_reserve_keys(gs_context *ctx, int64_t key_capacity);
+
+/* Number of the last frame gs_render made on this context that a
+ * gs_render_backward could still differentiate: 1 for the first frame, then
+ * counting up; 0 when there is none (no frame yet, the frame overflowed its
+ * key buffers, or gs_bin / gs_sort_pairs reused its buffers since). A caller
+ * that keeps several frames alive saves the number after each gs_render and
+ * compares it before a backward. */
+gs_status gs_last_frame_id(const gs_context *ctx, uint64_t *out /* host */);
 
 /* Statistics of the last gs_render on this context (host out). Waits for
  * deferred frames first and returns the first error among them (the

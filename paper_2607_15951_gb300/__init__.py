@@ -19,7 +19,7 @@ __all__ = ["GSError", "Context", "camera_struct", "options_struct", "gaussians_s
            "gs_create", "gs_destroy", "gs_project", "gs_bin", "gs_sort_pairs", "gs_tile_ranges",
            "gs_blend", "gs_render", "gs_sync_status", "gs_last_render_stats",
            "gs_set_stage_timing", "gs_last_stage_times", "gs_sort_pairs_noalloc", "gs_reserve_keys",
-           "gs_render_backward", "RasterizeGaussians",
+           "gs_render_backward", "gs_last_frame_id", "RasterizeGaussians",
            "RECORD_FLOATS"]
 
 RECORD_FLOATS = 12  # gs_record is 48 bytes = 12 x 4-byte words
@@ -239,6 +239,13 @@ def gs_last_render_stats(ctx: Context) -> dict:
             "n_tiles": s.n_tiles, "n_moved": s.n_moved, "rebinned": bool(s.rebinned)}
 
 
+def gs_last_frame_id(ctx: Context) -> int:
+    """Number of the context's last frame a backward can differentiate (0: none)."""
+    v = ctypes.c_uint64(0)
+    ctx.check(_lib().gs_last_frame_id(ctx.handle, ctypes.byref(v)))
+    return int(v.value)
+
+
 def gs_reserve_keys(ctx: Context, key_capacity: int) -> None:
     ctx.check(_lib().gs_reserve_keys(ctx.handle, int(key_capacity)))
 
@@ -309,15 +316,22 @@ def _autograd_function():
                    "n_contrib": torch.empty((H, W), dtype=torch.int32, device=means.device)}
             gs_render(ctx, g, sh_degree, cam, out["rgb"], out["final_T"], out["n_contrib"], None,
                       tile=tile, bg=bg, deferred=deferred, record_dtype=record_dtype)
-            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype)
+            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, gs_last_frame_id(ctx))
             fctx.save_for_backward(out["final_T"], out["n_contrib"])
             fctx.mark_non_differentiable(out["final_T"])
             return out["rgb"], out["final_T"]
 
         @staticmethod
         def backward(fctx, d_rgb, d_T):
-            ctx, cam, sh_degree, tile, bg, g, record_dtype = fctx.gs
+            ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, frame = fctx.gs
             final_T, n_contrib = fctx.saved_tensors
+            if gs_last_frame_id(ctx) != frame:
+                # Another frame was rendered on the context since this one
+                # (e.g. several views before one backward): render this frame
+                # again, which gives the same lists, final_T and n_contrib.
+                redo = render(ctx, g, sh_degree, cam, tile=tile, bg=bg, aux=True, record_dtype=record_dtype,
+                              deferred=deferred)
+                final_T, n_contrib = redo["final_T"], redo["n_contrib"]
             grads = {k: torch.empty_like(v) for k, v in g.items()}
             gs_render_backward(ctx, g, sh_degree, cam, final_T, n_contrib, d_rgb.contiguous(), grads,
                                tile=tile, bg=bg, record_dtype=record_dtype)
@@ -333,8 +347,9 @@ _RASTERIZE = None
 def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Context, cam, sh_degree: int,
                        tile=(16, 16), bg=(0.0, 0.0, 0.0), deferred: bool = True, record_dtype: int = 0):
     """Differentiable render: returns (rgb (H,W,3), final_T (H,W)); gradients
-    flow to the five parameter tensors. The backward of a render must run
-    before the next render on the same context.
+    flow to the five parameter tensors. Several renders may precede their
+    backwards on one context: a backward whose frame is no longer the
+    context's last renders it again first (same lists, same gradients).
 
     deferred=True (default) renders with GS_SYNC_DEFERRED: the forward does
     not wait for the GPU; the backward checks the forward's key count and

@@ -112,6 +112,7 @@ SIGNATURES = {
     "gs_render": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
                                  ctypes.POINTER(gs_options), ctypes.POINTER(gs_framebuffer), vp]),
     "gs_last_render_stats": (ctypes.c_int, [vp, ctypes.POINTER(gs_render_stats)]),
+    "gs_last_frame_id": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint64)]),
     "gs_reserve_keys": (ctypes.c_int, [vp, ctypes.c_int64]),
     "gs_render_batch_backward": (ctypes.c_int, [vp, ctypes.POINTER(gs_gaussians), ctypes.POINTER(gs_camera),
                                                 ctypes.c_int32, ctypes.POINTER(gs_options),

@@ -29,8 +29,13 @@ struct gs_context {
     DevBuf records, tiles, offsets, scan_scratch, keys, values, alt_keys, alt_values, sort_scratch,
         ranges;
     gs_render_stats stats{};
-    // State of the last gs_render, for gs_render_backward.
+    // State of the last gs_render, for gs_render_backward: the frame's
+    // number, its scene arrays, camera and options, and where its lists are.
     bool have_last = false;
+    uint64_t frame_id = 0;  // number of the last gs_render (1, 2, ...; 0: none)
+    gs_gaussians last_g{};
+    gs_camera last_cam{};
+    float last_bg[3] = {0.f, 0.f, 0.f};
     int64_t last_n = 0;
     int last_w = 0, last_h = 0, last_tw = 0, last_th = 0;
     const uint32_t *last_values = nullptr;
@@ -325,9 +330,52 @@ struct DeviceGuard {
 
 // Scan + emit + sort + ranges into the given key/value buffers (which must
 // hold `capacity` pairs); the other pair of buffers comes from the context.
-// Temporal state may point into the context's key buffers, which the stage
-// entry points reuse: they drop it.
-void drop_temporal(gs_context *ctx) { ctx->temporal.valid = false; }
+// The stage entry points reuse the context's key buffers, which the temporal
+// state and the last frame's lists (read by gs_render_backward) point into:
+// they drop both.
+void drop_temporal(gs_context *ctx) {
+    ctx->temporal.valid = false;
+    ctx->have_last = false;
+}
+
+// Records what gs_render_backward needs of the frame just enqueued (seq: its
+// deferred sequence number, 0 for a synchronised frame).
+void remember_frame(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam, const gs_options *opts,
+                    const GsGrid &grid, const uint32_t *values, const uint32_t *ranges, uint64_t seq) {
+    ctx->have_last = true;
+    ctx->frame_id += 1;
+    ctx->last_seq = seq;
+    ctx->last_g = *g;
+    ctx->last_cam = *cam;
+    for (int c = 0; c < 3; ++c) ctx->last_bg[c] = opts->bg[c];
+    ctx->last_n = g->n;
+    ctx->last_w = cam->width;
+    ctx->last_h = cam->height;
+    ctx->last_tw = grid.tile_w;
+    ctx->last_th = grid.tile_h;
+    ctx->last_values = values;
+    ctx->last_ranges = ranges;
+    ctx->last_dtype = opts->record_dtype;
+}
+
+// Is (g, cam, opts) the frame remembered by remember_frame? Compares the
+// scene's array pointers, count and SH degree, every camera field, the tile
+// shape, the background and the record precision.
+bool same_frame(const gs_context *ctx, const gs_gaussians *g, const gs_camera *cam, const gs_options *opts) {
+    const gs_gaussians &a = ctx->last_g;
+    if (a.means != g->means || a.log_scales != g->log_scales || a.quats != g->quats ||
+        a.opacity_logits != g->opacity_logits || a.sh != g->sh || a.n != g->n || a.sh_degree != g->sh_degree)
+        return false;
+    const gs_camera &c = ctx->last_cam;
+    for (int i = 0; i < 12; ++i)
+        if (c.world_to_cam[i] != cam->world_to_cam[i]) return false;
+    if (c.fx != cam->fx || c.fy != cam->fy || c.cx != cam->cx || c.cy != cam->cy || c.width != cam->width ||
+        c.height != cam->height || c.near_z != cam->near_z)
+        return false;
+    for (int i = 0; i < 3; ++i)
+        if (ctx->last_bg[i] != opts->bg[i]) return false;
+    return ctx->last_tw == opts->tile_w && ctx->last_th == opts->tile_h && ctx->last_dtype == opts->record_dtype;
+}
 
 gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *tiles, int64_t n,
                    const GsGrid &grid, uint64_t *keys, uint32_t *values, int64_t capacity,
@@ -536,16 +584,7 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     T.rects_n = n;
     T.last_churn = visible > 0 ? (double)h[1] / (double)visible : 0.0;
     if (ctx->timing) ctx->timed_once = true;
-    ctx->have_last = true;
-    ctx->last_seq = 0;
-    ctx->last_n = n;
-    ctx->last_w = cam->width;
-    ctx->last_h = cam->height;
-    ctx->last_tw = grid.tile_w;
-    ctx->last_th = grid.tile_h;
-    ctx->last_values = vals;
-    ctx->last_ranges = ranges;
-    ctx->last_dtype = dtype;
+    remember_frame(ctx, g, cam, opts, grid, vals, ranges, 0);
     *done = true;
     if (w) return collect_device_error(ctx, s);
     return GS_OK;
@@ -885,16 +924,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             p.bits = bits;
             ++ctx->ring_count;
             if (ctx->timing) ctx->timed_once = true;
-            ctx->have_last = true;
-            ctx->last_seq = p.seq;
-            ctx->last_n = n;
-            ctx->last_w = cam->width;
-            ctx->last_h = cam->height;
-            ctx->last_tw = grid.tile_w;
-            ctx->last_th = grid.tile_h;
-            ctx->last_values = sv;
-            ctx->last_ranges = ranges;
-            ctx->last_dtype = dtype;
+            remember_frame(ctx, g, cam, opts, grid, sv, ranges, p.seq);
             return GS_OK;
         }
         GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 5 * sizeof(unsigned long long),
@@ -916,16 +946,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             continue;
         }
         if (ctx->timing) ctx->timed_once = true;
-        ctx->have_last = true;
-        ctx->last_seq = 0;
-        ctx->last_n = n;
-        ctx->last_w = cam->width;
-        ctx->last_h = cam->height;
-        ctx->last_tw = grid.tile_w;
-        ctx->last_th = grid.tile_h;
-        ctx->last_values = sv;
-        ctx->last_ranges = ranges;
-        ctx->last_dtype = dtype;
+        remember_frame(ctx, g, cam, opts, grid, sv, ranges, 0);
         ctx->stats.n_moved = have_prev_rects ? (int64_t)ctx->h_counts[4] : 0;
         ctx->stats.rebinned = 0;
         if (temporal) {
@@ -975,9 +996,12 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
         bool retired = false;
         if ((st = retire_oldest(ctx, true, s, &retired)) != GS_OK) return st;
     }
-    if (!ctx->have_last || ctx->last_n != g->n || ctx->last_w != cam->width || ctx->last_h != cam->height ||
-        ctx->last_tw != opts->tile_w || ctx->last_th != opts->tile_h || ctx->last_dtype != opts->record_dtype)
-        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward must follow gs_render of the same scene and camera");
+    if (!ctx->have_last)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_backward needs a completed gs_render on this context");
+    if (!same_frame(ctx, g, cam, opts))
+        return fail(ctx, GS_ERR_INVALID_ARG,
+                    "gs_render_backward must follow gs_render of the same scene arrays, camera and options: the "
+                    "context's last frame (number " + std::to_string(ctx->frame_id) + ") differs");
     const GsGrid grid = make_grid(cam, opts);
     const int64_t n = g->n;
     if ((st = ensure(ctx, ctx->d_rec, (size_t)(n > 0 ? n : 1) * 9 * sizeof(float), "record gradients")) != GS_OK)
@@ -1361,6 +1385,12 @@ gs_status gs_last_stage_times(gs_context *ctx, gs_stage_times *out) {
     out->ranges_ms = el(EV_SORT, EV_RANGES);
     out->blend_ms = el(EV_RANGES, EV_BLEND);
     out->total_ms = el(EV_START, EV_BLEND);
+    return GS_OK;
+}
+
+gs_status gs_last_frame_id(const gs_context *ctx, uint64_t *out) {
+    if (!ctx || !out) return GS_ERR_INVALID_ARG;
+    *out = ctx->have_last ? ctx->frame_id : 0;
     return GS_OK;
 }
 

@@ -7,8 +7,9 @@
 // memory itself and forbids libraries from taking more. Such callers cannot
 // create a gs_context (its workspace grows with cudaMalloc). This entry point
 // takes its scratch from one array that is part of the library image
-// instead: a file-scope __device__ array of kScratchBytes (4-6 MiB),
-// which every GPU that loads libgs.so holds until the process exits.
+// instead: a file-scope __device__ array of kScratchBytes (about 4 MiB:
+// 4,227,328 bytes with the default partition size), which every GPU that
+// loads libgs.so holds until the process exits.
 //
 // Rules of use:
 //  * n is limited to GS_NOALLOC_SORT_MAX_PAIRS pairs; larger requests fail
@@ -18,9 +19,12 @@
 //    each other's results; serialise them.
 //  * The first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture begins.
+//    before any stream capture begins. The address is kept for the life of
+//    the process, so the device must not be reset (cudaDeviceReset) after
+//    that first call. Devices with an index of 64 or more are not served
+//    (GS_ERR_CUDA).
 //  * The call returns after the sort has finished on `stream` (it waits for
-//    the stream once to read the device error word).
+//    that stream once to read the device error word).
 #include <mutex>
 
 #include "gs_internal.cuh"
@@ -91,9 +95,11 @@ extern "C" gs_status gs_sort_pairs_noalloc(uint64_t *keys, uint32_t *values, int
             cudaMemcpyAsync(values, alt_vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return GS_ERR_CUDA;
     }
+    // The error word is read on the caller's stream, so the wait covers that
+    // stream only.
     uint32_t err = 0;
-    if (cudaStreamSynchronize(s) != cudaSuccess ||
-        cudaMemcpy(&err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpyAsync(&err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
         return GS_ERR_CUDA;
     if (err & gs::kErrTimeout) return GS_ERR_TIMEOUT;
     return err ? GS_ERR_INVALID_ARG : GS_OK;

@@ -54,6 +54,29 @@ def test_rebinned_frames_equal_full_binning(built, kind, step):
     print(kind, step, "rebinned", rebinned, "moved", moved)
 
 
+def test_rebinned_moved_frames_match_oracle(built, oracle_mod):
+    """Re-binned frames of a moving camera against the FP64 oracle's render of
+    the same camera (not only against the full binning): a mistake shared by
+    both binnings of this library cannot pass."""
+    from parity_util import RGB_TOL, compare_image
+    scene = scenes.clustered(200_000, 31, box=8.0)
+    g = gs.scene_to_device(scene)
+    cams = scenes.motion("orbit", 4, 480, 272, step=0.1)
+    ctx = gs.Context(0)
+    for i, c in enumerate(cams):
+        out = gs.render(ctx, g, scene.sh_degree, c, temporal=True)
+        torch.cuda.synchronize()
+        st = gs.gs_last_render_stats(ctx)
+        if i == 0:
+            continue
+        assert st["rebinned"] and st["n_moved"] > 0, st
+        _, _, img = oracle_mod.render(scene, c)
+        cmp = compare_image(out["rgb"].cpu().numpy(), out["final_T"].cpu().numpy(), img)
+        cmp.pop("keep")
+        print("re-binned frame", i, "moved", st["n_moved"], "vs FP64:", cmp)
+        assert cmp["max_rgb_err"] <= RGB_TOL and cmp["max_T_err"] <= RGB_TOL, cmp
+
+
 def test_rebinning_falls_back_and_recovers(built):
     # One tile holds more than the per-tile limit: every frame is binned in
     # full, with identical results.

@@ -32,8 +32,13 @@ def test_noalloc_sort_matches_context_sort():
     ctx = gs.Context(0)
     rng = np.random.default_rng(2024)
     stream = torch.cuda.current_stream().cuda_stream
-    # Two calls in a row: the second must not see the first call's leftovers.
-    for n, bits in [(200_003, 45), (5_001, 64)]:
+    # Calls in a row: each must not see the previous call's leftovers. An odd
+    # number of 8-bit passes (17 bits: 3, 40 bits: 5) leaves the result in the
+    # library's array, from where it is copied back; an even number (45 bits:
+    # 6, 64 bits: 8) leaves it in the caller's buffers. The last case fills
+    # the array to its stated maximum.
+    for n, bits in [(200_003, 45), (5_001, 64), (131_071, 17), (77_777, 40),
+                    (N.NOALLOC_SORT_MAX_PAIRS, 64)]:
         keys = _keys(rng, n, bits)
         vals = rng.permutation(n).astype(np.uint32)
         k_ref = torch.from_numpy(keys.view(np.int64)).cuda()
