@@ -134,14 +134,22 @@ typedef struct {
 enum { GS_BLEND_CULLED = 0, GS_BLEND_BASIC = 1, GS_BLEND_CULLED_WIDE = 2, GS_BLEND_CULLED_TILE = 3,
        GS_BLEND_CULLED_8X8 = 4, GS_BLEND_TMA = 5 };
 
-/* Precision of the projected records the blend reads (gs_render,
- * gs_render_backward, gs_render_batch). With F16 / BF16 the opacity and the
- * colour are stored in 16 bits (28-byte records instead of 36 read bytes);
- * the 2D mean and the conic stay FP32, because a 16-bit conic's relative
- * error, multiplied by |power| up to ln 255 at the 1/255 edge, exceeds the
- * image error bound on dense scenes. Values are decoded to FP32 when staged;
- * compositing and transmittance stay FP32. Binning always uses the FP32
- * projection, so the per-tile lists do not change. */
+/* Precision of the blend records gs_render, gs_render_backward and
+ * gs_render_batch write during the projection and the blend reads. Every
+ * record holds, in FP32, the 2D mean, the conic scaled to a base-2 exponent
+ * and the alpha threshold log2(1 / (255 opacity)) of the FP32 opacity, so
+ * every precision takes the same alpha >= 1/255 decisions (a 16-bit conic's
+ * relative error, multiplied by |power| up to ln 255 at the 1/255 edge, would
+ * exceed the image error bound on dense scenes). Opacity and colour:
+ *   F32   FP32 (48-byte records)
+ *   F16   FP16 opacity and colour (36 bytes)
+ *   BF16  FP16 opacity and BF16 colour stored as colour - 1 (36 bytes): the
+ *         offset keeps BF16's rounding error at or below 2^-9 on colours in
+ *         [0, 2), and the opacity needs FP16's 11 significant bits.
+ * With F16 and BF16 the image is within 4e-3 (max abs per channel) of the
+ * exact result. Values are decoded to FP32 when staged; compositing and
+ * transmittance stay FP32. Binning always uses the FP32 projection, so the
+ * per-tile lists do not change. */
 enum { GS_RECORD_F32 = 0, GS_RECORD_F16 = 1, GS_RECORD_BF16 = 2 };
 
 /* Options. gs_default_options() fills the standard values. */

@@ -40,10 +40,10 @@ struct gs_context {
     int last_w = 0, last_h = 0, last_tw = 0, last_th = 0;
     const uint32_t *last_values = nullptr;
     DevBuf d_rec;
-    DevBuf lp_geo, lp_oq, lp_gb;  // reduced-precision blend records
+    DevBuf br_geo, br_aux, br_col;  // blend records of the render path (16 B per slot each)
     // Batched path (own buffers: a captured graph holds their addresses).
     struct Batch {
-        DevBuf views, rec, meta, geo, oq, gb, scratch, ranges, order, queue, keys, vals, akeys, avals, sort;
+        DevBuf views, rec, meta, geo, aux, col, scratch, ranges, order, queue, keys, vals, akeys, avals, sort;
         ViewDesc *h_views = nullptr;
         int h_views_cap = 0;
         int64_t rec_cap = 0, key_cap = 0;
@@ -307,13 +307,36 @@ void mark(gs_context *ctx, int which, cudaStream_t s) {
     if (ctx->timing) cudaEventRecord(ctx->ev[which], s);
 }
 
-RecordReader reader(gs_context *ctx, const gs_record *rec, int dtype) {
+// Record form of the blend records written for record precision dtype.
+int rec_mode(int dtype) {
+    return dtype == GS_RECORD_F16 ? gs::kRecF16 : dtype == GS_RECORD_BF16 ? gs::kRecBF16 : gs::kRecF32;
+}
+
+// The blend records of the render path (or, with raw, caller's gs_records).
+RecordReader reader(gs_context *ctx, const gs_record *rec, int dtype, bool raw = false) {
     RecordReader r;
     r.rec32 = reinterpret_cast<const float4 *>(rec);
-    r.geo = static_cast<const float4 *>(ctx->lp_geo.ptr);
-    r.oq = static_cast<const uint2 *>(ctx->lp_oq.ptr);
-    r.gb = static_cast<const uint32_t *>(ctx->lp_gb.ptr);
-    r.dtype = dtype;
+    r.geo = static_cast<const float4 *>(ctx->br_geo.ptr);
+    r.aux = static_cast<const float4 *>(ctx->br_aux.ptr);
+    r.col = ctx->br_col.ptr;
+    r.mode = raw ? gs::kRecRaw : rec_mode(dtype);
+    return r;
+}
+
+// Where the render path's projection writes its blend records.
+gs::BlendRecordOut blend_out(gs_context *ctx, int dtype) {
+    return gs::BlendRecordOut{static_cast<float4 *>(ctx->br_geo.ptr), static_cast<float4 *>(ctx->br_aux.ptr),
+                              ctx->br_col.ptr, rec_mode(dtype)};
+}
+
+// The blend records of the last joint batch (one per compact record slot).
+RecordReader batch_reader(gs_context *ctx, int dtype) {
+    RecordReader r;
+    r.rec32 = static_cast<const float4 *>(ctx->batch.rec.ptr);
+    r.geo = static_cast<const float4 *>(ctx->batch.geo.ptr);
+    r.aux = static_cast<const float4 *>(ctx->batch.aux.ptr);
+    r.col = ctx->batch.col.ptr;
+    r.mode = rec_mode(dtype);
     return r;
 }
 
@@ -512,9 +535,7 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     mark(ctx, EV_START, s);
     const uint2 *prev_rect = static_cast<const uint2 *>(T.rects[T.rcur].ptr);
     uint2 *rect = static_cast<uint2 *>(T.rects[T.rcur ^ 1].ptr);
-    GS_CUDA(ctx, gs_launch_project_temporal(*g, make_cam(cam), grid, rec, static_cast<float4 *>(ctx->lp_geo.ptr),
-                                            static_cast<uint2 *>(ctx->lp_oq.ptr),
-                                            static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype, prev_rect, rect,
+    GS_CUDA(ctx, gs_launch_project_temporal(*g, make_cam(cam), grid, rec, blend_out(ctx, dtype), prev_rect, rect,
                                             static_cast<uint8_t *>(T.moved.ptr),
                                             static_cast<unsigned long long *>(T.moved_list.ptr), item_cap,
                                             counters, ctx->d_err, s));
@@ -638,7 +659,7 @@ void gs_destroy(gs_context *ctx) {
     DeviceGuard g(ctx->device);
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                       &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
-                      &ctx->fused_scratch, &ctx->d_rec, &ctx->lp_geo, &ctx->lp_oq, &ctx->lp_gb, &ctx->gathered};
+                      &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col, &ctx->gathered};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -652,7 +673,7 @@ void gs_destroy(gs_context *ctx) {
     for (int i = 0; i < EV_COUNT; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     auto &B = ctx->batch;
-    DevBuf *bb[] = {&B.views, &B.rec, &B.meta, &B.geo, &B.oq, &B.gb, &B.scratch, &B.ranges, &B.order,
+    DevBuf *bb[] = {&B.views, &B.rec, &B.meta, &B.geo, &B.aux, &B.col, &B.scratch, &B.ranges, &B.order,
                     &B.queue, &B.keys, &B.vals, &B.akeys, &B.avals, &B.sort, &B.d_rec, &B.bviews};
     for (DevBuf *b : bb)
         if (b->ptr) cudaFree(b->ptr);
@@ -679,7 +700,7 @@ size_t gs_workspace_bytes(const gs_context *ctx) {
     if (!ctx) return 0;
     const DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                             &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch,
-                            &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec, &ctx->lp_geo, &ctx->lp_oq, &ctx->lp_gb};
+                            &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col};
     size_t t = 0;
     for (const DevBuf *b : bufs) t += b->bytes;
     return t;
@@ -769,7 +790,7 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
     DeviceGuard dg(ctx->device);
     if (opts->record_dtype != GS_RECORD_F32)
         return fail(ctx, GS_ERR_UNSUPPORTED, "gs_blend reads FP32 gs_records; use gs_render for F16/BF16");
-    GS_CUDA(ctx, gs_launch_blend(reader(ctx, records, GS_RECORD_F32), values, ranges, make_grid(cam, opts),
+    GS_CUDA(ctx, gs_launch_blend(reader(ctx, records, GS_RECORD_F32, true), values, ranges, make_grid(cam, opts),
                                  cam->width, cam->height, opts->bg, *fb, opts->blend_variant,
                                  static_cast<cudaStream_t>(stream)));
     return GS_OK;
@@ -801,10 +822,9 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     const int sort_passes = tile_passes > 0 ? tile_passes : 1;
     const int key_bytes = tkey_bits <= 16 ? 2 : 4;
     const int dtype = opts->record_dtype;
-    if (dtype != GS_RECORD_F32 &&
-        ((st = ensure(ctx, ctx->lp_geo, (size_t)(n > 0 ? n : 1) * 16, "reduced-precision records")) != GS_OK ||
-         (st = ensure(ctx, ctx->lp_oq, (size_t)(n > 0 ? n : 1) * 8, "reduced-precision records")) != GS_OK ||
-         (st = ensure(ctx, ctx->lp_gb, (size_t)(n > 0 ? n : 1) * 4, "reduced-precision records")) != GS_OK))
+    if ((st = ensure(ctx, ctx->br_geo, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK ||
+        (st = ensure(ctx, ctx->br_aux, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK ||
+        (st = ensure(ctx, ctx->br_col, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK)
         return st;
     if ((st = ensure(ctx, ctx->records, (size_t)(n > 0 ? n : 1) * sizeof(gs_record), "records")) != GS_OK ||
         (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK)
@@ -877,9 +897,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             ev3[1] = ctx->ev[EV_DEPTH];
             ev3[2] = ctx->ev[EV_SCAN];
         }
-        GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, static_cast<float4 *>(ctx->lp_geo.ptr),
-                                           static_cast<uint2 *>(ctx->lp_oq.ptr),
-                                           static_cast<uint32_t *>(ctx->lp_gb.ptr), dtype,
+        GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, blend_out(ctx, dtype),
                                            xy_keys ? akeys : keys, key_bytes, xy_keys, xy_keys ? avals : vals,
                                            cap, ctx->d_counts,
                                            ctx->fused_scratch.ptr, sc, ctx->d_err, s, ev3, prect, prev_rect,
@@ -1036,9 +1054,10 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
     uint32_t *keys = static_cast<uint32_t *>(B.keys.ptr), *akeys = static_cast<uint32_t *>(B.akeys.ptr);
     uint32_t *vals = static_cast<uint32_t *>(B.vals.ptr), *avals = static_cast<uint32_t *>(B.avals.ptr);
     uint2 *meta = static_cast<uint2 *>(B.meta.ptr);
-    GS_CUDA(ctx, gs_launch_project_bin_batch(*g, views, n_views, static_cast<gs_record *>(B.rec.ptr),
-                                             static_cast<float4 *>(B.geo.ptr), static_cast<uint2 *>(B.oq.ptr),
-                                             static_cast<uint32_t *>(B.gb.ptr), dtype, meta, B.rec_cap, keys,
+    gs::BlendRecordOut bro{static_cast<float4 *>(B.geo.ptr), static_cast<float4 *>(B.aux.ptr), B.col.ptr,
+                           rec_mode(dtype)};
+    GS_CUDA(ctx, gs_launch_project_bin_batch(*g, views, n_views, static_cast<gs_record *>(B.rec.ptr), bro, meta,
+                                             B.rec_cap, keys,
                                              vals, B.key_cap, ctx->d_counts, B.scratch.ptr, sc, ctx->d_err, s));
     bool in_alt = false;
     GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, B.key_cap, ctx->d_counts + 2, sc, ctx->d_err,
@@ -1051,12 +1070,7 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
     uint32_t *qs = static_cast<uint32_t *>(B.queue.ptr);
     uint32_t *order = static_cast<uint32_t *>(B.order.ptr);
     GS_CUDA(ctx, gs_launch_queue(ranges, total_tiles, qs, order, s));
-    RecordReader rd;
-    rd.rec32 = static_cast<const float4 *>(B.rec.ptr);
-    rd.geo = static_cast<const float4 *>(B.geo.ptr);
-    rd.oq = static_cast<const uint2 *>(B.oq.ptr);
-    rd.gb = static_cast<const uint32_t *>(B.gb.ptr);
-    rd.dtype = dtype;
+    const RecordReader rd = batch_reader(ctx, dtype);
     GS_CUDA(ctx, gs_launch_blend_batch(rd, sv, ranges, views, n_views, opts->tile_w, opts->tile_h,
                                        opts->batch_depth ? opts->batch_depth : 256, order,
                                        total_tiles, qs + 193, s));
@@ -1139,16 +1153,15 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
     if (B.key_cap == 0) B.key_cap = std::max<int64_t>(int64_t(1) << 22, 4 * B.rec_cap);
     for (int attempt = 0; attempt < 3; ++attempt) {
         const int64_t rc = B.rec_cap, kc = B.key_cap;
-        void *before[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.oq.ptr, B.gb.ptr, B.scratch.ptr,
+        void *before[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.aux.ptr, B.col.ptr, B.scratch.ptr,
                           B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,
                           B.avals.ptr, B.sort.ptr};
-        const bool lp = opts->record_dtype != GS_RECORD_F32;
         if ((st = ensure(ctx, B.views, (size_t)n_views * sizeof(ViewDesc), "view table")) != GS_OK ||
             (st = ensure(ctx, B.rec, (size_t)rc * sizeof(gs_record), "batch records")) != GS_OK ||
             (st = ensure(ctx, B.meta, (size_t)rc * 8, "batch record meta")) != GS_OK ||
-            (lp && (st = ensure(ctx, B.geo, (size_t)rc * 16, "batch records")) != GS_OK) ||
-            (lp && (st = ensure(ctx, B.oq, (size_t)rc * 8, "batch records")) != GS_OK) ||
-            (lp && (st = ensure(ctx, B.gb, (size_t)rc * 4, "batch records")) != GS_OK) ||
+            (st = ensure(ctx, B.geo, (size_t)rc * 16, "batch blend records")) != GS_OK ||
+            (st = ensure(ctx, B.aux, (size_t)rc * 16, "batch blend records")) != GS_OK ||
+            (st = ensure(ctx, B.col, (size_t)rc * 16, "batch blend records")) != GS_OK ||
             (st = ensure(ctx, B.scratch, gs_batch_scratch_bytes(rc, kc, n, n_views), "batch scratch")) != GS_OK ||
             (st = ensure(ctx, B.ranges, (size_t)total_tiles * 8, "batch ranges")) != GS_OK ||
             (st = ensure(ctx, B.order, (size_t)total_tiles * 4, "batch queue")) != GS_OK ||
@@ -1160,7 +1173,7 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
             (st = ensure(ctx, B.sort, gs_sort_scratch_bytes_digits(kc, (bits - 32 + 7) / 8), "batch sort scratch")) !=
                 GS_OK)
             return st;
-        void *after[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.oq.ptr, B.gb.ptr, B.scratch.ptr,
+        void *after[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.aux.ptr, B.col.ptr, B.scratch.ptr,
                          B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,
                          B.avals.ptr, B.sort.ptr};
         std::vector<int64_t> full = sig;
@@ -1264,12 +1277,7 @@ gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const
         GS_CUDA(ctx, cudaMemsetAsync(out->d_opacity_logits, 0, (size_t)n * sizeof(float), s));
         GS_CUDA(ctx, cudaMemsetAsync(out->d_sh, 0, (size_t)n * kS * sizeof(float), s));
     }
-    RecordReader rd;
-    rd.rec32 = static_cast<const float4 *>(B.rec.ptr);
-    rd.geo = static_cast<const float4 *>(B.geo.ptr);
-    rd.oq = static_cast<const uint2 *>(B.oq.ptr);
-    rd.gb = static_cast<const uint32_t *>(B.gb.ptr);
-    rd.dtype = opts->record_dtype;
+    const RecordReader rd = batch_reader(ctx, opts->record_dtype);
     const ViewDesc *views = static_cast<const ViewDesc *>(B.views.ptr);
     GS_CUDA(ctx, gs_launch_blend_bwd_batch(rd, B.joint_values, static_cast<const uint32_t *>(B.ranges.ptr), views,
                                            static_cast<const GsBwdView *>(B.bviews.ptr), n_views, opts->tile_w,

@@ -1,12 +1,13 @@
 // gs_blend.cu — per-tile front-to-back alpha compositing (Eq. 1; Sec. 4.5
 // step 3). One thread block per screen tile. The tile's depth-ordered list
-// is walked in batches staged in shared memory; every record is turned once
-// per block into the form the inner loop wants:
+// is walked in batches staged in shared memory, in the form the inner loop
+// wants (the blend record written by the render path's projection, or the
+// same constants computed from a caller's gs_record):
 //   A, B, C   the conic scaled to the base-2 exponent, so that
 //             power * log2(e) = A dx^2 + B dx dy + C dy^2
 //   thr       log2(1 / (255 opacity)): alpha >= 1/255  <=>  exponent >= thr
 //   box       a conservative bounding box of the pixels where the record can
-//             reach alpha >= 1/255 (used only by the culled variant).
+//             reach alpha >= 1/255 (used only by the culled variants).
 //
 // Variants (identical outputs):
 //  * culled (default): each warp owns an 8x4 pixel block, one pixel per lane;
@@ -27,7 +28,6 @@ namespace {
 
 using namespace gs;
 
-constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kBatch = 256;
 
 struct BlendArgs {
@@ -58,50 +58,25 @@ struct SRec {
     float4 *box;  // (x0, x1, y0, y1) pixel-centre box where alpha can reach 1/255
 };
 
-// Builds the shared form of a record (words r0, r1 and blue of gs_record)
-// at slot s.
-__device__ __forceinline__ void stage_values(const float4 &r0, const float4 &r1, float blue, int s, const SRec &S,
-                                             bool want_box) {
-    const float q00 = r0.z, q01 = r0.w, q11 = r1.x, o = r1.y;
-    const float A = -0.5f * kLog2e * q00, B = -kLog2e * q01, C = -0.5f * kLog2e * q11;
-    const float thr = -log2f(255.f * o);
-    S.a[s] = make_float4(r0.x, r0.y, A, B);
-    S.b[s] = make_float2(C, thr);
-    S.col[s] = make_float4(o, r1.z, r1.w, blue);
+// Builds the shared form of a record at slot s from its blend-record words
+// (geo = u, v, A, B; aux = C, thr, hxy; col = opacity, red, green, blue).
+__device__ __forceinline__ void stage_values(const float4 &geo, const float4 &aux, const float4 &col, int s,
+                                             const SRec &S, bool want_box) {
+    S.a[s] = geo;
+    S.b[s] = make_float2(aux.x, aux.y);
+    S.col[s] = col;
     if (!want_box) return;
-    // alpha >= 1/255 needs (1/2) d^T Q d <= L = ln(255 o). The axis-aligned
-    // box of that ellipse has half-widths sqrt(2 L Sigma00), sqrt(2 L Sigma11)
-    // with Sigma = Q^-1. L is inflated to cover the FP32 evaluation error of
-    // the exponent, which is at most 8 eps kappa |exponent| for a conic of
-    // condition number kappa <= (q00 + q11)^2 / det; det by Kahan's method.
-    const float L = logf(255.f * o);
-    float4 box = make_float4(1.f, -1.f, 1.f, -1.f);  // empty
-    if (L > -1e-4f) {
-        const float w = q01 * q01;
-        const float e = fmaf(-q01, q01, w);
-        const float det = fmaf(q00, q11, -w) + e;
-        if (det > 0.f) {
-            const float tr = q00 + q11;
-            const float kappa = tr * tr / det;
-            const float Lp = (fmaxf(L, 0.f) + 1e-4f) * (1.f + 64.f * 1.2e-7f * kappa);
-            const float hx = sqrtf(2.f * Lp * (q11 / det)) * 1.0001f + 1e-3f;
-            const float hy = sqrtf(2.f * Lp * (q00 / det)) * 1.0001f + 1e-3f;
-            box = make_float4(r0.x - hx, r0.x + hx, r0.y - hy, r0.y + hy);
-            if (!(hx < 3e38f) || !(hy < 3e38f)) box = make_float4(-3e38f, 3e38f, -3e38f, 3e38f);
-        } else {
-            box = make_float4(-3e38f, 3e38f, -3e38f, 3e38f);  // cannot bound: never cull
-        }
-    }
-    S.box[s] = box;
+    const float2 h = blend_box_half(aux.z);
+    S.box[s] = make_float4(geo.x - h.x, geo.x + h.x, geo.y - h.y, geo.y + h.y);
 }
 
-// Builds the shared form of record g at slot s.
+// Builds the shared form of record g at slot s (RAW: from a gs_record).
+template <bool RAW = false>
 __device__ __forceinline__ void stage_record(const RecordReader &rd, uint32_t g, int s,
                                              const SRec &S, bool want_box) {
-    float4 r0, r1;
-    float blue;
-    rd.load(g, r0, r1, blue);
-    stage_values(r0, r1, blue, s, S, want_box);
+    float4 geo, aux, col;
+    rd.load<RAW>(g, geo, aux, col);
+    stage_values(geo, aux, col, s, S, want_box);
 }
 
 // Can a record reach alpha >= 1/255 at some pixel centre of the rectangle
@@ -173,7 +148,7 @@ __device__ __forceinline__ void write_pixel(const BlendArgs &a, int px, int py, 
 // 8x8 blocks (default) cull finely; wider blocks amortise each record's
 // ballot, shared-memory reads and x terms over more pixels.
 // ---------------------------------------------------------------------------
-template <int TW, int TH, int BW, int BH, int DEPTH = kBatch>
+template <int TW, int TH, int BW, int BH, int DEPTH = kBatch, bool RAW = false>
 __device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) {
     constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
     constexpr int kRows = 32 / BW;     // rows covered by the warp's lanes at once
@@ -206,7 +181,7 @@ __device__ __forceinline__ void blend_tile_culled(const BlendArgs &a, int tile) 
         if (__syncthreads_count(warp_done) == kThreads) break;
         for (int s = tid; s < DEPTH; s += kThreads) {
             const uint32_t k = start + s;
-            if (k < last) stage_record(a.rd, a.values[k], s, S, true);
+            if (k < last) stage_record<RAW>(a.rd, a.values[k], s, S, true);
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)DEPTH, last - start);
@@ -257,11 +232,11 @@ constexpr int blend_min_blocks(int warps, int pixels_per_lane) {
     return pixels_per_lane != 2 ? 1 : (36 / warps < 32 ? 36 / warps : 32);  // at most 32 blocks per SM
 }
 
-template <int TW, int TH, int BW, int BH>
+template <int TW, int TH, int BW, int BH, bool RAW>
 __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32,
                                   blend_min_blocks((TW / BW) * (TH / BH), BW * BH / 32))
     blend_culled_kernel(const BlendArgs a) {
-    blend_tile_culled<TW, TH, BW, BH>(a, blockIdx.x);
+    blend_tile_culled<TW, TH, BW, BH, kBatch, RAW>(a, blockIdx.x);
 }
 
 // Persistent blend over many views: blocks take global tiles from a queue
@@ -300,10 +275,10 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(c
 }
 
 // ---------------------------------------------------------------------------
-// Bulk-copy variant. A gather kernel writes each key's record (decoded to
-// FP32, 48 bytes) in list order, so a tile's records are contiguous; the
-// blend stages them 128 at a time with one cp.async.bulk copy into shared
-// memory, double-buffered (the copy of batch b + 1 overlaps batch b), each
+// Bulk-copy variant. A gather kernel writes each key's blend record (decoded
+// to FP32: geo, aux, col; 48 bytes) in list order, so a tile's records are
+// contiguous; the blend stages them 128 at a time with one cp.async.bulk
+// copy into shared memory, double-buffered (the copy of batch b + 1 overlaps batch b), each
 // completing on an mbarrier. The compute is the culled schedule's, so the
 // outputs are identical. Every wait is bounded in time and sets the error
 // word instead of hanging; a block waits for its copies in flight before it
@@ -317,12 +292,11 @@ __global__ void __launch_bounds__(256) gather_records_kernel(RecordReader rd, co
     const int64_t n = d_n ? (int64_t)*d_n : n_cap;
     for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x; k < n && k < n_cap;
          k += (int64_t)gridDim.x * 256) {
-        float4 r0, r1;
-        float blue;
-        rd.load(values[k], r0, r1, blue);
-        out[3 * k] = r0;
-        out[3 * k + 1] = r1;
-        out[3 * k + 2] = make_float4(blue, 0.f, 0.f, 0.f);
+        float4 geo, aux, col;
+        rd.load(values[k], geo, aux, col);
+        out[3 * k] = geo;
+        out[3 * k + 1] = aux;
+        out[3 * k + 2] = col;
     }
 }
 
@@ -425,7 +399,7 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32)
         const int cnt = min(kTmaBatch, n_list - b * kTmaBatch);
         for (int s = tid; s < cnt; s += kThreads) {
             const float4 *r = &s_raw[b & 1][3 * s];
-            stage_values(r[0], r[1], r[2].x, s, S, true);
+            stage_values(r[0], r[1], r[2], s, S, true);
         }
         __syncthreads();
         const int32_t pos0 = b * kTmaBatch + 1;
@@ -471,7 +445,7 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32)
 // ---------------------------------------------------------------------------
 // Basic variant: one thread per pixel, every record evaluated.
 // ---------------------------------------------------------------------------
-template <int TW, int TH>
+template <int TW, int TH, bool RAW>
 __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) {
     constexpr int kN = TW * TH;
     __shared__ float4 s_a[kBatch], s_col[kBatch];
@@ -490,7 +464,7 @@ __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) 
         if (__syncthreads_count(p.done) == kN) break;
         for (int s = tid; s < kBatch; s += kN) {
             const uint32_t k = start + s;
-            if (k < last) stage_record(a.rd, a.values[k], s, S, false);
+            if (k < last) stage_record<RAW>(a.rd, a.values[k], s, S, false);
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)kBatch, last - start);
@@ -563,32 +537,42 @@ cudaError_t gs_launch_blend_tma(const RecordReader &rd, const uint32_t *values, 
     return cudaGetLastError();
 }
 
+namespace {
+template <bool RAW>
+void launch_blend_variant(const BlendArgs &a, const GsGrid &grid, int variant, cudaStream_t s) {
+    const unsigned blocks = (unsigned)(grid.tiles_x * grid.tiles_y);
+    const int tw = grid.tile_w, th = grid.tile_h;
+    if (variant == GS_BLEND_BASIC) {
+        if (tw == 16 && th == 16) blend_basic_kernel<16, 16, RAW><<<blocks, 256, 0, s>>>(a);
+        else if (tw == 16 && th == 8) blend_basic_kernel<16, 8, RAW><<<blocks, 128, 0, s>>>(a);
+        else blend_basic_kernel<8, 8, RAW><<<blocks, 64, 0, s>>>(a);
+    } else if (variant == GS_BLEND_CULLED_WIDE && tw == 16) {
+        if (th == 16) blend_culled_kernel<16, 16, 16, 8, RAW><<<blocks, 64, 0, s>>>(a);
+        else blend_culled_kernel<16, 8, 16, 8, RAW><<<blocks, 32, 0, s>>>(a);
+    } else if (variant == GS_BLEND_CULLED_TILE && tw == 16 && th == 16) {
+        blend_culled_kernel<16, 16, 16, 16, RAW><<<blocks, 32, 0, s>>>(a);
+    } else if (variant == GS_BLEND_CULLED_8X8) {
+        if (tw == 16 && th == 16) blend_culled_kernel<16, 16, 8, 8, RAW><<<blocks, 128, 0, s>>>(a);
+        else if (tw == 16 && th == 8) blend_culled_kernel<16, 8, 8, 8, RAW><<<blocks, 64, 0, s>>>(a);
+        else blend_culled_kernel<8, 8, 8, 8, RAW><<<blocks, 32, 0, s>>>(a);
+    } else {
+        // GS_BLEND_CULLED (8x4 blocks), and the wide variants on tiles they do not divide
+        if (tw == 16 && th == 16) blend_culled_kernel<16, 16, 8, 4, RAW><<<blocks, 256, 0, s>>>(a);
+        else if (tw == 16 && th == 8) blend_culled_kernel<16, 8, 8, 4, RAW><<<blocks, 128, 0, s>>>(a);
+        else blend_culled_kernel<8, 8, 8, 4, RAW><<<blocks, 64, 0, s>>>(a);
+    }
+}
+}  // namespace
+
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s) {
     BlendArgs a{rd, values, ranges, grid, width, height,
                 {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
-    const unsigned blocks = (unsigned)(grid.tiles_x * grid.tiles_y);
-    const int tw = grid.tile_w, th = grid.tile_h;
-    if (variant == GS_BLEND_BASIC) {
-        if (tw == 16 && th == 16) blend_basic_kernel<16, 16><<<blocks, 256, 0, s>>>(a);
-        else if (tw == 16 && th == 8) blend_basic_kernel<16, 8><<<blocks, 128, 0, s>>>(a);
-        else blend_basic_kernel<8, 8><<<blocks, 64, 0, s>>>(a);
-    } else if (variant == GS_BLEND_CULLED_WIDE && tw == 16) {
-        if (th == 16) blend_culled_kernel<16, 16, 16, 8><<<blocks, 64, 0, s>>>(a);
-        else blend_culled_kernel<16, 8, 16, 8><<<blocks, 32, 0, s>>>(a);
-    } else if (variant == GS_BLEND_CULLED_TILE && tw == 16 && th == 16) {
-        blend_culled_kernel<16, 16, 16, 16><<<blocks, 32, 0, s>>>(a);
-    } else if (variant == GS_BLEND_CULLED_8X8) {
-        if (tw == 16 && th == 16) blend_culled_kernel<16, 16, 8, 8><<<blocks, 128, 0, s>>>(a);
-        else if (tw == 16 && th == 8) blend_culled_kernel<16, 8, 8, 8><<<blocks, 64, 0, s>>>(a);
-        else blend_culled_kernel<8, 8, 8, 8><<<blocks, 32, 0, s>>>(a);
-    } else {
-        // GS_BLEND_CULLED (8x4 blocks), and the wide variants on tiles they do not divide
-        if (tw == 16 && th == 16) blend_culled_kernel<16, 16, 8, 4><<<blocks, 256, 0, s>>>(a);
-        else if (tw == 16 && th == 8) blend_culled_kernel<16, 8, 8, 4><<<blocks, 128, 0, s>>>(a);
-        else blend_culled_kernel<8, 8, 8, 4><<<blocks, 64, 0, s>>>(a);
-    }
+    // Caller-provided gs_records (the stage API) get the per-key constants
+    // computed while staging; the render path's blend records carry them.
+    if (rd.mode == kRecRaw) launch_blend_variant<true>(a, grid, variant, s);
+    else launch_blend_variant<false>(a, grid, variant, s);
     return cudaGetLastError();
 }
 

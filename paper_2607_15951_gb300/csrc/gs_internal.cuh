@@ -167,48 +167,176 @@ __device__ __forceinline__ Rect tile_rect(float u, float v, int r, int tw, int t
     return R;
 }
 
-// Compact reduced-precision blend record (structure of arrays, 28 bytes):
-//   geo  float4  (u, v, Q00, Q01)          FP32
-//   oq   uint2   (Q11 as FP32 bits, 16-bit pair (opacity, red))
-//   gb   uint32  16-bit pair (green, blue)
-// The 2D mean and the conic stay FP32: the exponent's error is the conic's
-// relative error times |power| (up to ln 255 at the 1/255 edge), which with
-// 16-bit conics exceeds the image bound on dense scenes.
-__device__ __forceinline__ uint32_t pack2(float a, float b, int dtype) {
-    if (dtype == GS_RECORD_BF16) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<const uint32_t *>(&h);
+// What the blend needs of a record, computed once per visible Gaussian by
+// the render path's projections (and per staged key when the blend reads
+// caller-provided gs_records):
+//   A, B, C  the conic scaled to the base-2 exponent,
+//            power * log2(e) = A dx^2 + B dx dy + C dy^2;
+//   thr      log2(1 / (255 opacity)) of the FP32 opacity: alpha >= 1/255
+//            <=> exponent >= thr, so every record precision takes the alpha
+//            decisions of the FP32 path;
+//   hxy      half-widths (hx, hy) of a conservative box around the mean
+//            outside which alpha < 1/255, two FP16 rounded up (+inf: never
+//            cull; -inf: alpha never reaches 1/255).
+// alpha >= 1/255 needs (1/2) d^T Q d <= L = ln(255 o); that ellipse's
+// axis-aligned box has half-widths sqrt(2 L Sigma00), sqrt(2 L Sigma11) with
+// Sigma = Q^-1. L is inflated to cover the FP32 evaluation error of the
+// exponent, at most 8 eps kappa |exponent| for a conic of condition number
+// kappa <= (q00 + q11)^2 / det (det by Kahan's method).
+struct BlendPre {
+    float A, B, C, thr;
+    uint32_t hxy;
+};
+
+constexpr float kLog2eF = 1.4426950408889634f;
+
+__device__ __forceinline__ BlendPre blend_pre(float q00, float q01, float q11, float o) {
+    BlendPre p;
+    p.A = -0.5f * kLog2eF * q00;
+    p.B = -kLog2eF * q01;
+    p.C = -0.5f * kLog2eF * q11;
+    p.thr = -log2f(255.f * o);
+    const float L = logf(255.f * o);
+    float hx = -INFINITY, hy = -INFINITY;  // alpha never reaches 1/255
+    if (L > -1e-4f) {
+        hx = hy = INFINITY;  // cannot bound: never cull
+        const float w = q01 * q01;
+        const float e = fmaf(-q01, q01, w);
+        const float det = fmaf(q00, q11, -w) + e;
+        if (det > 0.f) {
+            const float tr = q00 + q11;
+            const float kappa = tr * tr / det;
+            const float Lp = (fmaxf(L, 0.f) + 1e-4f) * (1.f + 64.f * 1.2e-7f * kappa);
+            const float bx = sqrtf(2.f * Lp * (q11 / det)) * 1.0001f + 1e-3f;
+            const float by = sqrtf(2.f * Lp * (q00 / det)) * 1.0001f + 1e-3f;
+            if (bx < 3e38f && by < 3e38f) {
+                hx = bx;
+                hy = by;
+            }
+        }
     }
+    const __half2 h = __halves2half2(__float2half_ru(hx), __float2half_ru(hy));
+    p.hxy = *reinterpret_cast<const uint32_t *>(&h);
+    return p;
+}
+
+// Record forms the blend can read (RecordReader::mode). The render path
+// writes a blend record of three arrays per visible Gaussian (or per record
+// slot of a batch):
+//   geo  float4  (u, v, A, B)
+//   aux  float4  (C, thr, hxy bits, w)
+//   col  kRecF32:  float4 (red, green, blue, 0), w = opacity (48 bytes);
+//        kRecF16:  uint32 FP16 pair (green, blue), w = FP16 pair (opacity,
+//                  red) (36 bytes);
+//        kRecBF16: uint32 BF16 pair (green - 1, blue - 1), w = (FP16
+//                  opacity, BF16 red - 1) (36 bytes).
+// The 2D mean, the conic and the alpha threshold stay FP32: the exponent's
+// error is the conic's relative error times |power| (up to ln 255 at the
+// 1/255 edge), which with 16-bit conics exceeds the image bound on dense
+// scenes. With BF16 colours the opacity is FP16 (a product o G needs more
+// than BF16's 8 significant bits to stay within the image bound) and the
+// colours are stored less 1: colours lie in [0, 2) in practice, where
+// c - 1 in [-1, 1) keeps BF16's rounding error at or below 2^-9, half of
+// what c itself would get in [1, 2). kRecRaw reads gs_records (the stage
+// API's blend input) and computes the constants per staged key.
+enum : int { kRecRaw = 0, kRecF32 = 1, kRecF16 = 2, kRecBF16 = 3 };
+
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
     const __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-__device__ __forceinline__ float2 unpack2(uint32_t w, int dtype) {
-    if (dtype == GS_RECORD_BF16) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
-    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+__device__ __forceinline__ uint32_t pack_bf16x2_less1(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a - 1.f, b - 1.f);
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// What the blend kernels read of a record, in either precision.
-struct RecordReader {
-    const float4 *rec32;  // gs_record array (FP32)
-    const float4 *geo;    // reduced precision: (u, v, Q00, Q01)
-    const uint2 *oq;      // (Q11 bits, opacity | red)
-    const uint32_t *gb;   // green | blue
-    int dtype;            // GS_RECORD_*
-    __device__ __forceinline__ void load(uint32_t g, float4 &r0, float4 &r1, float &blue) const {
-        if (dtype == GS_RECORD_F32) {
-            r0 = __ldg(rec32 + 3 * (size_t)g);
-            r1 = __ldg(rec32 + 3 * (size_t)g + 1);
-            blue = __ldg(reinterpret_cast<const float *>(rec32 + 3 * (size_t)g + 2));
-            return;
+// w word of aux and the col word of the 16-bit forms.
+__device__ __forceinline__ uint32_t pack_op_red(float o, float r, int mode) {
+    if (mode == kRecBF16) {
+        const __half ho = __float2half_rn(o);
+        const __nv_bfloat16 br = __float2bfloat16_rn(r - 1.f);
+        return (uint32_t)*reinterpret_cast<const uint16_t *>(&ho) |
+               ((uint32_t)*reinterpret_cast<const uint16_t *>(&br) << 16);
+    }
+    return pack_f16x2(o, r);
+}
+
+__device__ __forceinline__ uint32_t pack_green_blue(float g, float b, int mode) {
+    return mode == kRecBF16 ? pack_bf16x2_less1(g, b) : pack_f16x2(g, b);
+}
+
+// Writes blend record slot j (geo, aux, col) from the gs_record words
+// (r0 = u, v, Q00, Q01; Q11; opacity; red, green, blue).
+struct BlendRecordOut {
+    float4 *geo;
+    float4 *aux;
+    void *col;  // float4 (kRecF32) or uint32 (16-bit forms)
+    int mode;   // kRecF32, kRecF16 or kRecBF16
+    __device__ __forceinline__ void write(size_t j, const float4 &r0, float q11, float o, float r, float g,
+                                          float b) const {
+        const BlendPre p = blend_pre(r0.z, r0.w, q11, o);
+        geo[j] = make_float4(r0.x, r0.y, p.A, p.B);
+        if (mode == kRecF32) {
+            aux[j] = make_float4(p.C, p.thr, __uint_as_float(p.hxy), o);
+            static_cast<float4 *>(col)[j] = make_float4(r, g, b, 0.f);
+        } else {
+            aux[j] = make_float4(p.C, p.thr, __uint_as_float(p.hxy), __uint_as_float(pack_op_red(o, r, mode)));
+            static_cast<uint32_t *>(col)[j] = pack_green_blue(g, b, mode);
         }
-        r0 = __ldg(geo + g);
-        const uint2 w = __ldg(oq + g);
-        const float2 orr = unpack2(w.y, dtype), gbb = unpack2(__ldg(gb + g), dtype);
-        r1 = make_float4(__uint_as_float(w.x), orr.x, orr.y, gbb.x);
-        blue = gbb.y;
     }
 };
+
+// What the blend kernels read of a record, in any form: geo = (u, v, A, B),
+// aux = (C, thr, hxy bits, -), col = (opacity, red, green, blue).
+struct RecordReader {
+    const float4 *rec32;  // kRecRaw: gs_record array
+    const float4 *geo;
+    const float4 *aux;
+    const void *col;
+    int mode;
+    // Any form (RAW: the caller guarantees mode == kRecRaw; kernels that only
+    // ever read blend records instantiate RAW = false and carry no code for
+    // the per-key constants).
+    template <bool RAW = false>
+    __device__ __forceinline__ void load(uint32_t g, float4 &og, float4 &oa, float4 &oc) const {
+        if (RAW) {
+            const float4 r0 = __ldg(rec32 + 3 * (size_t)g);
+            const float4 r1 = __ldg(rec32 + 3 * (size_t)g + 1);
+            const float blue = __ldg(reinterpret_cast<const float *>(rec32 + 3 * (size_t)g + 2));
+            const BlendPre p = blend_pre(r0.z, r0.w, r1.x, r1.y);
+            og = make_float4(r0.x, r0.y, p.A, p.B);
+            oa = make_float4(p.C, p.thr, __uint_as_float(p.hxy), 0.f);
+            oc = make_float4(r1.y, r1.z, r1.w, blue);
+            return;
+        }
+        og = __ldg(geo + g);
+        oa = __ldg(aux + g);
+        if (mode == kRecF32) {
+            const float4 c = __ldg(static_cast<const float4 *>(col) + g);
+            oc = make_float4(oa.w, c.x, c.y, c.z);
+            return;
+        }
+        const uint32_t w = __float_as_uint(oa.w), gb = __ldg(static_cast<const uint32_t *>(col) + g);
+        if (mode == kRecBF16) {
+            const __half ho = *reinterpret_cast<const __half *>(&w);
+            const uint32_t rb = w >> 16;
+            const float red = __uint_as_float(rb << 16) + 1.f;  // BF16 -> FP32 is a shift
+            const float green = __uint_as_float(gb << 16) + 1.f, blue = __uint_as_float(gb & 0xffff0000u) + 1.f;
+            oc = make_float4(__half2float(ho), red, green, blue);
+        } else {
+            const float2 orr = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+            const float2 gbb = __half22float2(*reinterpret_cast<const __half2 *>(&gb));
+            oc = make_float4(orr.x, orr.y, gbb.x, gbb.y);
+        }
+    }
+};
+
+// Half-widths of a blend record's box (hxy bits of aux.z).
+__device__ __forceinline__ float2 blend_box_half(float hxy_bits) {
+    const uint32_t w = __float_as_uint(hxy_bits);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
 
 // Records as three float4s (the gs_record layout):
 //   r0 = (u, v, Q00, Q01), r1 = (Q11, opacity, red, green),
@@ -389,8 +517,7 @@ cudaError_t gs_launch_ranges_tiles(const void *keys, int key_bytes, int64_t n_ca
                                    const unsigned long long *d_n, int32_t n_tiles, uint32_t *ranges,
                                    uint32_t *d_err, cudaStream_t s, int xy_tiles_x = 0);
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
-                                  gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
-                                  int lp_dtype,
+                                  gs_record *records, const gs::BlendRecordOut &br,
                                   void *keys, int key_bytes, bool xy_keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
@@ -406,8 +533,7 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
 // Gaussian's two rects) and counters (zeroed): [0] visible << 33 | keys,
 // [1] moved Gaussians, [2] work items.
 cudaError_t gs_launch_project_temporal(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
-                                       gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
-                                       int lp_dtype, const uint2 *prev_rect, uint2 *rect, uint8_t *moved,
+                                       gs_record *records, const gs::BlendRecordOut &br, const uint2 *prev_rect, uint2 *rect, uint8_t *moved,
                                        unsigned long long *items, int64_t item_capacity,
                                        unsigned long long *counters, uint32_t *d_err, cudaStream_t s);
 struct GsTemporalRebin {
@@ -462,8 +588,7 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
 // gs_launch_project_bin, with [1] = records used.
 size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity, int64_t n, int n_views);
 cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
-                                        gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
-                                        int lp_dtype, uint2 *meta, int64_t rec_capacity, uint32_t *keys,
+                                        gs_record *records, const gs::BlendRecordOut &br, uint2 *meta, int64_t rec_capacity, uint32_t *keys,
                                         uint32_t *values, int64_t key_capacity, unsigned long long *counts,
                                         void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s);
 // Persistent blend over a queue of global tiles (largest lists first).

@@ -303,10 +303,7 @@ constexpr int kProjBlock = 256 * kProjPer;        // ... and per block (one list
 
 struct ListArgs {
     ProjectArgs P;
-    float4 *lp_geo;              // optional reduced-precision blend records
-    uint2 *lp_oq;
-    uint32_t *lp_gb;
-    int lp_dtype;
+    BlendRecordOut br;           // blend records of the visible Gaussians (geo null: none)
     unsigned long long *packed;  // visible << 33 | keys
     uint2 *seg;                  // per block: (first list slot, visible count)
     uint32_t *seg_dst;           // per block: first slot of its segment in index order
@@ -531,7 +528,6 @@ __global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) 
         S.tiles[c] = pr.tiles;
         if (pr.tiles) {
             A.P.records[3 * g] = pr.r0;
-            if (A.lp_geo) A.lp_geo[g] = pr.r0;
             if (A.xy_keys) count_rect_digits(s_th, pr.rect, A.tile_passes);
             S.dbits[c] = __float_as_uint(pr.r2.y);
             S.qa[c] = pr.r1.x;
@@ -613,10 +609,9 @@ __global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) 
         float4 *out = A.P.records + 3 * g;
         out[1] = r1;
         out[2] = r2;
-        if (A.lp_geo) {
-            A.lp_oq[g] = make_uint2(__float_as_uint(r1.x), pack2(r1.y, r1.z, A.lp_dtype));
-            A.lp_gb[g] = pack2(r1.w, r2.x, A.lp_dtype);
-        }
+        // Word r0 was written by this thread in the projection loop above
+        // (same candidate-to-thread mapping).
+        if (A.br.geo) A.br.write(g, out[0], r1.x, r1.y, rgb.x, rgb.y, rgb.z);
     }
     if (!s_last) return;
     // Last block: every block's counts and list entries are in.
@@ -653,10 +648,7 @@ __global__ void __launch_bounds__(256) list_gather_kernel(const uint2 *__restric
 // ---------------------------------------------------------------------------
 struct TemporalProjectArgs {
     ProjectArgs P;
-    float4 *lp_geo;
-    uint2 *lp_oq;
-    uint32_t *lp_gb;
-    int lp_dtype;
+    BlendRecordOut br;             // blend records (geo null: none)
     const uint2 *prev_rect;        // n: previous frame's packed rects
     uint2 *rect;                   // n: this frame's
     uint8_t *moved;                // n: 1 if the rect changed
@@ -683,11 +675,7 @@ __global__ void __launch_bounds__(256) project_temporal_kernel(const TemporalPro
         out[0] = pr.r0;
         out[1] = pr.r1;
         out[2] = pr.r2;
-        if (A.lp_geo) {
-            A.lp_geo[i] = pr.r0;
-            A.lp_oq[i] = make_uint2(__float_as_uint(pr.r1.x), pack2(pr.r1.y, pr.r1.z, A.lp_dtype));
-            A.lp_gb[i] = pack2(pr.r1.w, pr.r2.x, A.lp_dtype);
-        }
+        if (A.br.geo) A.br.write(i, pr.r0, pr.r1.x, pr.r1.y, pr.r1.z, pr.r1.w, pr.r2.x);
     }
     bool mv = false;
     uint32_t chunks = 0;  // work items: one per kChunkTiles tiles of the larger rect
@@ -1124,10 +1112,7 @@ struct ListBatchArgs {
     ProjectArgs P;               // scene arrays (cam / grid unused; records compact)
     bool views_fast;             // grid (views, ranges) rather than (ranges, views)
     const ViewDesc *views;
-    float4 *lp_geo;
-    uint2 *lp_oq;
-    uint32_t *lp_gb;
-    int lp_dtype;
+    BlendRecordOut br;             // blend records (geo null: none)
     uint2 *meta;
     int64_t rec_capacity;
     unsigned long long *packed;  // records << 33 | keys
@@ -1256,7 +1241,6 @@ __global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBa
                 const bool fits = (int64_t)j < A.rec_capacity;
                 if (fits) {
                     A.P.records[3 * j] = S.r0[c];
-                    if (A.lp_geo) A.lp_geo[j] = S.r0[c];
                     A.meta[j] = make_uint2((uint32_t)view, (uint32_t)(i0 + S.cand[c0 + c]));
                     A.lkeys[j] = ((uint64_t)t << 32) | dbits;
                     A.lvals[j] = (uint32_t)j;
@@ -1283,10 +1267,7 @@ __global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBa
             float4 *out = A.P.records + 3 * (size_t)slot;
             out[1] = r1;
             out[2] = r2;
-            if (A.lp_geo) {
-                A.lp_oq[slot] = make_uint2(__float_as_uint(r1.x), pack2(r1.y, r1.z, A.lp_dtype));
-                A.lp_gb[slot] = pack2(r1.w, r2.x, A.lp_dtype);
-            }
+            if (A.br.geo) A.br.write(slot, S.r0[c], r1.x, r1.y, rgb.x, rgb.y, rgb.z);
         }
         __syncthreads();
     }
@@ -1448,8 +1429,7 @@ size_t gs_key_block_bytes(int64_t capacity) {
 }
 
 cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
-                                  gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
-                                  int lp_dtype,
+                                  gs_record *records, const gs::BlendRecordOut &br,
                                   void *keys, int key_bytes, bool xy_keys, uint32_t *values,
                                   int64_t capacity, unsigned long long *counts, void *scan_scratch,
                                   const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s,
@@ -1470,10 +1450,7 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
                       reinterpret_cast<float4 *>(records), nullptr,
                       reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
                       reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
-    A.lp_geo = lp_dtype == GS_RECORD_F32 ? nullptr : lp_geo;
-    A.lp_oq = lp_oq;
-    A.lp_gb = lp_gb;
-    A.lp_dtype = lp_dtype;
+    A.br = br;
     A.packed = reinterpret_cast<unsigned long long *>(base);
     A.seg = reinterpret_cast<uint2 *>(base + L.seg);
     A.seg_dst = reinterpret_cast<uint32_t *>(base + L.seg_dst);
@@ -1512,8 +1489,7 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
 }
 
 cudaError_t gs_launch_project_temporal(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
-                                       gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
-                                       int lp_dtype, const uint2 *prev_rect, uint2 *rect, uint8_t *moved,
+                                       gs_record *records, const gs::BlendRecordOut &br, const uint2 *prev_rect, uint2 *rect, uint8_t *moved,
                                        unsigned long long *items, int64_t item_capacity,
                                        unsigned long long *counters, uint32_t *d_err, cudaStream_t s) {
     if (g.n == 0) return cudaSuccess;
@@ -1522,10 +1498,7 @@ cudaError_t gs_launch_project_temporal(const gs_gaussians &g, const GsCameraDev 
                       reinterpret_cast<float4 *>(records), nullptr,
                       reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
                       reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
-    A.lp_geo = lp_dtype == GS_RECORD_F32 ? nullptr : lp_geo;
-    A.lp_oq = lp_oq;
-    A.lp_gb = lp_gb;
-    A.lp_dtype = lp_dtype;
+    A.br = br;
     A.prev_rect = prev_rect;
     A.rect = rect;
     A.moved = moved;
@@ -1890,8 +1863,7 @@ size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity, int64_
 }
 
 cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *views_dev, int n_views,
-                                        gs_record *records, float4 *lp_geo, uint2 *lp_oq, uint32_t *lp_gb,
-                                        int lp_dtype, uint2 *meta, int64_t rec_capacity, uint32_t *keys,
+                                        gs_record *records, const gs::BlendRecordOut &br, uint2 *meta, int64_t rec_capacity, uint32_t *keys,
                                         uint32_t *values, int64_t key_capacity, unsigned long long *counts,
                                         void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(counts, 0, 5 * sizeof(unsigned long long), s);
@@ -1907,10 +1879,7 @@ cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *v
                       reinterpret_cast<uintptr_t>(g.sh) % 16 == 0,
                       reinterpret_cast<uintptr_t>(g.quats) % 16 == 0};
     A.views = views_dev;
-    A.lp_geo = lp_dtype == GS_RECORD_F32 ? nullptr : lp_geo;
-    A.lp_oq = lp_oq;
-    A.lp_gb = lp_gb;
-    A.lp_dtype = lp_dtype;
+    A.br = br;
     A.meta = meta;
     A.rec_capacity = rec_capacity;
     A.packed = reinterpret_cast<unsigned long long *>(base);

@@ -25,7 +25,7 @@ import paper_2607_15951_gb300 as gs  # noqa: E402
 from paper_2607_15951_gb300 import _native as N  # noqa: E402
 from paper_2607_15951_gb300 import scenes  # noqa: E402
 
-from parity_util import compare_image  # noqa: E402
+from parity_util import compare_render  # noqa: E402
 
 # Stated bound for 16-bit records (max abs per channel on non-cutoff pixels).
 LOW_PRECISION_BOUND = 4e-3
@@ -74,8 +74,8 @@ def test_long_list_sort_matches_stable_sort(ctx, n, bits):
 
 
 def _oracle_view(oracle_mod, scene, cam, rgb, T):
-    _, _, img = oracle_mod.render(scene, cam)
-    st = compare_image(rgb.cpu().numpy(), T.cpu().numpy(), img)
+    pr, bn, img = oracle_mod.render(scene, cam)
+    st = compare_render(rgb.cpu().numpy(), T.cpu().numpy(), pr, bn, img, cam.width, cam.height)
     st.pop("keep")
     return st
 
