@@ -170,8 +170,24 @@ typedef struct {
     int32_t batch_depth;    /* gs_render_batch, joint schedule: records staged
                                per shared-memory batch of the blend, 64, 128
                                or 256 (0 = 256)                                */
-    int32_t reserved[1];    /* must be zero                                    */
+    int32_t cluster;        /* gs_render (and gs_render_batch, which then
+                               renders view by view): thread-block clusters of
+                               the blend, see GS_CLUSTER_*; 16x16 tiles only */
 } gs_options;
+
+/* Thread-block clusters of the blend (gs_options.cluster; Sec. 4.4 and 5.5
+ * of the paper share Gaussians between neighbouring screen tiles instead of
+ * routing them to each tile). With 2 or 4 the per-tile lists are built for
+ * list tiles of 2 x 1 or 2 x 2 screen tiles (32 x 16 or 32 x 32 pixels, so a
+ * splat spanning them is listed once instead of two or four times), and the
+ * thread blocks of one list tile run as one cluster: each stages a share of
+ * every batch of records into its shared memory and the others copy the
+ * records that reach their tile from it (distributed shared memory), so a
+ * record is read from L2 once per cluster. Colours and transmittance equal
+ * those of 16x16 lists bit for bit; n_contrib and n_eval count positions in
+ * the list tile's list (gs_render_backward accepts them). Not with temporal
+ * re-binning. */
+enum { GS_CLUSTER_NONE = 0, GS_CLUSTER_2X1 = 2, GS_CLUSTER_2X2 = 4 };
 
 /* How gs_render_batch schedules the views. JOINT: one projection, one key
  * sort and one persistent blend over all views (pays off for many short

@@ -63,7 +63,8 @@ def camera_struct(cam) -> N.gs_camera:
 
 
 def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
-                   blend_variant: int = 0, deferred: bool = False, temporal: bool = False) -> N.gs_options:
+                   blend_variant: int = 0, deferred: bool = False, temporal: bool = False,
+                   cluster: int = 0) -> N.gs_options:
     o = N.gs_options()
     _lib().gs_default_options(ctypes.byref(o))
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
@@ -73,6 +74,7 @@ def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
     o.blend_variant = int(blend_variant)
     o.sync_mode = N.GS_SYNC_DEFERRED if deferred else N.GS_SYNC_FRAME
     o.temporal = 1 if temporal else 0
+    o.cluster = int(cluster)
     return o
 
 
@@ -203,12 +205,14 @@ def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_co
 
 def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
               n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
-              record_dtype: int = 0, deferred: bool = False, temporal: bool = False, stream=None) -> None:
+              record_dtype: int = 0, deferred: bool = False, temporal: bool = False, cluster: int = 0,
+              stream=None) -> None:
     """deferred=True: GS_SYNC_DEFERRED (no host synchronisation; an overflow
     or device error is raised by a later call on the context).
-    temporal=True: re-bin from the previous frame's lists (same results)."""
+    temporal=True: re-bin from the previous frame's lists (same results).
+    cluster: GS_CLUSTER_2X1 / _2X2 blend in thread-block clusters."""
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred, temporal)
+    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred, temporal, cluster)
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
                                ctypes.byref(fb), _stream(stream)))
@@ -216,11 +220,11 @@ def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_c
 
 def gs_render_backward(ctx: Context, g: dict, sh_degree: int, cam, final_T, n_contrib, d_rgb,
                        grads: dict, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
-                       stream=None) -> None:
+                       cluster: int = 0, stream=None) -> None:
     """grads: dict of CUDA tensors shaped like g (keys means, log_scales, quats,
     opacity_logits, sh) and optionally 'records' (n, 9)."""
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype)
+    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, cluster=cluster)
     fb = _fb(None, final_T, n_contrib, None)
     out = N.gs_grads()
     out.d_means, out.d_log_scales, out.d_quats = (_ptr(grads["means"]), _ptr(grads["log_scales"]),
@@ -280,7 +284,7 @@ def scene_to_device(scene, device="cuda") -> dict:
 
 def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
            aux: bool = True, variant: int = 0, record_dtype: int = 0, deferred: bool = False,
-           temporal: bool = False, stream=None) -> dict:
+           temporal: bool = False, cluster: int = 0, stream=None) -> dict:
     """Allocate outputs with torch and call gs_render."""
     import torch
     H, W = int(cam.height), int(cam.width)
@@ -292,7 +296,7 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
         out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
               out.get("n_eval"), tile=tile, bg=bg, variant=variant, record_dtype=record_dtype,
-              deferred=deferred, temporal=temporal, stream=stream)
+              deferred=deferred, temporal=temporal, cluster=cluster, stream=stream)
     return out
 
 
@@ -306,7 +310,7 @@ def _autograd_function():
     class _Rasterize(torch.autograd.Function):
         @staticmethod
         def forward(fctx, means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree, tile, bg,
-                    deferred, record_dtype):
+                    deferred, record_dtype, cluster):
             g = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
                  "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
                  "sh": sh.contiguous()}
@@ -315,28 +319,28 @@ def _autograd_function():
                    "final_T": torch.empty((H, W), dtype=torch.float32, device=means.device),
                    "n_contrib": torch.empty((H, W), dtype=torch.int32, device=means.device)}
             gs_render(ctx, g, sh_degree, cam, out["rgb"], out["final_T"], out["n_contrib"], None,
-                      tile=tile, bg=bg, deferred=deferred, record_dtype=record_dtype)
-            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, gs_last_frame_id(ctx))
+                      tile=tile, bg=bg, deferred=deferred, record_dtype=record_dtype, cluster=cluster)
+            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, gs_last_frame_id(ctx))
             fctx.save_for_backward(out["final_T"], out["n_contrib"])
             fctx.mark_non_differentiable(out["final_T"])
             return out["rgb"], out["final_T"]
 
         @staticmethod
         def backward(fctx, d_rgb, d_T):
-            ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, frame = fctx.gs
+            ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, frame = fctx.gs
             final_T, n_contrib = fctx.saved_tensors
             if gs_last_frame_id(ctx) != frame:
                 # Another frame was rendered on the context since this one
                 # (e.g. several views before one backward): render this frame
                 # again, which gives the same lists, final_T and n_contrib.
                 redo = render(ctx, g, sh_degree, cam, tile=tile, bg=bg, aux=True, record_dtype=record_dtype,
-                              deferred=deferred)
+                              deferred=deferred, cluster=cluster)
                 final_T, n_contrib = redo["final_T"], redo["n_contrib"]
             grads = {k: torch.empty_like(v) for k, v in g.items()}
             gs_render_backward(ctx, g, sh_degree, cam, final_T, n_contrib, d_rgb.contiguous(), grads,
-                               tile=tile, bg=bg, record_dtype=record_dtype)
+                               tile=tile, bg=bg, record_dtype=record_dtype, cluster=cluster)
             return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
-                    grads["sh"], None, None, None, None, None, None, None)
+                    grads["sh"], None, None, None, None, None, None, None, None)
 
     return _Rasterize
 
@@ -345,7 +349,8 @@ _RASTERIZE = None
 
 
 def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Context, cam, sh_degree: int,
-                       tile=(16, 16), bg=(0.0, 0.0, 0.0), deferred: bool = True, record_dtype: int = 0):
+                       tile=(16, 16), bg=(0.0, 0.0, 0.0), deferred: bool = True, record_dtype: int = 0,
+                       cluster: int = 0):
     """Differentiable render: returns (rgb (H,W,3), final_T (H,W)); gradients
     flow to the five parameter tensors. Several renders may precede their
     backwards on one context: a backward whose frame is no longer the
@@ -356,12 +361,13 @@ def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Contex
     raises GSError (GS_ERR_CAPACITY) if that frame overflowed its buffers,
     which have then grown, so the iteration can simply be repeated.
     record_dtype: precision of the blend records (GS_RECORD_F32 / F16 / BF16),
-    used by the forward and the backward blend alike."""
+    used by the forward and the backward blend alike. cluster: thread-block
+    clusters of the forward blend (GS_CLUSTER_*)."""
     global _RASTERIZE
     if _RASTERIZE is None:
         _RASTERIZE = _autograd_function()
     return _RASTERIZE.apply(means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree,
-                            tuple(tile), tuple(bg), bool(deferred), int(record_dtype))
+                            tuple(tile), tuple(bg), bool(deferred), int(record_dtype), int(cluster))
 
 
 # ---------------------------------------------------------------------------
@@ -392,11 +398,13 @@ def alloc_outputs(cams, aux: bool = False, device="cuda") -> list:
 
 def gs_render_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, tile=(16, 16),
                     bg=(0.0, 0.0, 0.0), record_dtype: int = 0, direct: bool = False,
-                    batch_mode: int = 0, batch_depth: int = 0, stream=None):
+                    batch_mode: int = 0, batch_depth: int = 0, cluster: int = 0, stream=None):
     """batch_mode: N.GS_BATCH_AUTO (0), GS_BATCH_JOINT (1) or GS_BATCH_PER_VIEW (2);
-    batch_depth: blend staging depth of the joint schedule (0 = 256)."""
+    batch_depth: blend staging depth of the joint schedule (0 = 256);
+    cluster: thread-block clusters of the blend (the batch then renders view
+    by view)."""
     gs = gaussians_struct(g, sh_degree)
-    o = options_struct(tile, bg, record_dtype)
+    o = options_struct(tile, bg, record_dtype, cluster=cluster)
     o.direct_launch = 1 if direct else 0
     o.batch_mode = int(batch_mode)
     o.batch_depth = int(batch_depth)

@@ -37,7 +37,8 @@ struct gs_context {
     gs_camera last_cam{};
     float last_bg[3] = {0.f, 0.f, 0.f};
     int64_t last_n = 0;
-    int last_w = 0, last_h = 0, last_tw = 0, last_th = 0;
+    int last_w = 0, last_h = 0, last_tw = 0, last_th = 0, last_cluster = 1;
+    GsGrid last_grid{};  // the grid of the frame's lists
     const uint32_t *last_values = nullptr;
     DevBuf d_rec;
     DevBuf br_geo, br_aux, br_col;  // blend records of the render path (16 B per slot each)
@@ -172,7 +173,13 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
         return fail(ctx, GS_ERR_INVALID_ARG, "batch_mode must be GS_BATCH_AUTO, _JOINT or _PER_VIEW");
     if (o->batch_depth != 0 && o->batch_depth != 64 && o->batch_depth != 128 && o->batch_depth != 256)
         return fail(ctx, GS_ERR_INVALID_ARG, "batch_depth must be 0, 64, 128 or 256");
-    if (o->reserved[0] != 0) return fail(ctx, GS_ERR_INVALID_ARG, "reserved options must be 0");
+    if (o->cluster != GS_CLUSTER_NONE && o->cluster != 1 && o->cluster != GS_CLUSTER_2X1 &&
+        o->cluster != GS_CLUSTER_2X2)
+        return fail(ctx, GS_ERR_INVALID_ARG, "cluster must be GS_CLUSTER_NONE (0 or 1), _2X1 or _2X2");
+    if (o->cluster > 1 && !(o->tile_w == 16 && o->tile_h == 16))
+        return fail(ctx, GS_ERR_INVALID_ARG, "thread-block clusters need 16x16 tiles");
+    if (o->cluster > 1 && o->temporal)
+        return fail(ctx, GS_ERR_UNSUPPORTED, "temporal re-binning does not take thread-block clusters");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
     return GS_OK;
@@ -189,12 +196,14 @@ gs_status check_gaussians(gs_context *ctx, const gs_gaussians *g) {
     return GS_OK;
 }
 
+// The grid of the per-tile lists: the screen tiles, or with thread-block
+// clusters the list tiles of 2 x 1 / 2 x 2 screen tiles.
 GsGrid make_grid(const gs_camera *cam, const gs_options *o) {
     GsGrid gr;
-    gr.tile_w = o->tile_w;
-    gr.tile_h = o->tile_h;
-    gr.tiles_x = (cam->width + o->tile_w - 1) / o->tile_w;
-    gr.tiles_y = (cam->height + o->tile_h - 1) / o->tile_h;
+    gr.tile_w = o->cluster > 1 ? 2 * o->tile_w : o->tile_w;
+    gr.tile_h = o->cluster > 3 ? 2 * o->tile_h : o->tile_h;
+    gr.tiles_x = (cam->width + gr.tile_w - 1) / gr.tile_w;
+    gr.tiles_y = (cam->height + gr.tile_h - 1) / gr.tile_h;
     return gr;
 }
 
@@ -374,8 +383,10 @@ void remember_frame(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     ctx->last_n = g->n;
     ctx->last_w = cam->width;
     ctx->last_h = cam->height;
-    ctx->last_tw = grid.tile_w;
-    ctx->last_th = grid.tile_h;
+    ctx->last_tw = opts->tile_w;
+    ctx->last_th = opts->tile_h;
+    ctx->last_cluster = opts->cluster > 1 ? opts->cluster : 1;
+    ctx->last_grid = grid;
     ctx->last_values = values;
     ctx->last_ranges = ranges;
     ctx->last_dtype = opts->record_dtype;
@@ -397,7 +408,8 @@ bool same_frame(const gs_context *ctx, const gs_gaussians *g, const gs_camera *c
         return false;
     for (int i = 0; i < 3; ++i)
         if (ctx->last_bg[i] != opts->bg[i]) return false;
-    return ctx->last_tw == opts->tile_w && ctx->last_th == opts->tile_h && ctx->last_dtype == opts->record_dtype;
+    return ctx->last_tw == opts->tile_w && ctx->last_th == opts->tile_h && ctx->last_dtype == opts->record_dtype &&
+           ctx->last_cluster == (opts->cluster > 1 ? opts->cluster : 1);
 }
 
 gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *tiles, int64_t n,
@@ -469,6 +481,11 @@ gs_status launch_blend(gs_context *ctx, const RecordReader &rd, const uint32_t *
                        const GsGrid &grid, const gs_camera *cam, const gs_options *opts, const gs_framebuffer *fb,
                        const unsigned long long *d_n, int64_t n_cap, cudaStream_t s) {
     const int variant = blend_schedule(ctx, opts, grid.tiles_x * grid.tiles_y);
+    if (opts->cluster > 1) {
+        GS_CUDA(ctx, gs_launch_blend_cluster(rd, values, ranges, grid, opts->cluster, cam->width, cam->height,
+                                             opts->bg, *fb, variant == GS_BLEND_CULLED_8X8, s));
+        return GS_OK;
+    }
     if (variant == GS_BLEND_TMA) {
         gs_status st = ensure(ctx, ctx->gathered, (size_t)(n_cap > 0 ? n_cap : 1) * 48, "gathered records");
         if (st != GS_OK) return st;
@@ -717,6 +734,7 @@ gs_status gs_project(gs_context *ctx, const gs_gaussians *g, const gs_camera *ca
         return fail(ctx, GS_ERR_INVALID_ARG, "records/tiles are NULL");
     if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
         return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
+    if (opts->cluster > 1) return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters are a gs_render option");
     DeviceGuard dg(ctx->device);
     GS_CUDA(ctx, gs_launch_project(*g, make_cam(cam), make_grid(cam, opts), records, tiles,
                                    static_cast<cudaStream_t>(stream)));
@@ -735,6 +753,7 @@ gs_status gs_bin(gs_context *ctx, const gs_record *records, const uint32_t *tile
     if (capacity > 0 && (!keys || !values)) return fail(ctx, GS_ERR_INVALID_ARG, "keys/values are NULL");
     if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
         return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
+    if (opts->cluster > 1) return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters are a gs_render option");
     DeviceGuard dg(ctx->device);
     *n_keys = 0;
     st = bin_impl(ctx, records, tiles, n, make_grid(cam, opts), keys, values, capacity, false, ranges,
@@ -790,6 +809,7 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
     DeviceGuard dg(ctx->device);
     if (opts->record_dtype != GS_RECORD_F32)
         return fail(ctx, GS_ERR_UNSUPPORTED, "gs_blend reads FP32 gs_records; use gs_render for F16/BF16");
+    if (opts->cluster > 1) return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters are a gs_render option");
     GS_CUDA(ctx, gs_launch_blend(reader(ctx, records, GS_RECORD_F32, true), values, ranges, make_grid(cam, opts),
                                  cam->width, cam->height, opts->bg, *fb, opts->blend_variant,
                                  static_cast<cudaStream_t>(stream)));
@@ -1028,7 +1048,7 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
     GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)n * 9 * sizeof(float), s));
     GS_CUDA(ctx, gs_launch_blend_bwd(reader(ctx, static_cast<gs_record *>(ctx->records.ptr), ctx->last_dtype),
                                      ctx->last_values, ctx->last_ranges, grid, cam->width, cam->height,
-                                     opts->bg, d_rgb, fb->final_T, fb->n_contrib, d_rec, s));
+                                     opts->bg, d_rgb, fb->final_T, fb->n_contrib, d_rec, s, ctx->last_cluster));
     GS_CUDA(ctx, gs_launch_project_bwd(*g, make_cam(cam), grid, d_rec, *out, s));
     if (out->d_records && n > 0)
         GS_CUDA(ctx, cudaMemcpyAsync(out->d_records, d_rec, (size_t)n * 9 * sizeof(float),
@@ -1097,7 +1117,9 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto &B = ctx->batch;
     const int64_t n = g->n;
-    const bool per_view = opts->batch_mode == GS_BATCH_PER_VIEW ||
+    // Thread-block clusters are a property of the single-view blend: such a
+    // batch renders view by view.
+    const bool per_view = opts->batch_mode == GS_BATCH_PER_VIEW || opts->cluster > 1 ||
                           (opts->batch_mode == GS_BATCH_AUTO && B.keys_per_view > kBatchPerViewKeys);
     B.have_joint = false;
     if (per_view) {

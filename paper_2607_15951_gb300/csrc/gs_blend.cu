@@ -239,6 +239,216 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32,
     blend_tile_culled<TW, TH, BW, BH, kBatch, RAW>(a, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// Cluster variant: the per-tile lists are built for list tiles of CX x CY
+// screen tiles of 16 x 16 pixels (32 x 16 or 32 x 32 pixels), and the CX x CY
+// thread blocks of one list tile form a thread-block cluster that shares the
+// list's batches through distributed shared memory: per batch of CX CY S
+// records each block stages S of them (one global / L2 read per record and
+// cluster instead of one per screen tile; entries are dealt out round-robin)
+// and marks which of the cluster's tiles each can reach (the exact rectangle test of the culled schedule);
+// after a cluster barrier every block copies, in list order, the records
+// marked for its own tile from its peers' shared memory into its local
+// batch and blends it with the culled schedule. A record is marked for a
+// tile only if the tile lies in the record's 16 x 16 tile rect, so every
+// tile sees exactly its default list, in the same (depth, index) order. The cluster keeps staging
+// until every one of its blocks is done (a flag per block, read after a
+// cluster barrier, so all blocks take the same number of barriers). List
+// positions (n_contrib, n_eval) refer to the list tile's list; colours and
+// transmittance equal those of the per-16x16-tile lists bit for bit, because
+// each pixel sees the same records in the same order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Cluster-wide barrier; release / acquire order shared-memory writes before
+// it with peers' reads after it.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of the same shared-memory location in the block of cluster rank r.
+__device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t r) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(r));
+    return a;
+}
+
+__device__ __forceinline__ float4 ld_peer_f4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float2 ld_peer_f2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_peer_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+template <int CX, int CY, int BW, int BH, int S>
+__global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kernel(const BlendArgs a) {
+    constexpr int TW = 16, TH = 16, NC = CX * CY, L = NC * S;
+    constexpr int kWX = TW / BW, kThreads = kWX * (TH / BH) * 32;
+    constexpr int kRows = 32 / BW, kNP = BW * BH / 32;
+    static_assert(kRows * kNP == BH && kThreads <= 256, "block shape");
+    static_assert(L % kThreads == 0, "batch shape");
+    // This block's share of a batch, read by the whole cluster.
+    __shared__ float4 s_sa[S], s_scol[S], s_sbox[S];
+    __shared__ float2 s_sb[S];
+    __shared__ uint32_t s_smask[S];
+    // The records of the batch that can reach this block's tile, in list order.
+    __shared__ float4 s_a[L], s_col[L], s_box[L];
+    __shared__ float2 s_b[L];
+    __shared__ int32_t s_pos[L];
+    __shared__ float4 s_rect[NC];  // pixel-centre rectangles of the cluster's tiles, by rank
+    __shared__ int2 s_ptile[NC];   // the cluster's screen tiles, by rank
+    __shared__ int2 s_tile;        // this block's screen tile (read by peers)
+    __shared__ int s_done;         // all of this block's pixels have stopped (read by peers)
+    __shared__ uint32_t s_tmp[8];
+    const SRec SL{s_sa, s_sb, s_scol, s_sbox};
+
+    const uint32_t rank = cluster_ctarank();
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
+    const int px = bx + (lane % BW), py_base = by + lane / BW;
+    const float fx = px + 0.5f;
+    const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
+    const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
+    const int lt = (ty / CY) * a.grid.tiles_x + tx / CX;  // the list tile (same for the whole cluster)
+    const uint32_t first = a.ranges[2 * lt], last = a.ranges[2 * lt + 1];
+
+    Pix p[kNP];
+    bool mine_done = true;
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {
+        p[q] = Pix{1.f, 0.f, 0.f, 0.f, 0, 0, !(px < a.width && py_base + q * kRows < a.height)};
+        mine_done = mine_done && p[q].done;
+    }
+    bool warp_done = __all_sync(0xffffffffu, mine_done);
+    if (tid == 0) s_tile = make_int2(tx, ty);
+    __syncthreads();
+    cluster_sync_all();
+    if (tid < NC) {
+        const uint32_t ta = peer_addr(&s_tile, (uint32_t)tid);
+        const int ptx = (int)ld_peer_u32(ta), pty = (int)ld_peer_u32(ta + 4);
+        s_ptile[tid] = make_int2(ptx, pty);
+        // Pixel-centre extent of that tile, clipped to the image (empty when
+        // the tile lies outside it: x0 > x1).
+        s_rect[tid] = make_float4(ptx * TW + 0.5f, fminf(ptx * TW + TW - 0.5f, a.width - 0.5f), pty * TH + 0.5f,
+                                  fminf(pty * TH + TH - 0.5f, a.height - 0.5f));
+    }
+    __syncthreads();
+
+    for (uint32_t start = first; start < last; start += L) {
+        // Done flags of the previous batch, published by the barrier below;
+        // every block reads the same flags, so all leave together.
+        const int cta_done = __syncthreads_and(warp_done);
+        if (tid == 0) s_done = cta_done;
+        cluster_sync_all();
+        const int peer_done = tid < NC ? (int)ld_peer_u32(peer_addr(&s_done, (uint32_t)tid)) : 1;
+        if (__syncthreads_and(peer_done)) break;
+        // Stage this block's share of the batch (list entries start + rank,
+        // start + rank + NC, ...) and mark its tiles.
+        const int n_batch = (int)min((uint32_t)L, last - start);
+        for (int i = tid; i < S; i += kThreads) {
+            const uint32_t k = start + rank + (uint32_t)(NC * i);
+            uint32_t m = 0;
+            if (k < last) {
+                const uint32_t gi = a.values[k];
+                stage_record(a.rd, gi, i, SL, true);
+                // A tile takes the record only if its 16 x 16 tile rect (the
+                // rule of the default lists, from the record's integer
+                // radius) holds the tile, and a pixel of the tile can reach
+                // alpha >= 1/255.
+                const float4 ra = s_sa[i];
+                const int rad = __ldg(reinterpret_cast<const int *>(a.rd.rec32 + 3 * (size_t)gi + 2) + 2);
+                const Rect R16 = tile_rect(ra.x, ra.y, rad, TW, TH, 1 << 30, 1 << 30);
+#pragma unroll
+                for (int r = 0; r < NC; ++r) {
+                    const float4 R = s_rect[r];
+                    const int2 t = s_ptile[r];
+                    if (t.x >= R16.x0 && t.x < R16.x1 && t.y >= R16.y0 && t.y < R16.y1 && R.x <= R.y && R.z <= R.w &&
+                        record_touches(ra, s_sb[i], s_sbox[i], R.x, R.y, R.z, R.w))
+                        m |= 1u << r;
+                }
+            }
+            s_smask[i] = m;
+        }
+        cluster_sync_all();
+        // Gather the records marked for this tile, in list order (entry
+        // start + j sits in slot j / NC of rank j % NC).
+        int cnt = 0;
+        for (int j0 = 0; j0 < n_batch; j0 += kThreads) {
+            const int j = j0 + tid, sl = j % NC, i = j / NC;
+            const uint32_t m = j < n_batch ? ld_peer_u32(peer_addr(&s_smask[i], (uint32_t)sl)) : 0u;
+            const bool keep = (m >> rank) & 1u;
+            const uint32_t off = block_exclusive_scan_256(keep ? 1u : 0u, s_tmp);
+            if (keep) {
+                const int d = cnt + (int)off;
+                s_a[d] = ld_peer_f4(peer_addr(&s_sa[i], (uint32_t)sl));
+                s_b[d] = ld_peer_f2(peer_addr(&s_sb[i], (uint32_t)sl));
+                s_col[d] = ld_peer_f4(peer_addr(&s_scol[i], (uint32_t)sl));
+                s_box[d] = ld_peer_f4(peer_addr(&s_sbox[i], (uint32_t)sl));
+                s_pos[d] = (int32_t)(start - first) + j + 1;
+            }
+            cnt += __syncthreads_count(keep);
+        }
+        __syncthreads();
+        if (!warp_done) {
+            for (int c = 0; c < cnt; c += 32) {
+                const int j = c + lane;
+                const bool hit = j < cnt && record_touches(s_a[j], s_b[j], s_box[j], wx0, wx1, wy0, wy1);
+                uint32_t bits = __ballot_sync(0xffffffffu, hit);
+                while (bits) {
+                    const int jj = c + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const float4 ra = s_a[jj];
+                    const float2 rb = s_b[jj];
+                    const float dx = fx - ra.x;
+                    const float adx2 = ra.z * dx * dx, bdx = ra.w * dx;
+                    const int32_t pos = s_pos[jj];
+#pragma unroll
+                    for (int q = 0; q < kNP; ++q) {
+                        if (!p[q].done) {
+                            const float dy = (float)(py_base + q * kRows) + 0.5f - ra.y;
+                            composite(p[q], fmaf(dy, fmaf(rb.x, dy, bdx), adx2), rb.y, &s_col[jj], pos);
+                        }
+                    }
+                }
+                mine_done = true;
+#pragma unroll
+                for (int q = 0; q < kNP; ++q) mine_done = mine_done && p[q].done;
+                warp_done = __all_sync(0xffffffffu, mine_done);
+                if (warp_done) break;
+            }
+        }
+    }
+    // No block leaves while a peer may still read its shared memory.
+    cluster_sync_all();
+    const int32_t n_list = (int32_t)(last - first);
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {
+        if (!p[q].done) p[q].eval = n_list;
+        write_pixel(a, px, py_base + q * kRows, p[q]);
+    }
+}
+
 // Persistent blend over many views: blocks take global tiles from a queue
 // (largest lists first); each tile is rendered with its view's parameters.
 struct BlendBatchArgs {
@@ -564,6 +774,39 @@ void launch_blend_variant(const BlendArgs &a, const GsGrid &grid, int variant, c
 }
 }  // namespace
 
+namespace {
+template <int CX, int CY, int BW, int BH>
+cudaError_t launch_cluster(const BlendArgs &a, int width, int height, cudaStream_t s) {
+    constexpr int S = 512 / (CX * CY);  // records staged per block and batch (512 per cluster)
+    const int t16x = (width + 15) / 16, t16y = (height + 15) / 16;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((t16x + CX - 1) / CX * CX), (unsigned)((t16y + CY - 1) / CY * CY), 1);
+    cfg.blockDim = dim3((16 / BW) * (16 / BH) * 32, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CX;
+    attr[0].val.clusterDim.y = CY;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, blend_cluster_kernel<CX, CY, BW, BH, S>, a);
+}
+}  // namespace
+
+cudaError_t gs_launch_blend_cluster(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                    const GsGrid &list_grid, int cluster, int width, int height, const float bg[3],
+                                    const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s) {
+    BlendArgs a{rd, values, ranges, list_grid, width, height,
+                {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
+    if (cluster == 2) return wide_blocks ? launch_cluster<2, 1, 8, 8>(a, width, height, s)
+                                         : launch_cluster<2, 1, 8, 4>(a, width, height, s);
+    if (cluster == 4) return wide_blocks ? launch_cluster<2, 2, 8, 8>(a, width, height, s)
+                                         : launch_cluster<2, 2, 8, 4>(a, width, height, s);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s) {
@@ -603,6 +846,10 @@ struct BlendBwdArgs {
     const float *final_T;
     const int32_t *n_contrib;
     float *d_rec;  // n x 9
+    // Blocks cover TW x TH screen tiles, cta_tiles_x of them per row; the
+    // lists belong to list tiles of lcx x lcy screen tiles (1 x 1 unless the
+    // frame was blended in thread-block clusters).
+    int cta_tiles_x, lcx, lcy;
 };
 
 constexpr float kLn2 = 0.6931471805599453f;
@@ -689,14 +936,14 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs &a, int tile) 
     __shared__ int s_maxlast;
     const SRec S{s_a, s_b, s_col, s_box};
 
-    const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
+    const int tx = tile % a.cta_tiles_x, ty = tile / a.cta_tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
     const int px = bx + (lane % BW), py_base = by + lane / BW;
     const float fx = px + 0.5f;
     const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
     const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
-    const uint32_t first = a.ranges[2 * tile];
+    const uint32_t first = a.ranges[2 * ((ty / a.lcy) * a.grid.tiles_x + tx / a.lcx)];
 
     PixB p[kNP];
     int pys[kNP];
@@ -737,6 +984,14 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs &a, int tile) 
             const uint32_t g = a.values[first + beg + s];
             s_g[s] = g;
             stage_record(a.rd, g, s, S, true);
+            if (a.lcx > 1 || a.lcy > 1) {
+                // A cluster frame's lists belong to list tiles; this tile
+                // blended only the records whose 16 x 16 tile rect holds it.
+                const int rad = __ldg(reinterpret_cast<const int *>(a.rd.rec32 + 3 * (size_t)g + 2) + 2);
+                const Rect R = tile_rect(s_a[s].x, s_a[s].y, rad, TW, TH, 1 << 30, 1 << 30);
+                if (!(tx >= R.x0 && tx < R.x1 && ty >= R.y0 && ty < R.y1))
+                    s_box[s] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+            }
         }
         __syncthreads();
         if (wmax > beg) {
@@ -814,7 +1069,7 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_bwd_batch_kern
     const ViewDesc &V = b.views[lo];
     const GsBwdView &W = b.bviews[lo];
     BlendBwdArgs a{b.rd, b.values, b.ranges + 2 * (size_t)V.tile_base, V.grid, V.cam.width, V.cam.height,
-                   {V.bg[0], V.bg[1], V.bg[2]}, W.d_rgb, W.final_T, W.n_contrib, b.d_rec};
+                   {V.bg[0], V.bg[1], V.bg[2]}, W.d_rgb, W.final_T, W.n_contrib, b.d_rec, V.grid.tiles_x, 1, 1};
     blend_bwd_tile<TW, TH, 8, 8>(a, (int)(gt - V.tile_base));
 }
 
@@ -834,11 +1089,15 @@ cudaError_t gs_launch_blend_bwd_batch(const RecordReader &rd, const uint32_t *va
 cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                 const GsGrid &grid, int width, int height, const float bg[3],
                                 const float *d_rgb, const float *final_T, const int32_t *n_contrib,
-                                float *d_rec, cudaStream_t s) {
+                                float *d_rec, cudaStream_t s, int cluster) {
+    // A cluster frame's lists belong to list tiles of 2 x 1 or 2 x 2 screen
+    // tiles of 16 x 16; each block still differentiates one 16 x 16 tile.
+    const int lcx = cluster >= 2 ? 2 : 1, lcy = cluster >= 4 ? 2 : 1;
+    const int tw = grid.tile_w / lcx, th = grid.tile_h / lcy;
+    const int ctx_ = (width + tw - 1) / tw, cty = (height + th - 1) / th;
     BlendBwdArgs a{rd, values, ranges, grid, width, height,
-                   {bg[0], bg[1], bg[2]}, d_rgb, final_T, n_contrib, d_rec};
-    const unsigned blocks = (unsigned)(grid.tiles_x * grid.tiles_y);
-    const int tw = grid.tile_w, th = grid.tile_h;
+                   {bg[0], bg[1], bg[2]}, d_rgb, final_T, n_contrib, d_rec, ctx_, lcx, lcy};
+    const unsigned blocks = (unsigned)(ctx_ * cty);
     // Warp blocks 8x8 (two pixels per lane): finer 8x4 blocks, faster in the
     // forward pass, measured 3 % slower here (more warp reductions of the
     // record gradients per record).

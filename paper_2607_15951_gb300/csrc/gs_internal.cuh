@@ -480,6 +480,13 @@ cudaError_t gs_launch_sort_passes(uint16_t *keys, uint32_t *values, uint16_t *al
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s);
+// Thread-block-cluster blend: the lists belong to list tiles of cluster
+// screen tiles of 16 x 16 (cluster 2: 2 x 1, 4: 2 x 2; list_grid is their
+// grid); the blocks of a list tile form one cluster and share its batches
+// through distributed shared memory. wide_blocks: 8x8 warp blocks.
+cudaError_t gs_launch_blend_cluster(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                    const GsGrid &list_grid, int cluster, int width, int height, const float bg[3],
+                                    const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s);
 // GS_BLEND_TMA: gathers the records of the sorted list (*d_n pairs, or n_cap
 // without a device count) into `gather` (n_cap x 48 bytes, 16-byte aligned),
 // then blends with bulk copies of contiguous record batches.
@@ -566,7 +573,7 @@ cudaError_t gs_launch_temporal_rebin(const GsTemporalRebin &r, cudaStream_t s);
 cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                 const GsGrid &grid, int width, int height, const float bg[3],
                                 const float *d_rgb, const float *final_T, const int32_t *n_contrib,
-                                float *d_rec, cudaStream_t s);
+                                float *d_rec, cudaStream_t s, int cluster = 1);
 // Backward of a joint batch (gs_render_batch): blend gradients per compact
 // record slot over all views' tiles, then, per record slot (view, Gaussian),
 // the projection gradients under that view's camera, added to the Gaussian's
