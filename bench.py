@@ -292,9 +292,9 @@ def batched(gs, torch, args, flush, local) -> dict:
     ctx = gs.Context(local)
     stream = torch.cuda.current_stream()
     outs = gs.alloc_outputs(cams)
-    tile, tune_ms, depth = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
-                                                record_dtype=N.GS_RECORD_F16)
-    iters = max(3, args.steps // 100)
+    tile, tune_ms, depth, cluster = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
+                                                         record_dtype=N.GS_RECORD_F16)
+    iters = max(5, args.steps // 100)
 
     def timed(fn):
         for _ in range(2):
@@ -322,7 +322,7 @@ def batched(gs, torch, args, flush, local) -> dict:
 
     def batch():
         gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile, record_dtype=N.GS_RECORD_F16,
-                           batch_depth=depth)
+                           batch_depth=depth, cluster=cluster)
 
     ms_pv_sync = timed(per_view)
     # Deferred frames cannot regrow in place: reserve room for the largest view.
@@ -368,7 +368,8 @@ def batched(gs, torch, args, flush, local) -> dict:
             "batched_f32_views_per_s": round(v / (ms_b32 / 1e3), 1),
             "speedup_batched_f16_vs_per_view_f32": round(ms_pv / ms_b, 3),
             "ms_per_batch": round(ms_b, 3), "autotuned_tile": list(tile), "autotuned_depth": depth,
-            "autotune_ms_16x16_16x8_8x8": [round(x, 3) for x in tune_ms],
+            "autotuned_cluster": cluster,
+            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2": [round(x, 3) for x in tune_ms],
             "keys_per_batch": st["n_keys"], "iters": iters,
             "fwd_bwd_batched_f16_ms": round(ms_fb_b, 3), "fwd_bwd_per_view_f32_ms": round(ms_fb_v, 3),
             "fwd_bwd_speedup": round(ms_fb_v / ms_fb_b, 3),
@@ -439,8 +440,8 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
     ctx = gs.Context(local)
     stream = torch.cuda.current_stream()
     outs = gs.alloc_outputs(cams)
-    tile, tune_ms, depth = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
-                                                record_dtype=N.GS_RECORD_BF16)
+    tile, tune_ms, depth, cluster = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
+                                                         record_dtype=N.GS_RECORD_BF16)
     iters = 3
 
     def timed(fn):
@@ -458,7 +459,8 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
         return tot / iters
 
     ms_batch = timed(lambda: gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile,
-                                                record_dtype=N.GS_RECORD_BF16, batch_depth=depth))
+                                                record_dtype=N.GS_RECORD_BF16, batch_depth=depth,
+                                                cluster=cluster))
     keys_batch = gs.gs_last_render_stats(ctx)["n_keys"]
     k_max = 0
     for c, o in zip(cams, outs):
@@ -479,7 +481,8 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
         for p in params:
             p.grad = None
         for c, tgt in zip(cams, targets):
-            rgb, _ = gs.RasterizeGaussians(*params, ctx, c, scene.sh_degree, record_dtype=N.GS_RECORD_BF16)
+            rgb, _ = gs.RasterizeGaussians(*params, ctx, c, scene.sh_degree, record_dtype=N.GS_RECORD_BF16,
+                                           cluster=cluster)
             (rgb - tgt).abs().mean().backward()
 
     ms_fb = timed(fwd_bwd_views)
@@ -492,9 +495,10 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
             "per_view_f32_ms": round(ms_pv, 3), "per_view_f32_views_per_s": round(v / (ms_pv / 1e3), 2),
             "speedup_batched_bf16_vs_per_view_f32": round(ms_pv / ms_batch, 3),
             "fwd_bwd_bf16_ms_per_8_views": round(ms_fb, 3),
-            "fwd_bwd_note": "per view through RasterizeGaussians (BF16 records, FP32 compositing), L1 loss each",
-            "keys_per_batch": keys_batch, "autotuned_tile": list(tile),
-            "autotune_ms_16x16_16x8_8x8": [round(x, 3) for x in tune_ms], "iters": iters}
+            "fwd_bwd_note": "per view through RasterizeGaussians (BF16 records, FP32 compositing, the "
+                            "autotuned blend cluster), L1 loss each",
+            "keys_per_batch": keys_batch, "autotuned_tile": list(tile), "autotuned_cluster": cluster,
+            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2": [round(x, 3) for x in tune_ms], "iters": iters}
 
 
 def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:

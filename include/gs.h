@@ -400,11 +400,13 @@ gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const
                                    const gs_grads *out, void *stream);
 
 /* Autotuner of gs_render_batch: renders the batch with each screen-tile
- * shape (16x16, 16x8, 8x8) and, for the joint schedule, each blend staging
- * depth (256, 128, 64 records), times three runs of each with CUDA events,
- * and writes the fastest into opts->tile_w / tile_h / batch_depth. ms_out
- * (host, 3 floats, optional) receives per shape the mean time of its best
- * depth, in that order. */
+ * shape and blend cluster (16x16, 16x8, 8x8 without clusters; 16x16 with
+ * GS_CLUSTER_2X1 and with GS_CLUSTER_2X2, which render view by view) and,
+ * for the joint schedule, each blend staging depth (256, 128, 64 records),
+ * times three runs of each with CUDA events, and writes the fastest into
+ * opts->tile_w / tile_h / cluster / batch_depth. ms_out (host, 5 floats,
+ * optional) receives per candidate the mean time of its best depth, in that
+ * order. */
 gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
                             gs_options *opts, const gs_framebuffer *fbs, void *stream, float *ms_out);
 

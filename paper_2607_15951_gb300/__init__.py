@@ -480,10 +480,11 @@ def RasterizeGaussiansBatch(means, log_scales, quats, opacity_logits, sh, ctx: C
 
 def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(0.0, 0.0, 0.0),
                       record_dtype: int = 0, cache_path: str | None = None, stream=None):
-    """Runs the C autotuner (tile shapes 16x16, 16x8, 8x8 and, for the joint
-    schedule, staging depths 256, 128, 64) and returns ((tile_w, tile_h),
-    [ms per shape], depth). With cache_path, results are kept in a JSON file
-    keyed by GPU, scene size, view sizes and record precision."""
+    """Runs the C autotuner (tile shapes 16x16, 16x8, 8x8, 16x16 with 2x1 and
+    2x2 blend clusters and, for the joint schedule, staging depths 256, 128,
+    64) and returns ((tile_w, tile_h), [ms per candidate], depth, cluster).
+    With cache_path, results are kept in a JSON file keyed by GPU, scene
+    size, view sizes and record precision."""
     import json
     import os
     import torch
@@ -495,21 +496,23 @@ def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(
         if os.path.exists(cache_path):
             with open(cache_path) as f:
                 cache = json.load(f)
-            if key in cache:
-                return tuple(cache[key]["tile"]), cache[key]["ms"], cache[key].get("depth", 256)
+            if key in cache and "cluster" in cache[key]:
+                return (tuple(cache[key]["tile"]), cache[key]["ms"], cache[key].get("depth", 256),
+                        cache[key]["cluster"])
     gs = gaussians_struct(g, sh_degree)
     o = options_struct((16, 16), bg, record_dtype)
     carr, farr = _cams_fbs(cams, outs)
-    ms = (ctypes.c_float * 3)()
+    ms = (ctypes.c_float * 5)()
     ctx.check(_lib().gs_autotune_batch(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
                                        _stream(stream), ms))
     tile, times, depth = (int(o.tile_w), int(o.tile_h)), [float(x) for x in ms], int(o.batch_depth)
+    cluster = int(o.cluster)
     if cache_path:
         cache = {}
         if os.path.exists(cache_path):
             with open(cache_path) as f:
                 cache = json.load(f)
-        cache[key] = {"tile": list(tile), "ms": times, "depth": depth}
+        cache[key] = {"tile": list(tile), "ms": times, "depth": depth, "cluster": cluster}
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
-    return tile, times, depth
+    return tile, times, depth, cluster

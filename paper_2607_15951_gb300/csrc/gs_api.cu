@@ -1316,7 +1316,8 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     if (!ctx || !opts) return GS_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int shapes[3][2] = {{16, 16}, {16, 8}, {8, 8}};
+    // Screen tile (w, h) and thread-block cluster of each candidate.
+    const int shapes[5][3] = {{16, 16, 0}, {16, 8, 0}, {8, 8, 0}, {16, 16, GS_CLUSTER_2X1}, {16, 16, GS_CLUSTER_2X2}};
     const int depths[3] = {256, 128, 64};
     cudaEvent_t e0, e1;
     GS_CUDA(ctx, cudaEventCreate(&e0));
@@ -1324,12 +1325,13 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     float best = 1e30f;
     int best_k = 0, best_d = 0;
     gs_status st = GS_OK;
-    for (int k = 0; k < 3 && st == GS_OK; ++k) {
+    for (int k = 0; k < 5 && st == GS_OK; ++k) {
         float best_shape = 1e30f;
         for (int d = 0; d < 3 && st == GS_OK; ++d) {
             gs_options o = *opts;
             o.tile_w = shapes[k][0];
             o.tile_h = shapes[k][1];
+            o.cluster = shapes[k][2];
             o.batch_depth = depths[d];
             for (int w = 0; w < 2 && st == GS_OK; ++w) st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
             // The depth only matters to the joint schedule.
@@ -1359,6 +1361,7 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     if (st != GS_OK) return st;
     opts->tile_w = shapes[best_k][0];
     opts->tile_h = shapes[best_k][1];
+    opts->cluster = shapes[best_k][2];
     opts->batch_depth = depths[best_d];
     return GS_OK;
 }
