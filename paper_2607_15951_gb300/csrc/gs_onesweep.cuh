@@ -16,65 +16,62 @@ constexpr int kOsRadix = 256;
 constexpr int kOsLookAhead = GS_SORT_LOOKAHEAD;  // status words read per look-back step
 
 // Shared memory the partition needs: the reordered pairs, per-warp digit
-// counters, digit offsets and bases, scan scratch.
+// counters (later the digits' start offsets within the partition), the
+// digits' global destinations, scan scratch.
 template <typename KT, int ITEMS>
 __host__ __device__ constexpr size_t onesweep_partition_smem() {
-    return (size_t)kOsThreads * ITEMS * (sizeof(KT) + 4) + (size_t)kOsWarps * kOsRadix * 4 + 2 * kOsRadix * 4 +
+    return (size_t)kOsThreads * ITEMS * (sizeof(KT) + 4) + (size_t)kOsWarps * kOsRadix * 4 + kOsRadix * 4 +
            kOsWarps * 4 + 16;
 }
 
-// key/val: the partition's pairs, warp-striped (item j of lane l of warp w
-// is pair base + w*32*ITEMS + j*32 + l; pairs at or past n are ignored).
-// p: the partition's index in the order partitions were taken (a partition
-// only waits on earlier ones). status: this pass's look-back words
-// (parts x 256, zeroed); bucket: the pass's 256 exclusive digit offsets.
-// All 256 threads of the block call it.
-template <typename KT, int ITEMS>
-__device__ __forceinline__ void onesweep_partition(const KT (&key)[ITEMS], const uint32_t (&val)[ITEMS], int64_t base,
-                                                   int64_t n, int64_t p, int shift, unsigned long long *status,
-                                                   const uint32_t *bucket, KT *__restrict__ keys_out,
-                                                   uint32_t *__restrict__ vals_out, uint32_t *d_err,
-                                                   unsigned long long timeout_ns, bool ballot_rank,
-                                                   unsigned char *smem) {
+// The partition proper. FULL: all kTile pairs are in range (every partition
+// but the last), so no item needs a range test.
+template <typename KT, int ITEMS, bool FULL>
+__device__ __forceinline__ void onesweep_partition_body(const KT (&key)[ITEMS], const uint32_t (&val)[ITEMS],
+                                                        int valid, int64_t n, int64_t p, int shift,
+                                                        unsigned long long *status, const uint32_t *bucket,
+                                                        KT *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+                                                        uint32_t *d_err, unsigned long long timeout_ns,
+                                                        bool ballot_rank, unsigned char *smem) {
     constexpr int kItems = ITEMS, kTile = kOsThreads * ITEMS, kThreads = kOsThreads, kWarps = kOsWarps,
                   kRadix = kOsRadix;
     KT *s_keys = reinterpret_cast<KT *>(smem);                                  // kTile
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kTile);            // kTile
     uint32_t *s_whist = s_vals + kTile;                                         // kWarps x 256
-    uint32_t *s_doff = s_whist + kWarps * kRadix;                               // 256
-    uint32_t *s_gbase = s_doff + kRadix;                                        // 256
-    uint32_t *s_tmp = s_gbase + kRadix;                                         // kWarps
+    uint32_t *s_gdst = s_whist + kWarps * kRadix;                               // 256
+    uint32_t *s_tmp = s_gdst + kRadix;                                          // kWarps
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
     __syncthreads();
     uint32_t rank[kItems];
-    // Stable rank within the warp, in (item, lane) order. Out-of-range items
-    // get digit 256, which matches nothing real and is never counted.
+    // Stable rank within the warp, in (item, lane) order; out-of-range items
+    // (only in the last partition) are never counted.
     uint32_t *my_hist = s_whist + warp * kRadix;
+    const uint32_t lt_mask = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
-        const uint32_t d = idx < n ? (uint32_t)((key[j] >> shift) & 255) : 256u;
+        const bool in = FULL || warp * 32 * kItems + j * 32 + lane < valid;
+        const uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
         // Lanes with equal digits: warp match (fast when a warp holds few
-        // distinct digits), or 9 ballots, one per bit of 0..256 (constant
-        // cost, faster when digits are diverse).
+        // distinct digits), or one ballot per digit bit (constant cost,
+        // faster when digits are diverse).
         uint32_t peers;
         if (ballot_rank) {
-            peers = 0xffffffffu;
+            peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, in);
 #pragma unroll
-            for (int b = 0; b < 9; ++b) {
+            for (int b = 0; b < 8; ++b) {
                 const bool bit = (d >> b) & 1u;
                 const uint32_t m = __ballot_sync(0xffffffffu, bit);
                 peers &= bit ? m : ~m;
             }
         } else {
-            peers = __match_any_sync(0xffffffffu, d);
+            peers = __match_any_sync(0xffffffffu, in ? d : 256u);
         }
-        const uint32_t lt = peers & lanemask_lt();
-        const uint32_t before = d < 256u ? my_hist[d] : 0u;
+        const uint32_t lt = peers & lt_mask;
+        const uint32_t before = in ? my_hist[d] : 0u;
         __syncwarp();
         rank[j] = before + __popc(lt);
-        if (d < 256u && lt == 0u) my_hist[d] = before + __popc(peers);
+        if (in && lt == 0u) my_hist[d] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -94,7 +91,8 @@ __device__ __forceinline__ void onesweep_partition(const KT (&key)[ITEMS], const
         st_relaxed_u64(st, kFlagAgg | total);
     }
     const uint32_t doff = block_exclusive_scan_256(total, s_tmp);
-    s_doff[digit] = doff;
+    // Warp w's items of this digit start at doff + (earlier warps' count).
+    for (int w = 0; w < kWarps; ++w) s_whist[w * kRadix + digit] += doff;
 
     // Decoupled look-back for this digit over partitions p-1, p-2, ...,
     // reading kOsLookAhead status words per step so a chain of aggregates costs
@@ -136,34 +134,56 @@ __device__ __forceinline__ void onesweep_partition(const KT (&key)[ITEMS], const
         }
         st_relaxed_u64(st, kFlagIncl | ((excl + total) & kValueMask));
     }
-    s_gbase[digit] = bucket[digit] + (uint32_t)excl;
+    // Global slot of the partition's i-th pair of this digit: gdst + i (pair
+    // counts stay below 2^32, so the arithmetic is modulo 2^32).
+    s_gdst[digit] = bucket[digit] + (uint32_t)excl - doff;
     __syncthreads();
 
     // Reorder by digit in shared memory.
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
-        if (idx < n) {
-            const uint32_t d = (uint32_t)((key[j] >> shift) & 255);
-            const uint32_t pos = s_doff[d] + my_hist[d] + rank[j];
+        if (FULL || warp * 32 * kItems + j * 32 + lane < valid) {
+            const uint32_t d = (uint32_t)(key[j] >> shift) & 255u;
+            const uint32_t pos = my_hist[d] + rank[j];
             s_keys[pos] = key[j];
             s_vals[pos] = val[j];
         }
     }
     __syncthreads();
-    const int valid = (int)((n - base) < kTile ? (n - base) : kTile);
     for (int i = tid; i < valid; i += kThreads) {
         const KT k = s_keys[i];
-        const uint32_t d = (uint32_t)((k >> shift) & 255);
-        const uint64_t gp = (uint64_t)s_gbase[d] + (uint32_t)(i - s_doff[d]);
+        const uint32_t gp = s_gdst[(uint32_t)(k >> shift) & 255u] + (uint32_t)i;
         // Only reachable after a timed-out look-back left offsets meaningless.
-        if (gp >= (uint64_t)n) {
+        if ((int64_t)gp >= n) {
             atomicOr(d_err, kErrRange);
             continue;
         }
         keys_out[gp] = k;
         vals_out[gp] = s_vals[i];
     }
+}
+
+// key/val: the partition's pairs, warp-striped (item j of lane l of warp w
+// is pair base + w*32*ITEMS + j*32 + l; pairs at or past n are ignored).
+// p: the partition's index in the order partitions were taken (a partition
+// only waits on earlier ones). status: this pass's look-back words
+// (parts x 256, zeroed); bucket: the pass's 256 exclusive digit offsets.
+// All 256 threads of the block call it.
+template <typename KT, int ITEMS>
+__device__ __forceinline__ void onesweep_partition(const KT (&key)[ITEMS], const uint32_t (&val)[ITEMS], int64_t base,
+                                                   int64_t n, int64_t p, int shift, unsigned long long *status,
+                                                   const uint32_t *bucket, KT *__restrict__ keys_out,
+                                                   uint32_t *__restrict__ vals_out, uint32_t *d_err,
+                                                   unsigned long long timeout_ns, bool ballot_rank,
+                                                   unsigned char *smem) {
+    constexpr int kTile = kOsThreads * ITEMS;
+    const int valid = (int)(n - base < kTile ? n - base : kTile);
+    if (valid == kTile)
+        onesweep_partition_body<KT, ITEMS, true>(key, val, valid, n, p, shift, status, bucket, keys_out, vals_out,
+                                                 d_err, timeout_ns, ballot_rank, smem);
+    else
+        onesweep_partition_body<KT, ITEMS, false>(key, val, valid, n, p, shift, status, bucket, keys_out, vals_out,
+                                                  d_err, timeout_ns, ballot_rank, smem);
 }
 
 }  // namespace gs

@@ -875,6 +875,7 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
         }
         int e = -1;
         uint32_t g = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0, tiles_x = (uint32_t)G.tiles_x, tbase = 0;
+        uint32_t qy = 0, rx = 0;  // row and column of key k within its entry's rect
         uint32_t run_digit[kMaxTilePasses], run_count[kMaxTilePasses];
         uint32_t tk[kKeysPerThread], tv[kKeysPerThread];
         for (int d = 0; d < kMaxTilePasses; ++d) { run_digit[d] = 0xffffffffu; run_count[d] = 0; }
@@ -905,9 +906,14 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const EmitArgs E) {
                 x0 = (uint32_t)R.x0;
                 y0 = (uint32_t)R.y0;
                 eend = ebase + w * (uint32_t)(R.y1 - R.y0);
+                // Only the thread's first key can start inside an entry.
+                const uint32_t m = (uint32_t)(k - ebase);
+                qy = m ? m / w : 0u;
+                rx = m - qy * w;
+            } else if (++rx == w) {  // the next key of the same rect, row-major
+                rx = 0;
+                ++qy;
             }
-            const uint32_t m = (uint32_t)(k - ebase);
-            const uint32_t qy = m / w, rx = m - qy * w;
             const uint32_t tile = tbase + (y0 + qy) * tiles_x + x0 + rx;
             tk[q] = tile;
             tv[q] = g;
@@ -1043,6 +1049,7 @@ __global__ void __launch_bounds__(256, 3) emit_sort_kernel(const EmitSortArgs A)
         }
         int e = -1;
         uint32_t g = 0, w = 1, x0 = 0, y0 = 0, ebase = 0, eend = 0;
+        uint32_t qy = 0, rx = 0;  // row and column of key k within its entry's rect
         uint32_t tk[kKeysPerThread], tv[kKeysPerThread];
 #pragma unroll
         for (int q = 0; q < kKeysPerThread; ++q) {
@@ -1064,9 +1071,14 @@ __global__ void __launch_bounds__(256, 3) emit_sort_kernel(const EmitSortArgs A)
                 x0 = (uint32_t)R.x0;
                 y0 = (uint32_t)R.y0;
                 eend = ebase + w * (uint32_t)(R.y1 - R.y0);
+                // Only the thread's first key can start inside an entry.
+                const uint32_t m = (uint32_t)(k - ebase);
+                qy = m ? m / w : 0u;
+                rx = m - qy * w;
+            } else if (++rx == w) {  // the next key of the same rect, row-major
+                rx = 0;
+                ++qy;
             }
-            const uint32_t m = (uint32_t)(k - ebase);
-            const uint32_t qy = m / w, rx = m - qy * w;
             tk[q] = ((y0 + qy) << 8) | (x0 + rx);
             tv[q] = g;
         }
