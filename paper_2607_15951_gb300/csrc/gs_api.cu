@@ -44,7 +44,7 @@ struct gs_context {
     DevBuf br_geo, br_aux, br_col;  // blend records of the render path (16 B per slot each)
     // Batched path (own buffers: a captured graph holds their addresses).
     struct Batch {
-        DevBuf views, rec, meta, geo, aux, col, scratch, ranges, order, queue, keys, vals, akeys, avals, sort;
+        DevBuf views, rec, meta, geo, aux, col, scratch, ranges, order, queue, keys, vals, akeys, avals, sort, rts;
         ViewDesc *h_views = nullptr;
         int h_views_cap = 0;
         int64_t rec_cap = 0, key_cap = 0;
@@ -65,6 +65,7 @@ struct gs_context {
     bool pinned_capacity = false;  // set by gs_reserve_keys: do not shrink
     DevBuf fused_scratch;
     DevBuf gathered;  // records in list order (GS_BLEND_TMA)
+    DevBuf rts_scratch;  // per-partition digit counts and offsets of reduce-then-scan passes
     bool timing = false;
     bool timed_once = false;
     cudaEvent_t ev[8] = {};
@@ -676,7 +677,8 @@ void gs_destroy(gs_context *ctx) {
     DeviceGuard g(ctx->device);
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                       &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
-                      &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col, &ctx->gathered};
+                      &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col, &ctx->gathered,
+                      &ctx->rts_scratch};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -691,7 +693,7 @@ void gs_destroy(gs_context *ctx) {
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     auto &B = ctx->batch;
     DevBuf *bb[] = {&B.views, &B.rec, &B.meta, &B.geo, &B.aux, &B.col, &B.scratch, &B.ranges, &B.order,
-                    &B.queue, &B.keys, &B.vals, &B.akeys, &B.avals, &B.sort, &B.d_rec, &B.bviews};
+                    &B.queue, &B.keys, &B.vals, &B.akeys, &B.avals, &B.sort, &B.d_rec, &B.bviews, &B.rts};
     for (DevBuf *b : bb)
         if (b->ptr) cudaFree(b->ptr);
     if (B.exec) cudaGraphExecDestroy(B.exec);
@@ -717,7 +719,8 @@ size_t gs_workspace_bytes(const gs_context *ctx) {
     if (!ctx) return 0;
     const DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                             &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch,
-                            &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col};
+                            &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col,
+                            &ctx->gathered, &ctx->rts_scratch};
     size_t t = 0;
     for (const DevBuf *b : bufs) t += b->bytes;
     return t;
@@ -833,14 +836,11 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     const int bits = key_bits_for(n_tiles);
     // Tile keys: (row << 8 | column) for grids at most 256 tiles wide (the
     // tile sort's histograms then come from the rects and its first pass is
-    // fused with the emission), else tile ids.
-    const bool xy_keys = grid.tiles_x <= 256;
+    // fused with the emission), else tile ids. Both orders are the tile
+    // order, and both fit the same key width on grids of at most 256 x 256.
     int row_bits = 0;
     while ((1 << row_bits) < grid.tiles_y) ++row_bits;
-    const int tkey_bits = xy_keys ? 8 + row_bits : bits - 32;
-    const int tile_passes = (tkey_bits + 7) / 8;
-    const int sort_passes = tile_passes > 0 ? tile_passes : 1;
-    const int key_bytes = tkey_bits <= 16 ? 2 : 4;
+    const bool xy_possible = grid.tiles_x <= 256;
     const int dtype = opts->record_dtype;
     if ((st = ensure(ctx, ctx->br_geo, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK ||
         (st = ensure(ctx, ctx->br_aux, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK ||
@@ -891,12 +891,23 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     // the overflow is detected at the end and the frame is rendered again.
     for (int attempt = 0; attempt < 3; ++attempt) {
         const int64_t cap = ctx->key_capacity;
+        // Long lists sort their tile keys with reduce-then-scan passes (no
+        // look-back chains) after a plain emission of tile ids; short ones
+        // with onesweep passes, the first fused with the emission.
+        const bool rts = cap >= kRtsMinPairs;
+        const bool xy_keys = xy_possible && !rts;
+        const int tkey_bits = xy_keys ? 8 + row_bits : bits - 32;
+        const int tile_passes = (tkey_bits + 7) / 8;
+        const int sort_passes = tile_passes > 0 ? tile_passes : 1;
+        const int key_bytes = tkey_bits <= 16 ? 2 : 4;
+        const int64_t status_cap = rts ? 1 : cap;  // onesweep look-back words (none with rts)
         if ((st = ensure(ctx, ctx->keys, (size_t)cap * key_bytes, "keys")) != GS_OK ||
             (st = ensure(ctx, ctx->values, (size_t)cap * 4, "values")) != GS_OK ||
             (st = ensure(ctx, ctx->alt_keys, (size_t)cap * key_bytes, "alt keys")) != GS_OK ||
             (st = ensure(ctx, ctx->alt_values, (size_t)cap * 4, "alt values")) != GS_OK ||
-            (st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes_digits(cap, sort_passes), "sort scratch")) !=
-                GS_OK ||
+            (st = ensure(ctx, ctx->sort_scratch, gs_sort_scratch_bytes_digits(status_cap, sort_passes),
+                         "sort scratch")) != GS_OK ||
+            (rts && (st = ensure(ctx, ctx->rts_scratch, gs_sort_rts_scratch_bytes(cap), "sort scratch")) != GS_OK) ||
             (st = ensure(ctx, ctx->fused_scratch, gs_fused_scratch_bytes(n, cap), "front-end scratch")) != GS_OK)
             return st;
         void *keys = ctx->keys.ptr, *akeys = ctx->alt_keys.ptr;
@@ -907,9 +918,12 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         // Its digit histograms are counted from the tile rects during the
         // projection, and its first pass is fused with the emission (whose
         // output lands in the alternate buffers); at least one pass runs.
-        GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes_digits(cap, sort_passes), s));
-        GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, cap, 0, sort_passes);
-        sc.diverse_last = xy_keys;  // the row digit takes many values within a warp
+        GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes_digits(status_cap, sort_passes),
+                                     s));
+        GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, status_cap, 0, sort_passes);
+        // The row digit takes many values within a warp; so does the high
+        // byte of tile ids once the low byte is sorted.
+        sc.diverse_last = xy_keys || rts;
         mark(ctx, EV_START, s);
         cudaEvent_t ev3[3] = {nullptr, nullptr, nullptr};
         if (ctx->timing) {
@@ -929,7 +943,15 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         uint32_t *in_v = xy_keys ? avals : vals, *out_v = xy_keys ? vals : avals;
         const int first_pass = xy_keys ? 1 : 0;
         bool moved = false;
-        if (key_bytes == 2)
+        if (rts && key_bytes == 2)
+            GS_CUDA(ctx, gs_launch_sort_passes_rts(static_cast<uint16_t *>(in_k), in_v, static_cast<uint16_t *>(out_k),
+                                                   out_v, cap, ctx->d_counts + 2, sc, ctx->rts_scratch.ptr,
+                                                   ctx->d_err, &moved, s, first_pass));
+        else if (rts)
+            GS_CUDA(ctx, gs_launch_sort_passes_rts(static_cast<uint32_t *>(in_k), in_v, static_cast<uint32_t *>(out_k),
+                                                   out_v, cap, ctx->d_counts + 2, sc, ctx->rts_scratch.ptr,
+                                                   ctx->d_err, &moved, s, first_pass));
+        else if (key_bytes == 2)
             GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint16_t *>(in_k), in_v, static_cast<uint16_t *>(out_k),
                                                out_v, cap, ctx->d_counts + 2, sc, ctx->d_err, &moved, s,
                                                gs::kSpinTimeoutNs, 64, first_pass));
@@ -1068,9 +1090,12 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
                                  cudaMemcpyHostToDevice, s));
     // The tile sort: 32-bit global tile ids emitted in (depth, view, index)
     // order, so the stable sort on them alone orders every tile's list.
+    // Long key lists sort with reduce-then-scan passes (no look-back words).
     const int tile_passes = (bits - 32 + 7) / 8;
-    GS_CUDA(ctx, cudaMemsetAsync(B.sort.ptr, 0, gs_sort_scratch_bytes_digits(B.key_cap, tile_passes), s));
-    const GsSortScratch sc = gs_sort_carve_digits(B.sort.ptr, B.key_cap, 0, tile_passes);
+    const bool rts = B.key_cap >= kRtsMinPairs;
+    const int64_t status_cap = rts ? 1 : B.key_cap;
+    GS_CUDA(ctx, cudaMemsetAsync(B.sort.ptr, 0, gs_sort_scratch_bytes_digits(status_cap, tile_passes), s));
+    const GsSortScratch sc = gs_sort_carve_digits(B.sort.ptr, status_cap, 0, tile_passes);
     uint32_t *keys = static_cast<uint32_t *>(B.keys.ptr), *akeys = static_cast<uint32_t *>(B.akeys.ptr);
     uint32_t *vals = static_cast<uint32_t *>(B.vals.ptr), *avals = static_cast<uint32_t *>(B.avals.ptr);
     uint2 *meta = static_cast<uint2 *>(B.meta.ptr);
@@ -1080,8 +1105,12 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
                                              B.rec_cap, keys,
                                              vals, B.key_cap, ctx->d_counts, B.scratch.ptr, sc, ctx->d_err, s));
     bool in_alt = false;
-    GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, B.key_cap, ctx->d_counts + 2, sc, ctx->d_err,
-                                       &in_alt, s));
+    if (rts)
+        GS_CUDA(ctx, gs_launch_sort_passes_rts(keys, vals, akeys, avals, B.key_cap, ctx->d_counts + 2, sc, B.rts.ptr,
+                                               ctx->d_err, &in_alt, s));
+    else
+        GS_CUDA(ctx, gs_launch_sort_passes(keys, vals, akeys, avals, B.key_cap, ctx->d_counts + 2, sc, ctx->d_err,
+                                           &in_alt, s));
     const uint32_t *sk = in_alt ? akeys : keys;
     uint32_t *sv = in_alt ? avals : vals;
     B.joint_values = sv;
@@ -1177,7 +1206,7 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
         const int64_t rc = B.rec_cap, kc = B.key_cap;
         void *before[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.aux.ptr, B.col.ptr, B.scratch.ptr,
                           B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,
-                          B.avals.ptr, B.sort.ptr};
+                          B.avals.ptr, B.sort.ptr, B.rts.ptr};
         if ((st = ensure(ctx, B.views, (size_t)n_views * sizeof(ViewDesc), "view table")) != GS_OK ||
             (st = ensure(ctx, B.rec, (size_t)rc * sizeof(gs_record), "batch records")) != GS_OK ||
             (st = ensure(ctx, B.meta, (size_t)rc * 8, "batch record meta")) != GS_OK ||
@@ -1192,12 +1221,15 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
             (st = ensure(ctx, B.vals, (size_t)kc * 4, "batch values")) != GS_OK ||
             (st = ensure(ctx, B.akeys, (size_t)kc * 4, "batch keys")) != GS_OK ||
             (st = ensure(ctx, B.avals, (size_t)kc * 4, "batch values")) != GS_OK ||
-            (st = ensure(ctx, B.sort, gs_sort_scratch_bytes_digits(kc, (bits - 32 + 7) / 8), "batch sort scratch")) !=
-                GS_OK)
+            (st = ensure(ctx, B.sort,
+                         gs_sort_scratch_bytes_digits(kc >= kRtsMinPairs ? 1 : kc, (bits - 32 + 7) / 8),
+                         "batch sort scratch")) != GS_OK ||
+            (kc >= kRtsMinPairs &&
+             (st = ensure(ctx, B.rts, gs_sort_rts_scratch_bytes(kc), "batch sort scratch")) != GS_OK))
             return st;
         void *after[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.aux.ptr, B.col.ptr, B.scratch.ptr,
                          B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,
-                         B.avals.ptr, B.sort.ptr};
+                         B.avals.ptr, B.sort.ptr, B.rts.ptr};
         std::vector<int64_t> full = sig;
         full.push_back(rc);
         full.push_back(kc);

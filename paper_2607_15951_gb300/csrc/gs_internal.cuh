@@ -477,6 +477,25 @@ cudaError_t gs_launch_sort_passes(uint16_t *keys, uint32_t *values, uint16_t *al
                                   unsigned long long timeout_ns = gs::kSpinTimeoutNs, int max_passes = 64,
                                   int first_pass = 0);
 
+// Reduce-then-scan digit passes (long lists; see gs_sort.cu): the same
+// result as gs_launch_sort_passes with partitions of 3072 pairs that never
+// wait on one another. rts_scratch: gs_sort_rts_scratch_bytes(n_capacity).
+// sc supplies the passes, digit0 and the bucket offsets of every pass.
+constexpr int64_t kRtsMinPairs = int64_t(1) << 23;  // capacities from here on use it
+size_t gs_sort_rts_scratch_bytes(int64_t n_capacity);
+cudaError_t gs_launch_sort_passes_rts(uint16_t *keys, uint32_t *values, uint16_t *alt_keys, uint32_t *alt_values,
+                                      int64_t n_capacity, const unsigned long long *d_n, const GsSortScratch &sc,
+                                      void *rts_scratch, uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                      int first_pass = 0);
+cudaError_t gs_launch_sort_passes_rts(uint32_t *keys, uint32_t *values, uint32_t *alt_keys, uint32_t *alt_values,
+                                      int64_t n_capacity, const unsigned long long *d_n, const GsSortScratch &sc,
+                                      void *rts_scratch, uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                      int first_pass = 0);
+cudaError_t gs_launch_sort_passes_rts(uint64_t *keys, uint32_t *values, uint64_t *alt_keys, uint32_t *alt_values,
+                                      int64_t n_capacity, const unsigned long long *d_n, const GsSortScratch &sc,
+                                      void *rts_scratch, uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                      int first_pass = 0);
+
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
                             const gs_framebuffer &fb, int variant, cudaStream_t s);

@@ -32,7 +32,8 @@ __device__ __forceinline__ void onesweep_partition_body(const KT (&key)[ITEMS], 
                                                         unsigned long long *status, const uint32_t *bucket,
                                                         KT *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                                                         uint32_t *d_err, unsigned long long timeout_ns,
-                                                        bool ballot_rank, unsigned char *smem) {
+                                                        bool ballot_rank, unsigned char *smem,
+                                                        const uint32_t *rts, int64_t rts_stride) {
     constexpr int kItems = ITEMS, kTile = kOsThreads * ITEMS, kThreads = kOsThreads, kWarps = kOsWarps,
                   kRadix = kOsRadix;
     KT *s_keys = reinterpret_cast<KT *>(smem);                                  // kTile
@@ -85,20 +86,26 @@ __device__ __forceinline__ void onesweep_partition_body(const KT (&key)[ITEMS], 
         total += c;
     }
     unsigned long long *st = status + p * kRadix + digit;
-    if (p == 0) {
-        st_relaxed_u64(st, kFlagIncl | total);
-    } else {
-        st_relaxed_u64(st, kFlagAgg | total);
+    if (!rts) {
+        if (p == 0) {
+            st_relaxed_u64(st, kFlagIncl | total);
+        } else {
+            st_relaxed_u64(st, kFlagAgg | total);
+        }
     }
     const uint32_t doff = block_exclusive_scan_256(total, s_tmp);
     // Warp w's items of this digit start at doff + (earlier warps' count).
     for (int w = 0; w < kWarps; ++w) s_whist[w * kRadix + digit] += doff;
+    if (rts) {
+        // Reduce-then-scan: the partition's global offset per digit is known.
+        s_gdst[digit] = rts[(int64_t)digit * rts_stride] - doff;
+    }
 
     // Decoupled look-back for this digit over partitions p-1, p-2, ...,
     // reading kOsLookAhead status words per step so a chain of aggregates costs
     // one memory latency per kOsLookAhead partitions.
     unsigned long long excl = 0;
-    if (p > 0) {
+    if (!rts && p > 0) {
         unsigned long long t0 = 0;  // read at the first unpublished status word
         int64_t q = p - 1;
         uint32_t polls = 0;
@@ -136,7 +143,7 @@ __device__ __forceinline__ void onesweep_partition_body(const KT (&key)[ITEMS], 
     }
     // Global slot of the partition's i-th pair of this digit: gdst + i (pair
     // counts stay below 2^32, so the arithmetic is modulo 2^32).
-    s_gdst[digit] = bucket[digit] + (uint32_t)excl - doff;
+    if (!rts) s_gdst[digit] = bucket[digit] + (uint32_t)excl - doff;
     __syncthreads();
 
     // Reorder by digit in shared memory.
@@ -168,6 +175,8 @@ __device__ __forceinline__ void onesweep_partition_body(const KT (&key)[ITEMS], 
 // p: the partition's index in the order partitions were taken (a partition
 // only waits on earlier ones). status: this pass's look-back words
 // (parts x 256, zeroed); bucket: the pass's 256 exclusive digit offsets.
+// rts (reduce-then-scan passes): instead of the look-back, the partition's
+// global offset of digit d is rts[d * rts_stride] (status and bucket unused).
 // All 256 threads of the block call it.
 template <typename KT, int ITEMS>
 __device__ __forceinline__ void onesweep_partition(const KT (&key)[ITEMS], const uint32_t (&val)[ITEMS], int64_t base,
@@ -175,15 +184,16 @@ __device__ __forceinline__ void onesweep_partition(const KT (&key)[ITEMS], const
                                                    const uint32_t *bucket, KT *__restrict__ keys_out,
                                                    uint32_t *__restrict__ vals_out, uint32_t *d_err,
                                                    unsigned long long timeout_ns, bool ballot_rank,
-                                                   unsigned char *smem) {
+                                                   unsigned char *smem, const uint32_t *rts = nullptr,
+                                                   int64_t rts_stride = 0) {
     constexpr int kTile = kOsThreads * ITEMS;
     const int valid = (int)(n - base < kTile ? n - base : kTile);
     if (valid == kTile)
         onesweep_partition_body<KT, ITEMS, true>(key, val, valid, n, p, shift, status, bucket, keys_out, vals_out,
-                                                 d_err, timeout_ns, ballot_rank, smem);
+                                                 d_err, timeout_ns, ballot_rank, smem, rts, rts_stride);
     else
         onesweep_partition_body<KT, ITEMS, false>(key, val, valid, n, p, shift, status, bucket, keys_out, vals_out,
-                                                  d_err, timeout_ns, ballot_rank, smem);
+                                                  d_err, timeout_ns, ballot_rank, smem, rts, rts_stride);
 }
 
 }  // namespace gs

@@ -185,6 +185,154 @@ cudaError_t launch_passes(KT *keys, uint32_t *values, KT *alt_keys, uint32_t *al
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Reduce-then-scan digit passes, for long lists. A onesweep pass over many
+// partitions is held back by its look-back chains: every block walks back to
+// the nearest inclusive prefix while hundreds of partitions are in flight
+// (on a 174M-pair pass each 3072-pair partition lived ~80 us against ~10 us
+// of work). Here a pass is three launches and no block waits on another:
+//   1. each partition's 256 digit counts (reads the keys only);
+//   2. per digit, an exclusive scan over the partitions plus the digit's
+//      bucket offset: every partition's global offset per digit;
+//   3. the partition ranking and scatter of the onesweep pass, with those
+//      offsets in place of the look-back.
+// ---------------------------------------------------------------------------
+constexpr int kRtsItems = kLargeItems;
+constexpr int kRtsTile = kThreads * kRtsItems;
+constexpr int kRtsScanThreads = 1024;
+
+inline int64_t rts_parts(int64_t n) { return (n + kRtsTile - 1) / kRtsTile > 0 ? (n + kRtsTile - 1) / kRtsTile : 1; }
+
+template <typename KT>
+__global__ void __launch_bounds__(kThreads) rts_hist_kernel(const KT *__restrict__ keys, int64_t n_cap,
+                                                            const unsigned long long *d_n, int shift,
+                                                            int64_t stride, uint32_t *__restrict__ counts) {
+    __shared__ uint32_t h[kRadix];
+    const int tid = threadIdx.x;
+    const int64_t n = d_n ? (int64_t)*d_n : n_cap;
+    const int64_t base = (int64_t)blockIdx.x * kRtsTile;
+    if (base >= n) return;  // the scan reads only the partitions of the n pairs
+    h[tid] = 0;
+    __syncthreads();
+    const int cnt = (int)(n - base < kRtsTile ? n - base : kRtsTile);
+    for (int i = tid; i < cnt; i += kThreads) atomicAdd(&h[(uint32_t)(keys[base + i] >> shift) & 255u], 1u);
+    __syncthreads();
+    counts[(int64_t)tid * stride + blockIdx.x] = h[tid];
+}
+
+// Block d: exclusive scan of digit d's counts over the partitions, plus the
+// digit's bucket offset.
+__global__ void __launch_bounds__(kRtsScanThreads) rts_scan_kernel(const uint32_t *__restrict__ counts,
+                                                                   const uint32_t *__restrict__ bucket,
+                                                                   int64_t n_cap, const unsigned long long *d_n,
+                                                                   int64_t stride, uint32_t *__restrict__ offsets) {
+    __shared__ uint32_t s_w[kRtsScanThreads / 32];
+    __shared__ uint32_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = d_n ? (int64_t)*d_n : n_cap;
+    const int64_t parts = (n + kRtsTile - 1) / kRtsTile;
+    const uint32_t *c = counts + (int64_t)blockIdx.x * stride;
+    uint32_t *o = offsets + (int64_t)blockIdx.x * stride;
+    if (tid == 0) s_carry = bucket[blockIdx.x];
+    __syncthreads();
+    constexpr int kPer = 4;
+    for (int64_t c0 = 0; c0 < parts; c0 += (int64_t)kRtsScanThreads * kPer) {
+        uint32_t v[kPer], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t q = c0 + (int64_t)tid * kPer + k;
+            v[k] = q < parts ? c[q] : 0u;
+            sum += v[k];
+        }
+        uint32_t incl = sum;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = s_w[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += t;
+            }
+            s_w[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const uint32_t carry = s_carry;
+        uint32_t run = carry + (warp ? s_w[warp - 1] : 0u) + incl - sum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t q = c0 + (int64_t)tid * kPer + k;
+            if (q < parts) o[q] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == kRtsScanThreads - 1) s_carry = carry + s_w[31];
+        __syncthreads();
+    }
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(kThreads, 3)
+rts_scatter_kernel(const KT *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, KT *__restrict__ keys_out,
+                   uint32_t *__restrict__ vals_out, int64_t n_cap, const unsigned long long *d_n, int shift,
+                   int64_t stride, const uint32_t *__restrict__ offsets, uint32_t *d_err, bool ballot_rank) {
+    constexpr int kItems = kRtsItems;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = d_n ? (int64_t)*d_n : n_cap;
+    const int64_t p = blockIdx.x;
+    const int64_t base = p * kRtsTile;
+    if (base >= n) return;
+    KT key[kItems];
+    uint32_t val[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t idx = base + (int64_t)warp * 32 * kItems + j * 32 + lane;
+        key[j] = idx < n ? keys_in[idx] : (KT)~(KT)0;
+        val[j] = idx < n ? vals_in[idx] : 0u;
+    }
+    onesweep_partition<KT, kItems>(key, val, base, n, p, shift, nullptr, nullptr, keys_out, vals_out, d_err, 0ull,
+                                   ballot_rank, smem, offsets + p, stride);
+}
+
+template <typename KT>
+cudaError_t launch_passes_rts(KT *keys, uint32_t *values, KT *alt_keys, uint32_t *alt_values, int64_t n_capacity,
+                              const unsigned long long *d_n, const GsSortScratch &sc, void *rts_scratch,
+                              uint32_t *d_err, bool *result_in_alt, cudaStream_t s, int first_pass) {
+    *result_in_alt = false;
+    const int64_t parts = rts_parts(n_capacity);
+    uint32_t *counts = static_cast<uint32_t *>(rts_scratch);
+    uint32_t *offsets = counts + (int64_t)kRadix * parts;
+    const size_t smem = onesweep_smem<KT, kRtsItems>();
+    cudaError_t e = cudaFuncSetAttribute(rts_scatter_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const KT *kin = keys;
+    const uint32_t *vin = values;
+    KT *kout = alt_keys;
+    uint32_t *vout = alt_values;
+    for (int pass = first_pass; pass < sc.passes; ++pass) {
+        const int shift = 8 * (pass + sc.digit0);
+        const bool ballot = pass + 1 < sc.passes || sc.diverse_last;
+        rts_hist_kernel<KT><<<(unsigned)parts, kThreads, 0, s>>>(kin, n_capacity, d_n, shift, parts, counts);
+        rts_scan_kernel<<<kRadix, kRtsScanThreads, 0, s>>>(counts, sc.bucket + pass * kRadix, n_capacity, d_n, parts,
+                                                           offsets);
+        rts_scatter_kernel<KT><<<(unsigned)parts, kThreads, smem, s>>>(kin, vin, kout, vout, n_capacity, d_n, shift,
+                                                                       parts, offsets, d_err, ballot);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        kin = kout;
+        vin = vout;
+        kout = (kout == alt_keys) ? keys : alt_keys;
+        vout = (vout == alt_values) ? values : alt_values;
+    }
+    *result_in_alt = sc.passes > first_pass && ((sc.passes - first_pass) & 1) != 0;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 int gs_sort_passes(int key_bits) { return (key_bits + 7) / 8; }
@@ -254,6 +402,22 @@ cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
                            uint32_t *d_err, bool *result_in_alt, cudaStream_t s) {
     *result_in_alt = false;
     if (n <= 1 || key_bits <= 0) return cudaSuccess;
+    if (n >= kRtsMinPairs) {
+        // Long lists: reduce-then-scan passes. Their per-partition counts and
+        // offsets (2 KB per 3072 pairs) fit where the onesweep look-back
+        // words (2 KB per 3072 pairs and pass) would go.
+        const int passes = gs_sort_passes(key_bits);
+        const size_t head = header_bytes(passes);  // histograms, buckets, ticket
+        cudaError_t e = cudaMemsetAsync(scratch, 0, head, s);
+        if (e != cudaSuccess) return e;
+        const GsSortScratch sc = gs_sort_carve_digits(scratch, 1, 0, passes);
+        const unsigned hist_blocks = (unsigned)(rts_parts(n) < 608 ? rts_parts(n) : 608);
+        histogram_kernel<<<hist_blocks, kThreads, 0, s>>>(keys, n, sc.passes, sc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_passes_rts<uint64_t>(keys, values, alt_keys, alt_values, n, nullptr, sc,
+                                           static_cast<char *>(scratch) + head, d_err, result_in_alt, s, 0);
+    }
     cudaError_t e = cudaMemsetAsync(scratch, 0, gs_sort_scratch_bytes(n, key_bits), s);
     if (e != cudaSuccess) return e;
     const GsSortScratch sc = gs_sort_carve(scratch, n, key_bits);
@@ -263,4 +427,30 @@ cudaError_t gs_launch_sort(uint64_t *keys, uint32_t *values, uint64_t *alt_keys,
     if (e != cudaSuccess) return e;
     return gs_launch_sort_passes(keys, values, alt_keys, alt_values, n, nullptr, sc, d_err,
                                  result_in_alt, s);
+}
+
+size_t gs_sort_rts_scratch_bytes(int64_t n_capacity) { return (size_t)2 * kRadix * rts_parts(n_capacity) * 4; }
+
+cudaError_t gs_launch_sort_passes_rts(uint16_t *keys, uint32_t *values, uint16_t *alt_keys, uint32_t *alt_values,
+                                      int64_t n_capacity, const unsigned long long *d_n, const GsSortScratch &sc,
+                                      void *rts_scratch, uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                      int first_pass) {
+    return launch_passes_rts<uint16_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, rts_scratch, d_err,
+                                       result_in_alt, s, first_pass);
+}
+
+cudaError_t gs_launch_sort_passes_rts(uint32_t *keys, uint32_t *values, uint32_t *alt_keys, uint32_t *alt_values,
+                                      int64_t n_capacity, const unsigned long long *d_n, const GsSortScratch &sc,
+                                      void *rts_scratch, uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                      int first_pass) {
+    return launch_passes_rts<uint32_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, rts_scratch, d_err,
+                                       result_in_alt, s, first_pass);
+}
+
+cudaError_t gs_launch_sort_passes_rts(uint64_t *keys, uint32_t *values, uint64_t *alt_keys, uint32_t *alt_values,
+                                      int64_t n_capacity, const unsigned long long *d_n, const GsSortScratch &sc,
+                                      void *rts_scratch, uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
+                                      int first_pass) {
+    return launch_passes_rts<uint64_t>(keys, values, alt_keys, alt_values, n_capacity, d_n, sc, rts_scratch, d_err,
+                                       result_in_alt, s, first_pass);
 }
