@@ -303,10 +303,10 @@ __device__ __forceinline__ uint32_t ld_peer_u32(uint32_t a) {
 template <int CX, int CY, int BW, int BH, int S>
 __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kernel(const BlendArgs a) {
     constexpr int TW = 16, TH = 16, NC = CX * CY, L = NC * S;
-    constexpr int kWX = TW / BW, kThreads = kWX * (TH / BH) * 32;
+    constexpr int kWX = TW / BW, kThreads = kWX * (TH / BH) * 32, kWarps = kThreads / 32;
     constexpr int kRows = 32 / BW, kNP = BW * BH / 32;
     static_assert(kRows * kNP == BH && kThreads <= 256, "block shape");
-    static_assert(L % kThreads == 0, "batch shape");
+    static_assert(L % kThreads == 0 && S <= kThreads, "batch shape");
     // This block's share of a batch, read by the whole cluster.
     __shared__ float4 s_sa[S], s_scol[S], s_sbox[S];
     __shared__ float2 s_sb[S];
@@ -319,8 +319,7 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
     __shared__ int2 s_ptile[NC];   // the cluster's screen tiles, by rank
     __shared__ int2 s_tile;        // this block's screen tile (read by peers)
     __shared__ int s_done;         // all of this block's pixels have stopped (read by peers)
-    __shared__ uint32_t s_tmp[8];
-    const SRec SL{s_sa, s_sb, s_scol, s_sbox};
+    __shared__ uint32_t s_wcnt[2][kWarps];
 
     const uint32_t rank = cluster_ctarank();
     const int tx = blockIdx.x, ty = blockIdx.y;
@@ -355,16 +354,19 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
     }
     __syncthreads();
 
+    const SRec SL{s_sa, s_sb, s_scol, s_sbox};
     for (uint32_t start = first; start < last; start += L) {
         // Done flags of the previous batch, published by the barrier below;
-        // every block reads the same flags, so all leave together.
+        // every block reads the same flags, so all leave together (before
+        // staging a batch nobody needs). The barrier also ends every peer's
+        // reads of this block's previous share.
         const int cta_done = __syncthreads_and(warp_done);
         if (tid == 0) s_done = cta_done;
         cluster_sync_all();
         const int peer_done = tid < NC ? (int)ld_peer_u32(peer_addr(&s_done, (uint32_t)tid)) : 1;
         if (__syncthreads_and(peer_done)) break;
         // Stage this block's share of the batch (list entries start + rank,
-        // start + rank + NC, ...) and mark its tiles.
+        // start + rank + NC, ...) and mark the cluster tiles each can reach.
         const int n_batch = (int)min((uint32_t)L, last - start);
         for (int i = tid; i < S; i += kThreads) {
             const uint32_t k = start + rank + (uint32_t)(NC * i);
@@ -390,24 +392,34 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
             }
             s_smask[i] = m;
         }
-        cluster_sync_all();
+        cluster_sync_all();  // every share staged
         // Gather the records marked for this tile, in list order (entry
-        // start + j sits in slot j / NC of rank j % NC).
+        // start + j sits in slot j / NC of rank j % NC); per round of
+        // kThreads entries, warp counts give each warp its place.
         int cnt = 0;
-        for (int j0 = 0; j0 < n_batch; j0 += kThreads) {
+        for (int j0 = 0, rd_ = 0; j0 < n_batch; j0 += kThreads, rd_ ^= 1) {
             const int j = j0 + tid, sl = j % NC, i = j / NC;
             const uint32_t m = j < n_batch ? ld_peer_u32(peer_addr(&s_smask[i], (uint32_t)sl)) : 0u;
             const bool keep = (m >> rank) & 1u;
-            const uint32_t off = block_exclusive_scan_256(keep ? 1u : 0u, s_tmp);
+            const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) s_wcnt[rd_][warp] = __popc(ballot);
+            __syncthreads();
+            int before = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const int c = (int)s_wcnt[rd_][w];
+                before += w < warp ? c : 0;
+                total += c;
+            }
             if (keep) {
-                const int d = cnt + (int)off;
+                const int d = cnt + before + __popc(ballot & lanemask_lt());
                 s_a[d] = ld_peer_f4(peer_addr(&s_sa[i], (uint32_t)sl));
                 s_b[d] = ld_peer_f2(peer_addr(&s_sb[i], (uint32_t)sl));
                 s_col[d] = ld_peer_f4(peer_addr(&s_scol[i], (uint32_t)sl));
                 s_box[d] = ld_peer_f4(peer_addr(&s_sbox[i], (uint32_t)sl));
                 s_pos[d] = (int32_t)(start - first) + j + 1;
             }
-            cnt += __syncthreads_count(keep);
+            cnt += total;
         }
         __syncthreads();
         if (!warp_done) {
@@ -777,7 +789,7 @@ void launch_blend_variant(const BlendArgs &a, const GsGrid &grid, int variant, c
 namespace {
 template <int CX, int CY, int BW, int BH>
 cudaError_t launch_cluster(const BlendArgs &a, int width, int height, cudaStream_t s) {
-    constexpr int S = 512 / (CX * CY);  // records staged per block and batch (512 per cluster)
+    constexpr int S = 128;  // records staged per block and batch
     const int t16x = (width + 15) / 16, t16y = (height + 15) / 16;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((t16x + CX - 1) / CX * CX), (unsigned)((t16y + CY - 1) / CY * CY), 1);
