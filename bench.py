@@ -1,13 +1,14 @@
 """Forward-render throughput of the 3DGS rasterizer on one GB300.
 
 Default workload: the 1M-Gaussian clustered scene (SH degree 3) rendered at
-1920x1080 with 16x16 screen tiles, camera inside the scene. One step = one
+1920x1080 with 16x16 screen tiles, camera inside the scene. A frame is one
 whole forward pass (project -> bin -> blend) through the public C ABI
 (gs_render) with the Gaussians resident in HBM. The headline value renders
 consecutive frames on --frames-in-flight contexts / streams at once (each
-frame's latency-bound front end beside another frame's blend); the
-one-frame-at-a-time time (L2 flushed before each frame) and the per-stage
-times are reported beside it.
+frame's latency-bound front end beside another frame's blend); one step is
+one frame on each of those contexts (a batch of F frames), so every timed
+step keeps all F in flight. The one-frame-at-a-time time (L2 flushed before
+each frame) and the per-stage times are reported beside it.
 
 Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on the
 host cores instead (the reference arm for this build).
@@ -34,6 +35,9 @@ WORKLOADS = {
     "clustered_1m_1080p": "1M Gaussians (90% in 200 clusters, 10% uniform, 20 m box), SH3, "
                           "1920x1080, 16x16 tiles, camera inside the scene",
     "uniform_box_256": "10k Gaussians uniform in a box, SH0, 256x256, 16x16 tiles",
+    "imbalance_6m_4k_x8": "imbalance stress scene, first view: 6M Gaussians, 20% packed into 2% of the view, "
+                          "1% splats > 256 px, SH3, 3840x2160",
+    "imbalance_1m_4k_x2": "imbalance stress recipe at 1M Gaussians, first view, SH3, 3840x2160",
 }
 
 # FP32 operations per evaluated (pixel, Gaussian) pair that every evaluated
@@ -151,35 +155,38 @@ def peaks():
 
 
 def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary under
-    profiles/, or None if the kernel's source changed since that capture."""
-    import glob
+    """DRAM bytes per launch of `kernel` ("name@workload") from
+    profiles/traffic.json (written beside the committed ncu summaries), or
+    None if the kernel's source changed since that capture (its SHA-256
+    prefix is stored with the number)."""
     import hashlib
-    import re
-    pat = re.compile(r"<!-- traffic kernel=(\S+) bytes_per_launch=(\d+) source=(\S+) sha256_16=([0-9a-f]+) -->")
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
-        with open(path) as f:
-            text = f.read()
-        for m in pat.finditer(text):
-            if m.group(1) != kernel:
-                continue
-            src = os.path.join(ROOT, m.group(3))
-            if not os.path.exists(src):
-                return None, None
-            with open(src, "rb") as f:
-                if hashlib.sha256(f.read()).hexdigest()[:16] != m.group(4):
-                    return None, None
-            return int(m.group(2)), os.path.relpath(path, ROOT)
-    return None, None
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        entry = json.load(f).get(kernel)
+    if not entry:
+        return None, None
+    src = os.path.join(ROOT, entry["source"])
+    if not os.path.exists(src):
+        return None, None
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != entry["sha256_16"]:
+            return None, None
+    return int(entry["bytes_per_launch"]), entry["summary"]
 
 
-def tile_key_plan(tiles_x: int, tiles_y: int, key_bits: int) -> tuple:
+RTS_MIN_PAIRS = 1 << 23  # key capacities from which gs_render sorts with reduce-then-scan passes
+
+
+def tile_key_plan(tiles_x: int, tiles_y: int, key_bits: int, capacity: int = 0) -> tuple:
     """(key bytes, digit passes, passes run inside the emission) of gs_render's
     tile sort. Grids at most 256 tiles wide use (row << 8 | column) keys whose
-    first (column) pass runs inside the emission kernel; wider grids sort
-    tile ids (key_bits - 32 bits, key_bits as the library reports it) in
-    separate passes. Keys of at most 16 bits are 2 bytes, else 4."""
-    if tiles_x <= 256:
+    first (column) pass runs inside the emission kernel; wider grids, and key
+    capacities from RTS_MIN_PAIRS on (reduce-then-scan passes), sort tile ids
+    (key_bits - 32 bits, key_bits as the library reports it) in separate
+    passes. Keys of at most 16 bits are 2 bytes, else 4."""
+    if tiles_x <= 256 and capacity < RTS_MIN_PAIRS:
         row_bits = max(0, (tiles_y - 1).bit_length())
         tkey_bits, fused = 8 + row_bits, 1
     else:
@@ -191,16 +198,18 @@ def tile_key_plan(tiles_x: int, tiles_y: int, key_bits: int) -> tuple:
 def frame_bytes(n, n_vis, K, sh_degree, tiles_x, tiles_y, key_bits, pixels) -> dict:
     """Bytes each forward stage has to move in DRAM, per frame: every mean
     and log-scale (the screen bound), rotation, opacity and SH of the visible
-    Gaussians, records of 48 B, list entries of 12 B (gathered into index
-    order, then four depth passes), tile keys of 2 or 4 B with 4-byte values
-    (written once by the emission, after its fused pass where there is one,
-    then read and written by each remaining pass), and the image (rgb + final
-    T + last contributor)."""
+    Gaussians, the 48-byte record and the 48-byte FP32 blend record of each
+    visible Gaussian, list entries of 12 B (gathered into index order, then
+    four depth passes), tile keys of 2 or 4 B with 4-byte values (written
+    once by the emission, after its fused pass where there is one, then read
+    and written by each remaining pass), and the image (rgb + final T + last
+    contributor). The blend reads each visible Gaussian's blend record once
+    (repeat reads across tiles come from L2)."""
     s = 3 * (sh_degree + 1) ** 2
     kb, passes, fused = tile_key_plan(tiles_x, tiles_y, key_bits)
     n_tiles = tiles_x * tiles_y
     return {
-        "project": n * 24 + n_vis * (20 + 4 * s) + n_vis * (48 + 12),
+        "project": n * 24 + n_vis * (20 + 4 * s) + n_vis * (48 + 48 + 12),
         "depth_sort": n_vis * 24 + 4 * n_vis * 24,
         "entry_scan": n_vis * 12,
         "emit": n_vis * (32 + 8) + K * (kb + 4),
@@ -245,7 +254,7 @@ def fwd_bwd(gs, torch, args, flush, local) -> dict:
     for _ in range(args.warmup):
         it()
     torch.cuda.synchronize()
-    steps = max(3, args.steps // 10)
+    steps = max(20, args.steps // 10)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     fwd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for i in range(steps):
@@ -582,6 +591,8 @@ def main():
     ap.add_argument("--blend-variant", type=int, default=0,
                     help="0 culled 8x4 blocks (default), 1 basic, 2 culled 16x8, 3 culled tile, 4 culled 8x8, "
                          "5 TMA staging")
+    ap.add_argument("--cluster", type=int, default=0, help="thread-block clusters of the blend: 0, 2 (2x1), 4 (2x2)")
+    ap.add_argument("--record-dtype", type=int, default=0, help="blend records: 0 FP32, 1 FP16, 2 BF16")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -598,6 +609,7 @@ def main():
 
     scene, cams = scenes.workload(args.workload)
     cam = cams[0]
+    ropt = {"cluster": args.cluster, "record_dtype": args.record_dtype}
     H, W = cam.height, cam.width
     g = gs.scene_to_device(scene)
     ctx = gs.Context(local)
@@ -608,7 +620,7 @@ def main():
     def step(deferred=True):
         # GS_SYNC_DEFERRED: the frame is enqueued without a host round trip
         # (its counts are checked by a later call), so frames run back to back.
-        gs.gs_render(ctx, g, scene.sh_degree, cam, rgb, variant=args.blend_variant, deferred=deferred)
+        gs.gs_render(ctx, g, scene.sh_degree, cam, rgb, variant=args.blend_variant, deferred=deferred, **ropt)
 
     for _ in range(args.warmup):
         step(False)
@@ -619,7 +631,7 @@ def main():
     gs.gs_sync_status(ctx)
 
     # Algorithmic work of one frame (deterministic): evaluated and blended pairs.
-    aux = gs.render(ctx, g, scene.sh_degree, cam, variant=args.blend_variant)
+    aux = gs.render(ctx, g, scene.sh_degree, cam, variant=args.blend_variant, **ropt)
     torch.cuda.synchronize()
     n_eval_total = int(aux["n_eval"].to(torch.int64).sum().item())
     stats = gs.gs_last_render_stats(ctx)
@@ -657,9 +669,10 @@ def main():
 
     # Frames in flight: consecutive frames go to F contexts on F streams (each
     # context owns its workspace), so one frame's latency-bound front end runs
-    # beside another's issue-bound blend. The inputs rotate over 8 copies of
-    # the scene (1.9 GB, far above L2), so no flush is needed; the timed region
-    # spans all frames, from one event before the first to one after the last.
+    # beside another's issue-bound blend. One step is F consecutive frames, one
+    # per context. The inputs rotate over 8 copies of the scene (1.9 GB, far
+    # above L2), so no flush is needed; the timed region spans all steps, from
+    # one event before the first frame to one after the last.
     F = max(1, args.frames_in_flight)
     copies = [g] + [{k: v.clone() for k, v in g.items()} for _ in range(7)]
     pctx = [ctx] + [gs.Context(local) for _ in range(F - 1)]
@@ -667,7 +680,7 @@ def main():
     prgb = [rgb] + [torch.empty_like(rgb) for _ in range(F - 1)]
     for k in range(F):
         for _ in range(args.warmup):
-            gs.gs_render(pctx[k], g, scene.sh_degree, cam, prgb[k], variant=args.pipeline_blend_variant)
+            gs.gs_render(pctx[k], g, scene.sh_degree, cam, prgb[k], variant=args.pipeline_blend_variant, **ropt)
     torch.cuda.synchronize()
     barrier(world)
     clocks2 = ClockSampler(local)
@@ -677,11 +690,11 @@ def main():
     p0.record(stream)
     for ps in pstreams:
         ps.wait_event(p0)
-    for i in range(args.steps):
+    for i in range(args.steps * F):
         k = i % F
         with torch.cuda.stream(pstreams[k]):
             gs.gs_render(pctx[k], copies[i % len(copies)], scene.sh_degree, cam, prgb[k],
-                         variant=args.pipeline_blend_variant, deferred=True, stream=pstreams[k])
+                         variant=args.pipeline_blend_variant, deferred=True, stream=pstreams[k], **ropt)
     for ps in pstreams:
         stream.wait_stream(ps)
     p1.record(stream)
@@ -692,7 +705,8 @@ def main():
         gs.gs_sync_status(c)
     pipe_ms = max_over_ranks(p0.elapsed_time(p1), world)
     ms_per_step = pipe_ms / args.steps
-    value = whole_job_rate(args.steps, pipe_ms, world)
+    ms_per_frame = pipe_ms / (args.steps * F)
+    value = whole_job_rate(args.steps * F, pipe_ms, world)
     for c in pctx[1:]:
         c.close()
     del copies
@@ -742,7 +756,8 @@ def main():
                         dev_in[nb][k].copy_(host[k], non_blocking=True)
                     copied[nb].record(copy_stream)
             stream.wait_event(copied[b])
-            gs.gs_render(ctx, dev_in[b], scene.sh_degree, cam, rgb, variant=args.blend_variant, deferred=True)
+            gs.gs_render(ctx, dev_in[b], scene.sh_degree, cam, rgb, variant=args.blend_variant, deferred=True,
+                         **ropt)
             consumed[b].record(stream)
             host_rgb[b].copy_(rgb, non_blocking=True)
 
@@ -789,7 +804,9 @@ def main():
     blend_ms = stage_ms.get("blend_ms", float("nan"))
     flops = FLOPS_PER_EVAL * n_eval_total
     achieved = flops / (blend_ms / 1e3) / 1e12
-    traffic, traffic_src = profiled_traffic("blend_culled_kernel" if args.blend_variant == 0 else "blend_basic_kernel")
+    blend_kernel = ("blend_cluster_kernel" if args.cluster > 1 else
+                    "blend_culled_kernel" if args.blend_variant == 0 else "blend_basic_kernel")
+    traffic, traffic_src = profiled_traffic(f"{blend_kernel}@{args.workload}")
     roofline = {"kernel": "gs_blend", "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak_tflops, 4), "traffic": traffic,
@@ -797,11 +814,17 @@ def main():
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_clock:.0f} MHz",
                 "units_per_launch": n_eval_total, "flops_per_unit": FLOPS_PER_EVAL,
                 "launch_ms": round(blend_ms, 4),
-                "note": "blend kernel alone, one frame at a time (default 8x4 blocks); with frames in "
-                        "flight the blend work of a frame per frame interval is in frames_in_flight_effective",
-                "frames_in_flight_effective": {
-                    "TFLOP/s": round(flops * value / world / 1e12, 3),
-                    "frac": round(flops * value / world / 1e12 / fp32_peak_tflops, 4)}}
+                "note": "blend kernel alone, one frame at a time (default 8x4 blocks), live CUDA events "
+                        "recorded by the library around the launch (gs_set_stage_timing)"}
+    # The headline loop's own roofline: with frames in flight the blend work of
+    # one frame is done once per frame interval, and the frame's DRAM bytes
+    # move once per frame interval.
+    roofline_headline = {
+        "loop": f"{F} frames in flight, GS_BLEND_CULLED_8X8 blend",
+        "frame_ms": round(ms_per_frame, 5),
+        "blend_alu": {"bound": "alu", "achieved": round(flops * value / world / 1e12, 3),
+                      "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
+                      "frac": round(flops * value / world / 1e12 / fp32_peak_tflops, 4)}}
 
     # HBM view of the same frame: bytes each stage must move / its live time.
     fbytes = frame_bytes(scene.n, stats["n_visible"], stats["n_keys"], scene.sh_degree, (W + 15) // 16,
@@ -814,13 +837,18 @@ def main():
         t = stage_ms.get(stage_of[k], float("nan"))
         gbs = b / (t / 1e3) / 1e9 if t > 0 else float("nan")
         hbm[k] = {"bytes": int(b), "ms": round(t, 4), "GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)}
-    frame_gbs = sum(fbytes.values()) / (ms_per_step / 1e3) / 1e9
-    hbm["frame"] = {"bytes": int(sum(fbytes.values())), "ms": round(ms_per_step, 4), "GB/s": round(frame_gbs, 1),
+    frame_gbs = sum(fbytes.values()) / (ms_per_frame / 1e3) / 1e9
+    hbm["frame"] = {"bytes": int(sum(fbytes.values())), "ms": round(ms_per_frame, 5), "GB/s": round(frame_gbs, 1),
                     "frac": round(frame_gbs / hbm_peak, 4), "peak_GB/s": hbm_peak,
-                    "peak_source": "measured" if pk_kind == "measured" else "fallback"}
+                    "peak_source": "measured" if pk_kind == "measured" else "fallback",
+                    "note": "per frame of the headline loop"}
+    roofline_headline["frame_hbm"] = {"bound": "hbm", "achieved": round(frame_gbs, 1), "peak": hbm_peak,
+                                      "unit": "GB/s", "frac": round(frame_gbs / hbm_peak, 4),
+                                      "bytes_per_frame": int(sum(fbytes.values()))}
 
     line = {
-        "metric": "frames/s (1080p, 1M Gaussians, forward)",
+        "metric": ("frames/s (1080p, 1M Gaussians, forward)" if args.workload == "clustered_1m_1080p"
+                   else f"frames/s ({args.workload}, forward)"),
         "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -828,8 +856,11 @@ def main():
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "n_visible": stats["n_visible"], "n_keys": stats["n_keys"],
                    "key_bits": stats["key_bits"], "blend_variant": args.blend_variant,
+                   "cluster": args.cluster, "record_dtype": args.record_dtype,
                    "sync_mode": "deferred (GS_SYNC_DEFERRED)",
                    "frames_in_flight": F,
+                   "frames_per_step": F,
+                   "ms_per_frame": round(ms_per_frame, 5),
                    "frames_in_flight_blend_variant": args.pipeline_blend_variant,
                    "inputs": "8 rotating copies of the scene (8 x 236 MB, above L2) in the frames-in-flight loop",
                    "single_stream_frame_ms": round(single_ms, 4),
@@ -848,6 +879,7 @@ def main():
                                  "slower direction (the two overlap)"}},
         "gpu_launches": None,
         "roofline": roofline,
+        "roofline_headline": roofline_headline,
         "hbm_roofline": hbm,
         "peaks": {"source": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
         "clocks": clk_pipe,
@@ -858,8 +890,8 @@ def main():
     # the first tile pass inside it on grids at most 256 tiles wide), the
     # other tile passes, ranges, blend.
     _, passes, fused = tile_key_plan((W + 15) // 16, (H + 15) // 16, stats["key_bits"])
-    per_step = 10 + passes - fused
-    line["gpu_launches"] = per_step * args.steps
+    per_frame = 10 + passes - fused
+    line["gpu_launches"] = per_frame * F * args.steps
     if not args.no_fwd_bwd:
         line["fwd_bwd"] = fwd_bwd(gs, torch, args, flush, local)
     if not args.no_batched:

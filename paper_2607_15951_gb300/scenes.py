@@ -304,4 +304,6 @@ def workload(name: str):
         return clustered(1_000_000, 3), trajectory(64, 1003)
     if name == "imbalance_6m_4k_x8":
         return imbalance(6_000_000, 4), random_poses(8, 1004)
+    if name == "imbalance_1m_4k_x2":
+        return imbalance(1_000_000, 4), random_poses(2, 1004)
     raise KeyError(name)

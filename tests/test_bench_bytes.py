@@ -23,11 +23,18 @@ def test_tile_key_plan(tiles, key_bits, plan):
     assert bench.tile_key_plan(*tiles, key_bits) == plan
 
 
+def test_long_lists_sort_tile_ids_in_separate_passes():
+    # From 8M key slots on, the library emits tile ids and sorts them with
+    # reduce-then-scan passes, none inside the emission.
+    assert bench.tile_key_plan(240, 135, 47, capacity=bench.RTS_MIN_PAIRS) == (2, 2, 0)
+    assert bench.tile_key_plan(240, 135, 47, capacity=bench.RTS_MIN_PAIRS - 1) == (2, 2, 1)
+
+
 def test_frame_bytes_hand_count():
     # 10 Gaussians, 4 visible, 7 keys, SH degree 0 (3 floats), 2x2 tiles, 32x32 pixels.
     fb = bench.frame_bytes(10, 4, 7, 0, 2, 2, 34, 1024)
     assert fb == {
-        "project": 10 * 24 + 4 * (20 + 12) + 4 * 60,   # means + log-scales; quats, opacity, SH; record + list
+        "project": 10 * 24 + 4 * (20 + 12) + 4 * 108,  # means + log-scales; quats, opacity, SH; 2 records + list
         "depth_sort": 4 * 24 + 4 * 4 * 24,              # gather, then four passes
         "entry_scan": 4 * 12,
         "emit": 4 * 40 + 7 * (2 + 4),                   # entries read; keys + values written once
