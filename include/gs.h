@@ -163,8 +163,9 @@ typedef struct {
                                (default), 1 = launch the kernels directly      */
     int32_t sync_mode;      /* gs_render: GS_SYNC_FRAME (default) or
                                GS_SYNC_DEFERRED, see gs_render                 */
-    int32_t temporal;       /* gs_render: 1 = temporal re-binning, see
-                               gs_render (needs GS_SYNC_FRAME)                 */
+    int32_t temporal;       /* gs_render: temporal re-binning, see gs_render
+                               (needs GS_SYNC_FRAME): 0 off, 1 adaptive, 2
+                               whenever possible                              */
     int32_t batch_mode;     /* gs_render_batch: GS_BATCH_AUTO (default),
                                GS_BATCH_JOINT or GS_BATCH_PER_VIEW             */
     int32_t batch_depth;    /* gs_render_batch, joint schedule: records staged
@@ -314,16 +315,21 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
  *                     have then grown and the caller renders again.
  *                     gs_render_backward waits for the frame it
  *                     differentiates and fails if that frame overflowed. */
-/* Temporal re-binning (opts->temporal = 1; the paper's temporal-locality
- * idea, Sec. 5.4 and Sec. 6): when the previous frame on this context was
- * rendered the same way with the same Gaussian count and tile grid, this
- * frame's per-tile lists are rebuilt from that frame's: only Gaussians whose
- * tile rect changed ("moved", counted in gs_render_stats.n_moved) leave and
- * enter tiles, and each tile is put in this frame's (depth, index) order by
- * a merge or an in-tile sort. The lists, and so the image, are identical to
- * those of a full binning. The frame is binned from scratch instead when
- * there is no such state, when more than a quarter of the visible Gaussians
- * moved in the previous frame, or when a tile list exceeds 4096 entries. */
+/* Temporal re-binning (opts->temporal = 1 or 2; the paper's temporal-
+ * locality idea, Sec. 5.4 and Sec. 6): when the previous frame on this
+ * context was rendered the same way with the same Gaussian count and tile
+ * grid, this frame's per-tile lists are rebuilt from that frame's: only
+ * Gaussians whose tile rect changed ("moved", counted in
+ * gs_render_stats.n_moved) leave and enter tiles, and each tile is put in
+ * this frame's (depth, index) order by a merge or an in-tile sort. The
+ * lists, and so the image, are identical to those of a full binning. The
+ * frame is binned from scratch instead when there is no such state, when
+ * more than 8 % of the visible Gaussians moved in the previous frame, or
+ * when a tile list exceeds 4096 entries. With temporal = 1 the context also
+ * times the binning of both kinds of frames (CUDA events) and bins in full
+ * while re-binned frames measured slower, trying one re-binned frame in 8
+ * to measure again; temporal = 2 re-bins whenever it can. The churn
+ * (n_moved) is measured on every frame either way. */
 gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
                     const gs_options *opts, const gs_framebuffer *fb, void *stream);
 

@@ -63,7 +63,7 @@ def camera_struct(cam) -> N.gs_camera:
 
 
 def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
-                   blend_variant: int = 0, deferred: bool = False, temporal: bool = False,
+                   blend_variant: int = 0, deferred: bool = False, temporal: int = 0,
                    cluster: int = 0) -> N.gs_options:
     o = N.gs_options()
     _lib().gs_default_options(ctypes.byref(o))
@@ -73,7 +73,7 @@ def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
     o.record_dtype = int(record_dtype)
     o.blend_variant = int(blend_variant)
     o.sync_mode = N.GS_SYNC_DEFERRED if deferred else N.GS_SYNC_FRAME
-    o.temporal = 1 if temporal else 0
+    o.temporal = int(temporal)  # False/0 off, True/1 adaptive, 2 re-bin whenever possible
     o.cluster = int(cluster)
     return o
 
@@ -209,7 +209,8 @@ def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_c
               stream=None) -> None:
     """deferred=True: GS_SYNC_DEFERRED (no host synchronisation; an overflow
     or device error is raised by a later call on the context).
-    temporal=True: re-bin from the previous frame's lists (same results).
+    temporal=True (or 1): re-bin from the previous frame's lists when that
+    measured faster (same results); 2: re-bin whenever possible.
     cluster: GS_CLUSTER_2X1 / _2X2 blend in thread-block clusters."""
     gs = gaussians_struct(g, sh_degree)
     c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred, temporal, cluster)

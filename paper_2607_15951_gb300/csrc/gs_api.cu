@@ -98,6 +98,13 @@ struct gs_context {
         int rcur = 0;         // rects[rcur] holds the last frame's packed tile rects
         int64_t rects_n = -1;  // ... for this many Gaussians (-1: none)
         double last_churn = 0.0;  // moved / visible of the last frame
+        // Adaptive gate (opts->temporal == 1): device time of the binning
+        // (projection to ranges) of re-binned and of full frames, averaged
+        // over recent frames, and a counter of frames binned in full since
+        // re-binning last measured slower.
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        double full_ms = 0.0, rebin_ms = 0.0;
+        uint32_t gate = 0;
     } temporal;
 };
 
@@ -167,7 +174,7 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
         return fail(ctx, GS_ERR_INVALID_ARG, "direct_launch must be 0 or 1");
     if (o->sync_mode != GS_SYNC_FRAME && o->sync_mode != GS_SYNC_DEFERRED)
         return fail(ctx, GS_ERR_INVALID_ARG, "sync_mode must be GS_SYNC_FRAME or GS_SYNC_DEFERRED");
-    if (o->temporal != 0 && o->temporal != 1) return fail(ctx, GS_ERR_INVALID_ARG, "temporal must be 0 or 1");
+    if (o->temporal < 0 || o->temporal > 2) return fail(ctx, GS_ERR_INVALID_ARG, "temporal must be 0, 1 or 2");
     if (o->temporal && o->sync_mode != GS_SYNC_FRAME)
         return fail(ctx, GS_ERR_INVALID_ARG, "temporal re-binning needs sync_mode GS_SYNC_FRAME");
     if (o->batch_mode < GS_BATCH_AUTO || o->batch_mode > GS_BATCH_PER_VIEW)
@@ -371,6 +378,35 @@ void drop_temporal(gs_context *ctx) {
     ctx->have_last = false;
 }
 
+// Temporal mode's binning time: events around projection .. ranges.
+void temporal_mark(gs_context *ctx, int k, cudaStream_t s) {
+    if (ctx->temporal.ev[k]) cudaEventRecord(ctx->temporal.ev[k], s);
+}
+
+// After a synchronised temporal frame: folds its binning time into the
+// average of its kind.
+void temporal_sample(gs_context *ctx, bool rebinned) {
+    auto &T = ctx->temporal;
+    float ms = 0.f;
+    if (!T.ev[0] || cudaEventElapsedTime(&ms, T.ev[0], T.ev[1]) != cudaSuccess) return;
+    double &avg = rebinned ? T.rebin_ms : T.full_ms;
+    avg = avg > 0.0 ? 0.5 * avg + 0.5 * ms : ms;
+}
+
+// Whether a frame that may be re-binned should be. temporal == 2 always
+// re-bins; temporal == 1 re-bins while re-binned frames measured no slower
+// than full ones (2 % margin), and otherwise bins in full, re-binning one
+// frame in 8 to measure again (the scene, the camera motion or the GPU's
+// load may change).
+bool temporal_rebin_now(gs_context *ctx, int temporal) {
+    auto &T = ctx->temporal;
+    if (temporal == 2 || T.rebin_ms <= 0.0 || T.full_ms <= 0.0 || T.rebin_ms <= 1.02 * T.full_ms) {
+        T.gate = 0;
+        return true;
+    }
+    return (++T.gate % 8u) == 0u;
+}
+
 // Records what gs_render_backward needs of the frame just enqueued (seq: its
 // deferred sequence number, 0 for a synchronised frame).
 void remember_frame(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam, const gs_options *opts,
@@ -553,6 +589,7 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     mark(ctx, EV_START, s);
     const uint2 *prev_rect = static_cast<const uint2 *>(T.rects[T.rcur].ptr);
     uint2 *rect = static_cast<uint2 *>(T.rects[T.rcur ^ 1].ptr);
+    temporal_mark(ctx, 0, s);
     GS_CUDA(ctx, gs_launch_project_temporal(*g, make_cam(cam), grid, rec, blend_out(ctx, dtype), prev_rect, rect,
                                             static_cast<uint8_t *>(T.moved.ptr),
                                             static_cast<unsigned long long *>(T.moved_list.ptr), item_cap,
@@ -589,6 +626,7 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     R.cap_entries = kTemporalTileCap;
     R.d_err = ctx->d_err;
     GS_CUDA(ctx, gs_launch_temporal_rebin(R, s));
+    temporal_mark(ctx, 1, s);
     mark(ctx, EV_SORT, s);
     mark(ctx, EV_RANGES, s);
     if ((st = launch_blend(ctx, reader(ctx, rec, dtype), vals, ranges, grid, cam, opts, fb, counters + 3, cap, s)) !=
@@ -622,6 +660,7 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     T.rcur ^= 1;
     T.rects_n = n;
     T.last_churn = visible > 0 ? (double)h[1] / (double)visible : 0.0;
+    temporal_sample(ctx, true);
     if (ctx->timing) ctx->timed_once = true;
     remember_frame(ctx, g, cam, opts, grid, vals, ranges, 0);
     *done = true;
@@ -691,6 +730,8 @@ void gs_destroy(gs_context *ctx) {
         if (p.done) cudaEventDestroy(p.done);
     for (int i = 0; i < EV_COUNT; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    for (auto &e : ctx->temporal.ev)
+        if (e) cudaEventDestroy(e);
     auto &B = ctx->batch;
     DevBuf *bb[] = {&B.views, &B.rec, &B.meta, &B.geo, &B.aux, &B.col, &B.scratch, &B.ranges, &B.order,
                     &B.queue, &B.keys, &B.vals, &B.akeys, &B.avals, &B.sort, &B.d_rec, &B.bviews, &B.rts};
@@ -869,7 +910,9 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         if (T.valid && (T.n != n || T.tiles_x != grid.tiles_x || T.tiles_y != grid.tiles_y ||
                         T.tw != grid.tile_w || T.th != grid.tile_h))
             T.valid = false;
-        if (T.valid && T.last_churn <= kTemporalMaxChurn && n > 0) {
+        for (int k = 0; k < 2; ++k)
+            if (!T.ev[k]) GS_CUDA(ctx, cudaEventCreate(&T.ev[k]));
+        if (T.valid && T.last_churn <= kTemporalMaxChurn && n > 0 && temporal_rebin_now(ctx, opts->temporal)) {
             bool done = false;
             if ((st = render_rebinned(ctx, g, cam, opts, fb, s, &done)) != GS_OK) return st;
             if (done) return GS_OK;
@@ -925,6 +968,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         // byte of tile ids once the low byte is sorted.
         sc.diverse_last = xy_keys || rts;
         mark(ctx, EV_START, s);
+        if (temporal) temporal_mark(ctx, 0, s);
         cudaEvent_t ev3[3] = {nullptr, nullptr, nullptr};
         if (ctx->timing) {
             ev3[0] = ctx->ev[EV_PROJECT];
@@ -965,6 +1009,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         GS_CUDA(ctx, gs_launch_ranges_tiles(sk, key_bytes, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s,
                                             xy_keys ? grid.tiles_x : 0));
         mark(ctx, EV_RANGES, s);
+        if (temporal) temporal_mark(ctx, 1, s);
         if ((st = launch_blend(ctx, reader(ctx, rec, dtype), sv, ranges, grid, cam, opts, fb, ctx->d_counts + 2,
                                cap, s)) != GS_OK)
             return st;
@@ -1024,6 +1069,9 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             T.last_churn = have_prev_rects && ctx->stats.n_visible > 0
                                ? (double)ctx->h_counts[4] / (double)ctx->stats.n_visible
                                : 0.0;
+            // Only frames that compared rects with a previous frame's are
+            // the full-binning side of the gate's comparison.
+            if (have_prev_rects) temporal_sample(ctx, false);
         }
         // The sort grids cover the capacity: when it is far above this frame's
         // count, bring it down to twice the count (the buffers themselves only

@@ -37,7 +37,7 @@ def test_rebinned_frames_equal_full_binning(built, kind, step):
     rebinned, moved = [], []
     for c in cams:
         ref = gs.render(full, g, scene.sh_degree, c)
-        out = gs.render(temp, g, scene.sh_degree, c, temporal=True)
+        out = gs.render(temp, g, scene.sh_degree, c, temporal=2)
         torch.cuda.synchronize()
         _equal(ref, out)
         st = gs.gs_last_render_stats(temp)
@@ -64,7 +64,7 @@ def test_rebinned_moved_frames_match_oracle(built, oracle_mod):
     cams = scenes.motion("orbit", 4, 480, 272, step=0.1)
     ctx = gs.Context(0)
     for i, c in enumerate(cams):
-        out = gs.render(ctx, g, scene.sh_degree, c, temporal=True)
+        out = gs.render(ctx, g, scene.sh_degree, c, temporal=2)
         torch.cuda.synchronize()
         st = gs.gs_last_render_stats(ctx)
         if i == 0:
@@ -75,6 +75,26 @@ def test_rebinned_moved_frames_match_oracle(built, oracle_mod):
         cmp.pop("keep")
         print("re-binned frame", i, "moved", st["n_moved"], "vs FP64:", cmp)
         assert cmp["max_rgb_err"] <= RGB_TOL and cmp["max_T_err"] <= RGB_TOL, cmp
+
+
+def test_adaptive_gate_keeps_frames_exact(built):
+    """temporal = 1: the context times re-binned and full frames and picks
+    the faster, re-trying re-binning now and then; every frame still equals
+    the full binning's, and at least the first eligible frame is re-binned
+    (to measure it)."""
+    scene = scenes.clustered(200_000, 37, box=8.0)
+    g = gs.scene_to_device(scene)
+    cams = scenes.motion("static", 40, 480, 272)
+    full, temp = gs.Context(0), gs.Context(0)
+    rebinned = []
+    for c in cams:
+        ref = gs.render(full, g, scene.sh_degree, c)
+        out = gs.render(temp, g, scene.sh_degree, c, temporal=1)
+        torch.cuda.synchronize()
+        _equal(ref, out)
+        rebinned.append(gs.gs_last_render_stats(temp)["rebinned"])
+    assert not rebinned[0] and rebinned[1], rebinned
+    print("adaptive gate, static camera: re-binned frames", sum(rebinned), "of", len(rebinned))
 
 
 def test_rebinning_falls_back_and_recovers(built):
@@ -125,7 +145,7 @@ def test_backward_after_rebinned_frame(built):
         g = gs.scene_to_device(scene)
         out = None
         for c in cams:
-            out = gs.render(ctx, g, scene.sh_degree, c, temporal=temporal)
+            out = gs.render(ctx, g, scene.sh_degree, c, temporal=2 if temporal else 0)
         d_rgb = torch.sign(out["rgb"] - target) / target.numel()
         gr = {k: torch.empty_like(v) for k, v in g.items()}
         gs.gs_render_backward(ctx, g, scene.sh_degree, cams[-1], out["final_T"], out["n_contrib"],
