@@ -246,17 +246,17 @@ __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32,
 // list's batches through distributed shared memory: per batch of CX CY S
 // records each block stages S of them (one global / L2 read per record and
 // cluster instead of one per screen tile; entries are dealt out round-robin)
-// and marks which of the cluster's tiles each can reach (the exact rectangle test of the culled schedule);
-// after a cluster barrier every block copies, in list order, the records
-// marked for its own tile from its peers' shared memory into its local
-// batch and blends it with the culled schedule. A record is marked for a
-// tile only if the tile lies in the record's 16 x 16 tile rect, so every
-// tile sees exactly its default list, in the same (depth, index) order. The cluster keeps staging
-// until every one of its blocks is done (a flag per block, read after a
-// cluster barrier, so all blocks take the same number of barriers). List
-// positions (n_contrib, n_eval) refer to the list tile's list; colours and
-// transmittance equal those of the per-16x16-tile lists bit for bit, because
-// each pixel sees the same records in the same order.
+// and marks the cluster tiles each may reach: those in the record's 16 x 16
+// tile rect (the rule of the default lists) that its conservative box meets.
+// After a cluster barrier every block copies, in list order, the records
+// marked for its own tile from its peers' shared memory into its local batch
+// and blends it with the culled schedule, so every tile walks its default
+// list, in the same (depth, index) order, less records that cannot reach it.
+// The cluster keeps staging until every one of its blocks is done (a flag per
+// block, read after a cluster barrier, so all blocks take the same number of
+// barriers). List positions (n_contrib, n_eval) refer to the list tile's
+// list; colours and transmittance equal those of the per-16x16-tile lists
+// bit for bit, because each pixel sees the same records in the same order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -376,23 +376,24 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
                 stage_record(a.rd, gi, i, SL, true);
                 // A tile takes the record only if its 16 x 16 tile rect (the
                 // rule of the default lists, from the record's integer
-                // radius) holds the tile, and a pixel of the tile can reach
-                // alpha >= 1/255.
-                const float4 ra = s_sa[i];
+                // radius) holds the tile and the record's conservative box
+                // meets the tile (the warps test the exact ellipse later).
+                const float4 ra = s_sa[i], bx = s_sbox[i];
                 const int rad = __ldg(reinterpret_cast<const int *>(a.rd.rec32 + 3 * (size_t)gi + 2) + 2);
                 const Rect R16 = tile_rect(ra.x, ra.y, rad, TW, TH, 1 << 30, 1 << 30);
 #pragma unroll
                 for (int r = 0; r < NC; ++r) {
                     const float4 R = s_rect[r];
                     const int2 t = s_ptile[r];
-                    if (t.x >= R16.x0 && t.x < R16.x1 && t.y >= R16.y0 && t.y < R16.y1 && R.x <= R.y && R.z <= R.w &&
-                        record_touches(ra, s_sb[i], s_sbox[i], R.x, R.y, R.z, R.w))
+                    if (t.x >= R16.x0 && t.x < R16.x1 && t.y >= R16.y0 && t.y < R16.y1 && R.x <= R.y &&
+                        R.z <= R.w && bx.x <= R.y && bx.y >= R.x && bx.z <= R.w && bx.w >= R.z)
                         m |= 1u << r;
                 }
             }
             s_smask[i] = m;
         }
         cluster_sync_all();  // every share staged
+        if (cta_done) continue;  // this tile is finished: it only stages for its peers
         // Gather the records marked for this tile, in list order (entry
         // start + j sits in slot j / NC of rank j % NC); per round of
         // kThreads entries, warp counts give each warp its place.
