@@ -7,6 +7,8 @@ import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
 
 
 def _run(args, env_extra=None, timeout=300):
@@ -23,7 +25,9 @@ def test_reference_line_has_the_contract_keys(oracle_mod):
     assert len(lines) == 1
     d = lines[0]
     assert d["impl"] == "reference"
-    assert d["metric"] == "frames/s (1080p, 1M Gaussians, forward)"
+    # The same metric string and config object as the GPU arm's line.
+    assert d["metric"] == bench.headline_metric("uniform_box_256")
+    assert d["config"] == bench.headline_config("uniform_box_256")
     assert d["unit"] == "frames/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 1
     assert d["config"]["workload"] == "uniform_box_256"

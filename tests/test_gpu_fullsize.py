@@ -1,13 +1,13 @@
 """The full-size paths that only long key lists reach, in the launch
 configuration the benchmark times:
 
-* the onesweep sort's long-list partition shape (12 items per thread, three
-  blocks per SM, used from 8M pairs on), against numpy's stable argsort at
-  9M and 33M pairs with 16-, 32- and 64-bit keys;
+* the reduce-then-scan sort passes used from 8M pairs on (per-partition
+  digit counts, a scan per digit, a scatter with known offsets), against
+  numpy's stable argsort at 9M and 33M pairs with 16-, 32- and 64-bit keys;
 * the 64-view trajectory batch (1M Gaussians, views alternating 1280x720 and
   640x480, FP16 records, 16x16 tiles, staging depth 128): a joint batch of
-  about 25M keys whose global tile sort runs three 8-bit passes over 32-bit
-  tile ids in the long-list shape; every view equals its single-view render
+  about 25M keys whose global tile sort runs three reduce-then-scan passes
+  over 32-bit tile ids; every view equals its single-view render
   bit for bit, and one view of each size is within the FP16 bound of the
   FP64 oracle;
 * the automatic switch of gs_render_batch to view-by-view rendering after a
