@@ -608,11 +608,11 @@ def main():
     ap.add_argument("--no-imbalance", action="store_true")
     ap.add_argument("--frames-in-flight", type=int, default=8,
                     help="consecutive frames rendered on this many contexts / streams at once (headline value)")
-    ap.add_argument("--pipeline-blend-variant", type=int, default=4,
-                    help="blend schedule of the frames-in-flight loop (4: 8x8 blocks, fewest instructions)")
+    ap.add_argument("--pipeline-blend-variant", type=int, default=0,
+                    help="blend schedule of the frames-in-flight loop (0: the default, 8x8 blocks in packed pairs)")
     ap.add_argument("--blend-variant", type=int, default=0,
-                    help="0 culled 8x4 blocks (default), 1 basic, 2 culled 16x8, 3 culled tile, 4 culled 8x8, "
-                         "5 TMA staging")
+                    help="0 culled (default: 8x8 blocks, two pixels per lane in packed FP32 pairs), 1 basic, "
+                         "2 culled 16x8, 3 culled tile, 4 culled 8x8, 5 TMA staging")
     ap.add_argument("--cluster", type=int, default=0, help="thread-block clusters of the blend: 0, 2 (2x1), 4 (2x2)")
     ap.add_argument("--record-dtype", type=int, default=0, help="blend records: 0 FP32, 1 FP16, 2 BF16")
     args = ap.parse_args()
@@ -836,13 +836,13 @@ def main():
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_clock:.0f} MHz",
                 "units_per_launch": n_eval_total, "flops_per_unit": FLOPS_PER_EVAL,
                 "launch_ms": round(blend_ms, 4),
-                "note": "blend kernel alone, one frame at a time (default 8x4 blocks), live CUDA events "
+                "note": "blend kernel alone, one frame at a time (default schedule), live CUDA events "
                         "recorded by the library around the launch (gs_set_stage_timing)"}
     # The headline loop's own roofline: with frames in flight the blend work of
     # one frame is done once per frame interval, and the frame's DRAM bytes
     # move once per frame interval.
     roofline_headline = {
-        "loop": f"{F} frames in flight, GS_BLEND_CULLED_8X8 blend",
+        "loop": f"{F} frames in flight, blend schedule {args.pipeline_blend_variant}",
         "frame_ms": round(ms_per_frame, 5),
         "blend_alu": {"bound": "alu", "achieved": round(flops * value / world / 1e12, 3),
                       "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",

@@ -109,22 +109,24 @@ typedef struct {
 } gs_framebuffer;
 
 /* Blend schedules; all produce identical outputs.
- *   GS_BLEND_CULLED       each warp owns an 8x4 pixel block and skips records
- *                         that cannot reach alpha >= 1/255 in it (default);
- *                         gs_render switches to 8x8 blocks (as
- *                         GS_BLEND_CULLED_8X8) after a frame that averaged
- *                         more than 1024 keys per tile
+ *   GS_BLEND_CULLED       each warp owns a pixel block and skips records that
+ *                         cannot reach alpha >= 1/255 in it (default):
+ *                         gs_render uses 8x8 blocks (as GS_BLEND_CULLED_8X8;
+ *                         with thread-block clusters, 8x4 blocks until a
+ *                         frame averaged more than 1024 keys per list tile);
+ *                         gs_blend on caller-provided gs_records 8x4 blocks
  *   GS_BLEND_BASIC        one thread per pixel evaluates every record of its
  *                         tile
  *   GS_BLEND_CULLED_WIDE  as CULLED with 16x8 blocks (16-wide tiles; 8x8
  *                         tiles use 8x4 blocks)
  *   GS_BLEND_CULLED_TILE  as CULLED with one warp per 16x16 tile (other
  *                         tiles use 8x4 blocks)
- *   GS_BLEND_CULLED_8X8   as CULLED with 8x8 blocks (two pixels per lane):
- *                         fewer instructions per frame than CULLED but a
- *                         longer critical path per tile — slower for one
- *                         frame alone, faster when several frames are in
- *                         flight on other streams
+ *   GS_BLEND_CULLED_8X8   8x8 blocks, two pixels per lane: in gs_render
+ *                         (and gs_render_batch) the two pixels go through
+ *                         packed FP32 pair instructions (fma / mul / sub
+ *                         .f32x2, each element rounded as the scalar
+ *                         operation); gs_blend on gs_records computes them
+ *                         one at a time
  *   GS_BLEND_TMA          gs_render only (gs_blend falls back to CULLED): the
  *                         records of the sorted lists are first gathered in
  *                         list order, then each tile's batches are staged in
@@ -327,9 +329,13 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
  * more than 8 % of the visible Gaussians moved in the previous frame, or
  * when a tile list exceeds 4096 entries. With temporal = 1 the context also
  * times the binning of both kinds of frames (CUDA events) and bins in full
- * while re-binned frames measured slower, trying one re-binned frame in 8
- * to measure again; temporal = 2 re-bins whenever it can. The churn
- * (n_moved) is measured on every frame either way. */
+ * while re-binned frames measured slower, and re-bins only after a full
+ * frame measured the churn; once re-binning is ruled out (by
+ * that measurement or by the churn) the next 6 frames are rendered without
+ * tracking tile rects (n_moved = 0 on them), the two after them measure the
+ * churn again, and the gate tries one re-binned frame: one frame in 8
+ * re-measures. temporal = 2 re-bins whenever it can and measures the churn
+ * (n_moved) on every frame. */
 gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam,
                     const gs_options *opts, const gs_framebuffer *fb, void *stream);
 

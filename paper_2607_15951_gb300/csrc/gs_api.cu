@@ -105,6 +105,10 @@ struct gs_context {
         cudaEvent_t ev[2] = {nullptr, nullptr};
         double full_ms = 0.0, rebin_ms = 0.0;
         uint32_t gate = 0;
+        // Adaptive mode only: frames still to render without tracking rects
+        // (after a frame whose churn, or whose measured re-binning time,
+        // ruled re-binning out).
+        uint32_t cooldown = 0;
     } temporal;
 };
 
@@ -407,6 +411,15 @@ bool temporal_rebin_now(gs_context *ctx, int temporal) {
     return (++T.gate % 8u) == 0u;
 }
 
+// Adaptive mode: frames rendered without tracking rects once re-binning is
+// ruled out. Tracking (writing this frame's rects and comparing them with
+// the last frame's) costs every full frame some time, so after a frame that
+// found the churn above the limit, or that the gate sent to the full binning,
+// the next kTemporalCooldown frames skip it; the two frames after them track
+// again (the first writes rects, the second bins in full and measures the
+// churn), one frame in eight, as the gate re-measures.
+constexpr uint32_t kTemporalCooldown = 6;
+
 // Records what gs_render_backward needs of the frame just enqueued (seq: its
 // deferred sequence number, 0 for a synchronised frame).
 void remember_frame(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam, const gs_options *opts,
@@ -503,13 +516,17 @@ gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *ti
     return GS_OK;
 }
 
-// The default culled blend uses 8x4 warp blocks for shallow tile lists and
-// 8x8 blocks for deep ones (measured: 8x4 8 % faster at 141 entries per tile
-// on a 1080p frame, 8x8 faster at thousands per tile); the previous frame's
-// keys per tile decide. Both give identical images.
+// The default culled blend of gs_render uses 8x8 warp blocks, whose two
+// pixels per lane go through packed FP32 pair instructions (measured 0.188
+// against 0.197 ms for 8x4 blocks at 141 entries per tile on a 1080p frame,
+// and faster at thousands per tile). The cluster blend computes one pixel at
+// a time: 8x4 blocks for shallow lists, 8x8 for deep ones (more than 1024
+// entries per list tile in the previous frame). All give identical images.
 int blend_schedule(const gs_context *ctx, const gs_options *opts, int n_tiles) {
     if (opts->blend_variant != GS_BLEND_CULLED) return opts->blend_variant;
-    return ctx->stats.n_keys > (int64_t)1024 * n_tiles ? GS_BLEND_CULLED_8X8 : GS_BLEND_CULLED;
+    if (opts->cluster > 1)
+        return ctx->stats.n_keys > (int64_t)1024 * n_tiles ? GS_BLEND_CULLED_8X8 : GS_BLEND_CULLED;
+    return GS_BLEND_CULLED_8X8;
 }
 
 // The blend of a gs_render frame with `d_n` (device count, at most n_cap)
@@ -660,6 +677,7 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     T.rcur ^= 1;
     T.rects_n = n;
     T.last_churn = visible > 0 ? (double)h[1] / (double)visible : 0.0;
+    if (opts->temporal == 1 && T.last_churn > kTemporalMaxChurn) T.cooldown = kTemporalCooldown;
     temporal_sample(ctx, true);
     if (ctx->timing) ctx->timed_once = true;
     remember_frame(ctx, g, cam, opts, grid, vals, ranges, 0);
@@ -902,8 +920,15 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     gs_record *rec = static_cast<gs_record *>(ctx->records.ptr);
     uint32_t *ranges = static_cast<uint32_t *>(ctx->ranges.ptr);
     auto &T = ctx->temporal;
+    // temporal: the frame is rendered in temporal mode; track: it also
+    // writes and compares tile rects (not during an adaptive cool-down).
     const bool temporal = opts->temporal != 0;
-    if (!temporal) {
+    bool track = temporal;
+    if (temporal && opts->temporal == 1 && T.cooldown > 0) {
+        --T.cooldown;
+        track = false;
+    }
+    if (!track) {
         T.valid = false;
         T.rects_n = -1;
     } else {
@@ -912,10 +937,17 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             T.valid = false;
         for (int k = 0; k < 2; ++k)
             if (!T.ev[k]) GS_CUDA(ctx, cudaEventCreate(&T.ev[k]));
-        if (T.valid && T.last_churn <= kTemporalMaxChurn && n > 0 && temporal_rebin_now(ctx, opts->temporal)) {
-            bool done = false;
-            if ((st = render_rebinned(ctx, g, cam, opts, fb, s, &done)) != GS_OK) return st;
-            if (done) return GS_OK;
+        if (T.valid && T.last_churn <= kTemporalMaxChurn && n > 0) {
+            if (temporal_rebin_now(ctx, opts->temporal)) {
+                bool done = false;
+                if ((st = render_rebinned(ctx, g, cam, opts, fb, s, &done)) != GS_OK) return st;
+                if (done) return GS_OK;
+            } else {
+                // The gate chose the full binning: cool down, and let the
+                // gate re-bin the first frame it is asked about afterwards.
+                T.cooldown = kTemporalCooldown;
+                T.gate = 7;
+            }
         }
         if ((st = ensure(ctx, T.rects[0], (size_t)(n > 0 ? n : 1) * 8, "temporal rects")) != GS_OK ||
             (st = ensure(ctx, T.rects[1], (size_t)(n > 0 ? n : 1) * 8, "temporal rects")) != GS_OK)
@@ -925,9 +957,9 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     // to the previous frame's (if that frame had the same Gaussians and tile
     // grid) and counts the rects that changed: the churn that decides how the
     // next frame is binned.
-    const bool have_prev_rects = temporal && T.rects_n == n && T.tiles_x == grid.tiles_x &&
+    const bool have_prev_rects = track && T.rects_n == n && T.tiles_x == grid.tiles_x &&
                                  T.tiles_y == grid.tiles_y && T.tw == grid.tile_w && T.th == grid.tile_h;
-    uint2 *prect = temporal ? static_cast<uint2 *>(T.rects[T.rcur ^ (have_prev_rects ? 1 : 0)].ptr) : nullptr;
+    uint2 *prect = track ? static_cast<uint2 *>(T.rects[T.rcur ^ (have_prev_rects ? 1 : 0)].ptr) : nullptr;
     const uint2 *prev_rect = have_prev_rects ? static_cast<const uint2 *>(T.rects[T.rcur].ptr) : nullptr;
 
     // The key buffers are sized from earlier frames; if this frame needs more,
@@ -968,7 +1000,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         // byte of tile ids once the low byte is sorted.
         sc.diverse_last = xy_keys || rts;
         mark(ctx, EV_START, s);
-        if (temporal) temporal_mark(ctx, 0, s);
+        if (track) temporal_mark(ctx, 0, s);
         cudaEvent_t ev3[3] = {nullptr, nullptr, nullptr};
         if (ctx->timing) {
             ev3[0] = ctx->ev[EV_PROJECT];
@@ -1009,7 +1041,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         GS_CUDA(ctx, gs_launch_ranges_tiles(sk, key_bytes, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s,
                                             xy_keys ? grid.tiles_x : 0));
         mark(ctx, EV_RANGES, s);
-        if (temporal) temporal_mark(ctx, 1, s);
+        if (track) temporal_mark(ctx, 1, s);
         if ((st = launch_blend(ctx, reader(ctx, rec, dtype), sv, ranges, grid, cam, opts, fb, ctx->d_counts + 2,
                                cap, s)) != GS_OK)
             return st;
@@ -1054,7 +1086,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         remember_frame(ctx, g, cam, opts, grid, sv, ranges, 0);
         ctx->stats.n_moved = have_prev_rects ? (int64_t)ctx->h_counts[4] : 0;
         ctx->stats.rebinned = 0;
-        if (temporal) {
+        if (track) {
             T.valid = true;
             T.n = n;
             T.tiles_x = grid.tiles_x;
@@ -1066,12 +1098,19 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             T.cur = 0;
             if (have_prev_rects) T.rcur ^= 1;
             T.rects_n = n;
+            // Churn unknown (no earlier rects): temporal = 2 tries
+            // re-binning on the next frame; temporal = 1 first measures the
+            // churn on a full binning (a fast camera would make a re-binned
+            // frame cost more than the full binning saves).
             T.last_churn = have_prev_rects && ctx->stats.n_visible > 0
                                ? (double)ctx->h_counts[4] / (double)ctx->stats.n_visible
-                               : 0.0;
+                           : (!have_prev_rects && opts->temporal == 1) ? 1.0
+                                                                       : 0.0;
             // Only frames that compared rects with a previous frame's are
             // the full-binning side of the gate's comparison.
             if (have_prev_rects) temporal_sample(ctx, false);
+            if (opts->temporal == 1 && have_prev_rects && T.last_churn > kTemporalMaxChurn)
+                T.cooldown = kTemporalCooldown;
         }
         // The sort grids cover the capacity: when it is far above this frame's
         // count, bring it down to twice the count (the buffers themselves only

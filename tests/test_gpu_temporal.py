@@ -80,8 +80,8 @@ def test_rebinned_moved_frames_match_oracle(built, oracle_mod):
 def test_adaptive_gate_keeps_frames_exact(built):
     """temporal = 1: the context times re-binned and full frames and picks
     the faster, re-trying re-binning now and then; every frame still equals
-    the full binning's, and at least the first eligible frame is re-binned
-    (to measure it)."""
+    the full binning's, and the first frame after the churn was measured is
+    re-binned (to measure it)."""
     scene = scenes.clustered(200_000, 37, box=8.0)
     g = gs.scene_to_device(scene)
     cams = scenes.motion("static", 40, 480, 272)
@@ -93,8 +93,33 @@ def test_adaptive_gate_keeps_frames_exact(built):
         torch.cuda.synchronize()
         _equal(ref, out)
         rebinned.append(gs.gs_last_render_stats(temp)["rebinned"])
-    assert not rebinned[0] and rebinned[1], rebinned
+    # The first frame with rects to compare (frame 1) bins in full and
+    # measures the churn; frame 2 is re-binned.
+    assert not rebinned[0] and not rebinned[1] and rebinned[2], rebinned
     print("adaptive gate, static camera: re-binned frames", sum(rebinned), "of", len(rebinned))
+
+
+def test_adaptive_gate_cools_down_on_high_churn(built):
+    """temporal = 1 with a fast camera (churn far above the limit): after a
+    frame that measured the churn too high, six frames skip the rect tracking
+    (n_moved = 0), then one frame writes rects and the next bins in full and
+    measures the churn; every frame equals the full binning's."""
+    scene = scenes.clustered(200_000, 38, box=8.0)
+    g = gs.scene_to_device(scene)
+    cams = scenes.motion("rotate", 34, 480, 272, step=1.0)
+    full, temp = gs.Context(0), gs.Context(0)
+    moved = []
+    for c in cams:
+        ref = gs.render(full, g, scene.sh_degree, c)
+        out = gs.render(temp, g, scene.sh_degree, c, temporal=1)
+        torch.cuda.synchronize()
+        _equal(ref, out)
+        moved.append(gs.gs_last_render_stats(temp)["n_moved"])
+    tracked = [i for i, m in enumerate(moved) if m > 0]
+    print("adaptive gate, rotating camera: frames that measured the churn", tracked)
+    # Frame 1 bins in full and measures the churn; then one frame in eight:
+    # 9, 17, 25, 33.
+    assert tracked == list(range(1, len(cams), 8)), moved
 
 
 def test_rebinning_falls_back_and_recovers(built):
@@ -108,7 +133,7 @@ def test_rebinning_falls_back_and_recovers(built):
     cams = scenes.motion("translate", 3, 256, 256, step=0.001)
     full, temp = gs.Context(0), gs.Context(0)
     for c in cams:
-        _equal(gs.render(full, g, 0, c), gs.render(temp, g, 0, c, temporal=True))
+        _equal(gs.render(full, g, 0, c), gs.render(temp, g, 0, c, temporal=2))
         assert not gs.gs_last_render_stats(temp)["rebinned"]
     # Key buffers too small for the re-binned frame: it is binned again.
     scene = scenes.clustered(100_000, 33, box=8.0)
@@ -117,7 +142,7 @@ def test_rebinning_falls_back_and_recovers(built):
     full, temp = gs.Context(0), gs.Context(0)
     gs.gs_reserve_keys(temp, 2000)
     for c in cams:
-        _equal(gs.render(full, g, scene.sh_degree, c), gs.render(temp, g, scene.sh_degree, c, temporal=True))
+        _equal(gs.render(full, g, scene.sh_degree, c), gs.render(temp, g, scene.sh_degree, c, temporal=2))
 
 
 def test_intervening_calls_drop_the_state(built):
@@ -133,7 +158,7 @@ def test_intervening_calls_drop_the_state(built):
             k = torch.arange(1000, 0, -1, dtype=torch.int64, device="cuda")
             v = torch.arange(1000, dtype=torch.int32, device="cuda")
             gs.gs_sort_pairs(temp, k, v, 1000, 16)
-        _equal(gs.render(full, g, scene.sh_degree, c), gs.render(temp, g, scene.sh_degree, c, temporal=True))
+        _equal(gs.render(full, g, scene.sh_degree, c), gs.render(temp, g, scene.sh_degree, c, temporal=2))
 
 
 def test_backward_after_rebinned_frame(built):
