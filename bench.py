@@ -301,8 +301,8 @@ def batched(gs, torch, args, flush, local) -> dict:
     ctx = gs.Context(local)
     stream = torch.cuda.current_stream()
     outs = gs.alloc_outputs(cams)
-    tile, tune_ms, depth, cluster = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
-                                                         record_dtype=N.GS_RECORD_F16)
+    tile, tune_ms, depth, cluster, lists = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
+                                                                record_dtype=N.GS_RECORD_F16)
     iters = max(5, args.steps // 100)
 
     def timed(fn):
@@ -331,7 +331,7 @@ def batched(gs, torch, args, flush, local) -> dict:
 
     def batch():
         gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile, record_dtype=N.GS_RECORD_F16,
-                           batch_depth=depth, cluster=cluster)
+                           batch_depth=depth, cluster=cluster, list_tiles=lists)
 
     ms_pv_sync = timed(per_view)
     # Deferred frames cannot regrow in place: reserve room for the largest view.
@@ -377,8 +377,8 @@ def batched(gs, torch, args, flush, local) -> dict:
             "batched_f32_views_per_s": round(v / (ms_b32 / 1e3), 1),
             "speedup_batched_f16_vs_per_view_f32": round(ms_pv / ms_b, 3),
             "ms_per_batch": round(ms_b, 3), "autotuned_tile": list(tile), "autotuned_depth": depth,
-            "autotuned_cluster": cluster,
-            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2": [round(x, 3) for x in tune_ms],
+            "autotuned_cluster": cluster, "autotuned_list_tiles": lists,
+            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2_l2x1_l2x2": [round(x, 3) for x in tune_ms],
             "keys_per_batch": st["n_keys"], "iters": iters,
             "fwd_bwd_batched_f16_ms": round(ms_fb_b, 3), "fwd_bwd_per_view_f32_ms": round(ms_fb_v, 3),
             "fwd_bwd_speedup": round(ms_fb_v / ms_fb_b, 3),
@@ -455,8 +455,8 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
     ctx = gs.Context(local)
     stream = torch.cuda.current_stream()
     outs = gs.alloc_outputs(cams)
-    tile, tune_ms, depth, cluster = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
-                                                         record_dtype=N.GS_RECORD_BF16)
+    tile, tune_ms, depth, cluster, lists = gs.gs_autotune_batch(ctx, g, scene.sh_degree, cams, outs,
+                                                                record_dtype=N.GS_RECORD_BF16)
     iters = 3
 
     def timed(fn):
@@ -475,7 +475,7 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
 
     ms_batch = timed(lambda: gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, tile=tile,
                                                 record_dtype=N.GS_RECORD_BF16, batch_depth=depth,
-                                                cluster=cluster))
+                                                cluster=cluster, list_tiles=lists))
     keys_batch = gs.gs_last_render_stats(ctx)["n_keys"]
     k_max = 0
     for c, o in zip(cams, outs):
@@ -497,7 +497,7 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
             p.grad = None
         for c, tgt in zip(cams, targets):
             rgb, _ = gs.RasterizeGaussians(*params, ctx, c, scene.sh_degree, record_dtype=N.GS_RECORD_BF16,
-                                           cluster=cluster)
+                                           cluster=cluster, list_tiles=lists)
             (rgb - tgt).abs().mean().backward()
 
     ms_fb = timed(fwd_bwd_views)
@@ -511,9 +511,10 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
             "speedup_batched_bf16_vs_per_view_f32": round(ms_pv / ms_batch, 3),
             "fwd_bwd_bf16_ms_per_8_views": round(ms_fb, 3),
             "fwd_bwd_note": "per view through RasterizeGaussians (BF16 records, FP32 compositing, the "
-                            "autotuned blend cluster), L1 loss each",
+                            "autotuned list form), L1 loss each",
             "keys_per_batch": keys_batch, "autotuned_tile": list(tile), "autotuned_cluster": cluster,
-            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2": [round(x, 3) for x in tune_ms], "iters": iters}
+            "autotuned_list_tiles": lists,
+            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2_l2x1_l2x2": [round(x, 3) for x in tune_ms], "iters": iters}
 
 
 def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:
@@ -614,6 +615,8 @@ def main():
                     help="0 culled (default: 8x8 blocks, two pixels per lane in packed FP32 pairs), 1 basic, "
                          "2 culled 16x8, 3 culled tile, 4 culled 8x8, 5 TMA staging")
     ap.add_argument("--cluster", type=int, default=0, help="thread-block clusters of the blend: 0, 2 (2x1), 4 (2x2)")
+    ap.add_argument("--list-tiles", type=int, default=0,
+                    help="lists of list tiles without clusters: 0, 2 (2x1), 4 (2x2)")
     ap.add_argument("--record-dtype", type=int, default=0, help="blend records: 0 FP32, 1 FP16, 2 BF16")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -631,7 +634,7 @@ def main():
 
     scene, cams = scenes.workload(args.workload)
     cam = cams[0]
-    ropt = {"cluster": args.cluster, "record_dtype": args.record_dtype}
+    ropt = {"cluster": args.cluster, "list_tiles": args.list_tiles, "record_dtype": args.record_dtype}
     H, W = cam.height, cam.width
     g = gs.scene_to_device(scene)
     ctx = gs.Context(local)
@@ -827,6 +830,7 @@ def main():
     flops = FLOPS_PER_EVAL * n_eval_total
     achieved = flops / (blend_ms / 1e3) / 1e12
     blend_kernel = ("blend_cluster_kernel" if args.cluster > 1 else
+                    "blend_listtile_kernel" if args.list_tiles > 1 else
                     "blend_culled_kernel" if args.blend_variant == 0 else "blend_basic_kernel")
     traffic, traffic_src = profiled_traffic(f"{blend_kernel}@{args.workload}")
     roofline = {"kernel": "gs_blend", "bound": "alu", "achieved": round(achieved, 3),
@@ -876,7 +880,7 @@ def main():
         "config": headline_config(args.workload),
         "setup": {"n_visible": stats["n_visible"], "n_keys": stats["n_keys"],
                    "key_bits": stats["key_bits"], "blend_variant": args.blend_variant,
-                   "cluster": args.cluster, "record_dtype": args.record_dtype,
+                   "cluster": args.cluster, "list_tiles": args.list_tiles, "record_dtype": args.record_dtype,
                    "sync_mode": "deferred (GS_SYNC_DEFERRED)",
                    "frames_in_flight": F,
                    "frames_per_step": F,

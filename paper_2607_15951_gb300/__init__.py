@@ -64,7 +64,7 @@ def camera_struct(cam) -> N.gs_camera:
 
 def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
                    blend_variant: int = 0, deferred: bool = False, temporal: int = 0,
-                   cluster: int = 0) -> N.gs_options:
+                   cluster: int = 0, list_tiles: int = 0) -> N.gs_options:
     o = N.gs_options()
     _lib().gs_default_options(ctypes.byref(o))
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
@@ -75,6 +75,7 @@ def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
     o.sync_mode = N.GS_SYNC_DEFERRED if deferred else N.GS_SYNC_FRAME
     o.temporal = int(temporal)  # False/0 off, True/1 adaptive, 2 re-bin whenever possible
     o.cluster = int(cluster)
+    o.list_tiles = int(list_tiles)
     return o
 
 
@@ -206,14 +207,17 @@ def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_co
 def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
               n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
               record_dtype: int = 0, deferred: bool = False, temporal: bool = False, cluster: int = 0,
-              stream=None) -> None:
+              list_tiles: int = 0, stream=None) -> None:
     """deferred=True: GS_SYNC_DEFERRED (no host synchronisation; an overflow
     or device error is raised by a later call on the context).
     temporal=True (or 1): re-bin from the previous frame's lists when that
     measured faster (same results); 2: re-bin whenever possible.
-    cluster: GS_CLUSTER_2X1 / _2X2 blend in thread-block clusters."""
+    cluster: GS_CLUSTER_2X1 / _2X2 blend in thread-block clusters;
+    list_tiles: GS_LISTS_2X1 / _2X2 lists of list tiles, read by every
+    screen tile's block (no cluster)."""
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred, temporal, cluster)
+    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred, temporal, cluster,
+                                              list_tiles)
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
                                ctypes.byref(fb), _stream(stream)))
@@ -221,11 +225,11 @@ def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_c
 
 def gs_render_backward(ctx: Context, g: dict, sh_degree: int, cam, final_T, n_contrib, d_rgb,
                        grads: dict, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
-                       cluster: int = 0, stream=None) -> None:
+                       cluster: int = 0, list_tiles: int = 0, stream=None) -> None:
     """grads: dict of CUDA tensors shaped like g (keys means, log_scales, quats,
     opacity_logits, sh) and optionally 'records' (n, 9)."""
     gs = gaussians_struct(g, sh_degree)
-    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, cluster=cluster)
+    c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, cluster=cluster, list_tiles=list_tiles)
     fb = _fb(None, final_T, n_contrib, None)
     out = N.gs_grads()
     out.d_means, out.d_log_scales, out.d_quats = (_ptr(grads["means"]), _ptr(grads["log_scales"]),
@@ -285,7 +289,7 @@ def scene_to_device(scene, device="cuda") -> dict:
 
 def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
            aux: bool = True, variant: int = 0, record_dtype: int = 0, deferred: bool = False,
-           temporal: bool = False, cluster: int = 0, stream=None) -> dict:
+           temporal: bool = False, cluster: int = 0, list_tiles: int = 0, stream=None) -> dict:
     """Allocate outputs with torch and call gs_render."""
     import torch
     H, W = int(cam.height), int(cam.width)
@@ -297,7 +301,7 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
         out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
               out.get("n_eval"), tile=tile, bg=bg, variant=variant, record_dtype=record_dtype,
-              deferred=deferred, temporal=temporal, cluster=cluster, stream=stream)
+              deferred=deferred, temporal=temporal, cluster=cluster, list_tiles=list_tiles, stream=stream)
     return out
 
 
@@ -311,7 +315,7 @@ def _autograd_function():
     class _Rasterize(torch.autograd.Function):
         @staticmethod
         def forward(fctx, means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree, tile, bg,
-                    deferred, record_dtype, cluster):
+                    deferred, record_dtype, cluster, list_tiles):
             g = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
                  "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
                  "sh": sh.contiguous()}
@@ -320,28 +324,31 @@ def _autograd_function():
                    "final_T": torch.empty((H, W), dtype=torch.float32, device=means.device),
                    "n_contrib": torch.empty((H, W), dtype=torch.int32, device=means.device)}
             gs_render(ctx, g, sh_degree, cam, out["rgb"], out["final_T"], out["n_contrib"], None,
-                      tile=tile, bg=bg, deferred=deferred, record_dtype=record_dtype, cluster=cluster)
-            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, gs_last_frame_id(ctx))
+                      tile=tile, bg=bg, deferred=deferred, record_dtype=record_dtype, cluster=cluster,
+                      list_tiles=list_tiles)
+            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, list_tiles,
+                       gs_last_frame_id(ctx))
             fctx.save_for_backward(out["final_T"], out["n_contrib"])
             fctx.mark_non_differentiable(out["final_T"])
             return out["rgb"], out["final_T"]
 
         @staticmethod
         def backward(fctx, d_rgb, d_T):
-            ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, frame = fctx.gs
+            ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, list_tiles, frame = fctx.gs
             final_T, n_contrib = fctx.saved_tensors
             if gs_last_frame_id(ctx) != frame:
                 # Another frame was rendered on the context since this one
                 # (e.g. several views before one backward): render this frame
                 # again, which gives the same lists, final_T and n_contrib.
                 redo = render(ctx, g, sh_degree, cam, tile=tile, bg=bg, aux=True, record_dtype=record_dtype,
-                              deferred=deferred, cluster=cluster)
+                              deferred=deferred, cluster=cluster, list_tiles=list_tiles)
                 final_T, n_contrib = redo["final_T"], redo["n_contrib"]
             grads = {k: torch.empty_like(v) for k, v in g.items()}
             gs_render_backward(ctx, g, sh_degree, cam, final_T, n_contrib, d_rgb.contiguous(), grads,
-                               tile=tile, bg=bg, record_dtype=record_dtype, cluster=cluster)
+                               tile=tile, bg=bg, record_dtype=record_dtype, cluster=cluster,
+                               list_tiles=list_tiles)
             return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
-                    grads["sh"], None, None, None, None, None, None, None, None)
+                    grads["sh"], None, None, None, None, None, None, None, None, None)
 
     return _Rasterize
 
@@ -351,7 +358,7 @@ _RASTERIZE = None
 
 def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Context, cam, sh_degree: int,
                        tile=(16, 16), bg=(0.0, 0.0, 0.0), deferred: bool = True, record_dtype: int = 0,
-                       cluster: int = 0):
+                       cluster: int = 0, list_tiles: int = 0):
     """Differentiable render: returns (rgb (H,W,3), final_T (H,W)); gradients
     flow to the five parameter tensors. Several renders may precede their
     backwards on one context: a backward whose frame is no longer the
@@ -363,12 +370,14 @@ def RasterizeGaussians(means, log_scales, quats, opacity_logits, sh, ctx: Contex
     which have then grown, so the iteration can simply be repeated.
     record_dtype: precision of the blend records (GS_RECORD_F32 / F16 / BF16),
     used by the forward and the backward blend alike. cluster: thread-block
-    clusters of the forward blend (GS_CLUSTER_*)."""
+    clusters of the forward blend (GS_CLUSTER_*); list_tiles: lists of list
+    tiles without clusters (GS_LISTS_*)."""
     global _RASTERIZE
     if _RASTERIZE is None:
         _RASTERIZE = _autograd_function()
     return _RASTERIZE.apply(means, log_scales, quats, opacity_logits, sh, ctx, cam, sh_degree,
-                            tuple(tile), tuple(bg), bool(deferred), int(record_dtype), int(cluster))
+                            tuple(tile), tuple(bg), bool(deferred), int(record_dtype), int(cluster),
+                            int(list_tiles))
 
 
 # ---------------------------------------------------------------------------
@@ -399,13 +408,14 @@ def alloc_outputs(cams, aux: bool = False, device="cuda") -> list:
 
 def gs_render_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, tile=(16, 16),
                     bg=(0.0, 0.0, 0.0), record_dtype: int = 0, direct: bool = False,
-                    batch_mode: int = 0, batch_depth: int = 0, cluster: int = 0, stream=None):
+                    batch_mode: int = 0, batch_depth: int = 0, cluster: int = 0, list_tiles: int = 0,
+                    stream=None):
     """batch_mode: N.GS_BATCH_AUTO (0), GS_BATCH_JOINT (1) or GS_BATCH_PER_VIEW (2);
     batch_depth: blend staging depth of the joint schedule (0 = 256);
-    cluster: thread-block clusters of the blend (the batch then renders view
-    by view)."""
+    cluster / list_tiles: thread-block clusters of the blend, or lists of
+    list tiles without clusters (the batch then renders view by view)."""
     gs = gaussians_struct(g, sh_degree)
-    o = options_struct(tile, bg, record_dtype, cluster=cluster)
+    o = options_struct(tile, bg, record_dtype, cluster=cluster, list_tiles=list_tiles)
     o.direct_launch = 1 if direct else 0
     o.batch_mode = int(batch_mode)
     o.batch_depth = int(batch_depth)
@@ -482,8 +492,9 @@ def RasterizeGaussiansBatch(means, log_scales, quats, opacity_logits, sh, ctx: C
 def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(0.0, 0.0, 0.0),
                       record_dtype: int = 0, cache_path: str | None = None, stream=None):
     """Runs the C autotuner (tile shapes 16x16, 16x8, 8x8, 16x16 with 2x1 and
-    2x2 blend clusters and, for the joint schedule, staging depths 256, 128,
-    64) and returns ((tile_w, tile_h), [ms per candidate], depth, cluster).
+    2x2 blend clusters, 16x16 with 2x1 and 2x2 list tiles and, for the joint
+    schedule, staging depths 256, 128, 64) and returns ((tile_w, tile_h),
+    [ms per candidate], depth, cluster, list_tiles).
     With cache_path, results are kept in a JSON file keyed by GPU, scene
     size, view sizes and record precision."""
     import json
@@ -497,23 +508,24 @@ def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(
         if os.path.exists(cache_path):
             with open(cache_path) as f:
                 cache = json.load(f)
-            if key in cache and "cluster" in cache[key]:
+            if key in cache and "list_tiles" in cache[key]:
                 return (tuple(cache[key]["tile"]), cache[key]["ms"], cache[key].get("depth", 256),
-                        cache[key]["cluster"])
+                        cache[key]["cluster"], cache[key]["list_tiles"])
     gs = gaussians_struct(g, sh_degree)
     o = options_struct((16, 16), bg, record_dtype)
     carr, farr = _cams_fbs(cams, outs)
-    ms = (ctypes.c_float * 5)()
+    ms = (ctypes.c_float * 7)()
     ctx.check(_lib().gs_autotune_batch(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
                                        _stream(stream), ms))
     tile, times, depth = (int(o.tile_w), int(o.tile_h)), [float(x) for x in ms], int(o.batch_depth)
-    cluster = int(o.cluster)
+    cluster, list_tiles = int(o.cluster), int(o.list_tiles)
     if cache_path:
         cache = {}
         if os.path.exists(cache_path):
             with open(cache_path) as f:
                 cache = json.load(f)
-        cache[key] = {"tile": list(tile), "ms": times, "depth": depth, "cluster": cluster}
+        cache[key] = {"tile": list(tile), "ms": times, "depth": depth, "cluster": cluster,
+                      "list_tiles": list_tiles}
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
-    return tile, times, depth, cluster
+    return tile, times, depth, cluster, list_tiles

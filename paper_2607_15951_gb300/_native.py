@@ -36,6 +36,9 @@ GS_BATCH_PER_VIEW = 2
 GS_CLUSTER_NONE = 0
 GS_CLUSTER_2X1 = 2
 GS_CLUSTER_2X2 = 4
+GS_LISTS_1X1 = 0
+GS_LISTS_2X1 = 2
+GS_LISTS_2X2 = 4
 NOALLOC_SORT_MAX_PAIRS = 262144  # GS_NOALLOC_SORT_MAX_PAIRS in include/gs.h
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_CAPACITY", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}
@@ -78,7 +81,7 @@ class gs_options(ctypes.Structure):
                 ("blend_variant", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
                 ("sync_mode", ctypes.c_int32), ("temporal", ctypes.c_int32),
                 ("batch_mode", ctypes.c_int32), ("batch_depth", ctypes.c_int32),
-                ("cluster", ctypes.c_int32)]
+                ("cluster", ctypes.c_int32), ("list_tiles", ctypes.c_int32)]
 
 
 class gs_render_stats(ctypes.Structure):

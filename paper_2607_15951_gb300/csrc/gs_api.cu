@@ -192,6 +192,15 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
         return fail(ctx, GS_ERR_INVALID_ARG, "thread-block clusters need 16x16 tiles");
     if (o->cluster > 1 && o->temporal)
         return fail(ctx, GS_ERR_UNSUPPORTED, "temporal re-binning does not take thread-block clusters");
+    if (o->list_tiles != GS_LISTS_1X1 && o->list_tiles != 1 && o->list_tiles != GS_LISTS_2X1 &&
+        o->list_tiles != GS_LISTS_2X2)
+        return fail(ctx, GS_ERR_INVALID_ARG, "list_tiles must be GS_LISTS_1X1 (0 or 1), _2X1 or _2X2");
+    if (o->list_tiles > 1 && o->cluster > 1)
+        return fail(ctx, GS_ERR_INVALID_ARG, "list_tiles and cluster are exclusive");
+    if (o->list_tiles > 1 && !(o->tile_w == 16 && o->tile_h == 16))
+        return fail(ctx, GS_ERR_INVALID_ARG, "list tiles need 16x16 tiles");
+    if (o->list_tiles > 1 && o->temporal)
+        return fail(ctx, GS_ERR_UNSUPPORTED, "temporal re-binning does not take list tiles");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
     return GS_OK;
@@ -208,12 +217,19 @@ gs_status check_gaussians(gs_context *ctx, const gs_gaussians *g) {
     return GS_OK;
 }
 
+// Screen tiles per list tile: 1, 2 (2 x 1) or 4 (2 x 2), from the cluster
+// or list-tile option.
+int list_shape(const gs_options *o) {
+    return o->cluster > 1 ? o->cluster : (o->list_tiles > 1 ? o->list_tiles : 1);
+}
+
 // The grid of the per-tile lists: the screen tiles, or with thread-block
-// clusters the list tiles of 2 x 1 / 2 x 2 screen tiles.
+// clusters or list tiles the list tiles of 2 x 1 / 2 x 2 screen tiles.
 GsGrid make_grid(const gs_camera *cam, const gs_options *o) {
     GsGrid gr;
-    gr.tile_w = o->cluster > 1 ? 2 * o->tile_w : o->tile_w;
-    gr.tile_h = o->cluster > 3 ? 2 * o->tile_h : o->tile_h;
+    const int shape = list_shape(o);
+    gr.tile_w = shape > 1 ? 2 * o->tile_w : o->tile_w;
+    gr.tile_h = shape > 3 ? 2 * o->tile_h : o->tile_h;
     gr.tiles_x = (cam->width + gr.tile_w - 1) / gr.tile_w;
     gr.tiles_y = (cam->height + gr.tile_h - 1) / gr.tile_h;
     return gr;
@@ -435,7 +451,7 @@ void remember_frame(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     ctx->last_h = cam->height;
     ctx->last_tw = opts->tile_w;
     ctx->last_th = opts->tile_h;
-    ctx->last_cluster = opts->cluster > 1 ? opts->cluster : 1;
+    ctx->last_cluster = list_shape(opts);
     ctx->last_grid = grid;
     ctx->last_values = values;
     ctx->last_ranges = ranges;
@@ -459,7 +475,7 @@ bool same_frame(const gs_context *ctx, const gs_gaussians *g, const gs_camera *c
     for (int i = 0; i < 3; ++i)
         if (ctx->last_bg[i] != opts->bg[i]) return false;
     return ctx->last_tw == opts->tile_w && ctx->last_th == opts->tile_h && ctx->last_dtype == opts->record_dtype &&
-           ctx->last_cluster == (opts->cluster > 1 ? opts->cluster : 1);
+           ctx->last_cluster == list_shape(opts);
 }
 
 gs_status bin_impl(gs_context *ctx, const gs_record *records, const uint32_t *tiles, int64_t n,
@@ -535,6 +551,11 @@ gs_status launch_blend(gs_context *ctx, const RecordReader &rd, const uint32_t *
                        const GsGrid &grid, const gs_camera *cam, const gs_options *opts, const gs_framebuffer *fb,
                        const unsigned long long *d_n, int64_t n_cap, cudaStream_t s) {
     const int variant = blend_schedule(ctx, opts, grid.tiles_x * grid.tiles_y);
+    if (opts->list_tiles > 1) {
+        GS_CUDA(ctx, gs_launch_blend_listtile(rd, values, ranges, grid, opts->list_tiles, cam->width, cam->height,
+                                              opts->bg, *fb, s));
+        return GS_OK;
+    }
     if (opts->cluster > 1) {
         GS_CUDA(ctx, gs_launch_blend_cluster(rd, values, ranges, grid, opts->cluster, cam->width, cam->height,
                                              opts->bg, *fb, variant == GS_BLEND_CULLED_8X8, s));
@@ -796,7 +817,8 @@ gs_status gs_project(gs_context *ctx, const gs_gaussians *g, const gs_camera *ca
         return fail(ctx, GS_ERR_INVALID_ARG, "records/tiles are NULL");
     if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
         return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
-    if (opts->cluster > 1) return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters are a gs_render option");
+    if (list_shape(opts) > 1)
+        return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters and list tiles are gs_render options");
     DeviceGuard dg(ctx->device);
     GS_CUDA(ctx, gs_launch_project(*g, make_cam(cam), make_grid(cam, opts), records, tiles,
                                    static_cast<cudaStream_t>(stream)));
@@ -815,7 +837,8 @@ gs_status gs_bin(gs_context *ctx, const gs_record *records, const uint32_t *tile
     if (capacity > 0 && (!keys || !values)) return fail(ctx, GS_ERR_INVALID_ARG, "keys/values are NULL");
     if (reinterpret_cast<uintptr_t>(records) % 16 != 0)
         return fail(ctx, GS_ERR_INVALID_ARG, "records must be 16-byte aligned");
-    if (opts->cluster > 1) return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters are a gs_render option");
+    if (list_shape(opts) > 1)
+        return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters and list tiles are gs_render options");
     DeviceGuard dg(ctx->device);
     *n_keys = 0;
     st = bin_impl(ctx, records, tiles, n, make_grid(cam, opts), keys, values, capacity, false, ranges,
@@ -871,7 +894,8 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
     DeviceGuard dg(ctx->device);
     if (opts->record_dtype != GS_RECORD_F32)
         return fail(ctx, GS_ERR_UNSUPPORTED, "gs_blend reads FP32 gs_records; use gs_render for F16/BF16");
-    if (opts->cluster > 1) return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters are a gs_render option");
+    if (list_shape(opts) > 1)
+        return fail(ctx, GS_ERR_UNSUPPORTED, "thread-block clusters and list tiles are gs_render options");
     GS_CUDA(ctx, gs_launch_blend(reader(ctx, records, GS_RECORD_F32, true), values, ranges, make_grid(cam, opts),
                                  cam->width, cam->height, opts->bg, *fb, opts->blend_variant,
                                  static_cast<cudaStream_t>(stream)));
@@ -1233,9 +1257,9 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto &B = ctx->batch;
     const int64_t n = g->n;
-    // Thread-block clusters are a property of the single-view blend: such a
-    // batch renders view by view.
-    const bool per_view = opts->batch_mode == GS_BATCH_PER_VIEW || opts->cluster > 1 ||
+    // Thread-block clusters and list tiles are properties of the single-view
+    // blend: such a batch renders view by view.
+    const bool per_view = opts->batch_mode == GS_BATCH_PER_VIEW || list_shape(opts) > 1 ||
                           (opts->batch_mode == GS_BATCH_AUTO && B.keys_per_view > kBatchPerViewKeys);
     B.have_joint = false;
     if (per_view) {
@@ -1435,8 +1459,15 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     if (!ctx || !opts) return GS_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // Screen tile (w, h) and thread-block cluster of each candidate.
-    const int shapes[5][3] = {{16, 16, 0}, {16, 8, 0}, {8, 8, 0}, {16, 16, GS_CLUSTER_2X1}, {16, 16, GS_CLUSTER_2X2}};
+    // Screen tile (w, h), thread-block cluster and list tiles of each candidate.
+    constexpr int kShapes = 7;
+    const int shapes[kShapes][4] = {{16, 16, 0, 0},
+                                    {16, 8, 0, 0},
+                                    {8, 8, 0, 0},
+                                    {16, 16, GS_CLUSTER_2X1, 0},
+                                    {16, 16, GS_CLUSTER_2X2, 0},
+                                    {16, 16, 0, GS_LISTS_2X1},
+                                    {16, 16, 0, GS_LISTS_2X2}};
     const int depths[3] = {256, 128, 64};
     cudaEvent_t e0, e1;
     GS_CUDA(ctx, cudaEventCreate(&e0));
@@ -1444,13 +1475,14 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     float best = 1e30f;
     int best_k = 0, best_d = 0;
     gs_status st = GS_OK;
-    for (int k = 0; k < 5 && st == GS_OK; ++k) {
+    for (int k = 0; k < kShapes && st == GS_OK; ++k) {
         float best_shape = 1e30f;
         for (int d = 0; d < 3 && st == GS_OK; ++d) {
             gs_options o = *opts;
             o.tile_w = shapes[k][0];
             o.tile_h = shapes[k][1];
             o.cluster = shapes[k][2];
+            o.list_tiles = shapes[k][3];
             o.batch_depth = depths[d];
             for (int w = 0; w < 2 && st == GS_OK; ++w) st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
             // The depth only matters to the joint schedule.
@@ -1481,6 +1513,7 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     opts->tile_w = shapes[best_k][0];
     opts->tile_h = shapes[best_k][1];
     opts->cluster = shapes[best_k][2];
+    opts->list_tiles = shapes[best_k][3];
     opts->batch_depth = depths[best_d];
     return GS_OK;
 }

@@ -631,6 +631,149 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
     }
 }
 
+// ---------------------------------------------------------------------------
+// List-tile variant: the lists of 2x1 / 2x2 list tiles (as for the cluster
+// blend), each 16 x 16 screen tile blended by its own thread block, without a
+// cluster: the block reads its list tile's list itself and keeps the records
+// whose 16 x 16 tile rect (the rule of the default lists, from the record's
+// integer radius) holds its tile and whose conservative box meets it,
+// compacted in list order into its batch; the batch is blended in packed
+// pairs as by blend_tile_culled_x2. Colours and transmittance equal those of
+// the default lists bit for bit; list positions are the list tile's, as in
+// the cluster blend.
+// ---------------------------------------------------------------------------
+template <int CX, int CY, int DEPTH>
+__global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs a) {
+    constexpr int TW = 16, TH = 16, BW = 8, BH = 8, kRows = 4;
+    constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
+    static_assert(DEPTH % kThreads == 0 && DEPTH >= 2 * kThreads, "batch shape");
+    __shared__ ulonglong2 s_d0[DEPTH], s_d1[DEPTH], s_d2[DEPTH], s_c01[DEPTH], s_c2[DEPTH];
+    __shared__ int32_t s_pos[DEPTH];
+    __shared__ uint32_t s_wcnt[2][kWarps];
+    const SRecX2 S{s_d0, s_d1, s_d2, s_c01, s_c2};
+
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    if (tx * TW >= a.width || ty * TH >= a.height) return;  // padding of the list grid (whole block)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
+    const int px = bx + (lane % BW), py0 = by + lane / BW, py1 = py0 + kRows;
+    const float fx = px + 0.5f;
+    const f32x2 fx2 = x2(fx, fx);
+    const f32x2 fy2 = x2((float)py0 + 0.5f, (float)py1 + 0.5f);
+    const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
+    const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
+    // Pixel-centre extent of the tile (clipped to the image).
+    const float tx0 = tx * TW + 0.5f, tx1 = fminf(tx * TW + TW - 0.5f, a.width - 0.5f);
+    const float ty0 = ty * TH + 0.5f, ty1 = fminf(ty * TH + TH - 0.5f, a.height - 0.5f);
+    const int lt = (ty / CY) * a.grid.tiles_x + tx / CX;
+    const uint32_t first = a.ranges[2 * lt], last = a.ranges[2 * lt + 1];
+
+    f32x2 T2 = x2(1.f, 1.f), R2 = x2(0.f, 0.f), G2 = R2, B2 = R2;
+    int32_t last0 = 0, last1 = 0, eval0 = 0, eval1 = 0;
+    bool done0 = !(px < a.width && py0 < a.height), done1 = !(px < a.width && py1 < a.height);
+    bool warp_done = __all_sync(0xffffffffu, done0 && done1);
+
+    uint32_t next = first;
+    int rd_ = 0;
+    while (next < last) {
+        if (__syncthreads_count(warp_done) == kThreads) break;
+        // Fill the batch: rounds of kThreads list entries, the kept ones
+        // compacted in list order (per-warp counts give each warp its place).
+        int cnt = 0;
+        while (next < last && cnt <= DEPTH - kThreads) {
+            const uint32_t k = next + (uint32_t)tid;
+            bool keep = false;
+            uint32_t gi = 0;
+            float4 geo = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < last) {
+                gi = a.values[k];
+                geo = __ldg(a.rd.geo + gi);
+                const int rad = __ldg(reinterpret_cast<const int *>(a.rd.rec32 + 3 * (size_t)gi + 2) + 2);
+                const Rect R16 = tile_rect(geo.x, geo.y, rad, TW, TH, 1 << 30, 1 << 30);
+                if (tx >= R16.x0 && tx < R16.x1 && ty >= R16.y0 && ty < R16.y1) {
+                    const float2 h = blend_box_half(__ldg(a.rd.aux + gi).z);
+                    keep = geo.x - h.x <= tx1 && geo.x + h.x >= tx0 && geo.y - h.y <= ty1 && geo.y + h.y >= ty0;
+                }
+            }
+            const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) s_wcnt[rd_][warp] = __popc(ballot);
+            __syncthreads();
+            int before = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const int c = (int)s_wcnt[rd_][w];
+                before += w < warp ? c : 0;
+                total += c;
+            }
+            if (keep) {
+                const int d = cnt + before + __popc(ballot & lanemask_lt());
+                stage_record_x2<false>(a.rd, gi, d, S);
+                s_pos[d] = (int32_t)(k - first) + 1;
+            }
+            cnt += total;
+            next += kThreads;
+            rd_ ^= 1;
+        }
+        __syncthreads();
+        if (!warp_done) {
+            for (int c = 0; c < cnt; c += 32) {
+                const int j = c + lane;
+                const bool hit = j < cnt && record_touches_x2(S, j, wx0, wx1, wy0, wy1);
+                uint32_t bits = __ballot_sync(0xffffffffu, hit);
+                while (bits) {
+                    const int jj = c + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const ulonglong2 d0 = s_d0[jj], d1 = s_d1[jj];
+                    const f32x2 dx2 = x2_sub(fx2, d0.x);
+                    const f32x2 adx2 = x2_mul(x2_mul(d1.x, dx2), dx2), bdx2 = x2_mul(d1.y, dx2);
+                    const f32x2 dy2 = x2_sub(fy2, d0.y);
+                    const ulonglong2 d2 = s_d2[jj];
+                    float e0, e1, thr, hxy;
+                    x2_split(x2_fma(dy2, x2_fma(d2.x, dy2, bdx2), adx2), e0, e1);
+                    const ulonglong2 c2 = s_c2[jj];
+                    x2_split(c2.y, thr, hxy);
+                    const bool t0 = !done0 && !(e0 > 0.f || e0 < thr);
+                    const bool t1 = !done1 && !(e1 > 0.f || e1 < thr);
+                    if (!(t0 || t1)) continue;
+                    float a0, a1;
+                    x2_split(x2_mul(d2.y, x2(ex2(e0), ex2(e1))), a0, a1);
+                    const f32x2 w2 = x2_mul(x2(fminf(kAlphaMax, a0), fminf(kAlphaMax, a1)), T2);
+                    float w0, w1, tn0, tn1;
+                    x2_split(w2, w0, w1);
+                    x2_split(x2_sub(T2, w2), tn0, tn1);
+                    const bool s0 = t0 && tn0 < kTMin, s1 = t1 && tn1 < kTMin;
+                    const bool u0 = t0 && !s0, u1 = t1 && !s1;
+                    const f32x2 we2 = x2(u0 ? w0 : 0.f, u1 ? w1 : 0.f);
+                    T2 = x2_sub(T2, we2);
+                    const ulonglong2 c01 = s_c01[jj];
+                    R2 = x2_fma(c01.x, we2, R2);
+                    G2 = x2_fma(c01.y, we2, G2);
+                    B2 = x2_fma(c2.x, we2, B2);
+                    const int32_t pos = s_pos[jj];
+                    last0 = u0 ? pos : last0;
+                    last1 = u1 ? pos : last1;
+                    if (s0 || s1) {
+                        if (s0) done0 = true, eval0 = pos;
+                        if (s1) done1 = true, eval1 = pos;
+                    }
+                }
+                warp_done = __all_sync(0xffffffffu, done0 && done1);
+                if (warp_done) break;
+            }
+        }
+    }
+    const int32_t n_list = (int32_t)(last - first);
+    Pix p0, p1;
+    x2_split(T2, p0.T, p1.T);
+    x2_split(R2, p0.r, p1.r);
+    x2_split(G2, p0.g, p1.g);
+    x2_split(B2, p0.b, p1.b);
+    p0.last = last0, p1.last = last1;
+    p0.eval = done0 ? eval0 : n_list, p1.eval = done1 ? eval1 : n_list;
+    write_pixel(a, px, py0, p0);
+    write_pixel(a, px, py1, p1);
+}
+
 // Persistent blend over many views: blocks take global tiles from a queue
 // (largest lists first); each tile is rendered with its view's parameters.
 struct BlendBatchArgs {
@@ -976,6 +1119,18 @@ cudaError_t launch_cluster(const BlendArgs &a, int width, int height, cudaStream
     return cudaLaunchKernelEx(&cfg, blend_cluster_kernel<CX, CY, BW, BH, S>, a);
 }
 }  // namespace
+
+cudaError_t gs_launch_blend_listtile(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                     const GsGrid &list_grid, int lists, int width, int height, const float bg[3],
+                                     const gs_framebuffer &fb, cudaStream_t s) {
+    BlendArgs a{rd, values, ranges, list_grid, width, height,
+                {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
+    const dim3 grid((unsigned)((width + 15) / 16), (unsigned)((height + 15) / 16), 1);
+    if (lists == 2) blend_listtile_kernel<2, 1, 256><<<grid, 128, 0, s>>>(a);
+    else if (lists == 4) blend_listtile_kernel<2, 2, 256><<<grid, 128, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 cudaError_t gs_launch_blend_cluster(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                     const GsGrid &list_grid, int cluster, int width, int height, const float bg[3],

@@ -503,6 +503,11 @@ cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, cons
 // screen tiles of 16 x 16 (cluster 2: 2 x 1, 4: 2 x 2; list_grid is their
 // grid); the blocks of a list tile form one cluster and share its batches
 // through distributed shared memory. wide_blocks: 8x8 warp blocks.
+// Blend of list tiles (lists = 2: 2 x 1, 4: 2 x 2 screen tiles of 16 x 16)
+// without clusters: each screen tile's block reads its list tile's list.
+cudaError_t gs_launch_blend_listtile(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
+                                     const GsGrid &list_grid, int lists, int width, int height, const float bg[3],
+                                     const gs_framebuffer &fb, cudaStream_t s);
 cudaError_t gs_launch_blend_cluster(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                     const GsGrid &list_grid, int cluster, int width, int height, const float bg[3],
                                     const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s);

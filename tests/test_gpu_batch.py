@@ -72,11 +72,13 @@ def test_batch_tile_shapes_and_autotune(ctx, tmp_path):
         for a, b in zip(outs, ref):
             assert torch.equal(a["rgb"], b["rgb"]), tile
     cache = str(tmp_path / "tune.json")
-    tile, ms, depth, cluster = gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams), cache_path=cache)
-    assert tile in ((16, 16), (16, 8), (8, 8)) and len(ms) == 5 and all(m > 0 for m in ms)
-    assert depth in (64, 128, 256) and cluster in (0, 2, 4) and (cluster == 0 or tile == (16, 16))
+    tile, ms, depth, cluster, lists = gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams),
+                                                           cache_path=cache)
+    assert tile in ((16, 16), (16, 8), (8, 8)) and len(ms) == 7 and all(m > 0 for m in ms)
+    assert depth in (64, 128, 256) and cluster in (0, 2, 4) and lists in (0, 2, 4)
+    assert (cluster == 0 and lists == 0) or (tile == (16, 16) and min(cluster, lists) == 0)
     again = gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams), cache_path=cache)
-    assert (again[0], again[2], again[3]) == (tile, depth, cluster)
+    assert (again[0], again[2], again[3], again[4]) == (tile, depth, cluster, lists)
     for d in (64, 128, 256):  # every staging depth renders the same image
         outs = gs.alloc_outputs(cams, aux=True)
         gs.gs_render_batch(ctx, g, 0, cams, outs, tile=tile, batch_depth=d, batch_mode=N.GS_BATCH_JOINT)

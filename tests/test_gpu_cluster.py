@@ -1,11 +1,12 @@
-"""Thread-block-cluster blend (gs_options.cluster): lists built for list tiles
-of 2 x 1 or 2 x 2 screen tiles, the blocks of a list tile sharing its
-batches through distributed shared memory. Colours and transmittance must
-equal the default per-16x16-tile render bit for bit (each pixel sees the
-same records in the same order); list positions refer to the list tile's
-list, so n_contrib and n_eval are checked through the oracle's binning of
-the list tiles: the Gaussian at a pixel's last-contributor position is the
-same Gaussian as in the default render."""
+"""Lists of list tiles (2 x 1 or 2 x 2 screen tiles), blended either by
+thread-block clusters whose blocks share the list's batches through
+distributed shared memory (gs_options.cluster) or by every screen tile's
+block reading the list itself (gs_options.list_tiles). Colours and
+transmittance must equal the default per-16x16-tile render bit for bit (each
+pixel sees the same records in the same order); list positions refer to the
+list tile's list, so n_contrib and n_eval are checked through the oracle's
+binning of the list tiles: the Gaussian at a pixel's last-contributor
+position is the same Gaussian as in the default render."""
 import numpy as np
 import pytest
 
@@ -16,7 +17,10 @@ import paper_2607_15951_gb300 as gs  # noqa: E402
 from paper_2607_15951_gb300 import _native as N  # noqa: E402
 from paper_2607_15951_gb300 import scenes  # noqa: E402
 
-CLUSTERS = [N.GS_CLUSTER_2X1, N.GS_CLUSTER_2X2]
+# (option, value): the four list forms
+FORMS = [("cluster", N.GS_CLUSTER_2X1), ("cluster", N.GS_CLUSTER_2X2),
+         ("list_tiles", N.GS_LISTS_2X1), ("list_tiles", N.GS_LISTS_2X2)]
+FORM_IDS = ["c2x1", "c2x2", "l2x1", "l2x2"]
 
 
 @pytest.fixture(scope="module")
@@ -30,8 +34,8 @@ def ctx():
     c.close()
 
 
-def _list_tile(cluster):
-    return (32, 16) if cluster == N.GS_CLUSTER_2X1 else (32, 32)
+def _list_tile(shape):
+    return (32, 16) if shape == 2 else (32, 32)
 
 
 def _last_gaussian(nc, vals, ranges, width, tw, th):
@@ -52,9 +56,10 @@ CASES = [("uniform_box_256", lambda: (scenes.uniform_box(10_000, 0), scenes.pinh
          ("clustered_1m_1080p", lambda: scenes.workload("clustered_1m_1080p"))]
 
 
-@pytest.mark.parametrize("cluster", CLUSTERS, ids=["2x1", "2x2"])
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
-def test_cluster_blend_equals_default(ctx, oracle_mod, name, make, cluster):
+def test_list_tile_blends_equal_default(ctx, oracle_mod, name, make, form):
+    opt, shape = form
     scene, cam = make()
     if isinstance(cam, list):
         cam = cam[0]
@@ -62,11 +67,11 @@ def test_cluster_blend_equals_default(ctx, oracle_mod, name, make, cluster):
     ref = gs.render(ctx, g, scene.sh_degree, cam)
     torch.cuda.synchronize()
     k16 = gs.gs_last_render_stats(ctx)["n_keys"]
-    out = gs.render(ctx, g, scene.sh_degree, cam, cluster=cluster)
+    out = gs.render(ctx, g, scene.sh_degree, cam, **{opt: shape})
     torch.cuda.synchronize()
     gs.gs_sync_status(ctx)
     kc = gs.gs_last_render_stats(ctx)["n_keys"]
-    print(name, "cluster", cluster, "keys 16x16", k16, "list-tile keys", kc)
+    print(name, opt, shape, "keys 16x16", k16, "list-tile keys", kc)
     assert torch.equal(out["rgb"], ref["rgb"])
     assert torch.equal(out["final_T"], ref["final_T"])
     assert kc <= k16
@@ -77,7 +82,7 @@ def test_cluster_blend_equals_default(ctx, oracle_mod, name, make, cluster):
     # list grid reaches past the 16 x 16 grid (image sizes that are not whole
     # list tiles), Gaussians that touch only that margin are listed but have
     # no gs_project record; those sizes are checked on colours alone.
-    tw, th = _list_tile(cluster)
+    tw, th = _list_tile(shape)
     if -(-cam.width // tw) * tw != -(-cam.width // 16) * 16 or -(-cam.height // th) * th != -(-cam.height // 16) * 16:
         return
     rec = torch.zeros((scene.n, 12), dtype=torch.float32, device="cuda")
@@ -94,45 +99,47 @@ def test_cluster_blend_equals_default(ctx, oracle_mod, name, make, cluster):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("opt", ["cluster", "list_tiles"])
 @pytest.mark.parametrize("dtype", [N.GS_RECORD_F16, N.GS_RECORD_BF16], ids=["f16", "bf16"])
-def test_cluster_blend_with_low_precision_records(ctx, dtype):
+def test_list_tile_blends_with_low_precision_records(ctx, dtype, opt):
     scene = scenes.imbalance(300_000, seed=4, width=960, height=540)
     cam = scenes.pinhole(960, 540, 60.0)
     g = gs.scene_to_device(scene)
     ref = gs.render(ctx, g, scene.sh_degree, cam, record_dtype=dtype)
-    out = gs.render(ctx, g, scene.sh_degree, cam, record_dtype=dtype, cluster=N.GS_CLUSTER_2X2)
+    out = gs.render(ctx, g, scene.sh_degree, cam, record_dtype=dtype, **{opt: 4})
     torch.cuda.synchronize()
     assert torch.equal(out["rgb"], ref["rgb"])
     assert torch.equal(out["final_T"], ref["final_T"])
 
 
-def test_cluster_backward_equals_default(ctx):
+def test_list_tile_backward_equals_default(ctx):
     scene, cam = scenes.clustered(50_000, 42, box=5.0), scenes.pinhole(320, 180)
     g = gs.scene_to_device(scene)
     d = torch.randn((180, 320, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(4))
     res = []
-    for cl in (0, N.GS_CLUSTER_2X2):
-        out = gs.render(ctx, g, scene.sh_degree, cam, cluster=cl)
+    for kw in ({}, {"cluster": N.GS_CLUSTER_2X2}, {"list_tiles": N.GS_LISTS_2X2}, {"list_tiles": N.GS_LISTS_2X1}):
+        out = gs.render(ctx, g, scene.sh_degree, cam, **kw)
         grads = {k: torch.empty_like(v) for k, v in g.items()}
-        gs.gs_render_backward(ctx, g, scene.sh_degree, cam, out["final_T"], out["n_contrib"], d, grads,
-                              cluster=cl)
+        gs.gs_render_backward(ctx, g, scene.sh_degree, cam, out["final_T"], out["n_contrib"], d, grads, **kw)
         torch.cuda.synchronize()
         res.append(grads)
-    for k in res[0]:
-        a, b = res[1][k], res[0][k]
-        # float atomics: equal up to the summation order
-        assert torch.allclose(a, b, rtol=1e-4, atol=1e-5 * float(b.abs().max()) + 1e-12), k
+    for r in res[1:]:
+        for k in res[0]:
+            a, b = r[k], res[0][k]
+            # float atomics: equal up to the summation order
+            assert torch.allclose(a, b, rtol=1e-4, atol=1e-5 * float(b.abs().max()) + 1e-12), k
     # A backward with other cluster options than the frame's is refused.
     with pytest.raises(gs.GSError):
         gs.gs_render_backward(ctx, g, scene.sh_degree, cam, out["final_T"], out["n_contrib"], d, res[0])
 
 
-def test_cluster_batch_renders_views_alike(ctx):
+@pytest.mark.parametrize("opt", ["cluster", "list_tiles"])
+def test_list_tile_batch_renders_views_alike(ctx, opt):
     scene = scenes.clustered(100_000, 43, box=6.0)
     cams = scenes.trajectory(3, 1043, radius=2.0, sizes=((320, 180), (200, 120)))
     g = gs.scene_to_device(scene)
     outs = gs.alloc_outputs(cams, aux=True)
-    gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, cluster=N.GS_CLUSTER_2X2)
+    gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, **{opt: 4})
     torch.cuda.synchronize()
     for c, o in zip(cams, outs):
         ref = gs.render(ctx, g, scene.sh_degree, c)
@@ -140,9 +147,11 @@ def test_cluster_batch_renders_views_alike(ctx):
         assert torch.equal(o["rgb"], ref["rgb"]) and torch.equal(o["final_T"], ref["final_T"])
 
 
-def test_cluster_option_checks(ctx):
+def test_list_tile_option_checks(ctx):
     scene, cam = scenes.uniform_box(100, 1), scenes.pinhole(64, 64)
     g = gs.scene_to_device(scene)
-    for kw in ({"cluster": 3}, {"cluster": 4, "tile": (16, 8)}, {"cluster": 4, "temporal": True}):
+    for kw in ({"cluster": 3}, {"cluster": 4, "tile": (16, 8)}, {"cluster": 4, "temporal": True},
+               {"list_tiles": 3}, {"list_tiles": 4, "tile": (16, 8)}, {"list_tiles": 2, "temporal": True},
+               {"list_tiles": 4, "cluster": 4}):
         with pytest.raises(gs.GSError):
             gs.render(ctx, g, 0, cam, **kw)
