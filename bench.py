@@ -195,7 +195,7 @@ def tile_key_plan(tiles_x: int, tiles_y: int, key_bits: int, capacity: int = 0) 
     return (2 if tkey_bits <= 16 else 4), passes, min(fused, passes)
 
 
-def frame_bytes(n, n_vis, K, sh_degree, tiles_x, tiles_y, key_bits, pixels) -> dict:
+def frame_bytes(n, n_vis, K, sh_degree, tiles_x, tiles_y, key_bits, pixels, readers: int = 1) -> dict:
     """Bytes each forward stage has to move in DRAM, per frame: every mean
     and log-scale (the screen bound), rotation, opacity and SH of the visible
     Gaussians, the 48-byte record and the 48-byte FP32 blend record of each
@@ -204,7 +204,8 @@ def frame_bytes(n, n_vis, K, sh_degree, tiles_x, tiles_y, key_bits, pixels) -> d
     once by the emission, after its fused pass where there is one, then read
     and written by each remaining pass), and the image (rgb + final T + last
     contributor). The blend reads each visible Gaussian's blend record once
-    (repeat reads across tiles come from L2)."""
+    (repeat reads across tiles come from L2); with list tiles each list entry
+    is read by the `readers` screen tiles of its list tile."""
     s = 3 * (sh_degree + 1) ** 2
     kb, passes, fused = tile_key_plan(tiles_x, tiles_y, key_bits)
     n_tiles = tiles_x * tiles_y
@@ -215,8 +216,14 @@ def frame_bytes(n, n_vis, K, sh_degree, tiles_x, tiles_y, key_bits, pixels) -> d
         "emit": n_vis * (32 + 8) + K * (kb + 4),
         "tile_sort": (passes - fused) * K * 2 * (kb + 4),
         "ranges": K * kb + n_tiles * 8,
-        "blend": K * 4 + n_vis * 48 + pixels * 20,
+        "blend": K * 4 * readers + n_vis * 48 + pixels * 20,
     }
+
+
+def list_tile_dims(code: int) -> tuple:
+    """Screen tiles per list tile (columns, rows) of a gs_options.list_tiles
+    or cluster code: 0/1 -> 1x1, 2 -> 2x1, 4 -> 2x2, 16 -> 4x4, 64 -> 8x8."""
+    return {0: (1, 1), 1: (1, 1), 2: (2, 1), 4: (2, 2), 16: (4, 4), 64: (8, 8)}[code]
 
 
 def backward_bytes(n, n_vis, K, sh_degree, pixels) -> int:
@@ -378,7 +385,7 @@ def batched(gs, torch, args, flush, local) -> dict:
             "speedup_batched_f16_vs_per_view_f32": round(ms_pv / ms_b, 3),
             "ms_per_batch": round(ms_b, 3), "autotuned_tile": list(tile), "autotuned_depth": depth,
             "autotuned_cluster": cluster, "autotuned_list_tiles": lists,
-            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2_l2x1_l2x2": [round(x, 3) for x in tune_ms],
+            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2_l2x1_l2x2_l4x4_l8x8": [round(x, 3) for x in tune_ms],
             "keys_per_batch": st["n_keys"], "iters": iters,
             "fwd_bwd_batched_f16_ms": round(ms_fb_b, 3), "fwd_bwd_per_view_f32_ms": round(ms_fb_v, 3),
             "fwd_bwd_speedup": round(ms_fb_v / ms_fb_b, 3),
@@ -514,7 +521,7 @@ def imbalance_stress(gs, torch, args, flush, local) -> dict:
                             "autotuned list form), L1 loss each",
             "keys_per_batch": keys_batch, "autotuned_tile": list(tile), "autotuned_cluster": cluster,
             "autotuned_list_tiles": lists,
-            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2_l2x1_l2x2": [round(x, 3) for x in tune_ms], "iters": iters}
+            "autotune_ms_16x16_16x8_8x8_c2x1_c2x2_l2x1_l2x2_l4x4_l8x8": [round(x, 3) for x in tune_ms], "iters": iters}
 
 
 def cpu_baseline(scene, cam, budget_s: float = 12.0) -> dict:
@@ -611,12 +618,14 @@ def main():
                     help="consecutive frames rendered on this many contexts / streams at once (headline value)")
     ap.add_argument("--pipeline-blend-variant", type=int, default=0,
                     help="blend schedule of the frames-in-flight loop (0: the default, 8x8 blocks in packed pairs)")
+    ap.add_argument("--pipeline-list-tiles", type=int, default=4,
+                    help="list tiles of the frames-in-flight loop (4: 2x2 list tiles; 0: a list per screen tile)")
     ap.add_argument("--blend-variant", type=int, default=0,
                     help="0 culled (default: 8x8 blocks, two pixels per lane in packed FP32 pairs), 1 basic, "
                          "2 culled 16x8, 3 culled tile, 4 culled 8x8, 5 TMA staging")
     ap.add_argument("--cluster", type=int, default=0, help="thread-block clusters of the blend: 0, 2 (2x1), 4 (2x2)")
     ap.add_argument("--list-tiles", type=int, default=0,
-                    help="lists of list tiles without clusters: 0, 2 (2x1), 4 (2x2)")
+                    help="lists of list tiles without clusters: 0, 2 (2x1), 4 (2x2), 16 (4x4), 64 (8x8)")
     ap.add_argument("--record-dtype", type=int, default=0, help="blend records: 0 FP32, 1 FP16, 2 BF16")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -703,9 +712,10 @@ def main():
     pctx = [ctx] + [gs.Context(local) for _ in range(F - 1)]
     pstreams = [torch.cuda.Stream() for _ in range(F)]
     prgb = [rgb] + [torch.empty_like(rgb) for _ in range(F - 1)]
+    popt = dict(ropt, list_tiles=args.pipeline_list_tiles)
     for k in range(F):
         for _ in range(args.warmup):
-            gs.gs_render(pctx[k], g, scene.sh_degree, cam, prgb[k], variant=args.pipeline_blend_variant, **ropt)
+            gs.gs_render(pctx[k], g, scene.sh_degree, cam, prgb[k], variant=args.pipeline_blend_variant, **popt)
     torch.cuda.synchronize()
     barrier(world)
     clocks2 = ClockSampler(local)
@@ -719,7 +729,7 @@ def main():
         k = i % F
         with torch.cuda.stream(pstreams[k]):
             gs.gs_render(pctx[k], copies[i % len(copies)], scene.sh_degree, cam, prgb[k],
-                         variant=args.pipeline_blend_variant, deferred=True, stream=pstreams[k], **ropt)
+                         variant=args.pipeline_blend_variant, deferred=True, stream=pstreams[k], **popt)
     for ps in pstreams:
         stream.wait_stream(ps)
     p1.record(stream)
@@ -728,6 +738,7 @@ def main():
     barrier(world)
     for c in pctx:
         gs.gs_sync_status(c)
+    pstats = gs.gs_last_render_stats(pctx[0])  # a frame of the headline loop (its list form)
     pipe_ms = max_over_ranks(p0.elapsed_time(p1), world)
     ms_per_step = pipe_ms / args.steps
     ms_per_frame = pipe_ms / (args.steps * F)
@@ -846,7 +857,8 @@ def main():
     # one frame is done once per frame interval, and the frame's DRAM bytes
     # move once per frame interval.
     roofline_headline = {
-        "loop": f"{F} frames in flight, blend schedule {args.pipeline_blend_variant}",
+        "loop": f"{F} frames in flight, blend schedule {args.pipeline_blend_variant}, "
+                f"list tiles {args.pipeline_list_tiles}",
         "frame_ms": round(ms_per_frame, 5),
         "blend_alu": {"bound": "alu", "achieved": round(flops * value / world / 1e12, 3),
                       "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
@@ -863,14 +875,20 @@ def main():
         t = stage_ms.get(stage_of[k], float("nan"))
         gbs = b / (t / 1e3) / 1e9 if t > 0 else float("nan")
         hbm[k] = {"bytes": int(b), "ms": round(t, 4), "GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)}
-    frame_gbs = sum(fbytes.values()) / (ms_per_frame / 1e3) / 1e9
-    hbm["frame"] = {"bytes": int(sum(fbytes.values())), "ms": round(ms_per_frame, 5), "GB/s": round(frame_gbs, 1),
+    # The headline loop's frames: their own lists (list tiles), read by every
+    # screen tile of a list tile.
+    plx, ply = list_tile_dims(args.pipeline_list_tiles)
+    pbytes = frame_bytes(scene.n, pstats["n_visible"], pstats["n_keys"], scene.sh_degree,
+                         (W + 16 * plx - 1) // (16 * plx), (H + 16 * ply - 1) // (16 * ply), pstats["key_bits"],
+                         W * H, readers=plx * ply)
+    frame_gbs = sum(pbytes.values()) / (ms_per_frame / 1e3) / 1e9
+    hbm["frame"] = {"bytes": int(sum(pbytes.values())), "ms": round(ms_per_frame, 5), "GB/s": round(frame_gbs, 1),
                     "frac": round(frame_gbs / hbm_peak, 4), "peak_GB/s": hbm_peak,
                     "peak_source": "measured" if pk_kind == "measured" else "fallback",
                     "note": "per frame of the headline loop"}
     roofline_headline["frame_hbm"] = {"bound": "hbm", "achieved": round(frame_gbs, 1), "peak": hbm_peak,
                                       "unit": "GB/s", "frac": round(frame_gbs / hbm_peak, 4),
-                                      "bytes_per_frame": int(sum(fbytes.values()))}
+                                      "bytes_per_frame": int(sum(pbytes.values()))}
 
     line = {
         "metric": headline_metric(args.workload),
@@ -886,6 +904,8 @@ def main():
                    "frames_per_step": F,
                    "ms_per_frame": round(ms_per_frame, 5),
                    "frames_in_flight_blend_variant": args.pipeline_blend_variant,
+                   "frames_in_flight_list_tiles": args.pipeline_list_tiles,
+                   "frames_in_flight_keys": pstats["n_keys"],
                    "inputs": "8 rotating copies of the scene (8 x 236 MB, above L2) in the frames-in-flight loop",
                    "single_stream_frame_ms": round(single_ms, 4),
                    "single_stream_frames_per_s": round(1000.0 / single_ms, 3),
@@ -913,7 +933,8 @@ def main():
     # gather, four depth digit passes, the entry scan, the key emission (with
     # the first tile pass inside it on grids at most 256 tiles wide), the
     # other tile passes, ranges, blend.
-    _, passes, fused = tile_key_plan((W + 15) // 16, (H + 15) // 16, stats["key_bits"])
+    _, passes, fused = tile_key_plan((W + 16 * plx - 1) // (16 * plx), (H + 16 * ply - 1) // (16 * ply),
+                                     pstats["key_bits"])
     per_frame = 10 + passes - fused
     line["gpu_launches"] = per_frame * F * args.steps
     if not args.no_fwd_bwd:

@@ -196,16 +196,18 @@ typedef struct {
  * re-binning. */
 enum { GS_CLUSTER_NONE = 0, GS_CLUSTER_2X1 = 2, GS_CLUSTER_2X2 = 4 };
 
-/* List tiles without clusters (gs_options.list_tiles): with GS_LISTS_2X1 or
- * _2X2 the per-tile lists are built for list tiles of 2 x 1 or 2 x 2 screen
- * tiles as with the clusters above, but the thread block of every 16 x 16
- * screen tile reads its list tile's list itself, keeps (compacted in list
- * order) the records whose 16 x 16 tile rect holds its tile and whose
- * conservative box meets it, and blends them: no cluster barriers, at the
- * price of each list entry being read by two or four blocks. Outputs as with
- * the clusters (colours and transmittance equal the 16x16 lists' bit for
- * bit, list positions are the list tile's). Not with temporal re-binning. */
-enum { GS_LISTS_1X1 = 0, GS_LISTS_2X1 = 2, GS_LISTS_2X2 = 4 };
+/* List tiles without clusters (gs_options.list_tiles = the number of screen
+ * tiles per list tile): with GS_LISTS_2X1, _2X2, _4X4 or _8X8 the per-tile
+ * lists are built for list tiles of 2 x 1, 2 x 2, 4 x 4 or 8 x 8 screen
+ * tiles (so a splat spanning several screen tiles is listed fewer times),
+ * and the thread block of every 16 x 16 screen tile reads its list tile's
+ * list itself, keeps (compacted in list order) the records whose 16 x 16
+ * tile rect holds its tile and whose conservative box meets it, and blends
+ * them: no cluster barriers, at the price of each list entry being read by
+ * every screen tile of its list tile. Outputs as with the clusters (colours
+ * and transmittance equal the 16x16 lists' bit for bit, list positions are
+ * the list tile's). Not with temporal re-binning. */
+enum { GS_LISTS_1X1 = 0, GS_LISTS_2X1 = 2, GS_LISTS_2X2 = 4, GS_LISTS_4X4 = 16, GS_LISTS_8X8 = 64 };
 
 /* How gs_render_batch schedules the views. JOINT: one projection, one key
  * sort and one persistent blend over all views (pays off for many short
@@ -428,12 +430,12 @@ gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const
 
 /* Autotuner of gs_render_batch: renders the batch with each screen-tile
  * shape and list form (16x16, 16x8, 8x8 with a list per tile; 16x16 with
- * GS_CLUSTER_2X1, GS_CLUSTER_2X2, GS_LISTS_2X1 and GS_LISTS_2X2, which render
- * view by view) and, for the joint schedule, each blend staging depth (256,
- * 128, 64 records), times three runs of each with CUDA events, and writes
- * the fastest into opts->tile_w / tile_h / cluster / list_tiles /
- * batch_depth. ms_out (host, 7 floats, optional) receives per candidate the
- * mean time of its best depth, in that order. */
+ * GS_CLUSTER_2X1, GS_CLUSTER_2X2, GS_LISTS_2X1, GS_LISTS_2X2, GS_LISTS_4X4
+ * and GS_LISTS_8X8, which render view by view) and, for the joint schedule,
+ * each blend staging depth (256, 128, 64 records), times three runs of each
+ * with CUDA events, and writes the fastest into opts->tile_w / tile_h /
+ * cluster / list_tiles / batch_depth. ms_out (host, 9 floats, optional)
+ * receives per candidate the mean time of its best depth, in that order. */
 gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
                             gs_options *opts, const gs_framebuffer *fbs, void *stream, float *ms_out);
 

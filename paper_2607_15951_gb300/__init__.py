@@ -492,9 +492,9 @@ def RasterizeGaussiansBatch(means, log_scales, quats, opacity_logits, sh, ctx: C
 def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(0.0, 0.0, 0.0),
                       record_dtype: int = 0, cache_path: str | None = None, stream=None):
     """Runs the C autotuner (tile shapes 16x16, 16x8, 8x8, 16x16 with 2x1 and
-    2x2 blend clusters, 16x16 with 2x1 and 2x2 list tiles and, for the joint
-    schedule, staging depths 256, 128, 64) and returns ((tile_w, tile_h),
-    [ms per candidate], depth, cluster, list_tiles).
+    2x2 blend clusters, 16x16 with 2x1, 2x2, 4x4 and 8x8 list tiles and, for
+    the joint schedule, staging depths 256, 128, 64) and returns ((tile_w,
+    tile_h), [ms per candidate], depth, cluster, list_tiles).
     With cache_path, results are kept in a JSON file keyed by GPU, scene
     size, view sizes and record precision."""
     import json
@@ -514,7 +514,7 @@ def gs_autotune_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, bg=(
     gs = gaussians_struct(g, sh_degree)
     o = options_struct((16, 16), bg, record_dtype)
     carr, farr = _cams_fbs(cams, outs)
-    ms = (ctypes.c_float * 7)()
+    ms = (ctypes.c_float * 9)()
     ctx.check(_lib().gs_autotune_batch(ctx.handle, ctypes.byref(gs), carr, len(cams), ctypes.byref(o), farr,
                                        _stream(stream), ms))
     tile, times, depth = (int(o.tile_w), int(o.tile_h)), [float(x) for x in ms], int(o.batch_depth)

@@ -39,6 +39,8 @@ GS_CLUSTER_2X2 = 4
 GS_LISTS_1X1 = 0
 GS_LISTS_2X1 = 2
 GS_LISTS_2X2 = 4
+GS_LISTS_4X4 = 16
+GS_LISTS_8X8 = 64
 NOALLOC_SORT_MAX_PAIRS = 262144  # GS_NOALLOC_SORT_MAX_PAIRS in include/gs.h
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_CAPACITY", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}

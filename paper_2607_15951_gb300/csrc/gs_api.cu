@@ -104,6 +104,7 @@ struct gs_context {
         // re-binning last measured slower.
         cudaEvent_t ev[2] = {nullptr, nullptr};
         double full_ms = 0.0, rebin_ms = 0.0;
+        int full_seen = 0, rebin_seen = 0;  // frames of each kind timed so far
         uint32_t gate = 0;
         // Adaptive mode only: frames still to render without tracking rects
         // (after a frame whose churn, or whose measured re-binning time,
@@ -193,8 +194,8 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
     if (o->cluster > 1 && o->temporal)
         return fail(ctx, GS_ERR_UNSUPPORTED, "temporal re-binning does not take thread-block clusters");
     if (o->list_tiles != GS_LISTS_1X1 && o->list_tiles != 1 && o->list_tiles != GS_LISTS_2X1 &&
-        o->list_tiles != GS_LISTS_2X2)
-        return fail(ctx, GS_ERR_INVALID_ARG, "list_tiles must be GS_LISTS_1X1 (0 or 1), _2X1 or _2X2");
+        o->list_tiles != GS_LISTS_2X2 && o->list_tiles != GS_LISTS_4X4 && o->list_tiles != GS_LISTS_8X8)
+        return fail(ctx, GS_ERR_INVALID_ARG, "list_tiles must be GS_LISTS_1X1 (0 or 1), _2X1, _2X2, _4X4 or _8X8");
     if (o->list_tiles > 1 && o->cluster > 1)
         return fail(ctx, GS_ERR_INVALID_ARG, "list_tiles and cluster are exclusive");
     if (o->list_tiles > 1 && !(o->tile_w == 16 && o->tile_h == 16))
@@ -217,8 +218,8 @@ gs_status check_gaussians(gs_context *ctx, const gs_gaussians *g) {
     return GS_OK;
 }
 
-// Screen tiles per list tile: 1, 2 (2 x 1) or 4 (2 x 2), from the cluster
-// or list-tile option.
+// Screen tiles per list tile (a list_tile_dims code), from the cluster or
+// list-tile option.
 int list_shape(const gs_options *o) {
     return o->cluster > 1 ? o->cluster : (o->list_tiles > 1 ? o->list_tiles : 1);
 }
@@ -227,9 +228,10 @@ int list_shape(const gs_options *o) {
 // clusters or list tiles the list tiles of 2 x 1 / 2 x 2 screen tiles.
 GsGrid make_grid(const gs_camera *cam, const gs_options *o) {
     GsGrid gr;
-    const int shape = list_shape(o);
-    gr.tile_w = shape > 1 ? 2 * o->tile_w : o->tile_w;
-    gr.tile_h = shape > 3 ? 2 * o->tile_h : o->tile_h;
+    int lx = 1, ly = 1;
+    list_tile_dims(list_shape(o), &lx, &ly);
+    gr.tile_w = lx * o->tile_w;
+    gr.tile_h = ly * o->tile_h;
     gr.tiles_x = (cam->width + gr.tile_w - 1) / gr.tile_w;
     gr.tiles_y = (cam->height + gr.tile_h - 1) / gr.tile_h;
     return gr;
@@ -404,11 +406,13 @@ void temporal_mark(gs_context *ctx, int k, cudaStream_t s) {
 }
 
 // After a synchronised temporal frame: folds its binning time into the
-// average of its kind.
+// average of its kind. The first frame of each kind on a context is not
+// counted: it may include the kernels' first-launch loading.
 void temporal_sample(gs_context *ctx, bool rebinned) {
     auto &T = ctx->temporal;
     float ms = 0.f;
     if (!T.ev[0] || cudaEventElapsedTime(&ms, T.ev[0], T.ev[1]) != cudaSuccess) return;
+    if ((rebinned ? T.rebin_seen : T.full_seen)++ == 0) return;
     double &avg = rebinned ? T.rebin_ms : T.full_ms;
     avg = avg > 0.0 ? 0.5 * avg + 0.5 * ms : ms;
 }
@@ -1460,14 +1464,16 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // Screen tile (w, h), thread-block cluster and list tiles of each candidate.
-    constexpr int kShapes = 7;
+    constexpr int kShapes = 9;
     const int shapes[kShapes][4] = {{16, 16, 0, 0},
                                     {16, 8, 0, 0},
                                     {8, 8, 0, 0},
                                     {16, 16, GS_CLUSTER_2X1, 0},
                                     {16, 16, GS_CLUSTER_2X2, 0},
                                     {16, 16, 0, GS_LISTS_2X1},
-                                    {16, 16, 0, GS_LISTS_2X2}};
+                                    {16, 16, 0, GS_LISTS_2X2},
+                                    {16, 16, 0, GS_LISTS_4X4},
+                                    {16, 16, 0, GS_LISTS_8X8}};
     const int depths[3] = {256, 128, 64};
     cudaEvent_t e0, e1;
     GS_CUDA(ctx, cudaEventCreate(&e0));

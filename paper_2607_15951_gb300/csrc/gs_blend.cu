@@ -275,15 +275,22 @@ struct SRecX2 {
     ulonglong2 *d0, *d1, *d2, *c01, *c2;
 };
 
-template <bool RAW = false>
-__device__ __forceinline__ void stage_record_x2(const RecordReader &rd, uint32_t g, int s, const SRecX2 &S) {
-    float4 geo, aux, col;
-    rd.load<RAW>(g, geo, aux, col);
+// Stages a record from its blend-record words (geo, aux, col as RecordReader
+// loads them).
+__device__ __forceinline__ void stage_values_x2(const float4 &geo, const float4 &aux, const float4 &col, int s,
+                                                const SRecX2 &S) {
     S.d0[s] = make_ulonglong2(x2(geo.x, geo.x), x2(geo.y, geo.y));
     S.d1[s] = make_ulonglong2(x2(geo.z, geo.z), x2(geo.w, geo.w));
     S.d2[s] = make_ulonglong2(x2(aux.x, aux.x), x2(col.x, col.x));
     S.c01[s] = make_ulonglong2(x2(col.y, col.y), x2(col.z, col.z));
     S.c2[s] = make_ulonglong2(x2(col.w, col.w), x2(aux.y, aux.z));
+}
+
+template <bool RAW = false>
+__device__ __forceinline__ void stage_record_x2(const RecordReader &rd, uint32_t g, int s, const SRecX2 &S) {
+    float4 geo, aux, col;
+    rd.load<RAW>(g, geo, aux, col);
+    stage_values_x2(geo, aux, col, s, S);
 }
 
 // record_touches on a packed record (the box from u, v and the half-widths).
@@ -297,6 +304,83 @@ __device__ __forceinline__ bool record_touches_x2(const SRecX2 &S, int j, float 
                           make_float4(u - h.x, u + h.x, v - h.y, v + h.y), x0, x1, y0, y1);
 }
 
+// Compositing state of a lane's two pixels.
+struct PixX2 {
+    f32x2 T2, R2, G2, B2;
+    int32_t last0, last1, eval0, eval1;
+    bool done0, done1;
+};
+
+// One staged batch of cnt records (list positions pos0 + slot, or s_pos[slot]
+// when given) blended into the lane's two pixels, in batch order, with the
+// warp culling of the scalar schedule. Returns whether all the warp's pixels
+// have stopped.
+__device__ __forceinline__ bool blend_batch_x2(PixX2 &P, const SRecX2 &S, const int32_t *s_pos, int32_t pos0,
+                                               int cnt, f32x2 fx2, f32x2 fy2, float wx0, float wx1, float wy0,
+                                               float wy1, int lane) {
+    for (int c = 0; c < cnt; c += 32) {
+        const int j = c + lane;
+        const bool hit = j < cnt && record_touches_x2(S, j, wx0, wx1, wy0, wy1);
+        uint32_t bits = __ballot_sync(0xffffffffu, hit);
+        while (bits) {
+            const int jj = c + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const ulonglong2 d0 = S.d0[jj], d1 = S.d1[jj];
+            const f32x2 dx2 = x2_sub(fx2, d0.x);
+            const f32x2 adx2 = x2_mul(x2_mul(d1.x, dx2), dx2), bdx2 = x2_mul(d1.y, dx2);
+            const f32x2 dy2 = x2_sub(fy2, d0.y);
+            const ulonglong2 d2 = S.d2[jj];
+            float e0, e1, thr, hxy;
+            x2_split(x2_fma(dy2, x2_fma(d2.x, dy2, bdx2), adx2), e0, e1);
+            const ulonglong2 c2 = S.c2[jj];
+            x2_split(c2.y, thr, hxy);
+            // power > 0, or alpha < 1/255: the pixel skips the record
+            const bool t0 = !P.done0 && !(e0 > 0.f || e0 < thr);
+            const bool t1 = !P.done1 && !(e1 > 0.f || e1 < thr);
+            if (!(t0 || t1)) continue;
+            float a0, a1;
+            x2_split(x2_mul(d2.y, x2(ex2(e0), ex2(e1))), a0, a1);
+            const f32x2 w2 = x2_mul(x2(fminf(kAlphaMax, a0), fminf(kAlphaMax, a1)), P.T2);
+            float w0, w1, tn0, tn1;
+            x2_split(w2, w0, w1);
+            x2_split(x2_sub(P.T2, w2), tn0, tn1);
+            // T would fall below the limit: the pixel stops before this record.
+            const bool s0 = t0 && tn0 < kTMin, s1 = t1 && tn1 < kTMin;
+            const bool u0 = t0 && !s0, u1 = t1 && !s1;
+            const f32x2 we2 = x2(u0 ? w0 : 0.f, u1 ? w1 : 0.f);  // weights of the pixels that take it
+            P.T2 = x2_sub(P.T2, we2);
+            const ulonglong2 c01 = S.c01[jj];
+            P.R2 = x2_fma(c01.x, we2, P.R2);
+            P.G2 = x2_fma(c01.y, we2, P.G2);
+            P.B2 = x2_fma(c2.x, we2, P.B2);
+            const int32_t pos = s_pos ? s_pos[jj] : pos0 + jj;
+            P.last0 = u0 ? pos : P.last0;
+            P.last1 = u1 ? pos : P.last1;
+            if (s0 || s1) {
+                if (s0) P.done0 = true, P.eval0 = pos;
+                if (s1) P.done1 = true, P.eval1 = pos;
+            }
+        }
+        if (__all_sync(0xffffffffu, P.done0 && P.done1)) return true;
+    }
+    return __all_sync(0xffffffffu, P.done0 && P.done1);
+}
+
+// Writes the lane's two pixels (n_list: list length, the n_eval of pixels
+// that never stopped).
+__device__ __forceinline__ void write_pixels_x2(const BlendArgs &a, const PixX2 &P, int px, int py0, int py1,
+                                                int32_t n_list) {
+    Pix p0, p1;
+    x2_split(P.T2, p0.T, p1.T);
+    x2_split(P.R2, p0.r, p1.r);
+    x2_split(P.G2, p0.g, p1.g);
+    x2_split(P.B2, p0.b, p1.b);
+    p0.last = P.last0, p1.last = P.last1;
+    p0.eval = P.done0 ? P.eval0 : n_list, p1.eval = P.done1 ? P.eval1 : n_list;
+    write_pixel(a, px, py0, p0);
+    write_pixel(a, px, py1, p1);
+}
+
 template <int TW, int TH, int DEPTH, bool RAW>
 __device__ __forceinline__ void blend_tile_culled_x2(const BlendArgs &a, int tile) {
     constexpr int BW = 8, BH = 8, kRows = 4;
@@ -308,17 +392,15 @@ __device__ __forceinline__ void blend_tile_culled_x2(const BlendArgs &a, int til
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
     const int px = bx + (lane % BW), py0 = by + lane / BW, py1 = py0 + kRows;
-    const float fx = px + 0.5f;
-    const f32x2 fx2 = x2(fx, fx);
+    const f32x2 fx2 = x2(px + 0.5f, px + 0.5f);
     const f32x2 fy2 = x2((float)py0 + 0.5f, (float)py1 + 0.5f);
     const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
     const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
 
     const uint32_t first = a.ranges[2 * tile], last = a.ranges[2 * tile + 1];
-    f32x2 T2 = x2(1.f, 1.f), R2 = x2(0.f, 0.f), G2 = R2, B2 = R2;
-    int32_t last0 = 0, last1 = 0, eval0 = 0, eval1 = 0;
-    bool done0 = !(px < a.width && py0 < a.height), done1 = !(px < a.width && py1 < a.height);
-    bool warp_done = __all_sync(0xffffffffu, done0 && done1);
+    PixX2 P{x2(1.f, 1.f), x2(0.f, 0.f), x2(0.f, 0.f), x2(0.f, 0.f), 0, 0, 0, 0,
+            !(px < a.width && py0 < a.height), !(px < a.width && py1 < a.height)};
+    bool warp_done = __all_sync(0xffffffffu, P.done0 && P.done1);
 
     for (uint32_t start = first; start < last; start += DEPTH) {
         if (__syncthreads_count(warp_done) == kThreads) break;
@@ -329,65 +411,9 @@ __device__ __forceinline__ void blend_tile_culled_x2(const BlendArgs &a, int til
         __syncthreads();
         const int cnt = (int)min((uint32_t)DEPTH, last - start);
         const int32_t pos0 = (int32_t)(start - first) + 1;  // list position of slot 0
-        if (!warp_done) {
-            for (int c = 0; c < cnt; c += 32) {
-                const int j = c + lane;
-                const bool hit = j < cnt && record_touches_x2(S, j, wx0, wx1, wy0, wy1);
-                uint32_t bits = __ballot_sync(0xffffffffu, hit);
-                while (bits) {
-                    const int jj = c + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const ulonglong2 d0 = s_d0[jj], d1 = s_d1[jj];
-                    const f32x2 dx2 = x2_sub(fx2, d0.x);
-                    const f32x2 adx2 = x2_mul(x2_mul(d1.x, dx2), dx2), bdx2 = x2_mul(d1.y, dx2);
-                    const f32x2 dy2 = x2_sub(fy2, d0.y);
-                    const ulonglong2 d2 = s_d2[jj];
-                    float e0, e1, thr, hxy;
-                    x2_split(x2_fma(dy2, x2_fma(d2.x, dy2, bdx2), adx2), e0, e1);
-                    const ulonglong2 c2 = s_c2[jj];
-                    x2_split(c2.y, thr, hxy);
-                    // power > 0, or alpha < 1/255: the pixel skips the record
-                    const bool t0 = !done0 && !(e0 > 0.f || e0 < thr);
-                    const bool t1 = !done1 && !(e1 > 0.f || e1 < thr);
-                    if (!(t0 || t1)) continue;
-                    float a0, a1;
-                    x2_split(x2_mul(d2.y, x2(ex2(e0), ex2(e1))), a0, a1);
-                    const f32x2 w2 = x2_mul(x2(fminf(kAlphaMax, a0), fminf(kAlphaMax, a1)), T2);
-                    float w0, w1, tn0, tn1;
-                    x2_split(w2, w0, w1);
-                    x2_split(x2_sub(T2, w2), tn0, tn1);
-                    // T would fall below the limit: the pixel stops before this record.
-                    const bool s0 = t0 && tn0 < kTMin, s1 = t1 && tn1 < kTMin;
-                    const bool u0 = t0 && !s0, u1 = t1 && !s1;
-                    const f32x2 we2 = x2(u0 ? w0 : 0.f, u1 ? w1 : 0.f);  // weights of the pixels that take it
-                    T2 = x2_sub(T2, we2);
-                    const ulonglong2 c01 = s_c01[jj];
-                    R2 = x2_fma(c01.x, we2, R2);
-                    G2 = x2_fma(c01.y, we2, G2);
-                    B2 = x2_fma(c2.x, we2, B2);
-                    const int32_t pos = pos0 + jj;
-                    last0 = u0 ? pos : last0;
-                    last1 = u1 ? pos : last1;
-                    if (s0 || s1) {
-                        if (s0) done0 = true, eval0 = pos;
-                        if (s1) done1 = true, eval1 = pos;
-                    }
-                }
-                warp_done = __all_sync(0xffffffffu, done0 && done1);
-                if (warp_done) break;
-            }
-        }
+        if (!warp_done) warp_done = blend_batch_x2(P, S, nullptr, pos0, cnt, fx2, fy2, wx0, wx1, wy0, wy1, lane);
     }
-    const int32_t n_list = (int32_t)(last - first);
-    Pix p0, p1;
-    x2_split(T2, p0.T, p1.T);
-    x2_split(R2, p0.r, p1.r);
-    x2_split(G2, p0.g, p1.g);
-    x2_split(B2, p0.b, p1.b);
-    p0.last = last0, p1.last = last1;
-    p0.eval = done0 ? eval0 : n_list, p1.eval = done1 ? eval1 : n_list;
-    write_pixel(a, px, py0, p0);
-    write_pixel(a, px, py1, p1);
+    write_pixels_x2(a, P, px, py0, py1, (int32_t)(last - first));
 }
 
 // Resident blocks per SM the register allocation must allow. Two pixels per
@@ -657,8 +683,7 @@ __global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
     const int px = bx + (lane % BW), py0 = by + lane / BW, py1 = py0 + kRows;
-    const float fx = px + 0.5f;
-    const f32x2 fx2 = x2(fx, fx);
+    const f32x2 fx2 = x2(px + 0.5f, px + 0.5f);
     const f32x2 fy2 = x2((float)py0 + 0.5f, (float)py1 + 0.5f);
     const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
     const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
@@ -668,10 +693,9 @@ __global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs 
     const int lt = (ty / CY) * a.grid.tiles_x + tx / CX;
     const uint32_t first = a.ranges[2 * lt], last = a.ranges[2 * lt + 1];
 
-    f32x2 T2 = x2(1.f, 1.f), R2 = x2(0.f, 0.f), G2 = R2, B2 = R2;
-    int32_t last0 = 0, last1 = 0, eval0 = 0, eval1 = 0;
-    bool done0 = !(px < a.width && py0 < a.height), done1 = !(px < a.width && py1 < a.height);
-    bool warp_done = __all_sync(0xffffffffu, done0 && done1);
+    PixX2 P{x2(1.f, 1.f), x2(0.f, 0.f), x2(0.f, 0.f), x2(0.f, 0.f), 0, 0, 0, 0,
+            !(px < a.width && py0 < a.height), !(px < a.width && py1 < a.height)};
+    bool warp_done = __all_sync(0xffffffffu, P.done0 && P.done1);
 
     uint32_t next = first;
     int rd_ = 0;
@@ -684,10 +708,9 @@ __global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs 
             const uint32_t k = next + (uint32_t)tid;
             bool keep = false;
             uint32_t gi = 0;
-            float4 geo = make_float4(0.f, 0.f, 0.f, 0.f);
             if (k < last) {
                 gi = a.values[k];
-                geo = __ldg(a.rd.geo + gi);
+                const float4 geo = __ldg(a.rd.geo + gi);
                 const int rad = __ldg(reinterpret_cast<const int *>(a.rd.rec32 + 3 * (size_t)gi + 2) + 2);
                 const Rect R16 = tile_rect(geo.x, geo.y, rad, TW, TH, 1 << 30, 1 << 30);
                 if (tx >= R16.x0 && tx < R16.x1 && ty >= R16.y0 && ty < R16.y1) {
@@ -715,63 +738,9 @@ __global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs 
             rd_ ^= 1;
         }
         __syncthreads();
-        if (!warp_done) {
-            for (int c = 0; c < cnt; c += 32) {
-                const int j = c + lane;
-                const bool hit = j < cnt && record_touches_x2(S, j, wx0, wx1, wy0, wy1);
-                uint32_t bits = __ballot_sync(0xffffffffu, hit);
-                while (bits) {
-                    const int jj = c + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const ulonglong2 d0 = s_d0[jj], d1 = s_d1[jj];
-                    const f32x2 dx2 = x2_sub(fx2, d0.x);
-                    const f32x2 adx2 = x2_mul(x2_mul(d1.x, dx2), dx2), bdx2 = x2_mul(d1.y, dx2);
-                    const f32x2 dy2 = x2_sub(fy2, d0.y);
-                    const ulonglong2 d2 = s_d2[jj];
-                    float e0, e1, thr, hxy;
-                    x2_split(x2_fma(dy2, x2_fma(d2.x, dy2, bdx2), adx2), e0, e1);
-                    const ulonglong2 c2 = s_c2[jj];
-                    x2_split(c2.y, thr, hxy);
-                    const bool t0 = !done0 && !(e0 > 0.f || e0 < thr);
-                    const bool t1 = !done1 && !(e1 > 0.f || e1 < thr);
-                    if (!(t0 || t1)) continue;
-                    float a0, a1;
-                    x2_split(x2_mul(d2.y, x2(ex2(e0), ex2(e1))), a0, a1);
-                    const f32x2 w2 = x2_mul(x2(fminf(kAlphaMax, a0), fminf(kAlphaMax, a1)), T2);
-                    float w0, w1, tn0, tn1;
-                    x2_split(w2, w0, w1);
-                    x2_split(x2_sub(T2, w2), tn0, tn1);
-                    const bool s0 = t0 && tn0 < kTMin, s1 = t1 && tn1 < kTMin;
-                    const bool u0 = t0 && !s0, u1 = t1 && !s1;
-                    const f32x2 we2 = x2(u0 ? w0 : 0.f, u1 ? w1 : 0.f);
-                    T2 = x2_sub(T2, we2);
-                    const ulonglong2 c01 = s_c01[jj];
-                    R2 = x2_fma(c01.x, we2, R2);
-                    G2 = x2_fma(c01.y, we2, G2);
-                    B2 = x2_fma(c2.x, we2, B2);
-                    const int32_t pos = s_pos[jj];
-                    last0 = u0 ? pos : last0;
-                    last1 = u1 ? pos : last1;
-                    if (s0 || s1) {
-                        if (s0) done0 = true, eval0 = pos;
-                        if (s1) done1 = true, eval1 = pos;
-                    }
-                }
-                warp_done = __all_sync(0xffffffffu, done0 && done1);
-                if (warp_done) break;
-            }
-        }
+        if (!warp_done) warp_done = blend_batch_x2(P, S, s_pos, 0, cnt, fx2, fy2, wx0, wx1, wy0, wy1, lane);
     }
-    const int32_t n_list = (int32_t)(last - first);
-    Pix p0, p1;
-    x2_split(T2, p0.T, p1.T);
-    x2_split(R2, p0.r, p1.r);
-    x2_split(G2, p0.g, p1.g);
-    x2_split(B2, p0.b, p1.b);
-    p0.last = last0, p1.last = last1;
-    p0.eval = done0 ? eval0 : n_list, p1.eval = done1 ? eval1 : n_list;
-    write_pixel(a, px, py0, p0);
-    write_pixel(a, px, py1, p1);
+    write_pixels_x2(a, P, px, py0, py1, (int32_t)(last - first));
 }
 
 // Persistent blend over many views: blocks take global tiles from a queue
@@ -1126,8 +1095,10 @@ cudaError_t gs_launch_blend_listtile(const RecordReader &rd, const uint32_t *val
     BlendArgs a{rd, values, ranges, list_grid, width, height,
                 {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
     const dim3 grid((unsigned)((width + 15) / 16), (unsigned)((height + 15) / 16), 1);
-    if (lists == 2) blend_listtile_kernel<2, 1, 256><<<grid, 128, 0, s>>>(a);
-    else if (lists == 4) blend_listtile_kernel<2, 2, 256><<<grid, 128, 0, s>>>(a);
+    if (lists == GS_LISTS_2X1) blend_listtile_kernel<2, 1, 256><<<grid, 128, 0, s>>>(a);
+    else if (lists == GS_LISTS_2X2) blend_listtile_kernel<2, 2, 256><<<grid, 128, 0, s>>>(a);
+    else if (lists == GS_LISTS_4X4) blend_listtile_kernel<4, 4, 256><<<grid, 128, 0, s>>>(a);
+    else if (lists == GS_LISTS_8X8) blend_listtile_kernel<8, 8, 256><<<grid, 128, 0, s>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -1429,7 +1400,8 @@ cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, 
                                 float *d_rec, cudaStream_t s, int cluster) {
     // A cluster frame's lists belong to list tiles of 2 x 1 or 2 x 2 screen
     // tiles of 16 x 16; each block still differentiates one 16 x 16 tile.
-    const int lcx = cluster >= 2 ? 2 : 1, lcy = cluster >= 4 ? 2 : 1;
+    int lcx = 1, lcy = 1;
+    list_tile_dims(cluster, &lcx, &lcy);
     const int tw = grid.tile_w / lcx, th = grid.tile_h / lcy;
     const int ctx_ = (width + tw - 1) / tw, cty = (height + th - 1) / th;
     BlendBwdArgs a{rd, values, ranges, grid, width, height,

@@ -312,10 +312,13 @@ struct RecordReader {
         }
         og = __ldg(geo + g);
         oa = __ldg(aux + g);
+        oc = load_col(g, oa);
+    }
+    // (opacity, red, green, blue) of a blend record whose aux word is oa.
+    __device__ __forceinline__ float4 load_col(uint32_t g, const float4 &oa) const {
         if (mode == kRecF32) {
             const float4 c = __ldg(static_cast<const float4 *>(col) + g);
-            oc = make_float4(oa.w, c.x, c.y, c.z);
-            return;
+            return make_float4(oa.w, c.x, c.y, c.z);
         }
         const uint32_t w = __float_as_uint(oa.w), gb = __ldg(static_cast<const uint32_t *>(col) + g);
         if (mode == kRecBF16) {
@@ -323,12 +326,11 @@ struct RecordReader {
             const uint32_t rb = w >> 16;
             const float red = __uint_as_float(rb << 16) + 1.f;  // BF16 -> FP32 is a shift
             const float green = __uint_as_float(gb << 16) + 1.f, blue = __uint_as_float(gb & 0xffff0000u) + 1.f;
-            oc = make_float4(__half2float(ho), red, green, blue);
-        } else {
-            const float2 orr = __half22float2(*reinterpret_cast<const __half2 *>(&w));
-            const float2 gbb = __half22float2(*reinterpret_cast<const __half2 *>(&gb));
-            oc = make_float4(orr.x, orr.y, gbb.x, gbb.y);
+            return make_float4(__half2float(ho), red, green, blue);
         }
+        const float2 orr = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        const float2 gbb = __half22float2(*reinterpret_cast<const __half2 *>(&gb));
+        return make_float4(orr.x, orr.y, gbb.x, gbb.y);
     }
 };
 
@@ -503,7 +505,14 @@ cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, cons
 // screen tiles of 16 x 16 (cluster 2: 2 x 1, 4: 2 x 2; list_grid is their
 // grid); the blocks of a list tile form one cluster and share its batches
 // through distributed shared memory. wide_blocks: 8x8 warp blocks.
-// Blend of list tiles (lists = 2: 2 x 1, 4: 2 x 2 screen tiles of 16 x 16)
+// Screen tiles per list tile (1, 2: 2 x 1, 4: 2 x 2, 16: 4 x 4, 64: 8 x 8)
+// as columns x rows.
+inline void list_tile_dims(int code, int *lx, int *ly) {
+    *lx = code >= 64 ? 8 : code >= 16 ? 4 : code >= 2 ? 2 : 1;
+    *ly = code >= 64 ? 8 : code >= 16 ? 4 : code >= 4 ? 2 : 1;
+}
+
+// Blend of list tiles (lists: a list_tile_dims code above 1, 16 x 16 screen tiles)
 // without clusters: each screen tile's block reads its list tile's list.
 cudaError_t gs_launch_blend_listtile(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                      const GsGrid &list_grid, int lists, int width, int height, const float bg[3],

@@ -54,3 +54,12 @@ def test_launches_per_frame():
     for tiles, key_bits, launches in [((120, 68), 45, 11), ((512, 4), 43, 12), ((300, 300), 49, 13)]:
         _, passes, fused = bench.tile_key_plan(*tiles, key_bits)
         assert 10 + passes - fused == launches
+
+
+def test_list_tiles_read_each_entry_once_per_screen_tile():
+    # 2x2 list tiles: each list entry is read by the four screen tiles of its list tile.
+    one = bench.frame_bytes(10, 4, 7, 0, 2, 2, 34, 1024)
+    four = bench.frame_bytes(10, 4, 7, 0, 1, 1, 32, 1024, readers=4)
+    assert four["blend"] - one["blend"] == 3 * 7 * 4
+    assert [bench.list_tile_dims(c) for c in (0, 1, 2, 4, 16, 64)] == \
+        [(1, 1), (1, 1), (2, 1), (2, 2), (4, 4), (8, 8)]

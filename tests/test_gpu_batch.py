@@ -74,8 +74,8 @@ def test_batch_tile_shapes_and_autotune(ctx, tmp_path):
     cache = str(tmp_path / "tune.json")
     tile, ms, depth, cluster, lists = gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams),
                                                            cache_path=cache)
-    assert tile in ((16, 16), (16, 8), (8, 8)) and len(ms) == 7 and all(m > 0 for m in ms)
-    assert depth in (64, 128, 256) and cluster in (0, 2, 4) and lists in (0, 2, 4)
+    assert tile in ((16, 16), (16, 8), (8, 8)) and len(ms) == 9 and all(m > 0 for m in ms)
+    assert depth in (64, 128, 256) and cluster in (0, 2, 4) and lists in (0, 2, 4, 16, 64)
     assert (cluster == 0 and lists == 0) or (tile == (16, 16) and min(cluster, lists) == 0)
     again = gs.gs_autotune_batch(ctx, g, 0, cams, gs.alloc_outputs(cams), cache_path=cache)
     assert (again[0], again[2], again[3], again[4]) == (tile, depth, cluster, lists)

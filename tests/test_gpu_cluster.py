@@ -19,8 +19,9 @@ from paper_2607_15951_gb300 import scenes  # noqa: E402
 
 # (option, value): the four list forms
 FORMS = [("cluster", N.GS_CLUSTER_2X1), ("cluster", N.GS_CLUSTER_2X2),
-         ("list_tiles", N.GS_LISTS_2X1), ("list_tiles", N.GS_LISTS_2X2)]
-FORM_IDS = ["c2x1", "c2x2", "l2x1", "l2x2"]
+         ("list_tiles", N.GS_LISTS_2X1), ("list_tiles", N.GS_LISTS_2X2),
+         ("list_tiles", N.GS_LISTS_4X4), ("list_tiles", N.GS_LISTS_8X8)]
+FORM_IDS = ["c2x1", "c2x2", "l2x1", "l2x2", "l4x4", "l8x8"]
 
 
 @pytest.fixture(scope="module")
@@ -35,7 +36,7 @@ def ctx():
 
 
 def _list_tile(shape):
-    return (32, 16) if shape == 2 else (32, 32)
+    return {2: (32, 16), 4: (32, 32), 16: (64, 64), 64: (128, 128)}[shape]
 
 
 def _last_gaussian(nc, vals, ranges, width, tw, th):
@@ -117,7 +118,8 @@ def test_list_tile_backward_equals_default(ctx):
     g = gs.scene_to_device(scene)
     d = torch.randn((180, 320, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(4))
     res = []
-    for kw in ({}, {"cluster": N.GS_CLUSTER_2X2}, {"list_tiles": N.GS_LISTS_2X2}, {"list_tiles": N.GS_LISTS_2X1}):
+    for kw in ({}, {"cluster": N.GS_CLUSTER_2X2}, {"list_tiles": N.GS_LISTS_2X2}, {"list_tiles": N.GS_LISTS_8X8},
+               {"list_tiles": N.GS_LISTS_2X1}):
         out = gs.render(ctx, g, scene.sh_degree, cam, **kw)
         grads = {k: torch.empty_like(v) for k, v in g.items()}
         gs.gs_render_backward(ctx, g, scene.sh_degree, cam, out["final_T"], out["n_contrib"], d, grads, **kw)
@@ -151,7 +153,8 @@ def test_list_tile_option_checks(ctx):
     scene, cam = scenes.uniform_box(100, 1), scenes.pinhole(64, 64)
     g = gs.scene_to_device(scene)
     for kw in ({"cluster": 3}, {"cluster": 4, "tile": (16, 8)}, {"cluster": 4, "temporal": True},
-               {"list_tiles": 3}, {"list_tiles": 4, "tile": (16, 8)}, {"list_tiles": 2, "temporal": True},
+               {"list_tiles": 3}, {"list_tiles": 8}, {"list_tiles": 4, "tile": (16, 8)},
+               {"list_tiles": 2, "temporal": True},
                {"list_tiles": 4, "cluster": 4}):
         with pytest.raises(gs.GSError):
             gs.render(ctx, g, 0, cam, **kw)
