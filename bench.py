@@ -618,14 +618,15 @@ def main():
                     help="consecutive frames rendered on this many contexts / streams at once (headline value)")
     ap.add_argument("--pipeline-blend-variant", type=int, default=0,
                     help="blend schedule of the frames-in-flight loop (0: the default, 8x8 blocks in packed pairs)")
-    ap.add_argument("--pipeline-list-tiles", type=int, default=4,
-                    help="list tiles of the frames-in-flight loop (4: 2x2 list tiles; 0: a list per screen tile)")
+    ap.add_argument("--pipeline-list-tiles", type=int, default=16,
+                    help="list tiles of the frames-in-flight loop (16: 4x4 list tiles; 0: a list per screen tile)")
     ap.add_argument("--blend-variant", type=int, default=0,
                     help="0 culled (default: 8x8 blocks, two pixels per lane in packed FP32 pairs), 1 basic, "
                          "2 culled 16x8, 3 culled tile, 4 culled 8x8, 5 TMA staging")
     ap.add_argument("--cluster", type=int, default=0, help="thread-block clusters of the blend: 0, 2 (2x1), 4 (2x2)")
-    ap.add_argument("--list-tiles", type=int, default=0,
-                    help="lists of list tiles without clusters: 0, 2 (2x1), 4 (2x2), 16 (4x4), 64 (8x8)")
+    ap.add_argument("--list-tiles", type=int, default=16,
+                    help="lists of list tiles without clusters of the single-frame and end-to-end loops: "
+                         "0 (a list per screen tile), 2 (2x1), 4 (2x2), 16 (4x4, default), 64 (8x8)")
     ap.add_argument("--record-dtype", type=int, default=0, help="blend records: 0 FP32, 1 FP16, 2 BF16")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -643,6 +644,8 @@ def main():
 
     scene, cams = scenes.workload(args.workload)
     cam = cams[0]
+    if args.cluster > 1:  # clusters and list tiles are exclusive: clusters win
+        args.list_tiles = args.pipeline_list_tiles = 0
     ropt = {"cluster": args.cluster, "list_tiles": args.list_tiles, "record_dtype": args.record_dtype}
     H, W = cam.height, cam.width
     g = gs.scene_to_device(scene)
@@ -664,12 +667,16 @@ def main():
     torch.cuda.synchronize()
     gs.gs_sync_status(ctx)
 
-    # Algorithmic work of one frame (deterministic): evaluated and blended pairs.
-    aux = gs.render(ctx, g, scene.sh_degree, cam, variant=args.blend_variant, **ropt)
+    # Algorithmic work of one frame (deterministic): the pairs evaluated along
+    # the 16 x 16 tile lists of the method (a frame with a list per screen
+    # tile; list-tile frames count positions in longer lists).
+    aux = gs.render(ctx, g, scene.sh_degree, cam, variant=args.blend_variant, record_dtype=args.record_dtype)
     torch.cuda.synchronize()
     n_eval_total = int(aux["n_eval"].to(torch.int64).sum().item())
-    stats = gs.gs_last_render_stats(ctx)
     del aux
+    gs.gs_render(ctx, g, scene.sh_degree, cam, rgb, variant=args.blend_variant, **ropt)
+    torch.cuda.synchronize()
+    stats = gs.gs_last_render_stats(ctx)  # the measured list form's counts
 
     # Timed region: per-step CUDA events, L2 flushed between steps outside them.
     gs.gs_set_stage_timing(ctx, True)
@@ -865,8 +872,9 @@ def main():
                       "frac": round(flops * value / world / 1e12 / fp32_peak_tflops, 4)}}
 
     # HBM view of the same frame: bytes each stage must move / its live time.
-    fbytes = frame_bytes(scene.n, stats["n_visible"], stats["n_keys"], scene.sh_degree, (W + 15) // 16,
-                         (H + 15) // 16, stats["key_bits"], W * H)
+    slx, sly = list_tile_dims(max(args.list_tiles, args.cluster))
+    fbytes = frame_bytes(scene.n, stats["n_visible"], stats["n_keys"], scene.sh_degree, (W + 16 * slx - 1) // (16 * slx),
+                         (H + 16 * sly - 1) // (16 * sly), stats["key_bits"], W * H, readers=slx * sly)
     stage_of = {"project": "project_ms", "depth_sort": "depth_sort_ms", "entry_scan": "entry_scan_ms",
                 "emit": "emit_ms", "tile_sort": "tile_sort_ms", "ranges": "ranges_ms", "blend": "blend_ms"}
     hbm_peak = pk.get("hbm_gbs") or 6800.0

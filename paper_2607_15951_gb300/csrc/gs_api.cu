@@ -42,6 +42,7 @@ struct gs_context {
     const uint32_t *last_values = nullptr;
     DevBuf d_rec;
     DevBuf br_geo, br_aux, br_col;  // blend records of the render path (16 B per slot each)
+    DevBuf br_rect;                 // their 16 x 16 tile rects, for list-tile frames (8 B per slot)
     // Batched path (own buffers: a captured graph holds their addresses).
     struct Batch {
         DevBuf views, rec, meta, geo, aux, col, scratch, ranges, order, queue, keys, vals, akeys, avals, sort, rts;
@@ -359,13 +360,20 @@ RecordReader reader(gs_context *ctx, const gs_record *rec, int dtype, bool raw =
     r.aux = static_cast<const float4 *>(ctx->br_aux.ptr);
     r.col = ctx->br_col.ptr;
     r.mode = raw ? gs::kRecRaw : rec_mode(dtype);
+    r.rect16 = static_cast<const uint2 *>(ctx->br_rect.ptr);
     return r;
 }
 
-// Where the render path's projection writes its blend records.
-gs::BlendRecordOut blend_out(gs_context *ctx, int dtype) {
-    return gs::BlendRecordOut{static_cast<float4 *>(ctx->br_geo.ptr), static_cast<float4 *>(ctx->br_aux.ptr),
-                              ctx->br_col.ptr, rec_mode(dtype)};
+// Where the render path's projection writes its blend records (with cam:
+// also their 16 x 16 tile rects, which the list-tile blend reads).
+gs::BlendRecordOut blend_out(gs_context *ctx, int dtype, const gs_camera *cam = nullptr) {
+    return gs::BlendRecordOut{static_cast<float4 *>(ctx->br_geo.ptr),
+                              static_cast<float4 *>(ctx->br_aux.ptr),
+                              ctx->br_col.ptr,
+                              rec_mode(dtype),
+                              cam ? static_cast<uint2 *>(ctx->br_rect.ptr) : nullptr,
+                              cam ? (cam->width + 15) / 16 : 0,
+                              cam ? (cam->height + 15) / 16 : 0};
 }
 
 // The blend records of the last joint batch (one per compact record slot).
@@ -376,6 +384,7 @@ RecordReader batch_reader(gs_context *ctx, int dtype) {
     r.aux = static_cast<const float4 *>(ctx->batch.aux.ptr);
     r.col = ctx->batch.col.ptr;
     r.mode = rec_mode(dtype);
+    r.rect16 = nullptr;
     return r;
 }
 
@@ -760,7 +769,7 @@ void gs_destroy(gs_context *ctx) {
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                       &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
                       &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col, &ctx->gathered,
-                      &ctx->rts_scratch};
+                      &ctx->rts_scratch, &ctx->br_rect};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -804,7 +813,7 @@ size_t gs_workspace_bytes(const gs_context *ctx) {
     const DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                             &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch,
                             &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col,
-                            &ctx->gathered, &ctx->rts_scratch};
+                            &ctx->gathered, &ctx->rts_scratch, &ctx->br_rect};
     size_t t = 0;
     for (const DevBuf *b : bufs) t += b->bytes;
     return t;
@@ -931,7 +940,9 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
     const int dtype = opts->record_dtype;
     if ((st = ensure(ctx, ctx->br_geo, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK ||
         (st = ensure(ctx, ctx->br_aux, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK ||
-        (st = ensure(ctx, ctx->br_col, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK)
+        (st = ensure(ctx, ctx->br_col, (size_t)(n > 0 ? n : 1) * 16, "blend records")) != GS_OK ||
+        (opts->list_tiles > 1 &&
+         (st = ensure(ctx, ctx->br_rect, (size_t)(n > 0 ? n : 1) * 8, "blend record rects")) != GS_OK))
         return st;
     if ((st = ensure(ctx, ctx->records, (size_t)(n > 0 ? n : 1) * sizeof(gs_record), "records")) != GS_OK ||
         (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK)
@@ -1035,7 +1046,7 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
             ev3[1] = ctx->ev[EV_DEPTH];
             ev3[2] = ctx->ev[EV_SCAN];
         }
-        GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, blend_out(ctx, dtype),
+        GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, blend_out(ctx, dtype, opts->list_tiles > 1 ? cam : nullptr),
                                            xy_keys ? akeys : keys, key_bytes, xy_keys, xy_keys ? avals : vals,
                                            cap, ctx->d_counts,
                                            ctx->fused_scratch.ptr, sc, ctx->d_err, s, ev3, prect, prev_rect,

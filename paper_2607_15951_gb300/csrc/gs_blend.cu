@@ -658,15 +658,15 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
 }
 
 // ---------------------------------------------------------------------------
-// List-tile variant: the lists of 2x1 / 2x2 list tiles (as for the cluster
-// blend), each 16 x 16 screen tile blended by its own thread block, without a
-// cluster: the block reads its list tile's list itself and keeps the records
-// whose 16 x 16 tile rect (the rule of the default lists, from the record's
-// integer radius) holds its tile and whose conservative box meets it,
-// compacted in list order into its batch; the batch is blended in packed
-// pairs as by blend_tile_culled_x2. Colours and transmittance equal those of
-// the default lists bit for bit; list positions are the list tile's, as in
-// the cluster blend.
+// List-tile variant: the lists of list tiles of CX x CY screen tiles, each
+// 16 x 16 screen tile blended by its own thread block, without a cluster: the
+// block reads its list tile's list itself and keeps the records whose 16 x 16
+// tile rect (the rule of the default lists; packed per record by the
+// projection) holds its tile, compacted in list order into its batch; the
+// batch is blended in packed pairs as by blend_tile_culled_x2 (whose warp
+// culling drops the records that cannot reach a warp's pixels). Colours and
+// transmittance equal those of the default lists bit for bit; list positions
+// are the list tile's, as in the cluster blend.
 // ---------------------------------------------------------------------------
 template <int CX, int CY, int DEPTH>
 __global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs a) {
@@ -687,9 +687,6 @@ __global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs 
     const f32x2 fy2 = x2((float)py0 + 0.5f, (float)py1 + 0.5f);
     const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
     const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
-    // Pixel-centre extent of the tile (clipped to the image).
-    const float tx0 = tx * TW + 0.5f, tx1 = fminf(tx * TW + TW - 0.5f, a.width - 0.5f);
-    const float ty0 = ty * TH + 0.5f, ty1 = fminf(ty * TH + TH - 0.5f, a.height - 0.5f);
     const int lt = (ty / CY) * a.grid.tiles_x + tx / CX;
     const uint32_t first = a.ranges[2 * lt], last = a.ranges[2 * lt + 1];
 
@@ -710,13 +707,9 @@ __global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs 
             uint32_t gi = 0;
             if (k < last) {
                 gi = a.values[k];
-                const float4 geo = __ldg(a.rd.geo + gi);
-                const int rad = __ldg(reinterpret_cast<const int *>(a.rd.rec32 + 3 * (size_t)gi + 2) + 2);
-                const Rect R16 = tile_rect(geo.x, geo.y, rad, TW, TH, 1 << 30, 1 << 30);
-                if (tx >= R16.x0 && tx < R16.x1 && ty >= R16.y0 && ty < R16.y1) {
-                    const float2 h = blend_box_half(__ldg(a.rd.aux + gi).z);
-                    keep = geo.x - h.x <= tx1 && geo.x + h.x >= tx0 && geo.y - h.y <= ty1 && geo.y + h.y >= ty0;
-                }
+                const uint2 r = __ldg(a.rd.rect16 + gi);
+                keep = (uint32_t)tx >= (r.x & 0xffffu) && (uint32_t)tx < (r.x >> 16) &&
+                       (uint32_t)ty >= (r.y & 0xffffu) && (uint32_t)ty < (r.y >> 16);
             }
             const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
             if (lane == 0) s_wcnt[rd_][warp] = __popc(ballot);

@@ -273,10 +273,36 @@ struct BlendRecordOut {
     float4 *aux;
     void *col;  // float4 (kRecF32) or uint32 (16-bit forms)
     int mode;   // kRecF32, kRecF16 or kRecBF16
+    // Optional (list tiles): the 16 x 16 screen tiles that take the record,
+    // packed as (x0 | x1 << 16, y0 | y1 << 16): those of its tile rect (the
+    // rule of the 16 x 16 lists, from the integer radius rad, clamped to
+    // t16x x t16y) whose pixel centres its conservative box can reach (a
+    // superset of the exact test; an empty range when it reaches none).
+    uint2 *rect16;
+    int t16x, t16y;
     __device__ __forceinline__ void write(size_t j, const float4 &r0, float q11, float o, float r, float g,
-                                          float b) const {
+                                          float b, int rad = 0) const {
         const BlendPre p = blend_pre(r0.z, r0.w, q11, o);
         geo[j] = make_float4(r0.x, r0.y, p.A, p.B);
+        if (rect16) {
+            Rect R = tile_rect(r0.x, r0.y, rad, 16, 16, t16x, t16y);
+            const uint32_t hw = p.hxy;
+            const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(&hw));
+            if (!(h.x >= 0.f && h.y >= 0.f)) {
+                R.x1 = R.x0;  // alpha never reaches 1/255
+            } else if (h.x < 1e6f && h.y < 1e6f) {
+                // Tile t's pixel centres span [16 t + 0.5, 16 t + 15.5]; the
+                // box [u - hx, u + hx] can only meet tiles t with
+                // floor((u - hx - 0.5) / 16) <= t <= floor((u + hx) / 16).
+                R.x0 = max(R.x0, (int)floorf((r0.x - h.x - 0.5f) * 0.0625f));
+                R.x1 = min(R.x1, (int)floorf((r0.x + h.x) * 0.0625f) + 1);
+                R.y0 = max(R.y0, (int)floorf((r0.y - h.y - 0.5f) * 0.0625f));
+                R.y1 = min(R.y1, (int)floorf((r0.y + h.y) * 0.0625f) + 1);
+            }
+            rect16[j] = R.x0 < R.x1 && R.y0 < R.y1
+                            ? make_uint2((uint32_t)R.x0 | ((uint32_t)R.x1 << 16), (uint32_t)R.y0 | ((uint32_t)R.y1 << 16))
+                            : make_uint2(0u, 0u);
+        }
         if (mode == kRecF32) {
             aux[j] = make_float4(p.C, p.thr, __uint_as_float(p.hxy), o);
             static_cast<float4 *>(col)[j] = make_float4(r, g, b, 0.f);
@@ -295,6 +321,7 @@ struct RecordReader {
     const float4 *aux;
     const void *col;
     int mode;
+    const uint2 *rect16;  // the 16 x 16 tile rects (list-tile frames), as BlendRecordOut writes them
     // Any form (RAW: the caller guarantees mode == kRecRaw; kernels that only
     // ever read blend records instantiate RAW = false and carry no code for
     // the per-key constants).

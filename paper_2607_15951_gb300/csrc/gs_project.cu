@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(256, 4) project_list_kernel(const ListArgs A) 
         out[2] = r2;
         // Word r0 was written by this thread in the projection loop above
         // (same candidate-to-thread mapping).
-        if (A.br.geo) A.br.write(g, out[0], r1.x, r1.y, rgb.x, rgb.y, rgb.z);
+        if (A.br.geo) A.br.write(g, out[0], r1.x, r1.y, rgb.x, rgb.y, rgb.z, __float_as_int(S.rad[c]));
     }
     if (!s_last) return;
     // Last block: every block's counts and list entries are in.
