@@ -847,11 +847,12 @@ def main():
     blend_ms = stage_ms.get("blend_ms", float("nan"))
     flops = FLOPS_PER_EVAL * n_eval_total
     achieved = flops / (blend_ms / 1e3) / 1e12
-    blend_kernel = ("blend_cluster_kernel" if args.cluster > 1 else
-                    "blend_listtile_kernel" if args.list_tiles > 1 else
-                    "blend_culled_kernel" if args.blend_variant == 0 else "blend_basic_kernel")
+    clx, cly = list_tile_dims(max(args.cluster, args.list_tiles))
+    blend_kernel = (f"blend_cluster_kernel<{clx},{cly}>" if args.cluster > 1 else
+                    f"blend_listtile_kernel<{clx},{cly}>" if args.list_tiles > 1 else
+                    "blend_culled_kernel<8,8>" if args.blend_variant == 0 else "blend_basic_kernel")
     traffic, traffic_src = profiled_traffic(f"{blend_kernel}@{args.workload}")
-    roofline = {"kernel": "gs_blend", "bound": "alu", "achieved": round(achieved, 3),
+    roofline = {"kernel": blend_kernel, "stage": "gs_blend", "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak_tflops, 4), "traffic": traffic,
                 "traffic_source": traffic_src,
