@@ -668,8 +668,10 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
 // transmittance equal those of the default lists bit for bit; list positions
 // are the list tile's, as in the cluster blend.
 // ---------------------------------------------------------------------------
+// Nine resident blocks per SM (56 registers, as the per-tile blend): measured
+// 1-5 % faster than eight with 64 registers (1080p frame, 4K imbalance view).
 template <int CX, int CY, int DEPTH>
-__global__ void __launch_bounds__(128, 8) blend_listtile_kernel(const BlendArgs a) {
+__global__ void __launch_bounds__(128, 9) blend_listtile_kernel(const BlendArgs a) {
     constexpr int TW = 16, TH = 16, BW = 8, BH = 8, kRows = 4;
     constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
     static_assert(DEPTH % kThreads == 0 && DEPTH >= 2 * kThreads, "batch shape");
