@@ -566,7 +566,7 @@ gs_status launch_blend(gs_context *ctx, const RecordReader &rd, const uint32_t *
     const int variant = blend_schedule(ctx, opts, grid.tiles_x * grid.tiles_y);
     if (opts->list_tiles > 1) {
         GS_CUDA(ctx, gs_launch_blend_listtile(rd, values, ranges, grid, opts->list_tiles, cam->width, cam->height,
-                                              opts->bg, *fb, s));
+                                              opts->bg, *fb, variant == GS_BLEND_CULLED_WIDE, s));
         return GS_OK;
     }
     if (opts->cluster > 1) {

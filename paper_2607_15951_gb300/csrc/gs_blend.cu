@@ -312,12 +312,22 @@ struct PixX2 {
 };
 
 // One staged batch of cnt records (list positions pos0 + slot, or s_pos[slot]
-// when given) blended into the lane's two pixels, in batch order, with the
-// warp culling of the scalar schedule. Returns whether all the warp's pixels
-// have stopped.
-__device__ __forceinline__ bool blend_batch_x2(PixX2 &P, const SRecX2 &S, const int32_t *s_pos, int32_t pos0,
-                                               int cnt, f32x2 fx2, f32x2 fy2, float wx0, float wx1, float wy0,
-                                               float wy1, int lane) {
+// when given) blended into the lane's NP pixel pairs (all in one column, so
+// the x terms of a record are computed once), in batch order, with the warp
+// culling of the scalar schedule. Returns whether all the warp's pixels have
+// stopped.
+template <int NP>
+__device__ __forceinline__ bool all_done_x2(const PixX2 (&P)[NP]) {
+    bool mine = true;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) mine = mine && P[q].done0 && P[q].done1;
+    return __all_sync(0xffffffffu, mine);
+}
+
+template <int NP>
+__device__ __forceinline__ bool blend_batch_x2(PixX2 (&P)[NP], const SRecX2 &S, const int32_t *s_pos, int32_t pos0,
+                                               int cnt, f32x2 fx2, const f32x2 (&fy2)[NP], float wx0, float wx1,
+                                               float wy0, float wy1, int lane) {
     for (int c = 0; c < cnt; c += 32) {
         const int j = c + lane;
         const bool hit = j < cnt && record_touches_x2(S, j, wx0, wx1, wy0, wy1);
@@ -328,43 +338,71 @@ __device__ __forceinline__ bool blend_batch_x2(PixX2 &P, const SRecX2 &S, const 
             const ulonglong2 d0 = S.d0[jj], d1 = S.d1[jj];
             const f32x2 dx2 = x2_sub(fx2, d0.x);
             const f32x2 adx2 = x2_mul(x2_mul(d1.x, dx2), dx2), bdx2 = x2_mul(d1.y, dx2);
-            const f32x2 dy2 = x2_sub(fy2, d0.y);
             const ulonglong2 d2 = S.d2[jj];
-            float e0, e1, thr, hxy;
-            x2_split(x2_fma(dy2, x2_fma(d2.x, dy2, bdx2), adx2), e0, e1);
             const ulonglong2 c2 = S.c2[jj];
+            float thr, hxy;
             x2_split(c2.y, thr, hxy);
-            // power > 0, or alpha < 1/255: the pixel skips the record
-            const bool t0 = !P.done0 && !(e0 > 0.f || e0 < thr);
-            const bool t1 = !P.done1 && !(e1 > 0.f || e1 < thr);
-            if (!(t0 || t1)) continue;
-            float a0, a1;
-            x2_split(x2_mul(d2.y, x2(ex2(e0), ex2(e1))), a0, a1);
-            const f32x2 w2 = x2_mul(x2(fminf(kAlphaMax, a0), fminf(kAlphaMax, a1)), P.T2);
-            float w0, w1, tn0, tn1;
-            x2_split(w2, w0, w1);
-            x2_split(x2_sub(P.T2, w2), tn0, tn1);
-            // T would fall below the limit: the pixel stops before this record.
-            const bool s0 = t0 && tn0 < kTMin, s1 = t1 && tn1 < kTMin;
-            const bool u0 = t0 && !s0, u1 = t1 && !s1;
-            const f32x2 we2 = x2(u0 ? w0 : 0.f, u1 ? w1 : 0.f);  // weights of the pixels that take it
-            P.T2 = x2_sub(P.T2, we2);
-            const ulonglong2 c01 = S.c01[jj];
-            P.R2 = x2_fma(c01.x, we2, P.R2);
-            P.G2 = x2_fma(c01.y, we2, P.G2);
-            P.B2 = x2_fma(c2.x, we2, P.B2);
             const int32_t pos = s_pos ? s_pos[jj] : pos0 + jj;
-            P.last0 = u0 ? pos : P.last0;
-            P.last1 = u1 ? pos : P.last1;
-            if (s0 || s1) {
-                if (s0) P.done0 = true, P.eval0 = pos;
-                if (s1) P.done1 = true, P.eval1 = pos;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                PixX2 &Q = P[q];
+                const f32x2 dy2 = x2_sub(fy2[q], d0.y);
+                float e0, e1;
+                x2_split(x2_fma(dy2, x2_fma(d2.x, dy2, bdx2), adx2), e0, e1);
+                // power > 0, or alpha < 1/255: the pixel skips the record
+                const bool t0 = !Q.done0 && !(e0 > 0.f || e0 < thr);
+                const bool t1 = !Q.done1 && !(e1 > 0.f || e1 < thr);
+                if (!(t0 || t1)) continue;
+                float a0, a1;
+                x2_split(x2_mul(d2.y, x2(ex2(e0), ex2(e1))), a0, a1);
+                const f32x2 w2 = x2_mul(x2(fminf(kAlphaMax, a0), fminf(kAlphaMax, a1)), Q.T2);
+                float w0, w1, tn0, tn1;
+                x2_split(w2, w0, w1);
+                x2_split(x2_sub(Q.T2, w2), tn0, tn1);
+                // T would fall below the limit: the pixel stops before this record.
+                const bool s0 = t0 && tn0 < kTMin, s1 = t1 && tn1 < kTMin;
+                const bool u0 = t0 && !s0, u1 = t1 && !s1;
+                const f32x2 we2 = x2(u0 ? w0 : 0.f, u1 ? w1 : 0.f);  // weights of the pixels that take it
+                Q.T2 = x2_sub(Q.T2, we2);
+                const ulonglong2 c01 = S.c01[jj];
+                Q.R2 = x2_fma(c01.x, we2, Q.R2);
+                Q.G2 = x2_fma(c01.y, we2, Q.G2);
+                Q.B2 = x2_fma(c2.x, we2, Q.B2);
+                Q.last0 = u0 ? pos : Q.last0;
+                Q.last1 = u1 ? pos : Q.last1;
+                if (s0 || s1) {
+                    if (s0) Q.done0 = true, Q.eval0 = pos;
+                    if (s1) Q.done1 = true, Q.eval1 = pos;
+                }
             }
         }
-        if (__all_sync(0xffffffffu, P.done0 && P.done1)) return true;
+        if (all_done_x2(P)) return true;
     }
-    return __all_sync(0xffffffffu, P.done0 && P.done1);
+    return all_done_x2(P);
 }
+
+// A lane's pixels in a BW x 8 warp block (BW = 8: two, BW = 16: four), all in
+// column px: pair q holds rows py(q) and py(q) + 4, py(q) = by + lane / BW +
+// q * 32 / BW.
+template <int BW>
+struct LaneX2 {
+    static constexpr int NP = BW / 8, kRows = 32 / BW;
+    int px, pyb;
+    f32x2 fx2, fy2[NP];
+    PixX2 P[NP];
+    __device__ __forceinline__ LaneX2(const BlendArgs &a, int bx, int by, int lane) {
+        px = bx + (lane % BW);
+        pyb = by + lane / BW;
+        fx2 = x2(px + 0.5f, px + 0.5f);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const int y0 = pyb + q * kRows, y1 = y0 + 4;
+            fy2[q] = x2((float)y0 + 0.5f, (float)y1 + 0.5f);
+            P[q] = PixX2{x2(1.f, 1.f), x2(0.f, 0.f), x2(0.f, 0.f), x2(0.f, 0.f), 0, 0, 0, 0,
+                         !(px < a.width && y0 < a.height), !(px < a.width && y1 < a.height)};
+        }
+    }
+};
 
 // Writes the lane's two pixels (n_list: list length, the n_eval of pixels
 // that never stopped).
@@ -381,9 +419,9 @@ __device__ __forceinline__ void write_pixels_x2(const BlendArgs &a, const PixX2 
     write_pixel(a, px, py1, p1);
 }
 
-template <int TW, int TH, int DEPTH, bool RAW>
+template <int TW, int TH, int BW, int DEPTH, bool RAW>
 __device__ __forceinline__ void blend_tile_culled_x2(const BlendArgs &a, int tile) {
-    constexpr int BW = 8, BH = 8, kRows = 4;
+    constexpr int BH = 8;
     constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
     __shared__ ulonglong2 s_d0[DEPTH], s_d1[DEPTH], s_d2[DEPTH], s_c01[DEPTH], s_c2[DEPTH];
     const SRecX2 S{s_d0, s_d1, s_d2, s_c01, s_c2};
@@ -391,17 +429,12 @@ __device__ __forceinline__ void blend_tile_culled_x2(const BlendArgs &a, int til
     const int tx = tile % a.grid.tiles_x, ty = tile / a.grid.tiles_x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
-    const int px = bx + (lane % BW), py0 = by + lane / BW, py1 = py0 + kRows;
-    const f32x2 fx2 = x2(px + 0.5f, px + 0.5f);
-    const f32x2 fy2 = x2((float)py0 + 0.5f, (float)py1 + 0.5f);
+    LaneX2<BW> L(a, bx, by, lane);
     const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
     const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
 
     const uint32_t first = a.ranges[2 * tile], last = a.ranges[2 * tile + 1];
-    PixX2 P{x2(1.f, 1.f), x2(0.f, 0.f), x2(0.f, 0.f), x2(0.f, 0.f), 0, 0, 0, 0,
-            !(px < a.width && py0 < a.height), !(px < a.width && py1 < a.height)};
-    bool warp_done = __all_sync(0xffffffffu, P.done0 && P.done1);
-
+    bool warp_done = all_done_x2(L.P);
     for (uint32_t start = first; start < last; start += DEPTH) {
         if (__syncthreads_count(warp_done) == kThreads) break;
         for (int s = tid; s < DEPTH; s += kThreads) {
@@ -411,26 +444,36 @@ __device__ __forceinline__ void blend_tile_culled_x2(const BlendArgs &a, int til
         __syncthreads();
         const int cnt = (int)min((uint32_t)DEPTH, last - start);
         const int32_t pos0 = (int32_t)(start - first) + 1;  // list position of slot 0
-        if (!warp_done) warp_done = blend_batch_x2(P, S, nullptr, pos0, cnt, fx2, fy2, wx0, wx1, wy0, wy1, lane);
+        if (!warp_done)
+            warp_done = blend_batch_x2(L.P, S, nullptr, pos0, cnt, L.fx2, L.fy2, wx0, wx1, wy0, wy1, lane);
     }
-    write_pixels_x2(a, P, px, py0, py1, (int32_t)(last - first));
+    const int32_t n_list = (int32_t)(last - first);
+#pragma unroll
+    for (int q = 0; q < LaneX2<BW>::NP; ++q) {
+        const int y0 = L.pyb + q * LaneX2<BW>::kRows;
+        write_pixels_x2(a, L.P[q], L.px, y0, y0 + 4, n_list);
+    }
 }
 
 // Resident blocks per SM the register allocation must allow. Two pixels per
 // lane (8x8 blocks): 36 warps per SM (56 registers), measured 8 % more
 // frames/s with frames in flight than the unconstrained 64 registers and the
-// same time alone. One pixel per lane: no constraint; stating it lets the
-// allocator use 54 registers instead of 46, 4 % faster alone (0.205 ->
-// 0.197 ms on a 1080p frame) although one block fewer fits per SM.
+// same time alone. Four pixels per lane (16x8 blocks, two packed pairs): 28
+// warps per SM (72 registers). One pixel per lane: no constraint; stating it
+// lets the allocator use 54 registers instead of 46, 4 % faster alone (0.205
+// -> 0.197 ms on a 1080p frame) although one block fewer fits per SM.
 constexpr int blend_min_blocks(int warps, int pixels_per_lane) {
-    return pixels_per_lane != 2 ? 1 : (36 / warps < 32 ? 36 / warps : 32);  // at most 32 blocks per SM
+    return pixels_per_lane == 2 ? (36 / warps < 32 ? 36 / warps : 32)  // at most 32 blocks per SM
+         : pixels_per_lane == 4 ? (28 / warps < 32 ? 28 / warps : 32)
+                                : 1;
 }
 
 template <int TW, int TH, int BW, int BH, bool RAW>
 __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32,
                                   blend_min_blocks((TW / BW) * (TH / BH), BW * BH / 32))
     blend_culled_kernel(const BlendArgs a) {
-    if constexpr (BW == 8 && BH == 8 && !RAW) blend_tile_culled_x2<TW, TH, kBatchX2, false>(a, blockIdx.x);
+    if constexpr (BH == 8 && (BW == 8 || BW == 16) && !RAW)
+        blend_tile_culled_x2<TW, TH, BW, kBatchX2, false>(a, blockIdx.x);
     else blend_tile_culled<TW, TH, BW, BH, kBatch, RAW>(a, blockIdx.x);
 }
 
@@ -668,11 +711,17 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
 // transmittance equal those of the default lists bit for bit; list positions
 // are the list tile's, as in the cluster blend.
 // ---------------------------------------------------------------------------
-// Nine resident blocks per SM (56 registers, as the per-tile blend): measured
-// 1-5 % faster than eight with 64 registers (1080p frame, 4K imbalance view).
-template <int CX, int CY, int DEPTH>
-__global__ void __launch_bounds__(128, 9) blend_listtile_kernel(const BlendArgs a) {
-    constexpr int TW = 16, TH = 16, BW = 8, BH = 8, kRows = 4;
+// BW = 8 (8x8 warp blocks, four warps per tile): nine resident blocks per SM
+// (56 registers, as the per-tile blend), measured 1-5 % faster than eight
+// with 64 registers (1080p frame, 4K imbalance view). BW = 16 (16x8 warp
+// blocks, two warps per tile, two pixel pairs per lane): fourteen (72
+// registers), as the per-tile form.
+constexpr int listtile_min_blocks(int bw) { return bw == 8 ? 9 : 14; }
+
+template <int CX, int CY, int BW, int DEPTH>
+__global__ void __launch_bounds__(BW == 8 ? 128 : 64, listtile_min_blocks(BW))
+    blend_listtile_kernel(const BlendArgs a) {
+    constexpr int TW = 16, TH = 16, BH = 8;
     constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
     static_assert(DEPTH % kThreads == 0 && DEPTH >= 2 * kThreads, "batch shape");
     __shared__ ulonglong2 s_d0[DEPTH], s_d1[DEPTH], s_d2[DEPTH], s_c01[DEPTH], s_c2[DEPTH];
@@ -684,18 +733,13 @@ __global__ void __launch_bounds__(128, 9) blend_listtile_kernel(const BlendArgs 
     if (tx * TW >= a.width || ty * TH >= a.height) return;  // padding of the list grid (whole block)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
-    const int px = bx + (lane % BW), py0 = by + lane / BW, py1 = py0 + kRows;
-    const f32x2 fx2 = x2(px + 0.5f, px + 0.5f);
-    const f32x2 fy2 = x2((float)py0 + 0.5f, (float)py1 + 0.5f);
+    LaneX2<BW> L(a, bx, by, lane);
     const float wx0 = bx + 0.5f, wx1 = fminf(bx + BW - 0.5f, a.width - 0.5f);
     const float wy0 = by + 0.5f, wy1 = fminf(by + BH - 0.5f, a.height - 0.5f);
     const int lt = (ty / CY) * a.grid.tiles_x + tx / CX;
     const uint32_t first = a.ranges[2 * lt], last = a.ranges[2 * lt + 1];
 
-    PixX2 P{x2(1.f, 1.f), x2(0.f, 0.f), x2(0.f, 0.f), x2(0.f, 0.f), 0, 0, 0, 0,
-            !(px < a.width && py0 < a.height), !(px < a.width && py1 < a.height)};
-    bool warp_done = __all_sync(0xffffffffu, P.done0 && P.done1);
-
+    bool warp_done = all_done_x2(L.P);
     uint32_t next = first;
     int rd_ = 0;
     while (next < last) {
@@ -733,9 +777,14 @@ __global__ void __launch_bounds__(128, 9) blend_listtile_kernel(const BlendArgs 
             rd_ ^= 1;
         }
         __syncthreads();
-        if (!warp_done) warp_done = blend_batch_x2(P, S, s_pos, 0, cnt, fx2, fy2, wx0, wx1, wy0, wy1, lane);
+        if (!warp_done) warp_done = blend_batch_x2(L.P, S, s_pos, 0, cnt, L.fx2, L.fy2, wx0, wx1, wy0, wy1, lane);
     }
-    write_pixels_x2(a, P, px, py0, py1, (int32_t)(last - first));
+    const int32_t n_list = (int32_t)(last - first);
+#pragma unroll
+    for (int q = 0; q < LaneX2<BW>::NP; ++q) {
+        const int y0 = L.pyb + q * LaneX2<BW>::kRows;
+        write_pixels_x2(a, L.P[q], L.px, y0, y0 + 4, n_list);
+    }
 }
 
 // Persistent blend over many views: blocks take global tiles from a queue
@@ -769,7 +818,7 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(c
         const ViewDesc &V = b.views[lo];
         BlendArgs a{b.rd, b.values, b.ranges + 2 * (size_t)V.tile_base, V.grid, V.cam.width, V.cam.height,
                     {V.bg[0], V.bg[1], V.bg[2]}, V.rgb, V.final_T, V.n_contrib, V.n_eval};
-        blend_tile_culled_x2<TW, TH, DEPTH, false>(a, (int)(gt - V.tile_base));
+        blend_tile_culled_x2<TW, TH, 8, DEPTH, false>(a, (int)(gt - V.tile_base));
     }
 }
 
@@ -1086,15 +1135,23 @@ cudaError_t launch_cluster(const BlendArgs &a, int width, int height, cudaStream
 
 cudaError_t gs_launch_blend_listtile(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                      const GsGrid &list_grid, int lists, int width, int height, const float bg[3],
-                                     const gs_framebuffer &fb, cudaStream_t s) {
+                                     const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s) {
     BlendArgs a{rd, values, ranges, list_grid, width, height,
                 {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
     const dim3 grid((unsigned)((width + 15) / 16), (unsigned)((height + 15) / 16), 1);
-    if (lists == GS_LISTS_2X1) blend_listtile_kernel<2, 1, 256><<<grid, 128, 0, s>>>(a);
-    else if (lists == GS_LISTS_2X2) blend_listtile_kernel<2, 2, 256><<<grid, 128, 0, s>>>(a);
-    else if (lists == GS_LISTS_4X4) blend_listtile_kernel<4, 4, 256><<<grid, 128, 0, s>>>(a);
-    else if (lists == GS_LISTS_8X8) blend_listtile_kernel<8, 8, 256><<<grid, 128, 0, s>>>(a);
-    else return cudaErrorInvalidValue;
+    if (wide_blocks) {
+        if (lists == GS_LISTS_2X1) blend_listtile_kernel<2, 1, 16, 128><<<grid, 64, 0, s>>>(a);
+        else if (lists == GS_LISTS_2X2) blend_listtile_kernel<2, 2, 16, 128><<<grid, 64, 0, s>>>(a);
+        else if (lists == GS_LISTS_4X4) blend_listtile_kernel<4, 4, 16, 128><<<grid, 64, 0, s>>>(a);
+        else if (lists == GS_LISTS_8X8) blend_listtile_kernel<8, 8, 16, 128><<<grid, 64, 0, s>>>(a);
+        else return cudaErrorInvalidValue;
+    } else {
+        if (lists == GS_LISTS_2X1) blend_listtile_kernel<2, 1, 8, 256><<<grid, 128, 0, s>>>(a);
+        else if (lists == GS_LISTS_2X2) blend_listtile_kernel<2, 2, 8, 256><<<grid, 128, 0, s>>>(a);
+        else if (lists == GS_LISTS_4X4) blend_listtile_kernel<4, 4, 8, 256><<<grid, 128, 0, s>>>(a);
+        else if (lists == GS_LISTS_8X8) blend_listtile_kernel<8, 8, 8, 256><<<grid, 128, 0, s>>>(a);
+        else return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -540,10 +540,11 @@ inline void list_tile_dims(int code, int *lx, int *ly) {
 }
 
 // Blend of list tiles (lists: a list_tile_dims code above 1, 16 x 16 screen tiles)
-// without clusters: each screen tile's block reads its list tile's list.
+// without clusters: each screen tile's block reads its list tile's list
+// (wide_blocks: 16x8 warp blocks with two pixel pairs per lane, else 8x8).
 cudaError_t gs_launch_blend_listtile(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                      const GsGrid &list_grid, int lists, int width, int height, const float bg[3],
-                                     const gs_framebuffer &fb, cudaStream_t s);
+                                     const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s);
 cudaError_t gs_launch_blend_cluster(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                     const GsGrid &list_grid, int cluster, int width, int height, const float bg[3],
                                     const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s);

@@ -100,6 +100,22 @@ def test_list_tile_blends_equal_default(ctx, oracle_mod, name, make, form):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("lists", [N.GS_LISTS_2X1, N.GS_LISTS_4X4], ids=["l2x1", "l4x4"])
+def test_list_tiles_with_wide_warp_blocks(ctx, lists):
+    # 16x8 warp blocks (two packed pixel pairs per lane) over list tiles: the
+    # same outputs as 8x8 blocks, list positions included.
+    scene, cam = scenes.clustered(200_000, 44, box=6.0), scenes.pinhole(500, 300)
+    g = gs.scene_to_device(scene)
+    ref = gs.render(ctx, g, scene.sh_degree, cam, list_tiles=lists)
+    out = gs.render(ctx, g, scene.sh_degree, cam, list_tiles=lists, variant=N.GS_BLEND_CULLED_WIDE)
+    torch.cuda.synchronize()
+    for k in ("rgb", "final_T", "n_contrib", "n_eval"):
+        assert torch.equal(out[k], ref[k]), k
+    plain = gs.render(ctx, g, scene.sh_degree, cam)
+    torch.cuda.synchronize()
+    assert torch.equal(out["rgb"], plain["rgb"]) and torch.equal(out["final_T"], plain["final_T"])
+
+
 @pytest.mark.parametrize("opt", ["cluster", "list_tiles"])
 @pytest.mark.parametrize("dtype", [N.GS_RECORD_F16, N.GS_RECORD_BF16], ids=["f16", "bf16"])
 def test_list_tile_blends_with_low_precision_records(ctx, dtype, opt):
