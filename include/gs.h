@@ -287,8 +287,8 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *values, int64
  *   n <= GS_NOALLOC_SORT_MAX_PAIRS, else GS_ERR_CAPACITY (nothing launched).
  *   All calls share that array: calls that overlap on the GPU corrupt each
  *   other; serialise them. The first call on a device looks the array up
- *   with that device current (make it before any stream capture); the
- *   address is kept, so that device must not be reset after the first call.
+ *   with that device current; the address is kept, so that device must not
+ *   be reset after the first call.
  *   Device indices of 64 and above are not served (GS_ERR_CUDA).
  *   Returns after the sort has finished on `stream` (waits once on that
  *   stream to read the device error word); GS_ERR_TIMEOUT if a bounded wait

@@ -18,10 +18,9 @@
 //    overlap on the GPU (different streams, or host threads racing) corrupt
 //    each other's results; serialise them.
 //  * The first call on each device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture begins. The address is kept for the life of
-//    the process, so the device must not be reset (cudaDeviceReset) after
-//    that first call. Devices with an index of 64 or more are not served
+//    (cudaGetSymbolAddress) with that device current. The address is kept
+//    for the life of the process, so the device must not be reset
+//    (cudaDeviceReset) after that first call. Devices with an index of 64 or more are not served
 //    (GS_ERR_CUDA).
 //  * The call returns after the sort has finished on `stream` (it waits for
 //    that stream once to read the device error word).
