@@ -1616,18 +1616,8 @@ __device__ __forceinline__ float3 sh_colour_bwd(const float *__restrict__ src, f
     return gd;
 }
 
-// Shared-memory rows of one block's gradients: the SH row is padded to an
-// odd length so that the per-thread writes hit distinct banks.
-template <int DEG>
-struct BwdSmem {
-    static constexpr int kS = (DEG + 1) * (DEG + 1) * 3;
-    static constexpr int kSP = kS | 1;
-    static constexpr size_t bytes = (size_t)256 * (kSP + 11) * sizeof(float);
-};
-
-// One thread per Gaussian computes its gradients into shared memory; the
-// block then writes its contiguous output ranges with coalesced stores
-// (Gaussians that received no gradient get zeros).
+// Gradients of Gaussian i's parameters from the gradients of its record
+// (rec_grad, 9 floats); false, with all outputs zero, when it received none.
 template <int DEG>
 __device__ __forceinline__ bool project_bwd_one(const ProjectArgs &P, const GsCameraDev &K, int64_t i,
                                                 const float *rec_grad, float *dsh, float *gm_out, float *gls_out,
@@ -1763,46 +1753,8 @@ __device__ __forceinline__ bool project_bwd_one(const ProjectArgs &P, const GsCa
     return true;
 }
 
-template <int DEG>
-__global__ void __launch_bounds__(256) project_bwd_kernel(const ProjectBwdArgs B) {
-    using L = BwdSmem<DEG>;
-    extern __shared__ float smem[];
-    float *s_sh = smem;                  // 256 x kSP
-    float *s_m = s_sh + 256 * L::kSP;    // 256 x 3
-    float *s_l = s_m + 256 * 3;          // 256 x 3
-    float *s_q = s_l + 256 * 3;          // 256 x 4
-    float *s_o = s_q + 256 * 4;          // 256
-    const int t = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * 256;
-    const int64_t i = base + t;
-    if (i < B.P.n)
-        project_bwd_one<DEG>(B.P, B.P.cam, i, B.d_rec + 9 * i, s_sh + t * L::kSP, s_m + 3 * t, s_l + 3 * t,
-                             s_q + 4 * t, s_o + t);
-    __syncthreads();
-    const int cnt = (int)(B.P.n - base < 256 ? B.P.n - base : 256);
-    float *dsh = B.d_sh + base * L::kS;
-    for (int idx = t; idx < cnt * L::kS; idx += 256) dsh[idx] = s_sh[(idx / L::kS) * L::kSP + idx % L::kS];
-    for (int idx = t; idx < cnt * 3; idx += 256) {
-        B.d_means[base * 3 + idx] = s_m[idx];
-        B.d_log_scales[base * 3 + idx] = s_l[idx];
-    }
-    for (int idx = t; idx < cnt * 4; idx += 256) B.d_quats[base * 4 + idx] = s_q[idx];
-    if (t < cnt) B.d_logits[base + t] = s_o[t];
-}
-
 }  // namespace
 
-namespace {
-template <int DEG>
-cudaError_t launch_project_bwd(const ProjectBwdArgs &B, unsigned blocks, cudaStream_t s) {
-    const size_t smem = BwdSmem<DEG>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    project_bwd_kernel<DEG><<<blocks, 256, smem, s>>>(B);
-    return cudaGetLastError();
-}
-}  // namespace
 
 namespace {
 
@@ -1847,6 +1799,27 @@ cudaError_t gs_launch_project_bwd_batch(const gs_gaussians &g, const ViewDesc *v
     return cudaGetLastError();
 }
 
+namespace {
+// The zeros of the gradient arrays are written by memsets (at copy speed);
+// this kernel then writes, one thread per Gaussian, the gradients of the
+// Gaussians whose records received any (the visible ones; a frame has few of
+// them among the scene's Gaussians).
+template <int DEG>
+__global__ void __launch_bounds__(128) project_bwd_sparse_kernel(const ProjectBwdArgs B) {
+    constexpr int kS = (DEG + 1) * (DEG + 1) * 3;
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (i >= B.P.n) return;
+    float dsh[kS], gm[3], gls[3], gq[4], go;
+    if (!project_bwd_one<DEG>(B.P, B.P.cam, i, B.d_rec + 9 * i, dsh, gm, gls, gq, &go)) return;
+    for (int a = 0; a < 3; ++a) B.d_means[3 * i + a] = gm[a];
+    for (int a = 0; a < 3; ++a) B.d_log_scales[3 * i + a] = gls[a];
+    for (int a = 0; a < 4; ++a) B.d_quats[4 * i + a] = gq[a];
+    B.d_logits[i] = go;
+#pragma unroll
+    for (int a = 0; a < kS; ++a) B.d_sh[kS * i + a] = dsh[a];
+}
+}  // namespace
+
 cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   const float *d_rec, const gs_grads &out, cudaStream_t s) {
     if (g.n == 0) return cudaSuccess;
@@ -1859,13 +1832,24 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
     B.d_quats = out.d_quats;
     B.d_logits = out.d_opacity_logits;
     B.d_sh = out.d_sh;
-    const unsigned blocks = (unsigned)((g.n + 255) / 256);
+    // Zeros first (every array is overwritten), then the Gaussians with
+    // gradients: measured faster than writing every Gaussian's gradients from
+    // one kernel (which wrote zeros at a fraction of the copy bandwidth).
+    const size_t n = (size_t)g.n, kS = (size_t)(g.sh_degree + 1) * (g.sh_degree + 1) * 3;
+    cudaError_t e = cudaMemsetAsync(out.d_means, 0, n * 3 * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out.d_log_scales, 0, n * 3 * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out.d_quats, 0, n * 4 * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out.d_opacity_logits, 0, n * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out.d_sh, 0, n * kS * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((g.n + 127) / 128);
     switch (g.sh_degree) {
-        case 0: return launch_project_bwd<0>(B, blocks, s);
-        case 1: return launch_project_bwd<1>(B, blocks, s);
-        case 2: return launch_project_bwd<2>(B, blocks, s);
-        default: return launch_project_bwd<3>(B, blocks, s);
+        case 0: project_bwd_sparse_kernel<0><<<blocks, 128, 0, s>>>(B); break;
+        case 1: project_bwd_sparse_kernel<1><<<blocks, 128, 0, s>>>(B); break;
+        case 2: project_bwd_sparse_kernel<2><<<blocks, 128, 0, s>>>(B); break;
+        default: project_bwd_sparse_kernel<3><<<blocks, 128, 0, s>>>(B); break;
     }
+    return cudaGetLastError();
 }
 
 size_t gs_batch_scratch_bytes(int64_t rec_capacity, int64_t key_capacity, int64_t n, int n_views) {
