@@ -1190,17 +1190,18 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
                     "context's last frame (number " + std::to_string(ctx->frame_id) + ") differs");
     const GsGrid grid = make_grid(cam, opts);
     const int64_t n = g->n;
-    if ((st = ensure(ctx, ctx->d_rec, (size_t)(n > 0 ? n : 1) * 9 * sizeof(float), "record gradients")) != GS_OK)
+    if ((st = ensure(ctx, ctx->d_rec, (size_t)(n > 0 ? n : 1) * kRecGradStride * sizeof(float),
+                     "record gradients")) != GS_OK)
         return st;
     float *d_rec = static_cast<float *>(ctx->d_rec.ptr);
-    GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)n * 9 * sizeof(float), s));
+    GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)n * kRecGradStride * sizeof(float), s));
     GS_CUDA(ctx, gs_launch_blend_bwd(reader(ctx, static_cast<gs_record *>(ctx->records.ptr), ctx->last_dtype),
                                      ctx->last_values, ctx->last_ranges, grid, cam->width, cam->height,
                                      opts->bg, d_rgb, fb->final_T, fb->n_contrib, d_rec, s, ctx->last_cluster));
     GS_CUDA(ctx, gs_launch_project_bwd(*g, make_cam(cam), grid, d_rec, *out, s));
     if (out->d_records && n > 0)
-        GS_CUDA(ctx, cudaMemcpyAsync(out->d_records, d_rec, (size_t)n * 9 * sizeof(float),
-                                     cudaMemcpyDeviceToDevice, s));
+        GS_CUDA(ctx, cudaMemcpy2DAsync(out->d_records, 9 * sizeof(float), d_rec, kRecGradStride * sizeof(float),
+                                       9 * sizeof(float), (size_t)n, cudaMemcpyDeviceToDevice, s));
     return GS_OK;
 }
 
@@ -1441,14 +1442,15 @@ gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const
     DeviceGuard dg(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t n = g->n, nr = B.joint_records;
-    if ((st = ensure(ctx, B.d_rec, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(float), "batch record gradients")) !=
+    if ((st = ensure(ctx, B.d_rec, (size_t)(nr > 0 ? nr : 1) * kRecGradStride * sizeof(float),
+                     "batch record gradients")) !=
             GS_OK ||
         (st = ensure(ctx, B.bviews, (size_t)n_views * sizeof(GsBwdView), "batch backward views")) != GS_OK)
         return st;
     // A copy from pageable memory: the host table may be reused at once.
     GS_CUDA(ctx, cudaMemcpyAsync(B.bviews.ptr, bv.data(), bv.size() * sizeof(GsBwdView), cudaMemcpyHostToDevice, s));
     float *d_rec = static_cast<float *>(B.d_rec.ptr);
-    GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(float), s));
+    GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)(nr > 0 ? nr : 1) * kRecGradStride * sizeof(float), s));
     const size_t kS = (size_t)(g->sh_degree + 1) * (g->sh_degree + 1) * 3;
     if (n > 0) {
         GS_CUDA(ctx, cudaMemsetAsync(out->d_means, 0, (size_t)n * 3 * sizeof(float), s));
@@ -1464,7 +1466,8 @@ gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const
                                            opts->tile_h, B.joint_tiles, d_rec, s));
     GS_CUDA(ctx, gs_launch_project_bwd_batch(*g, views, static_cast<const uint2 *>(B.meta.ptr), nr, d_rec, *out, s));
     if (out->d_records && nr > 0)
-        GS_CUDA(ctx, cudaMemcpyAsync(out->d_records, d_rec, (size_t)nr * 9 * sizeof(float), cudaMemcpyDeviceToDevice,
+        GS_CUDA(ctx, cudaMemcpy2DAsync(out->d_records, 9 * sizeof(float), d_rec, kRecGradStride * sizeof(float),
+                                       9 * sizeof(float), (size_t)nr, cudaMemcpyDeviceToDevice,
                                      s));
     return GS_OK;
 }

@@ -1205,7 +1205,7 @@ struct BlendBwdArgs {
     const float *d_rgb;
     const float *final_T;
     const int32_t *n_contrib;
-    float *d_rec;  // n x 9
+    float *d_rec;  // n rows of kRecGradStride floats
     // Blocks cover TW x TH screen tiles, cta_tiles_x of them per row; the
     // lists belong to list tiles of lcx x lcy screen tiles (1 x 1 unless the
     // frame was blended in thread-block clusters).
@@ -1408,12 +1408,25 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs &a, int tile) 
             }
         }
         __syncthreads();
-        for (int s = tid; s < cnt * 9; s += kThreads) {
-            const float v = s_grad[s];
-            if (v != 0.f) {
-                atomicAdd(&a.d_rec[(size_t)s_g[s / 9] * 9 + s % 9], v);
-                s_grad[s] = 0.f;
-            }
+        // The batch's record gradients into global memory: one thread per
+        // record, a vector reduction per nonzero group of four.
+        for (int r = tid; r < cnt; r += kThreads) {
+            float *src = s_grad + 9 * r;
+            const float4 g0 = make_float4(src[0], src[1], src[2], src[3]);
+            const float4 g1 = make_float4(src[4], src[5], src[6], src[7]);
+            const float g8 = src[8];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) src[k] = 0.f;
+            float *dst = a.d_rec + (size_t)s_g[r] * kRecGradStride;
+            if (g0.x != 0.f || g0.y != 0.f || g0.z != 0.f || g0.w != 0.f)
+                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(g0.x), "f"(g0.y),
+                             "f"(g0.z), "f"(g0.w)
+                             : "memory");
+            if (g1.x != 0.f || g1.y != 0.f || g1.z != 0.f || g1.w != 0.f)
+                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4), "f"(g1.x), "f"(g1.y),
+                             "f"(g1.z), "f"(g1.w)
+                             : "memory");
+            if (g8 != 0.f) atomicAdd(dst + 8, g8);
         }
         __syncthreads();
     }
@@ -1434,7 +1447,7 @@ struct BlendBwdBatchArgs {
     const ViewDesc *views;
     const GsBwdView *bviews;    // d_rgb, final_T, n_contrib per view
     int n_views;
-    float *d_rec;               // record slots x 9
+    float *d_rec;               // record slots x kRecGradStride
 };
 
 template <int TW, int TH>

@@ -532,6 +532,12 @@ cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, cons
 // screen tiles of 16 x 16 (cluster 2: 2 x 1, 4: 2 x 2; list_grid is their
 // grid); the blocks of a list tile form one cluster and share its batches
 // through distributed shared memory. wide_blocks: 8x8 warp blocks.
+// Rows of the record-gradient buffers: the 9 gradients of a record
+// (u, v, Q00, Q01, Q11, opacity, red, green, blue) padded to 12 floats, so a
+// row is 16-byte aligned and the blend backward adds it with vector
+// reductions.
+constexpr int kRecGradStride = 12;
+
 // Screen tiles per list tile (1, 2: 2 x 1, 4: 2 x 2, 16: 4 x 4, 64: 8 x 8)
 // as columns x rows.
 inline void list_tile_dims(int code, int *lx, int *ly) {

@@ -1555,7 +1555,7 @@ namespace {
 
 struct ProjectBwdArgs {
     ProjectArgs P;
-    const float *d_rec;  // n x 9
+    const float *d_rec;  // n rows of kRecGradStride
     float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
 };
 
@@ -1771,7 +1771,7 @@ __global__ void __launch_bounds__(128)
     const uint2 m = meta[j];  // (view, Gaussian)
     const int64_t i = m.y;
     float dsh[kS], gm[3], gls[3], gq[4], go;
-    if (!project_bwd_one<DEG>(P, views[m.x].cam, i, d_rec + 9 * j, dsh, gm, gls, gq, &go)) return;
+    if (!project_bwd_one<DEG>(P, views[m.x].cam, i, d_rec + kRecGradStride * j, dsh, gm, gls, gq, &go)) return;
     for (int a = 0; a < 3; ++a) atomicAdd(out.d_means + 3 * i + a, gm[a]);
     for (int a = 0; a < 3; ++a) atomicAdd(out.d_log_scales + 3 * i + a, gls[a]);
     for (int a = 0; a < 4; ++a) atomicAdd(out.d_quats + 4 * i + a, gq[a]);
@@ -1810,7 +1810,7 @@ __global__ void __launch_bounds__(128) project_bwd_sparse_kernel(const ProjectBw
     const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
     if (i >= B.P.n) return;
     float dsh[kS], gm[3], gls[3], gq[4], go;
-    if (!project_bwd_one<DEG>(B.P, B.P.cam, i, B.d_rec + 9 * i, dsh, gm, gls, gq, &go)) return;
+    if (!project_bwd_one<DEG>(B.P, B.P.cam, i, B.d_rec + kRecGradStride * i, dsh, gm, gls, gq, &go)) return;
     for (int a = 0; a < 3; ++a) B.d_means[3 * i + a] = gm[a];
     for (int a = 0; a < 3; ++a) B.d_log_scales[3 * i + a] = gls[a];
     for (int a = 0; a < 4; ++a) B.d_quats[4 * i + a] = gq[a];

@@ -144,8 +144,11 @@ def test_list_tile_backward_equals_default(ctx):
     for r in res[1:]:
         for k in res[0]:
             a, b = r[k], res[0][k]
-            # float atomics: equal up to the summation order
-            assert torch.allclose(a, b, rtol=1e-4, atol=1e-5 * float(b.abs().max()) + 1e-12), k
+            # Float atomics sum each gradient in a run-dependent order: two
+            # backward passes of the same frame differ by up to ~1.2e-5 of the
+            # largest log-scale gradient (cancelling terms), so list forms are
+            # compared at 1e-4 of the largest gradient, plus 1e-4 relative.
+            assert torch.allclose(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()) + 1e-12), k
     # A backward with other cluster options than the frame's is refused.
     with pytest.raises(gs.GSError):
         gs.gs_render_backward(ctx, g, scene.sh_degree, cam, out["final_T"], out["n_contrib"], d, res[0])
