@@ -176,10 +176,10 @@ typedef struct {
     int32_t cluster;        /* gs_render (and gs_render_batch, which then
                                renders view by view): thread-block clusters of
                                the blend, see GS_CLUSTER_*; 16x16 tiles only */
-    int32_t list_tiles;     /* gs_render (and gs_render_batch, which then
-                               renders view by view): lists of list tiles
-                               without clusters, see GS_LISTS_*; 16x16 tiles
-                               only, not together with cluster               */
+    int32_t list_tiles;     /* gs_render and gs_render_batch (jointly too;
+                               not gs_render_batch_backward): lists of list
+                               tiles without clusters, see GS_LISTS_*; 16x16
+                               tiles only, not together with cluster         */
 } gs_options;
 
 /* Thread-block clusters of the blend (gs_options.cluster; Sec. 4.4 and 5.5
@@ -206,7 +206,9 @@ enum { GS_CLUSTER_NONE = 0, GS_CLUSTER_2X1 = 2, GS_CLUSTER_2X2 = 4 };
  * them: no cluster barriers, at the price of each list entry being read by
  * every screen tile of its list tile. Outputs as with the clusters (colours
  * and transmittance equal the 16x16 lists' bit for bit, list positions are
- * the list tile's). Not with temporal re-binning. */
+ * the list tile's). gs_render_batch's joint schedule takes them too (one work
+ * item per screen tile of a list tile); gs_render_batch_backward does not
+ * (GS_ERR_UNSUPPORTED). Not with temporal re-binning. */
 enum { GS_LISTS_1X1 = 0, GS_LISTS_2X1 = 2, GS_LISTS_2X2 = 4, GS_LISTS_4X4 = 16, GS_LISTS_8X8 = 64 };
 
 /* How gs_render_batch schedules the views. JOINT: one projection, one key
@@ -430,12 +432,13 @@ gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const
 
 /* Autotuner of gs_render_batch: renders the batch with each screen-tile
  * shape and list form (16x16, 16x8, 8x8 with a list per tile; 16x16 with
- * GS_CLUSTER_2X1, GS_CLUSTER_2X2, GS_LISTS_2X1, GS_LISTS_2X2, GS_LISTS_4X4
- * and GS_LISTS_8X8, which render view by view) and, for the joint schedule,
- * each blend staging depth (256, 128, 64 records), times three runs of each
- * with CUDA events, and writes the fastest into opts->tile_w / tile_h /
- * cluster / list_tiles / batch_depth. ms_out (host, 9 floats, optional)
- * receives per candidate the mean time of its best depth, in that order. */
+ * GS_CLUSTER_2X1 and GS_CLUSTER_2X2, which render view by view; 16x16 with
+ * GS_LISTS_2X1, GS_LISTS_2X2, GS_LISTS_4X4 and GS_LISTS_8X8) and, for the
+ * joint schedule with a list per tile, each blend staging depth (256, 128,
+ * 64 records), times three runs of each with CUDA events, and writes the
+ * fastest into opts->tile_w / tile_h / cluster / list_tiles / batch_depth.
+ * ms_out (host, 9 floats, optional) receives per candidate the mean time of
+ * its best depth, in that order. */
 gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_camera *cams, int32_t n_views,
                             gs_options *opts, const gs_framebuffer *fbs, void *stream, float *ms_out);
 

@@ -425,12 +425,13 @@ def gs_render_batch(ctx: Context, g: dict, sh_degree: int, cams, outs, *, tile=(
 
 
 def gs_render_batch_backward(ctx: Context, g: dict, sh_degree: int, cams, outs, d_rgbs, grads: dict, *,
-                             tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0, stream=None) -> None:
+                             tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0, list_tiles: int = 0,
+                             stream=None) -> None:
     """outs: the per-view dicts the joint gs_render_batch wrote (with final_T
     and n_contrib); d_rgbs: per-view CUDA tensors (H, W, 3); grads: dict of
     CUDA tensors shaped like g (and optionally 'records')."""
     gs = gaussians_struct(g, sh_degree)
-    o = options_struct(tile, bg, record_dtype)
+    o = options_struct(tile, bg, record_dtype, list_tiles=list_tiles)
     carr, farr = _cams_fbs(cams, outs)
     ptrs = (ctypes.c_void_p * len(cams))(*[_ptr(d) for d in d_rgbs])
     out = N.gs_grads()

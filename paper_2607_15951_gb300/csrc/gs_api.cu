@@ -46,6 +46,7 @@ struct gs_context {
     // Batched path (own buffers: a captured graph holds their addresses).
     struct Batch {
         DevBuf views, rec, meta, geo, aux, col, scratch, ranges, order, queue, keys, vals, akeys, avals, sort, rts;
+        DevBuf rect;  // 16 x 16 tile ranges of the records (list tiles)
         ViewDesc *h_views = nullptr;
         int h_views_cap = 0;
         int64_t rec_cap = 0, key_cap = 0;
@@ -56,7 +57,7 @@ struct gs_context {
         // The last joint batch, for gs_render_batch_backward.
         bool have_joint = false;
         int64_t joint_n = 0, joint_records = 0;
-        int joint_views = 0, joint_tw = 0, joint_th = 0, joint_dtype = 0;
+        int joint_views = 0, joint_tw = 0, joint_th = 0, joint_dtype = 0, joint_lists = 1;
         int32_t joint_tiles = 0;
         const uint32_t *joint_values = nullptr;
         DevBuf d_rec, bviews;
@@ -384,7 +385,7 @@ RecordReader batch_reader(gs_context *ctx, int dtype) {
     r.aux = static_cast<const float4 *>(ctx->batch.aux.ptr);
     r.col = ctx->batch.col.ptr;
     r.mode = rec_mode(dtype);
-    r.rect16 = nullptr;
+    r.rect16 = static_cast<const uint2 *>(ctx->batch.rect.ptr);
     return r;
 }
 
@@ -785,7 +786,7 @@ void gs_destroy(gs_context *ctx) {
     for (auto &e : ctx->temporal.ev)
         if (e) cudaEventDestroy(e);
     auto &B = ctx->batch;
-    DevBuf *bb[] = {&B.views, &B.rec, &B.meta, &B.geo, &B.aux, &B.col, &B.scratch, &B.ranges, &B.order,
+    DevBuf *bb[] = {&B.rect, &B.views, &B.rec, &B.meta, &B.geo, &B.aux, &B.col, &B.scratch, &B.ranges, &B.order,
                     &B.queue, &B.keys, &B.vals, &B.akeys, &B.avals, &B.sort, &B.d_rec, &B.bviews, &B.rts};
     for (DevBuf *b : bb)
         if (b->ptr) cudaFree(b->ptr);
@@ -1226,8 +1227,11 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
     uint32_t *keys = static_cast<uint32_t *>(B.keys.ptr), *akeys = static_cast<uint32_t *>(B.akeys.ptr);
     uint32_t *vals = static_cast<uint32_t *>(B.vals.ptr), *avals = static_cast<uint32_t *>(B.avals.ptr);
     uint2 *meta = static_cast<uint2 *>(B.meta.ptr);
+    const int lists = opts->list_tiles > 1 ? opts->list_tiles : 1;
+    int lx = 1, ly = 1;
+    list_tile_dims(lists, &lx, &ly);
     gs::BlendRecordOut bro{static_cast<float4 *>(B.geo.ptr), static_cast<float4 *>(B.aux.ptr), B.col.ptr,
-                           rec_mode(dtype)};
+                           rec_mode(dtype), lists > 1 ? static_cast<uint2 *>(B.rect.ptr) : nullptr};
     GS_CUDA(ctx, gs_launch_project_bin_batch(*g, views, n_views, static_cast<gs_record *>(B.rec.ptr), bro, meta,
                                              B.rec_cap, keys,
                                              vals, B.key_cap, ctx->d_counts, B.scratch.ptr, sc, ctx->d_err, s));
@@ -1245,11 +1249,12 @@ gs_status enqueue_batch(gs_context *ctx, const gs_gaussians *g, int n_views, con
     GS_CUDA(ctx, gs_launch_ranges_tiles(sk, 4, B.key_cap, ctx->d_counts + 2, total_tiles, ranges, ctx->d_err, s));
     uint32_t *qs = static_cast<uint32_t *>(B.queue.ptr);
     uint32_t *order = static_cast<uint32_t *>(B.order.ptr);
-    GS_CUDA(ctx, gs_launch_queue(ranges, total_tiles, qs, order, s));
+    // With list tiles, one queue item per (list tile, screen tile of it).
+    GS_CUDA(ctx, gs_launch_queue(ranges, total_tiles, qs, order, s, lx * ly));
     const RecordReader rd = batch_reader(ctx, dtype);
     GS_CUDA(ctx, gs_launch_blend_batch(rd, sv, ranges, views, n_views, opts->tile_w, opts->tile_h,
                                        opts->batch_depth ? opts->batch_depth : 256, order,
-                                       total_tiles, qs + 193, s));
+                                       (int32_t)(total_tiles * lx * ly), qs + 193, lists, s));
     GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, 4 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, s));
     GS_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -1273,9 +1278,9 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto &B = ctx->batch;
     const int64_t n = g->n;
-    // Thread-block clusters and list tiles are properties of the single-view
-    // blend: such a batch renders view by view.
-    const bool per_view = opts->batch_mode == GS_BATCH_PER_VIEW || list_shape(opts) > 1 ||
+    // Thread-block clusters are a property of the single-view blend: such a
+    // batch renders view by view (list tiles render jointly as well).
+    const bool per_view = opts->batch_mode == GS_BATCH_PER_VIEW || opts->cluster > 1 ||
                           (opts->batch_mode == GS_BATCH_AUTO && B.keys_per_view > kBatchPerViewKeys);
     B.have_joint = false;
     if (per_view) {
@@ -1310,7 +1315,7 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
     std::vector<int64_t> sig = {n, g->sh_degree, (int64_t)(uintptr_t)g->means, (int64_t)(uintptr_t)g->log_scales,
                                 (int64_t)(uintptr_t)g->quats, (int64_t)(uintptr_t)g->opacity_logits,
                                 (int64_t)(uintptr_t)g->sh, n_views, opts->tile_w, opts->tile_h,
-                                opts->record_dtype, opts->batch_depth};
+                                opts->record_dtype, opts->batch_depth, opts->list_tiles};
     for (int v = 0; v < n_views; ++v) {
         ViewDesc &V = B.h_views[v];
         V.cam = make_cam(&cams[v]);
@@ -1325,7 +1330,12 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
         sig.push_back(cams[v].width);
         sig.push_back(cams[v].height);
     }
-    if (total_tiles >= (int64_t(1) << 31)) return fail(ctx, GS_ERR_INVALID_ARG, "too many tiles in one batch");
+    {
+        int lx = 1, ly = 1;
+        list_tile_dims(opts->list_tiles > 1 ? opts->list_tiles : 1, &lx, &ly);
+        if (total_tiles * lx * ly >= (int64_t(1) << 31))
+            return fail(ctx, GS_ERR_INVALID_ARG, "too many tiles in one batch");
+    }
     const int bits = key_bits_for((int)total_tiles);
     if (B.rec_cap == 0) B.rec_cap = std::max<int64_t>(int64_t(1) << 20, n * n_views / 8);
     if (B.key_cap == 0) B.key_cap = std::max<int64_t>(int64_t(1) << 22, 4 * B.rec_cap);
@@ -1333,7 +1343,9 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
         const int64_t rc = B.rec_cap, kc = B.key_cap;
         void *before[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.aux.ptr, B.col.ptr, B.scratch.ptr,
                           B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,
-                          B.avals.ptr, B.sort.ptr, B.rts.ptr};
+                          B.avals.ptr, B.sort.ptr, B.rts.ptr, B.rect.ptr};
+        int qlx = 1, qly = 1;  // queue items per global tile
+        list_tile_dims(opts->list_tiles > 1 ? opts->list_tiles : 1, &qlx, &qly);
         if ((st = ensure(ctx, B.views, (size_t)n_views * sizeof(ViewDesc), "view table")) != GS_OK ||
             (st = ensure(ctx, B.rec, (size_t)rc * sizeof(gs_record), "batch records")) != GS_OK ||
             (st = ensure(ctx, B.meta, (size_t)rc * 8, "batch record meta")) != GS_OK ||
@@ -1342,7 +1354,8 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
             (st = ensure(ctx, B.col, (size_t)rc * 16, "batch blend records")) != GS_OK ||
             (st = ensure(ctx, B.scratch, gs_batch_scratch_bytes(rc, kc, n, n_views), "batch scratch")) != GS_OK ||
             (st = ensure(ctx, B.ranges, (size_t)total_tiles * 8, "batch ranges")) != GS_OK ||
-            (st = ensure(ctx, B.order, (size_t)total_tiles * 4, "batch queue")) != GS_OK ||
+            (st = ensure(ctx, B.order, (size_t)total_tiles * qlx * qly * 4, "batch queue")) != GS_OK ||
+            (opts->list_tiles > 1 && (st = ensure(ctx, B.rect, (size_t)rc * 8, "batch record rects")) != GS_OK) ||
             (st = ensure(ctx, B.queue, gs_queue_scratch_bytes(), "batch queue")) != GS_OK ||
             (st = ensure(ctx, B.keys, (size_t)kc * 4, "batch keys")) != GS_OK ||
             (st = ensure(ctx, B.vals, (size_t)kc * 4, "batch values")) != GS_OK ||
@@ -1356,7 +1369,7 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
             return st;
         void *after[] = {B.views.ptr, B.rec.ptr, B.meta.ptr, B.geo.ptr, B.aux.ptr, B.col.ptr, B.scratch.ptr,
                          B.ranges.ptr, B.order.ptr, B.queue.ptr, B.keys.ptr, B.vals.ptr, B.akeys.ptr,
-                         B.avals.ptr, B.sort.ptr, B.rts.ptr};
+                         B.avals.ptr, B.sort.ptr, B.rts.ptr, B.rect.ptr};
         std::vector<int64_t> full = sig;
         full.push_back(rc);
         full.push_back(kc);
@@ -1410,6 +1423,7 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
         B.joint_tw = opts->tile_w;
         B.joint_th = opts->tile_h;
         B.joint_dtype = opts->record_dtype;
+        B.joint_lists = opts->list_tiles > 1 ? opts->list_tiles : 1;
         B.joint_tiles = (int32_t)total_tiles;
         if (*ctx->h_err) return collect_device_error(ctx, s);
         return GS_OK;
@@ -1427,9 +1441,12 @@ gs_status gs_render_batch_backward(gs_context *ctx, const gs_gaussians *g, const
         return fail(ctx, GS_ERR_INVALID_ARG, "cameras, framebuffers, d_rgb and the gradient struct are required");
     auto &B = ctx->batch;
     if (!B.have_joint || B.joint_n != g->n || B.joint_views != n_views || B.joint_tw != opts->tile_w ||
-        B.joint_th != opts->tile_h || B.joint_dtype != opts->record_dtype)
+        B.joint_th != opts->tile_h || B.joint_dtype != opts->record_dtype ||
+        B.joint_lists != (opts->list_tiles > 1 ? opts->list_tiles : 1))
         return fail(ctx, GS_ERR_INVALID_ARG,
                     "gs_render_batch_backward must follow a joint gs_render_batch of the same scene, views and options");
+    if (B.joint_lists > 1)
+        return fail(ctx, GS_ERR_UNSUPPORTED, "gs_render_batch_backward does not take list tiles");
     if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
         return fail(ctx, GS_ERR_INVALID_ARG, "a gradient array is NULL");
     std::vector<GsBwdView> bv((size_t)n_views);
@@ -1505,8 +1522,8 @@ gs_status gs_autotune_batch(gs_context *ctx, const gs_gaussians *g, const gs_cam
             o.list_tiles = shapes[k][3];
             o.batch_depth = depths[d];
             for (int w = 0; w < 2 && st == GS_OK; ++w) st = gs_render_batch(ctx, g, cams, n_views, &o, fbs, stream);
-            // The depth only matters to the joint schedule.
-            const bool joint = ctx->batch.have_joint;
+            // The depth only matters to the joint schedule without list tiles.
+            const bool joint = ctx->batch.have_joint && o.list_tiles <= 1;
             float total = 0.f;
             for (int r = 0; r < 3 && st == GS_OK; ++r) {
                 cudaEventRecord(e0, s);

@@ -289,15 +289,16 @@ namespace {
 
 constexpr int kBuckets = 33;
 
-__global__ void queue_count_kernel(const uint32_t *__restrict__ ranges, int32_t n_tiles, uint32_t *qs) {
+__global__ void queue_count_kernel(const uint32_t *__restrict__ ranges, int64_t n_items, int subs, uint32_t *qs) {
     // qs: [0,64) counts, [64,128) starts, [128,192) cursors, 192 ticket, 193 head
     __shared__ uint32_t s_c[kBuckets];
     __shared__ bool s_last;
     for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) s_c[b] = 0;
     __syncthreads();
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_items;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        const int64_t tile = t / subs;
+        const uint32_t len = ranges[2 * tile + 1] - ranges[2 * tile];
         atomicAdd(&s_c[len ? 32 - __clz(len) : 0], 1u);
     }
     __syncthreads();
@@ -316,11 +317,12 @@ __global__ void queue_count_kernel(const uint32_t *__restrict__ ranges, int32_t 
     }
 }
 
-__global__ void queue_scatter_kernel(const uint32_t *__restrict__ ranges, int32_t n_tiles, uint32_t *qs,
+__global__ void queue_scatter_kernel(const uint32_t *__restrict__ ranges, int64_t n_items, int subs, uint32_t *qs,
                                      uint32_t *__restrict__ order) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tiles) return;
-    const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+    if (t >= n_items) return;
+    const int64_t tile = t / subs;
+    const uint32_t len = ranges[2 * tile + 1] - ranges[2 * tile];
     const int b = len ? 32 - __clz(len) : 0;
     order[qs[64 + b] + atomicAdd(&qs[128 + b], 1u)] = (uint32_t)t;
 }
@@ -330,14 +332,15 @@ __global__ void queue_scatter_kernel(const uint32_t *__restrict__ ranges, int32_
 size_t gs_queue_scratch_bytes() { return 256 * sizeof(uint32_t); }
 
 cudaError_t gs_launch_queue(const uint32_t *ranges, int32_t n_tiles, uint32_t *qs, uint32_t *order,
-                            cudaStream_t s) {
+                            cudaStream_t s, int subs) {
     cudaError_t e = cudaMemsetAsync(qs, 0, gs_queue_scratch_bytes(), s);
-    if (e != cudaSuccess || n_tiles == 0) return e;
-    const unsigned blocks = (unsigned)((n_tiles + 255) / 256);
-    queue_count_kernel<<<blocks < 608 ? blocks : 608, 256, 0, s>>>(ranges, n_tiles, qs);
+    const int64_t n_items = (int64_t)n_tiles * subs;
+    if (e != cudaSuccess || n_items == 0) return e;
+    const unsigned blocks = (unsigned)((n_items + 255) / 256);
+    queue_count_kernel<<<blocks < 608 ? blocks : 608, 256, 0, s>>>(ranges, n_items, subs, qs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    queue_scatter_kernel<<<blocks, 256, 0, s>>>(ranges, n_tiles, qs, order);
+    queue_scatter_kernel<<<blocks, 256, 0, s>>>(ranges, n_items, subs, qs, order);
     return cudaGetLastError();
 }
 

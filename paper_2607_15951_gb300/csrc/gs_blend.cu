@@ -719,8 +719,7 @@ __global__ void __launch_bounds__((16 / BW) * (16 / BH) * 32) blend_cluster_kern
 constexpr int listtile_min_blocks(int bw) { return bw == 8 ? 9 : 14; }
 
 template <int CX, int CY, int BW, int DEPTH>
-__global__ void __launch_bounds__(BW == 8 ? 128 : 64, listtile_min_blocks(BW))
-    blend_listtile_kernel(const BlendArgs a) {
+__device__ __forceinline__ void blend_listtile_tile(const BlendArgs &a, int tx, int ty) {
     constexpr int TW = 16, TH = 16, BH = 8;
     constexpr int kWX = TW / BW, kWarps = kWX * (TH / BH), kThreads = kWarps * 32;
     static_assert(DEPTH % kThreads == 0 && DEPTH >= 2 * kThreads, "batch shape");
@@ -729,8 +728,6 @@ __global__ void __launch_bounds__(BW == 8 ? 128 : 64, listtile_min_blocks(BW))
     __shared__ uint32_t s_wcnt[2][kWarps];
     const SRecX2 S{s_d0, s_d1, s_d2, s_c01, s_c2};
 
-    const int tx = blockIdx.x, ty = blockIdx.y;
-    if (tx * TW >= a.width || ty * TH >= a.height) return;  // padding of the list grid (whole block)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bx = tx * TW + (warp % kWX) * BW, by = ty * TH + (warp / kWX) * BH;
     LaneX2<BW> L(a, bx, by, lane);
@@ -787,6 +784,14 @@ __global__ void __launch_bounds__(BW == 8 ? 128 : 64, listtile_min_blocks(BW))
     }
 }
 
+template <int CX, int CY, int BW, int DEPTH>
+__global__ void __launch_bounds__(BW == 8 ? 128 : 64, listtile_min_blocks(BW))
+    blend_listtile_kernel(const BlendArgs a) {
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    if (tx * 16 >= a.width || ty * 16 >= a.height) return;  // padding of the list grid (whole block)
+    blend_listtile_tile<CX, CY, BW, DEPTH>(a, tx, ty);
+}
+
 // Persistent blend over many views: blocks take global tiles from a queue
 // (largest lists first); each tile is rendered with its view's parameters.
 struct BlendBatchArgs {
@@ -795,12 +800,15 @@ struct BlendBatchArgs {
     const uint32_t *ranges;   // indexed by global tile
     const ViewDesc *views;
     int n_views;
-    const uint32_t *order;    // global tiles in queue order
-    int32_t n_tiles;
+    const uint32_t *order;    // queue order: global tiles (with list tiles: global tile x sub-tiles + sub-tile)
+    int32_t n_tiles;          // items in the queue
     uint32_t *queue_head;
 };
 
-template <int TW, int TH, int DEPTH>
+// With list tiles (LX x LY screen tiles of 16 x 16 per list tile) the queue
+// holds one item per (list tile, screen tile of it), in list-length order,
+// and each item is blended as by blend_listtile_kernel.
+template <int TW, int TH, int DEPTH, int LX = 1, int LY = 1>
 __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(const BlendBatchArgs b) {
     __shared__ int s_item;
     for (;;) {
@@ -809,8 +817,9 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(c
         __syncthreads();
         const int item = s_item;
         if (item >= b.n_tiles) return;
-        const uint32_t gt = b.order[item];
-        int lo = 0, hi = b.n_views - 1;  // last view whose first tile <= gt
+        const uint32_t code = b.order[item];
+        const uint32_t gt = code / (LX * LY);  // global (list) tile
+        int lo = 0, hi = b.n_views - 1;        // last view whose first tile <= gt
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (b.views[mid].tile_base <= gt) lo = mid; else hi = mid - 1;
@@ -818,7 +827,15 @@ __global__ void __launch_bounds__((TW / 8) * (TH / 8) * 32) blend_batch_kernel(c
         const ViewDesc &V = b.views[lo];
         BlendArgs a{b.rd, b.values, b.ranges + 2 * (size_t)V.tile_base, V.grid, V.cam.width, V.cam.height,
                     {V.bg[0], V.bg[1], V.bg[2]}, V.rgb, V.final_T, V.n_contrib, V.n_eval};
-        blend_tile_culled_x2<TW, TH, 8, DEPTH, false>(a, (int)(gt - V.tile_base));
+        const int lt = (int)(gt - V.tile_base);
+        if constexpr (LX * LY == 1) {
+            blend_tile_culled_x2<TW, TH, 8, DEPTH, false>(a, lt);
+        } else {
+            const int sub = (int)(code % (LX * LY));
+            const int tx = (lt % V.grid.tiles_x) * LX + sub % LX, ty = (lt / V.grid.tiles_x) * LY + sub / LX;
+            if (tx * 16 < V.cam.width && ty * 16 < V.cam.height)  // block-uniform
+                blend_listtile_tile<LX, LY, 8, 256>(a, tx, ty);
+        }
     }
 }
 
@@ -1032,12 +1049,12 @@ __global__ void __launch_bounds__(TW *TH) blend_basic_kernel(const BlendArgs a) 
 }  // namespace
 
 namespace {
-template <int TW, int TH, int DEPTH>
+template <int TW, int TH, int DEPTH, int LX = 1, int LY = 1>
 void launch_blend_batch(const BlendBatchArgs &b, int sms, cudaStream_t s) {
     constexpr int kThreads = (TW / 8) * (TH / 8) * 32;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<TW, TH, DEPTH>, kThreads, 0);
-    blend_batch_kernel<TW, TH, DEPTH><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), kThreads, 0, s>>>(b);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<TW, TH, DEPTH, LX, LY>, kThreads, 0);
+    blend_batch_kernel<TW, TH, DEPTH, LX, LY><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), kThreads, 0, s>>>(b);
 }
 
 template <int DEPTH>
@@ -1050,11 +1067,20 @@ void launch_blend_batch_shape(const BlendBatchArgs &b, int tile_w, int tile_h, i
 
 cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                   const ViewDesc *views_dev, int n_views, int tile_w, int tile_h, int depth,
-                                  const uint32_t *order, int32_t n_tiles, uint32_t *queue_head, cudaStream_t s) {
-    BlendBatchArgs b{rd, values, ranges, views_dev, n_views, order, n_tiles, queue_head};
+                                  const uint32_t *order, int32_t n_items, uint32_t *queue_head, int lists,
+                                  cudaStream_t s) {
+    BlendBatchArgs b{rd, values, ranges, views_dev, n_views, order, n_items, queue_head};
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (lists > 1) {  // list tiles: 16x16 screen tiles, 256 records staged per batch
+        if (lists == GS_LISTS_2X1) launch_blend_batch<16, 16, 256, 2, 1>(b, sms, s);
+        else if (lists == GS_LISTS_2X2) launch_blend_batch<16, 16, 256, 2, 2>(b, sms, s);
+        else if (lists == GS_LISTS_4X4) launch_blend_batch<16, 16, 256, 4, 4>(b, sms, s);
+        else if (lists == GS_LISTS_8X8) launch_blend_batch<16, 16, 256, 8, 8>(b, sms, s);
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     // Persistent grid sized by occupancy; 8x8 warp blocks (in the queue loop
     // the 8x4 blocks' larger thread blocks measured slower: 7770 vs 8985
     // views/s on 64 views). depth = records staged per shared-memory batch.

@@ -665,12 +665,16 @@ cudaError_t gs_launch_project_bin_batch(const gs_gaussians &g, const ViewDesc *v
                                         gs_record *records, const gs::BlendRecordOut &br, uint2 *meta, int64_t rec_capacity, uint32_t *keys,
                                         uint32_t *values, int64_t key_capacity, unsigned long long *counts,
                                         void *scratch, const GsSortScratch &sc, uint32_t *d_err, cudaStream_t s);
-// Persistent blend over a queue of global tiles (largest lists first).
+// Persistent blend over a queue of global tiles (largest lists first); with
+// list tiles (lists > 1, a list_tile_dims code) the queue holds one item per
+// (global list tile, screen tile of it).
 cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                   const ViewDesc *views_dev, int n_views, int tile_w, int tile_h, int depth,
-                                  const uint32_t *order, int32_t n_tiles, uint32_t *queue_head, cudaStream_t s);
-// Largest-first work queue of global tiles; qs: gs_queue_scratch_bytes(),
-// the queue head the blend takes items from is qs[193].
+                                  const uint32_t *order, int32_t n_items, uint32_t *queue_head, int lists,
+                                  cudaStream_t s);
+// Largest-first work queue of global tiles, subs items per tile (item t
+// names tile t / subs); qs: gs_queue_scratch_bytes(), the queue head the
+// blend takes items from is qs[193].
 size_t gs_queue_scratch_bytes();
 cudaError_t gs_launch_queue(const uint32_t *ranges, int32_t n_tiles, uint32_t *qs, uint32_t *order,
-                            cudaStream_t s);
+                            cudaStream_t s, int subs = 1);

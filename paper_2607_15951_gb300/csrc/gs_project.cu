@@ -1279,7 +1279,13 @@ __global__ void __launch_bounds__(256, 3) project_list_batch_kernel(const ListBa
             float4 *out = A.P.records + 3 * (size_t)slot;
             out[1] = r1;
             out[2] = r2;
-            if (A.br.geo) A.br.write(slot, S.r0[c], r1.x, r1.y, rgb.x, rgb.y, rgb.z);
+            if (A.br.geo) {
+                // The 16 x 16 tile ranges (list tiles) are on this view's screen.
+                BlendRecordOut br = A.br;
+                br.t16x = (V.cam.width + 15) / 16;
+                br.t16y = (V.cam.height + 15) / 16;
+                br.write(slot, S.r0[c], r1.x, r1.y, rgb.x, rgb.y, rgb.z, __float_as_int(S.rad[c]));
+            }
         }
         __syncthreads();
     }

@@ -168,6 +168,29 @@ def test_list_tile_batch_renders_views_alike(ctx, opt):
         assert torch.equal(o["rgb"], ref["rgb"]) and torch.equal(o["final_T"], ref["final_T"])
 
 
+@pytest.mark.parametrize("lists", [N.GS_LISTS_2X1, N.GS_LISTS_4X4, N.GS_LISTS_8X8], ids=["l2x1", "l4x4", "l8x8"])
+def test_joint_batch_with_list_tiles(ctx, lists):
+    # The joint schedule with list tiles (one queue item per screen tile of a
+    # list tile) equals the view-by-view renders with the same list tiles, list
+    # positions included; its batched backward is refused.
+    scene = scenes.clustered(100_000, 45, box=6.0)
+    cams = scenes.trajectory(4, 1045, radius=2.0, sizes=((330, 190), (200, 120)))
+    g = gs.scene_to_device(scene)
+    outs = gs.alloc_outputs(cams, aux=True)
+    gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, list_tiles=lists, batch_mode=N.GS_BATCH_JOINT)
+    torch.cuda.synchronize()
+    for c, o in zip(cams, outs):
+        ref = gs.render(ctx, g, scene.sh_degree, c, list_tiles=lists)
+        torch.cuda.synchronize()
+        for k in ("rgb", "final_T", "n_contrib", "n_eval"):
+            assert torch.equal(o[k], ref[k]), k
+    gs.gs_render_batch(ctx, g, scene.sh_degree, cams, outs, list_tiles=lists, batch_mode=N.GS_BATCH_JOINT)
+    grads = {k: torch.empty_like(v) for k, v in g.items()}
+    d = [torch.ones_like(o["rgb"]) for o in outs]
+    with pytest.raises(gs.GSError):
+        gs.gs_render_batch_backward(ctx, g, scene.sh_degree, cams, outs, d, grads, list_tiles=lists)
+
+
 def test_list_tile_option_checks(ctx):
     scene, cam = scenes.uniform_box(100, 1), scenes.pinhole(64, 64)
     g = gs.scene_to_device(scene)
