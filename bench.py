@@ -628,6 +628,12 @@ def main():
                     help="lists of list tiles without clusters of the single-frame and end-to-end loops: "
                          "0 (a list per screen tile), 2 (2x1), 4 (2x2), 16 (4x4, default), 64 (8x8)")
     ap.add_argument("--record-dtype", type=int, default=0, help="blend records: 0 FP32, 1 FP16, 2 BF16")
+    ap.add_argument("--tile-order", type=int, default=0,
+                    help="order of the blend's tiles in the single-frame and end-to-end loops: 0 longest list "
+                         "first (default), 1 grid order")
+    ap.add_argument("--pipeline-tile-order", type=int, default=1,
+                    help="order of the blend's tiles in the frames-in-flight loop (1: grid order, measured faster "
+                         "there; 0: longest list first)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -646,7 +652,8 @@ def main():
     cam = cams[0]
     if args.cluster > 1:  # clusters and list tiles are exclusive: clusters win
         args.list_tiles = args.pipeline_list_tiles = 0
-    ropt = {"cluster": args.cluster, "list_tiles": args.list_tiles, "record_dtype": args.record_dtype}
+    ropt = {"cluster": args.cluster, "list_tiles": args.list_tiles, "record_dtype": args.record_dtype,
+            "tile_order": args.tile_order}
     H, W = cam.height, cam.width
     g = gs.scene_to_device(scene)
     ctx = gs.Context(local)
@@ -719,7 +726,7 @@ def main():
     pctx = [ctx] + [gs.Context(local) for _ in range(F - 1)]
     pstreams = [torch.cuda.Stream() for _ in range(F)]
     prgb = [rgb] + [torch.empty_like(rgb) for _ in range(F - 1)]
-    popt = dict(ropt, list_tiles=args.pipeline_list_tiles)
+    popt = dict(ropt, list_tiles=args.pipeline_list_tiles, tile_order=args.pipeline_tile_order)
     for k in range(F):
         for _ in range(args.warmup):
             gs.gs_render(pctx[k], g, scene.sh_degree, cam, prgb[k], variant=args.pipeline_blend_variant, **popt)
@@ -866,7 +873,8 @@ def main():
     # move once per frame interval.
     roofline_headline = {
         "loop": f"{F} frames in flight, blend schedule {args.pipeline_blend_variant}, "
-                f"list tiles {args.pipeline_list_tiles}",
+                f"list tiles {args.pipeline_list_tiles}, "
+                f"{'longest-first' if args.pipeline_tile_order == 0 else 'grid'} tile order",
         "frame_ms": round(ms_per_frame, 5),
         "blend_alu": {"bound": "alu", "achieved": round(flops * value / world / 1e12, 3),
                       "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
@@ -908,12 +916,15 @@ def main():
         "setup": {"n_visible": stats["n_visible"], "n_keys": stats["n_keys"],
                    "key_bits": stats["key_bits"], "blend_variant": args.blend_variant,
                    "cluster": args.cluster, "list_tiles": args.list_tiles, "record_dtype": args.record_dtype,
+                   "tile_order": ("longest list first" if args.tile_order == 0 else "grid"),
                    "sync_mode": "deferred (GS_SYNC_DEFERRED)",
                    "frames_in_flight": F,
                    "frames_per_step": F,
                    "ms_per_frame": round(ms_per_frame, 5),
                    "frames_in_flight_blend_variant": args.pipeline_blend_variant,
                    "frames_in_flight_list_tiles": args.pipeline_list_tiles,
+                   "frames_in_flight_tile_order": ("longest list first" if args.pipeline_tile_order == 0
+                                                   else "grid"),
                    "frames_in_flight_keys": pstats["n_keys"],
                    "inputs": "8 rotating copies of the scene (8 x 236 MB, above L2) in the frames-in-flight loop",
                    "single_stream_frame_ms": round(single_ms, 4),

@@ -180,6 +180,8 @@ typedef struct {
                                not gs_render_batch_backward): lists of list
                                tiles without clusters, see GS_LISTS_*; 16x16
                                tiles only, not together with cluster         */
+    int32_t tile_order;     /* gs_render: the order in which the blend's thread
+                               blocks take tiles, see GS_ORDER_*             */
 } gs_options;
 
 /* Thread-block clusters of the blend (gs_options.cluster; Sec. 4.4 and 5.5
@@ -210,6 +212,21 @@ enum { GS_CLUSTER_NONE = 0, GS_CLUSTER_2X1 = 2, GS_CLUSTER_2X2 = 4 };
  * item per screen tile of a list tile); gs_render_batch_backward does not
  * (GS_ERR_UNSUPPORTED). Not with temporal re-binning. */
 enum { GS_LISTS_1X1 = 0, GS_LISTS_2X1 = 2, GS_LISTS_2X2 = 4, GS_LISTS_4X4 = 16, GS_LISTS_8X8 = 64 };
+
+/* Order of gs_render's blend blocks (gs_options.tile_order). LONGEST_FIRST
+ * (default): one small kernel sorts the frame's (list) tiles by the bit
+ * length of their list, longest first, and block b of the culled blends
+ * (GS_BLEND_CULLED, _CULLED_WIDE, _CULLED_TILE, _CULLED_8X8) and of the
+ * list-tile blend takes the b-th tile of that order, so the tiles with the
+ * longest lists start first and the short ones fill the end of the launch
+ * (on a clustered scene a few tiles hold twenty times the mean list). GRID:
+ * block b takes tile b (row order). The images are identical. The basic,
+ * TMA and cluster blends, and gs_render_backward, always run in grid order.
+ * Measured on a 1M-Gaussian 1080p frame: one frame at a time longest first
+ * is faster (0.34 against 0.37 ms); with eight frames in flight on eight
+ * streams grid order is (their blends fill each other's ends, and the sort
+ * kernel and the ordered start cost ~3 %). */
+enum { GS_ORDER_LONGEST_FIRST = 0, GS_ORDER_GRID = 1 };
 
 /* How gs_render_batch schedules the views. JOINT: one projection, one key
  * sort and one persistent blend over all views (pays off for many short

@@ -64,7 +64,7 @@ def camera_struct(cam) -> N.gs_camera:
 
 def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
                    blend_variant: int = 0, deferred: bool = False, temporal: int = 0,
-                   cluster: int = 0, list_tiles: int = 0) -> N.gs_options:
+                   cluster: int = 0, list_tiles: int = 0, tile_order: int = 0) -> N.gs_options:
     o = N.gs_options()
     _lib().gs_default_options(ctypes.byref(o))
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
@@ -76,6 +76,7 @@ def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
     o.temporal = int(temporal)  # False/0 off, True/1 adaptive, 2 re-bin whenever possible
     o.cluster = int(cluster)
     o.list_tiles = int(list_tiles)
+    o.tile_order = int(tile_order)
     return o
 
 
@@ -207,17 +208,18 @@ def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_co
 def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
               n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
               record_dtype: int = 0, deferred: bool = False, temporal: bool = False, cluster: int = 0,
-              list_tiles: int = 0, stream=None) -> None:
+              list_tiles: int = 0, tile_order: int = 0, stream=None) -> None:
     """deferred=True: GS_SYNC_DEFERRED (no host synchronisation; an overflow
     or device error is raised by a later call on the context).
     temporal=True (or 1): re-bin from the previous frame's lists when that
     measured faster (same results); 2: re-bin whenever possible.
     cluster: GS_CLUSTER_2X1 / _2X2 blend in thread-block clusters;
-    list_tiles: GS_LISTS_2X1 / _2X2 lists of list tiles, read by every
-    screen tile's block (no cluster)."""
+    list_tiles: GS_LISTS_2X1 / _2X2 / _4X4 / _8X8 lists of list tiles, read
+    by every screen tile's block (no cluster);
+    tile_order: GS_ORDER_LONGEST_FIRST (0) or GS_ORDER_GRID (1) blend blocks."""
     gs = gaussians_struct(g, sh_degree)
     c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred, temporal, cluster,
-                                              list_tiles)
+                                              list_tiles, tile_order)
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
                                ctypes.byref(fb), _stream(stream)))
@@ -289,7 +291,8 @@ def scene_to_device(scene, device="cuda") -> dict:
 
 def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
            aux: bool = True, variant: int = 0, record_dtype: int = 0, deferred: bool = False,
-           temporal: bool = False, cluster: int = 0, list_tiles: int = 0, stream=None) -> dict:
+           temporal: bool = False, cluster: int = 0, list_tiles: int = 0, tile_order: int = 0,
+           stream=None) -> dict:
     """Allocate outputs with torch and call gs_render."""
     import torch
     H, W = int(cam.height), int(cam.width)
@@ -301,7 +304,8 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
         out["n_eval"] = torch.empty((H, W), dtype=torch.int32, device=dev)
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
               out.get("n_eval"), tile=tile, bg=bg, variant=variant, record_dtype=record_dtype,
-              deferred=deferred, temporal=temporal, cluster=cluster, list_tiles=list_tiles, stream=stream)
+              deferred=deferred, temporal=temporal, cluster=cluster, list_tiles=list_tiles,
+              tile_order=tile_order, stream=stream)
     return out
 
 

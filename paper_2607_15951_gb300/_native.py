@@ -41,6 +41,8 @@ GS_LISTS_2X1 = 2
 GS_LISTS_2X2 = 4
 GS_LISTS_4X4 = 16
 GS_LISTS_8X8 = 64
+GS_ORDER_LONGEST_FIRST = 0
+GS_ORDER_GRID = 1
 NOALLOC_SORT_MAX_PAIRS = 262144  # GS_NOALLOC_SORT_MAX_PAIRS in include/gs.h
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_CAPACITY", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}
@@ -83,7 +85,8 @@ class gs_options(ctypes.Structure):
                 ("blend_variant", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
                 ("sync_mode", ctypes.c_int32), ("temporal", ctypes.c_int32),
                 ("batch_mode", ctypes.c_int32), ("batch_depth", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("list_tiles", ctypes.c_int32)]
+                ("cluster", ctypes.c_int32), ("list_tiles", ctypes.c_int32),
+                ("tile_order", ctypes.c_int32)]
 
 
 class gs_render_stats(ctypes.Structure):

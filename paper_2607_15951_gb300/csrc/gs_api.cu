@@ -43,6 +43,7 @@ struct gs_context {
     DevBuf d_rec;
     DevBuf br_geo, br_aux, br_col;  // blend records of the render path (16 B per slot each)
     DevBuf br_rect;                 // their 16 x 16 tile rects, for list-tile frames (8 B per slot)
+    DevBuf tile_order;              // the blend's longest-list-first tile order (4 B per list tile)
     // Batched path (own buffers: a captured graph holds their addresses).
     struct Batch {
         DevBuf views, rec, meta, geo, aux, col, scratch, ranges, order, queue, keys, vals, akeys, avals, sort, rts;
@@ -204,6 +205,8 @@ gs_status check_options(gs_context *ctx, const gs_options *o) {
         return fail(ctx, GS_ERR_INVALID_ARG, "list tiles need 16x16 tiles");
     if (o->list_tiles > 1 && o->temporal)
         return fail(ctx, GS_ERR_UNSUPPORTED, "temporal re-binning does not take list tiles");
+    if (o->tile_order != GS_ORDER_LONGEST_FIRST && o->tile_order != GS_ORDER_GRID)
+        return fail(ctx, GS_ERR_INVALID_ARG, "tile_order must be GS_ORDER_LONGEST_FIRST or GS_ORDER_GRID");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ctx, GS_ERR_INVALID_ARG, "bg must be finite");
     return GS_OK;
@@ -559,15 +562,34 @@ int blend_schedule(const gs_context *ctx, const gs_options *opts, int n_tiles) {
     return GS_BLEND_CULLED_8X8;
 }
 
+// Longest lists first (GS_ORDER_LONGEST_FIRST): the culled and list-tile
+// blends take their tiles in the order of a small sort kernel, launched here
+// after the frame's ranges; *order stays null for grid order and for the
+// blends that do not take an order.
+gs_status launch_tile_order(gs_context *ctx, const uint32_t *ranges, const GsGrid &grid, const gs_options *opts,
+                            cudaStream_t s, const uint32_t **order) {
+    *order = nullptr;
+    const int n_tiles = grid.tiles_x * grid.tiles_y;
+    const int variant = blend_schedule(ctx, opts, n_tiles);
+    if (opts->tile_order != GS_ORDER_LONGEST_FIRST || opts->cluster > 1 ||
+        (opts->list_tiles <= 1 && (variant == GS_BLEND_BASIC || variant == GS_BLEND_TMA)))
+        return GS_OK;
+    gs_status st = ensure(ctx, ctx->tile_order, (size_t)(n_tiles > 0 ? n_tiles : 1) * 4, "tile order");
+    if (st != GS_OK) return st;
+    GS_CUDA(ctx, gs_launch_tile_order(ranges, n_tiles, static_cast<uint32_t *>(ctx->tile_order.ptr), s));
+    *order = static_cast<const uint32_t *>(ctx->tile_order.ptr);
+    return GS_OK;
+}
+
 // The blend of a gs_render frame with `d_n` (device count, at most n_cap)
-// pairs in its lists.
+// pairs in its lists; order: from launch_tile_order.
 gs_status launch_blend(gs_context *ctx, const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                        const GsGrid &grid, const gs_camera *cam, const gs_options *opts, const gs_framebuffer *fb,
-                       const unsigned long long *d_n, int64_t n_cap, cudaStream_t s) {
+                       const unsigned long long *d_n, int64_t n_cap, const uint32_t *order, cudaStream_t s) {
     const int variant = blend_schedule(ctx, opts, grid.tiles_x * grid.tiles_y);
     if (opts->list_tiles > 1) {
         GS_CUDA(ctx, gs_launch_blend_listtile(rd, values, ranges, grid, opts->list_tiles, cam->width, cam->height,
-                                              opts->bg, *fb, variant == GS_BLEND_CULLED_WIDE, s));
+                                              opts->bg, *fb, variant == GS_BLEND_CULLED_WIDE, order, s));
         return GS_OK;
     }
     if (opts->cluster > 1) {
@@ -582,7 +604,8 @@ gs_status launch_blend(gs_context *ctx, const RecordReader &rd, const uint32_t *
                                          static_cast<float4 *>(ctx->gathered.ptr), d_n, n_cap, ctx->d_err, s));
         return GS_OK;
     }
-    GS_CUDA(ctx, gs_launch_blend(rd, values, ranges, grid, cam->width, cam->height, opts->bg, *fb, variant, s));
+    GS_CUDA(ctx, gs_launch_blend(rd, values, ranges, grid, cam->width, cam->height, opts->bg, *fb, variant, s,
+                                 order));
     return GS_OK;
 }
 
@@ -680,9 +703,11 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     GS_CUDA(ctx, gs_launch_temporal_rebin(R, s));
     temporal_mark(ctx, 1, s);
     mark(ctx, EV_SORT, s);
+    const uint32_t *order = nullptr;
+    if ((st = launch_tile_order(ctx, ranges, grid, opts, s, &order)) != GS_OK) return st;
     mark(ctx, EV_RANGES, s);
-    if ((st = launch_blend(ctx, reader(ctx, rec, dtype), vals, ranges, grid, cam, opts, fb, counters + 3, cap, s)) !=
-        GS_OK)
+    if ((st = launch_blend(ctx, reader(ctx, rec, dtype), vals, ranges, grid, cam, opts, fb, counters + 3, cap, order,
+                           s)) != GS_OK)
         return st;
     mark(ctx, EV_BLEND, s);
     unsigned long long *h = ctx->h_ring;  // no deferred frame is in flight (drained before)
@@ -770,7 +795,7 @@ void gs_destroy(gs_context *ctx) {
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                       &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
                       &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col, &ctx->gathered,
-                      &ctx->rts_scratch, &ctx->br_rect};
+                      &ctx->rts_scratch, &ctx->br_rect, &ctx->tile_order};
     for (DevBuf *b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -814,7 +839,7 @@ size_t gs_workspace_bytes(const gs_context *ctx) {
     const DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                             &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch,
                             &ctx->ranges, &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col,
-                            &ctx->gathered, &ctx->rts_scratch, &ctx->br_rect};
+                            &ctx->gathered, &ctx->rts_scratch, &ctx->br_rect, &ctx->tile_order};
     size_t t = 0;
     for (const DevBuf *b : bufs) t += b->bytes;
     return t;
@@ -1080,10 +1105,14 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         uint32_t *sv = moved ? out_v : in_v;
         GS_CUDA(ctx, gs_launch_ranges_tiles(sk, key_bytes, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s,
                                             xy_keys ? grid.tiles_x : 0));
-        mark(ctx, EV_RANGES, s);
+        // (The temporal binning time ends with the ranges, as that of a
+        // re-binned frame does.)
         if (track) temporal_mark(ctx, 1, s);
+        const uint32_t *order = nullptr;
+        if ((st = launch_tile_order(ctx, ranges, grid, opts, s, &order)) != GS_OK) return st;
+        mark(ctx, EV_RANGES, s);
         if ((st = launch_blend(ctx, reader(ctx, rec, dtype), sv, ranges, grid, cam, opts, fb, ctx->d_counts + 2,
-                               cap, s)) != GS_OK)
+                               cap, order, s)) != GS_OK)
             return st;
         mark(ctx, EV_BLEND, s);
         if (deferred) {

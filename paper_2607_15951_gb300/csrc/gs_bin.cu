@@ -329,6 +329,76 @@ __global__ void queue_scatter_kernel(const uint32_t *__restrict__ ranges, int64_
 
 }  // namespace
 
+namespace {
+
+// Longest-list-first order of one frame's (list) tiles, one block: a
+// counting sort of the tiles by the bit length of their list, longest first
+// (tiles in one bucket keep an arbitrary order). Each thread loads the ranges
+// of up to kOrderUnroll tiles at once; lanes of a warp that fall in the same
+// bucket take one shared-memory atomic between them; the buckets of the
+// first kOrderCache tiles are kept in shared memory for the second pass.
+constexpr int kOrderThreads = 1024, kOrderUnroll = 8, kOrderCache = 32768;
+
+__device__ __forceinline__ int order_bucket(uint2 r) {
+    const uint32_t len = r.y - r.x;
+    return len ? 32 - __clz(len) : 0;
+}
+
+__global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(const uint2 *__restrict__ ranges,
+                                                                   int32_t n_tiles, uint32_t *__restrict__ order) {
+    __shared__ uint32_t s_count[kBuckets], s_next[kBuckets];
+    __shared__ uint8_t s_bucket[kOrderCache];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < kBuckets) s_count[tid] = 0;
+    __syncthreads();
+    // Tile base + j kOrderThreads + lane for j < kOrderUnroll (base: the
+    // warp's first tile, warp-uniform, so every lane takes each match).
+    for (int base = tid - lane; base < n_tiles; base += kOrderThreads * kOrderUnroll) {
+        uint2 r[kOrderUnroll];
+#pragma unroll
+        for (int j = 0; j < kOrderUnroll; ++j) {
+            const int t = base + j * kOrderThreads + lane;
+            r[j] = t < n_tiles ? ranges[t] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < kOrderUnroll; ++j) {
+            const int t = base + j * kOrderThreads + lane;
+            const int b = t < n_tiles ? order_bucket(r[j]) : kBuckets;  // kBuckets: no tile
+            const uint32_t peers = __match_any_sync(0xffffffffu, b);
+            if (b < kBuckets && lane == __ffs(peers) - 1) atomicAdd(&s_count[b], (uint32_t)__popc(peers));
+            if (t < n_tiles && t < kOrderCache) s_bucket[t] = (uint8_t)b;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (int b = kBuckets - 1; b >= 0; --b) {
+            s_next[b] = run;
+            run += s_count[b];
+        }
+    }
+    __syncthreads();
+    for (int base = tid - lane; base < n_tiles; base += kOrderThreads) {
+        const int t = base + lane;
+        const int b = t >= n_tiles ? kBuckets : t < kOrderCache ? (int)s_bucket[t] : order_bucket(ranges[t]);
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t first = 0;
+        if (b < kBuckets && lane == leader) first = atomicAdd(&s_next[b], (uint32_t)__popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (b < kBuckets) order[first + __popc(peers & lanemask_lt())] = (uint32_t)t;
+    }
+}
+
+}  // namespace
+
+cudaError_t gs_launch_tile_order(const uint32_t *ranges, int32_t n_tiles, uint32_t *order, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    // ranges: 2 n_tiles words from cudaMalloc, so 8-byte aligned pairs
+    tile_order_kernel<<<1, kOrderThreads, 0, s>>>(reinterpret_cast<const uint2 *>(ranges), n_tiles, order);
+    return cudaGetLastError();
+}
+
 size_t gs_queue_scratch_bytes() { return 256 * sizeof(uint32_t); }
 
 cudaError_t gs_launch_queue(const uint32_t *ranges, int32_t n_tiles, uint32_t *qs, uint32_t *order,

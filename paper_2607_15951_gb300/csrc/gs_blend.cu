@@ -41,6 +41,8 @@ struct BlendArgs {
     float *final_T;
     int32_t *n_contrib;
     int32_t *n_eval;
+    // Block b blends (list) tile order[b] (longest list first) when set, else tile b.
+    const uint32_t *order;
 };
 
 __device__ __forceinline__ float ex2(float x) {
@@ -472,9 +474,10 @@ template <int TW, int TH, int BW, int BH, bool RAW>
 __global__ void __launch_bounds__((TW / BW) * (TH / BH) * 32,
                                   blend_min_blocks((TW / BW) * (TH / BH), BW * BH / 32))
     blend_culled_kernel(const BlendArgs a) {
+    const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     if constexpr (BH == 8 && (BW == 8 || BW == 16) && !RAW)
-        blend_tile_culled_x2<TW, TH, BW, kBatchX2, false>(a, blockIdx.x);
-    else blend_tile_culled<TW, TH, BW, BH, kBatch, RAW>(a, blockIdx.x);
+        blend_tile_culled_x2<TW, TH, BW, kBatchX2, false>(a, tile);
+    else blend_tile_culled<TW, TH, BW, BH, kBatch, RAW>(a, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -787,7 +790,14 @@ __device__ __forceinline__ void blend_listtile_tile(const BlendArgs &a, int tx, 
 template <int CX, int CY, int BW, int DEPTH>
 __global__ void __launch_bounds__(BW == 8 ? 128 : 64, listtile_min_blocks(BW))
     blend_listtile_kernel(const BlendArgs a) {
-    const int tx = blockIdx.x, ty = blockIdx.y;
+    // Ordered: a 1-D grid of CX CY blocks per list tile, the list tiles
+    // longest list first; else the 2-D grid of screen tiles.
+    int tx = blockIdx.x, ty = blockIdx.y;
+    if (a.order) {
+        const int lt = (int)a.order[blockIdx.x / (CX * CY)], sub = (int)(blockIdx.x % (CX * CY));
+        tx = (lt % a.grid.tiles_x) * CX + sub % CX;
+        ty = (lt / a.grid.tiles_x) * CY + sub / CX;
+    }
     if (tx * 16 >= a.width || ty * 16 >= a.height) return;  // padding of the list grid (whole block)
     blend_listtile_tile<CX, CY, BW, DEPTH>(a, tx, ty);
 }
@@ -1161,10 +1171,12 @@ cudaError_t launch_cluster(const BlendArgs &a, int width, int height, cudaStream
 
 cudaError_t gs_launch_blend_listtile(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                      const GsGrid &list_grid, int lists, int width, int height, const float bg[3],
-                                     const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s) {
+                                     const gs_framebuffer &fb, bool wide_blocks, const uint32_t *order,
+                                     cudaStream_t s) {
     BlendArgs a{rd, values, ranges, list_grid, width, height,
-                {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
-    const dim3 grid((unsigned)((width + 15) / 16), (unsigned)((height + 15) / 16), 1);
+                {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval, order};
+    const dim3 grid = order ? dim3((unsigned)(list_grid.tiles_x * list_grid.tiles_y * lists), 1, 1)
+                            : dim3((unsigned)((width + 15) / 16), (unsigned)((height + 15) / 16), 1);
     if (wide_blocks) {
         if (lists == GS_LISTS_2X1) blend_listtile_kernel<2, 1, 16, 128><<<grid, 64, 0, s>>>(a);
         else if (lists == GS_LISTS_2X2) blend_listtile_kernel<2, 2, 16, 128><<<grid, 64, 0, s>>>(a);
@@ -1195,9 +1207,10 @@ cudaError_t gs_launch_blend_cluster(const RecordReader &rd, const uint32_t *valu
 
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
-                            const gs_framebuffer &fb, int variant, cudaStream_t s) {
+                            const gs_framebuffer &fb, int variant, cudaStream_t s, const uint32_t *order) {
+    // order: only the culled variants take it (block b blends tile order[b]).
     BlendArgs a{rd, values, ranges, grid, width, height,
-                {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval};
+                {bg[0], bg[1], bg[2]}, fb.rgb, fb.final_T, fb.n_contrib, fb.n_eval, order};
     // Caller-provided gs_records (the stage API) get the per-key constants
     // computed while staging; the render path's blend records carry them.
     if (rd.mode == kRecRaw) launch_blend_variant<true>(a, grid, variant, s);

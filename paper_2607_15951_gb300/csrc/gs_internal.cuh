@@ -525,9 +525,11 @@ cudaError_t gs_launch_sort_passes_rts(uint64_t *keys, uint32_t *values, uint64_t
                                       void *rts_scratch, uint32_t *d_err, bool *result_in_alt, cudaStream_t s,
                                       int first_pass = 0);
 
+// order (optional, the culled variants only): block b blends tile order[b]
+// (a longest-list-first order from gs_launch_tile_order).
 cudaError_t gs_launch_blend(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                             const GsGrid &grid, int width, int height, const float bg[3],
-                            const gs_framebuffer &fb, int variant, cudaStream_t s);
+                            const gs_framebuffer &fb, int variant, cudaStream_t s, const uint32_t *order = nullptr);
 // Thread-block-cluster blend: the lists belong to list tiles of cluster
 // screen tiles of 16 x 16 (cluster 2: 2 x 1, 4: 2 x 2; list_grid is their
 // grid); the blocks of a list tile form one cluster and share its batches
@@ -547,10 +549,12 @@ inline void list_tile_dims(int code, int *lx, int *ly) {
 
 // Blend of list tiles (lists: a list_tile_dims code above 1, 16 x 16 screen tiles)
 // without clusters: each screen tile's block reads its list tile's list
-// (wide_blocks: 16x8 warp blocks with two pixel pairs per lane, else 8x8).
+// (wide_blocks: 16x8 warp blocks with two pixel pairs per lane, else 8x8);
+// order (optional): the list tiles in the order their blocks start.
 cudaError_t gs_launch_blend_listtile(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                      const GsGrid &list_grid, int lists, int width, int height, const float bg[3],
-                                     const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s);
+                                     const gs_framebuffer &fb, bool wide_blocks, const uint32_t *order,
+                                     cudaStream_t s);
 cudaError_t gs_launch_blend_cluster(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                     const GsGrid &list_grid, int cluster, int width, int height, const float bg[3],
                                     const gs_framebuffer &fb, bool wide_blocks, cudaStream_t s);
@@ -672,6 +676,9 @@ cudaError_t gs_launch_blend_batch(const RecordReader &rd, const uint32_t *values
                                   const ViewDesc *views_dev, int n_views, int tile_w, int tile_h, int depth,
                                   const uint32_t *order, int32_t n_items, uint32_t *queue_head, int lists,
                                   cudaStream_t s);
+// Longest-list-first order of one frame's n_tiles (list) tiles into order
+// (n_tiles entries), from their ranges; one small kernel.
+cudaError_t gs_launch_tile_order(const uint32_t *ranges, int32_t n_tiles, uint32_t *order, cudaStream_t s);
 // Largest-first work queue of global tiles, subs items per tile (item t
 // names tile t / subs); qs: gs_queue_scratch_bytes(), the queue head the
 // blend takes items from is qs[193].

@@ -226,6 +226,30 @@ def test_gpu_gradient_matches_gpu_central_differences(ctx, seed, deg):
     assert checked >= 120, (checked, skipped)
 
 
+@pytest.mark.parametrize("form", [{}, {"tile": (16, 8)}, {"list_tiles": 4}, {"list_tiles": 64}],
+                         ids=["t16", "t16x8", "l2x2", "l8x8"])
+def test_backward_after_either_tile_order(ctx, form):
+    """A forward whose blend took its tiles longest list first leaves the
+    same frame to differentiate as a grid-order forward: the same gradients.
+    Float atomics add in a run-dependent order, so the comparison allows 1e-4
+    of the largest gradient (the run-to-run spread is ~1e-5)."""
+    scene, cam = scenes.clustered(50_000, 42, box=5.0), scenes.pinhole(320, 180)
+    g = gs.scene_to_device(scene)
+    d = torch.randn((180, 320, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    res = []
+    for order in (gs._native.GS_ORDER_LONGEST_FIRST, gs._native.GS_ORDER_GRID):
+        out = gs.render(ctx, g, scene.sh_degree, cam, tile_order=order, **form)
+        grads = {k: torch.empty_like(v) for k, v in g.items()}
+        bw = {k: v for k, v in form.items()}
+        gs.gs_render_backward(ctx, g, scene.sh_degree, cam, out["final_T"], out["n_contrib"], d, grads, **bw)
+        torch.cuda.synchronize()
+        res.append(grads)
+    for k in GROUPS:
+        a, b = res[0][k], res[1][k]
+        assert torch.isfinite(a).all(), k
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()) + 1e-12), k
+
+
 def test_autograd_function_matches_direct_call(ctx):
     scene, cam = scenes.uniform_box(1_000, 6), scenes.pinhole(96, 64)
     g = gs.scene_to_device(scene)

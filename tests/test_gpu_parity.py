@@ -407,6 +407,28 @@ def test_blend_variants_identical(ctx, name, make, tile):
             assert np.array_equal(outs[0][k], o[k]), k
 
 
+@pytest.mark.parametrize("name,make,tile", VARIANT_CASES, ids=[c[0] for c in VARIANT_CASES])
+def test_tile_order_does_not_change_the_image(ctx, name, make, tile):
+    """The blend blocks take the tiles longest list first (default) or in
+    grid order: every output is the same bit for bit, for each culled
+    schedule and, on 16x16 tiles, each list-tile form."""
+    scene, cam = make()
+    g = gs.scene_to_device(scene)
+    N_ = gs._native
+    forms = [dict(variant=v) for v in (N_.GS_BLEND_CULLED, N_.GS_BLEND_CULLED_WIDE, N_.GS_BLEND_CULLED_TILE,
+                                       N_.GS_BLEND_CULLED_8X8)]
+    if tile == (16, 16):
+        forms += [dict(list_tiles=c) for c in (N_.GS_LISTS_2X1, N_.GS_LISTS_2X2, N_.GS_LISTS_4X4, N_.GS_LISTS_8X8)]
+    for f in forms:
+        a = gs.render(ctx, g, scene.sh_degree, cam, tile=tile, tile_order=N_.GS_ORDER_LONGEST_FIRST, **f)
+        b = gs.render(ctx, g, scene.sh_degree, cam, tile=tile, tile_order=N_.GS_ORDER_GRID, **f)
+        torch.cuda.synchronize()
+        for k in ("rgb", "final_T", "n_contrib", "n_eval"):
+            assert torch.equal(a[k], b[k]), (f, k)
+    with pytest.raises(RuntimeError, match="tile_order"):
+        gs.render(ctx, g, scene.sh_degree, cam, tile=tile, tile_order=2)
+
+
 def test_render_regrows_key_buffers(oracle_mod):
     """A context whose key buffers are far too small still returns the exact
     frame: the overflow is detected and the frame rendered again."""
