@@ -161,8 +161,9 @@ typedef struct {
     int32_t record_dtype;   /* GS_RECORD_F32 (default), _F16 or _BF16          */
     int32_t blend_variant;  /* GS_BLEND_CULLED (default), _BASIC, _CULLED_WIDE,
                                _CULLED_TILE, _CULLED_8X8, _TMA                 */
-    int32_t direct_launch;  /* gs_render_batch: 0 = replay a captured CUDA graph
-                               (default), 1 = launch the kernels directly      */
+    int32_t direct_launch;  /* gs_render and gs_render_batch: 0 = replay a
+                               captured CUDA graph (default), 1 = launch the
+                               kernels directly, see gs_render               */
     int32_t sync_mode;      /* gs_render: GS_SYNC_FRAME (default) or
                                GS_SYNC_DEFERRED, see gs_render                 */
     int32_t temporal;       /* gs_render: temporal re-binning, see gs_render
@@ -352,7 +353,21 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
  *                     GS_ERR_CAPACITY without doing its own work: the buffers
  *                     have then grown and the caller renders again.
  *                     gs_render_backward waits for the frame it
- *                     differentiates and fails if that frame overflowed. */
+ *                     differentiates and fails if that frame overflowed.
+ * CUDA graph (opts->direct_launch = 0, default): the frame's launches (from
+ * the key sort's scratch reset to the blend) are captured once into a CUDA
+ * graph on a stream of the context's own, without running them, and
+ * replayed on `stream` by later frames with the same scene arrays (pointers,
+ * count, SH degree), image size, options (other than sync_mode),
+ * framebuffer pointers, key capacity and blend schedule while the context's
+ * buffers keep their addresses; each replay sets the frame's camera in the
+ * projection's launch, so the host issues one graph launch where it would
+ * issue about twenty calls. The context keeps eight such graphs (frames that
+ * alternate framebuffers or scenes replay too; re-binned frames of temporal
+ * mode have graphs of their own). Frames with stage timing on
+ * (gs_set_stage_timing), with GS_BLEND_TMA or with direct_launch = 1 launch
+ * the kernels directly, and so does a context after four captures in a row
+ * (for its next 32 frames). Results are the same either way. */
 /* Temporal re-binning (opts->temporal = 1 or 2; the paper's temporal-
  * locality idea, Sec. 5.4 and Sec. 6): when the previous frame on this
  * context was rendered the same way with the same Gaussian count and tile
@@ -364,8 +379,9 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
  * frame is binned from scratch instead when there is no such state, when
  * more than 8 % of the visible Gaussians moved in the previous frame, or
  * when a tile list exceeds 4096 entries. With temporal = 1 the context also
- * times the binning of both kinds of frames (CUDA events) and bins in full
- * while re-binned frames measured slower, and re-bins only after a full
+ * times both kinds of frames (CUDA events around the binning, or around the
+ * whole frame when it replays a CUDA graph) and bins in full while re-binned
+ * frames measured slower, and re-bins only after a full
  * frame measured the churn; once re-binning is ruled out (by
  * that measurement or by the churn) the next 6 frames are rendered without
  * tracking tile rects (n_moved = 0 on them), the two after them measure the

@@ -41,11 +41,23 @@ def _ptr(t) -> int | None:
     return int(t.data_ptr())
 
 
+_RAW_STREAM = None
+
+
 def _stream(stream) -> int | None:
+    """The cudaStream_t of a torch stream, or of the current one (read
+    through torch's raw-stream query where it exists: a stream object costs
+    several microseconds per call)."""
+    global _RAW_STREAM
+    if stream is not None:
+        return int(stream.cuda_stream)
     import torch
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    return int(stream.cuda_stream)
+    if _RAW_STREAM is None:
+        c = torch._C
+        _RAW_STREAM = ((lambda: c._cuda_getCurrentRawStream(c._cuda_getDevice()))
+                       if hasattr(c, "_cuda_getCurrentRawStream") and hasattr(c, "_cuda_getDevice")
+                       else (lambda: torch.cuda.current_stream().cuda_stream))
+    return int(_RAW_STREAM())
 
 
 def camera_struct(cam) -> N.gs_camera:
@@ -53,9 +65,7 @@ def camera_struct(cam) -> N.gs_camera:
     width, height, near_z (e.g. ``scenes.Camera``)."""
     import numpy as np
     c = N.gs_camera()
-    w2c = np.asarray(cam.world_to_cam, dtype=np.float32).reshape(12)
-    for i in range(12):
-        c.world_to_cam[i] = float(w2c[i])
+    c.world_to_cam[:] = np.asarray(cam.world_to_cam, dtype=np.float32).reshape(12).tolist()
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.width, c.height = int(cam.width), int(cam.height)
     c.near_z = float(getattr(cam, "near_z", 0.2))
@@ -65,8 +75,7 @@ def camera_struct(cam) -> N.gs_camera:
 def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
                    blend_variant: int = 0, deferred: bool = False, temporal: int = 0,
                    cluster: int = 0, list_tiles: int = 0, tile_order: int = 0) -> N.gs_options:
-    o = N.gs_options()
-    _lib().gs_default_options(ctypes.byref(o))
+    o = N.gs_options()  # zero-filled, as gs_default_options starts; every field it sets is set below
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
     for i in range(3):
         o.bg[i] = float(bg[i])
@@ -83,11 +92,12 @@ def options_struct(tile=(16, 16), bg=(0.0, 0.0, 0.0), record_dtype: int = 0,
 def gaussians_struct(g: dict, sh_degree: int) -> N.gs_gaussians:
     """gs_gaussians from a dict of contiguous float32 CUDA tensors with keys
     means, log_scales, quats, opacity_logits, sh."""
+    import torch
     s = N.gs_gaussians()
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
         t = g[k]
-        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32", k
-        setattr(s, k, _ptr(t))
+        assert t.is_cuda and t.dtype is torch.float32 and t.is_contiguous(), k
+        setattr(s, k, t.data_ptr())
     s.n = int(g["means"].shape[0])
     s.sh_degree = int(sh_degree)
     return s
@@ -208,7 +218,7 @@ def gs_blend(ctx: Context, records, values, ranges, cam, rgb, final_T=None, n_co
 def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_contrib=None,
               n_eval=None, *, tile=(16, 16), bg=(0.0, 0.0, 0.0), variant: int = 0,
               record_dtype: int = 0, deferred: bool = False, temporal: bool = False, cluster: int = 0,
-              list_tiles: int = 0, tile_order: int = 0, stream=None) -> None:
+              list_tiles: int = 0, tile_order: int = 0, direct: bool = False, stream=None) -> None:
     """deferred=True: GS_SYNC_DEFERRED (no host synchronisation; an overflow
     or device error is raised by a later call on the context).
     temporal=True (or 1): re-bin from the previous frame's lists when that
@@ -216,10 +226,13 @@ def gs_render(ctx: Context, g: dict, sh_degree: int, cam, rgb, final_T=None, n_c
     cluster: GS_CLUSTER_2X1 / _2X2 blend in thread-block clusters;
     list_tiles: GS_LISTS_2X1 / _2X2 / _4X4 / _8X8 lists of list tiles, read
     by every screen tile's block (no cluster);
-    tile_order: GS_ORDER_LONGEST_FIRST (0) or GS_ORDER_GRID (1) blend blocks."""
+    tile_order: GS_ORDER_LONGEST_FIRST (0) or GS_ORDER_GRID (1) blend blocks;
+    direct=True: launch the kernels directly instead of replaying the
+    context's CUDA graph of the frame."""
     gs = gaussians_struct(g, sh_degree)
     c, o = camera_struct(cam), options_struct(tile, bg, record_dtype, variant, deferred, temporal, cluster,
                                               list_tiles, tile_order)
+    o.direct_launch = 1 if direct else 0
     fb = _fb(rgb, final_T, n_contrib, n_eval)
     ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs), ctypes.byref(c), ctypes.byref(o),
                                ctypes.byref(fb), _stream(stream)))
@@ -292,7 +305,7 @@ def scene_to_device(scene, device="cuda") -> dict:
 def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0, 0.0, 0.0),
            aux: bool = True, variant: int = 0, record_dtype: int = 0, deferred: bool = False,
            temporal: bool = False, cluster: int = 0, list_tiles: int = 0, tile_order: int = 0,
-           stream=None) -> dict:
+           direct: bool = False, stream=None) -> dict:
     """Allocate outputs with torch and call gs_render."""
     import torch
     H, W = int(cam.height), int(cam.width)
@@ -305,7 +318,7 @@ def render(ctx: Context, g: dict, sh_degree: int, cam, *, tile=(16, 16), bg=(0.0
     gs_render(ctx, g, sh_degree, cam, out["rgb"], out.get("final_T"), out.get("n_contrib"),
               out.get("n_eval"), tile=tile, bg=bg, variant=variant, record_dtype=record_dtype,
               deferred=deferred, temporal=temporal, cluster=cluster, list_tiles=list_tiles,
-              tile_order=tile_order, stream=stream)
+              tile_order=tile_order, direct=direct, stream=stream)
     return out
 
 
@@ -334,10 +347,13 @@ def _autograd_function():
                        gs_last_frame_id(ctx))
             fctx.save_for_backward(out["final_T"], out["n_contrib"])
             fctx.mark_non_differentiable(out["final_T"])
+            fctx.set_materialize_grads(False)  # no zero tensor for the non-differentiable final_T
             return out["rgb"], out["final_T"]
 
         @staticmethod
         def backward(fctx, d_rgb, d_T):
+            if d_rgb is None:
+                return (None,) * 14
             ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, list_tiles, frame = fctx.gs
             final_T, n_contrib = fctx.saved_tensors
             if gs_last_frame_id(ctx) != frame:

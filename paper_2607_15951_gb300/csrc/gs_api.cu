@@ -44,6 +44,35 @@ struct gs_context {
     DevBuf br_geo, br_aux, br_col;  // blend records of the render path (16 B per slot each)
     DevBuf br_rect;                 // their 16 x 16 tile rects, for list-tile frames (8 B per slot)
     DevBuf tile_order;              // the blend's longest-list-first tile order (4 B per list tile)
+    // gs_render's captured frames: the launches of one frame as a CUDA
+    // graph, replayed (with the frame's camera set in the projection's
+    // launch) while the scene arrays, image size, options, framebuffer, key
+    // capacity, blend schedule and the context's buffers stay the same; a few
+    // are kept (least recently used replaced), so frames that alternate
+    // framebuffers or scenes still replay. buf_gen counts the reallocations
+    // of the context's buffers. After kGraphMissRun captures in a row the
+    // next kGraphSkip frames launch directly.
+    uint64_t buf_gen = 0;
+    static constexpr int kGraphs = 8, kGraphMissRun = 4, kGraphSkip = 32;
+    struct FrameGraph {
+        bool valid = false;
+        uint64_t last_use = 0;
+        int kind = 0;                 // 0: a full binning, 1: a re-binned frame
+        const void *extra[8] = {};    // further addresses the launches take (temporal state)
+        gs_gaussians g{};
+        gs_options o{};
+        gs_framebuffer fb{};
+        int w = 0, h = 0, variant = 0;
+        int64_t cap = 0;
+        uint64_t buf_gen = 0;
+        uint32_t *sv = nullptr;  // where the frame's sorted lists end up
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t project = nullptr;
+    } fg[kGraphs];
+    uint64_t graph_clock = 0;
+    int graph_miss_run = 0, graph_skip = 0;
+    cudaStream_t capture_stream = nullptr;
     // Batched path (own buffers: a captured graph holds their addresses).
     struct Batch {
         DevBuf views, rec, meta, geo, aux, col, scratch, ranges, order, queue, keys, vals, akeys, avals, sort, rts;
@@ -135,6 +164,7 @@ gs_status cuda_fail(gs_context *ctx, cudaError_t e, const char *where) {
 
 gs_status ensure(gs_context *ctx, DevBuf &b, size_t bytes, const char *what) {
     if (bytes <= b.bytes) return GS_OK;
+    ++ctx->buf_gen;
     size_t want = bytes + bytes / 4 + 256;
     if (b.ptr) {
         cudaError_t e = cudaFree(b.ptr);
@@ -414,8 +444,9 @@ void drop_temporal(gs_context *ctx) {
 }
 
 // Temporal mode's binning time: events around projection .. ranges.
+// (Not inside a capture: a graph's frames are timed around its launch.)
 void temporal_mark(gs_context *ctx, int k, cudaStream_t s) {
-    if (ctx->temporal.ev[k]) cudaEventRecord(ctx->temporal.ev[k], s);
+    if (ctx->temporal.ev[k] && s != ctx->capture_stream) cudaEventRecord(ctx->temporal.ev[k], s);
 }
 
 // After a synchronised temporal frame: folds its binning time into the
@@ -609,6 +640,111 @@ gs_status launch_blend(gs_context *ctx, const RecordReader &rd, const uint32_t *
     return GS_OK;
 }
 
+void drop_frame_graph(gs_context::FrameGraph &F) {
+    if (F.exec) cudaGraphExecDestroy(F.exec);
+    if (F.graph) cudaGraphDestroy(F.graph);
+    F = gs_context::FrameGraph{};
+}
+
+// Does the captured frame F serve (g, cam, opts, fb) with this key capacity,
+// blend schedule and the context's current buffers? (The camera pose and
+// intrinsics are set per replay; the sync mode acts after the graph.)
+bool frame_graph_fits(const gs_context *ctx, const gs_context::FrameGraph &F, int kind, const void *const extra[8],
+                      const gs_gaussians *g, const gs_camera *cam, const gs_options *opts, const gs_framebuffer *fb,
+                      int64_t cap, int variant) {
+    if (!F.valid || F.kind != kind) return false;
+    for (int i = 0; i < 8; ++i)
+        if (F.extra[i] != extra[i]) return false;
+    gs_options a = F.o, b = *opts;  // 4-byte fields only: no padding
+    a.sync_mode = b.sync_mode = 0;
+    return F.g.means == g->means && F.g.log_scales == g->log_scales && F.g.quats == g->quats &&
+           F.g.opacity_logits == g->opacity_logits && F.g.sh == g->sh && F.g.n == g->n &&
+           F.g.sh_degree == g->sh_degree && F.w == cam->width && F.h == cam->height &&
+           std::memcmp(&a, &b, sizeof a) == 0 && F.fb.rgb == fb->rgb && F.fb.final_T == fb->final_T &&
+           F.fb.n_contrib == fb->n_contrib && F.fb.n_eval == fb->n_eval && F.cap == cap && F.variant == variant &&
+           F.buf_gen == ctx->buf_gen;
+}
+
+// Enqueues a gs_render frame on s through one of the context's CUDA graphs:
+// a graph that fits the frame is launched with the frame's camera set in the
+// projection's launch; otherwise the least recently used slot captures the
+// frame's launches (on the context's own stream, so nothing runs) first. A
+// context whose frames keep missing (kGraphMissRun captures in a row)
+// launches the next kGraphSkip frames directly. enqueue(q) issues the frame's
+// launches on q and sets *sv.
+template <class Enqueue>
+gs_status replay_frame(gs_context *ctx, int kind, const void *const extra[8], const gs_gaussians *g,
+                       const gs_camera *cam, const gs_options *opts, const gs_framebuffer *fb, int64_t cap,
+                       int variant, const GsCameraDev &dcam, cudaStream_t s, Enqueue &enqueue, uint32_t **sv) {
+    if (ctx->graph_skip > 0) {
+        --ctx->graph_skip;
+        return enqueue(s);
+    }
+    gs_context::FrameGraph *F = nullptr, *lru = &ctx->fg[0];
+    for (auto &c : ctx->fg) {
+        if (frame_graph_fits(ctx, c, kind, extra, g, cam, opts, fb, cap, variant)) F = &c;
+        if (!c.valid || (lru->valid && c.last_use < lru->last_use)) lru = &c;
+    }
+    if (F) {
+        ctx->graph_miss_run = 0;
+    } else {
+        if (++ctx->graph_miss_run >= gs_context::kGraphMissRun) {
+            ctx->graph_miss_run = 0;
+            ctx->graph_skip = gs_context::kGraphSkip;
+            return enqueue(s);
+        }
+        F = lru;
+        drop_frame_graph(*F);
+        if (!ctx->capture_stream)
+            GS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        GS_CUDA(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        const gs_status st = enqueue(ctx->capture_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (st != GS_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            (void)cudaGetLastError();
+            return st != GS_OK ? st : cuda_fail(ctx, e, "cudaStreamEndCapture");
+        }
+        size_t count = 0;
+        cudaError_t e2 = cudaGraphGetNodes(graph, nullptr, &count);
+        std::vector<cudaGraphNode_t> nodes(count);
+        if (e2 == cudaSuccess && count > 0) e2 = cudaGraphGetNodes(graph, nodes.data(), &count);
+        cudaGraphNode_t project = nullptr;
+        int found = 0;
+        for (size_t i = 0; e2 == cudaSuccess && i < count; ++i)
+            if (gs_is_camera_node(nodes[i])) project = nodes[i], ++found;
+        cudaGraphExec_t exec = nullptr;
+        if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&exec, graph, 0);
+        if (e2 != cudaSuccess || found != (g->n > 0 ? 1 : 0)) {
+            if (exec) cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            return e2 != cudaSuccess ? cuda_fail(ctx, e2, "CUDA graph of the frame")
+                                     : fail(ctx, GS_ERR_CUDA, "CUDA graph of the frame: projection launch not found");
+        }
+        F->valid = true;
+        F->kind = kind;
+        for (int i = 0; i < 8; ++i) F->extra[i] = extra[i];
+        F->g = *g;
+        F->o = *opts;
+        F->fb = *fb;
+        F->w = cam->width;
+        F->h = cam->height;
+        F->variant = variant;
+        F->cap = cap;
+        F->buf_gen = ctx->buf_gen;
+        F->sv = *sv;
+        F->graph = graph;
+        F->exec = exec;
+        F->project = project;
+    }
+    F->last_use = ++ctx->graph_clock;
+    if (F->project) GS_CUDA(ctx, gs_set_node_camera(F->exec, F->project, dcam));
+    GS_CUDA(ctx, cudaGraphLaunch(F->exec, s));
+    *sv = F->sv;
+    return GS_OK;
+}
+
 // Above this fraction of moved Gaussians (of the visible ones) in the last
 // frame, the next frame is binned from scratch: re-binning pays off only
 // while few tiles change (measured break-even near 10 % on a 1M-Gaussian
@@ -657,58 +793,75 @@ gs_status render_rebinned(gs_context *ctx, const gs_gaussians *g, const gs_camer
     uint32_t *ins_first = reinterpret_cast<uint32_t *>(ts + zero_bytes);
     // counters: [0] visible << 33 | keys, [1] moved Gaussians, [2] their work items,
     // [3] entries, [4] arrivals, [5] the scan's partition counter
-    GS_CUDA(ctx, cudaMemsetAsync(ts, 0, zero_bytes, s));
     gs_record *rec = static_cast<gs_record *>(ctx->records.ptr);
     uint32_t *vals = static_cast<uint32_t *>(T.vals[out].ptr);
     uint32_t *ranges = static_cast<uint32_t *>(T.ranges[out].ptr);
-    mark(ctx, EV_START, s);
     const uint2 *prev_rect = static_cast<const uint2 *>(T.rects[T.rcur].ptr);
     uint2 *rect = static_cast<uint2 *>(T.rects[T.rcur ^ 1].ptr);
-    temporal_mark(ctx, 0, s);
-    GS_CUDA(ctx, gs_launch_project_temporal(*g, make_cam(cam), grid, rec, blend_out(ctx, dtype), prev_rect, rect,
-                                            static_cast<uint8_t *>(T.moved.ptr),
-                                            static_cast<unsigned long long *>(T.moved_list.ptr), item_cap,
-                                            counters, ctx->d_err, s));
-    mark(ctx, EV_PROJECT, s);
-    mark(ctx, EV_DEPTH, s);
-    mark(ctx, EV_SCAN, s);
-    mark(ctx, EV_EMIT, s);
-    GsTemporalRebin R;
-    R.records = reinterpret_cast<const float4 *>(rec);
-    R.prev_vals = T.prev_vals;
-    R.prev_ranges = T.prev_ranges;
-    R.moved = static_cast<const uint8_t *>(T.moved.ptr);
-    R.removed = removed;
-    R.added = added;
-    R.items = static_cast<const unsigned long long *>(T.moved_list.ptr);
-    R.n_items = counters + 2;
-    R.item_capacity = item_cap;
-    R.prev_rect = prev_rect;
-    R.rect = rect;
-    R.n_tiles = n_tiles;
-    R.tiles_x = grid.tiles_x;
-    R.n_gaussians = n;
-    R.ranges = ranges;
-    R.vals = vals;
-    R.capacity = cap;
-    R.ins_first = ins_first;
-    R.ins_cursor = ins_cursor;
-    R.ins_vals = static_cast<uint32_t *>(T.ins_vals.ptr);
-    R.ins_capacity = cap;
-    R.totals = counters + 3;
-    R.scan_counter = reinterpret_cast<uint32_t *>(counters + 5);
-    R.scan_status = status;
-    R.cap_entries = kTemporalTileCap;
-    R.d_err = ctx->d_err;
-    GS_CUDA(ctx, gs_launch_temporal_rebin(R, s));
-    temporal_mark(ctx, 1, s);
-    mark(ctx, EV_SORT, s);
-    const uint32_t *order = nullptr;
-    if ((st = launch_tile_order(ctx, ranges, grid, opts, s, &order)) != GS_OK) return st;
-    mark(ctx, EV_RANGES, s);
-    if ((st = launch_blend(ctx, reader(ctx, rec, dtype), vals, ranges, grid, cam, opts, fb, counters + 3, cap, order,
-                           s)) != GS_OK)
+    const GsCameraDev dcam = make_cam(cam);
+    // The frame's launches on stream q (enqueued directly or captured into
+    // the context's CUDA graph of re-binned frames, as in gs_render).
+    auto enqueue = [&](cudaStream_t q) -> gs_status {
+        GS_CUDA(ctx, cudaMemsetAsync(ts, 0, zero_bytes, q));
+        mark(ctx, EV_START, q);
+        temporal_mark(ctx, 0, q);
+        GS_CUDA(ctx, gs_launch_project_temporal(*g, dcam, grid, rec, blend_out(ctx, dtype), prev_rect, rect,
+                                                static_cast<uint8_t *>(T.moved.ptr),
+                                                static_cast<unsigned long long *>(T.moved_list.ptr), item_cap,
+                                                counters, ctx->d_err, q));
+        mark(ctx, EV_PROJECT, q);
+        mark(ctx, EV_DEPTH, q);
+        mark(ctx, EV_SCAN, q);
+        mark(ctx, EV_EMIT, q);
+        GsTemporalRebin R;
+        R.records = reinterpret_cast<const float4 *>(rec);
+        R.prev_vals = T.prev_vals;
+        R.prev_ranges = T.prev_ranges;
+        R.moved = static_cast<const uint8_t *>(T.moved.ptr);
+        R.removed = removed;
+        R.added = added;
+        R.items = static_cast<const unsigned long long *>(T.moved_list.ptr);
+        R.n_items = counters + 2;
+        R.item_capacity = item_cap;
+        R.prev_rect = prev_rect;
+        R.rect = rect;
+        R.n_tiles = n_tiles;
+        R.tiles_x = grid.tiles_x;
+        R.n_gaussians = n;
+        R.ranges = ranges;
+        R.vals = vals;
+        R.capacity = cap;
+        R.ins_first = ins_first;
+        R.ins_cursor = ins_cursor;
+        R.ins_vals = static_cast<uint32_t *>(T.ins_vals.ptr);
+        R.ins_capacity = cap;
+        R.totals = counters + 3;
+        R.scan_counter = reinterpret_cast<uint32_t *>(counters + 5);
+        R.scan_status = status;
+        R.cap_entries = kTemporalTileCap;
+        R.d_err = ctx->d_err;
+        GS_CUDA(ctx, gs_launch_temporal_rebin(R, q));
+        temporal_mark(ctx, 1, q);
+        mark(ctx, EV_SORT, q);
+        const uint32_t *order = nullptr;
+        gs_status st2;
+        if ((st2 = launch_tile_order(ctx, ranges, grid, opts, q, &order)) != GS_OK) return st2;
+        mark(ctx, EV_RANGES, q);
+        return launch_blend(ctx, reader(ctx, rec, dtype), vals, ranges, grid, cam, opts, fb, counters + 3, cap, order,
+                            q);
+    };
+    const int variant = blend_schedule(ctx, opts, n_tiles);
+    if (!ctx->timing && opts->direct_launch == 0 && variant != GS_BLEND_TMA) {
+        const void *extra[8] = {T.prev_vals, T.prev_ranges, prev_rect, rect, vals, ranges,
+                                reinterpret_cast<const void *>(static_cast<uintptr_t>(item_cap))};
+        uint32_t *sv = vals;
+        temporal_mark(ctx, 0, s);
+        if ((st = replay_frame(ctx, 1, extra, g, cam, opts, fb, cap, variant, dcam, s, enqueue, &sv)) != GS_OK)
+            return st;
+        temporal_mark(ctx, 1, s);
+    } else if ((st = enqueue(s)) != GS_OK) {
         return st;
+    }
     mark(ctx, EV_BLEND, s);
     unsigned long long *h = ctx->h_ring;  // no deferred frame is in flight (drained before)
     h[5] = 0;
@@ -792,6 +945,8 @@ gs_status gs_create(gs_context **out, int device) {
 void gs_destroy(gs_context *ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
+    for (auto &F : ctx->fg) drop_frame_graph(F);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     DevBuf *bufs[] = {&ctx->records, &ctx->tiles, &ctx->offsets, &ctx->scan_scratch, &ctx->keys,
                       &ctx->values, &ctx->alt_keys, &ctx->alt_values, &ctx->sort_scratch, &ctx->ranges,
                       &ctx->fused_scratch, &ctx->d_rec, &ctx->br_geo, &ctx->br_aux, &ctx->br_col, &ctx->gathered,
@@ -971,7 +1126,8 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
          (st = ensure(ctx, ctx->br_rect, (size_t)(n > 0 ? n : 1) * 8, "blend record rects")) != GS_OK))
         return st;
     if ((st = ensure(ctx, ctx->records, (size_t)(n > 0 ? n : 1) * sizeof(gs_record), "records")) != GS_OK ||
-        (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK)
+        (st = ensure(ctx, ctx->ranges, (size_t)n_tiles * 8, "ranges")) != GS_OK ||
+        (st = ensure(ctx, ctx->tile_order, (size_t)n_tiles * 4 + 4, "tile order")) != GS_OK)
         return st;
     const bool deferred = opts->sync_mode == GS_SYNC_DEFERRED;
     // Earlier deferred frames: all of them before a synchronised frame, the
@@ -1053,67 +1209,88 @@ gs_status gs_render(gs_context *ctx, const gs_gaussians *g, const gs_camera *cam
         void *keys = ctx->keys.ptr, *akeys = ctx->alt_keys.ptr;
         uint32_t *vals = static_cast<uint32_t *>(ctx->values.ptr);
         uint32_t *avals = static_cast<uint32_t *>(ctx->alt_values.ptr);
-        // The tile sort: keys are tile ids emitted in (depth, index) order,
-        // so the stable sort on them alone gives each tile's list in order.
-        // Its digit histograms are counted from the tile rects during the
-        // projection, and its first pass is fused with the emission (whose
-        // output lands in the alternate buffers); at least one pass runs.
-        GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes_digits(status_cap, sort_passes),
-                                     s));
-        GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, status_cap, 0, sort_passes);
-        // The row digit takes many values within a warp; so does the high
-        // byte of tile ids once the low byte is sorted.
-        sc.diverse_last = xy_keys || rts;
-        mark(ctx, EV_START, s);
-        if (track) temporal_mark(ctx, 0, s);
-        cudaEvent_t ev3[3] = {nullptr, nullptr, nullptr};
-        if (ctx->timing) {
-            ev3[0] = ctx->ev[EV_PROJECT];
-            ev3[1] = ctx->ev[EV_DEPTH];
-            ev3[2] = ctx->ev[EV_SCAN];
-        }
-        GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, blend_out(ctx, dtype, opts->list_tiles > 1 ? cam : nullptr),
-                                           xy_keys ? akeys : keys, key_bytes, xy_keys, xy_keys ? avals : vals,
-                                           cap, ctx->d_counts,
-                                           ctx->fused_scratch.ptr, sc, ctx->d_err, s, ev3, prect, prev_rect,
-                                           ctx->d_counts + 4));
-        mark(ctx, EV_EMIT, s);
-        // The remaining passes, from the emission's output (the alternate
-        // buffers after the fused first pass, else keys / vals).
-        void *in_k = xy_keys ? akeys : keys, *out_k = xy_keys ? keys : akeys;
-        uint32_t *in_v = xy_keys ? avals : vals, *out_v = xy_keys ? vals : avals;
-        const int first_pass = xy_keys ? 1 : 0;
-        bool moved = false;
-        if (rts && key_bytes == 2)
-            GS_CUDA(ctx, gs_launch_sort_passes_rts(static_cast<uint16_t *>(in_k), in_v, static_cast<uint16_t *>(out_k),
-                                                   out_v, cap, ctx->d_counts + 2, sc, ctx->rts_scratch.ptr,
-                                                   ctx->d_err, &moved, s, first_pass));
-        else if (rts)
-            GS_CUDA(ctx, gs_launch_sort_passes_rts(static_cast<uint32_t *>(in_k), in_v, static_cast<uint32_t *>(out_k),
-                                                   out_v, cap, ctx->d_counts + 2, sc, ctx->rts_scratch.ptr,
-                                                   ctx->d_err, &moved, s, first_pass));
-        else if (key_bytes == 2)
-            GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint16_t *>(in_k), in_v, static_cast<uint16_t *>(out_k),
-                                               out_v, cap, ctx->d_counts + 2, sc, ctx->d_err, &moved, s,
-                                               gs::kSpinTimeoutNs, 64, first_pass));
-        else
-            GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint32_t *>(in_k), in_v, static_cast<uint32_t *>(out_k),
-                                               out_v, cap, ctx->d_counts + 2, sc, ctx->d_err, &moved, s,
-                                               gs::kSpinTimeoutNs, 64, first_pass));
-        mark(ctx, EV_SORT, s);
-        const void *sk = moved ? out_k : in_k;
-        uint32_t *sv = moved ? out_v : in_v;
-        GS_CUDA(ctx, gs_launch_ranges_tiles(sk, key_bytes, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, s,
-                                            xy_keys ? grid.tiles_x : 0));
-        // (The temporal binning time ends with the ranges, as that of a
-        // re-binned frame does.)
-        if (track) temporal_mark(ctx, 1, s);
-        const uint32_t *order = nullptr;
-        if ((st = launch_tile_order(ctx, ranges, grid, opts, s, &order)) != GS_OK) return st;
-        mark(ctx, EV_RANGES, s);
-        if ((st = launch_blend(ctx, reader(ctx, rec, dtype), sv, ranges, grid, cam, opts, fb, ctx->d_counts + 2,
-                               cap, order, s)) != GS_OK)
+        // The frame's launches, from the tile sort's scratch reset to the
+        // blend, on stream q: enqueued directly, or captured once into a CUDA
+        // graph that later frames replay with their own camera.
+        uint32_t *sv = nullptr;
+        auto enqueue = [&](cudaStream_t q) -> gs_status {
+            // The tile sort: keys are tile ids emitted in (depth, index)
+            // order, so the stable sort on them alone gives each tile's list
+            // in order. Its digit histograms are counted from the tile rects
+            // during the projection, and its first pass is fused with the
+            // emission (whose output lands in the alternate buffers); at
+            // least one pass runs.
+            GS_CUDA(ctx, cudaMemsetAsync(ctx->sort_scratch.ptr, 0, gs_sort_scratch_bytes_digits(status_cap, sort_passes),
+                                         q));
+            GsSortScratch sc = gs_sort_carve_digits(ctx->sort_scratch.ptr, status_cap, 0, sort_passes);
+            // The row digit takes many values within a warp; so does the high
+            // byte of tile ids once the low byte is sorted.
+            sc.diverse_last = xy_keys || rts;
+            mark(ctx, EV_START, q);
+            if (track) temporal_mark(ctx, 0, q);
+            cudaEvent_t ev3[3] = {nullptr, nullptr, nullptr};
+            if (ctx->timing) {
+                ev3[0] = ctx->ev[EV_PROJECT];
+                ev3[1] = ctx->ev[EV_DEPTH];
+                ev3[2] = ctx->ev[EV_SCAN];
+            }
+            GS_CUDA(ctx, gs_launch_project_bin(*g, dcam, grid, rec, blend_out(ctx, dtype, opts->list_tiles > 1 ? cam : nullptr),
+                                               xy_keys ? akeys : keys, key_bytes, xy_keys, xy_keys ? avals : vals,
+                                               cap, ctx->d_counts,
+                                               ctx->fused_scratch.ptr, sc, ctx->d_err, q, ev3, prect, prev_rect,
+                                               ctx->d_counts + 4));
+            mark(ctx, EV_EMIT, q);
+            // The remaining passes, from the emission's output (the alternate
+            // buffers after the fused first pass, else keys / vals).
+            void *in_k = xy_keys ? akeys : keys, *out_k = xy_keys ? keys : akeys;
+            uint32_t *in_v = xy_keys ? avals : vals, *out_v = xy_keys ? vals : avals;
+            const int first_pass = xy_keys ? 1 : 0;
+            bool moved = false;
+            if (rts && key_bytes == 2)
+                GS_CUDA(ctx, gs_launch_sort_passes_rts(static_cast<uint16_t *>(in_k), in_v, static_cast<uint16_t *>(out_k),
+                                                       out_v, cap, ctx->d_counts + 2, sc, ctx->rts_scratch.ptr,
+                                                       ctx->d_err, &moved, q, first_pass));
+            else if (rts)
+                GS_CUDA(ctx, gs_launch_sort_passes_rts(static_cast<uint32_t *>(in_k), in_v, static_cast<uint32_t *>(out_k),
+                                                       out_v, cap, ctx->d_counts + 2, sc, ctx->rts_scratch.ptr,
+                                                       ctx->d_err, &moved, q, first_pass));
+            else if (key_bytes == 2)
+                GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint16_t *>(in_k), in_v, static_cast<uint16_t *>(out_k),
+                                                   out_v, cap, ctx->d_counts + 2, sc, ctx->d_err, &moved, q,
+                                                   gs::kSpinTimeoutNs, 64, first_pass));
+            else
+                GS_CUDA(ctx, gs_launch_sort_passes(static_cast<uint32_t *>(in_k), in_v, static_cast<uint32_t *>(out_k),
+                                                   out_v, cap, ctx->d_counts + 2, sc, ctx->d_err, &moved, q,
+                                                   gs::kSpinTimeoutNs, 64, first_pass));
+            mark(ctx, EV_SORT, q);
+            const void *sk = moved ? out_k : in_k;
+            sv = moved ? out_v : in_v;
+            GS_CUDA(ctx, gs_launch_ranges_tiles(sk, key_bytes, cap, ctx->d_counts + 2, n_tiles, ranges, ctx->d_err, q,
+                                                xy_keys ? grid.tiles_x : 0));
+            // (The temporal binning time ends with the ranges, as that of a
+            // re-binned frame does.)
+            if (track) temporal_mark(ctx, 1, q);
+            const uint32_t *order = nullptr;
+            gs_status st;
+            if ((st = launch_tile_order(ctx, ranges, grid, opts, q, &order)) != GS_OK) return st;
+            mark(ctx, EV_RANGES, q);
+            if ((st = launch_blend(ctx, reader(ctx, rec, dtype), sv, ranges, grid, cam, opts, fb, ctx->d_counts + 2,
+                                   cap, order, q)) != GS_OK)
+                return st;
+            return GS_OK;
+        };
+        const int variant = blend_schedule(ctx, opts, n_tiles);
+        if (!ctx->timing && opts->direct_launch == 0 && variant != GS_BLEND_TMA) {
+            // With tile rects tracked, the temporal gate times the whole
+            // graph (binning and blend) of both kinds of frames.
+            const void *extra[8] = {prect, prev_rect};
+            if (track) temporal_mark(ctx, 0, s);
+            if ((st = replay_frame(ctx, 0, extra, g, cam, opts, fb, cap, variant, dcam, s, enqueue, &sv)) != GS_OK)
+                return st;
+            if (track) temporal_mark(ctx, 1, s);
+        } else if ((st = enqueue(s)) != GS_OK) {
             return st;
+        }
         mark(ctx, EV_BLEND, s);
         if (deferred) {
             const int slot = (ctx->ring_head + ctx->ring_count) % gs_context::kRing;
@@ -1224,7 +1401,7 @@ gs_status gs_render_backward(gs_context *ctx, const gs_gaussians *g, const gs_ca
                      "record gradients")) != GS_OK)
         return st;
     float *d_rec = static_cast<float *>(ctx->d_rec.ptr);
-    GS_CUDA(ctx, cudaMemsetAsync(d_rec, 0, (size_t)n * kRecGradStride * sizeof(float), s));
+    GS_CUDA(ctx, gs_launch_zero_grads(*g, *out, d_rec, (size_t)n * kRecGradStride, s));
     GS_CUDA(ctx, gs_launch_blend_bwd(reader(ctx, static_cast<gs_record *>(ctx->records.ptr), ctx->last_dtype),
                                      ctx->last_values, ctx->last_ranges, grid, cam->width, cam->height,
                                      opts->bg, d_rgb, fb->final_T, fb->n_contrib, d_rec, s, ctx->last_cluster));

@@ -604,6 +604,12 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
                                   const uint2 *prev_rect = nullptr /* previous frame's: */,
                                   unsigned long long *moved = nullptr /* count of rects that differ */);
 
+// CUDA graphs of gs_render frames: is `node` (of a captured graph) the
+// projection's launch (gs_launch_project_bin or gs_launch_project_temporal),
+// and set the camera that launch takes in an instantiated graph (the rest of
+// its arguments stays as captured).
+bool gs_is_camera_node(cudaGraphNode_t node);
+cudaError_t gs_set_node_camera(cudaGraphExec_t exec, cudaGraphNode_t node, const GsCameraDev &cam);
 // Temporal re-binning (gs_temporal.cu). Projection step: records as
 // gs_launch_project_bin, plus per Gaussian its packed tile rect (`rect`),
 // compared with the previous frame's (`prev_rect`): `moved` flags, work
@@ -640,7 +646,12 @@ size_t gs_temporal_merge_smem(int cap_entries);
 size_t gs_temporal_scan_status_bytes(int32_t n_tiles);
 cudaError_t gs_launch_temporal_rebin(const GsTemporalRebin &r, cudaStream_t s);
 
-// Backward kernels.
+// Backward kernels. gs_launch_zero_grads zeroes the five gradient arrays of
+// g's Gaussians and the rec_words floats of d_rec in one launch (before the
+// blend backward adds into d_rec and the projection backward writes the
+// gradients of the Gaussians that received any).
+cudaError_t gs_launch_zero_grads(const gs_gaussians &g, const gs_grads &out, float *d_rec, size_t rec_words,
+                                 cudaStream_t s);
 cudaError_t gs_launch_blend_bwd(const RecordReader &rd, const uint32_t *values, const uint32_t *ranges,
                                 const GsGrid &grid, int width, int height, const float bg[3],
                                 const float *d_rgb, const float *final_T, const int32_t *n_contrib,

@@ -1506,6 +1506,54 @@ cudaError_t gs_launch_project_bin(const gs_gaussians &g, const GsCameraDev &cam,
     return launch_list_stages(L, base, g.n, blocks, A.dsc, E, key_bytes, false, xy_keys, counts, d_err, s, marks);
 }
 
+namespace {
+// 1: a launch of project_list_kernel, 2: of project_temporal_kernel, else 0.
+int camera_node_kind(const cudaKernelNodeParams &p) {
+    if (p.func == reinterpret_cast<void *>(project_list_kernel<0>) ||
+        p.func == reinterpret_cast<void *>(project_list_kernel<1>) ||
+        p.func == reinterpret_cast<void *>(project_list_kernel<2>) ||
+        p.func == reinterpret_cast<void *>(project_list_kernel<3>))
+        return 1;
+    if (p.func == reinterpret_cast<void *>(project_temporal_kernel<0>) ||
+        p.func == reinterpret_cast<void *>(project_temporal_kernel<1>) ||
+        p.func == reinterpret_cast<void *>(project_temporal_kernel<2>) ||
+        p.func == reinterpret_cast<void *>(project_temporal_kernel<3>))
+        return 2;
+    return 0;
+}
+}  // namespace
+
+bool gs_is_camera_node(cudaGraphNode_t node) {
+    cudaGraphNodeType type;
+    if (cudaGraphNodeGetType(node, &type) != cudaSuccess || type != cudaGraphNodeTypeKernel) return false;
+    cudaKernelNodeParams p{};
+    if (cudaGraphKernelNodeGetParams(node, &p) != cudaSuccess) return false;
+    return camera_node_kind(p) != 0;
+}
+
+cudaError_t gs_set_node_camera(cudaGraphExec_t exec, cudaGraphNode_t node, const GsCameraDev &cam) {
+    cudaKernelNodeParams p{};
+    cudaError_t e = cudaGraphKernelNodeGetParams(node, &p);
+    if (e != cudaSuccess) return e;
+    p.extra = nullptr;
+    const int kind = camera_node_kind(p);
+    if (kind == 1) {
+        ListArgs A = *static_cast<const ListArgs *>(p.kernelParams[0]);
+        A.P.cam = cam;
+        void *args[1] = {&A};
+        p.kernelParams = args;
+        return cudaGraphExecKernelNodeSetParams(exec, node, &p);
+    }
+    if (kind == 2) {
+        TemporalProjectArgs A = *static_cast<const TemporalProjectArgs *>(p.kernelParams[0]);
+        A.P.cam = cam;
+        void *args[1] = {&A};
+        p.kernelParams = args;
+        return cudaGraphExecKernelNodeSetParams(exec, node, &p);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t gs_launch_project_temporal(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                        gs_record *records, const gs::BlendRecordOut &br, const uint2 *prev_rect, uint2 *rect, uint8_t *moved,
                                        unsigned long long *items, int64_t item_capacity,
@@ -1826,6 +1874,44 @@ __global__ void __launch_bounds__(128) project_bwd_sparse_kernel(const ProjectBw
 }
 }  // namespace
 
+namespace {
+// Zeros of several float arrays in one launch: blockIdx.y picks the array,
+// blocks stride over its 16-byte chunks (the 4-byte words before the first
+// and after the last whole chunk are written one by one).
+struct ZeroSpans {
+    float *ptr[6];
+    size_t words[6];
+};
+
+__global__ void __launch_bounds__(256) zero_spans_kernel(const ZeroSpans z) {
+    float *p = z.ptr[blockIdx.y];
+    const size_t n = z.words[blockIdx.y];
+    if (!p || n == 0) return;
+    const size_t head = ((16 - reinterpret_cast<uintptr_t>(p) % 16) % 16) / 4;  // words before a 16-byte boundary
+    const size_t h = head < n ? head : n;
+    const size_t chunks = (n - h) / 4;
+    uint4 *body = reinterpret_cast<uint4 *>(p + h);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < chunks; i += (size_t)gridDim.x * blockDim.x)
+        body[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x == 0 && threadIdx.x < 8) {
+        const size_t t = h + chunks * 4;  // first word of the tail
+        if (threadIdx.x < h) p[threadIdx.x] = 0.f;
+        if (t + threadIdx.x < n && threadIdx.x < 4) p[t + threadIdx.x] = 0.f;
+    }
+}
+}  // namespace
+
+cudaError_t gs_launch_zero_grads(const gs_gaussians &g, const gs_grads &out, float *d_rec, size_t rec_words,
+                                 cudaStream_t s) {
+    const size_t n = g.n > 0 ? (size_t)g.n : 0, kS = (size_t)(g.sh_degree + 1) * (g.sh_degree + 1) * 3;
+    ZeroSpans z{{out.d_means, out.d_log_scales, out.d_quats, out.d_opacity_logits, out.d_sh, d_rec},
+                {n * 3, n * 3, n * 4, n, n * kS, rec_words}};
+    for (int i = 0; i < 6; ++i)
+        if (reinterpret_cast<uintptr_t>(z.ptr[i]) % 4 != 0) return cudaErrorInvalidValue;  // float arrays
+    zero_spans_kernel<<<dim3(152 * 4, 6, 1), 256, 0, s>>>(z);
+    return cudaGetLastError();
+}
+
 cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam, const GsGrid &grid,
                                   const float *d_rec, const gs_grads &out, cudaStream_t s) {
     if (g.n == 0) return cudaSuccess;
@@ -1838,16 +1924,10 @@ cudaError_t gs_launch_project_bwd(const gs_gaussians &g, const GsCameraDev &cam,
     B.d_quats = out.d_quats;
     B.d_logits = out.d_opacity_logits;
     B.d_sh = out.d_sh;
-    // Zeros first (every array is overwritten), then the Gaussians with
-    // gradients: measured faster than writing every Gaussian's gradients from
-    // one kernel (which wrote zeros at a fraction of the copy bandwidth).
-    const size_t n = (size_t)g.n, kS = (size_t)(g.sh_degree + 1) * (g.sh_degree + 1) * 3;
-    cudaError_t e = cudaMemsetAsync(out.d_means, 0, n * 3 * sizeof(float), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(out.d_log_scales, 0, n * 3 * sizeof(float), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(out.d_quats, 0, n * 4 * sizeof(float), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(out.d_opacity_logits, 0, n * sizeof(float), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(out.d_sh, 0, n * kS * sizeof(float), s);
-    if (e != cudaSuccess) return e;
+    // The arrays hold zeros already (gs_launch_zero_grads); only the
+    // Gaussians with gradients are written: measured faster than writing
+    // every Gaussian's gradients from one kernel (which wrote zeros at a
+    // fraction of the copy bandwidth).
     const unsigned blocks = (unsigned)((g.n + 127) / 128);
     switch (g.sh_degree) {
         case 0: project_bwd_sparse_kernel<0><<<blocks, 128, 0, s>>>(B); break;
