@@ -340,11 +340,13 @@ def _autograd_function():
             out = {"rgb": torch.empty((H, W, 3), dtype=torch.float32, device=means.device),
                    "final_T": torch.empty((H, W), dtype=torch.float32, device=means.device),
                    "n_contrib": torch.empty((H, W), dtype=torch.int32, device=means.device)}
-            gs_render(ctx, g, sh_degree, cam, out["rgb"], out["final_T"], out["n_contrib"], None,
-                      tile=tile, bg=bg, deferred=deferred, record_dtype=record_dtype, cluster=cluster,
-                      list_tiles=list_tiles)
-            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, list_tiles,
-                       gs_last_frame_id(ctx))
+            # The C structs are built once and kept for the backward.
+            gs_s, c = gaussians_struct(g, sh_degree), camera_struct(cam)
+            o = options_struct(tile, bg, record_dtype, 0, deferred, 0, cluster, list_tiles)
+            fb = _fb(out["rgb"], out["final_T"], out["n_contrib"], None)
+            ctx.check(_lib().gs_render(ctx.handle, ctypes.byref(gs_s), ctypes.byref(c), ctypes.byref(o),
+                                       ctypes.byref(fb), _stream(None)))
+            fctx.gs = (ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, list_tiles, gs_s, c, o)
             fctx.save_for_backward(out["final_T"], out["n_contrib"])
             fctx.mark_non_differentiable(out["final_T"])
             fctx.set_materialize_grads(False)  # no zero tensor for the non-differentiable final_T
@@ -354,19 +356,30 @@ def _autograd_function():
         def backward(fctx, d_rgb, d_T):
             if d_rgb is None:
                 return (None,) * 14
-            ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, list_tiles, frame = fctx.gs
+            ctx, cam, sh_degree, tile, bg, g, record_dtype, deferred, cluster, list_tiles, gs_s, c, o = fctx.gs
             final_T, n_contrib = fctx.saved_tensors
-            if gs_last_frame_id(ctx) != frame:
+            grads = {k: torch.empty_like(v) for k, v in g.items()}
+            gr = N.gs_grads()
+            gr.d_means, gr.d_log_scales, gr.d_quats = (grads["means"].data_ptr(), grads["log_scales"].data_ptr(),
+                                                       grads["quats"].data_ptr())
+            gr.d_opacity_logits, gr.d_sh = grads["opacity_logits"].data_ptr(), grads["sh"].data_ptr()
+            d = d_rgb.contiguous()
+
+            def differentiate(T, nc):
+                fb = _fb(None, T, nc, None)
+                return _lib().gs_render_backward(ctx.handle, ctypes.byref(gs_s), ctypes.byref(c), ctypes.byref(o),
+                                                 ctypes.byref(fb), d.data_ptr(), ctypes.byref(gr), _stream(None))
+
+            st = differentiate(final_T, n_contrib)
+            if st == N.GS_ERR_INVALID_ARG:
                 # Another frame was rendered on the context since this one
-                # (e.g. several views before one backward): render this frame
-                # again, which gives the same lists, final_T and n_contrib.
+                # (e.g. several views before one backward), which the call
+                # refuses: render this frame again (the same lists, final_T
+                # and n_contrib) and differentiate that.
                 redo = render(ctx, g, sh_degree, cam, tile=tile, bg=bg, aux=True, record_dtype=record_dtype,
                               deferred=deferred, cluster=cluster, list_tiles=list_tiles)
-                final_T, n_contrib = redo["final_T"], redo["n_contrib"]
-            grads = {k: torch.empty_like(v) for k, v in g.items()}
-            gs_render_backward(ctx, g, sh_degree, cam, final_T, n_contrib, d_rgb.contiguous(), grads,
-                               tile=tile, bg=bg, record_dtype=record_dtype, cluster=cluster,
-                               list_tiles=list_tiles)
+                st = differentiate(redo["final_T"], redo["n_contrib"])
+            ctx.check(st)
             return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
                     grads["sh"], None, None, None, None, None, None, None, None, None)
 

@@ -742,6 +742,20 @@ __device__ __forceinline__ void blend_listtile_tile(const BlendArgs &a, int tx, 
     bool warp_done = all_done_x2(L.P);
     uint32_t next = first;
     int rd_ = 0;
+    // The list reads run ahead of the rounds that use them: a thread holds
+    // its entry of the round being filled (gi0) with that entry's tile range
+    // (r0), and its entry of the next round (gi1); each round issues the next
+    // round's range load and the value load two rounds ahead, so neither
+    // waits in the round (nor in the blend) that follows. An entry past the
+    // list has range (0, 0), which no tile holds.
+    uint32_t gi0 = 0, gi1 = 0;
+    uint2 r0 = make_uint2(0u, 0u);
+    {
+        const uint32_t k0 = first + (uint32_t)tid, k1 = k0 + kThreads;
+        if (k0 < last) gi0 = a.values[k0];
+        if (k1 < last) gi1 = a.values[k1];
+        if (k0 < last) r0 = __ldg(a.rd.rect16 + gi0);
+    }
     while (next < last) {
         if (__syncthreads_count(warp_done) == kThreads) break;
         // Fill the batch: rounds of kThreads list entries, the kept ones
@@ -749,14 +763,14 @@ __device__ __forceinline__ void blend_listtile_tile(const BlendArgs &a, int tx, 
         int cnt = 0;
         while (next < last && cnt <= DEPTH - kThreads) {
             const uint32_t k = next + (uint32_t)tid;
-            bool keep = false;
-            uint32_t gi = 0;
-            if (k < last) {
-                gi = a.values[k];
-                const uint2 r = __ldg(a.rd.rect16 + gi);
-                keep = (uint32_t)tx >= (r.x & 0xffffu) && (uint32_t)tx < (r.x >> 16) &&
-                       (uint32_t)ty >= (r.y & 0xffffu) && (uint32_t)ty < (r.y >> 16);
-            }
+            const uint32_t gi = gi0;
+            const uint2 r = r0;
+            const uint32_t k1 = k + kThreads, k2 = k1 + kThreads;
+            r0 = k1 < last ? __ldg(a.rd.rect16 + gi1) : make_uint2(0u, 0u);
+            gi0 = gi1;
+            gi1 = k2 < last ? a.values[k2] : 0u;
+            const bool keep = (uint32_t)tx >= (r.x & 0xffffu) && (uint32_t)tx < (r.x >> 16) &&
+                              (uint32_t)ty >= (r.y & 0xffffu) && (uint32_t)ty < (r.y >> 16);
             const uint32_t ballot = __ballot_sync(0xffffffffu, keep);
             if (lane == 0) s_wcnt[rd_][warp] = __popc(ballot);
             __syncthreads();
