@@ -1494,6 +1494,10 @@ gs_status gs_render_batch(gs_context *ctx, const gs_gaussians *g, const gs_camer
         o.sync_mode = GS_SYNC_FRAME;
         o.temporal = 0;
         o.batch_mode = GS_BATCH_AUTO;
+        // Each view has its own framebuffer: more views than the context
+        // keeps frame graphs would capture every frame, so they launch
+        // directly.
+        if (n_views > gs_context::kGraphs) o.direct_launch = 1;
         int64_t keys = 0, visible = 0, tiles = 0;
         for (int v = 0; v < n_views; ++v) {
             if ((st = gs_render(ctx, g, &cams[v], &o, &fbs[v], stream)) != GS_OK) return st;
