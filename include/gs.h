@@ -367,7 +367,9 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
  * mode have graphs of their own). Frames with stage timing on
  * (gs_set_stage_timing), with GS_BLEND_TMA or with direct_launch = 1 launch
  * the kernels directly, and so does a context after four captures in a row
- * (for its next 32 frames). Results are the same either way. */
+ * (for its next 32 frames, doubling up to 1024 while captures keep missing,
+ * e.g. a loop over more views than the context keeps graphs for). Results
+ * are the same either way. */
 /* Temporal re-binning (opts->temporal = 1 or 2; the paper's temporal-
  * locality idea, Sec. 5.4 and Sec. 6): when the previous frame on this
  * context was rendered the same way with the same Gaussian count and tile

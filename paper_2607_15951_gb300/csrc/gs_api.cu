@@ -51,9 +51,11 @@ struct gs_context {
     // are kept (least recently used replaced), so frames that alternate
     // framebuffers or scenes still replay. buf_gen counts the reallocations
     // of the context's buffers. After kGraphMissRun captures in a row the
-    // next kGraphSkip frames launch directly.
+    // next graph_skip_len frames launch directly (32 at first, doubling up to
+    // 1024 while the pattern repeats, back to 32 after a replay).
     uint64_t buf_gen = 0;
-    static constexpr int kGraphs = 8, kGraphMissRun = 4, kGraphSkip = 32;
+    static constexpr int kGraphs = 8, kGraphMissRun = 4, kGraphSkip = 32, kGraphSkipMax = 1024;
+    int graph_skip_len = kGraphSkip;
     struct FrameGraph {
         bool valid = false;
         uint64_t last_use = 0;
@@ -670,8 +672,8 @@ bool frame_graph_fits(const gs_context *ctx, const gs_context::FrameGraph &F, in
 // projection's launch; otherwise the least recently used slot captures the
 // frame's launches (on the context's own stream, so nothing runs) first. A
 // context whose frames keep missing (kGraphMissRun captures in a row)
-// launches the next kGraphSkip frames directly. enqueue(q) issues the frame's
-// launches on q and sets *sv.
+// launches its next graph_skip_len frames directly. enqueue(q) issues the
+// frame's launches on q and sets *sv.
 template <class Enqueue>
 gs_status replay_frame(gs_context *ctx, int kind, const void *const extra[8], const gs_gaussians *g,
                        const gs_camera *cam, const gs_options *opts, const gs_framebuffer *fb, int64_t cap,
@@ -687,10 +689,12 @@ gs_status replay_frame(gs_context *ctx, int kind, const void *const extra[8], co
     }
     if (F) {
         ctx->graph_miss_run = 0;
+        ctx->graph_skip_len = gs_context::kGraphSkip;
     } else {
         if (++ctx->graph_miss_run >= gs_context::kGraphMissRun) {
             ctx->graph_miss_run = 0;
-            ctx->graph_skip = gs_context::kGraphSkip;
+            ctx->graph_skip = ctx->graph_skip_len;
+            ctx->graph_skip_len = std::min(2 * ctx->graph_skip_len, gs_context::kGraphSkipMax);
             return enqueue(s);
         }
         F = lru;

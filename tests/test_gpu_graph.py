@@ -105,3 +105,24 @@ def test_backward_of_a_replayed_frame(ctxs):
     for k in res[0]:
         a, b = res[0][k], res[1][k]
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()) + 1e-12), k
+
+
+def test_frames_cycling_over_more_framebuffers_than_graphs(ctxs):
+    """Twelve framebuffers in turn (more than the context keeps graphs for):
+    captures miss, the context switches to direct launches for a while, tries
+    again; every frame still equals a directly launched one."""
+    _, direct_ctx = ctxs
+    scene = scenes.clustered(20_000, 55, box=5.0)
+    g = gs.scene_to_device(scene)
+    cams = scenes.trajectory(12, 1055, radius=2.0, sizes=((160, 96),))
+    c = gs.Context(0)
+    outs = gs.alloc_outputs(cams, aux=True)
+    refs = [gs.render(direct_ctx, g, scene.sh_degree, cam, direct=True) for cam in cams]
+    for i in range(60):
+        v = i % len(cams)
+        o = outs[v]
+        gs.gs_render(c, g, scene.sh_degree, cams[v], o["rgb"], o["final_T"], o["n_contrib"], o["n_eval"],
+                     deferred=bool(i % 3))
+        gs.gs_sync_status(c)
+        _equal(o, refs[v])
+    c.close()
