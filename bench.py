@@ -619,7 +619,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-temporal", action="store_true")
     ap.add_argument("--no-imbalance", action="store_true")
-    ap.add_argument("--frames-in-flight", type=int, default=8,
+    ap.add_argument("--frames-in-flight", type=int, default=16,
                     help="consecutive frames rendered on this many contexts / streams at once (headline value)")
     ap.add_argument("--pipeline-blend-variant", type=int, default=0,
                     help="blend schedule of the frames-in-flight loop (0: the default, 8x8 blocks in packed pairs)")

@@ -134,10 +134,12 @@ def test_frames_in_flight_on_several_contexts_and_streams(built):
 
 def test_frames_in_flight_full_size_as_benchmarked(built):
     """The throughput configuration at full size: the 1M-Gaussian 1080p frame
-    rendered deferred on eight contexts, each on its own stream, with the
-    8x8-block blend and the inputs rotating over copies of the scene; every
-    frame equals the synchronous default render of the same frame bit for
-    bit (and that render is checked against the FP64 oracle elsewhere)."""
+    rendered deferred on sixteen contexts, each on its own stream, with 4x4
+    list tiles in grid tile order and the inputs rotating over copies of the
+    scene (and, with eight contexts, the 8x8-block blend with a list per
+    tile); every frame equals the synchronous default render of the same
+    frame bit for bit (and that render is checked against the FP64 oracle
+    elsewhere)."""
     scene, cams = scenes.workload("clustered_1m_1080p")
     cam = cams[0]
     g = gs.scene_to_device(scene)
@@ -146,30 +148,32 @@ def test_frames_in_flight_full_size_as_benchmarked(built):
     ref = gs.render(ref_ctx, g, scene.sh_degree, cam)
     torch.cuda.synchronize()
     gs.gs_sync_status(ref_ctx)
-    F, frames = 8, 16
-    ctxs = [gs.Context(0) for _ in range(F)]
-    streams = [torch.cuda.Stream() for _ in range(F)]
-    for c in ctxs:  # warm-up frame per context, as the benchmark does
-        gs.render(c, g, scene.sh_degree, cam, aux=False, variant=4)
-    torch.cuda.synchronize()
-    H, W = cam.height, cam.width
-    outs = [{"rgb": torch.empty((H, W, 3), device="cuda"),
-             "final_T": torch.empty((H, W), device="cuda"),
-             "n_contrib": torch.empty((H, W), dtype=torch.int32, device="cuda")} for _ in range(frames)]
-    start = torch.cuda.Event()
-    start.record()
-    for s in streams:
-        s.wait_event(start)
-    for i, o in enumerate(outs):
-        k = i % F
-        with torch.cuda.stream(streams[k]):
-            gs.gs_render(ctxs[k], copies[i % len(copies)], scene.sh_degree, cam, o["rgb"], o["final_T"],
-                         o["n_contrib"], variant=4, deferred=True, stream=streams[k])
-    torch.cuda.synchronize()
-    for c in ctxs:
-        gs.gs_sync_status(c)
-        c.close()
-    for o in outs:
-        for key in ("rgb", "final_T", "n_contrib"):
-            assert torch.equal(ref[key], o[key]), key
+    for F, frames, opt in ((16, 32, dict(list_tiles=16, tile_order=1)), (8, 16, dict(variant=4))):
+        ctxs = [gs.Context(0) for _ in range(F)]
+        streams = [torch.cuda.Stream() for _ in range(F)]
+        for c in ctxs:  # warm-up frame per context, as the benchmark does
+            gs.render(c, g, scene.sh_degree, cam, aux=False, **opt)
+        torch.cuda.synchronize()
+        H, W = cam.height, cam.width
+        outs = [{"rgb": torch.empty((H, W, 3), device="cuda"),
+                 "final_T": torch.empty((H, W), device="cuda"),
+                 "n_contrib": torch.empty((H, W), dtype=torch.int32, device="cuda")} for _ in range(frames)]
+        start = torch.cuda.Event()
+        start.record()
+        for s in streams:
+            s.wait_event(start)
+        for i, o in enumerate(outs):
+            k = i % F
+            with torch.cuda.stream(streams[k]):
+                gs.gs_render(ctxs[k], copies[i % len(copies)], scene.sh_degree, cam, o["rgb"], o["final_T"],
+                             o["n_contrib"], deferred=True, stream=streams[k], **opt)
+        torch.cuda.synchronize()
+        for c in ctxs:
+            gs.gs_sync_status(c)
+            c.close()
+        for o in outs:
+            assert torch.equal(ref["rgb"], o["rgb"]) and torch.equal(ref["final_T"], o["final_T"]), (F, opt)
+            if "list_tiles" not in opt:  # list-tile frames count list-tile positions
+                assert torch.equal(ref["n_contrib"], o["n_contrib"]), (F, opt)
+        del outs
     ref_ctx.close()
