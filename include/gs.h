@@ -365,8 +365,8 @@ gs_status gs_blend(gs_context *ctx, const gs_record *records, const uint32_t *va
  * issue about twenty calls. The context keeps eight such graphs (frames that
  * alternate framebuffers or scenes replay too; re-binned frames of temporal
  * mode have graphs of their own). Frames with stage timing on
- * (gs_set_stage_timing), with GS_BLEND_TMA or with direct_launch = 1 launch
- * the kernels directly, and so does a context after four captures in a row
+ * (gs_set_stage_timing), with GS_BLEND_TMA, with direct_launch = 1 or on a
+ * stream the caller is capturing launch the kernels directly, and so does a context after four captures in a row
  * (for its next 32 frames, doubling up to 1024 while captures keep missing,
  * e.g. a loop over more views than the context keeps graphs for). Results
  * are the same either way. */

@@ -682,6 +682,12 @@ gs_status replay_frame(gs_context *ctx, int kind, const void *const extra[8], co
         --ctx->graph_skip;
         return enqueue(s);
     }
+    // A caller capturing its own graph on s gets the launches themselves.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        (void)cudaGetLastError();
+        return enqueue(s);
+    }
     gs_context::FrameGraph *F = nullptr, *lru = &ctx->fg[0];
     for (auto &c : ctx->fg) {
         if (frame_graph_fits(ctx, c, kind, extra, g, cam, opts, fb, cap, variant)) F = &c;
