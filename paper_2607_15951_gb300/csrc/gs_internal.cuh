@@ -9,7 +9,7 @@
 #include "../../include/gs.h"
 
 // Shared-memory carveout preference for the kernels of the render path
-// (-1: leave the driver's choice).
+// (-1: leave the CUDA runtime's default).
 #ifndef GS_CARVEOUT
 #define GS_CARVEOUT -1
 #endif
